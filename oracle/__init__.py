@@ -1,0 +1,175 @@
+"""FP64 CPU oracle: Python entry points over ``pndf_oracle.c``.
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg use this package.  It imports nothing from the
+CUDA package and the CUDA package imports nothing from it.
+
+Functions
+---------
+pndf(st, queries)          -> D (float64), flags (uint32), hits (int64), hit_hash (uint32)
+projarea(st, queries, w)   -> P (float64)
+tri_integral(n0, n1, n2, w) -> integral of max(m~.w, 0)/m~_z over one normal triangle
+
+``st`` is an (N, N, 2) array (texel (i, j) at ``st[j, i]``); ``queries`` an
+(n, >=7) array of (x, y, sxx, sxy, syy, ms, mt).  Inputs are converted to
+float64 exactly.  Work is split over host threads by query range (ctypes
+releases the GIL during each call).
+
+Flag bits (per query): 1 near an edge (1e-6 in normal space), 2 a hit within
+1e-4 of the q = 16 cut, 4 near a zero-area triangle, 8 a hit on a triangle of
+normal-space area < 1e-10, 16 invalid covariance.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pndf_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+
+F_NEAR_EDGE = 1
+F_NEAR_CUT = 2
+F_DEGENERATE = 4
+F_TINY = 8
+F_INVALID = 16
+F_EXCLUDE = F_NEAR_EDGE | F_NEAR_CUT | F_DEGENERATE | F_INVALID
+
+_lock = threading.Lock()
+_default = None
+
+
+def build(force: bool = False, src: str = _SRC, out: str = _SO) -> str:
+    """Compile the oracle with gcc (no FP contraction, so x86 and Arm agree)."""
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src):
+        tmp = out + f".tmp{os.getpid()}"
+        subprocess.run(["gcc", "-O2", "-std=c99", "-D_GNU_SOURCE", "-ffp-contract=off", "-fno-fast-math",
+                        "-shared", "-fPIC", "-o", tmp, src, "-lm"], check=True)
+        os.replace(tmp, out)
+    return out
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(ctypes.POINTER(t))
+
+
+def _as_map(st) -> np.ndarray:
+    st = np.asarray(st.cpu() if hasattr(st, "cpu") else st)
+    assert st.ndim == 3 and st.shape[0] == st.shape[1] and st.shape[2] == 2, st.shape
+    return np.ascontiguousarray(st, dtype=np.float64)
+
+
+def _as_queries(q) -> np.ndarray:
+    q = np.asarray(q.cpu() if hasattr(q, "cpu") else q)
+    return np.ascontiguousarray(q[:, :7], dtype=np.float64)
+
+
+def default_threads() -> int:
+    return max(1, os.cpu_count() or 1)
+
+
+def _chunks(n, threads, min_chunk=16):
+    nchunks = max(1, min(threads * 8, (n + min_chunk - 1) // min_chunk))
+    edges = np.linspace(0, n, nchunks + 1).astype(np.int64)
+    return [(int(a), int(b)) for a, b in zip(edges[:-1], edges[1:]) if b > a]
+
+
+class Oracle:
+    """The oracle bound to one compiled library (the default build, or a
+    deliberately altered copy in the mutation tests)."""
+
+    F_NEAR_EDGE = F_NEAR_EDGE
+    F_NEAR_CUT = F_NEAR_CUT
+    F_DEGENERATE = F_DEGENERATE
+    F_TINY = F_TINY
+    F_INVALID = F_INVALID
+    F_EXCLUDE = F_EXCLUDE
+
+    def __init__(self, so_path: str):
+        lib = ctypes.CDLL(so_path)
+        dp = ctypes.POINTER(ctypes.c_double)
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        lib.oracle_pndf.argtypes = [dp, ctypes.c_int, dp, ctypes.c_int64, ctypes.c_int64, dp, u32p, i64p, u32p]
+        lib.oracle_pndf.restype = None
+        lib.oracle_projarea.argtypes = [dp, ctypes.c_int, dp, dp, ctypes.c_int64, ctypes.c_int64, dp]
+        lib.oracle_projarea.restype = None
+        lib.oracle_tri_integral.argtypes = [ctypes.c_double] * 9
+        lib.oracle_tri_integral.restype = ctypes.c_double
+        self.lib = lib
+
+    def pndf(self, st, queries, threads: int | None = None):
+        lib = self.lib
+        stm = _as_map(st)
+        q = _as_queries(queries)
+        n = q.shape[0]
+        D = np.zeros(n, np.float64)
+        flags = np.zeros(n, np.uint32)
+        hits = np.zeros(n, np.int64)
+        hh = np.zeros(n, np.uint32)
+        N = stm.shape[0]
+
+        def run(r):
+            lib.oracle_pndf(_ptr(stm, ctypes.c_double), N, _ptr(q, ctypes.c_double), r[0], r[1],
+                            _ptr(D, ctypes.c_double), _ptr(flags, ctypes.c_uint32),
+                            _ptr(hits, ctypes.c_int64), _ptr(hh, ctypes.c_uint32))
+
+        threads = threads or default_threads()
+        if n:
+            with ThreadPoolExecutor(max_workers=threads) as ex:
+                list(ex.map(run, _chunks(n, threads)))
+        return D, flags, hits, hh
+
+    def projarea(self, st, queries, omega, threads: int | None = None):
+        lib = self.lib
+        stm = _as_map(st)
+        q = _as_queries(queries)
+        w = np.ascontiguousarray(np.asarray(omega.cpu() if hasattr(omega, "cpu") else omega)[:, :3],
+                                 dtype=np.float64)
+        n = q.shape[0]
+        assert w.shape[0] == n
+        P = np.zeros(n, np.float64)
+        N = stm.shape[0]
+
+        def run(r):
+            lib.oracle_projarea(_ptr(stm, ctypes.c_double), N, _ptr(q, ctypes.c_double),
+                                _ptr(w, ctypes.c_double), r[0], r[1], _ptr(P, ctypes.c_double))
+
+        threads = threads or default_threads()
+        if n:
+            with ThreadPoolExecutor(max_workers=threads) as ex:
+                list(ex.map(run, _chunks(n, threads, 4)))
+        return P
+
+    def tri_integral(self, n0, n1, n2, w) -> float:
+        return float(self.lib.oracle_tri_integral(float(n0[0]), float(n0[1]), float(n1[0]), float(n1[1]),
+                                                  float(n2[0]), float(n2[1]),
+                                                  float(w[0]), float(w[1]), float(w[2])))
+
+
+def _get() -> Oracle:
+    global _default
+    with _lock:
+        if _default is None:
+            _default = Oracle(build())
+    return _default
+
+
+def pndf(st, queries, threads: int | None = None):
+    return _get().pndf(st, queries, threads)
+
+
+def projarea(st, queries, omega, threads: int | None = None):
+    return _get().projarea(st, queries, omega, threads)
+
+
+def tri_integral(n0, n1, n2, w) -> float:
+    return _get().tri_integral(n0, n1, n2, w)

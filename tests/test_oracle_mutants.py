@@ -1,0 +1,72 @@
+"""The pins are strong enough: each plausible mistake, planted in a copy of
+the oracle source and compiled on the CPU, makes at least one pin fail.
+
+The mistakes are ones a reader of the paper could make: the other quad
+diagonal (Eq. 3), a signed or halved Jacobian (Eq. 4), the barycentric roles
+swapped when mapping back to uv (Eq. 5), the footprint covariance or
+normalisation wrong, the printed "+" of Eq. 11's line term, the "d_x"
+projection cosine of App. B, a reversed arc, a wrong clip root (Alg. 1) and a
+misplaced per-triangle kernel sample.
+"""
+
+import os
+
+import pytest
+
+import oracle
+import test_oracle_pins as pins  # noqa: E402
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "pndf_oracle.c")
+
+PNDF_PINS = [pins.test_affine_closed_form, pins.test_mass_invariant, pins.test_binning_converges,
+             pins.test_transpose_symmetry]
+AREA_PINS = [pins.test_stokes_matches_area_quadrature, pins.test_projarea_normal_incidence_is_shoelace,
+             pins.test_projarea_uv_form]
+
+MUTANTS = {
+    "other_diagonal": (
+        [("ax = i; ay = j; bx = i + 1; by = j; cx = i; cy = j + 1;\n                    na = n0; nb = n1; nc = n2;",
+          "ax = i; ay = j; bx = i + 1; by = j; cx = i + 1; cy = j + 1;\n                    na = n0; nb = n1; nc = n3;"),
+         ("ax = i + 1; ay = j + 1; bx = i; by = j + 1; cx = i + 1; cy = j;\n                    na = n3; nb = n2; nc = n1;",
+          "ax = i + 1; ay = j + 1; bx = i; by = j + 1; cx = i; cy = j;\n                    na = n3; nb = n2; nc = n0;")],
+        PNDF_PINS),
+    "signed_jacobian": ([("double J = fabs(A2);", "double J = A2;")], PNDF_PINS),
+    "area_not_twice_area": ([("D += norm * exp(-0.5 * q) / J;", "D += norm * exp(-0.5 * q) / (0.5 * J);")], PNDF_PINS),
+    "bary_roles_swapped": ([("double ux = ax * l0 + bx * l1 + cx * l2;", "double ux = ax * l0 + bx * l2 + cx * l1;"),
+                            ("double uy = ay * l0 + by * l1 + cy * l2;", "double uy = ay * l0 + by * l2 + cy * l1;")],
+                           PNDF_PINS),
+    "inverse_cov_sign": ([("double ia = syy / det, ib = -sxy / det, ic = sxx / det;\n    double norm = 1.0 / (2.0 * M_PI * sqrt(det));\n    int i0, i1, j0, j1;\n    quad_range(N, x, y, sxx, syy, &i0, &i1, &j0, &j1);\n    double D = 0.0;",
+                           "double ia = syy / det, ib = sxy / det, ic = sxx / det;\n    double norm = 1.0 / (2.0 * M_PI * sqrt(det));\n    int i0, i1, j0, j1;\n    quad_range(N, x, y, sxx, syy, &i0, &i1, &j0, &j1);\n    double D = 0.0;")],
+                         PNDF_PINS),
+    "kernel_missing_2pi": ([("double norm = 1.0 / (2.0 * M_PI * sqrt(det));\n    int i0, i1, j0, j1;\n    quad_range(N, x, y, sxx, syy, &i0, &i1, &j0, &j1);\n    double D = 0.0;",
+                             "double norm = 1.0 / (sqrt(det));\n    int i0, i1, j0, j1;\n    quad_range(N, x, y, sxx, syy, &i0, &i1, &j0, &j1);\n    double D = 0.0;")],
+                           PNDF_PINS),
+    "line_term_plus_sign": ([("return tz - tx;", "return tz + tx;")], AREA_PINS),
+    "projection_cosine_dx": ([("double tx = 0.5 * wx * r2 * dy *", "double tx = 0.5 * wx * r2 * dx *")], AREA_PINS),
+    "arc_reversed": ([("return 0.5 * (Fasin(e[1]) - Fasin(s[1]));", "return 0.5 * (Fasin(s[1]) - Fasin(e[1]));")],
+                     AREA_PINS),
+    "clip_start_uses_t1": ([("oa[0] = a[0] * (1.0 - t0) + b[0] * t0;\n            oa[1] = a[1] * (1.0 - t0) + b[1] * t0;",
+                             "oa[0] = a[0] * (1.0 - t1) + b[0] * t1;\n            oa[1] = a[1] * (1.0 - t1) + b[1] * t1;")],
+                           AREA_PINS),
+    "kernel_at_wrong_centroid": ([("double gx = i + (tri == 0 ? 1.0 / 3.0 : 2.0 / 3.0) - x;",
+                                   "double gx = i + (tri == 0 ? 2.0 / 3.0 : 1.0 / 3.0) - x;")], AREA_PINS),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name, tmp_path):
+    edits, which = MUTANTS[name]
+    src = open(SRC).read()
+    for old, new in edits:
+        assert src.count(old) == 1, (name, old)
+        src = src.replace(old, new)
+    path = tmp_path / f"{name}.c"
+    path.write_text(src)
+    mutant = oracle.Oracle(oracle.build(force=True, src=str(path), out=str(tmp_path / f"{name}.so")))
+    caught = []
+    for pin in which:
+        try:
+            pin(mutant)
+        except AssertionError:
+            caught.append(pin.__name__)
+    assert caught, f"no pin caught mutant {name}"
