@@ -1,0 +1,210 @@
+/*
+ * pndf.h - C ABI of the GB300 P-NDF library (libpndf.so).
+ *
+ * Position-normal manifold P-NDF evaluation (Wu, Luan, Hasan, Ramamoorthi,
+ * "Position-Normal Manifold for Efficient Glint Rendering on High-Resolution
+ * Normal Maps", Sec. 4) and the analytic projected-area integral (Sec. 4.3,
+ * App. B).  Every function here is host-callable C; no C++ or framework type
+ * crosses this boundary.  All compute runs in CUDA kernels for sm_103a.
+ *
+ * Conventions shared by every entry point
+ *   - Texel u = (i, j) of an N x N normal map sits at element j*N + i
+ *     (row-major, i along x).  Its value is the projected-hemisphere normal
+ *     n = (s, t) (Sec. 3, Eq. 2).  Positions are unnormalised texel units
+ *     (Tab. 1).
+ *   - Quad (i, j), 0 <= i, j <= N-2, is split along the u1-u2 diagonal into
+ *     a lower triangle (u0, u1, u2) and an upper triangle (u3, u2, u1)
+ *     (Eq. 3).  Triangle id = 2 * (j*(N-1) + i) + (0 lower | 1 upper).
+ *   - The footprint kernel k_r is the Gaussian exp(-q/2) / (2 pi sqrt(det S))
+ *     with q = d^T S^-1 d, cut to zero where q > 16 (the 4-sigma ellipse),
+ *     not renormalised.  The map is not periodic.
+ *   - "stream" is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are asynchronous on that stream.  Argument errors are
+ *     returned synchronously; device-side errors (invalid query, capacity)
+ *     set a per-device status word read by pndf_device_status().
+ *   - Buffers named *_dev are device pointers owned by the caller; the
+ *     library never frees them and reads/writes them only within the call's
+ *     stream order.  Hierarchies are library-owned device memory.
+ *   - Thread safety: distinct streams may call concurrently.  A hierarchy is
+ *     immutable after its build completes, so concurrent evaluations on it
+ *     are safe; it must not be freed while work on it is in flight.
+ */
+#ifndef PNDF_H
+#define PNDF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pndf_hierarchy pndf_hierarchy;
+
+typedef enum pndf_status {
+    PNDF_OK = 0,
+    PNDF_ERR_INVALID_ARG = 1,  /* bad pointer, size, format or parameter            */
+    PNDF_ERR_OOM = 2,          /* device allocation failed                          */
+    PNDF_ERR_CUDA = 3,         /* a CUDA runtime call failed                        */
+    PNDF_ERR_TIMEOUT = 4,      /* a bounded device-side wait ran out                */
+    PNDF_ERR_CAPACITY = 5,     /* a fixed-size device buffer would overflow         */
+    PNDF_ERR_UNSUPPORTED = 6,  /* valid request this build does not implement       */
+    PNDF_ERR_DEVICE = 7        /* pndf_device_status: a kernel recorded an error     */
+} pndf_status;
+
+typedef enum pndf_texel_fmt {
+    PNDF_TEXEL_F32X2 = 0,      /* float  (s, t) pairs, 8 bytes per texel            */
+    PNDF_TEXEL_F16X2 = 1       /* binary16 (s, t) pairs, 4 bytes per texel           */
+} pndf_texel_fmt;
+
+typedef enum pndf_bounds_fmt {
+    PNDF_BOUNDS_F32 = 0,           /* exact float32 min/max per node (16 B)         */
+    PNDF_BOUNDS_F16_OUTWARD = 1    /* binary16 min rounded down, max rounded up (8 B) */
+} pndf_bounds_fmt;
+
+typedef struct pndf_build_params {
+    int32_t n;           /* texels per side, 2 <= n <= 16384                      */
+    int32_t texel_fmt;   /* pndf_texel_fmt                                        */
+    int32_t bounds_fmt;  /* pndf_bounds_fmt                                       */
+    int32_t leaf_level;  /* 0 = default (2): stored bottom level, 2^l x 2^l quads */
+} pndf_build_params;
+
+/* One P-NDF query, 32 bytes: footprint centre x = (x, y) in texels, the 2x2
+ * footprint covariance S = [[sxx, sxy], [sxy, syy]] in texel^2 (must be
+ * positive definite), and the query normal m = (ms, mt) (Eq. 2). */
+typedef struct pndf_query {
+    float x, y, sxx, sxy, syy, ms, mt, pad;
+} pndf_query;
+
+/* Optional per-query counters (32 bytes), written when stats_dev != NULL. */
+typedef struct pndf_query_stats {
+    uint32_t nodes;        /* hierarchy nodes tested                                 */
+    uint32_t leaf_blocks;  /* leaf blocks whose triangles were tested                */
+    uint32_t tri_tests;    /* triangles tested against m                             */
+    uint32_t hits;         /* contributing hits (m inside, q <= 16)                  */
+    uint32_t hit_hash;     /* sum mod 2^32 of MurmurHash3-fmix32(triangle id) over hits */
+    uint32_t fp64_tris;    /* triangles evaluated in FP64 (normal area < 1e-10)      */
+    uint32_t degenerate;   /* zero-area normal triangles met inside their bbox       */
+    uint32_t reserved;
+} pndf_query_stats;
+
+/* Per-query flag bits written to flags_out_dev. */
+#define PNDF_QF_FP64 1u       /* a triangle of normal-space area < 1e-10 was hit-tested in FP64 */
+#define PNDF_QF_INVALID 4u    /* covariance not positive definite: D = NaN                       */
+#define PNDF_QF_OVERFLOW 8u   /* traversal stack overflow: D incomplete (never expected)          */
+
+typedef enum pndf_eval_mode {
+    PNDF_MODE_HIERARCHY = 0,  /* min/max bound-pyramid traversal (Sec. 4.2)          */
+    PNDF_MODE_FLAT = 1        /* every leaf block in the footprint box, no pruning   */
+} pndf_eval_mode;
+
+typedef struct pndf_eval_config {
+    int32_t mode;           /* pndf_eval_mode                                         */
+    int32_t sort;           /* 1 = key queries by (entry level, tile) and sort first */
+    int32_t warps_per_cta;  /* 0 = library default                                   */
+    int32_t ctas_per_sm;    /* 0 = as many as fit                                    */
+} pndf_eval_config;
+
+/*
+ * Build the min/max normal-bound pyramid of a normal map (Sec. 4.2, Fig. 5a).
+ * A node at level l covers 2^l x 2^l quads; it stores the bounding box of the
+ * normals of all texels of its quads, so the normal triangles of every quad
+ * below it lie inside.  Levels leaf_level..L are stored (2^L >= N-1), each
+ * in Morton order so the four children of a node are contiguous; nodes
+ * without quads hold an empty box.  The texels are copied into the
+ * hierarchy (the caller may free texels_dev once the stream reaches the end
+ * of this call's work).  On success *out owns device memory until
+ * pndf_free_hierarchy().
+ *   texels_dev: device, N*N texels in params->texel_fmt, row-major.
+ * Errors: INVALID_ARG (null pointers, N out of range, unknown formats),
+ *         OOM, CUDA.
+ */
+pndf_status pndf_build_hierarchy(const void *texels_dev, const pndf_build_params *params,
+                                 void *stream, pndf_hierarchy **out);
+
+/* Release a hierarchy (synchronises its device memory release with the
+ * device; safe on NULL). */
+void pndf_free_hierarchy(pndf_hierarchy *h);
+
+/* Device bytes held by a hierarchy (texel copy + pyramid). */
+size_t pndf_hierarchy_bytes(const pndf_hierarchy *h);
+
+/*
+ * Batched P-NDF evaluation, Eq. 5 (the exact solution of Eq. 2):
+ *   D(m, x) = sum over triangles abc with m in n(abc) of
+ *             k_r(a l0 + b l1 + c l2 - x) / |(n_b - n_a) x (n_c - n_a)|,
+ *   (l0, l1, l2) = bary(m, n(abc)) (Tab. 1).
+ * The hit test is closed (all barycentrics >= 0, m inside the closed normal
+ * bounding box); zero-area normal triangles are skipped (a delta, not a
+ * density); triangles of normal-space area below 1e-10 are tested and
+ * weighted in FP64, all others in FP32.  The pyramid only prunes, so the set
+ * of contributing triangles equals that of the flat mode.
+ *   q_dev:          device, nq pndf_query records.
+ *   D_out_dev:      device, nq floats, caller order.
+ *   flags_out_dev:  device, nq uint32 (PNDF_QF_* bits) or NULL.
+ *   stats_dev:      device, nq pndf_query_stats or NULL.
+ * nq = 0 is valid and launches nothing.  Scratch memory for the key sort
+ * (about 6 bytes per query plus 64 KiB) is allocated stream-ordered from the
+ * device's default memory pool and released on the same stream.
+ * Errors: INVALID_ARG, OOM, CUDA.  Invalid queries give D = NaN and set
+ * PNDF_QF_INVALID (and the device status word).
+ */
+pndf_status pndf_eval_batch(const pndf_hierarchy *h, const pndf_query *q_dev, int64_t nq,
+                            float *D_out_dev, uint32_t *flags_out_dev, pndf_query_stats *stats_dev,
+                            void *stream);
+
+/* pndf_eval_batch with explicit mode, sorting and launch shape (cfg may be
+ * NULL for the defaults). */
+pndf_status pndf_eval_batch_ex(const pndf_hierarchy *h, const pndf_query *q_dev, int64_t nq,
+                               float *D_out_dev, uint32_t *flags_out_dev, pndf_query_stats *stats_dev,
+                               const pndf_eval_config *cfg, void *stream);
+
+/*
+ * End-to-end variant with HOST buffers: copies nq queries from q_host to the
+ * device, evaluates as pndf_eval_batch, and copies D back to D_host, all on
+ * stream; returns after the stream has completed the copy-back.  Pinned host
+ * memory gives full copy bandwidth; pageable memory works but is slower.
+ * Device staging (36 bytes per query) is allocated stream-ordered.
+ */
+pndf_status pndf_eval_batch_host(const pndf_hierarchy *h, const pndf_query *q_host, int64_t nq,
+                                 float *D_host, void *stream);
+
+/*
+ * Analytic projected area P(w) of each footprint (Eq. 9-11, App. B):
+ *   P(w) = sum over triangles T of k_r(T) / |(n_b - n_a) x (n_c - n_a)|
+ *          * integral over n+(T) of (w_x m~_x / m~_z + w_z) dm
+ * in the frame rotated so w_y = 0, with n+(T) the part of the normal
+ * triangle whose normals see w, clipped per Alg. 1 and integrated by
+ * Stokes (lines and ellipse arcs, Eq. 11, minus sign on the w_x line term).
+ * k_r(T) is the kernel at T's uv centroid (cut at q > 16).  Normal triangles
+ * with |cross| < 1e-12 use the collapse limit (1/2) max(n~.w, 0)/n~_z.  The
+ * aggregated diffuse BRDF is f_d = P / (pi w_z) (Eq. 13) and the
+ * shadow-masking Lambda = P / w_z - 1 (Sec. 4.3).
+ *   q_dev:     device, nq pndf_query (x, y, sxx, sxy, syy used; ms, mt ignored).
+ *   omega_dev: device, 3*nq floats, unit directions with w_z > 0.
+ *   P_out_dev: device, nq floats.
+ * Every triangle of the footprint is integrated (no pruning applies: every
+ * visible triangle contributes).  Large footprints are split into tiles whose
+ * partial sums are reduced in a fixed order.
+ * Errors: INVALID_ARG, OOM, CUDA.
+ */
+pndf_status pndf_diffuse_projected_area(const pndf_hierarchy *h, const pndf_query *q_dev,
+                                        const float *omega_dev, int64_t nq, float *P_out_dev,
+                                        void *stream);
+
+/* Read and clear the per-device status word that kernels set on device-side
+ * errors (synchronises stream).  PNDF_OK if none; PNDF_ERR_DEVICE otherwise,
+ * with the raw PNDF_QF_* bits in *bits_out when bits_out != NULL. */
+pndf_status pndf_device_status(void *stream, uint32_t *bits_out);
+
+/* Static, human-readable name of a status code. */
+const char *pndf_status_string(pndf_status s);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int32_t pndf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PNDF_H */

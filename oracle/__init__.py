@@ -41,6 +41,7 @@ F_DEGENERATE = 4
 F_TINY = 8
 F_INVALID = 16
 F_EXCLUDE = F_NEAR_EDGE | F_NEAR_CUT | F_DEGENERATE | F_INVALID
+GL_POINTS = 16
 
 _lock = threading.Lock()
 _default = None
@@ -100,7 +101,8 @@ class Oracle:
         i64p = ctypes.POINTER(ctypes.c_int64)
         lib.oracle_pndf.argtypes = [dp, ctypes.c_int, dp, ctypes.c_int64, ctypes.c_int64, dp, u32p, i64p, u32p]
         lib.oracle_pndf.restype = None
-        lib.oracle_projarea.argtypes = [dp, ctypes.c_int, dp, dp, ctypes.c_int64, ctypes.c_int64, dp]
+        lib.oracle_projarea.argtypes = [dp, ctypes.c_int, dp, dp, ctypes.c_int64, ctypes.c_int64, dp, dp, dp,
+                                        ctypes.c_int]
         lib.oracle_projarea.restype = None
         lib.oracle_tri_integral.argtypes = [ctypes.c_double] * 9
         lib.oracle_tri_integral.restype = ctypes.c_double
@@ -138,10 +140,13 @@ class Oracle:
         assert w.shape[0] == n
         P = np.zeros(n, np.float64)
         N = stm.shape[0]
+        # Gauss-Legendre nodes for the collapsed-triangle uv form (numpy's leggauss)
+        glx, glw = (np.ascontiguousarray(a) for a in np.polynomial.legendre.leggauss(GL_POINTS))
 
         def run(r):
             lib.oracle_projarea(_ptr(stm, ctypes.c_double), N, _ptr(q, ctypes.c_double),
-                                _ptr(w, ctypes.c_double), r[0], r[1], _ptr(P, ctypes.c_double))
+                                _ptr(w, ctypes.c_double), r[0], r[1], _ptr(P, ctypes.c_double),
+                                _ptr(glx, ctypes.c_double), _ptr(glw, ctypes.c_double), GL_POINTS)
 
         threads = threads or default_threads()
         if n:

@@ -319,13 +319,77 @@ double oracle_tri_integral(double n0x, double n0y, double n1x, double n1y,
 
 /*
  * P(w) for one footprint, Eq. 10: sum over triangles of
- * k_r(T) / (2 ||n(T)||) * integral over n+(T).  Triangles whose normal
- * triangle has |(n_b - n_a) x (n_c - n_a)| < 1e-12 use the limit of that
- * ratio as the triangle collapses: (1/2) max(n~ . w, 0) / n~_z at the
- * normal-space centroid (the uv-form integrand of Eq. 13 over a uv triangle
- * of area 1/2).
+ * k_r(T) / (2 ||n(T)||) * integral over n+(T).  A triangle whose normal
+ * triangle has |(n_b - n_a) x (n_c - n_a)| < 1e-12 has collapsed onto a
+ * segment (or a point), where Eq. 10's ratio is 0/0; its contribution is
+ * then the uv-space form of Eq. 13 over its uv triangle (see
+ * collapsed_uv_form).
  */
-static double projarea_one(const double *st, int N, const double *qq, const double *w)
+/* max(m~ . w, 0) / m~_z */
+static double visible_cos_ratio(double mx, double my, const double *w)
+{
+    double mz = sqrt(1.0 - mx * mx - my * my);
+    double c = mx * w[0] + my * w[1] + mz * w[2];
+    return (c > 0.0 ? c : 0.0) / mz;
+}
+
+/*
+ * Eq. 13's uv-space integral over a uv triangle (area 1/2) whose normal
+ * image is a segment: integral over T_uv of max(n~(u) . w, 0) / n~_z(u) du.
+ * With P, Q the two farthest normal vertices and tau the position along
+ * P -> Q, tau(u) is affine on the triangle, so a uniform point of the
+ * triangle maps to the piecewise-linear (triangular) density on
+ * [tau_1, tau_3] with its peak at tau_2 (the sorted vertex positions).  The
+ * visible part of the segment is the interval Alg. 1 keeps; each linear
+ * piece of the density is integrated over it by Gauss-Legendre (gl_x, gl_w
+ * on [-1, 1], ngl points).
+ */
+static double collapsed_uv_form(const double *a, const double *b, const double *c, const double *w,
+                                double c_phi, double s_phi, const double *gl_x, const double *gl_w, int ngl)
+{
+    const double *v[3] = {a, b, c};
+    double best = -1.0;
+    int ip = 0, iq = 1;
+    for (int i = 0; i < 3; ++i)
+        for (int j = i + 1; j < 3; ++j) {
+            double dx = v[j][0] - v[i][0], dy = v[j][1] - v[i][1];
+            double d2 = dx * dx + dy * dy;
+            if (d2 > best) { best = d2; ip = i; iq = j; }
+        }
+    if (best == 0.0) return 0.5 * visible_cos_ratio(a[0], a[1], w);
+    const double *P = v[ip], *Q = v[iq];
+    double ex = Q[0] - P[0], ey = Q[1] - P[1];
+    double tau[3];
+    for (int i = 0; i < 3; ++i) tau[i] = ((v[i][0] - P[0]) * ex + (v[i][1] - P[1]) * ey) / best;
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2 - i; ++j)
+            if (tau[j] > tau[j + 1]) { double t = tau[j]; tau[j] = tau[j + 1]; tau[j + 1] = t; }
+    /* visible interval of P -> Q from Alg. 1 in the rotated frame */
+    double pr[2] = {c_phi * P[0] + s_phi * P[1], -s_phi * P[0] + c_phi * P[1]};
+    double qr[2] = {c_phi * Q[0] + s_phi * Q[1], -s_phi * Q[0] + c_phi * Q[1]};
+    double oa[2], ob[2];
+    int ca, cb;
+    if (!clip_edge(pr, qr, w[2], oa, ob, &ca, &cb)) return 0.0;
+    double L2 = (qr[0] - pr[0]) * (qr[0] - pr[0]) + (qr[1] - pr[1]) * (qr[1] - pr[1]);
+    double tlo = ((oa[0] - pr[0]) * (qr[0] - pr[0]) + (oa[1] - pr[1]) * (qr[1] - pr[1])) / L2;
+    double thi = ((ob[0] - pr[0]) * (qr[0] - pr[0]) + (ob[1] - pr[1]) * (qr[1] - pr[1])) / L2;
+    double span = tau[2] - tau[0];
+    double sum = 0.0;
+    for (int piece = 0; piece < 2; ++piece) {
+        double t0 = tau[piece], t1 = tau[piece + 1];
+        double lo = fmax(t0, tlo), hi = fmin(t1, thi);
+        if (!(hi > lo) || t1 == t0) continue;
+        for (int g = 0; g < ngl; ++g) {
+            double t = 0.5 * (lo + hi) + 0.5 * (hi - lo) * gl_x[g];
+            double dens = piece == 0 ? 2.0 * (t - t0) / (span * (t1 - t0)) : 2.0 * (t1 - t) / (span * (t1 - t0));
+            sum += 0.5 * (hi - lo) * gl_w[g] * dens * visible_cos_ratio(P[0] + t * ex, P[1] + t * ey, w);
+        }
+    }
+    return 0.5 * sum;
+}
+
+static double projarea_one(const double *st, int N, const double *qq, const double *w,
+                           const double *gl_x, const double *gl_w, int ngl)
 {
     double x = qq[0], y = qq[1], sxx = qq[2], sxy = qq[3], syy = qq[4];
     double det = sxx * syy - sxy * sxy;
@@ -357,10 +421,7 @@ static double projarea_one(const double *st, int N, const double *qq, const doub
                 const double *a = n[vid[tri][0]], *b = n[vid[tri][1]], *cc = n[vid[tri][2]];
                 double A2 = area2(a[0], a[1], b[0], b[1], cc[0], cc[1]);
                 if (fabs(A2) < 1e-12) {
-                    double mxc = (a[0] + b[0] + cc[0]) / 3.0, myc = (a[1] + b[1] + cc[1]) / 3.0;
-                    double mz = sqrt(1.0 - mxc * mxc - myc * myc);
-                    double cosv = mxc * wx + myc * wy + mz * wz;
-                    P += k * 0.5 * (cosv > 0.0 ? cosv : 0.0) / mz;
+                    P += k * collapsed_uv_form(a, b, cc, w, c, s, gl_x, gl_w, ngl);
                     continue;
                 }
                 double v[3][2] = {{c * a[0] + s * a[1], -s * a[0] + c * a[1]},
@@ -379,7 +440,7 @@ static double projarea_one(const double *st, int N, const double *qq, const doub
 }
 
 void oracle_projarea(const double *st, int N, const double *q, const double *w,
-                     int64_t k0, int64_t k1, double *P)
+                     int64_t k0, int64_t k1, double *P, const double *gl_x, const double *gl_w, int ngl)
 {
-    for (int64_t k = k0; k < k1; ++k) P[k] = projarea_one(st, N, q + 7 * k, w + 3 * k);
+    for (int64_t k = k0; k < k1; ++k) P[k] = projarea_one(st, N, q + 7 * k, w + 3 * k, gl_x, gl_w, ngl);
 }

@@ -1,0 +1,232 @@
+// Min/max normal-bound pyramid build (Sec. 4.2, Fig. 5a).
+//
+// A node at level l covers 2^l x 2^l quads and stores the bounding box
+// (s_min, t_min, s_max, t_max) of the normals of every texel its quads touch,
+// so each normal triangle below it lies inside the box.  Levels
+// kLeafLevel..L are stored; level l is a (2^(L-l))^2 array in Morton order,
+// so the four children of node k at level l are nodes 4k..4k+3 at level l-1
+// (one 64-byte line in FP32, one 32-byte sector in FP16).
+//
+// Kernel 1 (build_tiles): one CTA per 64 x 64-quad tile.  The tile's 65 x 65
+// texels are staged in shared memory with 16-byte vector loads (float4 = two
+// FP32 texels, uint4 = four FP16 texels), each thread reduces one leaf-level
+// node (5 x 5 texels), and levels up to 6 are reduced in shared memory.  A
+// tile is a Morton-aligned square at every level, so its nodes form one
+// contiguous run and the writes are fully coalesced.
+// Kernel 2 (build_up): one launch per level above the tile, four contiguous
+// children reduced per thread.
+// FP16 bounds round outward (min toward -inf, max toward +inf) so pruning
+// stays conservative: the FP16 box contains the FP32 box.
+#include "common.cuh"
+
+namespace pndf {
+namespace {
+
+constexpr int kTileQuadsMax = 64;
+constexpr int kTileTexMax = kTileQuadsMax + 1;
+constexpr int kBuildThreads = 256;
+
+struct Box {
+    float smin, tmin, smax, tmax;
+};
+
+__device__ __forceinline__ Box empty_box()
+{
+    return Box{__int_as_float(0x7f800000), __int_as_float(0x7f800000), __int_as_float(0xff800000),
+               __int_as_float(0xff800000)};
+}
+
+__device__ __forceinline__ void grow(Box &b, const Box &o)
+{
+    b.smin = fminf(b.smin, o.smin);
+    b.tmin = fminf(b.tmin, o.tmin);
+    b.smax = fmaxf(b.smax, o.smax);
+    b.tmax = fmaxf(b.tmax, o.tmax);
+}
+
+template <int BFMT>
+__device__ __forceinline__ void store_box(void *lv, size_t idx, const Box &b)
+{
+    if (BFMT == PNDF_BOUNDS_F32) {
+        reinterpret_cast<float4 *>(lv)[idx] = make_float4(b.smin, b.tmin, b.smax, b.tmax);
+    } else {
+        __half2 lo = __halves2half2(__float2half_rd(b.smin), __float2half_rd(b.tmin));
+        __half2 hi = __halves2half2(__float2half_ru(b.smax), __float2half_ru(b.tmax));
+        uint2 v;
+        v.x = *reinterpret_cast<uint32_t *>(&lo);
+        v.y = *reinterpret_cast<uint32_t *>(&hi);
+        reinterpret_cast<uint2 *>(lv)[idx] = v;
+    }
+}
+
+template <int BFMT>
+__device__ __forceinline__ Box load_box(const void *lv, size_t idx)
+{
+    if (BFMT == PNDF_BOUNDS_F32) {
+        float4 v = reinterpret_cast<const float4 *>(lv)[idx];
+        return Box{v.x, v.y, v.z, v.w};
+    } else {
+        uint2 v = reinterpret_cast<const uint2 *>(lv)[idx];
+        __half2 lo = *reinterpret_cast<__half2 *>(&v.x);
+        __half2 hi = *reinterpret_cast<__half2 *>(&v.y);
+        float2 l = __half22float2(lo), h = __half22float2(hi);
+        return Box{l.x, l.y, h.x, h.y};
+    }
+}
+
+template <int TFMT>
+__device__ __forceinline__ float2 load_texel(const void *t, size_t idx)
+{
+    if (TFMT == PNDF_TEXEL_F32X2) return reinterpret_cast<const float2 *>(t)[idx];
+    return __half22float2(reinterpret_cast<const __half2 *>(t)[idx]);
+}
+
+// VEC = texels per 16-byte load (2 for FP32, 4 for FP16), or 1 when rows are
+// not 16-byte aligned (n not a multiple of VEC).
+template <int TFMT, int BFMT, int VEC>
+__global__ void __launch_bounds__(kBuildThreads) build_tiles(const void *__restrict__ src, MapDesc d, int tileQ,
+                                                            int lq)
+{
+    __shared__ float2 tex[kTileTexMax * kTileTexMax];
+    __shared__ Box box[2][(kTileQuadsMax / kLeafQuads) * (kTileQuadsMax / kLeafQuads)];
+
+    const int n = d.n;
+    const int tw = tileQ + 1;
+    const int c0 = blockIdx.x * tileQ, r0 = blockIdx.y * tileQ;
+    const int tid = threadIdx.x;
+
+    // ---- stage texels: VEC-wide loads for the first tileQ columns ----
+    const int nvec = tileQ / VEC;
+    for (int idx = tid; idx < tw * nvec; idx += kBuildThreads) {
+        int r = idx / nvec, v = idx - r * nvec;
+        int gr = r0 + r, gc = c0 + v * VEC;
+        if (gr >= n || gc >= n) continue;
+        size_t g = size_t(gr) * n + gc;
+        float2 *dst = &tex[r * kTileTexMax + v * VEC];
+        if (VEC == 2) {
+            float4 p = reinterpret_cast<const float4 *>(src)[g >> 1];
+            dst[0] = make_float2(p.x, p.y);
+            dst[1] = make_float2(p.z, p.w);
+        } else if (VEC == 4) {
+            uint4 p = reinterpret_cast<const uint4 *>(src)[g >> 2];
+            dst[0] = __half22float2(*reinterpret_cast<__half2 *>(&p.x));
+            dst[1] = __half22float2(*reinterpret_cast<__half2 *>(&p.y));
+            dst[2] = __half22float2(*reinterpret_cast<__half2 *>(&p.z));
+            dst[3] = __half22float2(*reinterpret_cast<__half2 *>(&p.w));
+        } else {
+            dst[0] = load_texel<TFMT>(src, g);
+        }
+    }
+    // the shared last column of the tile
+    for (int r = tid; r < tw; r += kBuildThreads) {
+        int gr = r0 + r, gc = c0 + tileQ;
+        if (gr < n && gc < n) tex[r * kTileTexMax + tileQ] = load_texel<TFMT>(src, size_t(gr) * n + gc);
+    }
+    __syncthreads();
+
+    // ---- leaf-level nodes: thread i owns the node with local Morton index i ----
+    const int T = tileQ / kLeafQuads;  // leaf nodes per tile side
+    const uint32_t tile_m = morton2(blockIdx.x, blockIdx.y);
+    int cur = T * T;
+    if (tid < cur) {
+        int a = compact1by1(tid), c = compact1by1(tid >> 1);
+        int q0 = c0 + a * kLeafQuads, p0 = r0 + c * kLeafQuads;  // first quad column / row
+        Box b = empty_box();
+        if (q0 <= n - 2 && p0 <= n - 2) {
+            int ce = min(a * kLeafQuads + kLeafQuads, n - 1 - c0);
+            int re = min(c * kLeafQuads + kLeafQuads, n - 1 - r0);
+            for (int r = c * kLeafQuads; r <= re; ++r) {
+                for (int cc = a * kLeafQuads; cc <= ce; ++cc) {
+                    float2 v = tex[r * kTileTexMax + cc];
+                    b.smin = fminf(b.smin, v.x);
+                    b.tmin = fminf(b.tmin, v.y);
+                    b.smax = fmaxf(b.smax, v.x);
+                    b.tmax = fmaxf(b.tmax, v.y);
+                }
+            }
+        }
+        box[0][tid] = b;
+        store_box<BFMT>(const_cast<void *>(d.lv[kLeafLevel]), size_t(tile_m) * cur + tid, b);
+    }
+    __syncthreads();
+
+    // ---- reduce inside the tile up to level lq ----
+    int s = 0;
+    for (int l = kLeafLevel + 1; l <= lq; ++l) {
+        cur >>= 2;
+        if (tid < cur) {
+            Box b = box[s][4 * tid];
+            grow(b, box[s][4 * tid + 1]);
+            grow(b, box[s][4 * tid + 2]);
+            grow(b, box[s][4 * tid + 3]);
+            box[s ^ 1][tid] = b;
+            store_box<BFMT>(const_cast<void *>(d.lv[l]), size_t(tile_m) * cur + tid, b);
+        }
+        s ^= 1;
+        __syncthreads();
+    }
+}
+
+template <int BFMT>
+__global__ void build_up(const void *__restrict__ child, void *__restrict__ parent, size_t count)
+{
+    size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    Box b = load_box<BFMT>(child, 4 * i);
+    grow(b, load_box<BFMT>(child, 4 * i + 1));
+    grow(b, load_box<BFMT>(child, 4 * i + 2));
+    grow(b, load_box<BFMT>(child, 4 * i + 3));
+    if (BFMT == PNDF_BOUNDS_F32) {
+        store_box<BFMT>(parent, i, b);
+    } else {
+        // children are already binary16 values: the reduction is exact
+        __half2 lo = __floats2half2_rn(b.smin, b.tmin);
+        __half2 hi = __floats2half2_rn(b.smax, b.tmax);
+        uint2 v;
+        v.x = *reinterpret_cast<uint32_t *>(&lo);
+        v.y = *reinterpret_cast<uint32_t *>(&hi);
+        reinterpret_cast<uint2 *>(parent)[i] = v;
+    }
+}
+
+template <int TFMT, int BFMT>
+cudaError_t launch_tiles(const void *src, const MapDesc &d, cudaStream_t s)
+{
+    const int side = 1 << d.L;
+    const int tileQ = side < kTileQuadsMax ? side : kTileQuadsMax;
+    int lq = 0;
+    while ((1 << lq) < tileQ) ++lq;
+    dim3 grid(side / tileQ, side / tileQ);
+    constexpr int VEC = TFMT == PNDF_TEXEL_F32X2 ? 2 : 4;
+    if (d.n % VEC == 0 && (reinterpret_cast<uintptr_t>(src) & 15u) == 0)
+        build_tiles<TFMT, BFMT, VEC><<<grid, kBuildThreads, 0, s>>>(src, d, tileQ, lq);
+    else
+        build_tiles<TFMT, BFMT, 1><<<grid, kBuildThreads, 0, s>>>(src, d, tileQ, lq);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    for (int l = lq + 1; l <= d.L; ++l) {
+        size_t cnt = level_nodes(d.L, l);
+        unsigned blocks = unsigned((cnt + 255) / 256);
+        build_up<BFMT><<<blocks, 256, 0, s>>>(d.lv[l - 1], const_cast<void *>(d.lv[l]), cnt);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t launch_build(const void *texels_src, pndf_hierarchy *h, cudaStream_t s)
+{
+    const MapDesc &d = h->d;
+    size_t tb = size_t(d.n) * d.n * (d.texel_fmt == PNDF_TEXEL_F32X2 ? 8 : 4);
+    cudaError_t e = cudaMemcpyAsync(const_cast<void *>(d.texels), texels_src, tb, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+    if (d.texel_fmt == PNDF_TEXEL_F32X2)
+        return d.bounds_fmt == PNDF_BOUNDS_F32 ? launch_tiles<PNDF_TEXEL_F32X2, PNDF_BOUNDS_F32>(texels_src, d, s)
+                                               : launch_tiles<PNDF_TEXEL_F32X2, PNDF_BOUNDS_F16_OUTWARD>(texels_src, d, s);
+    return d.bounds_fmt == PNDF_BOUNDS_F32 ? launch_tiles<PNDF_TEXEL_F16X2, PNDF_BOUNDS_F32>(texels_src, d, s)
+                                           : launch_tiles<PNDF_TEXEL_F16X2, PNDF_BOUNDS_F16_OUTWARD>(texels_src, d, s);
+}
+
+}  // namespace pndf

@@ -1,0 +1,186 @@
+// C ABI entry points of libpndf.so (declarations and contracts in pndf.h).
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "common.cuh"
+
+using namespace pndf;
+
+namespace {
+
+cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
+
+bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+pndf_status check_hierarchy(const pndf_hierarchy *h)
+{
+    if (!h || !h->mem) return PNDF_ERR_INVALID_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PNDF_ERR_CUDA;
+    if (dev != h->device) return PNDF_ERR_INVALID_ARG;  // must be called with the hierarchy's device current
+    return PNDF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pndf_status pndf_build_hierarchy(const void *texels_dev, const pndf_build_params *p, void *stream,
+                                 pndf_hierarchy **out)
+{
+    if (!out) return PNDF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!texels_dev || !p) return PNDF_ERR_INVALID_ARG;
+    if (p->n < 2 || p->n > 16384) return PNDF_ERR_INVALID_ARG;
+    if (p->texel_fmt != PNDF_TEXEL_F32X2 && p->texel_fmt != PNDF_TEXEL_F16X2) return PNDF_ERR_INVALID_ARG;
+    if (p->bounds_fmt != PNDF_BOUNDS_F32 && p->bounds_fmt != PNDF_BOUNDS_F16_OUTWARD) return PNDF_ERR_INVALID_ARG;
+    if (p->leaf_level != 0 && p->leaf_level != kLeafLevel) return PNDF_ERR_UNSUPPORTED;
+    if (!aligned(texels_dev, p->texel_fmt == PNDF_TEXEL_F32X2 ? 8 : 4)) return PNDF_ERR_INVALID_ARG;
+
+    pndf_hierarchy *h = new (std::nothrow) pndf_hierarchy();
+    if (!h) return PNDF_ERR_OOM;
+    memset(&h->d, 0, sizeof(h->d));
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        delete h;
+        return PNDF_ERR_CUDA;
+    }
+    MapDesc &d = h->d;
+    d.n = p->n;
+    d.L = top_level(p->n);
+    d.texel_fmt = p->texel_fmt;
+    d.bounds_fmt = p->bounds_fmt;
+    const size_t node_b = p->bounds_fmt == PNDF_BOUNDS_F32 ? 16 : 8;
+    const size_t texel_b = p->texel_fmt == PNDF_TEXEL_F32X2 ? 8 : 4;
+    auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
+    size_t off[kMaxLevels + 1];
+    size_t total = up(size_t(d.n) * d.n * texel_b);
+    for (int l = kLeafLevel; l <= d.L; ++l) {
+        off[l] = total;
+        total += up(level_nodes(d.L, l) * node_b);
+    }
+    if (cudaMalloc(&h->mem, total) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return PNDF_ERR_OOM;
+    }
+    h->bytes = total;
+    char *base = static_cast<char *>(h->mem);
+    d.texels = base;
+    for (int l = kLeafLevel; l <= d.L; ++l) d.lv[l] = base + off[l];
+    cudaError_t e = launch_build(texels_dev, h, as_stream(stream));
+    if (e != cudaSuccess) {
+        cudaFree(h->mem);
+        delete h;
+        return PNDF_ERR_CUDA;
+    }
+    *out = h;
+    return PNDF_OK;
+}
+
+void pndf_free_hierarchy(pndf_hierarchy *h)
+{
+    if (!h) return;
+    if (h->mem) {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (cur != h->device) cudaSetDevice(h->device);
+        cudaFree(h->mem);
+        if (cur != h->device && cur >= 0) cudaSetDevice(cur);
+    }
+    delete h;
+}
+
+size_t pndf_hierarchy_bytes(const pndf_hierarchy *h) { return h ? h->bytes : 0; }
+
+pndf_status pndf_eval_batch_ex(const pndf_hierarchy *h, const pndf_query *q_dev, int64_t nq, float *D_out_dev,
+                               uint32_t *flags_out_dev, pndf_query_stats *stats_dev, const pndf_eval_config *cfg,
+                               void *stream)
+{
+    pndf_status st = check_hierarchy(h);
+    if (st != PNDF_OK) return st;
+    if (nq < 0 || nq > int64_t(0x7fffffff)) return PNDF_ERR_INVALID_ARG;
+    if (nq > 0 && (!q_dev || !D_out_dev)) return PNDF_ERR_INVALID_ARG;
+    if (q_dev && !aligned(q_dev, 16)) return PNDF_ERR_INVALID_ARG;
+    pndf_eval_config c{PNDF_MODE_HIERARCHY, 1, 0, 0};
+    if (cfg) c = *cfg;
+    if (c.mode != PNDF_MODE_HIERARCHY && c.mode != PNDF_MODE_FLAT) return PNDF_ERR_INVALID_ARG;
+    if (c.warps_per_cta < 0 || c.warps_per_cta > 8 || c.ctas_per_sm < 0) return PNDF_ERR_INVALID_ARG;
+    return launch_eval(h, q_dev, nq, D_out_dev, flags_out_dev, stats_dev, c, as_stream(stream));
+}
+
+pndf_status pndf_eval_batch(const pndf_hierarchy *h, const pndf_query *q_dev, int64_t nq, float *D_out_dev,
+                            uint32_t *flags_out_dev, pndf_query_stats *stats_dev, void *stream)
+{
+    return pndf_eval_batch_ex(h, q_dev, nq, D_out_dev, flags_out_dev, stats_dev, nullptr, stream);
+}
+
+pndf_status pndf_eval_batch_host(const pndf_hierarchy *h, const pndf_query *q_host, int64_t nq, float *D_host,
+                                 void *stream)
+{
+    pndf_status st = check_hierarchy(h);
+    if (st != PNDF_OK) return st;
+    if (nq < 0 || nq > int64_t(0x7fffffff)) return PNDF_ERR_INVALID_ARG;
+    if (nq == 0) return PNDF_OK;
+    if (!q_host || !D_host) return PNDF_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    size_t qb = size_t(nq) * sizeof(pndf_query), db = size_t(nq) * sizeof(float);
+    size_t qoff = (db + 255) & ~size_t(255);
+    void *buf = nullptr;
+    if (cudaMallocAsync(&buf, qoff + qb, s) != cudaSuccess) {
+        cudaGetLastError();
+        return PNDF_ERR_OOM;
+    }
+    float *Dd = static_cast<float *>(buf);
+    pndf_query *qd = reinterpret_cast<pndf_query *>(static_cast<char *>(buf) + qoff);
+    cudaError_t e = cudaMemcpyAsync(qd, q_host, qb, cudaMemcpyHostToDevice, s);
+    pndf_eval_config c{PNDF_MODE_HIERARCHY, 1, 0, 0};
+    if (e == cudaSuccess) st = launch_eval(h, qd, nq, Dd, nullptr, nullptr, c, s);
+    if (e == cudaSuccess && st == PNDF_OK) e = cudaMemcpyAsync(D_host, Dd, db, cudaMemcpyDeviceToHost, s);
+    cudaError_t ef = cudaFreeAsync(buf, s);
+    cudaError_t es = cudaStreamSynchronize(s);
+    if (st != PNDF_OK) return st;
+    if (e != cudaSuccess || ef != cudaSuccess || es != cudaSuccess) return PNDF_ERR_CUDA;
+    return PNDF_OK;
+}
+
+pndf_status pndf_diffuse_projected_area(const pndf_hierarchy *h, const pndf_query *q_dev, const float *omega_dev,
+                                        int64_t nq, float *P_out_dev, void *stream)
+{
+    pndf_status st = check_hierarchy(h);
+    if (st != PNDF_OK) return st;
+    if (nq < 0 || nq > int64_t(0x7fffffff)) return PNDF_ERR_INVALID_ARG;
+    if (nq > 0 && (!q_dev || !omega_dev || !P_out_dev)) return PNDF_ERR_INVALID_ARG;
+    if (q_dev && !aligned(q_dev, 16)) return PNDF_ERR_INVALID_ARG;
+    return launch_projarea(h, q_dev, omega_dev, nq, P_out_dev, as_stream(stream));
+}
+
+pndf_status pndf_device_status(void *stream, uint32_t *bits_out)
+{
+    uint32_t a = 0, b = 0;
+    cudaError_t e = read_status_eval(as_stream(stream), &a, true);
+    if (e == cudaSuccess) e = read_status_projarea(as_stream(stream), &b, true);
+    if (bits_out) *bits_out = a | b;
+    if (e != cudaSuccess) return PNDF_ERR_CUDA;
+    return (a | b) ? PNDF_ERR_DEVICE : PNDF_OK;
+}
+
+const char *pndf_status_string(pndf_status s)
+{
+    switch (s) {
+    case PNDF_OK: return "ok";
+    case PNDF_ERR_INVALID_ARG: return "invalid argument";
+    case PNDF_ERR_OOM: return "out of device memory";
+    case PNDF_ERR_CUDA: return "CUDA runtime error";
+    case PNDF_ERR_TIMEOUT: return "device wait timed out";
+    case PNDF_ERR_CAPACITY: return "device buffer capacity exceeded";
+    case PNDF_ERR_UNSUPPORTED: return "unsupported request";
+    case PNDF_ERR_DEVICE: return "kernel recorded a device-side error";
+    }
+    return "unknown status";
+}
+
+int32_t pndf_version(void) { return 100; }
+
+}  // extern "C"

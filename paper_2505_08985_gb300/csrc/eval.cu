@@ -1,0 +1,614 @@
+// Batched P-NDF evaluation over the position-normal manifold (Sec. 4.1-4.2).
+//
+// Per query (footprint centre x, covariance S, normal m) the result is Eq. 5:
+//   D = sum over triangles abc with m in n(abc) of
+//       k_r(a l0 + b l1 + c l2 - x) / |(n_b - n_a) x (n_c - n_a)|.
+//
+// Pipeline (all on the caller's stream):
+//   key_hist  : entry level l = ceil(log2 r) of the 4-sigma box half-width r
+//               (App. C, "entry level") and a 16 x 16 tile of the centre ->
+//               16-bit key; shared-memory histogram.
+//   key_scan  : exclusive scan of the 4096 bins (one CTA).
+//   key_place : counting-sort placement -> query order, largest footprints
+//               first, spatially grouped inside a level.
+//   traverse  : persistent warps pull queries from an atomic cursor; one warp
+//               per query.  Depth-first descent of the min/max pyramid with a
+//               per-warp shared-memory stack: each step pops up to 8 nodes,
+//               lane k tests child (k & 3) of popped node (k >> 2) - uv box
+//               against the 4-sigma ellipse first, then the normal box against
+//               m - and ballot/popc compaction pushes survivors.  Surviving
+//               leaf blocks (4 x 4 quads = 32 triangles) are tested one per
+//               lane; the block's 25 texels are loaded once and shuffled.  The
+//               query's sum is reduced across the warp and written in caller
+//               order (the unpermute is fused into the store).
+// Hit test (tie rule): m inside the closed normal bounding box and all three
+// edge functions sign-consistent with the triangle orientation (>= 0 after
+// orientation, i.e. closed barycentrics).  Zero-area normal triangles are a
+// delta and are skipped.  Edge functions use an FMA difference of products on
+// vertex-relative differences; triangles whose FP32 |cross| is below 2e-10
+// (normal-space area below 1e-10) are re-tested and weighted in FP64.
+#include "common.cuh"
+
+namespace pndf {
+
+__device__ unsigned int g_status_eval;
+
+namespace {
+
+constexpr int kStackCap = 512;     // DFS stack entries per warp (bound: 24 per level + 48)
+constexpr int kKeyBins = 16 * 256;  // 16 entry levels x 16 x 16 tiles
+constexpr unsigned kFull = 0xffffffffu;
+
+// Kahan's difference of products a*b - c*d with one FMA correction.
+__device__ __forceinline__ float dop(float a, float b, float c, float d)
+{
+    float w = c * d;
+    float e = fmaf(-c, d, w);
+    float f = fmaf(a, b, -w);
+    return f + e;
+}
+
+// Twice the signed area of (p, q, r): (q - p) x (r - p).
+__device__ __forceinline__ float orient(float px, float py, float qx, float qy, float rx, float ry)
+{
+    return dop(qx - px, ry - py, qy - py, rx - px);
+}
+
+__device__ __forceinline__ double orient_d(double px, double py, double qx, double qy, double rx, double ry)
+{
+    return (qx - px) * (ry - py) - (qy - py) * (rx - px);
+}
+
+// MurmurHash3 32-bit finalizer (Appleby), fingerprints hit sets in stats mode.
+__device__ __forceinline__ uint32_t fmix32(uint32_t h)
+{
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+struct Query {
+    float x, y;          // footprint centre
+    float ia, ib, ic;    // S^-1 = [[ia, ib], [ib, ic]]
+    float norm;          // 1 / (2 pi sqrt(det S))
+    float mx, my;        // query normal
+    float rx, ry;        // half-widths of the 4-sigma box (slightly inflated)
+    bool valid;
+};
+
+__device__ __forceinline__ Query make_query(const pndf_query &r)
+{
+    Query q;
+    q.x = r.x;
+    q.y = r.y;
+    q.mx = r.ms;
+    q.my = r.mt;
+    float det = r.sxx * r.syy - r.sxy * r.sxy;
+    q.valid = (r.sxx > 0.f) && (r.syy > 0.f) && (det > 0.f) && isfinite(det) && isfinite(r.x) &&
+              isfinite(r.y) && isfinite(r.ms) && isfinite(r.mt);
+    float inv = 1.0f / det;
+    q.ia = r.syy * inv;
+    q.ib = -r.sxy * inv;
+    q.ic = r.sxx * inv;
+    q.norm = 1.0f / (2.0f * kPi * sqrtf(det));
+    // q <= 16 implies |dx| <= 4 sqrt(sxx); inflate so rounding never clips the box
+    q.rx = 4.0f * sqrtf(r.sxx) * (1.0f + 1e-5f) + 1e-6f;
+    q.ry = 4.0f * sqrtf(r.syy) * (1.0f + 1e-5f) + 1e-6f;
+    return q;
+}
+
+__device__ __forceinline__ float qform(const Query &q, float dx, float dy)
+{
+    return fmaf(q.ia * dx, dx, fmaf(2.0f * q.ib * dx, dy, q.ic * dy * dy));
+}
+
+// Minimum of q over the box [dx0, dx1] x [dy0, dy1] (offsets from the centre).
+// The quadratic is convex with its minimum at the origin; off the box, the
+// minimum lies on an edge whose outer side holds the origin, where it is a
+// clamped 1D minimum.
+__device__ __forceinline__ float qmin_box(const Query &q, float dx0, float dx1, float dy0, float dy1)
+{
+    if (dx0 <= 0.f && dx1 >= 0.f && dy0 <= 0.f && dy1 >= 0.f) return 0.f;
+    float best = __int_as_float(0x7f800000);
+    if (dx0 > 0.f || dx1 < 0.f) {
+        float X = dx0 > 0.f ? dx0 : dx1;
+        float y = fminf(fmaxf(-q.ib * X / q.ic, dy0), dy1);
+        best = fminf(best, qform(q, X, y));
+    }
+    if (dy0 > 0.f || dy1 < 0.f) {
+        float Y = dy0 > 0.f ? dy0 : dy1;
+        float x = fminf(fmaxf(-q.ib * Y / q.ia, dx0), dx1);
+        best = fminf(best, qform(q, x, Y));
+    }
+    return best;
+}
+
+template <int BFMT>
+__device__ __forceinline__ float4 node_box(const MapDesc &d, int l, uint32_t m)
+{
+    if (BFMT == PNDF_BOUNDS_F32) return __ldg(reinterpret_cast<const float4 *>(d.lv[l]) + m);
+    uint2 v = __ldg(reinterpret_cast<const uint2 *>(d.lv[l]) + m);
+    float2 lo = __half22float2(*reinterpret_cast<__half2 *>(&v.x));
+    float2 hi = __half22float2(*reinterpret_cast<__half2 *>(&v.y));
+    return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+
+template <int TFMT>
+__device__ __forceinline__ float2 texel(const MapDesc &d, int i, int j)
+{
+    size_t idx = size_t(j) * d.n + i;
+    if (TFMT == PNDF_TEXEL_F32X2) return __ldg(reinterpret_cast<const float2 *>(d.texels) + idx);
+    __half2 h = __ldg(reinterpret_cast<const __half2 *>(d.texels) + idx);
+    return __half22float2(h);
+}
+
+// Node (level l, coords a, c): uv box [a 2^l, (a+1) 2^l] x [c 2^l, (c+1) 2^l].
+template <int BFMT>
+__device__ __forceinline__ bool node_test(const MapDesc &d, const Query &q, int l, uint32_t a, uint32_t c)
+{
+    float sz = float(1u << l);
+    float dx0 = float(a) * sz - q.x, dy0 = float(c) * sz - q.y;
+    if (qmin_box(q, dx0, dx0 + sz, dy0, dy0 + sz) > kQPrune) return false;
+    float4 b = node_box<BFMT>(d, l, morton2(a, c));
+    return q.mx >= b.x && q.mx <= b.z && q.my >= b.y && q.my <= b.w;
+}
+
+__device__ __forceinline__ uint32_t pack(int l, uint32_t a, uint32_t c)
+{
+    return (uint32_t(l) << 28) | (a << 14) | c;
+}
+
+struct Acc {
+    float s, c;  // Neumaier compensated sum
+    uint32_t hits, hash, tests, fp64, degen, leaves, nodes;
+    uint32_t flags;
+};
+
+__device__ __forceinline__ void acc_add(Acc &a, float w)
+{
+    float t = a.s + w;
+    if (fabsf(a.s) >= fabsf(w))
+        a.c += (a.s - t) + w;
+    else
+        a.c += (w - t) + a.s;
+    a.s = t;
+}
+
+// Test the lane's triangle of a leaf block and accumulate its contribution.
+// tri 0: (u0, u1, u2) with a = (i, j), b = a + (1, 0), c = a + (0, 1);
+// tri 1: (u3, u2, u1) with a = (i+1, j+1), b = a - (1, 0), c = a - (0, 1).
+template <bool STATS>
+__device__ __forceinline__ void test_triangle(const Query &q, float2 na, float2 nb, float2 nc, int ai, int aj,
+                                              float dir, uint32_t tri_id, Acc &acc)
+{
+    if (STATS) acc.tests++;
+    float lox = fminf(na.x, fminf(nb.x, nc.x)), hix = fmaxf(na.x, fmaxf(nb.x, nc.x));
+    float loy = fminf(na.y, fminf(nb.y, nc.y)), hiy = fmaxf(na.y, fmaxf(nb.y, nc.y));
+    if (q.mx < lox || q.mx > hix || q.my < loy || q.my > hiy) return;
+    float cr = orient(na.x, na.y, nb.x, nb.y, nc.x, nc.y);
+    float l1, l2, J;
+    if (fabsf(cr) >= kTinyCross) {
+        float e0 = orient(nb.x, nb.y, nc.x, nc.y, q.mx, q.my);
+        float e1 = orient(nc.x, nc.y, na.x, na.y, q.mx, q.my);
+        float e2 = orient(na.x, na.y, nb.x, nb.y, q.mx, q.my);
+        bool hit = cr > 0.f ? (e0 >= 0.f && e1 >= 0.f && e2 >= 0.f) : (e0 <= 0.f && e1 <= 0.f && e2 <= 0.f);
+        if (!hit) return;
+        float inv = 1.0f / cr;
+        l1 = e1 * inv;
+        l2 = e2 * inv;
+        J = fabsf(cr);
+    } else {
+        // near-singular normal triangle: FP64 test and weight
+        double ax = na.x, ay = na.y, bx = nb.x, by = nb.y, cx = nc.x, cy = nc.y, mx = q.mx, my = q.my;
+        double dcr = orient_d(ax, ay, bx, by, cx, cy);
+        if (dcr == 0.0) {
+            if (STATS) acc.degen++;
+            return;
+        }
+        if (STATS) acc.fp64++;
+        acc.flags |= PNDF_QF_FP64;
+        double e0 = orient_d(bx, by, cx, cy, mx, my);
+        double e1 = orient_d(cx, cy, ax, ay, mx, my);
+        double e2 = orient_d(ax, ay, bx, by, mx, my);
+        bool hit = dcr > 0.0 ? (e0 >= 0.0 && e1 >= 0.0 && e2 >= 0.0) : (e0 <= 0.0 && e1 <= 0.0 && e2 <= 0.0);
+        if (!hit) return;
+        double dl1 = e1 / dcr, dl2 = e2 / dcr;
+        double dx = (double(ai) - double(q.x)) + dir * dl1;
+        double dy = (double(aj) - double(q.y)) + dir * dl2;
+        double qq = double(q.ia) * dx * dx + 2.0 * double(q.ib) * dx * dy + double(q.ic) * dy * dy;
+        if (qq > double(kQCut)) return;
+        double w = double(q.norm) * exp(-0.5 * qq) / fabs(dcr);
+        acc_add(acc, float(w));
+        if (STATS) {
+            acc.hits++;
+            acc.hash += fmix32(tri_id);
+        }
+        return;
+    }
+    float dx = (float(ai) - q.x) + dir * l1;
+    float dy = (float(aj) - q.y) + dir * l2;
+    float qq = qform(q, dx, dy);
+    if (qq > kQCut) return;
+    acc_add(acc, q.norm * expf(-0.5f * qq) / J);
+    if (STATS) {
+        acc.hits++;
+        acc.hash += fmix32(tri_id);
+    }
+}
+
+// All 32 lanes: the leaf block at level kLeafLevel with block coords (a, c).
+template <int TFMT, bool STATS>
+__device__ __forceinline__ void process_leaf(const MapDesc &d, const Query &q, uint32_t a, uint32_t c, int lane,
+                                             Acc &acc)
+{
+    const int n = d.n;
+    const int i0 = int(a) << kLeafLevel, j0 = int(c) << kLeafLevel;
+    // lanes 0..24 fetch the block's 5 x 5 texels once
+    int tc = lane % kLeafTexels, tr = lane / kLeafTexels;
+    float2 tv = make_float2(0.f, 0.f);
+    if (lane < kLeafTexels * kLeafTexels && i0 + tc < n && j0 + tr < n) tv = texel<TFMT>(d, i0 + tc, j0 + tr);
+    int qd = lane >> 1, qx = qd & 3, qy = qd >> 2, tri = lane & 1;
+    int base = qy * kLeafTexels + qx;
+    int sa = tri ? base + kLeafTexels + 1 : base;
+    int sb = tri ? base + kLeafTexels : base + 1;
+    int sc = tri ? base + 1 : base + kLeafTexels;
+    float2 na, nb, nc;
+    na.x = __shfl_sync(kFull, tv.x, sa);
+    na.y = __shfl_sync(kFull, tv.y, sa);
+    nb.x = __shfl_sync(kFull, tv.x, sb);
+    nb.y = __shfl_sync(kFull, tv.y, sb);
+    nc.x = __shfl_sync(kFull, tv.x, sc);
+    nc.y = __shfl_sync(kFull, tv.y, sc);
+    int gi = i0 + qx, gj = j0 + qy;
+    if (STATS && lane == 0) acc.leaves++;
+    if (gi <= n - 2 && gj <= n - 2) {
+        uint32_t id = 2u * (uint32_t(gj) * uint32_t(n - 1) + uint32_t(gi)) + uint32_t(tri);
+        test_triangle<STATS>(q, na, nb, nc, tri ? gi + 1 : gi, tri ? gj + 1 : gj, tri ? -1.f : 1.f, id, acc);
+    }
+}
+
+// Nodes of size sz (S per side) whose closed extent [a sz, (a+1) sz] meets
+// [x - r, x + r]; clamped in float first so no int conversion can overflow.
+// Empty (a0 > a1) when the interval misses the map.
+__device__ __forceinline__ void node_range(float x, float r, float sz, int S, int &a0, int &a1)
+{
+    float f0 = fmaxf(ceilf((x - r) / sz) - 1.0f, 0.0f);
+    float f1 = fminf(floorf((x + r) / sz), float(S - 1));
+    if (!(f0 <= f1)) {
+        a0 = 1;
+        a1 = 0;
+        return;
+    }
+    a0 = int(f0);
+    a1 = int(f1);
+}
+
+__device__ __forceinline__ int entry_level(const Query &q, int L)
+{
+    float r = fmaxf(q.rx, q.ry);
+    int l = kLeafLevel;
+    while (l < L && float(1u << l) < r) ++l;
+    return l;
+}
+
+template <int BFMT, int TFMT, bool STATS, bool FLAT>
+__device__ void eval_one(const MapDesc &d, const pndf_query &rec, int lane, uint32_t *stk, uint32_t *lq,
+                         float &D_out, uint32_t &flags_out, pndf_query_stats *st_out)
+{
+    Query q = make_query(rec);
+    Acc acc = {0.f, 0.f, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    if (!q.valid) {
+        if (lane == 0) {
+            D_out = __int_as_float(0x7fc00000);
+            flags_out = PNDF_QF_INVALID;
+            atomicOr(&g_status_eval, PNDF_QF_INVALID);
+            if (STATS) *st_out = pndf_query_stats{0, 0, 0, 0, 0, 0, 0, 0};
+        }
+        return;
+    }
+    const int L = d.L;
+    if (FLAT) {
+        // every leaf block meeting the 4-sigma box, no pruning
+        const int S = 1 << (L - kLeafLevel);
+        const float sz = float(kLeafQuads);
+        int a0, a1, c0, c1;
+        node_range(q.x, q.rx, sz, S, a0, a1);
+        node_range(q.y, q.ry, sz, S, c0, c1);
+        for (int c = c0; c <= c1; ++c)
+            for (int a = a0; a <= a1; ++a) process_leaf<TFMT, STATS>(d, q, a, c, lane, acc);
+    } else {
+        const int e = entry_level(q, L);
+        const int S = 1 << (L - e);
+        const float sz = float(1u << e);
+        int a0, a1, c0, c1;
+        node_range(q.x, q.rx, sz, S, a0, a1);
+        node_range(q.y, q.ry, sz, S, c0, c1);
+        int top = 0, nleaf = 0;
+        const unsigned lt = (1u << lane) - 1u;
+        // entry nodes: at most 4 x 4
+        {
+            int a = a0 + (lane & 3), c = c0 + (lane >> 2);
+            bool pass = lane < 16 && a <= a1 && c <= c1 && node_test<BFMT>(d, q, e, a, c);
+            if (STATS) acc.nodes += (lane < 16 && a <= a1 && c <= c1) ? 1u : 0u;
+            unsigned m = __ballot_sync(kFull, pass);
+            if (pass) {
+                int pos = __popc(m & lt);
+                if (e == kLeafLevel)
+                    lq[pos] = pack(e, a, c);
+                else
+                    stk[pos] = pack(e, a, c);
+            }
+            if (e == kLeafLevel)
+                nleaf = __popc(m);
+            else
+                top = __popc(m);
+            __syncwarp();
+        }
+        bool overflow = false;
+        while (true) {
+            for (int i = 0; i < nleaf; ++i) {
+                uint32_t ent = lq[i];
+                process_leaf<TFMT, STATS>(d, q, (ent >> 14) & 0x3fffu, ent & 0x3fffu, lane, acc);
+            }
+            nleaf = 0;
+            if (top == 0) break;
+            int npop = min(top, 8);
+            top -= npop;
+            int slot = lane >> 2;
+            uint32_t ent = slot < npop ? stk[top + slot] : 0u;
+            __syncwarp();
+            bool pass = false;
+            int cl = 0;
+            uint32_t ca = 0, cc = 0;
+            if (slot < npop) {
+                int l = int(ent >> 28);
+                cl = l - 1;
+                ca = 2u * ((ent >> 14) & 0x3fffu) + (lane & 1);
+                cc = 2u * (ent & 0x3fffu) + ((lane >> 1) & 1);
+                pass = node_test<BFMT>(d, q, cl, ca, cc);
+                if (STATS) acc.nodes++;
+            }
+            bool to_leaf = pass && cl == kLeafLevel, to_stack = pass && cl > kLeafLevel;
+            unsigned ml = __ballot_sync(kFull, to_leaf);
+            unsigned ms = __ballot_sync(kFull, to_stack);
+            if (to_leaf) lq[__popc(ml & lt)] = pack(cl, ca, cc);
+            if (to_stack) {
+                int pos = top + __popc(ms & lt);
+                if (pos < kStackCap) stk[pos] = pack(cl, ca, cc);
+            }
+            nleaf = __popc(ml);
+            top += __popc(ms);
+            if (top > kStackCap) {
+                top = kStackCap;
+                overflow = true;
+            }
+            __syncwarp();
+        }
+        if (overflow) acc.flags |= PNDF_QF_OVERFLOW;
+    }
+    // warp reduction (fixed order: deterministic for a given query)
+    float s = acc.s, c = acc.c;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        float so = __shfl_down_sync(kFull, s, off);
+        float co = __shfl_down_sync(kFull, c, off);
+        float t = s + so;
+        float err = fabsf(s) >= fabsf(so) ? (s - t) + so : (so - t) + s;
+        s = t;
+        c += co + err;
+    }
+    uint32_t fl = __reduce_or_sync(kFull, acc.flags);
+    if (STATS) {
+        acc.hits = __reduce_add_sync(kFull, acc.hits);
+        acc.hash = __reduce_add_sync(kFull, acc.hash);
+        acc.tests = __reduce_add_sync(kFull, acc.tests);
+        acc.fp64 = __reduce_add_sync(kFull, acc.fp64);
+        acc.degen = __reduce_add_sync(kFull, acc.degen);
+        acc.nodes = __reduce_add_sync(kFull, acc.nodes);
+        acc.leaves = __reduce_add_sync(kFull, acc.leaves);
+    }
+    if (lane == 0) {
+        D_out = s + c;
+        flags_out = fl;
+        if (fl & PNDF_QF_OVERFLOW) atomicOr(&g_status_eval, PNDF_QF_OVERFLOW);
+        if (STATS)
+            *st_out = pndf_query_stats{acc.nodes, acc.leaves, acc.tests, acc.hits, acc.hash, acc.fp64, acc.degen, 0};
+    }
+}
+
+template <int BFMT, int TFMT, bool STATS, bool FLAT>
+__global__ void __launch_bounds__(256) traverse_kernel(MapDesc d, const pndf_query *__restrict__ qs,
+                                                      const uint32_t *__restrict__ order, int64_t nq,
+                                                      float *__restrict__ D, uint32_t *__restrict__ flags,
+                                                      pndf_query_stats *__restrict__ stats,
+                                                      unsigned long long *__restrict__ cursor)
+{
+    extern __shared__ uint32_t smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t *stk = smem + warp * (kStackCap + 32);
+    uint32_t *lq = stk + kStackCap;
+    while (true) {
+        unsigned long long k = 0;
+        if (lane == 0) k = atomicAdd(cursor, 1ull);
+        k = __shfl_sync(kFull, k, 0);
+        if (k >= (unsigned long long)nq) break;
+        int64_t qi = order ? int64_t(order[k]) : int64_t(k);
+        pndf_query rec = qs[qi];
+        float Dv;
+        uint32_t fv;
+        eval_one<BFMT, TFMT, STATS, FLAT>(d, rec, lane, stk, lq, Dv, fv, stats ? stats + qi : nullptr);
+        if (lane == 0) {
+            D[qi] = Dv;
+            if (flags) flags[qi] = fv;
+        }
+    }
+}
+
+// ---- query keying and counting sort ----
+
+__global__ void key_hist(MapDesc d, const pndf_query *__restrict__ qs, int64_t nq, uint16_t *__restrict__ keys,
+                         uint32_t *__restrict__ hist)
+{
+    __shared__ uint32_t h[kKeyBins];
+    for (int i = threadIdx.x; i < kKeyBins; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const float inv_n = 16.0f / float(d.n);
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < nq; k += int64_t(gridDim.x) * blockDim.x) {
+        pndf_query r = qs[k];
+        Query q = make_query(r);
+        int e = q.valid ? entry_level(q, d.L) : 0;
+        int tx = min(15, max(0, int(r.x * inv_n))), ty = min(15, max(0, int(r.y * inv_n)));
+        uint16_t key = uint16_t(((15 - e) << 8) | morton2(tx, ty));
+        keys[k] = key;
+        atomicAdd(&h[key], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kKeyBins; i += blockDim.x)
+        if (h[i]) atomicAdd(&hist[i], h[i]);
+}
+
+// One CTA of 1024 threads: exclusive scan of kKeyBins counts in place.
+__global__ void __launch_bounds__(1024) key_scan(uint32_t *__restrict__ hist)
+{
+    constexpr int per = kKeyBins / 1024;
+    __shared__ uint32_t part[1024];
+    uint32_t v[per], sum = 0;
+    for (int i = 0; i < per; ++i) {
+        v[i] = hist[threadIdx.x * per + i];
+        sum += v[i];
+    }
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        uint32_t t = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += t;
+        __syncthreads();
+    }
+    uint32_t run = part[threadIdx.x] - sum;
+    for (int i = 0; i < per; ++i) {
+        hist[threadIdx.x * per + i] = run;
+        run += v[i];
+    }
+}
+
+__global__ void key_place(const uint16_t *__restrict__ keys, int64_t nq, uint32_t *__restrict__ offsets,
+                          uint32_t *__restrict__ order)
+{
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < nq; k += int64_t(gridDim.x) * blockDim.x) {
+        uint32_t pos = atomicAdd(&offsets[keys[k]], 1u);
+        order[pos] = uint32_t(k);
+    }
+}
+
+template <int BFMT, int TFMT, bool STATS, bool FLAT>
+cudaError_t launch_traverse(const MapDesc &d, const pndf_query *q, const uint32_t *order, int64_t nq, float *D,
+                            uint32_t *flags, pndf_query_stats *stats, unsigned long long *cursor, int warps,
+                            int ctas_per_sm, cudaStream_t s)
+{
+    auto kern = traverse_kernel<BFMT, TFMT, STATS, FLAT>;
+    int threads = warps * 32;
+    size_t smem = size_t(warps) * (kStackCap + 32) * sizeof(uint32_t);
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    if (ctas_per_sm > 0 && ctas_per_sm < occ) occ = ctas_per_sm;
+    int64_t want = (nq + warps - 1) / warps;
+    int64_t grid = int64_t(sms) * occ;
+    if (grid > want) grid = want;
+    if (grid < 1) grid = 1;
+    kern<<<unsigned(grid), threads, smem, s>>>(d, q, order, nq, D, flags, stats, cursor);
+    return cudaGetLastError();
+}
+
+template <int BFMT, int TFMT>
+cudaError_t dispatch_stats(const MapDesc &d, const pndf_query *q, const uint32_t *order, int64_t nq, float *D,
+                           uint32_t *flags, pndf_query_stats *stats, unsigned long long *cursor,
+                           const pndf_eval_config &cfg, cudaStream_t s)
+{
+    int warps = cfg.warps_per_cta > 0 ? cfg.warps_per_cta : 8;
+    bool flat = cfg.mode == PNDF_MODE_FLAT;
+    if (stats)
+        return flat ? launch_traverse<BFMT, TFMT, true, true>(d, q, order, nq, D, flags, stats, cursor, warps,
+                                                               cfg.ctas_per_sm, s)
+                    : launch_traverse<BFMT, TFMT, true, false>(d, q, order, nq, D, flags, stats, cursor, warps,
+                                                                cfg.ctas_per_sm, s);
+    return flat ? launch_traverse<BFMT, TFMT, false, true>(d, q, order, nq, D, flags, stats, cursor, warps,
+                                                            cfg.ctas_per_sm, s)
+                : launch_traverse<BFMT, TFMT, false, false>(d, q, order, nq, D, flags, stats, cursor, warps,
+                                                             cfg.ctas_per_sm, s);
+}
+
+}  // namespace
+
+pndf_status launch_eval(const pndf_hierarchy *h, const pndf_query *q, int64_t nq, float *D, uint32_t *flags,
+                        pndf_query_stats *stats, const pndf_eval_config &cfg, cudaStream_t s)
+{
+    if (nq == 0) return PNDF_OK;
+    const MapDesc &d = h->d;
+    const bool sort = cfg.sort != 0;
+    // scratch: cursor (8 B, padded to 256), key histogram, keys, order
+    size_t off_hist = 256, off_keys = off_hist + kKeyBins * sizeof(uint32_t);
+    size_t off_order = off_keys + ((size_t(nq) * sizeof(uint16_t) + 255) & ~size_t(255));
+    size_t bytes = sort ? off_order + size_t(nq) * sizeof(uint32_t) : 256;
+    void *scratch = nullptr;
+    if (cudaMallocAsync(&scratch, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return PNDF_ERR_OOM;
+    }
+    char *base = static_cast<char *>(scratch);
+    auto *cursor = reinterpret_cast<unsigned long long *>(base);
+    uint32_t *order = nullptr;
+    cudaError_t e = cudaMemsetAsync(base, 0, sort ? off_keys : 256, s);
+    if (e == cudaSuccess && sort) {
+        auto *hist = reinterpret_cast<uint32_t *>(base + off_hist);
+        auto *keys = reinterpret_cast<uint16_t *>(base + off_keys);
+        order = reinterpret_cast<uint32_t *>(base + off_order);
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        int64_t blocks = (nq + 255) / 256;
+        if (blocks > int64_t(sms) * 4) blocks = int64_t(sms) * 4;
+        key_hist<<<unsigned(blocks), 256, 0, s>>>(d, q, nq, keys, hist);
+        key_scan<<<1, 1024, 0, s>>>(hist);
+        key_place<<<unsigned(blocks), 256, 0, s>>>(keys, nq, hist, order);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        if (d.bounds_fmt == PNDF_BOUNDS_F32)
+            e = d.texel_fmt == PNDF_TEXEL_F32X2
+                    ? dispatch_stats<PNDF_BOUNDS_F32, PNDF_TEXEL_F32X2>(d, q, order, nq, D, flags, stats, cursor, cfg, s)
+                    : dispatch_stats<PNDF_BOUNDS_F32, PNDF_TEXEL_F16X2>(d, q, order, nq, D, flags, stats, cursor, cfg, s);
+        else
+            e = d.texel_fmt == PNDF_TEXEL_F32X2
+                    ? dispatch_stats<PNDF_BOUNDS_F16_OUTWARD, PNDF_TEXEL_F32X2>(d, q, order, nq, D, flags, stats, cursor,
+                                                                             cfg, s)
+                    : dispatch_stats<PNDF_BOUNDS_F16_OUTWARD, PNDF_TEXEL_F16X2>(d, q, order, nq, D, flags, stats, cursor,
+                                                                             cfg, s);
+    }
+    cudaError_t ef = cudaFreeAsync(scratch, s);
+    if (e != cudaSuccess || ef != cudaSuccess) return PNDF_ERR_CUDA;
+    return PNDF_OK;
+}
+
+cudaError_t read_status_eval(cudaStream_t s, uint32_t *bits, bool clear)
+{
+    unsigned int v = 0;
+    cudaError_t e = cudaMemcpyFromSymbolAsync(&v, g_status_eval, sizeof(v), 0, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && clear && v) {
+        unsigned int z = 0;
+        e = cudaMemcpyToSymbolAsync(g_status_eval, &z, sizeof(z), 0, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    *bits = v;
+    return e;
+}
+
+}  // namespace pndf

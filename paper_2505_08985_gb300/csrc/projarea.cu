@@ -1,0 +1,584 @@
+// Analytic projected area P(w) of a footprint (Sec. 4.3, Eq. 9-11, App. B).
+//
+//   P(w) = sum over footprint triangles T of k_r(T) / |cross(T)| * V_T(w),
+//   V_T(w) = integral over n+(T) of (w . m~) / m~_z dm,
+// where n+(T) is the part of the normal triangle whose normals see w, k_r(T)
+// the kernel at T's uv centroid (cut where q > 16), cross(T) = (n_b - n_a) x
+// (n_c - n_a).  Every triangle in the footprint is integrated (no pruning:
+// every visible triangle contributes).
+//
+// Per triangle (FP32):
+//  * all three vertices see w  =>  the whole triangle does (the visible region,
+//    a right half-disk joined to a left half-ellipse, is convex; App. B), and
+//    V_T = w_z A + w_x Wx + w_y Wy with Wx = -oint m~_z dm_y, Wy = oint m~_z
+//    dm_x (Green's theorem on d(-m~_z)/dm_x = m_x/m~_z).  Along an edge the
+//    mean of m~_z is the arc-area formula of App. B; it is evaluated in a
+//    cancellation-free form (the asin difference as one atan2 of exact
+//    products), so no rotation is needed and the 1/|cross| division keeps
+//    FP32 accuracy for small triangles.
+//  * otherwise: rotate so w_y = 0, orient counter-clockwise, clip each edge
+//    with Alg. 1, sum Eq. 11's line terms (minus sign on the w_x part) and the
+//    ellipse arcs (1/2)[F(e_y) - F(s_y)] that join an exit to the next entry.
+//  * |cross| < 1e-7 (normal area < 5e-8): the 3-point edge-midpoint rule on
+//    max(m~.w, 0)/m~_z, exact for quadratics; the triangle spans < 1e-3 in
+//    normal space so its error is far below FP32 rounding of the other path.
+//
+// Work decomposition: each request's footprint is cut into bands of kBand quad
+// rows; one warp integrates one band (lane = quad column, two triangles per
+// lane), compensated sums are reduced across the warp and stored per band;
+// a second kernel adds a request's bands in fixed order, so results do not
+// depend on scheduling or on which other requests share the launch.
+#include "common.cuh"
+
+namespace pndf {
+
+__device__ unsigned int g_status_projarea;
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kBand = 8;                 // quad rows per work item
+
+__device__ __forceinline__ float dop(float a, float b, float c, float d)
+{
+    float w = c * d;
+    float e = fmaf(-c, d, w);
+    float f = fmaf(a, b, -w);
+    return f + e;
+}
+
+__device__ __forceinline__ float zof(float2 p)
+{
+    return sqrtf(fmaxf(0.f, 1.f - fmaf(p.x, p.x, p.y * p.y)));
+}
+
+// phi(t) = t - sin t, by its Taylor series for small |t| (no cancellation).
+__device__ __forceinline__ float phi_small(float t)
+{
+    if (fabsf(t) < 0.25f) {
+        float t2 = t * t;
+        return t * t2 * (1.f / 6.f) * (1.f - t2 * (1.f / 20.f) * (1.f - t2 * (1.f / 42.f) * (1.f - t2 * (1.f / 72.f))));
+    }
+    return t - sinf(t);
+}
+
+// Curvature part H of the mean of m~_z = sqrt(1 - |m|^2) along p0 -> p1, over
+// its trapezoid value (z0 + z1)/2.  With d the unit direction, u the abscissa
+// along the line (u1 = u0 + L) and r^2 = 1 - s^2 = z0^2 + u0^2 (s the line's
+// distance to the origin), the arc-area formula of App. B gives
+//   L * mean = (1/2)[u z]_{u0}^{u1} + (r^2/2)(asin(u1/r) - asin(u0/r)),
+// so L * H = (r^2/2)(dth - sin dth) with dth the asin difference, which is
+// atan2(X, Y), X = u1 z0 - u0 z1 = L (r^2 + z0 z1 + u0 u1) / (z0 + z1),
+// Y = z0 z1 + u0 u1 (both free of cancellation).
+__device__ __forceinline__ float edge_curv(float2 p0, float z0, float2 p1, float z1)
+{
+    float ex = p1.x - p0.x, ey = p1.y - p0.y;
+    float L2 = fmaf(ex, ex, ey * ey);
+    if (L2 == 0.f) return 0.f;
+    float L = sqrtf(L2);
+    float inv = 1.f / L;
+    float u0 = fmaf(ex, p0.x, ey * p0.y) * inv;
+    float u1 = u0 + L;
+    float r2 = fmaf(z0, z0, u0 * u0);
+    float Y = fmaf(z0, z1, u0 * u1);
+    float X = L * (r2 + Y) / (z0 + z1);
+    return 0.5f * r2 * phi_small(atan2f(X, Y)) * inv;
+}
+
+// z(q) - z(p) for z = sqrt(1 - |m|^2), from (|p|^2 - |q|^2) / (z(p) + z(q)).
+__device__ __forceinline__ float zdiff(float2 p, float zp, float2 q, float zq)
+{
+    return -fmaf(q.x - p.x, q.x + p.x, (q.y - p.y) * (q.y + p.y)) / (zp + zq);
+}
+
+// ---- FP64 path: the paper's per-triangle algorithm (rotation, Alg. 1,
+// Eq. 11 lines with a minus sign on the w_x part, ellipse arcs), used for
+// partially visible triangles and for ill-conditioned slivers ----
+
+__device__ __forceinline__ double Fasin_d(double p)
+{
+    p = fmin(1.0, fmax(-1.0, p));
+    return asin(p) + p * sqrt(fmax(0.0, 1.0 - p * p));
+}
+
+__device__ bool clip_edge_d(const double a[2], const double b[2], double wz, double oa[2], double ob[2], bool &ca,
+                            bool &cb)
+{
+    double dx = b[0] - a[0], dy = b[1] - a[1];
+    double w2 = wz * wz;
+    double A = w2 * dy * dy + dx * dx;
+    double B = 2.0 * (w2 * a[1] * dy + a[0] * dx);
+    double C = w2 * (a[1] * a[1] - 1.0) + a[0] * a[0];
+    double C1 = w2 * (b[1] * b[1] - 1.0) + b[0] * b[0];
+    double disc = B * B - 4.0 * A * C;
+    bool c0 = C > 0.0 && a[0] < 0.0;
+    bool c1 = C1 > 0.0 && b[0] < 0.0;
+    oa[0] = a[0];
+    oa[1] = a[1];
+    ob[0] = b[0];
+    ob[1] = b[1];
+    ca = false;
+    cb = false;
+    if (c0 || c1) {
+        if (disc < 0.0) return false;
+        double sq = sqrt(disc);
+        double t0 = (-B - sq) / (2.0 * A);
+        double t1 = (-B + sq) / (2.0 * A);
+        if (c0 && c1 && (t0 < 0.0 || t0 > 1.0 || t1 < 0.0 || t1 > 1.0)) return false;
+        if (c0) {
+            oa[0] = a[0] + t0 * dx;
+            oa[1] = a[1] + t0 * dy;
+            ca = true;
+        }
+        if (c1) {
+            ob[0] = a[0] + t1 * dx;
+            ob[1] = a[1] + t1 * dy;
+            cb = true;
+        }
+    }
+    return true;
+}
+
+__device__ double line_term_d(const double p[2], const double q[2], double wr, double wz)
+{
+    double tz = 0.5 * wz * (q[1] - p[1]) * (q[0] + p[0]);
+    double ex = q[0] - p[0], ey = q[1] - p[1];
+    double len = sqrt(ex * ex + ey * ey);
+    if (len == 0.0) return 0.0;
+    double dx = ex / len, dy = ey / len;
+    double sd = dy * p[0] - dx * p[1];
+    double r2 = 1.0 - sd * sd;
+    double r = sqrt(r2);
+    double tx = 0.5 * wr * r2 * dy * (Fasin_d((dx * q[0] + dy * q[1]) / r) - Fasin_d((dx * p[0] + dy * p[1]) / r));
+    return tz - tx;
+}
+
+struct Dir {
+    float wx, wy, wz;  // unit direction
+    float c, s, wr;    // rotation to w_y = 0: (c, s) = w_xy / |w_xy|, wr = |w_xy|
+};
+
+constexpr int kGL = 16;
+// Gauss-Legendre nodes and weights on [-1, 1], computed on the host.
+struct GLTable {
+    double x[kGL], w[kGL];
+};
+
+// max(m~ . w, 0) / m~_z in FP64
+__device__ __forceinline__ double vis_ratio_d(double mx, double my, double wx, double wy, double wz)
+{
+    double mz = sqrt(fmax(0.0, 1.0 - mx * mx - my * my));
+    double c = mx * wx + my * wy + mz * wz;
+    return fmax(c, 0.0) / mz;
+}
+
+// Eq. 13's uv-space integral over a uv triangle (area 1/2) whose normal image
+// collapsed onto a segment: a uniform point of the triangle maps to the
+// piecewise-linear density on the sorted vertex positions tau_1..tau_3 along
+// the segment P -> Q (the farthest vertex pair); the visible interval comes
+// from Alg. 1; each linear piece is integrated by Gauss-Legendre.
+__device__ __noinline__ double collapsed_uv_form_d(const double v[3][2], double wx, double wy, double wz, double cs,
+                                                    double sn, const GLTable &gl)
+{
+    double best = -1.0;
+    int ip = 0, iq = 1;
+    for (int i = 0; i < 3; ++i)
+        for (int j = i + 1; j < 3; ++j) {
+            double dx = v[j][0] - v[i][0], dy = v[j][1] - v[i][1];
+            double d2 = dx * dx + dy * dy;
+            if (d2 > best) {
+                best = d2;
+                ip = i;
+                iq = j;
+            }
+        }
+    if (best == 0.0) return 0.5 * vis_ratio_d(v[0][0], v[0][1], wx, wy, wz);
+    const double *P = v[ip], *Q = v[iq];
+    double ex = Q[0] - P[0], ey = Q[1] - P[1];
+    double tau[3];
+    for (int i = 0; i < 3; ++i) tau[i] = ((v[i][0] - P[0]) * ex + (v[i][1] - P[1]) * ey) / best;
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2 - i; ++j)
+            if (tau[j] > tau[j + 1]) {
+                double t = tau[j];
+                tau[j] = tau[j + 1];
+                tau[j + 1] = t;
+            }
+    double pr[2] = {cs * P[0] + sn * P[1], -sn * P[0] + cs * P[1]};
+    double qr[2] = {cs * Q[0] + sn * Q[1], -sn * Q[0] + cs * Q[1]};
+    double oa[2], ob[2];
+    bool ca, cb;
+    if (!clip_edge_d(pr, qr, wz, oa, ob, ca, cb)) return 0.0;
+    double L2 = (qr[0] - pr[0]) * (qr[0] - pr[0]) + (qr[1] - pr[1]) * (qr[1] - pr[1]);
+    double tlo = ((oa[0] - pr[0]) * (qr[0] - pr[0]) + (oa[1] - pr[1]) * (qr[1] - pr[1])) / L2;
+    double thi = ((ob[0] - pr[0]) * (qr[0] - pr[0]) + (ob[1] - pr[1]) * (qr[1] - pr[1])) / L2;
+    double span = tau[2] - tau[0];
+    double sum = 0.0;
+    for (int piece = 0; piece < 2; ++piece) {
+        double t0 = tau[piece], t1 = tau[piece + 1];
+        double lo = fmax(t0, tlo), hi = fmin(t1, thi);
+        if (!(hi > lo) || t1 == t0) continue;
+        for (int g = 0; g < kGL; ++g) {
+            double t = 0.5 * (lo + hi) + 0.5 * (hi - lo) * gl.x[g];
+            double dens = piece == 0 ? 2.0 * (t - t0) / (span * (t1 - t0)) : 2.0 * (t1 - t) / (span * (t1 - t0));
+            sum += 0.5 * (hi - lo) * gl.w[g] * dens * vis_ratio_d(P[0] + t * ex, P[1] + t * ey, wx, wy, wz);
+        }
+    }
+    return 0.5 * sum;
+}
+
+__device__ __noinline__ float tri_ratio_d(float2 a, float2 b, float2 c, const Dir &w, const GLTable &gl)
+{
+    double wx = w.wx, wy = w.wy, wz = w.wz;
+    double wr = sqrt(wx * wx + wy * wy);
+    double cs = wr > 0.0 ? wx / wr : 1.0, sn = wr > 0.0 ? wy / wr : 0.0;
+    double A2 = (double(b.x) - a.x) * (double(c.y) - a.y) - (double(b.y) - a.y) * (double(c.x) - a.x);
+    if (fabs(A2) < 1e-12) {
+        double vv[3][2] = {{a.x, a.y}, {b.x, b.y}, {c.x, c.y}};
+        return float(collapsed_uv_form_d(vv, wx, wy, wz, cs, sn, gl));
+    }
+    double v[3][2] = {{cs * a.x + sn * a.y, -sn * a.x + cs * a.y}, {0, 0}, {0, 0}};
+    const float2 &p1 = A2 > 0.0 ? b : c, &p2 = A2 > 0.0 ? c : b;
+    v[1][0] = cs * p1.x + sn * p1.y;
+    v[1][1] = -sn * p1.x + cs * p1.y;
+    v[2][0] = cs * p2.x + sn * p2.y;
+    v[2][1] = -sn * p2.x + cs * p2.y;
+    double oa[3][2], ob[3][2];
+    bool alive[3], ca[3], cb[3];
+    for (int k = 0; k < 3; ++k) alive[k] = clip_edge_d(v[k], v[(k + 1) % 3], wz, oa[k], ob[k], ca[k], cb[k]);
+    double sum = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        if (!alive[k]) continue;
+        sum += line_term_d(oa[k], ob[k], wr, wz);
+        int nx = alive[(k + 1) % 3] ? (k + 1) % 3 : (alive[(k + 2) % 3] ? (k + 2) % 3 : k);
+        if (cb[k] || ca[nx]) sum += 0.5 * (Fasin_d(ob[k][1]) - Fasin_d(oa[nx][1]));
+    }
+    return float(sum / fabs(A2));
+}
+
+// V_T / |cross| for one triangle (vertices a, b, c with z values).
+__device__ __forceinline__ float tri_ratio(float2 a, float za, float2 b, float zb, float2 c, float zc, const Dir &w,
+                                           const GLTable &gl)
+{
+    float va = fmaf(w.wx, a.x, fmaf(w.wy, a.y, w.wz * za));
+    float vb = fmaf(w.wx, b.x, fmaf(w.wy, b.y, w.wz * zb));
+    float vc = fmaf(w.wx, c.x, fmaf(w.wy, c.y, w.wz * zc));
+    if (!(va >= 0.f && vb >= 0.f && vc >= 0.f)) return tri_ratio_d(a, b, c, w, gl);
+    float2 ab = make_float2(b.x - a.x, b.y - a.y), ac = make_float2(c.x - a.x, c.y - a.y);
+    float2 bc = make_float2(c.x - b.x, c.y - b.y);
+    float cr = dop(ab.x, ac.y, ab.y, ac.x);
+    float P2 = fmaxf(fmaf(ab.x, ab.x, ab.y * ab.y), fmaxf(fmaf(ac.x, ac.x, ac.y * ac.y), fmaf(bc.x, bc.x, bc.y * bc.y)));
+    if (P2 == 0.f) return 0.5f * (w.wz + fmaf(w.wx, a.x, w.wy * a.y) / za);  // all three normals equal
+    // The boundary form below has FP32 error about 1.5 eps P^2 / |cross|.
+    if (P2 > 2.0f * fabsf(cr)) {
+        if (P2 < 1e-4f) {
+            // small sliver: 3-point edge-midpoint rule (exact for quadratics) on
+            // the mean of (w . m~)/m~_z; V / |cross| = mean / 2
+            float2 m0 = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y + b.y));
+            float2 m1 = make_float2(0.5f * (b.x + c.x), 0.5f * (b.y + c.y));
+            float2 m2 = make_float2(0.5f * (c.x + a.x), 0.5f * (c.y + a.y));
+            float z0 = zof(m0), z1 = zof(m1), z2 = zof(m2);
+            float f0 = fmaf(w.wx, m0.x, w.wy * m0.y) / z0;
+            float f1 = fmaf(w.wx, m1.x, w.wy * m1.y) / z1;
+            float f2 = fmaf(w.wx, m2.x, w.wy * m2.y) / z2;
+            return 0.5f * w.wz + (f0 + f1 + f2) * (1.f / 6.f);
+        }
+        if (P2 > 200.0f * fabsf(cr)) return tri_ratio_d(a, b, c, w, gl);  // long sliver or collapsed
+    }
+    // Fully visible: V = w_z A + w_x Wx + w_y Wy, Wx = -oint m~_z dm_y,
+    // Wy = oint m~_z dm_x.  With the edge mean of m~_z split into its
+    // trapezoid value and the curvature part H, the trapezoid sums collapse to
+    // 2x2 determinants of vertex differences in (x, z) and (y, z).
+    float dzab = zdiff(a, za, b, zb), dzac = zdiff(a, za, c, zc);
+    float dety = dop(ab.y, dzac, ac.y, dzab);
+    float detx = dop(ab.x, dzac, ac.x, dzab);
+    float hab = edge_curv(a, za, b, zb), hbc = edge_curv(b, zb, c, zc), hca = edge_curv(c, zc, a, za);
+    float Wx = 0.5f * dety - (hab * ab.y + hbc * bc.y - hca * ac.y);
+    float Wy = -0.5f * detx + (hab * ab.x + hbc * bc.x - hca * ac.x);
+    // orientation-following integrals over the signed cross = the
+    // counter-clockwise value over |cross|
+    return 0.5f * w.wz + fmaf(w.wx, Wx, w.wy * Wy) / cr;
+}
+
+struct Req {
+    float x, y, ia, ib, ic, norm, ry;
+    int j0, j1, i0, i1;
+    bool valid;
+};
+
+__device__ __forceinline__ Req make_req(const pndf_query &r, int n)
+{
+    Req q;
+    float det = r.sxx * r.syy - r.sxy * r.sxy;
+    q.valid = (r.sxx > 0.f) && (r.syy > 0.f) && (det > 0.f) && isfinite(det) && isfinite(r.x) && isfinite(r.y);
+    q.x = r.x;
+    q.y = r.y;
+    float inv = 1.f / det;
+    q.ia = r.syy * inv;
+    q.ib = -r.sxy * inv;
+    q.ic = r.sxx * inv;
+    q.norm = 1.f / (2.f * kPi * sqrtf(det));
+    float rx = 4.f * sqrtf(r.sxx) * (1.f + 1e-5f) + 1e-6f;
+    q.ry = 4.f * sqrtf(r.syy) * (1.f + 1e-5f) + 1e-6f;
+    // quads whose centroid (i + 1/3 or 2/3) can lie in the 4-sigma box
+    // clamped in float first so no int conversion can overflow
+    float fi0 = fmaxf(floorf(r.x - rx) - 1.f, 0.f), fi1 = fminf(ceilf(r.x + rx), float(n - 2));
+    float fj0 = fmaxf(floorf(r.y - q.ry) - 1.f, 0.f), fj1 = fminf(ceilf(r.y + q.ry), float(n - 2));
+    bool empty = !(fi0 <= fi1) || !(fj0 <= fj1);
+    q.i0 = empty ? 0 : int(fi0);
+    q.i1 = empty ? -1 : int(fi1);
+    q.j0 = empty ? 0 : int(fj0);
+    q.j1 = empty ? -1 : int(fj1);
+    if (!q.valid || q.i0 > q.i1 || q.j0 > q.j1) {
+        q.i1 = q.i0 - 1;
+        q.j1 = q.j0 - 1;
+    }
+    return q;
+}
+
+__device__ __forceinline__ float wq(const Req &q, float dx, float dy)
+{
+    return fmaf(q.ia * dx, dx, fmaf(2.f * q.ib * dx, dy, q.ic * dy * dy));
+}
+
+template <int TFMT>
+__device__ __forceinline__ float2 texel(const MapDesc &d, int i, int j)
+{
+    size_t idx = size_t(j) * d.n + i;
+    if (TFMT == PNDF_TEXEL_F32X2) return __ldg(reinterpret_cast<const float2 *>(d.texels) + idx);
+    return __half22float2(__ldg(reinterpret_cast<const __half2 *>(d.texels) + idx));
+}
+
+__global__ void pa_bands(MapDesc d, const pndf_query *__restrict__ qs, int64_t k0, int cnt, uint32_t *__restrict__ nb)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= cnt) return;
+    Req q = make_req(qs[k0 + t], d.n);
+    int rows = q.j1 - q.j0 + 1;
+    nb[t] = rows > 0 ? uint32_t((rows + kBand - 1) / kBand) : 0u;
+}
+
+// exclusive scan of cnt (<= 65536) values in place, one CTA of 1024 threads;
+// total goes to nb[cnt]
+__global__ void __launch_bounds__(1024) pa_scan(uint32_t *__restrict__ nb, int cnt)
+{
+    __shared__ uint32_t part[1024];
+    const int per = (cnt + 1023) / 1024;
+    const int b0 = threadIdx.x * per;
+    uint32_t sum = 0;
+    for (int i = 0; i < per; ++i)
+        if (b0 + i < cnt) sum += nb[b0 + i];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        uint32_t t = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += t;
+        __syncthreads();
+    }
+    uint32_t run = part[threadIdx.x] - sum;
+    for (int i = 0; i < per; ++i) {
+        if (b0 + i < cnt) {
+            uint32_t v = nb[b0 + i];
+            nb[b0 + i] = run;
+            run += v;
+        }
+    }
+    if (threadIdx.x == 1023) nb[cnt] = part[1023];
+}
+
+template <int TFMT>
+__global__ void __launch_bounds__(256) pa_items(MapDesc d, const pndf_query *__restrict__ qs,
+                                               const float *__restrict__ omega, int64_t k0, int cnt,
+                                               const uint32_t *__restrict__ off, float2 *__restrict__ part,
+                                               unsigned int *__restrict__ cursor, GLTable gl)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t total = off[cnt];
+    while (true) {
+        uint32_t it = 0;
+        if (lane == 0) it = atomicAdd(cursor, 1u);
+        it = __shfl_sync(kFull, it, 0);
+        if (it >= total) break;
+        // request owning this item: last t with off[t] <= it
+        int lo = 0, hi = cnt - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (off[mid] <= it)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const int t = lo;
+        const pndf_query rec = qs[k0 + t];
+        const Req q = make_req(rec, d.n);
+        Dir w;
+        w.wx = omega[3 * (k0 + t)];
+        w.wy = omega[3 * (k0 + t) + 1];
+        w.wz = omega[3 * (k0 + t) + 2];
+        w.wr = sqrtf(fmaf(w.wx, w.wx, w.wy * w.wy));
+        w.c = w.wr > 0.f ? w.wx / w.wr : 1.f;
+        w.s = w.wr > 0.f ? w.wy / w.wr : 0.f;
+        const int band = int(it - off[t]);
+        const int jb0 = q.j0 + band * kBand, jb1 = min(q.j1, jb0 + kBand - 1);
+        float s = 0.f, c = 0.f;
+        for (int j = jb0; j <= jb1; ++j) {
+            const float dyl = (float(j) - q.y) + (1.f / 3.f), dyu = (float(j) - q.y) + (2.f / 3.f);
+            for (int ib = q.i0; ib <= q.i1; ib += 32) {
+                const int i = ib + lane;
+                if (i > q.i1) continue;
+                const float dxl = (float(i) - q.x) + (1.f / 3.f), dxu = (float(i) - q.x) + (2.f / 3.f);
+                const float ql = wq(q, dxl, dyl), qu = wq(q, dxu, dyu);
+                if (ql > kQCut && qu > kQCut) continue;
+                float2 n0 = texel<TFMT>(d, i, j), n1 = texel<TFMT>(d, i + 1, j);
+                float2 n2 = texel<TFMT>(d, i, j + 1), n3 = texel<TFMT>(d, i + 1, j + 1);
+                float z0 = zof(n0), z1 = zof(n1), z2 = zof(n2), z3 = zof(n3);
+                float v[2] = {0.f, 0.f};
+                if (ql <= kQCut) v[0] = q.norm * expf(-0.5f * ql) * tri_ratio(n0, z0, n1, z1, n2, z2, w, gl);
+                if (qu <= kQCut) v[1] = q.norm * expf(-0.5f * qu) * tri_ratio(n3, z3, n2, z2, n1, z1, w, gl);
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    float tt = s + v[k];
+                    c += fabsf(s) >= fabsf(v[k]) ? (s - tt) + v[k] : (v[k] - tt) + s;
+                    s = tt;
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            float so = __shfl_down_sync(kFull, s, o), co = __shfl_down_sync(kFull, c, o);
+            float tt = s + so;
+            float err = fabsf(s) >= fabsf(so) ? (s - tt) + so : (so - tt) + s;
+            s = tt;
+            c += co + err;
+        }
+        if (lane == 0) part[it] = make_float2(s, c);
+    }
+}
+
+// one warp per request: fixed-order sum of its bands
+__global__ void pa_reduce(const pndf_query *__restrict__ qs, int64_t k0, int cnt, const uint32_t *__restrict__ off,
+                          const float2 *__restrict__ part, float *__restrict__ P)
+{
+    const int lane = threadIdx.x & 31;
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (t >= cnt) return;
+    const uint32_t b0 = off[t], b1 = off[t + 1];
+    float s = 0.f, c = 0.f;
+    for (uint32_t b = b0 + lane; b < b1; b += 32) {
+        float2 p = part[b];
+        float tt = s + p.x;
+        c += (fabsf(s) >= fabsf(p.x) ? (s - tt) + p.x : (p.x - tt) + s) + p.y;
+        s = tt;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        float so = __shfl_down_sync(kFull, s, o), co = __shfl_down_sync(kFull, c, o);
+        float tt = s + so;
+        float err = fabsf(s) >= fabsf(so) ? (s - tt) + so : (so - tt) + s;
+        s = tt;
+        c += co + err;
+    }
+    if (lane == 0) {
+        const pndf_query r = qs[k0 + t];
+        float det = r.sxx * r.syy - r.sxy * r.sxy;
+        bool valid = (r.sxx > 0.f) && (r.syy > 0.f) && (det > 0.f) && isfinite(det) && isfinite(r.x) && isfinite(r.y);
+        if (!valid) atomicOr(&g_status_projarea, PNDF_QF_INVALID);
+        P[k0 + t] = valid ? s + c : __int_as_float(0x7fc00000);
+    }
+}
+
+// Gauss-Legendre rule on [-1, 1]: nodes are the roots of P_n, found by
+// Newton's method from the Chebyshev-like initial guesses cos(pi (i + 3/4) /
+// (n + 1/2)); weights 2 / ((1 - x^2) P_n'(x)^2).
+GLTable make_gl()
+{
+    GLTable t;
+    const int n = kGL;
+    for (int i = 0; i < n; ++i) {
+        double x = cos(3.14159265358979323846 * (i + 0.75) / (n + 0.5));
+        double dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = x;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (x * p1 - p0) / (x * x - 1.0);
+            double dx = p1 / dp;
+            x -= dx;
+            if (fabs(dx) < 1e-16) break;
+        }
+        t.x[i] = x;
+        t.w[i] = 2.0 / ((1.0 - x * x) * dp * dp);
+    }
+    return t;
+}
+
+}  // namespace
+
+pndf_status launch_projarea(const pndf_hierarchy *h, const pndf_query *q, const float *omega, int64_t nq, float *P,
+                            cudaStream_t s)
+{
+    if (nq == 0) return PNDF_OK;
+    const MapDesc &d = h->d;
+    const int maxbands = (d.n - 1 + kBand - 1) / kBand + 1;
+    // requests per chunk: bounded by the scan (65536) and by 256 MiB of band partials
+    int64_t chunk = (int64_t(1) << 28) / (int64_t(sizeof(float2)) * maxbands);
+    if (chunk > 65536) chunk = 65536;
+    if (chunk < 1024) chunk = 1024;
+    if (chunk > nq) chunk = nq;
+    size_t off_bytes = ((size_t(chunk) + 1) * sizeof(uint32_t) + 255) & ~size_t(255);
+    size_t part_bytes = size_t(chunk) * maxbands * sizeof(float2);
+    void *scratch = nullptr;
+    if (cudaMallocAsync(&scratch, 256 + off_bytes + part_bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return PNDF_ERR_OOM;
+    }
+    char *base = static_cast<char *>(scratch);
+    auto *cursor = reinterpret_cast<unsigned int *>(base);
+    auto *off = reinterpret_cast<uint32_t *>(base + 256);
+    auto *part = reinterpret_cast<float2 *>(base + 256 + off_bytes);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    static const GLTable gl = make_gl();
+    cudaError_t e = cudaSuccess;
+    for (int64_t k0 = 0; k0 < nq && e == cudaSuccess; k0 += chunk) {
+        int cnt = int(nq - k0 < chunk ? nq - k0 : chunk);
+        e = cudaMemsetAsync(cursor, 0, sizeof(unsigned int), s);
+        if (e != cudaSuccess) break;
+        pa_bands<<<(cnt + 255) / 256, 256, 0, s>>>(d, q, k0, cnt, off);
+        pa_scan<<<1, 1024, 0, s>>>(off, cnt);
+        int occ = 0;
+        if (d.texel_fmt == PNDF_TEXEL_F32X2) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pa_items<PNDF_TEXEL_F32X2>, 256, 0);
+            pa_items<PNDF_TEXEL_F32X2><<<sms * (occ > 0 ? occ : 1), 256, 0, s>>>(d, q, omega, k0, cnt, off, part, cursor, gl);
+        } else {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pa_items<PNDF_TEXEL_F16X2>, 256, 0);
+            pa_items<PNDF_TEXEL_F16X2><<<sms * (occ > 0 ? occ : 1), 256, 0, s>>>(d, q, omega, k0, cnt, off, part, cursor, gl);
+        }
+        pa_reduce<<<(cnt * 32 + 255) / 256, 256, 0, s>>>(q, k0, cnt, off, part, P);
+        e = cudaGetLastError();
+    }
+    cudaError_t ef = cudaFreeAsync(scratch, s);
+    if (e != cudaSuccess || ef != cudaSuccess) return PNDF_ERR_CUDA;
+    return PNDF_OK;
+}
+
+cudaError_t read_status_projarea(cudaStream_t s, uint32_t *bits, bool clear)
+{
+    unsigned int v = 0;
+    cudaError_t e = cudaMemcpyFromSymbolAsync(&v, g_status_projarea, sizeof(v), 0, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && clear && v) {
+        unsigned int z = 0;
+        e = cudaMemcpyToSymbolAsync(g_status_projarea, &z, sizeof(z), 0, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    *bits = v;
+    return e;
+}
+
+}  // namespace pndf

@@ -1,0 +1,231 @@
+"""Python binding of libpndf.so: the C ABI entry points under the same names.
+
+Argument marshalling only: every step runs in the library's CUDA kernels.
+Torch tensors provide device memory and the current CUDA stream.  Importing
+this module loads the library and raises if it is missing; there is no
+fallback path.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import _build
+
+PNDF_OK = 0
+STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA runtime error",
+                4: "device wait timed out", 5: "device buffer capacity exceeded", 6: "unsupported request",
+                7: "kernel recorded a device-side error"}
+
+PNDF_TEXEL_F32X2 = 0
+PNDF_TEXEL_F16X2 = 1
+PNDF_BOUNDS_F32 = 0
+PNDF_BOUNDS_F16_OUTWARD = 1
+PNDF_MODE_HIERARCHY = 0
+PNDF_MODE_FLAT = 1
+PNDF_QF_FP64 = 1
+PNDF_QF_INVALID = 4
+PNDF_QF_OVERFLOW = 8
+
+STATS_FIELDS = ("nodes", "leaf_blocks", "tri_tests", "hits", "hit_hash", "fp64_tris", "degenerate", "reserved")
+
+
+class PndfError(RuntimeError):
+    def __init__(self, fn: str, code: int):
+        super().__init__(f"{fn}: {STATUS_NAMES.get(code, code)} (status {code})")
+        self.code = code
+
+
+class _BuildParams(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("texel_fmt", ctypes.c_int32), ("bounds_fmt", ctypes.c_int32),
+                ("leaf_level", ctypes.c_int32)]
+
+
+class _EvalConfig(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("sort", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32)]
+
+
+def _load() -> ctypes.CDLL:
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libpndf.so is not built ({path}); run __graft_entry__.build() or "
+                          f"python -m paper_2505_08985_gb300._build")
+    lib = ctypes.CDLL(path)
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    sig = {
+        "pndf_build_hierarchy": ([vp, ctypes.POINTER(_BuildParams), vp, ctypes.POINTER(vp)], i32),
+        "pndf_free_hierarchy": ([vp], None),
+        "pndf_hierarchy_bytes": ([vp], ctypes.c_size_t),
+        "pndf_eval_batch": ([vp, vp, i64, vp, vp, vp, vp], i32),
+        "pndf_eval_batch_ex": ([vp, vp, i64, vp, vp, vp, ctypes.POINTER(_EvalConfig), vp], i32),
+        "pndf_eval_batch_host": ([vp, vp, i64, vp, vp], i32),
+        "pndf_diffuse_projected_area": ([vp, vp, vp, i64, vp, vp], i32),
+        "pndf_device_status": ([vp, ctypes.POINTER(ctypes.c_uint32)], i32),
+        "pndf_status_string": ([i32], ctypes.c_char_p),
+        "pndf_version": ([], i32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+LIB = _load()
+
+
+def _check(fn: str, code: int):
+    if code != PNDF_OK:
+        raise PndfError(fn, code)
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(t) -> int | None:
+    return None if t is None else int(t.data_ptr())
+
+
+def _need(t: torch.Tensor, name: str, dtype=None, device=True, shape_last=None):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if device and not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape_last is not None and t.shape[-1] != shape_last:
+        raise ValueError(f"{name} must have last dimension {shape_last}")
+
+
+class Hierarchy:
+    """A built pyramid (library-owned device memory) plus the map's size/format."""
+
+    def __init__(self, handle: int, n: int, texel_fmt: int, bounds_fmt: int, device: torch.device):
+        self.handle = handle
+        self.n = n
+        self.texel_fmt = texel_fmt
+        self.bounds_fmt = bounds_fmt
+        self.device = device
+
+    @property
+    def nbytes(self) -> int:
+        return int(LIB.pndf_hierarchy_bytes(self.handle)) if self.handle else 0
+
+    def free(self):
+        if self.handle:
+            LIB.pndf_free_hierarchy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def pndf_build_hierarchy(texels: torch.Tensor, bounds_fmt: int = PNDF_BOUNDS_F32, stream=None) -> Hierarchy:
+    """texels: (N, N, 2) float32 or float16 CUDA tensor, texel (i, j) at [j, i]."""
+    _need(texels, "texels", shape_last=2)
+    if texels.dim() != 3 or texels.shape[0] != texels.shape[1]:
+        raise ValueError("texels must be (N, N, 2)")
+    if texels.dtype == torch.float32:
+        tf = PNDF_TEXEL_F32X2
+    elif texels.dtype == torch.float16:
+        tf = PNDF_TEXEL_F16X2
+    else:
+        raise ValueError("texels must be float32 or float16")
+    p = _BuildParams(int(texels.shape[0]), tf, int(bounds_fmt), 0)
+    h = ctypes.c_void_p()
+    with torch.cuda.device(texels.device):
+        _check("pndf_build_hierarchy", LIB.pndf_build_hierarchy(_ptr(texels), ctypes.byref(p), _stream(stream),
+                                                                ctypes.byref(h)))
+    return Hierarchy(h.value, int(texels.shape[0]), tf, int(bounds_fmt), texels.device)
+
+
+def pndf_free_hierarchy(h: Hierarchy):
+    h.free()
+
+
+def _queries(q: torch.Tensor):
+    _need(q, "queries", dtype=torch.float32, shape_last=8)
+    return q.shape[0]
+
+
+def pndf_eval_batch(h: Hierarchy, queries: torch.Tensor, out: torch.Tensor | None = None,
+                    flags: torch.Tensor | None = None, stats: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """queries: (nq, 8) float32 CUDA tensor (x, y, sxx, sxy, syy, ms, mt, pad).
+    Returns D (nq,) float32.  flags: optional (nq,) int32; stats: optional (nq, 8) int32."""
+    return pndf_eval_batch_ex(h, queries, out=out, flags=flags, stats=stats, stream=stream)
+
+
+def pndf_eval_batch_ex(h: Hierarchy, queries: torch.Tensor, out=None, flags=None, stats=None, mode: int = 0,
+                       sort: bool = True, warps_per_cta: int = 0, ctas_per_sm: int = 0, stream=None) -> torch.Tensor:
+    nq = _queries(queries)
+    if out is None:
+        out = torch.empty(nq, dtype=torch.float32, device=queries.device)
+    _need(out, "out", dtype=torch.float32)
+    if flags is not None:
+        _need(flags, "flags", dtype=torch.int32)
+    if stats is not None:
+        _need(stats, "stats", dtype=torch.int32, shape_last=8)
+    cfg = _EvalConfig(int(mode), 1 if sort else 0, int(warps_per_cta), int(ctas_per_sm))
+    with torch.cuda.device(queries.device):
+        _check("pndf_eval_batch_ex", LIB.pndf_eval_batch_ex(h.handle, _ptr(queries), nq, _ptr(out), _ptr(flags),
+                                                            _ptr(stats), ctypes.byref(cfg), _stream(stream)))
+    return out
+
+
+def pndf_eval_batch_host(h: Hierarchy, queries_host: torch.Tensor, out_host: torch.Tensor | None = None,
+                         stream=None) -> torch.Tensor:
+    """Host-buffer variant: queries_host (nq, 8) float32 CPU (pinned for full speed)."""
+    _need(queries_host, "queries_host", dtype=torch.float32, device=False, shape_last=8)
+    nq = queries_host.shape[0]
+    if out_host is None:
+        out_host = torch.empty(nq, dtype=torch.float32, pin_memory=queries_host.is_pinned())
+    _need(out_host, "out_host", dtype=torch.float32, device=False)
+    with torch.cuda.device(h.device):
+        _check("pndf_eval_batch_host", LIB.pndf_eval_batch_host(h.handle, _ptr(queries_host), nq, _ptr(out_host),
+                                                                _stream(stream)))
+    return out_host
+
+
+def pndf_diffuse_projected_area(h: Hierarchy, queries: torch.Tensor, omega: torch.Tensor,
+                                out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """omega: (nq, 3) float32 CUDA unit directions with w_z > 0.  Returns P (nq,)."""
+    nq = _queries(queries)
+    _need(omega, "omega", dtype=torch.float32, shape_last=3)
+    if omega.shape[0] != nq:
+        raise ValueError("omega must have one row per query")
+    if out is None:
+        out = torch.empty(nq, dtype=torch.float32, device=queries.device)
+    _need(out, "out", dtype=torch.float32)
+    with torch.cuda.device(queries.device):
+        _check("pndf_diffuse_projected_area", LIB.pndf_diffuse_projected_area(h.handle, _ptr(queries), _ptr(omega), nq,
+                                                                              _ptr(out), _stream(stream)))
+    return out
+
+
+def pndf_device_status(stream=None) -> int:
+    """Read and clear the device status word; returns the PNDF_QF_* bits (0 if clean)."""
+    bits = ctypes.c_uint32(0)
+    code = LIB.pndf_device_status(_stream(stream), ctypes.byref(bits))
+    if code not in (PNDF_OK, 7):
+        raise PndfError("pndf_device_status", code)
+    return int(bits.value)
+
+
+def pndf_status_string(code: int) -> str:
+    return LIB.pndf_status_string(int(code)).decode()
+
+
+def pndf_version() -> int:
+    return int(LIB.pndf_version())

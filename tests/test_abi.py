@@ -1,0 +1,84 @@
+"""The C-ABI library builds, loads, and exports every symbol pndf.h declares.
+
+No compute call is made here (no GPU needed): only argument validation paths
+that return before touching the device.
+"""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2505_08985_gb300 import _build
+    path = _build.build()
+    return ctypes.CDLL(path)
+
+
+def declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(pndf_[a-z0-9_]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("pndf_build_hierarchy", "pndf_eval_batch", "pndf_diffuse_projected_area",
+                     "pndf_free_hierarchy", "pndf_status_string"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+
+
+def test_status_strings(lib):
+    lib.pndf_status_string.restype = ctypes.c_char_p
+    lib.pndf_status_string.argtypes = [ctypes.c_int]
+    assert lib.pndf_status_string(0) == b"ok"
+    assert lib.pndf_status_string(1) == b"invalid argument"
+    assert lib.pndf_status_string(99) == b"unknown status"
+    assert lib.pndf_version() >= 100
+
+
+def test_argument_errors_without_device(lib):
+    vp = ctypes.c_void_p
+    lib.pndf_build_hierarchy.argtypes = [vp, vp, vp, ctypes.POINTER(vp)]
+    out = vp(1234)
+    assert lib.pndf_build_hierarchy(None, None, None, ctypes.byref(out)) == 1
+    assert out.value is None  # cleared on error
+    assert lib.pndf_build_hierarchy(None, None, None, None) == 1
+    lib.pndf_eval_batch.argtypes = [vp, vp, ctypes.c_int64, vp, vp, vp, vp]
+    assert lib.pndf_eval_batch(None, None, 0, None, None, None, None) == 1
+    lib.pndf_diffuse_projected_area.argtypes = [vp, vp, vp, ctypes.c_int64, vp, vp]
+    assert lib.pndf_diffuse_projected_area(None, None, None, 0, None, None) == 1
+    lib.pndf_free_hierarchy.argtypes = [vp]
+    lib.pndf_free_hierarchy(None)  # no-op
+    lib.pndf_hierarchy_bytes.restype = ctypes.c_size_t
+    lib.pndf_hierarchy_bytes.argtypes = [vp]
+    assert lib.pndf_hierarchy_bytes(None) == 0
+
+
+def test_build_params_invalid_n(lib):
+    class P(ctypes.Structure):
+        _fields_ = [("n", ctypes.c_int32), ("texel_fmt", ctypes.c_int32), ("bounds_fmt", ctypes.c_int32),
+                    ("leaf_level", ctypes.c_int32)]
+
+    vp = ctypes.c_void_p
+    lib.pndf_build_hierarchy.argtypes = [vp, ctypes.POINTER(P), vp, ctypes.POINTER(vp)]
+    out = vp()
+    dummy = ctypes.c_void_p(256)  # never dereferenced: validation fails first
+    for bad in (P(1, 0, 0, 0), P(16385, 0, 0, 0), P(64, 7, 0, 0), P(64, 0, 9, 0)):
+        assert lib.pndf_build_hierarchy(dummy, ctypes.byref(bad), None, ctypes.byref(out)) == 1
+    assert lib.pndf_build_hierarchy(dummy, ctypes.byref(P(64, 0, 0, 3)), None, ctypes.byref(out)) == 6

@@ -1,0 +1,249 @@
+"""GPU parity of the P-NDF path (pndf_build_hierarchy + pndf_eval_batch)
+against the FP64 oracle, through the C ABI.
+
+Bar: per-query relative error <= 1e-4 on every query the oracle does not flag
+(normal-space edge ties within 1e-6, hits within 1e-4 of the q = 16 cut,
+zero-area ties, invalid covariance), exact zeros where the oracle has no
+hit, and identical hit counts and hit-set fingerprints.
+"""
+
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2505_08985_gb300 import synth
+from parity import RTOL, check_pndf, rel_err
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_08985_gb300 import pndf
+    return pndf
+
+
+def run(P, st, q, bounds=0, mode=0, sort=True, warps=0, stats=True):
+    h = P.pndf_build_hierarchy(st.to(DEV), bounds_fmt=bounds)
+    qd = q.to(DEV)
+    flags = torch.zeros(q.shape[0], dtype=torch.int32, device=DEV)
+    stt = torch.zeros(q.shape[0], 8, dtype=torch.int32, device=DEV) if stats else None
+    D = P.pndf_eval_batch_ex(h, qd, flags=flags, stats=stt, mode=mode, sort=sort, warps_per_cta=warps)
+    torch.cuda.synchronize()
+    out = (D.cpu().double().numpy(), flags.cpu().numpy().astype(np.uint32),
+           None if stt is None else stt.cpu().numpy().astype(np.int64))
+    h.free()
+    return out
+
+
+def test_bumps256_4096_queries(P):
+    """The small plain-method workload: 256^2 bumps map, 4096 isotropic sigma=4 queries."""
+    cfg = synth.BUMPS_256
+    st = synth.bumps_map(n=cfg["n"], seed=cfg["seed"])
+    q = synth.make_queries(st, cfg["queries"], cfg["mix"], cfg["seed"])
+    ref = oracle.pndf(st, q)
+    D, fl, stt = run(P, st, q)
+    s = check_pndf(D, ref, hits_gpu=stt[:, 3], hash_gpu=stt[:, 4], label="bumps256")
+    assert s["nonzero"] > 0.8 * s["compared"]
+    assert s["excluded"] < 0.05 * q.shape[0]
+    assert P.pndf_device_status() == 0
+
+
+def test_hierarchy_prunes_only(P):
+    """Pyramid traversal and flat evaluation test exactly the same contributing
+    triangles (every query, ties included: both use the same leaf predicate)."""
+    st = synth.bumps_map(n=200, n_bumps=40, seed=7)
+    q = synth.make_queries(st, 3000, synth.QueryMix(sigma=(0.7, 12.0), aspect=(1.0, 4.0), frac_near=0.8), 7)
+    Dh, _, sh = run(P, st, q, mode=0)
+    Df, _, sf = run(P, st, q, mode=1)
+    assert np.array_equal(sh[:, 3], sf[:, 3]) and np.array_equal(sh[:, 4], sf[:, 4])
+    assert rel_err(Dh, Df).max() <= 1e-6
+    # and pruning is real: far fewer triangle tests than the flat scan
+    assert sh[:, 2].sum() < 0.5 * sf[:, 2].sum()
+
+
+def test_fp16_outward_bounds_keep_hit_sets(P):
+    """FP16 bounds rounded outward only prune less: hit sets are identical to
+    FP32 bounds and D agrees to summation-order rounding."""
+    st = synth.scratch_map(n=512, n_grooves=120, seed=3)
+    q = synth.make_queries(st, 4000, synth.QueryMix(sigma=(1.0, 32.0), aspect=(1.0, 4.0), frac_near=0.7), 3)
+    D32, _, s32 = run(P, st, q, bounds=0)
+    D16, _, s16 = run(P, st, q, bounds=1)
+    assert np.array_equal(s32[:, 3], s16[:, 3]) and np.array_equal(s32[:, 4], s16[:, 4])
+    assert rel_err(D16, D32).max() <= 1e-6
+    assert s16[:, 0].sum() >= s32[:, 0].sum()  # looser boxes visit at least as many nodes
+    ref = oracle.pndf(st, q)
+    check_pndf(D16, ref, hits_gpu=s16[:, 3], hash_gpu=s16[:, 4], label="scratch512 fp16 bounds")
+
+
+def test_fp16_texels(P):
+    """A binary16-stored map: the map is its FP16 values (decoded exactly by the oracle)."""
+    st = synth.flake_normals(256, 300, seed=4).half()
+    q = synth.make_queries(st.float(), 2000, synth.QueryMix(sigma=(1.0, 20.0), frac_near=0.7), 4)
+    ref = oracle.pndf(st.float(), q)
+    for bounds in (0, 1):
+        D, _, stt = run(P, st, q, bounds=bounds)
+        check_pndf(D, ref, hits_gpu=stt[:, 3], hash_gpu=stt[:, 4], label=f"fp16 texels bounds={bounds}")
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 6, 37, 100, 129, 257])
+def test_ragged_map_sizes(P, n):
+    """Maps whose quad count is not a power of two (padded pyramid, partial
+    tiles, odd rows that disable vector loads), footprints crossing or outside
+    the border."""
+    st = synth.bumps_map(n=n, n_bumps=max(1, n // 8), seed=n)
+    mix = synth.QueryMix(sigma=(0.5, max(1.0, n / 4)), aspect=(1.0, 3.0), frac_near=0.8,
+                         centre_margin=-0.2 * n - 2)
+    q = synth.make_queries(st, 600, mix, n)
+    ref = oracle.pndf(st, q)
+    D, _, stt = run(P, st, q)
+    check_pndf(D, ref, hits_gpu=stt[:, 3], hash_gpu=stt[:, 4], label=f"n={n}")
+
+
+def test_affine_field_closed_form(P):
+    """Affine normal field: D = k_r(M^-1 (m - n0) - x) / |det M| (Eq. 2),
+    independent of the oracle."""
+    n0 = (-0.2001953125, -0.150390625)
+    M = np.array(((44 / 4096, 8 / 4096), (-12 / 4096, 40 / 4096)))
+    N = 32
+    st = synth.affine_normals(N, n0, M)
+    rng = np.random.default_rng(11)
+    nq = 2000
+    us = rng.uniform(0.01, N - 1.01, (nq, 2))
+    m = (np.asarray(n0)[None] + us @ M.T).astype(np.float32).astype(np.float64)
+    x = rng.uniform(4, 27, nq)
+    y = rng.uniform(4, 27, nq)
+    s = rng.uniform(0.8, 3.0, nq)
+    q = np.stack([x, y, s * s, np.zeros(nq), s * s, m[:, 0], m[:, 1], np.zeros(nq)], 1).astype(np.float32)
+    qt = torch.from_numpy(q)
+    D, _, stt = run(P, st, qt)
+    q64 = q.astype(np.float64)
+    ustar = np.linalg.solve(M[None], (q64[:, 5:7] - np.asarray(n0)[None])[:, :, None])[:, :, 0]
+    d = ustar - q64[:, :2]
+    qq = (d ** 2).sum(1) / q64[:, 2]
+    expect = np.where(qq <= 16, np.exp(-0.5 * qq) / (2 * np.pi * q64[:, 2]) / abs(np.linalg.det(M)), 0.0)
+    ref = oracle.pndf(st, qt)
+    ok = (ref[1] & oracle.F_EXCLUDE) == 0
+    assert ok.mean() > 0.95
+    r = rel_err(D[ok], expect[ok])
+    assert r.max() <= RTOL, r.max()
+
+
+def test_large_footprints_deep_traversal(P):
+    """Footprints up to sigma = 150 on a 1024^2 flake map (deep descent, many entry nodes)."""
+    st = synth.flake_normals(1024, 3000, seed=9)
+    q = synth.make_queries(st, 300, synth.QueryMix(sigma=(20.0, 150.0), frac_near=0.8), 9)
+    ref = oracle.pndf(st, q)
+    D, _, stt = run(P, st, q)
+    s = check_pndf(D, ref, hits_gpu=stt[:, 3], hash_gpu=stt[:, 4], label="flake1024 large")
+    assert s["nonzero"] > 100
+
+
+def test_empty_and_single(P):
+    st = synth.bumps_map(n=64, n_bumps=4, seed=2)
+    h = P.pndf_build_hierarchy(st.to(DEV))
+    D = P.pndf_eval_batch(h, torch.zeros(0, 8, dtype=torch.float32, device=DEV))
+    assert D.shape == (0,)
+    q = synth.make_queries(st, 1, synth.QueryMix(sigma=(3.0, 3.0)), 2)
+    D1 = P.pndf_eval_batch(h, q.to(DEV)).cpu().double().numpy()
+    check_pndf(D1, oracle.pndf(st, q), label="single")
+    h.free()
+
+
+def test_invalid_queries_flagged(P):
+    st = synth.bumps_map(n=64, n_bumps=4, seed=2)
+    q = synth.make_queries(st, 8, synth.QueryMix(sigma=(3.0, 3.0)), 2)
+    q[1, 2] = -1.0                      # sxx < 0
+    q[2, 3] = 100.0                     # not positive definite
+    q[3, 0] = float("nan")
+    h = P.pndf_build_hierarchy(st.to(DEV))
+    flags = torch.zeros(8, dtype=torch.int32, device=DEV)
+    D = P.pndf_eval_batch(h, q.to(DEV), flags=flags).cpu().numpy()
+    fl = flags.cpu().numpy()
+    assert np.all(np.isnan(D[1:4])) and np.all(fl[1:4] & P.PNDF_QF_INVALID)
+    assert not np.isnan(D[0]) and not np.isnan(D[4:]).any()
+    assert P.pndf_device_status() & P.PNDF_QF_INVALID
+    assert P.pndf_device_status() == 0  # cleared by the read
+    h.free()
+
+
+def test_result_independent_of_batch(P):
+    """A query's D is bit-identical alone, in a batch, sorted or unsorted and
+    with another launch shape: one warp owns a query and its reduction order."""
+    st = synth.scratch_map(n=256, n_grooves=40, seed=12)
+    q = synth.make_queries(st, 2048, synth.QueryMix(sigma=(1.0, 24.0), aspect=(1.0, 4.0), frac_near=0.8), 12)
+    D_all, _, _ = run(P, st, q, stats=False)
+    D_uns, _, _ = run(P, st, q, sort=False, stats=False)
+    D_w4, _, _ = run(P, st, q, warps=4, stats=False)
+    D_sub, _, _ = run(P, st, q[100:117], stats=False)
+    assert np.array_equal(D_all, D_uns) and np.array_equal(D_all, D_w4)
+    assert np.array_equal(D_all[100:117], D_sub)
+
+
+def test_host_buffer_entry_point(P):
+    st = synth.bumps_map(n=128, n_bumps=16, seed=5)
+    q = synth.make_queries(st, 3000, synth.QueryMix(sigma=(1.0, 8.0)), 5)
+    h = P.pndf_build_hierarchy(st.to(DEV))
+    Dh = P.pndf_eval_batch_host(h, q.pin_memory())
+    Dd = P.pndf_eval_batch(h, q.to(DEV)).cpu()
+    assert torch.equal(Dh, Dd)
+    h.free()
+
+
+def _sampled(nq_total, k, rng):
+    return np.sort(rng.choice(nq_total, size=k, replace=False))
+
+
+def test_scratch2048_1m_sampled(P):
+    """The 2048^2 scratch workload at full size (1M anisotropic queries) in the
+    default launch configuration; a sample is checked against the oracle."""
+    cfg = synth.SCRATCH_2048
+    st = synth.scratch_map(n=cfg["n"], seed=cfg["seed"], device=DEV)
+    q = synth.make_queries(st, cfg["queries"], cfg["mix"], cfg["seed"])
+    for bounds in (0, 1):
+        h = P.pndf_build_hierarchy(st, bounds_fmt=bounds)
+        stt = torch.zeros(q.shape[0], 8, dtype=torch.int32, device=DEV)
+        D = P.pndf_eval_batch(h, q, stats=stt).cpu().double().numpy()
+        stt = stt.cpu().numpy().astype(np.int64)
+        h.free()
+        idx = _sampled(q.shape[0], 3000, np.random.default_rng(bounds))
+        ref = oracle.pndf(st.cpu(), q.cpu()[idx])
+        s = check_pndf(D[idx], ref, hits_gpu=stt[idx, 3], hash_gpu=stt[idx, 4], label=f"scratch2048 b={bounds}")
+        assert s["nonzero"] > 500
+        assert np.isfinite(D).all()
+
+
+def test_flake8192_4m_sampled(P):
+    """The 8192^2 flake workload at full size (4M queries, sigma 1..512), FP32
+    and FP16-outward bounds; a sigma-stratified sample checked against the oracle."""
+    cfg = synth.FLAKE_8192
+    st = synth.flake_map(n=cfg["n"], seed=cfg["seed"], device=DEV)
+    q = synth.make_queries(st, cfg["queries"], cfg["mix"], cfg["seed"])
+    sig = torch.sqrt(q[:, 2]).cpu().numpy()
+    rng = np.random.default_rng(5)
+    # stratify: 8 log-sigma bins, 40 queries each (large ones are expensive for the oracle)
+    edges = np.exp(np.linspace(0, math.log(512), 9))
+    idx = []
+    for a, b in zip(edges[:-1], edges[1:]):
+        cand = np.flatnonzero((sig >= a) & (sig < b))
+        idx.append(rng.choice(cand, size=min(40, cand.size), replace=False))
+    idx = np.sort(np.concatenate(idx))
+    ref = oracle.pndf(st.cpu(), q.cpu()[idx])
+    Ds = {}
+    for bounds in (0, 1):
+        h = P.pndf_build_hierarchy(st, bounds_fmt=bounds)
+        stt = torch.zeros(q.shape[0], 8, dtype=torch.int32, device=DEV)
+        D = P.pndf_eval_batch(h, q, stats=stt).cpu().double().numpy()
+        stt = stt.cpu().numpy().astype(np.int64)
+        h.free()
+        check_pndf(D[idx], ref, hits_gpu=stt[idx, 3], hash_gpu=stt[idx, 4], label=f"flake8192 b={bounds}")
+        Ds[bounds] = (D, stt)
+    assert np.array_equal(Ds[0][1][:, 4], Ds[1][1][:, 4])
+    assert rel_err(Ds[1][0], Ds[0][0]).max() <= 1e-6

@@ -6,7 +6,8 @@ diagonal (Eq. 3), a signed or halved Jacobian (Eq. 4), the barycentric roles
 swapped when mapping back to uv (Eq. 5), the footprint covariance or
 normalisation wrong, the printed "+" of Eq. 11's line term, the "d_x"
 projection cosine of App. B, a reversed arc, a wrong clip root (Alg. 1) and a
-misplaced per-triangle kernel sample.
+misplaced per-triangle kernel sample, and a collapsed normal triangle
+treated as a point at its centroid.
 """
 
 import os
@@ -21,7 +22,7 @@ SRC = os.path.join(os.path.dirname(oracle.__file__), "pndf_oracle.c")
 PNDF_PINS = [pins.test_affine_closed_form, pins.test_mass_invariant, pins.test_binning_converges,
              pins.test_transpose_symmetry]
 AREA_PINS = [pins.test_stokes_matches_area_quadrature, pins.test_projarea_normal_incidence_is_shoelace,
-             pins.test_projarea_uv_form]
+             pins.test_projarea_uv_form, pins.test_projarea_uv_form_collapsed_triangles]
 
 MUTANTS = {
     "other_diagonal": (
@@ -48,6 +49,9 @@ MUTANTS = {
     "clip_start_uses_t1": ([("oa[0] = a[0] * (1.0 - t0) + b[0] * t0;\n            oa[1] = a[1] * (1.0 - t0) + b[1] * t0;",
                              "oa[0] = a[0] * (1.0 - t1) + b[0] * t1;\n            oa[1] = a[1] * (1.0 - t1) + b[1] * t1;")],
                            AREA_PINS),
+    "collapsed_as_centroid_point": ([("P += k * collapsed_uv_form(a, b, cc, w, c, s, gl_x, gl_w, ngl);",
+                                      "P += k * 0.5 * visible_cos_ratio((a[0] + b[0] + cc[0]) / 3.0, "
+                                      "(a[1] + b[1] + cc[1]) / 3.0, w);")], AREA_PINS),
     "kernel_at_wrong_centroid": ([("double gx = i + (tri == 0 ? 1.0 / 3.0 : 2.0 / 3.0) - x;",
                                    "double gx = i + (tri == 0 ? 2.0 / 3.0 : 1.0 / 3.0) - x;")], AREA_PINS),
 }

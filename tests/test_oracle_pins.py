@@ -352,3 +352,50 @@ def test_projarea_uv_form(oracle_mod):
                     val = np.maximum(n[:, 0] * w[k, 0] + n[:, 1] * w[k, 1] + nz * w[k, 2], 0) / nz
                     tot += g * val.sum() / (K * K)
         assert abs(P[k] - tot) <= 2e-3 * tot, (k, P[k], tot)
+
+
+def test_projarea_uv_form_collapsed_triangles(oracle_mod):
+    """Steep bumps clamp |s|, |t| to 0.4, so many normal triangles collapse onto
+    segments (exactly zero area); Eq. 13's uv-space integral still fixes their
+    contribution, and the oracle must match dense uv quadrature there too."""
+    h = synth.bumps_height(20, 3, seed=4, amp=(4.0, 5.0), sig=(2.5, 3.0), noise=0.0)
+    st = synth.normals_from_height(h).double().numpy()
+    N = st.shape[0]
+    n0, n1, n2 = st[:-1, :-1], st[:-1, 1:], st[1:, :-1]
+    cr = (n1[..., 0] - n0[..., 0]) * (n2[..., 1] - n0[..., 1]) - (n1[..., 1] - n0[..., 1]) * (n2[..., 0] - n0[..., 0])
+    collinear = (np.abs(cr) < 1e-12) & (np.abs(n1 - n0).sum(-1) + np.abs(n2 - n0).sum(-1) > 0.05)
+    assert collinear.sum() >= 10, int(collinear.sum())
+    q = np.array([[9.5, 9.7, 6.0, 0.5, 5.0, 0, 0], [10.2, 9.1, 3.0, -0.3, 4.0, 0, 0]])
+    w = np.array([[0.3, -0.5, math.sqrt(1 - 0.34)], [-0.9, 0.2, math.sqrt(1 - 0.85)]])
+    _check_uv_form(oracle_mod, st, q, w, 1e-3)
+    # long collapsed segments: s = 0.4 everywhere, t alternating +-0.4, so every
+    # normal triangle is a segment of length 0.8
+    N = 8
+    jj, ii = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+    st2 = np.stack([np.full((N, N), 0.4), np.where((ii + jj) % 2 == 0, 0.4, -0.4)], -1)
+    q2 = np.array([[3.5, 3.5, 1.5, 0.2, 1.2, 0, 0], [3.2, 3.9, 2.5, -0.4, 2.0, 0, 0]])
+    w2 = np.array([[0.0, 0.95, math.sqrt(1 - 0.9025)], [-0.6, -0.6, math.sqrt(1 - 0.72)]])
+    _check_uv_form(oracle_mod, st2, q2, w2, 1e-3)
+
+
+def _check_uv_form(oracle_mod, st, q, w, rtol):
+    N = st.shape[0]
+    P = oracle_mod.projarea(st, q, w)
+    K = 60
+    f = (np.arange(K) + 0.5) / K
+    U, V = np.meshgrid(f, f, indexing="ij")
+    U, V = U.ravel(), V.ravel()
+    lower = U + V < 1
+    for k in range(len(q)):
+        tot = 0.0
+        for j in range(N - 1):
+            for i in range(N - 1):
+                for sel, off in ((lower, 1 / 3), (~lower, 2 / 3)):
+                    g, _ = gauss(i + off - q[k, 0], j + off - q[k, 1], q[k, 2], q[k, 3], q[k, 4])
+                    if g == 0:
+                        continue
+                    n = interp_normal(st, i + U[sel], j + V[sel])
+                    nz = np.sqrt(1 - (n ** 2).sum(1))
+                    val = np.maximum(n[:, 0] * w[k, 0] + n[:, 1] * w[k, 1] + nz * w[k, 2], 0) / nz
+                    tot += g * val.sum() / (K * K)
+        assert abs(P[k] - tot) <= rtol * tot, (k, P[k], tot)
