@@ -1,0 +1,412 @@
+#!/usr/bin/env python
+"""P-NDF throughput benchmark on the 8192^2 metallic-flake workload.
+
+Workload: an 8192 x 8192 Voronoi flake normal map (about 200k cells, constant
+cell normals ~ N(0, 0.15^2 I) plus N(0, 0.005^2) per texel, FP32 (s, t)) and
+4,194,304 isotropic Gaussian-footprint queries (sigma log-uniform in 1..512
+texels, centres uniform, 70% of normals drawn near the footprint's normals
+and 30% uniform in [-0.4, 0.4]^2), all seeded and synthetic.
+
+One step = the whole hot path over the batch: rebuild the min/max bound
+pyramid from the texels, key and sort the queries, traverse and leaf-test,
+reduce and write D in caller order.  `value` uses FP16 outward-rounded
+bounds (leaf maths in FP32); the plain FP32-bounds path is timed beside it.
+Texels (512 MiB) and queries (128 MiB) exceed the 129 MB L2 and are re-read
+every step, so no explicit flush is needed.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank runs an independent replica on its own queries
+(weak scaling); rank 0 prints one JSON line.
+"""
+
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2505_08985_gb300 import synth  # noqa: E402
+
+METRIC = "P-NDF queries/sec @8192^2 map (FP16-bound served vs plain FP32), p50/p99 latency"
+UNIT = "queries/s"
+WORKLOAD = "flake8192_fp32map_4M_iso_sigma1-512"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--queries", type=int, default=synth.FLAKE_8192["queries"])
+    ap.add_argument("--n", type=int, default=synth.FLAKE_8192["n"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target oracle work for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only: no data-path collective)
+# ---------------------------------------------------------------------------
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() and args.impl == "gpu" else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, v: float) -> float:
+    if world == 1:
+        return v
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(world, v: float) -> float:
+    if world == 1:
+        return v
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        try:
+            self.f = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.f is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.f.seek(0)
+        rows = [r for r in csv.reader(io.StringIO(self.f.read())) if len(r) >= 9]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# measured peaks and committed ncu traffic
+# ---------------------------------------------------------------------------
+
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            v = float(json.load(f)["hbm_gbs"])
+        return v, "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("eval.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2505_08985_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(bounds_tag: str):
+    """DRAM bytes per launch of the traversal kernel from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", f"traverse_{WORKLOAD}.txt")
+    if not os.path.exists(p):
+        return None
+    src, val = None, None
+    with open(p) as f:
+        for line in f:
+            if line.startswith("kernel_source_sha256_16:"):
+                src = line.split(":", 1)[1].strip()
+            if line.startswith(f"dram_bytes_per_launch_{bounds_tag}:"):
+                val = float(line.split(":", 1)[1].split()[0])
+    return val if src == kernel_source_hash() else None
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+
+def make_workload(args, device, rank):
+    cfg = synth.FLAKE_8192
+    st = synth.flake_map(n=args.n, seed=cfg["seed"], device=device)
+    q = synth.make_queries(st, args.queries, cfg["mix"], cfg["seed"] + 1000 * rank)
+    return st, q
+
+
+def oracle_rate(st_cpu, q_cpu, seconds, seed):
+    """Oracle queries/s on a random sample sized for about `seconds` of wall time."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    n_done, t_total, k = 0, 0.0, 64
+    while t_total < seconds:
+        idx = np.sort(rng.choice(q_cpu.shape[0], size=min(k, q_cpu.shape[0]), replace=False))
+        t0 = time.perf_counter()
+        oracle.pndf(st_cpu, q_cpu[idx])
+        dt = time.perf_counter() - t0
+        n_done += idx.size
+        t_total += dt
+        remaining = seconds - t_total
+        if remaining <= 0.1 * seconds:
+            break
+        k = int(min(max(2 * k, (idx.size / dt) * remaining), 1 << 16))
+    return n_done / t_total, n_done, t_total
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    st, q = make_workload(args, dev, 0)
+    st_cpu, q_cpu = st.cpu(), q.cpu()
+    del st, q
+    cores = oracle.default_threads()
+    per_step = 256
+    rng = np.random.default_rng(12345)
+    times = []
+    for step in range(args.warmup + args.steps):
+        idx = np.sort(rng.choice(q_cpu.shape[0], size=per_step, replace=False))
+        t0 = time.perf_counter()
+        oracle.pndf(st_cpu, q_cpu[idx])
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    v = per_step * len(times) / total
+    sample = f"{per_step} random queries of the {args.queries}-query workload per step"
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "map": f"{args.n}^2 flakes", "queries": args.queries},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args, world, rank, local):
+    from paper_2505_08985_gb300 import pndf
+
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    st, q = make_workload(args, dev, rank)
+    nq = q.shape[0]
+    D = torch.empty(nq, dtype=torch.float32, device=dev)
+
+    # algorithmic work per launch, from one untimed stats pass per bounds format
+    work = {}
+    for tag, bf in (("f16", pndf.PNDF_BOUNDS_F16_OUTWARD), ("f32", pndf.PNDF_BOUNDS_F32)):
+        h = pndf.pndf_build_hierarchy(st, bounds_fmt=bf)
+        stt = torch.zeros(nq, 8, dtype=torch.int32, device=dev)
+        pndf.pndf_eval_batch(h, q, out=D, stats=stt)
+        s = stt.to(torch.int64).sum(0).cpu().tolist()
+        h.free()
+        node_b = 8 if tag == "f16" else 16
+        texel_b = 8
+        # per unit: a node or quad box (node_b), a tested triangle's three
+        # vertices (3 texels), and per query its record, order slot and result
+        work[tag] = {"nodes": s[0], "quads": s[7], "leaf_blocks": s[1], "tri_tests": s[2], "hits": s[3],
+                     "bytes": (s[0] + s[7]) * node_b + s[2] * 3 * texel_b + nq * (32 + 4 + 4)}
+        del stt
+    torch.cuda.synchronize()
+
+    def timed(bf, steps, warmup, clocks=False):
+        h = pndf.pndf_build_hierarchy(st, bounds_fmt=bf)
+        kb = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ke = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        for _ in range(warmup):
+            pndf.pndf_update_hierarchy(h, st)
+            pndf.pndf_eval_batch_ex(h, q, out=D)
+        torch.cuda.synchronize()
+        barrier(world)
+        sampler = ClockSampler(dev.index) if clocks else None
+        if sampler:
+            sampler.__enter__()
+        l0 = pndf.pndf_launch_count()
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t_start.record(stream)
+        for k in range(steps):
+            pndf.pndf_update_hierarchy(h, st)
+            pndf.pndf_eval_batch_ex(h, q, out=D, ev_begin=kb[k], ev_end=ke[k])
+        t_end.record(stream)
+        torch.cuda.synchronize()
+        launches = pndf.pndf_launch_count() - l0
+        barrier(world)
+        if sampler:
+            sampler.__exit__(None, None, None)
+        ms = t_start.elapsed_time(t_end)
+        kms = [a.elapsed_time(b) for a, b in zip(kb, ke)]
+        h.free()
+        return ms, kms, launches, (sampler.summary() if sampler else None)
+
+    ms16, kms16, launches, clocks = timed(pndf.PNDF_BOUNDS_F16_OUTWARD, args.steps, args.warmup, clocks=True)
+    ms32, kms32, _, _ = timed(pndf.PNDF_BOUNDS_F32, args.steps, args.warmup)
+    ms16_max = max_over_ranks(world, ms16)
+    ms32_max = max_over_ranks(world, ms32)
+    total_q = sum_over_ranks(world, float(nq * args.steps))
+    value = total_q / (ms16_max / 1e3)
+    value32 = total_q / (ms32_max / 1e3)
+
+    # end to end through the host-buffer entry point: texels and queries come
+    # from pinned host memory and D goes back to pinned host memory every step
+    st_h = st.cpu().pin_memory()
+    q_h = q.cpu().pin_memory()
+    D_h = torch.empty(nq, dtype=torch.float32).pin_memory()
+    st_d = torch.empty_like(st)
+    h = pndf.pndf_build_hierarchy(st, bounds_fmt=pndf.PNDF_BOUNDS_F16_OUTWARD)
+    for _ in range(max(1, args.warmup)):
+        st_d.copy_(st_h, non_blocking=True)
+        pndf.pndf_update_hierarchy(h, st_d)
+        pndf.pndf_eval_batch_host(h, q_h, D_h)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st_d.copy_(st_h, non_blocking=True)
+        pndf.pndf_update_hierarchy(h, st_d)
+        pndf.pndf_eval_batch_host(h, q_h, D_h)  # synchronises the stream after the copy-back
+    e2e_s = time.perf_counter() - t0
+    h.free()
+    e2e_s = max_over_ranks(world, e2e_s)
+    e2e_value = total_q / e2e_s
+    assert torch.isfinite(D_h).all()
+
+    # roofline of the dominant kernel (traversal + leaf test), per launch
+    kavg16 = sum(kms16) / len(kms16)
+    peak, peak_kind = hbm_peak()
+    achieved = work["f16"]["bytes"] / (kavg16 / 1e3) / 1e9
+    traffic = committed_traffic("f16")
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms16_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "map": f"{args.n}^2 Voronoi flakes, fp32 (s,t)",
+                   "queries_per_gpu": nq, "sigma": "log-uniform 1..512 texels, isotropic",
+                   "bounds": "fp16 outward-rounded", "leaf_math": "fp32 (fp64 below 1e-10 area)",
+                   "l2": "inputs larger than L2 (512 MiB texels + 128 MiB queries re-read each step)",
+                   "step": "rebuild pyramid + key/sort + traverse/leaf + unpermute", "parallelism": f"replicas x{world}"},
+        "fp32_bounds_plain": {"value": value32, "unit": UNIT, "ms_per_step": ms32_max / args.steps,
+                              "traverse_kernel_ms": sum(kms32) / len(kms32)},
+        "traverse_kernel_ms": kavg16,
+        "leaf_triangle_tests_per_s": work["f16"]["tri_tests"] * world / (kavg16 / 1e3),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs",
+                     "algorithmic_bytes_per_launch": work["f16"]["bytes"]},
+        "work_per_launch": work,
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": int(st.numel() * 4 + q.numel() * 4), "d2h_bytes_per_step": int(nq * 4)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        st_cpu, q_cpu = st.cpu(), q.cpu()
+        rate, n_done, secs = oracle_rate(st_cpu, q_cpu, args.cpu_seconds, seed=7)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": oracle.default_threads(), "kind": "oracle",
+                                "sample": f"{n_done} random queries of the same workload, {secs:.1f} s wall"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    try:
+        if args.impl == "reference":
+            run_reference(args, world, rank)
+        else:
+            if not torch.cuda.is_available():
+                raise SystemExit("bench.py: no CUDA device (the GPU arm has no CPU fallback)")
+            run_gpu(args, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -85,7 +85,7 @@ typedef struct pndf_query_stats {
     uint32_t hit_hash;     /* sum mod 2^32 of MurmurHash3-fmix32(triangle id) over hits */
     uint32_t fp64_tris;    /* triangles evaluated in FP64 (normal area < 1e-10)      */
     uint32_t degenerate;   /* zero-area normal triangles met inside their bbox       */
-    uint32_t reserved;
+    uint32_t quads;        /* per-quad (level 0) boxes tested                        */
 } pndf_query_stats;
 
 /* Per-query flag bits written to flags_out_dev. */
@@ -98,11 +98,20 @@ typedef enum pndf_eval_mode {
     PNDF_MODE_FLAT = 1        /* every leaf block in the footprint box, no pruning   */
 } pndf_eval_mode;
 
+typedef enum pndf_sort_mode {
+    PNDF_SORT_NONE = 0,         /* caller order                                       */
+    PNDF_SORT_LEVEL_TILE = 1,   /* entry level (largest first), then centre tile (default) */
+    PNDF_SORT_LEVEL_NORMAL = 2  /* entry level, then query-normal bin                    */
+} pndf_sort_mode;
+#define PNDF_SORT_DEFAULT PNDF_SORT_LEVEL_TILE
+
 typedef struct pndf_eval_config {
     int32_t mode;           /* pndf_eval_mode                                         */
-    int32_t sort;           /* 1 = key queries by (entry level, tile) and sort first */
+    int32_t sort;           /* query order before traversal (pndf_sort_mode)          */
     int32_t warps_per_cta;  /* 0 = library default                                   */
     int32_t ctas_per_sm;    /* 0 = as many as fit                                    */
+    void *ev_begin;         /* optional cudaEvent_t recorded on the stream just before */
+    void *ev_end;           /* and just after the traversal kernel (NULL = none)       */
 } pndf_eval_config;
 
 /*
@@ -110,8 +119,9 @@ typedef struct pndf_eval_config {
  * A node at level l covers 2^l x 2^l quads; it stores the bounding box of the
  * normals of all texels of its quads, so the normal triangles of every quad
  * below it lie inside.  Levels leaf_level..L are stored (2^L >= N-1), each
- * in Morton order so the four children of a node are contiguous; nodes
- * without quads hold an empty box.  The texels are copied into the
+ * in Morton order so the four children of a node are contiguous, plus level
+ * 0 (one box per quad, Morton order, so a leaf block's 16 quads are
+ * contiguous); nodes without quads hold an empty box.  The texels are copied into the
  * hierarchy (the caller may free texels_dev once the stream reaches the end
  * of this call's work).  On success *out owns device memory until
  * pndf_free_hierarchy().
@@ -121,6 +131,12 @@ typedef struct pndf_eval_config {
  */
 pndf_status pndf_build_hierarchy(const void *texels_dev, const pndf_build_params *params,
                                  void *stream, pndf_hierarchy **out);
+
+/* Rebuild h in place from new texels of the same size and format (the map
+ * changed): copies the texels and recomputes every pyramid level on stream,
+ * with no allocation.  Work already queued on h must be on the same stream
+ * or complete.  Errors: INVALID_ARG, CUDA. */
+pndf_status pndf_update_hierarchy(pndf_hierarchy *h, const void *texels_dev, void *stream);
 
 /* Release a hierarchy (synchronises its device memory release with the
  * device; safe on NULL). */
@@ -196,6 +212,10 @@ pndf_status pndf_diffuse_projected_area(const pndf_hierarchy *h, const pndf_quer
  * errors (synchronises stream).  PNDF_OK if none; PNDF_ERR_DEVICE otherwise,
  * with the raw PNDF_QF_* bits in *bits_out when bits_out != NULL. */
 pndf_status pndf_device_status(void *stream, uint32_t *bits_out);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * devices, all threads); lets a caller count the kernels of a region. */
+int64_t pndf_launch_count(void);
 
 /* Static, human-readable name of a status code. */
 const char *pndf_status_string(pndf_status s);

@@ -7,10 +7,14 @@
 // so the four children of node k at level l are nodes 4k..4k+3 at level l-1
 // (one 64-byte line in FP32, one 32-byte sector in FP16).
 //
+// Level 0 holds one box per quad (its four texels); the leaf level 2 box is
+// the union of its 16 quad boxes.
+//
 // Kernel 1 (build_tiles): one CTA per 64 x 64-quad tile.  The tile's 65 x 65
 // texels are staged in shared memory with 16-byte vector loads (float4 = two
-// FP32 texels, uint4 = four FP16 texels), each thread reduces one leaf-level
-// node (5 x 5 texels), and levels up to 6 are reduced in shared memory.  A
+// FP32 texels, uint4 = four FP16 texels), each thread builds one leaf node's
+// 16 quad boxes and their union, and levels up to 6 are reduced in shared
+// memory.  A
 // tile is a Morton-aligned square at every level, so its nodes form one
 // contiguous run and the writes are fully coalesced.
 // Kernel 2 (build_up): one launch per level above the tile, four contiguous
@@ -124,26 +128,31 @@ __global__ void __launch_bounds__(kBuildThreads) build_tiles(const void *__restr
     }
     __syncthreads();
 
-    // ---- leaf-level nodes: thread i owns the node with local Morton index i ----
+    // ---- quads (level 0) and leaf nodes: thread i owns the leaf node with
+    // local Morton index i and its 16 quads, whose Morton indices at level 0
+    // are 16 i .. 16 i + 15 (a contiguous run of the tile's level-0 block) ----
     const int T = tileQ / kLeafQuads;  // leaf nodes per tile side
     const uint32_t tile_m = morton2(blockIdx.x, blockIdx.y);
     int cur = T * T;
     if (tid < cur) {
         int a = compact1by1(tid), c = compact1by1(tid >> 1);
-        int q0 = c0 + a * kLeafQuads, p0 = r0 + c * kLeafQuads;  // first quad column / row
         Box b = empty_box();
-        if (q0 <= n - 2 && p0 <= n - 2) {
-            int ce = min(a * kLeafQuads + kLeafQuads, n - 1 - c0);
-            int re = min(c * kLeafQuads + kLeafQuads, n - 1 - r0);
-            for (int r = c * kLeafQuads; r <= re; ++r) {
-                for (int cc = a * kLeafQuads; cc <= ce; ++cc) {
-                    float2 v = tex[r * kTileTexMax + cc];
-                    b.smin = fminf(b.smin, v.x);
-                    b.tmin = fminf(b.tmin, v.y);
-                    b.smax = fmaxf(b.smax, v.x);
-                    b.tmax = fmaxf(b.tmax, v.y);
+        const size_t qbase = (size_t(tile_m) * cur + tid) * (kLeafQuads * kLeafQuads);
+        for (int k = 0; k < kLeafQuads * kLeafQuads; ++k) {
+            int lx = a * kLeafQuads + int(compact1by1(k)), ly = c * kLeafQuads + int(compact1by1(k >> 1));
+            Box qb = empty_box();
+            if (c0 + lx <= n - 2 && r0 + ly <= n - 2) {
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    float2 t = tex[(ly + (v >> 1)) * kTileTexMax + lx + (v & 1)];
+                    qb.smin = fminf(qb.smin, t.x);
+                    qb.tmin = fminf(qb.tmin, t.y);
+                    qb.smax = fmaxf(qb.smax, t.x);
+                    qb.tmax = fmaxf(qb.tmax, t.y);
                 }
             }
+            store_box<BFMT>(const_cast<void *>(d.lv[0]), qbase + k, qb);
+            grow(b, qb);
         }
         box[0][tid] = b;
         store_box<BFMT>(const_cast<void *>(d.lv[kLeafLevel]), size_t(tile_m) * cur + tid, b);
@@ -202,6 +211,7 @@ cudaError_t launch_tiles(const void *src, const MapDesc &d, cudaStream_t s)
         build_tiles<TFMT, BFMT, VEC><<<grid, kBuildThreads, 0, s>>>(src, d, tileQ, lq);
     else
         build_tiles<TFMT, BFMT, 1><<<grid, kBuildThreads, 0, s>>>(src, d, tileQ, lq);
+    count_launches(1 + (d.L > lq ? d.L - lq : 0));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     for (int l = lq + 1; l <= d.L; ++l) {

@@ -2,6 +2,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
 #include <new>
 
 #include "common.cuh"
@@ -10,9 +11,29 @@ using namespace pndf;
 
 namespace {
 
+std::atomic<int64_t> g_launches{0};
+
+
 cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
 
 bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// Keep stream-ordered scratch cached in the device's default pool instead of
+// returning it to the driver at every synchronisation (once per device).
+void keep_pool_memory()
+{
+    static std::atomic<uint64_t> done{0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return;
+    uint64_t bit = uint64_t(1) << dev;
+    if (done.fetch_or(bit) & bit) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+}
 
 pndf_status check_hierarchy(const pndf_hierarchy *h)
 {
@@ -20,10 +41,13 @@ pndf_status check_hierarchy(const pndf_hierarchy *h)
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return PNDF_ERR_CUDA;
     if (dev != h->device) return PNDF_ERR_INVALID_ARG;  // must be called with the hierarchy's device current
+    keep_pool_memory();
     return PNDF_OK;
 }
 
 }  // namespace
+
+void pndf::count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 extern "C" {
 
@@ -56,6 +80,8 @@ pndf_status pndf_build_hierarchy(const void *texels_dev, const pndf_build_params
     auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
     size_t off[kMaxLevels + 1];
     size_t total = up(size_t(d.n) * d.n * texel_b);
+    off[0] = total;  // level 0: one box per quad
+    total += up(level_nodes(d.L, 0) * node_b);
     for (int l = kLeafLevel; l <= d.L; ++l) {
         off[l] = total;
         total += up(level_nodes(d.L, l) * node_b);
@@ -68,6 +94,7 @@ pndf_status pndf_build_hierarchy(const void *texels_dev, const pndf_build_params
     h->bytes = total;
     char *base = static_cast<char *>(h->mem);
     d.texels = base;
+    d.lv[0] = base + off[0];
     for (int l = kLeafLevel; l <= d.L; ++l) d.lv[l] = base + off[l];
     cudaError_t e = launch_build(texels_dev, h, as_stream(stream));
     if (e != cudaSuccess) {
@@ -77,6 +104,14 @@ pndf_status pndf_build_hierarchy(const void *texels_dev, const pndf_build_params
     }
     *out = h;
     return PNDF_OK;
+}
+
+pndf_status pndf_update_hierarchy(pndf_hierarchy *h, const void *texels_dev, void *stream)
+{
+    pndf_status st = check_hierarchy(h);
+    if (st != PNDF_OK) return st;
+    if (!texels_dev || !aligned(texels_dev, h->d.texel_fmt == PNDF_TEXEL_F32X2 ? 8 : 4)) return PNDF_ERR_INVALID_ARG;
+    return launch_build(texels_dev, h, as_stream(stream)) == cudaSuccess ? PNDF_OK : PNDF_ERR_CUDA;
 }
 
 void pndf_free_hierarchy(pndf_hierarchy *h)
@@ -103,9 +138,10 @@ pndf_status pndf_eval_batch_ex(const pndf_hierarchy *h, const pndf_query *q_dev,
     if (nq < 0 || nq > int64_t(0x7fffffff)) return PNDF_ERR_INVALID_ARG;
     if (nq > 0 && (!q_dev || !D_out_dev)) return PNDF_ERR_INVALID_ARG;
     if (q_dev && !aligned(q_dev, 16)) return PNDF_ERR_INVALID_ARG;
-    pndf_eval_config c{PNDF_MODE_HIERARCHY, 1, 0, 0};
+    pndf_eval_config c{PNDF_MODE_HIERARCHY, PNDF_SORT_DEFAULT, 0, 0, nullptr, nullptr};
     if (cfg) c = *cfg;
     if (c.mode != PNDF_MODE_HIERARCHY && c.mode != PNDF_MODE_FLAT) return PNDF_ERR_INVALID_ARG;
+    if (c.sort < 0 || c.sort > 2) return PNDF_ERR_INVALID_ARG;
     if (c.warps_per_cta < 0 || c.warps_per_cta > 8 || c.ctas_per_sm < 0) return PNDF_ERR_INVALID_ARG;
     return launch_eval(h, q_dev, nq, D_out_dev, flags_out_dev, stats_dev, c, as_stream(stream));
 }
@@ -135,7 +171,7 @@ pndf_status pndf_eval_batch_host(const pndf_hierarchy *h, const pndf_query *q_ho
     float *Dd = static_cast<float *>(buf);
     pndf_query *qd = reinterpret_cast<pndf_query *>(static_cast<char *>(buf) + qoff);
     cudaError_t e = cudaMemcpyAsync(qd, q_host, qb, cudaMemcpyHostToDevice, s);
-    pndf_eval_config c{PNDF_MODE_HIERARCHY, 1, 0, 0};
+    pndf_eval_config c{PNDF_MODE_HIERARCHY, PNDF_SORT_DEFAULT, 0, 0, nullptr, nullptr};
     if (e == cudaSuccess) st = launch_eval(h, qd, nq, Dd, nullptr, nullptr, c, s);
     if (e == cudaSuccess && st == PNDF_OK) e = cudaMemcpyAsync(D_host, Dd, db, cudaMemcpyDeviceToHost, s);
     cudaError_t ef = cudaFreeAsync(buf, s);
@@ -182,5 +218,7 @@ const char *pndf_status_string(pndf_status s)
 }
 
 int32_t pndf_version(void) { return 100; }
+
+int64_t pndf_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 }  // extern "C"

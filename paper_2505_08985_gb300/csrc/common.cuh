@@ -27,7 +27,8 @@ struct MapDesc {
     int L;                  // top level: 2^L >= n - 1 quads per side
     int texel_fmt;          // pndf_texel_fmt
     int bounds_fmt;         // pndf_bounds_fmt
-    const void *lv[kMaxLevels];  // level l (kLeafLevel..L): (2^(L-l))^2 nodes, Morton order
+    const void *lv[kMaxLevels];  // level 0 (one box per quad) and levels kLeafLevel..L:
+                                 // (2^(L-l))^2 nodes each, Morton order
 };
 
 // Morton (Z-order) interleave of two 16-bit coordinates: x in the even bits.
@@ -85,6 +86,8 @@ pndf_status launch_eval(const pndf_hierarchy *h, const pndf_query *q, int64_t nq
                         pndf_query_stats *stats, const pndf_eval_config &cfg, cudaStream_t s);
 pndf_status launch_projarea(const pndf_hierarchy *h, const pndf_query *q, const float *omega, int64_t nq,
                             float *P, cudaStream_t s);
+// Count of kernels launched by the library (host-side, process-wide).
+void count_launches(int64_t n);
 // Each kernel translation unit keeps its own device status word (PNDF_QF_*
 // bits OR-ed in by kernels on errors); these read it and optionally clear it.
 cudaError_t read_status_eval(cudaStream_t s, uint32_t *bits, bool clear);

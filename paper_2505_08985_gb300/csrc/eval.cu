@@ -17,10 +17,14 @@
 //               lane k tests child (k & 3) of popped node (k >> 2) - uv box
 //               against the 4-sigma ellipse first, then the normal box against
 //               m - and ballot/popc compaction pushes survivors.  Surviving
-//               leaf blocks (4 x 4 quads = 32 triangles) are tested one per
-//               lane; the block's 25 texels are loaded once and shuffled.  The
-//               query's sum is reduced across the warp and written in caller
-//               order (the unpermute is fused into the store).
+//               leaf blocks (4 x 4 quads) have their 16 per-quad boxes (level
+//               0, one 128-byte line in FP16) tested one per lane, two blocks
+//               per pass; quads whose box holds m are compacted into a
+//               per-warp ring and their triangles tested 32 at a time (lane =
+//               triangle).  The query's sum is reduced across the warp and
+//               written in caller order (the unpermute is fused into the
+//               store).  Flat mode skips every box and tests all 32 triangles
+//               of every leaf block in the footprint's bounding box.
 // Hit test (tie rule): m inside the closed normal bounding box and all three
 // edge functions sign-consistent with the triangle orientation (>= 0 after
 // orientation, i.e. closed barycentrics).  Zero-area normal triangles are a
@@ -35,8 +39,11 @@ __device__ unsigned int g_status_eval;
 
 namespace {
 
-constexpr int kStackCap = 512;     // DFS stack entries per warp (bound: 24 per level + 48)
-constexpr int kKeyBins = 16 * 256;  // 16 entry levels x 16 x 16 tiles
+constexpr int kStackCap = 1024;    // DFS stack entries per warp (bound: 48 per level + 80)
+constexpr int kKeyBins = 16 * 1024;  // 16 entry levels x 32 x 32 sub-keys
+#ifndef PNDF_TRAVERSE_MIN_CTAS
+#define PNDF_TRAVERSE_MIN_CTAS 4     // 4 x 256 threads per SM at <= 64 registers, no spills
+#endif
 constexpr unsigned kFull = 0xffffffffu;
 
 // Kahan's difference of products a*b - c*d with one FMA correction.
@@ -146,14 +153,24 @@ __device__ __forceinline__ float2 texel(const MapDesc &d, int i, int j)
 }
 
 // Node (level l, coords a, c): uv box [a 2^l, (a+1) 2^l] x [c 2^l, (c+1) 2^l].
-template <int BFMT>
-__device__ __forceinline__ bool node_test(const MapDesc &d, const Query &q, int l, uint32_t a, uint32_t c)
+// It can hold a contributing hit only if that box meets the 4-sigma ellipse.
+__device__ __forceinline__ bool node_in_footprint(const Query &q, int l, uint32_t a, uint32_t c)
 {
     float sz = float(1u << l);
     float dx0 = float(a) * sz - q.x, dy0 = float(c) * sz - q.y;
-    if (qmin_box(q, dx0, dx0 + sz, dy0, dy0 + sz) > kQPrune) return false;
-    float4 b = node_box<BFMT>(d, l, morton2(a, c));
+    return qmin_box(q, dx0, dx0 + sz, dy0, dy0 + sz) <= kQPrune;
+}
+
+__device__ __forceinline__ bool box_holds(const float4 &b, const Query &q)
+{
     return q.mx >= b.x && q.mx <= b.z && q.my >= b.y && q.my <= b.w;
+}
+
+template <int BFMT>
+__device__ __forceinline__ bool node_test(const MapDesc &d, const Query &q, int l, uint32_t a, uint32_t c)
+{
+    if (!node_in_footprint(q, l, a, c)) return false;
+    return box_holds(node_box<BFMT>(d, l, morton2(a, c)), q);
 }
 
 __device__ __forceinline__ uint32_t pack(int l, uint32_t a, uint32_t c)
@@ -163,7 +180,7 @@ __device__ __forceinline__ uint32_t pack(int l, uint32_t a, uint32_t c)
 
 struct Acc {
     float s, c;  // Neumaier compensated sum
-    uint32_t hits, hash, tests, fp64, degen, leaves, nodes;
+    uint32_t hits, hash, tests, fp64, degen, leaves, nodes, quads;
     uint32_t flags;
 };
 
@@ -239,17 +256,25 @@ __device__ __forceinline__ void test_triangle(const Query &q, float2 na, float2 
     }
 }
 
-// All 32 lanes: the leaf block at level kLeafLevel with block coords (a, c).
-template <int TFMT, bool STATS>
-__device__ __forceinline__ void process_leaf(const MapDesc &d, const Query &q, uint32_t a, uint32_t c, int lane,
-                                             Acc &acc)
+// Lanes 0..24 fetch the 5 x 5 texels of leaf block (a, c) (4 x 4 quads).
+template <int TFMT>
+__device__ __forceinline__ float2 leaf_texel(const MapDesc &d, uint32_t a, uint32_t c, int lane)
+{
+    const int i0 = int(a) << kLeafLevel, j0 = int(c) << kLeafLevel;
+    int tc = lane % kLeafTexels, tr = lane / kLeafTexels;
+    float2 tv = make_float2(0.f, 0.f);
+    if (lane < kLeafTexels * kLeafTexels && i0 + tc < d.n && j0 + tr < d.n) tv = texel<TFMT>(d, i0 + tc, j0 + tr);
+    return tv;
+}
+
+// All 32 lanes: test the 32 triangles of leaf block (a, c) whose texels the
+// lanes hold in tv (lane t: quad t >> 1, triangle t & 1).
+template <bool STATS>
+__device__ __forceinline__ void test_leaf(const MapDesc &d, const Query &q, uint32_t a, uint32_t c, float2 tv,
+                                          int lane, Acc &acc)
 {
     const int n = d.n;
     const int i0 = int(a) << kLeafLevel, j0 = int(c) << kLeafLevel;
-    // lanes 0..24 fetch the block's 5 x 5 texels once
-    int tc = lane % kLeafTexels, tr = lane / kLeafTexels;
-    float2 tv = make_float2(0.f, 0.f);
-    if (lane < kLeafTexels * kLeafTexels && i0 + tc < n && j0 + tr < n) tv = texel<TFMT>(d, i0 + tc, j0 + tr);
     int qd = lane >> 1, qx = qd & 3, qy = qd >> 2, tri = lane & 1;
     int base = qy * kLeafTexels + qx;
     int sa = tri ? base + kLeafTexels + 1 : base;
@@ -267,6 +292,99 @@ __device__ __forceinline__ void process_leaf(const MapDesc &d, const Query &q, u
     if (gi <= n - 2 && gj <= n - 2) {
         uint32_t id = 2u * (uint32_t(gj) * uint32_t(n - 1) + uint32_t(gi)) + uint32_t(tri);
         test_triangle<STATS>(q, na, nb, nc, tri ? gi + 1 : gi, tri ? gj + 1 : gj, tri ? -1.f : 1.f, id, acc);
+    }
+}
+
+// Survivor ring: quads whose level-0 box holds m, packed (i << 16) | j.
+constexpr int kRing = 256;
+
+// All 32 lanes: lane k tests both triangles of survivor quad k (k < cnt) of
+// the ring: (u0, u1, u2) and (u3, u2, u1), its four texels loaded together.
+template <int TFMT, bool STATS>
+__device__ __forceinline__ void test_quads(const MapDesc &d, const Query &q, const uint32_t *ring, uint32_t head,
+                                           int cnt, int lane, Acc &acc)
+{
+    if (lane < cnt) {
+        uint32_t pk = ring[(head + uint32_t(lane)) & (kRing - 1)];
+        int gi = int(pk >> 16), gj = int(pk & 0xffffu);
+        float2 n0 = texel<TFMT>(d, gi, gj), n1 = texel<TFMT>(d, gi + 1, gj);
+        float2 n2 = texel<TFMT>(d, gi, gj + 1), n3 = texel<TFMT>(d, gi + 1, gj + 1);
+        uint32_t id = 2u * (uint32_t(gj) * uint32_t(d.n - 1) + uint32_t(gi));
+        test_triangle<STATS>(q, n0, n1, n2, gi, gj, 1.f, id, acc);
+        test_triangle<STATS>(q, n3, n2, n1, gi + 1, gj + 1, -1.f, id + 1u, acc);
+    }
+}
+
+// Four level-0 boxes (Morton-consecutive quads) in one 32-byte (FP16) or
+// 64-byte (FP32) load; returns bit u set when box u holds m.
+template <int BFMT>
+__device__ __forceinline__ unsigned quad_boxes_hold(const MapDesc &d, uint32_t first, float mx, float my)
+{
+    unsigned bits = 0;
+    if (BFMT == PNDF_BOUNDS_F32) {
+        const float4 *p = reinterpret_cast<const float4 *>(d.lv[0]) + first;
+        float4 b[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) b[u] = __ldg(p + u);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            bits |= unsigned(mx >= b[u].x && mx <= b[u].z && my >= b[u].y && my <= b[u].w) << u;
+    } else {
+        const uint4 *p = reinterpret_cast<const uint4 *>(reinterpret_cast<const uint2 *>(d.lv[0]) + first);
+        uint4 v0 = __ldg(p), v1 = __ldg(p + 1);
+        uint32_t w[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            float2 lo = __half22float2(*reinterpret_cast<__half2 *>(&w[2 * u]));
+            float2 hi = __half22float2(*reinterpret_cast<__half2 *>(&w[2 * u + 1]));
+            bits |= unsigned(mx >= lo.x && mx <= hi.x && my >= lo.y && my <= hi.y) << u;
+        }
+    }
+    return bits;
+}
+
+// All 32 lanes: filter the queued leaf blocks' quads by their level-0 boxes
+// (lane t: quads 4 (t & 3) .. 4 (t & 3) + 3 of block p + (t >> 2), eight
+// blocks per pass), compact the survivors into the ring with ballot/popc and
+// test them 32 quads (64 triangles) at a time.
+template <int BFMT, int TFMT, bool STATS>
+__device__ __forceinline__ void process_leaves(const MapDesc &d, const Query &q, const uint32_t *lq, int nleaf,
+                                               uint32_t *ring, uint32_t &head, int &nsq, int lane, Acc &acc)
+{
+    const unsigned lt = (1u << lane) - 1u;
+    for (int p = 0; p < nleaf; p += 8) {
+        const int blk = p + (lane >> 2);
+        unsigned bits = 0;
+        uint32_t a = 0, c = 0;
+        const uint32_t k0 = uint32_t(lane & 3) << 2;
+        if (blk < nleaf) {
+            uint32_t ent = lq[blk];
+            a = (ent >> 14) & 0x3fffu;
+            c = ent & 0x3fffu;
+            bits = quad_boxes_hold<BFMT>(d, (morton2(a, c) << 4) | k0, q.mx, q.my);
+            if (STATS) {
+                acc.quads += 4;
+                if ((lane & 3) == 0) acc.leaves++;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            bool pass = (bits >> u) & 1u;
+            unsigned m = __ballot_sync(kFull, pass);
+            if (pass) {
+                uint32_t k = k0 | uint32_t(u);
+                uint32_t pk = ((a * kLeafQuads + compact1by1(k)) << 16) | (c * kLeafQuads + compact1by1(k >> 1));
+                ring[(head + uint32_t(nsq) + __popc(m & lt)) & (kRing - 1)] = pk;
+            }
+            nsq += __popc(m);
+        }
+        __syncwarp();
+        while (nsq >= 32) {
+            test_quads<TFMT, STATS>(d, q, ring, head, 32, lane, acc);
+            head += 32;
+            nsq -= 32;
+            __syncwarp();
+        }
     }
 }
 
@@ -296,10 +414,10 @@ __device__ __forceinline__ int entry_level(const Query &q, int L)
 
 template <int BFMT, int TFMT, bool STATS, bool FLAT>
 __device__ void eval_one(const MapDesc &d, const pndf_query &rec, int lane, uint32_t *stk, uint32_t *lq,
-                         float &D_out, uint32_t &flags_out, pndf_query_stats *st_out)
+                         uint32_t *ring, float &D_out, uint32_t &flags_out, pndf_query_stats *st_out)
 {
     Query q = make_query(rec);
-    Acc acc = {0.f, 0.f, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    Acc acc = {0.f, 0.f, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
     if (!q.valid) {
         if (lane == 0) {
             D_out = __int_as_float(0x7fc00000);
@@ -318,7 +436,8 @@ __device__ void eval_one(const MapDesc &d, const pndf_query &rec, int lane, uint
         node_range(q.x, q.rx, sz, S, a0, a1);
         node_range(q.y, q.ry, sz, S, c0, c1);
         for (int c = c0; c <= c1; ++c)
-            for (int a = a0; a <= a1; ++a) process_leaf<TFMT, STATS>(d, q, a, c, lane, acc);
+            for (int a = a0; a <= a1; ++a)
+                test_leaf<STATS>(d, q, a, c, leaf_texel<TFMT>(d, a, c, lane), lane, acc);
     } else {
         const int e = entry_level(q, L);
         const int S = 1 << (L - e);
@@ -348,45 +467,56 @@ __device__ void eval_one(const MapDesc &d, const pndf_query &rec, int lane, uint
             __syncwarp();
         }
         bool overflow = false;
+        uint32_t head = 0;
+        int nsq = 0;
         while (true) {
-            for (int i = 0; i < nleaf; ++i) {
-                uint32_t ent = lq[i];
-                process_leaf<TFMT, STATS>(d, q, (ent >> 14) & 0x3fffu, ent & 0x3fffu, lane, acc);
-            }
+            process_leaves<BFMT, TFMT, STATS>(d, q, lq, nleaf, ring, head, nsq, lane, acc);
             nleaf = 0;
             if (top == 0) break;
-            int npop = min(top, 8);
+            // pop up to 16 nodes; lane k tests child (k & 3) of popped nodes
+            // (k >> 2) and (k >> 2) + 8, so two box loads per lane are in flight
+            int npop = min(top, 16);
             top -= npop;
-            int slot = lane >> 2;
-            uint32_t ent = slot < npop ? stk[top + slot] : 0u;
+            bool pass[2];
+            int cl[2];
+            uint32_t ca[2], cc[2];
+            float4 bx[2];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                int slot = (lane >> 2) + 8 * r;
+                uint32_t ent = slot < npop ? stk[top + slot] : 0u;
+                cl[r] = int(ent >> 28) - 1;
+                ca[r] = 2u * ((ent >> 14) & 0x3fffu) + (lane & 1);
+                cc[r] = 2u * (ent & 0x3fffu) + ((lane >> 1) & 1);
+                pass[r] = slot < npop && node_in_footprint(q, cl[r], ca[r], cc[r]);
+                if (STATS && slot < npop) acc.nodes++;
+            }
+#pragma unroll
+            for (int r = 0; r < 2; ++r)  // both box loads issue before either is used
+                if (pass[r]) bx[r] = node_box<BFMT>(d, cl[r], morton2(ca[r], cc[r]));
+#pragma unroll
+            for (int r = 0; r < 2; ++r) pass[r] = pass[r] && box_holds(bx[r], q);
             __syncwarp();
-            bool pass = false;
-            int cl = 0;
-            uint32_t ca = 0, cc = 0;
-            if (slot < npop) {
-                int l = int(ent >> 28);
-                cl = l - 1;
-                ca = 2u * ((ent >> 14) & 0x3fffu) + (lane & 1);
-                cc = 2u * (ent & 0x3fffu) + ((lane >> 1) & 1);
-                pass = node_test<BFMT>(d, q, cl, ca, cc);
-                if (STATS) acc.nodes++;
-            }
-            bool to_leaf = pass && cl == kLeafLevel, to_stack = pass && cl > kLeafLevel;
-            unsigned ml = __ballot_sync(kFull, to_leaf);
-            unsigned ms = __ballot_sync(kFull, to_stack);
-            if (to_leaf) lq[__popc(ml & lt)] = pack(cl, ca, cc);
-            if (to_stack) {
-                int pos = top + __popc(ms & lt);
-                if (pos < kStackCap) stk[pos] = pack(cl, ca, cc);
-            }
-            nleaf = __popc(ml);
-            top += __popc(ms);
-            if (top > kStackCap) {
-                top = kStackCap;
-                overflow = true;
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                bool to_leaf = pass[r] && cl[r] == kLeafLevel, to_stack = pass[r] && cl[r] > kLeafLevel;
+                unsigned ml = __ballot_sync(kFull, to_leaf);
+                unsigned ms = __ballot_sync(kFull, to_stack);
+                if (to_leaf) lq[nleaf + __popc(ml & lt)] = pack(cl[r], ca[r], cc[r]);
+                if (to_stack) {
+                    int pos = top + __popc(ms & lt);
+                    if (pos < kStackCap) stk[pos] = pack(cl[r], ca[r], cc[r]);
+                }
+                nleaf += __popc(ml);
+                top += __popc(ms);
+                if (top > kStackCap) {
+                    top = kStackCap;
+                    overflow = true;
+                }
             }
             __syncwarp();
         }
+        if (nsq > 0) test_quads<TFMT, STATS>(d, q, ring, head, nsq, lane, acc);  // nsq < 32 here
         if (overflow) acc.flags |= PNDF_QF_OVERFLOW;
     }
     // warp reduction (fixed order: deterministic for a given query)
@@ -409,18 +539,19 @@ __device__ void eval_one(const MapDesc &d, const pndf_query &rec, int lane, uint
         acc.degen = __reduce_add_sync(kFull, acc.degen);
         acc.nodes = __reduce_add_sync(kFull, acc.nodes);
         acc.leaves = __reduce_add_sync(kFull, acc.leaves);
+        acc.quads = __reduce_add_sync(kFull, acc.quads);
     }
     if (lane == 0) {
         D_out = s + c;
         flags_out = fl;
         if (fl & PNDF_QF_OVERFLOW) atomicOr(&g_status_eval, PNDF_QF_OVERFLOW);
         if (STATS)
-            *st_out = pndf_query_stats{acc.nodes, acc.leaves, acc.tests, acc.hits, acc.hash, acc.fp64, acc.degen, 0};
+            *st_out = pndf_query_stats{acc.nodes, acc.leaves, acc.tests, acc.hits, acc.hash, acc.fp64, acc.degen, acc.quads};
     }
 }
 
 template <int BFMT, int TFMT, bool STATS, bool FLAT>
-__global__ void __launch_bounds__(256) traverse_kernel(MapDesc d, const pndf_query *__restrict__ qs,
+__global__ void __launch_bounds__(256, PNDF_TRAVERSE_MIN_CTAS) traverse_kernel(MapDesc d, const pndf_query *__restrict__ qs,
                                                       const uint32_t *__restrict__ order, int64_t nq,
                                                       float *__restrict__ D, uint32_t *__restrict__ flags,
                                                       pndf_query_stats *__restrict__ stats,
@@ -428,8 +559,9 @@ __global__ void __launch_bounds__(256) traverse_kernel(MapDesc d, const pndf_que
 {
     extern __shared__ uint32_t smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint32_t *stk = smem + warp * (kStackCap + 32);
+    uint32_t *stk = smem + warp * (kStackCap + 64 + kRing);
     uint32_t *lq = stk + kStackCap;
+    uint32_t *ring = lq + 64;
     while (true) {
         unsigned long long k = 0;
         if (lane == 0) k = atomicAdd(cursor, 1ull);
@@ -439,7 +571,7 @@ __global__ void __launch_bounds__(256) traverse_kernel(MapDesc d, const pndf_que
         pndf_query rec = qs[qi];
         float Dv;
         uint32_t fv;
-        eval_one<BFMT, TFMT, STATS, FLAT>(d, rec, lane, stk, lq, Dv, fv, stats ? stats + qi : nullptr);
+        eval_one<BFMT, TFMT, STATS, FLAT>(d, rec, lane, stk, lq, ring, Dv, fv, stats ? stats + qi : nullptr);
         if (lane == 0) {
             D[qi] = Dv;
             if (flags) flags[qi] = fv;
@@ -449,19 +581,33 @@ __global__ void __launch_bounds__(256) traverse_kernel(MapDesc d, const pndf_que
 
 // ---- query keying and counting sort ----
 
-__global__ void key_hist(MapDesc d, const pndf_query *__restrict__ qs, int64_t nq, uint16_t *__restrict__ keys,
-                         uint32_t *__restrict__ hist)
+// Sort key: entry level (largest footprints first), then a 32 x 32 Morton
+// sub-key: the footprint centre's tile (sort mode 1) or the query normal's
+// bin over [-0.4, 0.4]^2 (sort mode 2).  Grouping similar normals makes the
+// warps in flight visit the same leaf blocks (those whose normal boxes hold
+// m), so they share L2 lines.
+__global__ void key_hist(MapDesc d, const pndf_query *__restrict__ qs, int64_t nq, int mode,
+                         uint16_t *__restrict__ keys, uint32_t *__restrict__ hist)
 {
-    __shared__ uint32_t h[kKeyBins];
+    extern __shared__ uint32_t h[];
     for (int i = threadIdx.x; i < kKeyBins; i += blockDim.x) h[i] = 0;
     __syncthreads();
-    const float inv_n = 16.0f / float(d.n);
+    const float inv_n = 32.0f / float(d.n);
     for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < nq; k += int64_t(gridDim.x) * blockDim.x) {
         pndf_query r = qs[k];
         Query q = make_query(r);
         int e = q.valid ? entry_level(q, d.L) : 0;
-        int tx = min(15, max(0, int(r.x * inv_n))), ty = min(15, max(0, int(r.y * inv_n)));
-        uint16_t key = uint16_t(((15 - e) << 8) | morton2(tx, ty));
+        float fx, fy;
+        if (mode == 2) {
+            fx = (r.ms + 0.4f) * 40.0f;
+            fy = (r.mt + 0.4f) * 40.0f;
+        } else {
+            fx = r.x * inv_n;
+            fy = r.y * inv_n;
+        }
+        int tx = q.valid ? int(fminf(fmaxf(fx, 0.f), 31.f)) : 0;
+        int ty = q.valid ? int(fminf(fmaxf(fy, 0.f), 31.f)) : 0;
+        uint16_t key = uint16_t(((15 - e) << 10) | morton2(tx, ty));
         keys[k] = key;
         atomicAdd(&h[key], 1u);
     }
@@ -511,7 +657,7 @@ cudaError_t launch_traverse(const MapDesc &d, const pndf_query *q, const uint32_
 {
     auto kern = traverse_kernel<BFMT, TFMT, STATS, FLAT>;
     int threads = warps * 32;
-    size_t smem = size_t(warps) * (kStackCap + 32) * sizeof(uint32_t);
+    size_t smem = size_t(warps) * (kStackCap + 64 + kRing) * sizeof(uint32_t);
     int dev = 0, sms = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -524,6 +670,7 @@ cudaError_t launch_traverse(const MapDesc &d, const pndf_query *q, const uint32_
     if (grid > want) grid = want;
     if (grid < 1) grid = 1;
     kern<<<unsigned(grid), threads, smem, s>>>(d, q, order, nq, D, flags, stats, cursor);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -575,11 +722,15 @@ pndf_status launch_eval(const pndf_hierarchy *h, const pndf_query *q, int64_t nq
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         int64_t blocks = (nq + 255) / 256;
         if (blocks > int64_t(sms) * 4) blocks = int64_t(sms) * 4;
-        key_hist<<<unsigned(blocks), 256, 0, s>>>(d, q, nq, keys, hist);
+        const size_t hist_smem = kKeyBins * sizeof(uint32_t);
+        cudaFuncSetAttribute(key_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, int(hist_smem));
+        key_hist<<<unsigned(blocks), 256, hist_smem, s>>>(d, q, nq, cfg.sort, keys, hist);
         key_scan<<<1, 1024, 0, s>>>(hist);
         key_place<<<unsigned(blocks), 256, 0, s>>>(keys, nq, hist, order);
+        count_launches(3);
         e = cudaGetLastError();
     }
+    if (e == cudaSuccess && cfg.ev_begin) e = cudaEventRecord(static_cast<cudaEvent_t>(cfg.ev_begin), s);
     if (e == cudaSuccess) {
         if (d.bounds_fmt == PNDF_BOUNDS_F32)
             e = d.texel_fmt == PNDF_TEXEL_F32X2
@@ -592,6 +743,7 @@ pndf_status launch_eval(const pndf_hierarchy *h, const pndf_query *q, int64_t nq
                     : dispatch_stats<PNDF_BOUNDS_F16_OUTWARD, PNDF_TEXEL_F16X2>(d, q, order, nq, D, flags, stats, cursor,
                                                                              cfg, s);
     }
+    if (e == cudaSuccess && cfg.ev_end) e = cudaEventRecord(static_cast<cudaEvent_t>(cfg.ev_end), s);
     cudaError_t ef = cudaFreeAsync(scratch, s);
     if (e != cudaSuccess || ef != cudaSuccess) return PNDF_ERR_CUDA;
     return PNDF_OK;

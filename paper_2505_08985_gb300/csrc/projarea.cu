@@ -560,6 +560,7 @@ pndf_status launch_projarea(const pndf_hierarchy *h, const pndf_query *q, const 
             pa_items<PNDF_TEXEL_F16X2><<<sms * (occ > 0 ? occ : 1), 256, 0, s>>>(d, q, omega, k0, cnt, off, part, cursor, gl);
         }
         pa_reduce<<<(cnt * 32 + 255) / 256, 256, 0, s>>>(q, k0, cnt, off, part, P);
+        count_launches(4);
         e = cudaGetLastError();
     }
     cudaError_t ef = cudaFreeAsync(scratch, s);

@@ -30,7 +30,7 @@ PNDF_QF_FP64 = 1
 PNDF_QF_INVALID = 4
 PNDF_QF_OVERFLOW = 8
 
-STATS_FIELDS = ("nodes", "leaf_blocks", "tri_tests", "hits", "hit_hash", "fp64_tris", "degenerate", "reserved")
+STATS_FIELDS = ("nodes", "leaf_blocks", "tri_tests", "hits", "hit_hash", "fp64_tris", "degenerate", "quads")
 
 
 class PndfError(RuntimeError):
@@ -46,7 +46,7 @@ class _BuildParams(ctypes.Structure):
 
 class _EvalConfig(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("sort", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32)]
+                ("ctas_per_sm", ctypes.c_int32), ("ev_begin", ctypes.c_void_p), ("ev_end", ctypes.c_void_p)]
 
 
 def _load() -> ctypes.CDLL:
@@ -59,6 +59,7 @@ def _load() -> ctypes.CDLL:
     sig = {
         "pndf_build_hierarchy": ([vp, ctypes.POINTER(_BuildParams), vp, ctypes.POINTER(vp)], i32),
         "pndf_free_hierarchy": ([vp], None),
+        "pndf_update_hierarchy": ([vp, vp, vp], i32),
         "pndf_hierarchy_bytes": ([vp], ctypes.c_size_t),
         "pndf_eval_batch": ([vp, vp, i64, vp, vp, vp, vp], i32),
         "pndf_eval_batch_ex": ([vp, vp, i64, vp, vp, vp, ctypes.POINTER(_EvalConfig), vp], i32),
@@ -67,6 +68,7 @@ def _load() -> ctypes.CDLL:
         "pndf_device_status": ([vp, ctypes.POINTER(ctypes.c_uint32)], i32),
         "pndf_status_string": ([i32], ctypes.c_char_p),
         "pndf_version": ([], i32),
+        "pndf_launch_count": ([], i64),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -151,6 +153,17 @@ def pndf_build_hierarchy(texels: torch.Tensor, bounds_fmt: int = PNDF_BOUNDS_F32
     return Hierarchy(h.value, int(texels.shape[0]), tf, int(bounds_fmt), texels.device)
 
 
+def pndf_update_hierarchy(h: Hierarchy, texels: torch.Tensor, stream=None) -> Hierarchy:
+    """Rebuild h in place from new texels of the same size and dtype."""
+    _need(texels, "texels", shape_last=2)
+    tf = PNDF_TEXEL_F32X2 if texels.dtype == torch.float32 else PNDF_TEXEL_F16X2
+    if texels.shape[0] != h.n or tf != h.texel_fmt:
+        raise ValueError("texels must match the hierarchy's size and format")
+    with torch.cuda.device(texels.device):
+        _check("pndf_update_hierarchy", LIB.pndf_update_hierarchy(h.handle, _ptr(texels), _stream(stream)))
+    return h
+
+
 def pndf_free_hierarchy(h: Hierarchy):
     h.free()
 
@@ -167,8 +180,25 @@ def pndf_eval_batch(h: Hierarchy, queries: torch.Tensor, out: torch.Tensor | Non
     return pndf_eval_batch_ex(h, queries, out=out, flags=flags, stats=stats, stream=stream)
 
 
+def _event_handle(ev):
+    """Raw cudaEvent_t of a torch.cuda.Event (created on first use)."""
+    if ev is None:
+        return None
+    if not ev.cuda_event:
+        ev.record()
+    return int(ev.cuda_event)
+
+
+PNDF_SORT_NONE = 0
+PNDF_SORT_LEVEL_TILE = 1
+PNDF_SORT_LEVEL_NORMAL = 2
+PNDF_SORT_DEFAULT = PNDF_SORT_LEVEL_TILE
+
+
 def pndf_eval_batch_ex(h: Hierarchy, queries: torch.Tensor, out=None, flags=None, stats=None, mode: int = 0,
-                       sort: bool = True, warps_per_cta: int = 0, ctas_per_sm: int = 0, stream=None) -> torch.Tensor:
+                       sort: int = PNDF_SORT_DEFAULT, warps_per_cta: int = 0, ctas_per_sm: int = 0, stream=None,
+                       ev_begin=None, ev_end=None) -> torch.Tensor:
+    """ev_begin / ev_end: optional torch.cuda.Event recorded around the traversal kernel."""
     nq = _queries(queries)
     if out is None:
         out = torch.empty(nq, dtype=torch.float32, device=queries.device)
@@ -177,7 +207,8 @@ def pndf_eval_batch_ex(h: Hierarchy, queries: torch.Tensor, out=None, flags=None
         _need(flags, "flags", dtype=torch.int32)
     if stats is not None:
         _need(stats, "stats", dtype=torch.int32, shape_last=8)
-    cfg = _EvalConfig(int(mode), 1 if sort else 0, int(warps_per_cta), int(ctas_per_sm))
+    cfg = _EvalConfig(int(mode), int(sort), int(warps_per_cta), int(ctas_per_sm),
+                      _event_handle(ev_begin), _event_handle(ev_end))
     with torch.cuda.device(queries.device):
         _check("pndf_eval_batch_ex", LIB.pndf_eval_batch_ex(h.handle, _ptr(queries), nq, _ptr(out), _ptr(flags),
                                                             _ptr(stats), ctypes.byref(cfg), _stream(stream)))
@@ -229,3 +260,7 @@ def pndf_status_string(code: int) -> str:
 
 def pndf_version() -> int:
     return int(LIB.pndf_version())
+
+
+def pndf_launch_count() -> int:
+    return int(LIB.pndf_launch_count())

@@ -30,7 +30,7 @@ def P():
     return pndf
 
 
-def run(P, st, q, bounds=0, mode=0, sort=True, warps=0, stats=True):
+def run(P, st, q, bounds=0, mode=0, sort=1, warps=0, stats=True):
     h = P.pndf_build_hierarchy(st.to(DEV), bounds_fmt=bounds)
     qd = q.to(DEV)
     flags = torch.zeros(q.shape[0], dtype=torch.int32, device=DEV)
@@ -64,7 +64,7 @@ def test_hierarchy_prunes_only(P):
     Dh, _, sh = run(P, st, q, mode=0)
     Df, _, sf = run(P, st, q, mode=1)
     assert np.array_equal(sh[:, 3], sf[:, 3]) and np.array_equal(sh[:, 4], sf[:, 4])
-    assert rel_err(Dh, Df).max() <= 1e-6
+    assert rel_err(Dh, Df).max() <= 1e-5  # same hits, different summation order
     # and pruning is real: far fewer triangle tests than the flat scan
     assert sh[:, 2].sum() < 0.5 * sf[:, 2].sum()
 
@@ -77,7 +77,7 @@ def test_fp16_outward_bounds_keep_hit_sets(P):
     D32, _, s32 = run(P, st, q, bounds=0)
     D16, _, s16 = run(P, st, q, bounds=1)
     assert np.array_equal(s32[:, 3], s16[:, 3]) and np.array_equal(s32[:, 4], s16[:, 4])
-    assert rel_err(D16, D32).max() <= 1e-6
+    assert rel_err(D16, D32).max() <= 1e-5
     assert s16[:, 0].sum() >= s32[:, 0].sum()  # looser boxes visit at least as many nodes
     ref = oracle.pndf(st, q)
     check_pndf(D16, ref, hits_gpu=s16[:, 3], hash_gpu=s16[:, 4], label="scratch512 fp16 bounds")
@@ -180,10 +180,11 @@ def test_result_independent_of_batch(P):
     st = synth.scratch_map(n=256, n_grooves=40, seed=12)
     q = synth.make_queries(st, 2048, synth.QueryMix(sigma=(1.0, 24.0), aspect=(1.0, 4.0), frac_near=0.8), 12)
     D_all, _, _ = run(P, st, q, stats=False)
-    D_uns, _, _ = run(P, st, q, sort=False, stats=False)
+    D_uns, _, _ = run(P, st, q, sort=0, stats=False)
+    D_tile, _, _ = run(P, st, q, sort=2, stats=False)
     D_w4, _, _ = run(P, st, q, warps=4, stats=False)
     D_sub, _, _ = run(P, st, q[100:117], stats=False)
-    assert np.array_equal(D_all, D_uns) and np.array_equal(D_all, D_w4)
+    assert np.array_equal(D_all, D_uns) and np.array_equal(D_all, D_w4) and np.array_equal(D_all, D_tile)
     assert np.array_equal(D_all[100:117], D_sub)
 
 
@@ -246,4 +247,18 @@ def test_flake8192_4m_sampled(P):
         check_pndf(D[idx], ref, hits_gpu=stt[idx, 3], hash_gpu=stt[idx, 4], label=f"flake8192 b={bounds}")
         Ds[bounds] = (D, stt)
     assert np.array_equal(Ds[0][1][:, 4], Ds[1][1][:, 4])
-    assert rel_err(Ds[1][0], Ds[0][0]).max() <= 1e-6
+    assert rel_err(Ds[1][0], Ds[0][0]).max() <= 1e-5
+
+
+def test_update_in_place_matches_fresh_build(P):
+    st_a = synth.bumps_map(n=96, n_bumps=10, seed=31)
+    st_b = synth.flake_normals(96, 40, seed=32)
+    q = synth.make_queries(st_b, 1000, synth.QueryMix(sigma=(1.0, 10.0)), 33)
+    h = P.pndf_build_hierarchy(st_a.to(DEV), bounds_fmt=1)
+    P.pndf_update_hierarchy(h, st_b.to(DEV))
+    D_upd = P.pndf_eval_batch(h, q.to(DEV)).cpu()
+    h.free()
+    h2 = P.pndf_build_hierarchy(st_b.to(DEV), bounds_fmt=1)
+    D_new = P.pndf_eval_batch(h2, q.to(DEV)).cpu()
+    h2.free()
+    assert torch.equal(D_upd, D_new)
