@@ -176,6 +176,30 @@ pndf_status pndf_eval_batch_ex(const pndf_hierarchy *h, const pndf_query *q_dev,
                                const pndf_eval_config *cfg, void *stream);
 
 /*
+ * Allocation-free variant of pndf_eval_batch (the paper has no counterpart:
+ * this serves callers that may not allocate device memory, such as a
+ * renderer plugin whose host owns all device allocations, a real-time thread
+ * that cannot take cudaMalloc's device-wide synchronisation, or code with a
+ * fixed device-memory budget).  Same result as pndf_eval_batch with the
+ * default configuration, for at most pndf_eval_noalloc_max_queries()
+ * (1,048,576) queries per call; larger batches return PNDF_ERR_CAPACITY
+ * before any work is queued.  The sort scratch is one fixed device array
+ * (about 6.4 MB) that every GPU loading the library holds until the process
+ * exits; nothing is allocated or freed.  The first call on each device looks
+ * up that array's device address (cudaGetSymbolAddress) with the device
+ * current, so make it before any stream capture.  Every call shares the
+ * array: calls whose work can overlap on the GPU (another stream, or earlier
+ * work still running) race on it and must be serialised by the caller.
+ *   flags_out_dev: device, nq uint32 (PNDF_QF_* bits) or NULL.
+ * Errors: INVALID_ARG, CAPACITY, CUDA.
+ */
+pndf_status pndf_eval_batch_noalloc(const pndf_hierarchy *h, const pndf_query *q_dev, int64_t nq,
+                                    float *D_out_dev, uint32_t *flags_out_dev, void *stream);
+
+/* Largest nq that pndf_eval_batch_noalloc accepts. */
+int64_t pndf_eval_noalloc_max_queries(void);
+
+/*
  * End-to-end variant with HOST buffers: copies nq queries from q_host to the
  * device, evaluates as pndf_eval_batch, and copies D back to D_host, all on
  * stream; returns after the stream has completed the copy-back.  Pinned host

@@ -152,6 +152,20 @@ pndf_status pndf_eval_batch(const pndf_hierarchy *h, const pndf_query *q_dev, in
     return pndf_eval_batch_ex(h, q_dev, nq, D_out_dev, flags_out_dev, stats_dev, nullptr, stream);
 }
 
+pndf_status pndf_eval_batch_noalloc(const pndf_hierarchy *h, const pndf_query *q_dev, int64_t nq, float *D_out_dev,
+                                    uint32_t *flags_out_dev, void *stream)
+{
+    pndf_status st = check_hierarchy(h);
+    if (st != PNDF_OK) return st;
+    if (nq < 0) return PNDF_ERR_INVALID_ARG;
+    if (nq > noalloc_max_queries()) return PNDF_ERR_CAPACITY;
+    if (nq > 0 && (!q_dev || !D_out_dev)) return PNDF_ERR_INVALID_ARG;
+    if (q_dev && !aligned(q_dev, 16)) return PNDF_ERR_INVALID_ARG;
+    return launch_eval_noalloc(h, q_dev, nq, D_out_dev, flags_out_dev, as_stream(stream));
+}
+
+int64_t pndf_eval_noalloc_max_queries(void) { return noalloc_max_queries(); }
+
 pndf_status pndf_eval_batch_host(const pndf_hierarchy *h, const pndf_query *q_host, int64_t nq, float *D_host,
                                  void *stream)
 {

@@ -86,6 +86,10 @@ pndf_status launch_eval(const pndf_hierarchy *h, const pndf_query *q, int64_t nq
                         pndf_query_stats *stats, const pndf_eval_config &cfg, cudaStream_t s);
 pndf_status launch_projarea(const pndf_hierarchy *h, const pndf_query *q, const float *omega, int64_t nq,
                             float *P, cudaStream_t s);
+// Allocation-free evaluation with the sort scratch in a fixed device array.
+pndf_status launch_eval_noalloc(const pndf_hierarchy *h, const pndf_query *q, int64_t nq, float *D, uint32_t *flags,
+                                cudaStream_t s);
+int64_t noalloc_max_queries();
 // Count of kernels launched by the library (host-side, process-wide).
 void count_launches(int64_t n);
 // Each kernel translation unit keeps its own device status word (PNDF_QF_*

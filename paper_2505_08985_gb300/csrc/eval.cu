@@ -31,6 +31,8 @@
 // delta and are skipped.  Edge functions use an FMA difference of products on
 // vertex-relative differences; triangles whose FP32 |cross| is below 2e-10
 // (normal-space area below 1e-10) are re-tested and weighted in FP64.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace pndf {
@@ -747,6 +749,102 @@ pndf_status launch_eval(const pndf_hierarchy *h, const pndf_query *q, int64_t nq
     cudaError_t ef = cudaFreeAsync(scratch, s);
     if (e != cudaSuccess || ef != cudaSuccess) return PNDF_ERR_CUDA;
     return PNDF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free evaluation (pndf_eval_batch_noalloc).
+//
+// Some callers cannot allocate device memory while they evaluate: a renderer
+// plugin whose host owns every device allocation and forbids others, a
+// real-time thread that must not take cudaMalloc's implicit device-wide
+// synchronisation or its latency, or code that budgets device memory exactly
+// ahead of time.  For them the sort scratch lives in one fixed device array,
+// defined here at file scope and held by every GPU that loads the library
+// until the process exits.  The host never uses the array's name as an
+// address: on the first call on each device, with that device current, the
+// device address is looked up once with cudaGetSymbolAddress and cached.
+// Every call shares the array and it keeps the previous call's contents, so
+// the cursor and histogram are cleared on the stream at the start of each
+// call; calls whose work overlaps on the GPU (different streams, or work not
+// yet complete on another stream) race on the array and must be serialised by
+// the caller.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr int64_t kNoallocMaxQueries = int64_t(1) << 20;
+constexpr size_t kNoallocHistOff = 256;
+constexpr size_t kNoallocKeysOff = kNoallocHistOff + size_t(kKeyBins) * sizeof(uint32_t);
+constexpr size_t kNoallocOrderOff = kNoallocKeysOff + size_t(kNoallocMaxQueries) * sizeof(uint16_t);
+constexpr size_t kNoallocBytes = kNoallocOrderOff + size_t(kNoallocMaxQueries) * sizeof(uint32_t);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+std::mutex g_noalloc_mutex;
+void *g_noalloc_ptr[64] = {};
+
+// Device address of g_noalloc_scratch on the current device (looked up once).
+cudaError_t noalloc_scratch(void **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+int64_t noalloc_max_queries() { return kNoallocMaxQueries; }
+
+pndf_status launch_eval_noalloc(const pndf_hierarchy *h, const pndf_query *q, int64_t nq, float *D, uint32_t *flags,
+                                cudaStream_t s)
+{
+    if (nq > kNoallocMaxQueries) return PNDF_ERR_CAPACITY;
+    if (nq == 0) return PNDF_OK;
+    void *scratch = nullptr;
+    if (noalloc_scratch(&scratch) != cudaSuccess) return PNDF_ERR_CUDA;
+    const MapDesc &d = h->d;
+    pndf_eval_config cfg{PNDF_MODE_HIERARCHY, PNDF_SORT_DEFAULT, 0, 0, nullptr, nullptr};
+    char *base = static_cast<char *>(scratch);
+    auto *cursor = reinterpret_cast<unsigned long long *>(base);
+    auto *hist = reinterpret_cast<uint32_t *>(base + kNoallocHistOff);
+    auto *keys = reinterpret_cast<uint16_t *>(base + kNoallocKeysOff);
+    auto *order = reinterpret_cast<uint32_t *>(base + kNoallocOrderOff);
+    cudaError_t e = cudaMemsetAsync(base, 0, kNoallocKeysOff, s);  // cursor and histogram start at zero
+    if (e != cudaSuccess) return PNDF_ERR_CUDA;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t blocks = (nq + 255) / 256;
+    if (blocks > int64_t(sms) * 4) blocks = int64_t(sms) * 4;
+    const size_t hist_smem = kKeyBins * sizeof(uint32_t);
+    cudaFuncSetAttribute(key_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, int(hist_smem));
+    key_hist<<<unsigned(blocks), 256, hist_smem, s>>>(d, q, nq, cfg.sort, keys, hist);
+    key_scan<<<1, 1024, 0, s>>>(hist);
+    key_place<<<unsigned(blocks), 256, 0, s>>>(keys, nq, hist, order);
+    count_launches(3);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return PNDF_ERR_CUDA;
+    if (d.bounds_fmt == PNDF_BOUNDS_F32)
+        e = d.texel_fmt == PNDF_TEXEL_F32X2
+                ? dispatch_stats<PNDF_BOUNDS_F32, PNDF_TEXEL_F32X2>(d, q, order, nq, D, flags, nullptr, cursor, cfg, s)
+                : dispatch_stats<PNDF_BOUNDS_F32, PNDF_TEXEL_F16X2>(d, q, order, nq, D, flags, nullptr, cursor, cfg, s);
+    else
+        e = d.texel_fmt == PNDF_TEXEL_F32X2
+                ? dispatch_stats<PNDF_BOUNDS_F16_OUTWARD, PNDF_TEXEL_F32X2>(d, q, order, nq, D, flags, nullptr, cursor,
+                                                                         cfg, s)
+                : dispatch_stats<PNDF_BOUNDS_F16_OUTWARD, PNDF_TEXEL_F16X2>(d, q, order, nq, D, flags, nullptr, cursor,
+                                                                         cfg, s);
+    return e == cudaSuccess ? PNDF_OK : PNDF_ERR_CUDA;
 }
 
 cudaError_t read_status_eval(cudaStream_t s, uint32_t *bits, bool clear)

@@ -64,6 +64,8 @@ def _load() -> ctypes.CDLL:
         "pndf_eval_batch": ([vp, vp, i64, vp, vp, vp, vp], i32),
         "pndf_eval_batch_ex": ([vp, vp, i64, vp, vp, vp, ctypes.POINTER(_EvalConfig), vp], i32),
         "pndf_eval_batch_host": ([vp, vp, i64, vp, vp], i32),
+        "pndf_eval_batch_noalloc": ([vp, vp, i64, vp, vp, vp], i32),
+        "pndf_eval_noalloc_max_queries": ([], i64),
         "pndf_diffuse_projected_area": ([vp, vp, vp, i64, vp, vp], i32),
         "pndf_device_status": ([vp, ctypes.POINTER(ctypes.c_uint32)], i32),
         "pndf_status_string": ([i32], ctypes.c_char_p),
@@ -213,6 +215,27 @@ def pndf_eval_batch_ex(h: Hierarchy, queries: torch.Tensor, out=None, flags=None
         _check("pndf_eval_batch_ex", LIB.pndf_eval_batch_ex(h.handle, _ptr(queries), nq, _ptr(out), _ptr(flags),
                                                             _ptr(stats), ctypes.byref(cfg), _stream(stream)))
     return out
+
+
+def pndf_eval_batch_noalloc(h: Hierarchy, queries: torch.Tensor, out: torch.Tensor | None = None,
+                            flags: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """pndf_eval_batch without any device allocation inside the library (the
+    sort scratch is a fixed device array of the library; see pndf.h).  The
+    caller supplies `out` if it must not allocate either."""
+    nq = _queries(queries)
+    if out is None:
+        out = torch.empty(nq, dtype=torch.float32, device=queries.device)
+    _need(out, "out", dtype=torch.float32)
+    if flags is not None:
+        _need(flags, "flags", dtype=torch.int32)
+    with torch.cuda.device(queries.device):
+        _check("pndf_eval_batch_noalloc", LIB.pndf_eval_batch_noalloc(h.handle, _ptr(queries), nq, _ptr(out),
+                                                                      _ptr(flags), _stream(stream)))
+    return out
+
+
+def pndf_eval_noalloc_max_queries() -> int:
+    return int(LIB.pndf_eval_noalloc_max_queries())
 
 
 def pndf_eval_batch_host(h: Hierarchy, queries_host: torch.Tensor, out_host: torch.Tensor | None = None,
