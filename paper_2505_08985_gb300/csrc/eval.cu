@@ -163,6 +163,18 @@ __device__ __forceinline__ bool node_in_footprint(const Query &q, int l, uint32_
     return qmin_box(q, dx0, dx0 + sz, dy0, dy0 + sz) <= kQPrune;
 }
 
+// The node's uv box lies entirely inside the pruning ellipse (the quadratic is
+// convex, so its maximum over the box is at a corner); every descendant then
+// passes the footprint test and skips it.
+__device__ __forceinline__ bool node_inside(const Query &q, int l, uint32_t a, uint32_t c)
+{
+    float sz = float(1u << l);
+    float dx0 = float(a) * sz - q.x, dy0 = float(c) * sz - q.y;
+    float dx1 = dx0 + sz, dy1 = dy0 + sz;
+    float m = fmaxf(fmaxf(qform(q, dx0, dy0), qform(q, dx1, dy0)), fmaxf(qform(q, dx0, dy1), qform(q, dx1, dy1)));
+    return m <= kQPrune;
+}
+
 __device__ __forceinline__ bool box_holds(const float4 &b, const Query &q)
 {
     return q.mx >= b.x && q.mx <= b.z && q.my >= b.y && q.my <= b.w;
@@ -175,10 +187,14 @@ __device__ __forceinline__ bool node_test(const MapDesc &d, const Query &q, int 
     return box_holds(node_box<BFMT>(d, l, morton2(a, c)), q);
 }
 
-__device__ __forceinline__ uint32_t pack(int l, uint32_t a, uint32_t c)
+// Stack / leaf-queue entry: level in bits 28-31, "inside the ellipse" in bit
+// 27, the node's Morton index at its level in bits 0-26 (at most 2 (L - 1) =
+// 26 bits for L <= 14).  A child's Morton index is (m << 2) | (dy << 1 | dx).
+__device__ __forceinline__ uint32_t pack(int l, bool inside, uint32_t m)
 {
-    return (uint32_t(l) << 28) | (a << 14) | c;
+    return (uint32_t(l) << 28) | (uint32_t(inside) << 27) | m;
 }
+constexpr uint32_t kMortonMask = (1u << 27) - 1u;
 
 struct Acc {
     float s, c;  // Neumaier compensated sum
@@ -360,10 +376,10 @@ __device__ __forceinline__ void process_leaves(const MapDesc &d, const Query &q,
         uint32_t a = 0, c = 0;
         const uint32_t k0 = uint32_t(lane & 3) << 2;
         if (blk < nleaf) {
-            uint32_t ent = lq[blk];
-            a = (ent >> 14) & 0x3fffu;
-            c = ent & 0x3fffu;
-            bits = quad_boxes_hold<BFMT>(d, (morton2(a, c) << 4) | k0, q.mx, q.my);
+            uint32_t m = lq[blk] & kMortonMask;
+            a = compact1by1(m);
+            c = compact1by1(m >> 1);
+            bits = quad_boxes_hold<BFMT>(d, (m << 4) | k0, q.mx, q.my);
             if (STATS) {
                 acc.quads += 4;
                 if ((lane & 3) == 0) acc.leaves++;
@@ -374,8 +390,9 @@ __device__ __forceinline__ void process_leaves(const MapDesc &d, const Query &q,
             bool pass = (bits >> u) & 1u;
             unsigned m = __ballot_sync(kFull, pass);
             if (pass) {
-                uint32_t k = k0 | uint32_t(u);
-                uint32_t pk = ((a * kLeafQuads + compact1by1(k)) << 16) | (c * kLeafQuads + compact1by1(k >> 1));
+                uint32_t k = k0 | uint32_t(u);  // Morton index of the quad in its 4 x 4 block
+                uint32_t kx = (k & 1u) | ((k >> 1) & 2u), ky = ((k >> 1) & 1u) | ((k >> 2) & 2u);
+                uint32_t pk = ((a * kLeafQuads + kx) << 16) | (c * kLeafQuads + ky);
                 ring[(head + uint32_t(nsq) + __popc(m & lt)) & (kRing - 1)] = pk;
             }
             nsq += __popc(m);
@@ -452,15 +469,18 @@ __device__ void eval_one(const MapDesc &d, const pndf_query &rec, int lane, uint
         // entry nodes: at most 4 x 4
         {
             int a = a0 + (lane & 3), c = c0 + (lane >> 2);
-            bool pass = lane < 16 && a <= a1 && c <= c1 && node_test<BFMT>(d, q, e, a, c);
-            if (STATS) acc.nodes += (lane < 16 && a <= a1 && c <= c1) ? 1u : 0u;
+            bool valid = lane < 16 && a <= a1 && c <= c1;
+            bool pass = valid && node_test<BFMT>(d, q, e, a, c);
+            bool inside = pass && node_inside(q, e, a, c);
+            if (STATS) acc.nodes += valid ? 1u : 0u;
             unsigned m = __ballot_sync(kFull, pass);
             if (pass) {
                 int pos = __popc(m & lt);
+                uint32_t ent = pack(e, inside, morton2(a, c));
                 if (e == kLeafLevel)
-                    lq[pos] = pack(e, a, c);
+                    lq[pos] = ent;
                 else
-                    stk[pos] = pack(e, a, c);
+                    stk[pos] = ent;
             }
             if (e == kLeafLevel)
                 nleaf = __popc(m);
@@ -479,23 +499,29 @@ __device__ void eval_one(const MapDesc &d, const pndf_query &rec, int lane, uint
             // (k >> 2) and (k >> 2) + 8, so two box loads per lane are in flight
             int npop = min(top, 16);
             top -= npop;
-            bool pass[2];
+            bool pass[2], ins[2];
             int cl[2];
-            uint32_t ca[2], cc[2];
+            uint32_t cm[2];
             float4 bx[2];
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
                 int slot = (lane >> 2) + 8 * r;
                 uint32_t ent = slot < npop ? stk[top + slot] : 0u;
                 cl[r] = int(ent >> 28) - 1;
-                ca[r] = 2u * ((ent >> 14) & 0x3fffu) + (lane & 1);
-                cc[r] = 2u * (ent & 0x3fffu) + ((lane >> 1) & 1);
-                pass[r] = slot < npop && node_in_footprint(q, cl[r], ca[r], cc[r]);
+                cm[r] = ((ent & kMortonMask) << 2) | uint32_t(lane & 3);
+                ins[r] = (ent >> 27) & 1u;
+                pass[r] = slot < npop;
+                if (pass[r] && !ins[r]) {
+                    // parent straddles the ellipse: test this child's uv box
+                    uint32_t a = compact1by1(cm[r]), c = compact1by1(cm[r] >> 1);
+                    pass[r] = node_in_footprint(q, cl[r], a, c);
+                    ins[r] = pass[r] && node_inside(q, cl[r], a, c);
+                }
                 if (STATS && slot < npop) acc.nodes++;
             }
 #pragma unroll
             for (int r = 0; r < 2; ++r)  // both box loads issue before either is used
-                if (pass[r]) bx[r] = node_box<BFMT>(d, cl[r], morton2(ca[r], cc[r]));
+                if (pass[r]) bx[r] = node_box<BFMT>(d, cl[r], cm[r]);
 #pragma unroll
             for (int r = 0; r < 2; ++r) pass[r] = pass[r] && box_holds(bx[r], q);
             __syncwarp();
@@ -504,10 +530,10 @@ __device__ void eval_one(const MapDesc &d, const pndf_query &rec, int lane, uint
                 bool to_leaf = pass[r] && cl[r] == kLeafLevel, to_stack = pass[r] && cl[r] > kLeafLevel;
                 unsigned ml = __ballot_sync(kFull, to_leaf);
                 unsigned ms = __ballot_sync(kFull, to_stack);
-                if (to_leaf) lq[nleaf + __popc(ml & lt)] = pack(cl[r], ca[r], cc[r]);
+                if (to_leaf) lq[nleaf + __popc(ml & lt)] = pack(cl[r], ins[r], cm[r]);
                 if (to_stack) {
                     int pos = top + __popc(ms & lt);
-                    if (pos < kStackCap) stk[pos] = pack(cl[r], ca[r], cc[r]);
+                    if (pos < kStackCap) stk[pos] = pack(cl[r], ins[r], cm[r]);
                 }
                 nleaf += __popc(ml);
                 top += __popc(ms);
