@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--n", type=int, default=synth.FLAKE_8192["n"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-batches", type=int, default=2000, help="serving workload size (0 = skip serving)")
+    ap.add_argument("--serve-load", type=float, default=0.8, help="offered load, fraction of plain FP32 capacity")
     return ap.parse_args()
 
 
@@ -259,6 +261,61 @@ def run_reference(args, world, rank):
 
 
 # ---------------------------------------------------------------------------
+# serving: four resident maps, Poisson stream of camera batches
+# ---------------------------------------------------------------------------
+
+def run_serving(args, dev):
+    from paper_2505_08985_gb300 import pndf, serve
+
+    sts = synth.serving_maps(device=dev)
+    batches = synth.serving_batches(args.serve_batches, seed=9)
+    qs = [synth.camera_queries(sts[m].shape[0], n, seed=sd, device=dev) for (m, n, sd) in batches]
+    h16 = [pndf.pndf_build_hierarchy(st, bounds_fmt=pndf.PNDF_BOUNDS_F16_OUTWARD) for st in sts]
+    h32 = [pndf.pndf_build_hierarchy(st, bounds_fmt=pndf.PNDF_BOUNDS_F32) for st in sts]
+    torch.cuda.synchronize()
+
+    def requests(arrivals):
+        return [serve.Request(rid=k, map=batches[k][0], queries=qs[k], arrival=a) for k, a in enumerate(arrivals)]
+
+    n = len(batches)
+    total = sum(b[1] for b in batches)
+    t0 = time.perf_counter()
+    plain_cap = serve.run_plain(h32, requests([0.0] * n), realtime=False)
+    rate = args.serve_load * plain_cap["queries_per_s"] / (total / n)
+    # autotune on the first batches of the stream at the target load
+    ns = min(n, 300)
+    sample = requests([0.0] * ns)
+    tune = serve.autotune(h16, sample, arrivals=serve.poisson_arrivals(ns, rate, seed=5))
+    batcher = serve.ContinuousBatcher(h16, step_queries=tune.step_queries, warps_per_cta=tune.warps_per_cta,
+                                      ctas_per_sm=tune.ctas_per_sm)
+    served_cap = batcher.run(requests([0.0] * n), realtime=False)
+    arrivals = serve.poisson_arrivals(n, rate, seed=17)
+    served = batcher.run(requests(arrivals), realtime=True)
+    steps = batcher.steps
+    batcher.close()
+    plain = serve.run_plain(h32, requests(arrivals), realtime=True)
+    for h in h16 + h32:
+        h.free()
+    del qs
+    keep = ("p50_ms", "p99_ms", "mean_ms", "queries_per_s", "span_s")
+    return {
+        "workload": "4 resident maps (1024^2 bumps, 2048^2 scratches, 4096^2 and 8192^2 flakes); "
+                    f"{n} camera batches, sizes log-U(1K, 1M), {total} queries; Poisson arrivals at "
+                    f"{args.serve_load:g} x plain FP32 capacity ({rate:.1f} batches/s)",
+        "served_fp16": {k: served[k] for k in keep},
+        "plain_fp32": {k: plain[k] for k in keep},
+        "capacity_queries_per_s": {"served_fp16": served_cap["queries_per_s"],
+                                   "plain_fp32": plain_cap["queries_per_s"]},
+        "autotune": {"objective": "lowest p99 on the first batches at the target load",
+                     "step_queries": tune.step_queries, "warps_per_cta": tune.warps_per_cta,
+                     "ctas_per_sm": tune.ctas_per_sm,
+                     "table [step, ctas_per_sm, warps, p99_ms, q/s]": tune.table},
+        "steps_last_run": steps,
+        "wall_s": time.perf_counter() - t0,
+    }
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 
@@ -380,6 +437,14 @@ def run_gpu(args, world, rank, local):
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
+
+    if args.serve_batches > 0:
+        del st, q, D, st_h, q_h, D_h, st_d
+        torch.cuda.empty_cache()
+        line["serving"] = run_serving(args, dev)
+        line["serving"]["note"] = "per GPU (each rank serves its own replica of the stream)"
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            st, q = make_workload(args, dev, rank)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle

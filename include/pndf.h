@@ -232,6 +232,72 @@ pndf_status pndf_diffuse_projected_area(const pndf_hierarchy *h, const pndf_quer
                                         const float *omega_dev, int64_t nq, float *P_out_dev,
                                         void *stream);
 
+/*
+ * Evaluation order for a batch (the keying and counting sort that
+ * pndf_eval_batch applies internally, App. C entry level): order_dev receives
+ * a permutation of 0..nq-1, largest footprints first, grouped by tile.
+ *   order_dev: device, nq uint32.  Scratch is stream-ordered from the pool.
+ * Errors: INVALID_ARG, OOM, CUDA.
+ */
+pndf_status pndf_sort_queries(const pndf_hierarchy *h, const pndf_query *q_dev, int64_t nq, uint32_t *order_dev,
+                              void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Serving: continuous batching over several resident hierarchies.
+ *
+ * A server holds a table of hierarchies (same texel and bounds formats) and
+ * runs steps.  A step evaluates a list of segments, each a slice of one
+ * request's queries on one map, in a single persistent kernel launch: warps
+ * pull queries from all segments through one work cursor, so requests of
+ * different sizes and maps share the GPU.  Each step is a CUDA graph (copy of
+ * the segment table from pinned host memory, cursor reset, kernel) replayed
+ * with new table contents; two table slots alternate, so the host can queue
+ * step k+1 while step k runs.  A query's result does not depend on which
+ * other segments share its step (one warp evaluates it with a fixed order).
+ * ------------------------------------------------------------------------- */
+
+typedef struct pndf_segment {
+    const pndf_query *q;    /* device: the request's query records                    */
+    const uint32_t *order;  /* device: evaluation order (indices into q), or NULL      */
+    float *D;               /* device: the request's results, indexed like q           */
+    uint32_t *flags;        /* device: per-query PNDF_QF_* bits, or NULL               */
+    int32_t map;            /* index into the server's hierarchy table                 */
+    int32_t first;          /* first position of this slice (in order[], else in q[])  */
+    int32_t count;          /* queries in this slice                                   */
+    int32_t reserved;
+} pndf_segment;
+
+typedef struct pndf_server pndf_server;
+
+typedef struct pndf_server_config {
+    int32_t max_segments;   /* segments per step (0 = 1024)                           */
+    int32_t warps_per_cta;  /* 0 = 8                                                  */
+    int32_t ctas_per_sm;    /* 0 = as many as fit                                     */
+    int32_t reserved;
+} pndf_server_config;
+
+/* Create a server over nmaps (1..8) hierarchies on the current device; maps
+ * must outlive the server.  Allocates its tables (device and pinned host) and
+ * captures the step graphs.  Errors: INVALID_ARG (formats differ, bad counts),
+ * OOM, CUDA. */
+pndf_status pndf_server_create(const pndf_hierarchy *const *maps, int32_t nmaps, const pndf_server_config *cfg,
+                               pndf_server **out);
+
+/* Queue one step over nsegs segments (host array, copied before return) on
+ * stream; ev_done (optional cudaEvent_t) is recorded when the step's kernel
+ * completes.  Blocks only if the table slot is still in use by the step
+ * before the previous one.  All pointers in the segments must stay valid
+ * until the step completes.  Errors: INVALID_ARG (bad map index, count,
+ * pointers, nsegs > max_segments), CUDA. */
+pndf_status pndf_server_step(pndf_server *srv, const pndf_segment *segs_host, int32_t nsegs, void *stream,
+                             void *ev_done);
+
+/* Wait for every queued step of this server. */
+pndf_status pndf_server_sync(pndf_server *srv);
+
+/* Release the server (waits for its queued steps; safe on NULL). */
+void pndf_server_destroy(pndf_server *srv);
+
 /* Read and clear the per-device status word that kernels set on device-side
  * errors (synchronises stream).  PNDF_OK if none; PNDF_ERR_DEVICE otherwise,
  * with the raw PNDF_QF_* bits in *bits_out when bits_out != NULL. */

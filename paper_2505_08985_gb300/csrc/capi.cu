@@ -166,6 +166,17 @@ pndf_status pndf_eval_batch_noalloc(const pndf_hierarchy *h, const pndf_query *q
 
 int64_t pndf_eval_noalloc_max_queries(void) { return noalloc_max_queries(); }
 
+pndf_status pndf_sort_queries(const pndf_hierarchy *h, const pndf_query *q_dev, int64_t nq, uint32_t *order_dev,
+                              void *stream)
+{
+    pndf_status st = check_hierarchy(h);
+    if (st != PNDF_OK) return st;
+    if (nq < 0 || nq > int64_t(0x7fffffff)) return PNDF_ERR_INVALID_ARG;
+    if (nq > 0 && (!q_dev || !order_dev)) return PNDF_ERR_INVALID_ARG;
+    if (q_dev && !aligned(q_dev, 16)) return PNDF_ERR_INVALID_ARG;
+    return launch_sort(h, q_dev, nq, order_dev, as_stream(stream));
+}
+
 pndf_status pndf_eval_batch_host(const pndf_hierarchy *h, const pndf_query *q_host, int64_t nq, float *D_host,
                                  void *stream)
 {

@@ -10,6 +10,7 @@
 namespace pndf {
 
 constexpr int kMaxLevels = 16;
+constexpr int kServeMaxMaps = 8;     // hierarchies per server
 constexpr int kLeafLevel = 2;        // stored bottom level: 4 x 4 quads = 32 triangles = one warp
 constexpr int kLeafQuads = 1 << kLeafLevel;
 constexpr int kLeafTexels = kLeafQuads + 1;
@@ -86,6 +87,12 @@ pndf_status launch_eval(const pndf_hierarchy *h, const pndf_query *q, int64_t nq
                         pndf_query_stats *stats, const pndf_eval_config &cfg, cudaStream_t s);
 pndf_status launch_projarea(const pndf_hierarchy *h, const pndf_query *q, const float *omega, int64_t nq,
                             float *P, cudaStream_t s);
+// Evaluation order of a batch (key + counting sort).
+pndf_status launch_sort(const pndf_hierarchy *h, const pndf_query *q, int64_t nq, uint32_t *order, cudaStream_t s);
+// One serving step over a device segment table (see serve.cu).
+cudaError_t launch_serve(int texel_fmt, int bounds_fmt, const MapDesc *maps, int nmaps, const uint32_t *table,
+                         const pndf_segment *segs, unsigned long long *cursor, int warps, int ctas_per_sm,
+                         cudaStream_t s);
 // Allocation-free evaluation with the sort scratch in a fixed device array.
 pndf_status launch_eval_noalloc(const pndf_hierarchy *h, const pndf_query *q, int64_t nq, float *D, uint32_t *flags,
                                 cudaStream_t s);

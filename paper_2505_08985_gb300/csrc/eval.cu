@@ -778,6 +778,135 @@ pndf_status launch_eval(const pndf_hierarchy *h, const pndf_query *q, int64_t nq
 }
 
 // ---------------------------------------------------------------------------
+// Sorting a batch on its own (pndf_sort_queries).
+// ---------------------------------------------------------------------------
+
+pndf_status launch_sort(const pndf_hierarchy *h, const pndf_query *q, int64_t nq, uint32_t *order, cudaStream_t s)
+{
+    if (nq == 0) return PNDF_OK;
+    size_t off_keys = size_t(kKeyBins) * sizeof(uint32_t);
+    size_t bytes = off_keys + ((size_t(nq) * sizeof(uint16_t) + 255) & ~size_t(255));
+    void *scratch = nullptr;
+    if (cudaMallocAsync(&scratch, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return PNDF_ERR_OOM;
+    }
+    auto *hist = static_cast<uint32_t *>(scratch);
+    auto *keys = reinterpret_cast<uint16_t *>(static_cast<char *>(scratch) + off_keys);
+    cudaError_t e = cudaMemsetAsync(hist, 0, off_keys, s);
+    if (e == cudaSuccess) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        int64_t blocks = (nq + 255) / 256;
+        if (blocks > int64_t(sms) * 4) blocks = int64_t(sms) * 4;
+        const size_t hist_smem = kKeyBins * sizeof(uint32_t);
+        cudaFuncSetAttribute(key_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, int(hist_smem));
+        key_hist<<<unsigned(blocks), 256, hist_smem, s>>>(h->d, q, nq, PNDF_SORT_DEFAULT, keys, hist);
+        key_scan<<<1, 1024, 0, s>>>(hist);
+        key_place<<<unsigned(blocks), 256, 0, s>>>(keys, nq, hist, order);
+        count_launches(3);
+        e = cudaGetLastError();
+    }
+    cudaError_t ef = cudaFreeAsync(scratch, s);
+    return (e == cudaSuccess && ef == cudaSuccess) ? PNDF_OK : PNDF_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Serving step kernel: one persistent launch over a table of segments.
+//
+// Table layout (device): uint32 nsegs, uint32 prefix[nsegs + 1] (prefix[0] =
+// 0, prefix[i] = queries in segments 0..i-1), then the pndf_segment array at
+// a 16-byte boundary.  Warps pull global work indices from one cursor; index k
+// belongs to the last segment i with prefix[i] <= k.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+template <int BFMT, int TFMT>
+__global__ void __launch_bounds__(256, PNDF_TRAVERSE_MIN_CTAS)
+    serve_kernel(const MapDesc *__restrict__ maps, int nmaps, const uint32_t *__restrict__ table,
+                 const pndf_segment *__restrict__ segs, unsigned long long *__restrict__ cursor)
+{
+    extern __shared__ uint32_t smem[];
+    __shared__ MapDesc smaps[kServeMaxMaps];
+    {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(maps);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(smaps);
+        const int words = nmaps * int(sizeof(MapDesc) / sizeof(uint32_t));
+        for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t *stk = smem + warp * (kStackCap + 64 + kRing);
+    uint32_t *lq = stk + kStackCap;
+    uint32_t *ring = lq + 64;
+    const int nsegs = int(table[0]);
+    const uint32_t *prefix = table + 1;
+    const uint32_t total = prefix[nsegs];
+    while (true) {
+        unsigned long long k = 0;
+        if (lane == 0) k = atomicAdd(cursor, 1ull);
+        k = __shfl_sync(kFull, k, 0);
+        if (k >= total) break;
+        int lo = 0, hi = nsegs - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (prefix[mid] <= uint32_t(k))
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const pndf_segment sg = segs[lo];
+        const int64_t j = int64_t(sg.first) + int64_t(uint32_t(k) - prefix[lo]);
+        const int64_t qi = sg.order ? int64_t(sg.order[j]) : j;
+        const pndf_query rec = sg.q[qi];
+        float Dv;
+        uint32_t fv;
+        eval_one<BFMT, TFMT, false, false>(smaps[sg.map], rec, lane, stk, lq, ring, Dv, fv, nullptr);
+        if (lane == 0) {
+            sg.D[qi] = Dv;
+            if (sg.flags) sg.flags[qi] = fv;
+        }
+    }
+}
+
+template <int BFMT, int TFMT>
+cudaError_t launch_serve_t(const MapDesc *maps, int nmaps, const uint32_t *table, const pndf_segment *segs,
+                           unsigned long long *cursor, int warps, int ctas_per_sm, cudaStream_t s)
+{
+    auto kern = serve_kernel<BFMT, TFMT>;
+    int threads = warps * 32;
+    size_t smem = size_t(warps) * (kStackCap + 64 + kRing) * sizeof(uint32_t);
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    if (ctas_per_sm > 0 && ctas_per_sm < occ) occ = ctas_per_sm;
+    kern<<<unsigned(sms * occ), threads, smem, s>>>(maps, nmaps, table, segs, cursor);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_serve(int texel_fmt, int bounds_fmt, const MapDesc *maps, int nmaps, const uint32_t *table,
+                         const pndf_segment *segs, unsigned long long *cursor, int warps, int ctas_per_sm,
+                         cudaStream_t s)
+{
+    if (bounds_fmt == PNDF_BOUNDS_F32)
+        return texel_fmt == PNDF_TEXEL_F32X2
+                   ? launch_serve_t<PNDF_BOUNDS_F32, PNDF_TEXEL_F32X2>(maps, nmaps, table, segs, cursor, warps, ctas_per_sm, s)
+                   : launch_serve_t<PNDF_BOUNDS_F32, PNDF_TEXEL_F16X2>(maps, nmaps, table, segs, cursor, warps, ctas_per_sm, s);
+    return texel_fmt == PNDF_TEXEL_F32X2
+               ? launch_serve_t<PNDF_BOUNDS_F16_OUTWARD, PNDF_TEXEL_F32X2>(maps, nmaps, table, segs, cursor, warps,
+                                                                          ctas_per_sm, s)
+               : launch_serve_t<PNDF_BOUNDS_F16_OUTWARD, PNDF_TEXEL_F16X2>(maps, nmaps, table, segs, cursor, warps,
+                                                                          ctas_per_sm, s);
+}
+
+// ---------------------------------------------------------------------------
 // Allocation-free evaluation (pndf_eval_batch_noalloc).
 //
 // Some callers cannot allocate device memory while they evaluate: a renderer

@@ -1,0 +1,182 @@
+// Serving runtime: a table of resident hierarchies and graph-replayed steps.
+//
+// Each step evaluates a list of segments (slices of requests, possibly on
+// different maps) in one persistent kernel launch.  The segment table is
+// written into a pinned host buffer and copied to the device by the step's
+// CUDA graph (copy, cursor reset, kernel), captured once per table slot.  Two
+// slots alternate: writing slot k's host buffer only waits for the step that
+// last used that slot, so one step can be queued while the previous runs.
+#include <string.h>
+
+#include <new>
+
+#include "common.cuh"
+
+using namespace pndf;
+
+namespace {
+
+struct Slot {
+    void *host = nullptr;            // pinned: header + prefix + segments
+    void *dev = nullptr;             // device: same layout, then the work cursor
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t done = nullptr;
+    bool used = false;
+};
+
+size_t prefix_bytes(int max_segs) { return ((size_t(max_segs) + 2) * sizeof(uint32_t) + 15) & ~size_t(15); }
+
+size_t table_bytes(int max_segs) { return prefix_bytes(max_segs) + size_t(max_segs) * sizeof(pndf_segment); }
+
+}  // namespace
+
+struct pndf_server {
+    int device = 0;
+    int nmaps = 0;
+    int texel_fmt = 0, bounds_fmt = 0;
+    int max_segs = 0, warps = 8, ctas = 0;
+    MapDesc *maps_dev = nullptr;
+    cudaStream_t cap = nullptr;
+    Slot slot[2];
+    int next = 0;
+};
+
+namespace {
+
+void release(pndf_server *s)
+{
+    if (!s) return;
+    for (Slot &sl : s->slot) {
+        if (sl.done) cudaEventSynchronize(sl.done);
+        if (sl.exec) cudaGraphExecDestroy(sl.exec);
+        if (sl.done) cudaEventDestroy(sl.done);
+        if (sl.dev) cudaFree(sl.dev);
+        if (sl.host) cudaFreeHost(sl.host);
+    }
+    if (s->maps_dev) cudaFree(s->maps_dev);
+    if (s->cap) cudaStreamDestroy(s->cap);
+    delete s;
+}
+
+cudaError_t capture_slot(pndf_server *s, Slot &sl)
+{
+    const size_t tb = table_bytes(s->max_segs);
+    const uint32_t *table = static_cast<const uint32_t *>(sl.dev);
+    const pndf_segment *segs =
+        reinterpret_cast<const pndf_segment *>(static_cast<const char *>(sl.dev) + prefix_bytes(s->max_segs));
+    auto *cursor = reinterpret_cast<unsigned long long *>(static_cast<char *>(sl.dev) + tb);
+    cudaError_t e = cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaMemcpyAsync(sl.dev, sl.host, tb, cudaMemcpyHostToDevice, s->cap);
+    cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), s->cap);
+    launch_serve(s->texel_fmt, s->bounds_fmt, s->maps_dev, s->nmaps, table, segs, cursor, s->warps, s->ctas, s->cap);
+    cudaGraph_t g = nullptr;
+    cudaError_t ec = cudaStreamEndCapture(s->cap, &g);
+    if (ec != cudaSuccess) return ec;
+    e = cudaGraphInstantiate(&sl.exec, g, 0);
+    cudaGraphDestroy(g);
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+pndf_status pndf_server_create(const pndf_hierarchy *const *maps, int32_t nmaps, const pndf_server_config *cfg,
+                               pndf_server **out)
+{
+    if (!out) return PNDF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!maps || nmaps < 1 || nmaps > kServeMaxMaps) return PNDF_ERR_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PNDF_ERR_CUDA;
+    for (int i = 0; i < nmaps; ++i) {
+        if (!maps[i] || !maps[i]->mem || maps[i]->device != dev) return PNDF_ERR_INVALID_ARG;
+        if (maps[i]->d.texel_fmt != maps[0]->d.texel_fmt || maps[i]->d.bounds_fmt != maps[0]->d.bounds_fmt)
+            return PNDF_ERR_INVALID_ARG;
+    }
+    pndf_server_config c{1024, 8, 0, 0};
+    if (cfg) {
+        if (cfg->max_segments < 0 || cfg->warps_per_cta < 0 || cfg->warps_per_cta > 8 || cfg->ctas_per_sm < 0)
+            return PNDF_ERR_INVALID_ARG;
+        if (cfg->max_segments) c.max_segments = cfg->max_segments;
+        if (cfg->warps_per_cta) c.warps_per_cta = cfg->warps_per_cta;
+        c.ctas_per_sm = cfg->ctas_per_sm;
+    }
+    if (c.max_segments > (1 << 16)) return PNDF_ERR_INVALID_ARG;
+    pndf_server *s = new (std::nothrow) pndf_server();
+    if (!s) return PNDF_ERR_OOM;
+    s->device = dev;
+    s->nmaps = nmaps;
+    s->texel_fmt = maps[0]->d.texel_fmt;
+    s->bounds_fmt = maps[0]->d.bounds_fmt;
+    s->max_segs = c.max_segments;
+    s->warps = c.warps_per_cta;
+    s->ctas = c.ctas_per_sm;
+    MapDesc host_maps[kServeMaxMaps];
+    for (int i = 0; i < nmaps; ++i) host_maps[i] = maps[i]->d;
+    const size_t tb = table_bytes(s->max_segs);
+    bool ok = cudaMalloc(&s->maps_dev, sizeof(MapDesc) * nmaps) == cudaSuccess &&
+              cudaMemcpy(s->maps_dev, host_maps, sizeof(MapDesc) * nmaps, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) == cudaSuccess;
+    for (int k = 0; ok && k < 2; ++k) {
+        Slot &sl = s->slot[k];
+        ok = cudaMallocHost(&sl.host, tb) == cudaSuccess && cudaMalloc(&sl.dev, tb + 256) == cudaSuccess &&
+             cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) == cudaSuccess;
+        if (ok) {
+            memset(sl.host, 0, tb);
+            ok = capture_slot(s, sl) == cudaSuccess;
+        }
+    }
+    if (!ok) {
+        cudaError_t e = cudaGetLastError();
+        release(s);
+        return e == cudaErrorMemoryAllocation ? PNDF_ERR_OOM : PNDF_ERR_CUDA;
+    }
+    *out = s;
+    return PNDF_OK;
+}
+
+pndf_status pndf_server_step(pndf_server *s, const pndf_segment *segs, int32_t nsegs, void *stream, void *ev_done)
+{
+    if (!s) return PNDF_ERR_INVALID_ARG;
+    if (nsegs < 0 || nsegs > s->max_segs || (nsegs > 0 && !segs)) return PNDF_ERR_INVALID_ARG;
+    uint64_t total = 0;
+    for (int i = 0; i < nsegs; ++i) {
+        const pndf_segment &g = segs[i];
+        if (g.map < 0 || g.map >= s->nmaps || g.count < 0 || g.first < 0) return PNDF_ERR_INVALID_ARG;
+        if (g.count > 0 && (!g.q || !g.D)) return PNDF_ERR_INVALID_ARG;
+        total += uint64_t(g.count);
+    }
+    if (total >= (uint64_t(1) << 32)) return PNDF_ERR_INVALID_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != s->device) return PNDF_ERR_INVALID_ARG;
+    Slot &sl = s->slot[s->next];
+    s->next ^= 1;
+    if (sl.used && cudaEventSynchronize(sl.done) != cudaSuccess) return PNDF_ERR_CUDA;
+    uint32_t *hdr = static_cast<uint32_t *>(sl.host);
+    hdr[0] = uint32_t(nsegs);
+    uint32_t *prefix = hdr + 1;
+    prefix[0] = 0;
+    for (int i = 0; i < nsegs; ++i) prefix[i + 1] = prefix[i] + uint32_t(segs[i].count);
+    memcpy(static_cast<char *>(sl.host) + prefix_bytes(s->max_segs), segs, sizeof(pndf_segment) * size_t(nsegs));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaGraphLaunch(sl.exec, st);
+    if (e == cudaSuccess) e = cudaEventRecord(sl.done, st);
+    if (e == cudaSuccess && ev_done) e = cudaEventRecord(static_cast<cudaEvent_t>(ev_done), st);
+    sl.used = true;
+    count_launches(1);
+    return e == cudaSuccess ? PNDF_OK : PNDF_ERR_CUDA;
+}
+
+pndf_status pndf_server_sync(pndf_server *s)
+{
+    if (!s) return PNDF_ERR_INVALID_ARG;
+    for (Slot &sl : s->slot)
+        if (sl.used && cudaEventSynchronize(sl.done) != cudaSuccess) return PNDF_ERR_CUDA;
+    return PNDF_OK;
+}
+
+void pndf_server_destroy(pndf_server *s) { release(s); }
+
+}  // extern "C"

@@ -49,6 +49,17 @@ class _EvalConfig(ctypes.Structure):
                 ("ctas_per_sm", ctypes.c_int32), ("ev_begin", ctypes.c_void_p), ("ev_end", ctypes.c_void_p)]
 
 
+class _Segment(ctypes.Structure):
+    _fields_ = [("q", ctypes.c_void_p), ("order", ctypes.c_void_p), ("D", ctypes.c_void_p),
+                ("flags", ctypes.c_void_p), ("map", ctypes.c_int32), ("first", ctypes.c_int32),
+                ("count", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class _ServerConfig(ctypes.Structure):
+    _fields_ = [("max_segments", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 def _load() -> ctypes.CDLL:
     path = _build.LIB
     if not os.path.exists(path):
@@ -71,6 +82,11 @@ def _load() -> ctypes.CDLL:
         "pndf_status_string": ([i32], ctypes.c_char_p),
         "pndf_version": ([], i32),
         "pndf_launch_count": ([], i64),
+        "pndf_sort_queries": ([vp, vp, i64, vp, vp], i32),
+        "pndf_server_create": ([ctypes.POINTER(vp), i32, ctypes.POINTER(_ServerConfig), ctypes.POINTER(vp)], i32),
+        "pndf_server_step": ([vp, ctypes.POINTER(_Segment), i32, vp, vp], i32),
+        "pndf_server_sync": ([vp], i32),
+        "pndf_server_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -287,3 +303,73 @@ def pndf_version() -> int:
 
 def pndf_launch_count() -> int:
     return int(LIB.pndf_launch_count())
+
+
+def pndf_sort_queries(h: Hierarchy, queries: torch.Tensor, order: torch.Tensor | None = None,
+                      stream=None) -> torch.Tensor:
+    """Evaluation order of a batch (int32 permutation, largest footprints first)."""
+    nq = _queries(queries)
+    if order is None:
+        order = torch.empty(nq, dtype=torch.int32, device=queries.device)
+    _need(order, "order", dtype=torch.int32)
+    with torch.cuda.device(queries.device):
+        _check("pndf_sort_queries", LIB.pndf_sort_queries(h.handle, _ptr(queries), nq, _ptr(order), _stream(stream)))
+    return order
+
+
+class Server:
+    """A serving table of resident hierarchies (see pndf_server_create)."""
+
+    def __init__(self, handle: int, maps: list, max_segments: int):
+        self.handle = handle
+        self.maps = list(maps)
+        self.max_segments = max_segments
+        self._segs = (_Segment * max_segments)()
+
+    def destroy(self):
+        if self.handle:
+            LIB.pndf_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def pndf_server_create(maps: list, max_segments: int = 1024, warps_per_cta: int = 0, ctas_per_sm: int = 0) -> Server:
+    arr = (ctypes.c_void_p * len(maps))(*[m.handle for m in maps])
+    cfg = _ServerConfig(int(max_segments), int(warps_per_cta), int(ctas_per_sm), 0)
+    h = ctypes.c_void_p()
+    with torch.cuda.device(maps[0].device):
+        _check("pndf_server_create", LIB.pndf_server_create(arr, len(maps), ctypes.byref(cfg), ctypes.byref(h)))
+    return Server(h.value, maps, int(max_segments))
+
+
+def pndf_server_step(srv: Server, segments: list, stream=None, ev_done=None):
+    """segments: list of (map_index, queries, order_or_None, D, flags_or_None, first, count);
+    tensors must stay alive until the step completes."""
+    n = len(segments)
+    if n > srv.max_segments:
+        raise ValueError("too many segments for this server")
+    segs = srv._segs
+    for i, (mi, q, order, D, flags, first, count) in enumerate(segments):
+        sg = segs[i]
+        sg.q = _ptr(q)
+        sg.order = _ptr(order)
+        sg.D = _ptr(D)
+        sg.flags = _ptr(flags)
+        sg.map = int(mi)
+        sg.first = int(first)
+        sg.count = int(count)
+        sg.reserved = 0
+    _check("pndf_server_step", LIB.pndf_server_step(srv.handle, segs, n, _stream(stream), _event_handle(ev_done)))
+
+
+def pndf_server_sync(srv: Server):
+    _check("pndf_server_sync", LIB.pndf_server_sync(srv.handle))
+
+
+def pndf_server_destroy(srv: Server):
+    srv.destroy()

@@ -1,0 +1,241 @@
+"""Continuous-batching P-NDF serving over several resident hierarchies.
+
+Requests (a batch of queries on one map) arrive over time.  The batcher
+admits arrived requests while their working buffers (evaluation order and
+results, 8 bytes per query) fit a device-memory budget, sorts each once on a
+copy stream, and runs steps: each step takes up to `step_queries` queries from
+the admitted requests in arrival order (a large request spans several steps;
+small ones share a step) and evaluates them in one persistent kernel launch
+replayed from a CUDA graph (pndf_server_step).  Up to two steps are in flight,
+so requests that arrive while the GPU works are admitted and joined to the
+next step as soon as memory frees up.
+
+A request's latency runs from its arrival to the device completion of the step
+that holds its last queries, on one clock: the device timeline anchored by an
+event recorded when the run starts.
+
+The plain baseline launches each batch alone with pndf_eval_batch (FP32
+bounds, no graphs, no sharing of launches) in arrival order.
+"""
+
+from __future__ import annotations
+
+import math
+import statistics
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import torch
+
+from . import pndf
+
+BYTES_PER_QUERY = 8  # order (4) + result (4) held while a request is admitted
+
+
+@dataclass
+class Request:
+    rid: int
+    map: int
+    queries: torch.Tensor            # (n, 8) float32 on the serving device, owned by the client
+    arrival: float                   # seconds from the run's time origin
+    D: torch.Tensor | None = None    # results, filled by the run
+    order: torch.Tensor | None = None
+    ready: torch.cuda.Event | None = None
+    next: int = 0
+    waited: bool = False
+    done: torch.cuda.Event | None = None
+    latency: float = math.nan
+
+    @property
+    def n(self) -> int:
+        return int(self.queries.shape[0])
+
+
+def percentile(xs, p):
+    xs = sorted(xs)
+    if not xs:
+        return math.nan
+    k = (len(xs) - 1) * p
+    lo, hi = math.floor(k), math.ceil(k)
+    return xs[lo] + (xs[hi] - xs[lo]) * (k - lo)
+
+
+def summarize(reqs, t_first, t_last):
+    lat = [r.latency for r in reqs]
+    nq = sum(r.n for r in reqs)
+    span = max(t_last - t_first, 1e-9)
+    return {"requests": len(reqs), "queries": nq, "p50_ms": 1e3 * percentile(lat, 0.5),
+            "p99_ms": 1e3 * percentile(lat, 0.99), "mean_ms": 1e3 * statistics.fmean(lat),
+            "queries_per_s": nq / span, "span_s": span}
+
+
+class ContinuousBatcher:
+    """Continuous batching over `maps` (same texel and bounds formats)."""
+
+    def __init__(self, maps, step_queries: int = 1 << 20, memory_budget: int = 2 << 30, max_segments: int = 1024,
+                 warps_per_cta: int = 0, ctas_per_sm: int = 0):
+        self.maps = list(maps)
+        self.device = self.maps[0].device
+        self.step_queries = int(step_queries)
+        self.budget = int(memory_budget)
+        self.server = pndf.pndf_server_create(self.maps, max_segments=max_segments, warps_per_cta=warps_per_cta,
+                                              ctas_per_sm=ctas_per_sm)
+        self.max_segments = max_segments
+        self.copy_stream = torch.cuda.Stream(self.device)
+        self.step_stream = torch.cuda.Stream(self.device)
+        self.steps = 0
+
+    def close(self):
+        self.server.destroy()
+
+    def _admit(self, r: Request):
+        with torch.cuda.stream(self.copy_stream):
+            r.order = pndf.pndf_sort_queries(self.maps[r.map], r.queries, stream=self.copy_stream)
+            r.D = torch.empty(r.n, dtype=torch.float32, device=self.device)
+            r.ready = torch.cuda.Event()
+            r.ready.record(self.copy_stream)
+        r.order.record_stream(self.step_stream)
+        r.D.record_stream(self.step_stream)
+        r.queries.record_stream(self.copy_stream)
+        r.queries.record_stream(self.step_stream)
+
+    def _form_step(self, active: deque):
+        segs, finishing = [], []
+        total = 0
+        while active and total < self.step_queries and len(segs) < self.max_segments:
+            r = active[0]
+            if not r.waited:
+                self.step_stream.wait_event(r.ready)
+                r.waited = True
+            take = min(r.n - r.next, self.step_queries - total)
+            segs.append((r.map, r.queries, r.order, r.D, None, r.next, take))
+            r.next += take
+            total += take
+            if r.next == r.n:
+                finishing.append(active.popleft())
+        return segs, finishing
+
+    def run(self, requests, realtime: bool = True):
+        """Serve `requests` (arrival times relative to the start of the run;
+        with realtime=False every request is present at time 0).  Returns the
+        summary dict; each request gets `latency`, `D` and `done`."""
+        reqs = sorted(requests, key=lambda r: r.arrival)
+        for r in reqs:
+            r.next, r.waited, r.done, r.latency = 0, False, None, math.nan
+        torch.cuda.synchronize(self.device)
+        t0_ev = torch.cuda.Event(enable_timing=True)
+        t0_ev.record(self.step_stream)
+        t0_ev.synchronize()
+        t0 = time.perf_counter()
+        pending = deque(reqs)
+        active: deque = deque()
+        inflight: deque = deque()
+        used = 0
+        while pending or active or inflight:
+            now = time.perf_counter() - t0
+            progressed = False
+            while pending and (not realtime or pending[0].arrival <= now) and \
+                    (used + pending[0].n * BYTES_PER_QUERY <= self.budget or (not active and not inflight)):
+                r = pending.popleft()
+                self._admit(r)
+                active.append(r)
+                used += r.n * BYTES_PER_QUERY
+                progressed = True
+            if active and len(inflight) < 2:
+                segs, fin = self._form_step(active)
+                ev = torch.cuda.Event(enable_timing=True)
+                pndf.pndf_server_step(self.server, segs, stream=self.step_stream, ev_done=ev)
+                self.steps += 1
+                inflight.append((ev, fin, segs))
+                continue
+            while inflight and inflight[0][0].query():
+                ev, fin, _ = inflight.popleft()
+                for r in fin:
+                    r.done = ev
+                    used -= r.n * BYTES_PER_QUERY
+                progressed = True
+            if progressed:
+                continue
+            if inflight and (not pending or not realtime or pending[0].arrival > now + 2e-4 or
+                             used + pending[0].n * BYTES_PER_QUERY > self.budget):
+                inflight[0][0].synchronize()
+            elif pending and realtime:
+                time.sleep(max(0.0, min(pending[0].arrival - (time.perf_counter() - t0), 5e-4)))
+        torch.cuda.synchronize(self.device)
+        for r in reqs:
+            r.latency = t0_ev.elapsed_time(r.done) / 1e3 - r.arrival
+        t_last = max(t0_ev.elapsed_time(r.done) / 1e3 for r in reqs)
+        return summarize(reqs, min(r.arrival for r in reqs), t_last)
+
+
+def run_plain(maps, requests, realtime: bool = True):
+    """Baseline: each batch launched alone (pndf_eval_batch) in arrival order."""
+    reqs = sorted(requests, key=lambda r: r.arrival)
+    dev = maps[0].device
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.synchronize(dev)
+    t0_ev = torch.cuda.Event(enable_timing=True)
+    t0_ev.record(stream)
+    t0_ev.synchronize()
+    t0 = time.perf_counter()
+    for r in reqs:
+        if realtime:
+            wait = r.arrival - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+        with torch.cuda.stream(stream):
+            r.D = torch.empty(r.n, dtype=torch.float32, device=dev)
+            pndf.pndf_eval_batch(maps[r.map], r.queries, out=r.D, stream=stream)
+            r.done = torch.cuda.Event(enable_timing=True)
+            r.done.record(stream)
+    torch.cuda.synchronize(dev)
+    for r in reqs:
+        r.latency = t0_ev.elapsed_time(r.done) / 1e3 - r.arrival
+    t_last = max(t0_ev.elapsed_time(r.done) / 1e3 for r in reqs)
+    return summarize(reqs, min(r.arrival for r in reqs), t_last)
+
+
+def poisson_arrivals(n: int, rate: float, seed: int):
+    g = torch.Generator().manual_seed(seed)
+    gaps = -torch.log(1.0 - torch.rand(n, generator=g, dtype=torch.float64)) / rate
+    return torch.cumsum(gaps, 0).tolist()
+
+
+@dataclass
+class TuneResult:
+    step_queries: int
+    ctas_per_sm: int
+    warps_per_cta: int
+    p99_ms: float
+    queries_per_s: float
+    table: list = field(default_factory=list)
+
+
+def autotune(maps, sample, arrivals=None, step_candidates=(1 << 16, 1 << 18, 1 << 20, 1 << 22),
+             cta_candidates=(0,), warp_candidates=(8, 4)):
+    """Pick step size and launch shape for the served path on a sample of
+    requests.  With `arrivals` (a Poisson stream at the target load) the
+    candidate with the lowest p99 latency wins (ties broken by throughput);
+    without, the highest saturated throughput wins."""
+    best = None
+    table = []
+    for ctas in cta_candidates:
+        for warps in warp_candidates:
+            for step in step_candidates:
+                b = ContinuousBatcher(maps, step_queries=step, warps_per_cta=warps, ctas_per_sm=ctas)
+                b.run(sample, realtime=False)  # warm
+                if arrivals is not None:
+                    for r, a in zip(sample, arrivals):
+                        r.arrival = a
+                s = b.run(sample, realtime=arrivals is not None)
+                b.close()
+                table.append((step, ctas, warps, s["p99_ms"], s["queries_per_s"]))
+                key = (s["p99_ms"], -s["queries_per_s"]) if arrivals is not None else (-s["queries_per_s"],)
+                if best is None or key < best[0]:
+                    best = (key, TuneResult(step, ctas, warps, s["p99_ms"], s["queries_per_s"]))
+    for r in sample:
+        r.arrival = 0.0
+    out = best[1]
+    out.table = table
+    return out

@@ -326,3 +326,106 @@ BUMPS_256 = dict(n=256, queries=4096, mix=QueryMix(sigma=(4.0, 4.0)), seed=1)
 SCRATCH_2048 = dict(n=2048, queries=1 << 20, mix=QueryMix(sigma=(1.0, 64.0), aspect=(1.0, 4.0), frac_near=0.7), seed=2)
 FLAKE_8192 = dict(n=8192, queries=1 << 22, mix=QueryMix(sigma=(1.0, 512.0), frac_near=0.7), seed=3)
 MIXED_16384 = dict(n=16384, queries=1 << 23, mix=QueryMix(sigma=(1.0, 1024.0), frac_near=0.7), seed=5)
+
+
+# ---------------------------------------------------------------------------
+# camera-driven queries (serving workload)
+# ---------------------------------------------------------------------------
+
+def camera_queries(n_map: int, nq: int, seed: int, tilt_deg=(0.0, 75.0), dist=(0.3, 3.0), fov_deg=40.0,
+                   image=1024, device="cpu") -> torch.Tensor:
+    """(nq, 8) float32 CPU queries seen by a seeded pinhole camera over the
+    textured plane z = 0 (the map spans the world square [0, 1]^2, texel units
+    = world * n_map).
+
+    The camera looks at a random point of the map from distance log-U(dist)
+    with tilt U(tilt_deg) from the plane's normal; nq random pixels of an
+    image x image view are traced.  A pixel's footprint covariance is
+    Sigma = J J^T with J the exact ray differentials of the plane hit point
+    (texels per pixel), scaled down where needed so 4 sigma <= n_map / 2.  The
+    query normal is the xy part of the half vector between a random light
+    direction (uniform on the upper hemisphere) and the view direction.
+    Per-pixel draws come from a generator on `device` (the camera itself from
+    a CPU generator), so large batches can be made on the GPU.
+    """
+    g = _cpu_gen(seed, 60)
+    tilt = math.radians(float(_u(g, 1, *tilt_deg)))
+    yaw = float(_u(g, 1, 0.0, 2 * math.pi))
+    d0 = float(_log_u(g, 1, *dist))
+    target = torch.stack([_u(g, 1, 0.2, 0.8), _u(g, 1, 0.2, 0.8), torch.zeros(1, dtype=torch.float64)]).squeeze(1)
+    back = torch.tensor([math.sin(tilt) * math.cos(yaw), math.sin(tilt) * math.sin(yaw), math.cos(tilt)],
+                        dtype=torch.float64)
+    cam = target + d0 * back
+    fwd = -back
+    up0 = torch.tensor([0.0, 0.0, 1.0], dtype=torch.float64) if abs(math.cos(tilt)) < 0.999 else \
+        torch.tensor([math.cos(yaw), math.sin(yaw), 0.0], dtype=torch.float64)
+    right = torch.linalg.cross(fwd, up0)
+    right = right / torch.linalg.vector_norm(right)
+    up = torch.linalg.cross(right, fwd)
+    half = math.tan(math.radians(fov_deg) / 2)
+    px = 2.0 * half / image  # image-plane step per pixel at unit distance
+    dev = torch.device(device)
+    gd = _dev_gen(seed, 61, dev)
+    cam, fwd, right, up = (v.to(dev) for v in (cam, fwd, right, up))
+
+    def ud(n, lo, hi):
+        return lo + (hi - lo) * torch.rand(n, generator=gd, dtype=torch.float64, device=dev)
+
+    out = []
+    need = nq
+    while need > 0:
+        m = int(need * 1.3) + 16
+        a = ud(m, -half, half)
+        b = ud(m, -half, half)
+        d = fwd[None] + a[:, None] * right[None] + b[:, None] * up[None]
+        ok = d[:, 2] < -1e-6
+        a, b, d = a[ok], b[ok], d[ok]
+        t = -cam[2] / d[:, 2]
+        hit = cam[None] + t[:, None] * d
+        # exact differentials of the plane hit point w.r.t. one pixel step
+        J = []
+        for axis in (right, up):
+            dd = px * axis
+            dt = -t * dd[2] / d[:, 2]
+            J.append((t[:, None] * dd[None, :2] + dt[:, None] * d[:, :2]) * n_map)
+        Ja, Jb = J  # columns of J (texels per pixel)
+        sxx = Ja[:, 0] ** 2 + Jb[:, 0] ** 2
+        syy = Ja[:, 1] ** 2 + Jb[:, 1] ** 2
+        sxy = Ja[:, 0] * Ja[:, 1] + Jb[:, 0] * Jb[:, 1]
+        # largest standard deviation; cap 4 sigma at n_map / 2
+        tr, det = sxx + syy, sxx * syy - sxy * sxy
+        lmax = 0.5 * tr + torch.sqrt(torch.clamp(0.25 * tr * tr - det, min=0.0))
+        cap = (n_map / 8.0) ** 2
+        scale = torch.clamp(cap / lmax, max=1.0)
+        sxx, syy, sxy = sxx * scale, syy * scale, sxy * scale
+        # light uniform on the hemisphere, view = towards the camera
+        z = ud(a.numel(), 0.0, 1.0)
+        ph = ud(a.numel(), 0.0, 2 * math.pi)
+        r = torch.sqrt(1 - z * z)
+        light = torch.stack([r * torch.cos(ph), r * torch.sin(ph), z], 1)
+        view = -d / torch.linalg.vector_norm(d, dim=1, keepdim=True)
+        h = light + view
+        h = h / torch.linalg.vector_norm(h, dim=1, keepdim=True).clamp(min=1e-12)
+        q = torch.stack([hit[:, 0] * n_map, hit[:, 1] * n_map, sxx, sxy, syy, h[:, 0], h[:, 1],
+                         torch.zeros_like(sxx)], 1)
+        out.append(q)
+        need -= q.shape[0]
+    return torch.cat(out)[:nq].to(torch.float32).contiguous()
+
+
+def serving_maps(device="cpu"):
+    """The four resident maps of the serving workload: 1024^2 bumps, 2048^2
+    scratches, 4096^2 and 8192^2 flakes (fp32 (s, t))."""
+    return [bumps_map(n=1024, n_bumps=1024, seed=11, device=device),
+            scratch_map(n=2048, n_grooves=2000, seed=12, device=device),
+            flake_map(n=4096, n_cells=50_000, seed=13, device=device),
+            flake_map(n=8192, n_cells=200_000, seed=14, device=device)]
+
+
+def serving_batches(n_batches: int, seed: int, sizes=(1000, 1_000_000)):
+    """(map index, batch size, camera seed) per batch: size log-uniform in
+    `sizes`, map uniform over the four serving maps."""
+    g = _cpu_gen(seed, 70)
+    n = torch.exp(_u(g, n_batches, math.log(sizes[0]), math.log(sizes[1]))).round().long()
+    maps = torch.randint(0, 4, (n_batches,), generator=g)
+    return [(int(maps[k]), int(n[k]), seed * 100_000 + k) for k in range(n_batches)]

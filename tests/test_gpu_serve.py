@@ -1,0 +1,103 @@
+"""Serving: continuous batching over several resident hierarchies.
+
+Each request's densities must be the same alone (pndf_eval_batch on its map)
+and in the mix (sliced across steps, sharing steps with other requests and
+maps): one warp evaluates a query with a fixed order, so equality is bitwise.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2505_08985_gb300 import synth
+from parity import check_pndf
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_08985_gb300 import pndf
+    return pndf
+
+
+@pytest.fixture(scope="module")
+def maps_and_requests(P):
+    from paper_2505_08985_gb300 import serve
+    sts = [synth.bumps_map(n=256, n_bumps=40, seed=21, device=DEV),
+           synth.scratch_map(n=512, n_grooves=120, seed=22, device=DEV),
+           synth.flake_normals(1024, 3000, seed=23, device=DEV)]
+    rng = np.random.default_rng(5)
+    reqs = []
+    for k in range(40):
+        m = int(rng.integers(0, 3))
+        n = int(np.exp(rng.uniform(np.log(50), np.log(30000))))
+        q = synth.camera_queries(sts[m].shape[0], n, seed=1000 + k, device=DEV)
+        reqs.append(serve.Request(rid=k, map=m, queries=q, arrival=0.0))
+    return sts, reqs
+
+
+def test_served_equals_alone(P, maps_and_requests):
+    from paper_2505_08985_gb300 import serve
+    sts, reqs = maps_and_requests
+    hs = [P.pndf_build_hierarchy(st, bounds_fmt=P.PNDF_BOUNDS_F16_OUTWARD) for st in sts]
+    alone = [P.pndf_eval_batch(hs[r.map], r.queries).cpu() for r in reqs]
+    b = serve.ContinuousBatcher(hs, step_queries=20000, max_segments=64)
+    s = b.run(reqs, realtime=False)
+    assert b.steps >= 5  # requests really were sliced across and shared steps
+    for r, a in zip(reqs, alone):
+        assert torch.equal(r.D.cpu(), a), r.rid
+    assert s["requests"] == len(reqs) and s["queries"] == sum(r.n for r in reqs)
+    # Poisson arrivals in real time give the same results
+    times = serve.poisson_arrivals(len(reqs), rate=2000.0, seed=3)
+    for r, t in zip(reqs, times):
+        r.arrival = t
+    s2 = b.run(reqs, realtime=True)
+    for r, a in zip(reqs, alone):
+        assert torch.equal(r.D.cpu(), a), r.rid
+    assert np.isfinite(s2["p99_ms"]) and s2["p99_ms"] >= s2["p50_ms"] >= 0
+    b.close()
+    # the plain per-batch path agrees too
+    sp = serve.run_plain(hs, reqs, realtime=False)
+    for r, a in zip(reqs, alone):
+        assert torch.equal(r.D.cpu(), a), r.rid
+    assert sp["requests"] == len(reqs)
+    for h in hs:
+        h.free()
+
+
+def test_served_matches_oracle(P, maps_and_requests):
+    from paper_2505_08985_gb300 import serve
+    sts, reqs = maps_and_requests
+    hs = [P.pndf_build_hierarchy(st, bounds_fmt=P.PNDF_BOUNDS_F16_OUTWARD) for st in sts]
+    sub = [r for r in reqs if r.n < 3000][:6]
+    b = serve.ContinuousBatcher(hs, step_queries=4096)
+    b.run(sub, realtime=False)
+    b.close()
+    for r in sub:
+        ref = oracle.pndf(sts[r.map].cpu(), r.queries.cpu())
+        check_pndf(r.D.cpu().double().numpy(), ref, label=f"served request {r.rid}")
+    for h in hs:
+        h.free()
+
+
+def test_server_rejects_mixed_formats(P):
+    a = P.pndf_build_hierarchy(synth.bumps_map(n=64, n_bumps=4, seed=1).to(DEV), bounds_fmt=0)
+    b = P.pndf_build_hierarchy(synth.bumps_map(n=64, n_bumps=4, seed=2).to(DEV), bounds_fmt=1)
+    with pytest.raises(P.PndfError):
+        P.pndf_server_create([a, b])
+    srv = P.pndf_server_create([a], max_segments=4)
+    q = synth.camera_queries(64, 10, seed=1, device=DEV)
+    D = torch.empty(10, device=DEV)
+    with pytest.raises(P.PndfError):  # map index out of range
+        P.pndf_server_step(srv, [(1, q, None, D, None, 0, 10)])
+    P.pndf_server_step(srv, [(0, q, None, D, None, 0, 10)])
+    P.pndf_server_sync(srv)
+    assert torch.equal(D, P.pndf_eval_batch(a, q))
+    srv.destroy()
+    a.free()
+    b.free()
