@@ -101,7 +101,9 @@ typedef enum pndf_eval_mode {
 typedef enum pndf_sort_mode {
     PNDF_SORT_NONE = 0,         /* caller order                                       */
     PNDF_SORT_LEVEL_TILE = 1,   /* entry level (largest first), then centre tile (default) */
-    PNDF_SORT_LEVEL_NORMAL = 2  /* entry level, then query-normal bin                    */
+    PNDF_SORT_LEVEL_NORMAL = 2, /* entry level, then query-normal bin                    */
+    PNDF_SORT_LEVEL_TILE_NORMAL = 3, /* entry level, centre tile, then normal bin          */
+    PNDF_SORT_LEVEL_NORMAL_TILE = 4  /* entry level, normal bin, then centre tile          */
 } pndf_sort_mode;
 #define PNDF_SORT_DEFAULT PNDF_SORT_LEVEL_TILE
 
@@ -160,8 +162,9 @@ size_t pndf_hierarchy_bytes(const pndf_hierarchy *h);
  *   flags_out_dev:  device, nq uint32 (PNDF_QF_* bits) or NULL.
  *   stats_dev:      device, nq pndf_query_stats or NULL.
  * nq = 0 is valid and launches nothing.  Scratch memory for the key sort
- * (about 6 bytes per query plus 64 KiB) is allocated stream-ordered from the
- * device's default memory pool and released on the same stream.
+ * (8 bytes per query plus a histogram of 16 KiB to 1 MiB) is allocated
+ * stream-ordered from the device's default memory pool and released on the
+ * same stream.
  * Errors: INVALID_ARG, OOM, CUDA.  Invalid queries give D = NaN and set
  * PNDF_QF_INVALID (and the device status word).
  */
@@ -184,7 +187,7 @@ pndf_status pndf_eval_batch_ex(const pndf_hierarchy *h, const pndf_query *q_dev,
  * default configuration, for at most pndf_eval_noalloc_max_queries()
  * (1,048,576) queries per call; larger batches return PNDF_ERR_CAPACITY
  * before any work is queued.  The sort scratch is one fixed device array
- * (about 6.4 MB) that every GPU loading the library holds until the process
+ * (about 9.4 MB) that every GPU loading the library holds until the process
  * exits; nothing is allocated or freed.  The first call on each device looks
  * up that array's device address (cudaGetSymbolAddress) with the device
  * current, so make it before any stream capture.  Every call shares the

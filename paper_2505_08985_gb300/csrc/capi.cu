@@ -141,7 +141,7 @@ pndf_status pndf_eval_batch_ex(const pndf_hierarchy *h, const pndf_query *q_dev,
     pndf_eval_config c{PNDF_MODE_HIERARCHY, PNDF_SORT_DEFAULT, 0, 0, nullptr, nullptr};
     if (cfg) c = *cfg;
     if (c.mode != PNDF_MODE_HIERARCHY && c.mode != PNDF_MODE_FLAT) return PNDF_ERR_INVALID_ARG;
-    if (c.sort < 0 || c.sort > 2) return PNDF_ERR_INVALID_ARG;
+    if (c.sort < 0 || c.sort > 4) return PNDF_ERR_INVALID_ARG;
     if (c.warps_per_cta < 0 || c.warps_per_cta > 8 || c.ctas_per_sm < 0) return PNDF_ERR_INVALID_ARG;
     return launch_eval(h, q_dev, nq, D_out_dev, flags_out_dev, stats_dev, c, as_stream(stream));
 }

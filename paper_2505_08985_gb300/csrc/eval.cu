@@ -42,7 +42,8 @@ __device__ unsigned int g_status_eval;
 namespace {
 
 constexpr int kStackCap = 1024;    // DFS stack entries per warp (bound: 48 per level + 80)
-constexpr int kKeyBins = 16 * 1024;  // 16 entry levels x 32 x 32 sub-keys
+constexpr int kMaxSubBits = 14;                   // sub-key bits below the 4 entry-level bits
+constexpr int kKeyBins = 1 << (4 + kMaxSubBits);  // largest histogram (2^18 bins)
 #ifndef PNDF_TRAVERSE_MIN_CTAS
 #define PNDF_TRAVERSE_MIN_CTAS 4     // 4 x 256 threads per SM at <= 64 registers, no spills
 #endif
@@ -609,73 +610,134 @@ __global__ void __launch_bounds__(256, PNDF_TRAVERSE_MIN_CTAS) traverse_kernel(M
 
 // ---- query keying and counting sort ----
 
-// Sort key: entry level (largest footprints first), then a 32 x 32 Morton
-// sub-key: the footprint centre's tile (sort mode 1) or the query normal's
-// bin over [-0.4, 0.4]^2 (sort mode 2).  Grouping similar normals makes the
-// warps in flight visit the same leaf blocks (those whose normal boxes hold
-// m), so they share L2 lines.
-__global__ void key_hist(MapDesc d, const pndf_query *__restrict__ qs, int64_t nq, int mode,
-                         uint16_t *__restrict__ keys, uint32_t *__restrict__ hist)
+// Sort key: entry level (largest footprints first, 4 bits), then a sub-key of
+// `sub` bits (6..14, more for larger batches): the footprint centre's tile
+// (mode 1), the query normal's bin over [-0.4, 0.4]^2 (mode 2), or both, tile
+// major (mode 3) or normal-bin major (mode 4).  Grouping queries that share a
+// region and a normal makes the warps in flight visit the same nodes and leaf
+// blocks, so they share L1/L2 lines.  The order never changes a result.
+__device__ __forceinline__ uint32_t sort_key(const MapDesc &d, const pndf_query &r, int mode, int sub)
 {
-    extern __shared__ uint32_t h[];
-    for (int i = threadIdx.x; i < kKeyBins; i += blockDim.x) h[i] = 0;
-    __syncthreads();
-    const float inv_n = 32.0f / float(d.n);
+    Query q = make_query(r);
+    if (!q.valid) return 0u;
+    int e = entry_level(q, d.L);
+    int tb, mb;  // bits per axis for the tile and the normal bin
+    if (mode == 1) {
+        tb = sub >> 1;
+        mb = 0;
+    } else if (mode == 2) {
+        tb = 0;
+        mb = sub >> 1;
+    } else {
+        tb = (sub + 2) >> 2;
+        mb = (sub >> 1) - tb;
+    }
+    float ts = float(1 << tb) / float(d.n), ms = float(1 << mb) / 0.8f;
+    uint32_t tx = uint32_t(fminf(fmaxf(r.x * ts, 0.f), float((1 << tb) - 1)));
+    uint32_t ty = uint32_t(fminf(fmaxf(r.y * ts, 0.f), float((1 << tb) - 1)));
+    uint32_t mx = uint32_t(fminf(fmaxf((r.ms + 0.4f) * ms, 0.f), float((1 << mb) - 1)));
+    uint32_t my = uint32_t(fminf(fmaxf((r.mt + 0.4f) * ms, 0.f), float((1 << mb) - 1)));
+    uint32_t t = morton2(tx, ty), m = morton2(mx, my);
+    uint32_t k = mode == 4 ? (m << (2 * tb)) | t : (t << (2 * mb)) | m;
+    return (uint32_t(15 - e) << sub) | k;
+}
+
+// Sub-key bits for a batch of nq queries: about 16 queries per bin on average.
+inline int sort_sub_bits(int64_t nq)
+{
+    int b = 6;
+    while (b < kMaxSubBits && (int64_t(1) << (b + 4 + 2)) * 16 <= nq) b += 2;
+    return b;
+}
+
+__global__ void key_hist(MapDesc d, const pndf_query *__restrict__ qs, int64_t nq, int mode, int sub,
+                         uint32_t *__restrict__ keys, uint32_t *__restrict__ hist)
+{
     for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < nq; k += int64_t(gridDim.x) * blockDim.x) {
-        pndf_query r = qs[k];
-        Query q = make_query(r);
-        int e = q.valid ? entry_level(q, d.L) : 0;
-        float fx, fy;
-        if (mode == 2) {
-            fx = (r.ms + 0.4f) * 40.0f;
-            fy = (r.mt + 0.4f) * 40.0f;
-        } else {
-            fx = r.x * inv_n;
-            fy = r.y * inv_n;
-        }
-        int tx = q.valid ? int(fminf(fmaxf(fx, 0.f), 31.f)) : 0;
-        int ty = q.valid ? int(fminf(fmaxf(fy, 0.f), 31.f)) : 0;
-        uint16_t key = uint16_t(((15 - e) << 10) | morton2(tx, ty));
+        uint32_t key = sort_key(d, qs[k], mode, sub);
         keys[k] = key;
-        atomicAdd(&h[key], 1u);
+        atomicAdd(&hist[key], 1u);
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < kKeyBins; i += blockDim.x)
-        if (h[i]) atomicAdd(&hist[i], h[i]);
 }
 
-// One CTA of 1024 threads: exclusive scan of kKeyBins counts in place.
-__global__ void __launch_bounds__(1024) key_scan(uint32_t *__restrict__ hist)
+// One CTA of 1024 threads: exclusive scan of nbins (a multiple of 4096) counts
+// in place, 4096 bins per round, four consecutive bins per thread.
+__global__ void __launch_bounds__(1024) key_scan(uint32_t *__restrict__ hist, int nbins)
 {
-    constexpr int per = kKeyBins / 1024;
-    __shared__ uint32_t part[1024];
-    uint32_t v[per], sum = 0;
-    for (int i = 0; i < per; ++i) {
-        v[i] = hist[threadIdx.x * per + i];
-        sum += v[i];
-    }
-    part[threadIdx.x] = sum;
+    __shared__ uint32_t warp_tot[32];
+    __shared__ uint32_t carry_s;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry_s = 0;
     __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        uint32_t t = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
+    for (int base = 0; base < nbins; base += 4096) {
+        uint4 v = reinterpret_cast<uint4 *>(hist + base)[threadIdx.x];
+        uint32_t sum = v.x + v.y + v.z + v.w;
+        uint32_t incl = sum;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            uint32_t t = __shfl_up_sync(kFull, incl, off);
+            if (lane >= off) incl += t;
+        }
+        if (lane == 31) warp_tot[warp] = incl;
         __syncthreads();
-        part[threadIdx.x] += t;
+        if (warp == 0) {
+            uint32_t w = warp_tot[lane], wi = w;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                uint32_t t = __shfl_up_sync(kFull, wi, off);
+                if (lane >= off) wi += t;
+            }
+            warp_tot[lane] = wi - w;  // exclusive prefix of warp totals
+        }
         __syncthreads();
-    }
-    uint32_t run = part[threadIdx.x] - sum;
-    for (int i = 0; i < per; ++i) {
-        hist[threadIdx.x * per + i] = run;
-        run += v[i];
+        uint32_t run = carry_s + warp_tot[warp] + incl - sum;
+        uint4 o;
+        o.x = run;
+        o.y = o.x + v.x;
+        o.z = o.y + v.y;
+        o.w = o.z + v.z;
+        reinterpret_cast<uint4 *>(hist + base)[threadIdx.x] = o;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry_s = run + sum;
+        __syncthreads();
     }
 }
 
-__global__ void key_place(const uint16_t *__restrict__ keys, int64_t nq, uint32_t *__restrict__ offsets,
+__global__ void key_place(const uint32_t *__restrict__ keys, int64_t nq, uint32_t *__restrict__ offsets,
                           uint32_t *__restrict__ order)
 {
     for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < nq; k += int64_t(gridDim.x) * blockDim.x) {
         uint32_t pos = atomicAdd(&offsets[keys[k]], 1u);
         order[pos] = uint32_t(k);
     }
+}
+
+// Key, histogram, scan and placement: order receives a permutation of 0..nq-1.
+// scratch: hist (zeroed by the caller, 1 << (4 + sub) bins) and keys (nq).
+cudaError_t sort_launch(const MapDesc &d, const pndf_query *q, int64_t nq, int mode, uint32_t *hist, uint32_t *keys,
+                        uint32_t *order, cudaStream_t s)
+{
+    const int sub = sort_sub_bits(nq);
+    int nbins = 1 << (4 + sub);
+    if (nbins < 4096) nbins = 4096;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t blocks = (nq + 255) / 256;
+    if (blocks > int64_t(sms) * 8) blocks = int64_t(sms) * 8;
+    key_hist<<<unsigned(blocks), 256, 0, s>>>(d, q, nq, mode, sub, keys, hist);
+    key_scan<<<1, 1024, 0, s>>>(hist, nbins);
+    key_place<<<unsigned(blocks), 256, 0, s>>>(keys, nq, hist, order);
+    count_launches(3);
+    return cudaGetLastError();
+}
+
+// Histogram bytes a batch of nq queries needs (a multiple of 16 KiB).
+inline size_t sort_hist_bytes(int64_t nq)
+{
+    size_t bins = size_t(1) << (4 + sort_sub_bits(nq));
+    if (bins < 4096) bins = 4096;
+    return bins * sizeof(uint32_t);
 }
 
 template <int BFMT, int TFMT, bool STATS, bool FLAT>
@@ -729,8 +791,9 @@ pndf_status launch_eval(const pndf_hierarchy *h, const pndf_query *q, int64_t nq
     const MapDesc &d = h->d;
     const bool sort = cfg.sort != 0;
     // scratch: cursor (8 B, padded to 256), key histogram, keys, order
-    size_t off_hist = 256, off_keys = off_hist + kKeyBins * sizeof(uint32_t);
-    size_t off_order = off_keys + ((size_t(nq) * sizeof(uint16_t) + 255) & ~size_t(255));
+    const size_t hist_b = sort_hist_bytes(nq);
+    size_t off_hist = 256, off_keys = off_hist + hist_b;
+    size_t off_order = off_keys + ((size_t(nq) * sizeof(uint32_t) + 255) & ~size_t(255));
     size_t bytes = sort ? off_order + size_t(nq) * sizeof(uint32_t) : 256;
     void *scratch = nullptr;
     if (cudaMallocAsync(&scratch, bytes, s) != cudaSuccess) {
@@ -742,21 +805,9 @@ pndf_status launch_eval(const pndf_hierarchy *h, const pndf_query *q, int64_t nq
     uint32_t *order = nullptr;
     cudaError_t e = cudaMemsetAsync(base, 0, sort ? off_keys : 256, s);
     if (e == cudaSuccess && sort) {
-        auto *hist = reinterpret_cast<uint32_t *>(base + off_hist);
-        auto *keys = reinterpret_cast<uint16_t *>(base + off_keys);
         order = reinterpret_cast<uint32_t *>(base + off_order);
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        int64_t blocks = (nq + 255) / 256;
-        if (blocks > int64_t(sms) * 4) blocks = int64_t(sms) * 4;
-        const size_t hist_smem = kKeyBins * sizeof(uint32_t);
-        cudaFuncSetAttribute(key_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, int(hist_smem));
-        key_hist<<<unsigned(blocks), 256, hist_smem, s>>>(d, q, nq, cfg.sort, keys, hist);
-        key_scan<<<1, 1024, 0, s>>>(hist);
-        key_place<<<unsigned(blocks), 256, 0, s>>>(keys, nq, hist, order);
-        count_launches(3);
-        e = cudaGetLastError();
+        e = sort_launch(d, q, nq, cfg.sort, reinterpret_cast<uint32_t *>(base + off_hist),
+                        reinterpret_cast<uint32_t *>(base + off_keys), order, s);
     }
     if (e == cudaSuccess && cfg.ev_begin) e = cudaEventRecord(static_cast<cudaEvent_t>(cfg.ev_begin), s);
     if (e == cudaSuccess) {
@@ -784,30 +835,17 @@ pndf_status launch_eval(const pndf_hierarchy *h, const pndf_query *q, int64_t nq
 pndf_status launch_sort(const pndf_hierarchy *h, const pndf_query *q, int64_t nq, uint32_t *order, cudaStream_t s)
 {
     if (nq == 0) return PNDF_OK;
-    size_t off_keys = size_t(kKeyBins) * sizeof(uint32_t);
-    size_t bytes = off_keys + ((size_t(nq) * sizeof(uint16_t) + 255) & ~size_t(255));
+    size_t off_keys = sort_hist_bytes(nq);
+    size_t bytes = off_keys + ((size_t(nq) * sizeof(uint32_t) + 255) & ~size_t(255));
     void *scratch = nullptr;
     if (cudaMallocAsync(&scratch, bytes, s) != cudaSuccess) {
         cudaGetLastError();
         return PNDF_ERR_OOM;
     }
     auto *hist = static_cast<uint32_t *>(scratch);
-    auto *keys = reinterpret_cast<uint16_t *>(static_cast<char *>(scratch) + off_keys);
+    auto *keys = reinterpret_cast<uint32_t *>(static_cast<char *>(scratch) + off_keys);
     cudaError_t e = cudaMemsetAsync(hist, 0, off_keys, s);
-    if (e == cudaSuccess) {
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        int64_t blocks = (nq + 255) / 256;
-        if (blocks > int64_t(sms) * 4) blocks = int64_t(sms) * 4;
-        const size_t hist_smem = kKeyBins * sizeof(uint32_t);
-        cudaFuncSetAttribute(key_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, int(hist_smem));
-        key_hist<<<unsigned(blocks), 256, hist_smem, s>>>(h->d, q, nq, PNDF_SORT_DEFAULT, keys, hist);
-        key_scan<<<1, 1024, 0, s>>>(hist);
-        key_place<<<unsigned(blocks), 256, 0, s>>>(keys, nq, hist, order);
-        count_launches(3);
-        e = cudaGetLastError();
-    }
+    if (e == cudaSuccess) e = sort_launch(h->d, q, nq, PNDF_SORT_DEFAULT, hist, keys, order, s);
     cudaError_t ef = cudaFreeAsync(scratch, s);
     return (e == cudaSuccess && ef == cudaSuccess) ? PNDF_OK : PNDF_ERR_CUDA;
 }
@@ -930,7 +968,7 @@ namespace {
 constexpr int64_t kNoallocMaxQueries = int64_t(1) << 20;
 constexpr size_t kNoallocHistOff = 256;
 constexpr size_t kNoallocKeysOff = kNoallocHistOff + size_t(kKeyBins) * sizeof(uint32_t);
-constexpr size_t kNoallocOrderOff = kNoallocKeysOff + size_t(kNoallocMaxQueries) * sizeof(uint16_t);
+constexpr size_t kNoallocOrderOff = kNoallocKeysOff + size_t(kNoallocMaxQueries) * sizeof(uint32_t);
 constexpr size_t kNoallocBytes = kNoallocOrderOff + size_t(kNoallocMaxQueries) * sizeof(uint32_t);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
@@ -972,22 +1010,12 @@ pndf_status launch_eval_noalloc(const pndf_hierarchy *h, const pndf_query *q, in
     char *base = static_cast<char *>(scratch);
     auto *cursor = reinterpret_cast<unsigned long long *>(base);
     auto *hist = reinterpret_cast<uint32_t *>(base + kNoallocHistOff);
-    auto *keys = reinterpret_cast<uint16_t *>(base + kNoallocKeysOff);
+    auto *keys = reinterpret_cast<uint32_t *>(base + kNoallocKeysOff);
     auto *order = reinterpret_cast<uint32_t *>(base + kNoallocOrderOff);
-    cudaError_t e = cudaMemsetAsync(base, 0, kNoallocKeysOff, s);  // cursor and histogram start at zero
+    // cursor and histogram start at zero
+    cudaError_t e = cudaMemsetAsync(base, 0, kNoallocHistOff + sort_hist_bytes(nq), s);
     if (e != cudaSuccess) return PNDF_ERR_CUDA;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int64_t blocks = (nq + 255) / 256;
-    if (blocks > int64_t(sms) * 4) blocks = int64_t(sms) * 4;
-    const size_t hist_smem = kKeyBins * sizeof(uint32_t);
-    cudaFuncSetAttribute(key_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, int(hist_smem));
-    key_hist<<<unsigned(blocks), 256, hist_smem, s>>>(d, q, nq, cfg.sort, keys, hist);
-    key_scan<<<1, 1024, 0, s>>>(hist);
-    key_place<<<unsigned(blocks), 256, 0, s>>>(keys, nq, hist, order);
-    count_launches(3);
-    e = cudaGetLastError();
+    e = sort_launch(d, q, nq, cfg.sort, hist, keys, order, s);
     if (e != cudaSuccess) return PNDF_ERR_CUDA;
     if (d.bounds_fmt == PNDF_BOUNDS_F32)
         e = d.texel_fmt == PNDF_TEXEL_F32X2

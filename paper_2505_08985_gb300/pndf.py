@@ -210,6 +210,8 @@ def _event_handle(ev):
 PNDF_SORT_NONE = 0
 PNDF_SORT_LEVEL_TILE = 1
 PNDF_SORT_LEVEL_NORMAL = 2
+PNDF_SORT_LEVEL_TILE_NORMAL = 3
+PNDF_SORT_LEVEL_NORMAL_TILE = 4
 PNDF_SORT_DEFAULT = PNDF_SORT_LEVEL_TILE
 
 
