@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-batches", type=int, default=2000, help="serving workload size (0 = skip serving)")
     ap.add_argument("--serve-load", type=float, default=0.8, help="offered load, fraction of plain FP32 capacity")
+    ap.add_argument("--mixed-requests", type=int, default=4096,
+                    help="projected-area + P-NDF sample on the 16384^2 FP16 map (0 = skip)")
     return ap.parse_args()
 
 
@@ -261,6 +263,71 @@ def run_reference(args, world, rank):
 
 
 # ---------------------------------------------------------------------------
+# glint + diffuse on the 16384^2 FP16 map: P-NDF and projected area
+# ---------------------------------------------------------------------------
+
+def footprint_triangles(q: torch.Tensor, n: int) -> int:
+    """Triangles whose uv centroid lies in the 4-sigma ellipse and inside the
+    map (the triangles one projected-area request integrates), counted per
+    quad row from the ellipse's x-interval at the two centroid heights."""
+    q = q.double().cpu()
+    tot = 0
+    for x, y, sxx, sxy, syy in q[:, :5].tolist():
+        det = sxx * syy - sxy * sxy
+        ia, ib, ic = syy / det, -sxy / det, sxx / det
+        ry = 4.0 * math.sqrt(syy)
+        j0, j1 = max(0, int(math.floor(y - ry)) - 1), min(n - 2, int(math.ceil(y + ry)))
+        if j0 > j1:
+            continue
+        j = torch.arange(j0, j1 + 1, dtype=torch.float64)
+        for off in (1.0 / 3.0, 2.0 / 3.0):
+            dy = j + off - y
+            disc = (ib * dy) ** 2 - ia * (ic * dy * dy - 16.0)
+            ok = disc >= 0
+            sq = torch.sqrt(torch.clamp(disc, min=0.0))
+            lo = x + (-ib * dy - sq) / ia - off
+            hi = x + (-ib * dy + sq) / ia - off
+            i_lo = torch.clamp(torch.ceil(lo), min=0)
+            i_hi = torch.clamp(torch.floor(hi), max=n - 2)
+            cnt = torch.clamp(i_hi - i_lo + 1, min=0)
+            tot += int(cnt[ok].sum())
+    return tot
+
+
+def run_mixed(args, dev):
+    from paper_2505_08985_gb300 import pndf
+
+    cfg = synth.MIXED_16384
+    st = synth.mixed_map(n=cfg["n"], seed=cfg["seed"], device=dev).half()
+    nq = args.mixed_requests
+    q = synth.make_queries(st.float(), 2 * nq, cfg["mix"], cfg["seed"])
+    qa, qp = q[:nq].contiguous(), q[nq:].contiguous()
+    w = synth.hemisphere_dirs(nq, seed=cfg["seed"], device=dev)
+    h = pndf.pndf_build_hierarchy(st, bounds_fmt=pndf.PNDF_BOUNDS_F16_OUTWARD)
+    P = torch.empty(nq, dtype=torch.float32, device=dev)
+    D = torch.empty(nq, dtype=torch.float32, device=dev)
+    pndf.pndf_diffuse_projected_area(h, qa[:256], w[:256], out=P[:256])  # warm
+    pndf.pndf_eval_batch(h, qp, out=D)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record()
+    pndf.pndf_diffuse_projected_area(h, qa, w, out=P)
+    ev[1].record()
+    pndf.pndf_eval_batch(h, qp, out=D)
+    ev[2].record()
+    torch.cuda.synchronize()
+    pa_ms, pn_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    assert torch.isfinite(P).all() and torch.isfinite(D).all()
+    tris = footprint_triangles(qa, cfg["n"])
+    h.free()
+    return {"workload": f"16384^2 binary16 mixed map (scratches + flakes); {nq} projected-area requests and {nq} "
+                        "P-NDF queries, sigma log-U(1, 1024), light uniform on the hemisphere",
+            "projected_area": {"requests_per_s": nq / (pa_ms / 1e3), "ms": pa_ms, "triangles": tris,
+                               "triangles_per_s": tris / (pa_ms / 1e3)},
+            "pndf": {"queries_per_s": nq / (pn_ms / 1e3), "ms": pn_ms}}
+
+
+# ---------------------------------------------------------------------------
 # serving: four resident maps, Poisson stream of camera batches
 # ---------------------------------------------------------------------------
 
@@ -438,13 +505,17 @@ def run_gpu(args, world, rank, local):
         "clocks": clocks,
     }
 
-    if args.serve_batches > 0:
+    if args.serve_batches > 0 or args.mixed_requests > 0:
         del st, q, D, st_h, q_h, D_h, st_d
         torch.cuda.empty_cache()
+    if args.mixed_requests > 0:
+        line["glint_diffuse_16384"] = run_mixed(args, dev)
+        torch.cuda.empty_cache()
+    if args.serve_batches > 0:
         line["serving"] = run_serving(args, dev)
         line["serving"]["note"] = "per GPU (each rank serves its own replica of the stream)"
-        if rank == 0 and world == 1 and not args.no_cpu_baseline:
-            st, q = make_workload(args, dev, rank)
+    if (args.serve_batches > 0 or args.mixed_requests > 0) and rank == 0 and world == 1 and not args.no_cpu_baseline:
+        st, q = make_workload(args, dev, rank)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle

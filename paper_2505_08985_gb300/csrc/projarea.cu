@@ -256,19 +256,62 @@ __device__ __noinline__ float tri_ratio_d(float2 a, float2 b, float2 c, const Di
     return float(sum / fabs(A2));
 }
 
-// V_T / |cross| for one triangle (vertices a, b, c with z values).
-__device__ __forceinline__ float tri_ratio(float2 a, float za, float2 b, float zb, float2 c, float zc, const Dir &w,
-                                           const GLTable &gl)
+// Squared distance from the origin to segment p -> q.
+__device__ __forceinline__ float seg_dist2(float px, float py, float qx, float qy)
+{
+    float vx = qx - px, vy = qy - py;
+    float L2 = fmaf(vx, vx, vy * vy);
+    float t = L2 > 0.f ? fminf(fmaxf(-fmaf(px, vx, py * vy) / L2, 0.f), 1.f) : 0.f;
+    float dx = fmaf(t, vx, px), dy = fmaf(t, vy, py);
+    return fmaf(dx, dx, dy * dy);
+}
+
+// True when the triangle provably sees nothing of w: in the frame rotated so
+// w_y = 0 all three vertices have m_x < 0 (the visible part there is the
+// half-ellipse (m_x / w_z)^2 + m_y^2 <= 1) and the triangle stays clear of
+// that ellipse (distance > 1 from the origin after scaling m_x by 1 / w_z,
+// with a margin for FP32 rounding).  Alg. 1 drops every edge of such a
+// triangle, so its integral is exactly 0.
+__device__ __forceinline__ bool invisible_and_clear(float2 a, float2 b, float2 c, const Dir &w)
+{
+    float ax = fmaf(w.c, a.x, w.s * a.y), bx = fmaf(w.c, b.x, w.s * b.y), cx = fmaf(w.c, c.x, w.s * c.y);
+    if (!(ax < 0.f && bx < 0.f && cx < 0.f)) return false;
+    float ay = fmaf(-w.s, a.x, w.c * a.y), by = fmaf(-w.s, b.x, w.c * b.y), cy = fmaf(-w.s, c.x, w.c * c.y);
+    float iz = 1.f / w.wz;
+    ax *= iz;
+    bx *= iz;
+    cx *= iz;
+    // the origin must not lie inside the scaled triangle
+    float o0 = dop(bx - ax, -ay, by - ay, -ax), o1 = dop(cx - bx, -by, cy - by, -bx), o2 = dop(ax - cx, -cy, ay - cy, -cx);
+    if ((o0 >= 0.f && o1 >= 0.f && o2 >= 0.f) || (o0 <= 0.f && o1 <= 0.f && o2 <= 0.f)) return false;
+    float d2 = fminf(seg_dist2(ax, ay, bx, by), fminf(seg_dist2(bx, by, cx, cy), seg_dist2(cx, cy, ax, ay)));
+    return d2 > 1.0045f;  // (1 + 2.25e-3)^2
+}
+
+// V_T / |cross| for one triangle in FP32 when that is accurate: returns false
+// when the triangle needs the FP64 path (partially visible, long sliver,
+// collapsed), which the caller defers and batches.
+__device__ __forceinline__ bool tri_ratio_fast(float2 a, float za, float2 b, float zb, float2 c, float zc,
+                                               const Dir &w, float &out)
 {
     float va = fmaf(w.wx, a.x, fmaf(w.wy, a.y, w.wz * za));
     float vb = fmaf(w.wx, b.x, fmaf(w.wy, b.y, w.wz * zb));
     float vc = fmaf(w.wx, c.x, fmaf(w.wy, c.y, w.wz * zc));
-    if (!(va >= 0.f && vb >= 0.f && vc >= 0.f)) return tri_ratio_d(a, b, c, w, gl);
     float2 ab = make_float2(b.x - a.x, b.y - a.y), ac = make_float2(c.x - a.x, c.y - a.y);
     float2 bc = make_float2(c.x - b.x, c.y - b.y);
     float cr = dop(ab.x, ac.y, ab.y, ac.x);
     float P2 = fmaxf(fmaf(ab.x, ab.x, ab.y * ab.y), fmaxf(fmaf(ac.x, ac.x, ac.y * ac.y), fmaf(bc.x, bc.x, bc.y * bc.y)));
-    if (P2 == 0.f) return 0.5f * (w.wz + fmaf(w.wx, a.x, w.wy * a.y) / za);  // all three normals equal
+    if (!(va >= 0.f && vb >= 0.f && vc >= 0.f)) {
+        // partially visible triangles take the FP64 path: when most of a
+        // footprint is shadowed P itself is tiny, and FP32 clipping (roots of
+        // nearly tangent edges, arcs) would dominate its relative error
+        out = 0.f;
+        return invisible_and_clear(a, b, c, w);
+    }
+    if (P2 == 0.f) {  // all three normals equal
+        out = 0.5f * (w.wz + fmaf(w.wx, a.x, w.wy * a.y) / za);
+        return true;
+    }
     // The boundary form below has FP32 error about 1.5 eps P^2 / |cross|.
     if (P2 > 2.0f * fabsf(cr)) {
         if (P2 < 1e-4f) {
@@ -281,9 +324,10 @@ __device__ __forceinline__ float tri_ratio(float2 a, float za, float2 b, float z
             float f0 = fmaf(w.wx, m0.x, w.wy * m0.y) / z0;
             float f1 = fmaf(w.wx, m1.x, w.wy * m1.y) / z1;
             float f2 = fmaf(w.wx, m2.x, w.wy * m2.y) / z2;
-            return 0.5f * w.wz + (f0 + f1 + f2) * (1.f / 6.f);
+            out = 0.5f * w.wz + (f0 + f1 + f2) * (1.f / 6.f);
+            return true;
         }
-        if (P2 > 200.0f * fabsf(cr)) return tri_ratio_d(a, b, c, w, gl);  // long sliver or collapsed
+        if (P2 > 2000.0f * fabsf(cr)) return false;  // long sliver or collapsed: FP64
     }
     // Fully visible: V = w_z A + w_x Wx + w_y Wy, Wx = -oint m~_z dm_y,
     // Wy = oint m~_z dm_x.  With the edge mean of m~_z split into its
@@ -297,7 +341,8 @@ __device__ __forceinline__ float tri_ratio(float2 a, float za, float2 b, float z
     float Wy = -0.5f * detx + (hab * ab.x + hbc * bc.x - hca * ac.x);
     // orientation-following integrals over the signed cross = the
     // counter-clockwise value over |cross|
-    return 0.5f * w.wz + fmaf(w.wx, Wx, w.wy * Wy) / cr;
+    out = 0.5f * w.wz + fmaf(w.wx, Wx, w.wy * Wy) / cr;
+    return true;
 }
 
 struct Req {
@@ -349,6 +394,26 @@ __device__ __forceinline__ float2 texel(const MapDesc &d, int i, int j)
     return __half22float2(__ldg(reinterpret_cast<const __half2 *>(d.texels) + idx));
 }
 
+// Ring of triangles deferred to the FP64 path, per warp: (i << 15) | (j << 1)
+// | tri and the triangle's kernel weight; processed 32 at a time so the slow
+// path runs with every lane busy.
+constexpr int kDefer = 128;
+
+// Lane's deferred triangle (ring slot head + lane): kernel weight times the
+// FP64 value of V_T / |cross| (tri 0 = (u0, u1, u2), tri 1 = (u3, u2, u1)).
+template <int TFMT>
+__device__ __forceinline__ float deferred_value(const MapDesc &d, const Dir &w, const GLTable &gl,
+                                                const uint32_t *dq_id, const float *dq_w, uint32_t head, int lane)
+{
+    uint32_t slot = (head + uint32_t(lane)) & (kDefer - 1);
+    uint32_t id = dq_id[slot];
+    int i = int(id >> 15), j = int((id >> 1) & 0x3fffu), tri = int(id & 1u);
+    float2 a = texel<TFMT>(d, i + tri, j + tri);
+    float2 b = texel<TFMT>(d, i + 1 - tri, j + tri);
+    float2 c = texel<TFMT>(d, i + tri, j + 1 - tri);
+    return dq_w[slot] * tri_ratio_d(a, b, c, w, gl);
+}
+
 __global__ void pa_bands(MapDesc d, const pndf_query *__restrict__ qs, int64_t k0, int cnt, uint32_t *__restrict__ nb)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -393,7 +458,12 @@ __global__ void __launch_bounds__(256) pa_items(MapDesc d, const pndf_query *__r
                                                const uint32_t *__restrict__ off, float2 *__restrict__ part,
                                                unsigned int *__restrict__ cursor, GLTable gl)
 {
-    const int lane = threadIdx.x & 31;
+    __shared__ uint32_t dq_id_s[8][kDefer];
+    __shared__ float dq_w_s[8][kDefer];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t *dq_id = dq_id_s[warp];
+    float *dq_w = dq_w_s[warp];
     const uint32_t total = off[cnt];
     while (true) {
         uint32_t it = 0;
@@ -422,27 +492,70 @@ __global__ void __launch_bounds__(256) pa_items(MapDesc d, const pndf_query *__r
         const int band = int(it - off[t]);
         const int jb0 = q.j0 + band * kBand, jb1 = min(q.j1, jb0 + kBand - 1);
         float s = 0.f, c = 0.f;
+        uint32_t head = 0;
+        int nd = 0;  // deferred triangles waiting in the ring (warp-uniform)
         for (int j = jb0; j <= jb1; ++j) {
             const float dyl = (float(j) - q.y) + (1.f / 3.f), dyu = (float(j) - q.y) + (2.f / 3.f);
             for (int ib = q.i0; ib <= q.i1; ib += 32) {
                 const int i = ib + lane;
-                if (i > q.i1) continue;
-                const float dxl = (float(i) - q.x) + (1.f / 3.f), dxu = (float(i) - q.x) + (2.f / 3.f);
-                const float ql = wq(q, dxl, dyl), qu = wq(q, dxu, dyu);
-                if (ql > kQCut && qu > kQCut) continue;
-                float2 n0 = texel<TFMT>(d, i, j), n1 = texel<TFMT>(d, i + 1, j);
-                float2 n2 = texel<TFMT>(d, i, j + 1), n3 = texel<TFMT>(d, i + 1, j + 1);
-                float z0 = zof(n0), z1 = zof(n1), z2 = zof(n2), z3 = zof(n3);
-                float v[2] = {0.f, 0.f};
-                if (ql <= kQCut) v[0] = q.norm * expf(-0.5f * ql) * tri_ratio(n0, z0, n1, z1, n2, z2, w, gl);
-                if (qu <= kQCut) v[1] = q.norm * expf(-0.5f * qu) * tri_ratio(n3, z3, n2, z2, n1, z1, w, gl);
+                float v[2] = {0.f, 0.f}, kw[2] = {0.f, 0.f};
+                bool dfr[2] = {false, false};
+                if (i <= q.i1) {
+                    const float dxl = (float(i) - q.x) + (1.f / 3.f), dxu = (float(i) - q.x) + (2.f / 3.f);
+                    const float ql = wq(q, dxl, dyl), qu = wq(q, dxu, dyu);
+                    if (ql <= kQCut || qu <= kQCut) {
+                        float2 n0 = texel<TFMT>(d, i, j), n1 = texel<TFMT>(d, i + 1, j);
+                        float2 n2 = texel<TFMT>(d, i, j + 1), n3 = texel<TFMT>(d, i + 1, j + 1);
+                        float z0 = zof(n0), z1 = zof(n1), z2 = zof(n2), z3 = zof(n3);
+                        float r;
+                        if (ql <= kQCut) {
+                            kw[0] = q.norm * expf(-0.5f * ql);
+                            if (tri_ratio_fast(n0, z0, n1, z1, n2, z2, w, r))
+                                v[0] = kw[0] * r;
+                            else
+                                dfr[0] = true;
+                        }
+                        if (qu <= kQCut) {
+                            kw[1] = q.norm * expf(-0.5f * qu);
+                            if (tri_ratio_fast(n3, z3, n2, z2, n1, z1, w, r))
+                                v[1] = kw[1] * r;
+                            else
+                                dfr[1] = true;
+                        }
+                    }
+                }
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
                     float tt = s + v[k];
                     c += fabsf(s) >= fabsf(v[k]) ? (s - tt) + v[k] : (v[k] - tt) + s;
                     s = tt;
+                    // queue the triangles that need the FP64 path
+                    unsigned m = __ballot_sync(kFull, dfr[k]);
+                    if (dfr[k]) {
+                        uint32_t pos = (head + uint32_t(nd) + __popc(m & lt)) & (kDefer - 1);
+                        dq_id[pos] = (uint32_t(i) << 15) | (uint32_t(j) << 1) | uint32_t(k);
+                        dq_w[pos] = kw[k];
+                    }
+                    nd += __popc(m);
+                }
+                __syncwarp();
+                while (nd >= 32) {
+                    float val = deferred_value<TFMT>(d, w, gl, dq_id, dq_w, head, lane);
+                    float tt = s + val;
+                    c += fabsf(s) >= fabsf(val) ? (s - tt) + val : (val - tt) + s;
+                    s = tt;
+                    head += 32;
+                    nd -= 32;
+                    __syncwarp();
                 }
             }
+        }
+        if (nd > 0) {
+            float val = lane < nd ? deferred_value<TFMT>(d, w, gl, dq_id, dq_w, head, lane) : 0.f;
+            float tt = s + val;
+            c += fabsf(s) >= fabsf(val) ? (s - tt) + val : (val - tt) + s;
+            s = tt;
+            __syncwarp();
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
