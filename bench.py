@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--queries", type=int, default=synth.FLAKE_8192["queries"])
-    ap.add_argument("--n", type=int, default=synth.FLAKE_8192["n"])
+    ap.add_argument("--map-size", dest="n", type=int, default=synth.FLAKE_8192["n"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-batches", type=int, default=2000, help="serving workload size (0 = skip serving)")
