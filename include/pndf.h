@@ -254,8 +254,8 @@ pndf_status pndf_sort_queries(const pndf_hierarchy *h, const pndf_query *q_dev, 
  * pull queries from all segments through one work cursor, so requests of
  * different sizes and maps share the GPU.  Each step is a CUDA graph (copy of
  * the segment table from pinned host memory, cursor reset, kernel) replayed
- * with new table contents; two table slots alternate, so the host can queue
- * step k+1 while step k runs.  A query's result does not depend on which
+ * with new table contents; table slots rotate, so the host can queue
+ * several steps while earlier ones run.  A query's result does not depend on which
  * other segments share its step (one warp evaluates it with a fixed order).
  * ------------------------------------------------------------------------- */
 
@@ -276,7 +276,7 @@ typedef struct pndf_server_config {
     int32_t max_segments;   /* segments per step (0 = 1024)                           */
     int32_t warps_per_cta;  /* 0 = 8                                                  */
     int32_t ctas_per_sm;    /* 0 = as many as fit                                     */
-    int32_t reserved;
+    int32_t slots;          /* table slots, 2..8 (0 = 4): steps that can be queued     */
 } pndf_server_config;
 
 /* Create a server over nmaps (1..8) hierarchies on the current device; maps
@@ -288,8 +288,8 @@ pndf_status pndf_server_create(const pndf_hierarchy *const *maps, int32_t nmaps,
 
 /* Queue one step over nsegs segments (host array, copied before return) on
  * stream; ev_done (optional cudaEvent_t) is recorded when the step's kernel
- * completes.  Blocks only if the table slot is still in use by the step
- * before the previous one.  All pointers in the segments must stay valid
+ * completes.  Blocks only if the next table slot is still in use by the step
+ * queued `slots` steps earlier.  All pointers in the segments must stay valid
  * until the step completes.  Errors: INVALID_ARG (bad map index, count,
  * pointers, nsegs > max_segments), CUDA. */
 pndf_status pndf_server_step(pndf_server *srv, const pndf_segment *segs_host, int32_t nsegs, void *stream,

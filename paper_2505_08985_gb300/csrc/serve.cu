@@ -3,9 +3,9 @@
 // Each step evaluates a list of segments (slices of requests, possibly on
 // different maps) in one persistent kernel launch.  The segment table is
 // written into a pinned host buffer and copied to the device by the step's
-// CUDA graph (copy, cursor reset, kernel), captured once per table slot.  Two
-// slots alternate: writing slot k's host buffer only waits for the step that
-// last used that slot, so one step can be queued while the previous runs.
+// CUDA graph (copy, cursor reset, kernel), captured once per table slot.
+// Slots rotate: writing a slot's host buffer only waits for the step that last
+// used that slot, so several steps can be queued while earlier ones run.
 #include <string.h>
 
 #include <new>
@@ -37,7 +37,9 @@ struct pndf_server {
     int max_segs = 0, warps = 8, ctas = 0;
     MapDesc *maps_dev = nullptr;
     cudaStream_t cap = nullptr;
-    Slot slot[2];
+    static constexpr int kMaxSlots = 8;
+    Slot slot[kMaxSlots];
+    int nslots = 4;
     int next = 0;
 };
 
@@ -48,6 +50,7 @@ void release(pndf_server *s)
     if (!s) return;
     for (Slot &sl : s->slot) {
         if (sl.done) cudaEventSynchronize(sl.done);
+        if (!sl.host && !sl.dev && !sl.exec && !sl.done) continue;
         if (sl.exec) cudaGraphExecDestroy(sl.exec);
         if (sl.done) cudaEventDestroy(sl.done);
         if (sl.dev) cudaFree(sl.dev);
@@ -95,12 +98,14 @@ pndf_status pndf_server_create(const pndf_hierarchy *const *maps, int32_t nmaps,
         if (maps[i]->d.texel_fmt != maps[0]->d.texel_fmt || maps[i]->d.bounds_fmt != maps[0]->d.bounds_fmt)
             return PNDF_ERR_INVALID_ARG;
     }
-    pndf_server_config c{1024, 8, 0, 0};
+    pndf_server_config c{1024, 8, 0, 4};
     if (cfg) {
-        if (cfg->max_segments < 0 || cfg->warps_per_cta < 0 || cfg->warps_per_cta > 8 || cfg->ctas_per_sm < 0)
+        if (cfg->max_segments < 0 || cfg->warps_per_cta < 0 || cfg->warps_per_cta > 8 || cfg->ctas_per_sm < 0 ||
+            cfg->slots < 0 || cfg->slots == 1 || cfg->slots > pndf_server::kMaxSlots)
             return PNDF_ERR_INVALID_ARG;
         if (cfg->max_segments) c.max_segments = cfg->max_segments;
         if (cfg->warps_per_cta) c.warps_per_cta = cfg->warps_per_cta;
+        if (cfg->slots) c.slots = cfg->slots;
         c.ctas_per_sm = cfg->ctas_per_sm;
     }
     if (c.max_segments > (1 << 16)) return PNDF_ERR_INVALID_ARG;
@@ -113,13 +118,14 @@ pndf_status pndf_server_create(const pndf_hierarchy *const *maps, int32_t nmaps,
     s->max_segs = c.max_segments;
     s->warps = c.warps_per_cta;
     s->ctas = c.ctas_per_sm;
+    s->nslots = c.slots;
     MapDesc host_maps[kServeMaxMaps];
     for (int i = 0; i < nmaps; ++i) host_maps[i] = maps[i]->d;
     const size_t tb = table_bytes(s->max_segs);
     bool ok = cudaMalloc(&s->maps_dev, sizeof(MapDesc) * nmaps) == cudaSuccess &&
               cudaMemcpy(s->maps_dev, host_maps, sizeof(MapDesc) * nmaps, cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) == cudaSuccess;
-    for (int k = 0; ok && k < 2; ++k) {
+    for (int k = 0; ok && k < s->nslots; ++k) {
         Slot &sl = s->slot[k];
         ok = cudaMallocHost(&sl.host, tb) == cudaSuccess && cudaMalloc(&sl.dev, tb + 256) == cudaSuccess &&
              cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) == cudaSuccess;
@@ -152,7 +158,7 @@ pndf_status pndf_server_step(pndf_server *s, const pndf_segment *segs, int32_t n
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != s->device) return PNDF_ERR_INVALID_ARG;
     Slot &sl = s->slot[s->next];
-    s->next ^= 1;
+    s->next = (s->next + 1) % s->nslots;
     if (sl.used && cudaEventSynchronize(sl.done) != cudaSuccess) return PNDF_ERR_CUDA;
     uint32_t *hdr = static_cast<uint32_t *>(sl.host);
     hdr[0] = uint32_t(nsegs);

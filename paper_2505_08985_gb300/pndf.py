@@ -57,7 +57,7 @@ class _Segment(ctypes.Structure):
 
 class _ServerConfig(ctypes.Structure):
     _fields_ = [("max_segments", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("ctas_per_sm", ctypes.c_int32), ("slots", ctypes.c_int32)]
 
 
 def _load() -> ctypes.CDLL:
@@ -322,10 +322,11 @@ def pndf_sort_queries(h: Hierarchy, queries: torch.Tensor, order: torch.Tensor |
 class Server:
     """A serving table of resident hierarchies (see pndf_server_create)."""
 
-    def __init__(self, handle: int, maps: list, max_segments: int):
+    def __init__(self, handle: int, maps: list, max_segments: int, slots: int = 4):
         self.handle = handle
         self.maps = list(maps)
         self.max_segments = max_segments
+        self.slots = slots
         self._segs = (_Segment * max_segments)()
 
     def destroy(self):
@@ -340,13 +341,14 @@ class Server:
             pass
 
 
-def pndf_server_create(maps: list, max_segments: int = 1024, warps_per_cta: int = 0, ctas_per_sm: int = 0) -> Server:
+def pndf_server_create(maps: list, max_segments: int = 1024, warps_per_cta: int = 0, ctas_per_sm: int = 0,
+                       slots: int = 0) -> Server:
     arr = (ctypes.c_void_p * len(maps))(*[m.handle for m in maps])
-    cfg = _ServerConfig(int(max_segments), int(warps_per_cta), int(ctas_per_sm), 0)
+    cfg = _ServerConfig(int(max_segments), int(warps_per_cta), int(ctas_per_sm), int(slots))
     h = ctypes.c_void_p()
     with torch.cuda.device(maps[0].device):
         _check("pndf_server_create", LIB.pndf_server_create(arr, len(maps), ctypes.byref(cfg), ctypes.byref(h)))
-    return Server(h.value, maps, int(max_segments))
+    return Server(h.value, maps, int(max_segments), int(slots) or 4)
 
 
 def pndf_server_step(srv: Server, segments: list, stream=None, ev_done=None):

@@ -6,7 +6,7 @@ results, 8 bytes per query) fit a device-memory budget, sorts each once on a
 copy stream, and runs steps: each step takes up to `step_queries` queries from
 the admitted requests in arrival order (a large request spans several steps;
 small ones share a step) and evaluates them in one persistent kernel launch
-replayed from a CUDA graph (pndf_server_step).  Up to two steps are in flight,
+replayed from a CUDA graph (pndf_server_step).  Up to slots - 1 steps are in flight,
 so requests that arrive while the GPU works are admitted and joined to the
 next step as soon as memory frees up.
 
@@ -74,13 +74,14 @@ class ContinuousBatcher:
     """Continuous batching over `maps` (same texel and bounds formats)."""
 
     def __init__(self, maps, step_queries: int = 1 << 20, memory_budget: int = 2 << 30, max_segments: int = 1024,
-                 warps_per_cta: int = 0, ctas_per_sm: int = 0):
+                 warps_per_cta: int = 0, ctas_per_sm: int = 0, slots: int = 4):
         self.maps = list(maps)
         self.device = self.maps[0].device
         self.step_queries = int(step_queries)
         self.budget = int(memory_budget)
         self.server = pndf.pndf_server_create(self.maps, max_segments=max_segments, warps_per_cta=warps_per_cta,
-                                              ctas_per_sm=ctas_per_sm)
+                                              ctas_per_sm=ctas_per_sm, slots=slots)
+        self.max_inflight = max(1, slots - 1)
         self.max_segments = max_segments
         self.copy_stream = torch.cuda.Stream(self.device)
         self.step_stream = torch.cuda.Stream(self.device)
@@ -142,7 +143,7 @@ class ContinuousBatcher:
                 active.append(r)
                 used += r.n * BYTES_PER_QUERY
                 progressed = True
-            if active and len(inflight) < 2:
+            if active and len(inflight) < self.max_inflight:
                 segs, fin = self._form_step(active)
                 ev = torch.cuda.Event(enable_timing=True)
                 pndf.pndf_server_step(self.server, segs, stream=self.step_stream, ev_done=ev)
