@@ -41,7 +41,7 @@ __device__ unsigned int g_status_eval;
 
 namespace {
 
-constexpr int kStackCap = 1024;    // DFS stack entries per warp (bound: 48 per level + 80)
+constexpr int kStackCap = 768;     // DFS stack entries per warp (about 48 per level + 64 in the worst case)
 constexpr int kMaxSubBits = 14;                   // sub-key bits below the 4 entry-level bits
 constexpr int kKeyBins = 1 << (4 + kMaxSubBits);  // largest histogram (2^18 bins)
 #ifndef PNDF_TRAVERSE_MIN_CTAS
@@ -275,6 +275,63 @@ __device__ __forceinline__ void test_triangle(const Query &q, float2 na, float2 
     }
 }
 
+// The hit decision of test_triangle alone: true for an FP32 hit (writes the
+// orientation-signed cross and edge functions e1, e2, so l1 = e1 / cross,
+// l2 = e2 / cross).  Near-singular triangles (FP32 |cross| < 2e-10) are
+// decided, weighted and accumulated here in FP64 and return false.
+template <bool STATS>
+__device__ __forceinline__ bool edge_test(const Query &q, float2 na, float2 nb, float2 nc, int ai, int aj, float dir,
+                                          uint32_t tri_id, Acc &acc, float &cr_o, float &e1_o, float &e2_o)
+{
+    if (STATS) acc.tests++;
+    float lox = fminf(na.x, fminf(nb.x, nc.x)), hix = fmaxf(na.x, fmaxf(nb.x, nc.x));
+    float loy = fminf(na.y, fminf(nb.y, nc.y)), hiy = fmaxf(na.y, fmaxf(nb.y, nc.y));
+    if (q.mx < lox || q.mx > hix || q.my < loy || q.my > hiy) return false;
+    float cr = orient(na.x, na.y, nb.x, nb.y, nc.x, nc.y);
+    if (fabsf(cr) >= kTinyCross) {
+        float e0 = orient(nb.x, nb.y, nc.x, nc.y, q.mx, q.my);
+        float e1 = orient(nc.x, nc.y, na.x, na.y, q.mx, q.my);
+        float e2 = orient(na.x, na.y, nb.x, nb.y, q.mx, q.my);
+        bool hit = cr > 0.f ? (e0 >= 0.f && e1 >= 0.f && e2 >= 0.f) : (e0 <= 0.f && e1 <= 0.f && e2 <= 0.f);
+        cr_o = cr;
+        e1_o = e1;
+        e2_o = e2;
+        return hit;
+    }
+    test_triangle<STATS>(q, na, nb, nc, ai, aj, dir, tri_id, acc);  // FP64 branch
+    if (STATS) acc.tests--;
+    return false;
+}
+
+// Hit ring: FP32 hits waiting for their footprint weight, as (cross, e1, e2,
+// (i << 15) | (j << 1) | tri) with (i, j) the quad.
+constexpr int kHitRing = 64;
+
+// All 32 lanes: lane k < cnt weighs hit k of the ring (the tail of test_triangle).
+template <bool STATS>
+__device__ __forceinline__ void drain_hits(const Query &q, int n, const float4 *hits, uint32_t hh, int cnt, int lane,
+                                           Acc &acc)
+{
+    if (lane < cnt) {
+        float4 h = hits[(hh + uint32_t(lane)) & (kHitRing - 1)];
+        uint32_t pk = __float_as_uint(h.w);
+        int gi = int(pk >> 15), gj = int((pk >> 1) & 0x3fffu), tri = int(pk & 1u);
+        float inv = 1.0f / h.x;
+        float l1 = h.y * inv, l2 = h.z * inv;
+        float dir = tri ? -1.f : 1.f;
+        float dx = (float(gi + tri) - q.x) + dir * l1;
+        float dy = (float(gj + tri) - q.y) + dir * l2;
+        float qq = qform(q, dx, dy);
+        if (qq <= kQCut) {
+            acc_add(acc, q.norm * expf(-0.5f * qq) / fabsf(h.x));
+            if (STATS) {
+                acc.hits++;
+                acc.hash += fmix32(2u * (uint32_t(gj) * uint32_t(n - 1) + uint32_t(gi)) + uint32_t(tri));
+            }
+        }
+    }
+}
+
 // Lanes 0..24 fetch the 5 x 5 texels of leaf block (a, c) (4 x 4 quads).
 template <int TFMT>
 __device__ __forceinline__ float2 leaf_texel(const MapDesc &d, uint32_t a, uint32_t c, int lane)
@@ -316,21 +373,53 @@ __device__ __forceinline__ void test_leaf(const MapDesc &d, const Query &q, uint
 
 // Survivor ring: quads whose level-0 box holds m, packed (i << 16) | j.
 constexpr int kRing = 256;
+// Shared memory per warp: DFS stack, leaf queue (64), survivor ring, hit ring.
+constexpr int kWarpSmemWords = kStackCap + 64 + kRing + 4 * kHitRing;
+
+// Per-warp leaf state: survivor-quad ring and hit ring with their heads/counts.
+struct LeafState {
+    uint32_t *ring;
+    float4 *hits;
+    uint32_t head, hh;
+    int nsq, nh;
+};
 
 // All 32 lanes: lane k tests both triangles of survivor quad k (k < cnt) of
-// the ring: (u0, u1, u2) and (u3, u2, u1), its four texels loaded together.
+// the ring, (u0, u1, u2) and (u3, u2, u1), its four texels loaded together;
+// hits are compacted into the hit ring and weighed 32 at a time.
 template <int TFMT, bool STATS>
-__device__ __forceinline__ void test_quads(const MapDesc &d, const Query &q, const uint32_t *ring, uint32_t head,
-                                           int cnt, int lane, Acc &acc)
+__device__ __forceinline__ void test_quads(const MapDesc &d, const Query &q, LeafState &ls, int cnt, int lane,
+                                           Acc &acc)
 {
+    const unsigned lt = (1u << lane) - 1u;
+    bool h0 = false, h1 = false;
+    float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
     if (lane < cnt) {
-        uint32_t pk = ring[(head + uint32_t(lane)) & (kRing - 1)];
+        uint32_t pk = ls.ring[(ls.head + uint32_t(lane)) & (kRing - 1)];
         int gi = int(pk >> 16), gj = int(pk & 0xffffu);
         float2 n0 = texel<TFMT>(d, gi, gj), n1 = texel<TFMT>(d, gi + 1, gj);
         float2 n2 = texel<TFMT>(d, gi, gj + 1), n3 = texel<TFMT>(d, gi + 1, gj + 1);
         uint32_t id = 2u * (uint32_t(gj) * uint32_t(d.n - 1) + uint32_t(gi));
-        test_triangle<STATS>(q, n0, n1, n2, gi, gj, 1.f, id, acc);
-        test_triangle<STATS>(q, n3, n2, n1, gi + 1, gj + 1, -1.f, id + 1u, acc);
+        uint32_t hp = (uint32_t(gi) << 15) | (uint32_t(gj) << 1);
+        float cr, e1, e2;
+        h0 = edge_test<STATS>(q, n0, n1, n2, gi, gj, 1.f, id, acc, cr, e1, e2);
+        if (h0) v0 = make_float4(cr, e1, e2, __uint_as_float(hp));
+        h1 = edge_test<STATS>(q, n3, n2, n1, gi + 1, gj + 1, -1.f, id + 1u, acc, cr, e1, e2);
+        if (h1) v1 = make_float4(cr, e1, e2, __uint_as_float(hp | 1u));
+    }
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {  // at most 31 + 32 entries queue between drains
+        bool h = t ? h1 : h0;
+        unsigned m = __ballot_sync(kFull, h);
+        if (h) ls.hits[(ls.hh + uint32_t(ls.nh) + __popc(m & lt)) & (kHitRing - 1)] = t ? v1 : v0;
+        ls.nh += __popc(m);
+        __syncwarp();
+        if (ls.nh >= 32) {
+            drain_hits<STATS>(q, d.n, ls.hits, ls.hh, 32, lane, acc);
+            ls.hh += 32;
+            ls.nh -= 32;
+            __syncwarp();
+        }
     }
 }
 
@@ -368,7 +457,7 @@ __device__ __forceinline__ unsigned quad_boxes_hold(const MapDesc &d, uint32_t f
 // test them 32 quads (64 triangles) at a time.
 template <int BFMT, int TFMT, bool STATS>
 __device__ __forceinline__ void process_leaves(const MapDesc &d, const Query &q, const uint32_t *lq, int nleaf,
-                                               uint32_t *ring, uint32_t &head, int &nsq, int lane, Acc &acc)
+                                               LeafState &ls, int lane, Acc &acc)
 {
     const unsigned lt = (1u << lane) - 1u;
     for (int p = 0; p < nleaf; p += 8) {
@@ -394,15 +483,15 @@ __device__ __forceinline__ void process_leaves(const MapDesc &d, const Query &q,
                 uint32_t k = k0 | uint32_t(u);  // Morton index of the quad in its 4 x 4 block
                 uint32_t kx = (k & 1u) | ((k >> 1) & 2u), ky = ((k >> 1) & 1u) | ((k >> 2) & 2u);
                 uint32_t pk = ((a * kLeafQuads + kx) << 16) | (c * kLeafQuads + ky);
-                ring[(head + uint32_t(nsq) + __popc(m & lt)) & (kRing - 1)] = pk;
+                ls.ring[(ls.head + uint32_t(ls.nsq) + __popc(m & lt)) & (kRing - 1)] = pk;
             }
-            nsq += __popc(m);
+            ls.nsq += __popc(m);
         }
         __syncwarp();
-        while (nsq >= 32) {
-            test_quads<TFMT, STATS>(d, q, ring, head, 32, lane, acc);
-            head += 32;
-            nsq -= 32;
+        while (ls.nsq >= 32) {
+            test_quads<TFMT, STATS>(d, q, ls, 32, lane, acc);
+            ls.head += 32;
+            ls.nsq -= 32;
             __syncwarp();
         }
     }
@@ -434,7 +523,7 @@ __device__ __forceinline__ int entry_level(const Query &q, int L)
 
 template <int BFMT, int TFMT, bool STATS, bool FLAT>
 __device__ void eval_one(const MapDesc &d, const pndf_query &rec, int lane, uint32_t *stk, uint32_t *lq,
-                         uint32_t *ring, float &D_out, uint32_t &flags_out, pndf_query_stats *st_out)
+                         uint32_t *ring, float4 *hits, float &D_out, uint32_t &flags_out, pndf_query_stats *st_out)
 {
     Query q = make_query(rec);
     Acc acc = {0.f, 0.f, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
@@ -490,10 +579,9 @@ __device__ void eval_one(const MapDesc &d, const pndf_query &rec, int lane, uint
             __syncwarp();
         }
         bool overflow = false;
-        uint32_t head = 0;
-        int nsq = 0;
+        LeafState ls{ring, hits, 0u, 0u, 0, 0};
         while (true) {
-            process_leaves<BFMT, TFMT, STATS>(d, q, lq, nleaf, ring, head, nsq, lane, acc);
+            process_leaves<BFMT, TFMT, STATS>(d, q, lq, nleaf, ls, lane, acc);
             nleaf = 0;
             if (top == 0) break;
             // pop up to 16 nodes; lane k tests child (k & 3) of popped nodes
@@ -545,7 +633,8 @@ __device__ void eval_one(const MapDesc &d, const pndf_query &rec, int lane, uint
             }
             __syncwarp();
         }
-        if (nsq > 0) test_quads<TFMT, STATS>(d, q, ring, head, nsq, lane, acc);  // nsq < 32 here
+        if (ls.nsq > 0) test_quads<TFMT, STATS>(d, q, ls, ls.nsq, lane, acc);  // nsq < 32 here
+        if (ls.nh > 0) drain_hits<STATS>(q, d.n, ls.hits, ls.hh, ls.nh, lane, acc);  // nh < 32 here
         if (overflow) acc.flags |= PNDF_QF_OVERFLOW;
     }
     // warp reduction (fixed order: deterministic for a given query)
@@ -588,9 +677,10 @@ __global__ void __launch_bounds__(256, PNDF_TRAVERSE_MIN_CTAS) traverse_kernel(M
 {
     extern __shared__ uint32_t smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint32_t *stk = smem + warp * (kStackCap + 64 + kRing);
+    uint32_t *stk = smem + warp * kWarpSmemWords;
     uint32_t *lq = stk + kStackCap;
     uint32_t *ring = lq + 64;
+    float4 *hits = reinterpret_cast<float4 *>(ring + kRing);
     while (true) {
         unsigned long long k = 0;
         if (lane == 0) k = atomicAdd(cursor, 1ull);
@@ -600,7 +690,7 @@ __global__ void __launch_bounds__(256, PNDF_TRAVERSE_MIN_CTAS) traverse_kernel(M
         pndf_query rec = qs[qi];
         float Dv;
         uint32_t fv;
-        eval_one<BFMT, TFMT, STATS, FLAT>(d, rec, lane, stk, lq, ring, Dv, fv, stats ? stats + qi : nullptr);
+        eval_one<BFMT, TFMT, STATS, FLAT>(d, rec, lane, stk, lq, ring, hits, Dv, fv, stats ? stats + qi : nullptr);
         if (lane == 0) {
             D[qi] = Dv;
             if (flags) flags[qi] = fv;
@@ -747,7 +837,7 @@ cudaError_t launch_traverse(const MapDesc &d, const pndf_query *q, const uint32_
 {
     auto kern = traverse_kernel<BFMT, TFMT, STATS, FLAT>;
     int threads = warps * 32;
-    size_t smem = size_t(warps) * (kStackCap + 64 + kRing) * sizeof(uint32_t);
+    size_t smem = size_t(warps) * kWarpSmemWords * sizeof(uint32_t);
     int dev = 0, sms = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -876,9 +966,10 @@ __global__ void __launch_bounds__(256, PNDF_TRAVERSE_MIN_CTAS)
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint32_t *stk = smem + warp * (kStackCap + 64 + kRing);
+    uint32_t *stk = smem + warp * kWarpSmemWords;
     uint32_t *lq = stk + kStackCap;
     uint32_t *ring = lq + 64;
+    float4 *hits = reinterpret_cast<float4 *>(ring + kRing);
     const int nsegs = int(table[0]);
     const uint32_t *prefix = table + 1;
     const uint32_t total = prefix[nsegs];
@@ -901,7 +992,7 @@ __global__ void __launch_bounds__(256, PNDF_TRAVERSE_MIN_CTAS)
         const pndf_query rec = sg.q[qi];
         float Dv;
         uint32_t fv;
-        eval_one<BFMT, TFMT, false, false>(smaps[sg.map], rec, lane, stk, lq, ring, Dv, fv, nullptr);
+        eval_one<BFMT, TFMT, false, false>(smaps[sg.map], rec, lane, stk, lq, ring, hits, Dv, fv, nullptr);
         if (lane == 0) {
             sg.D[qi] = Dv;
             if (sg.flags) sg.flags[qi] = fv;
@@ -915,7 +1006,7 @@ cudaError_t launch_serve_t(const MapDesc *maps, int nmaps, const uint32_t *table
 {
     auto kern = serve_kernel<BFMT, TFMT>;
     int threads = warps * 32;
-    size_t smem = size_t(warps) * (kStackCap + 64 + kRing) * sizeof(uint32_t);
+    size_t smem = size_t(warps) * kWarpSmemWords * sizeof(uint32_t);
     int dev = 0, sms = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
