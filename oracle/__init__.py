@@ -7,6 +7,9 @@ CUDA package and the CUDA package imports nothing from it.
 Functions
 ---------
 pndf(st, queries)          -> D (float64), flags (uint32), hits (int64), hit_hash (uint32)
+cluster_fits(st)           -> ClusterFits: corner normals and residual of every node, Eq. 7-8
+cluster_fit(st, l, I, J)   -> (c (4, 2), e) for one node, or None outside the map
+pndf_cluster(st, queries, tau, fits=None) -> as pndf, with the cluster cut e <= r_x r_y tau
 projarea(st, queries, w)   -> P (float64)
 tri_integral(n0, n1, n2, w) -> integral of max(m~.w, 0)/m~_z over one normal triangle
 
@@ -17,7 +20,8 @@ releases the GIL during each call).
 
 Flag bits (per query): 1 near an edge (1e-6 in normal space), 2 a hit within
 1e-4 of the q = 16 cut, 4 near a zero-area triangle, 8 a hit on a triangle of
-normal-space area < 1e-10, 16 invalid covariance.
+normal-space area < 1e-10, 16 invalid covariance, 32 (cluster cut only) a
+residual or the entry-level radius within 1e-4 (relative) of its threshold.
 """
 
 from __future__ import annotations
@@ -40,7 +44,8 @@ F_NEAR_CUT = 2
 F_DEGENERATE = 4
 F_TINY = 8
 F_INVALID = 16
-F_EXCLUDE = F_NEAR_EDGE | F_NEAR_CUT | F_DEGENERATE | F_INVALID
+F_NEAR_TAU = 32
+F_EXCLUDE = F_NEAR_EDGE | F_NEAR_CUT | F_DEGENERATE | F_INVALID | F_NEAR_TAU
 GL_POINTS = 16
 
 _lock = threading.Lock()
@@ -77,6 +82,36 @@ def default_threads() -> int:
     return max(1, os.cpu_count() or 1)
 
 
+def top_level(N: int) -> int:
+    """Pyramid height: the smallest L >= 2 with 2^L >= N - 1 quads per side."""
+    L = 0
+    while (1 << L) < N - 1:
+        L += 1
+    return max(L, 2)
+
+
+class ClusterFits:
+    """Corner normals c (n_nodes, 8) and residuals e (n_nodes,) of every node
+    at levels 2..L, level by level, row-major (J, I) within a level; e = inf
+    where the node has no cluster (not entirely inside the map)."""
+
+    def __init__(self, N: int):
+        self.N = N
+        self.L = top_level(N)
+        self.offsets = {}
+        off = 0
+        for l in range(2, self.L + 1):
+            self.offsets[l] = off
+            off += (1 << (self.L - l)) ** 2
+        self.c = np.zeros((off, 8), np.float64)
+        self.e = np.full(off, np.inf, np.float64)
+
+    def level(self, l: int):
+        S = 1 << (self.L - l)
+        o = self.offsets[l]
+        return self.c[o:o + S * S].reshape(S, S, 4, 2), self.e[o:o + S * S].reshape(S, S)
+
+
 def _chunks(n, threads, min_chunk=16):
     nchunks = max(1, min(threads * 8, (n + min_chunk - 1) // min_chunk))
     edges = np.linspace(0, n, nchunks + 1).astype(np.int64)
@@ -106,6 +141,13 @@ class Oracle:
         lib.oracle_projarea.restype = None
         lib.oracle_tri_integral.argtypes = [ctypes.c_double] * 9
         lib.oracle_tri_integral.restype = ctypes.c_double
+        lib.oracle_cluster_fit.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp]
+        lib.oracle_cluster_fit.restype = ctypes.c_int
+        lib.oracle_cluster_build.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp]
+        lib.oracle_cluster_build.restype = None
+        lib.oracle_pndf_cluster.argtypes = [dp, ctypes.c_int, dp, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
+                                            dp, dp, dp, u32p, i64p, u32p]
+        lib.oracle_pndf_cluster.restype = None
         self.lib = lib
 
     def pndf(self, st, queries, threads: int | None = None):
@@ -123,6 +165,57 @@ class Oracle:
             lib.oracle_pndf(_ptr(stm, ctypes.c_double), N, _ptr(q, ctypes.c_double), r[0], r[1],
                             _ptr(D, ctypes.c_double), _ptr(flags, ctypes.c_uint32),
                             _ptr(hits, ctypes.c_int64), _ptr(hh, ctypes.c_uint32))
+
+        threads = threads or default_threads()
+        if n:
+            with ThreadPoolExecutor(max_workers=threads) as ex:
+                list(ex.map(run, _chunks(n, threads)))
+        return D, flags, hits, hh
+
+    def cluster_fit(self, st, l: int, I: int, J: int):
+        stm = _as_map(st)
+        c = np.zeros(8, np.float64)
+        e = np.zeros(1, np.float64)
+        ok = self.lib.oracle_cluster_fit(_ptr(stm, ctypes.c_double), stm.shape[0], l, I, J,
+                                         _ptr(c, ctypes.c_double), _ptr(e, ctypes.c_double))
+        return (c.reshape(4, 2), float(e[0])) if ok else None
+
+    def cluster_fits(self, st, threads: int | None = None) -> ClusterFits:
+        stm = _as_map(st)
+        N = stm.shape[0]
+        fits = ClusterFits(N)
+        jobs = []
+        for l in range(2, fits.L + 1):
+            S = 1 << (fits.L - l)
+            jobs += [(l, a, b) for a, b in _chunks(S, threads or default_threads(), 1)]
+        jobs.sort(key=lambda j: -j[0])  # the costly top levels first
+
+        def run(j):
+            self.lib.oracle_cluster_build(_ptr(stm, ctypes.c_double), N, j[0], j[1], j[2],
+                                          _ptr(fits.c, ctypes.c_double), _ptr(fits.e, ctypes.c_double))
+
+        with ThreadPoolExecutor(max_workers=threads or default_threads()) as ex:
+            list(ex.map(run, jobs))
+        return fits
+
+    def pndf_cluster(self, st, queries, tau: float, fits: ClusterFits | None = None, threads: int | None = None):
+        lib = self.lib
+        stm = _as_map(st)
+        q = _as_queries(queries)
+        n = q.shape[0]
+        N = stm.shape[0]
+        fits = fits if fits is not None else self.cluster_fits(stm, threads)
+        assert fits.N == N
+        D = np.zeros(n, np.float64)
+        flags = np.zeros(n, np.uint32)
+        hits = np.zeros(n, np.int64)
+        hh = np.zeros(n, np.uint32)
+
+        def run(r):
+            lib.oracle_pndf_cluster(_ptr(stm, ctypes.c_double), N, _ptr(q, ctypes.c_double), r[0], r[1],
+                                    float(tau), _ptr(fits.c, ctypes.c_double), _ptr(fits.e, ctypes.c_double),
+                                    _ptr(D, ctypes.c_double), _ptr(flags, ctypes.c_uint32),
+                                    _ptr(hits, ctypes.c_int64), _ptr(hh, ctypes.c_uint32))
 
         threads = threads or default_threads()
         if n:
@@ -178,3 +271,15 @@ def projarea(st, queries, omega, threads: int | None = None):
 
 def tri_integral(n0, n1, n2, w) -> float:
     return _get().tri_integral(n0, n1, n2, w)
+
+
+def cluster_fit(st, l: int, I: int, J: int):
+    return _get().cluster_fit(st, l, I, J)
+
+
+def cluster_fits(st, threads: int | None = None) -> ClusterFits:
+    return _get().cluster_fits(st, threads)
+
+
+def pndf_cluster(st, queries, tau: float, fits: ClusterFits | None = None, threads: int | None = None):
+    return _get().pndf_cluster(st, queries, tau, fits, threads)

@@ -444,3 +444,341 @@ void oracle_projarea(const double *st, int N, const double *q, const double *w,
 {
     for (int64_t k = k0; k < k1; ++k) P[k] = projarea_one(st, N, q + 7 * k, w + 3 * k, gl_x, gl_w, ngl);
 }
+
+/* ------------------------------------------------------------------------- */
+/* Cluster hierarchy and tau cut (Sec. 4.3 on mesh clustering, Eq. 7-8,     */
+/* App. A).                                                                  */
+/* ------------------------------------------------------------------------- */
+/*
+ * A node (l, I, J) covers the 2^l x 2^l quads [aI, aI + a) x [aJ, aJ + a),
+ * a = 2^l, and uv square [aI, aI + a] x [aJ, aJ + a].  Its cluster is one
+ * 1 x 1 grid of two triangles split like a quad (anti-diagonal), with corner
+ * normals c00, c10, c01, c11 at uv (aI, aJ), (aI + a, aJ), (aI, aJ + a),
+ * (aI + a, aJ + a): lower (c00, c10, c01), upper (c11, c01, c10).
+ *
+ * Eq. 7: the corner normals minimise
+ *     F(c) = integral over the node of ||n^l(u) - n(u)||^2 / |det J(u)| du,
+ * with n^l piecewise linear on the cluster triangles and n piecewise linear
+ * on the fine triangles.  Every fine triangle lies inside one cluster
+ * triangle, so the integrand is a quadratic on each fine triangle and the
+ * three-point edge-midpoint rule integrates it exactly.  |det J| on a fine
+ * triangle is its |cross|; Eq. 6 clamps the Jacobian at 1e-6, and the weight
+ * 1 / max(|cross|, 1e-6) uses the same clamp so that flat triangles stay
+ * finite.  The residual e^l of Eq. 8 is read as the 2-norm of the weighted
+ * approximation error at the optimum, sqrt(F(c*)) (the printed norm of the
+ * normal-equation residual is zero at the optimum); sqrt(F) has units of
+ * texel^2, like r_x r_y, so tau is dimensionless.
+ *
+ * Readings: clusters exist at levels >= 2 (the 4 x 4-quad block and above)
+ * and only for nodes whose quads all lie inside the map; the cut is taken top
+ * down from the query's entry nodes (the level-l nodes meeting the 4-sigma
+ * box, l = the smallest level >= 2 with 2^l >= max(r_x, r_y), at most the top
+ * level), and a node is a cluster when e^l <= r_x r_y tau with r_x = 4
+ * sqrt(Sigma_xx), r_y = 4 sqrt(Sigma_yy).  The cut depends on the footprint
+ * only, not on m, so D with clusters is the P-NDF of a piecewise-linear
+ * surrogate map; a node that is not cut is replaced by its children, and a
+ * level-2 node that is not cut by its exact triangles (Eq. 5).
+ */
+#define ORACLE_JAC_EPS 1e-6
+#define ORACLE_TAU_EPS 1e-4
+
+enum { OF_NEAR_TAU = 32u };  /* e^l or 2^l within 1e-4 (relative) of its threshold */
+
+static int top_level_of(int N)
+{
+    int L = 0;
+    while ((1 << L) < N - 1) ++L;
+    return L < 2 ? 2 : L;
+}
+
+/* Hat functions of the cluster at normalised local coordinates (s, t). */
+static void cluster_basis(double s, double t, int upper, double phi[4])
+{
+    if (!upper) {
+        phi[0] = 1.0 - s - t; phi[1] = s; phi[2] = t; phi[3] = 0.0;
+    } else {
+        phi[0] = 0.0; phi[1] = 1.0 - t; phi[2] = 1.0 - s; phi[3] = s + t - 1.0;
+    }
+}
+
+/* Solve G x = R (4 x 4, two right-hand sides) by Gaussian elimination with
+ * partial pivoting.  Returns 0 if G is singular. */
+static int solve4(double G[4][4], double R[4][2], double x[4][2])
+{
+    for (int k = 0; k < 4; ++k) {
+        int p = k;
+        for (int r = k + 1; r < 4; ++r)
+            if (fabs(G[r][k]) > fabs(G[p][k])) p = r;
+        if (G[p][k] == 0.0) return 0;
+        if (p != k) {
+            for (int c = 0; c < 4; ++c) { double tmp = G[k][c]; G[k][c] = G[p][c]; G[p][c] = tmp; }
+            for (int c = 0; c < 2; ++c) { double tmp = R[k][c]; R[k][c] = R[p][c]; R[p][c] = tmp; }
+        }
+        for (int r = k + 1; r < 4; ++r) {
+            double f = G[r][k] / G[k][k];
+            for (int c = k; c < 4; ++c) G[r][c] -= f * G[k][c];
+            for (int c = 0; c < 2; ++c) R[r][c] -= f * R[k][c];
+        }
+    }
+    for (int k = 3; k >= 0; --k)
+        for (int c = 0; c < 2; ++c) {
+            double v = R[k][c];
+            for (int j = k + 1; j < 4; ++j) v -= G[k][j] * x[j][c];
+            x[k][c] = v / G[k][k];
+        }
+    return 1;
+}
+
+/* The fine triangles of quad (i, j): uv vertices and normals, Tab. 1 order. */
+static void quad_tri(const double *st, int N, int i, int j, int tri, double uv[3][2], double nv[3][2])
+{
+    static const int lower[3][2] = {{0, 0}, {1, 0}, {0, 1}};
+    static const int upper[3][2] = {{1, 1}, {0, 1}, {1, 0}};
+    const int (*v)[2] = tri ? upper : lower;
+    for (int k = 0; k < 3; ++k) {
+        uv[k][0] = i + v[k][0];
+        uv[k][1] = j + v[k][1];
+        texel(st, N, i + v[k][0], j + v[k][1], nv[k]);
+    }
+}
+
+/* Weighted quadrature points of the fine triangles of node (l, I, J): calls
+ * fn(ctx, s, t, upper, n, weight) for each edge midpoint, with weight =
+ * (area / 3) / max(|cross|, eps). */
+typedef void (*midpoint_fn)(void *ctx, double s, double t, int upper, const double n[2], double w);
+
+static void node_midpoints(const double *st, int N, int l, int I, int J, midpoint_fn fn, void *ctx)
+{
+    int a = 1 << l;
+    for (int j = a * J; j < a * J + a; ++j)
+        for (int i = a * I; i < a * I + a; ++i)
+            for (int tri = 0; tri < 2; ++tri) {
+                double uv[3][2], nv[3][2];
+                quad_tri(st, N, i, j, tri, uv, nv);
+                double cr = fabs(area2(nv[0][0], nv[0][1], nv[1][0], nv[1][1], nv[2][0], nv[2][1]));
+                double w = (0.5 / 3.0) / fmax(cr, ORACLE_JAC_EPS);
+                /* which cluster triangle holds this fine triangle: its centroid */
+                double cs = ((uv[0][0] + uv[1][0] + uv[2][0]) / 3.0 - a * I) / a;
+                double ct = ((uv[0][1] + uv[1][1] + uv[2][1]) / 3.0 - a * J) / a;
+                int upper = cs + ct > 1.0;
+                for (int k = 0; k < 3; ++k) {
+                    int k2 = (k + 1) % 3;
+                    double s = (0.5 * (uv[k][0] + uv[k2][0]) - a * I) / a;
+                    double t = (0.5 * (uv[k][1] + uv[k2][1]) - a * J) / a;
+                    double n[2] = {0.5 * (nv[k][0] + nv[k2][0]), 0.5 * (nv[k][1] + nv[k2][1])};
+                    fn(ctx, s, t, upper, n, w);
+                }
+            }
+}
+
+struct normal_eq { double G[4][4], R[4][2]; };
+
+static void add_normal_eq(void *ctx, double s, double t, int upper, const double n[2], double w)
+{
+    struct normal_eq *ne = (struct normal_eq *)ctx;
+    double phi[4];
+    cluster_basis(s, t, upper, phi);
+    for (int r = 0; r < 4; ++r) {
+        for (int c = 0; c < 4; ++c) ne->G[r][c] += w * phi[r] * phi[c];
+        ne->R[r][0] += w * phi[r] * n[0];
+        ne->R[r][1] += w * phi[r] * n[1];
+    }
+}
+
+struct misfit { const double *c; double F; };
+
+static void add_misfit(void *ctx, double s, double t, int upper, const double n[2], double w)
+{
+    struct misfit *mf = (struct misfit *)ctx;
+    double phi[4];
+    cluster_basis(s, t, upper, phi);
+    double dx = -n[0], dy = -n[1];
+    for (int a = 0; a < 4; ++a) {
+        dx += phi[a] * mf->c[2 * a];
+        dy += phi[a] * mf->c[2 * a + 1];
+    }
+    mf->F += w * (dx * dx + dy * dy);
+}
+
+/*
+ * Eq. 7-8 for node (l, I, J): corner normals c = (c00, c10, c01, c11) as
+ * (s, t) pairs and e = sqrt(F(c)).  Returns 0 (c and e untouched) when the node is
+ * not entirely inside the map or the normal equations are singular.
+ */
+int oracle_cluster_fit(const double *st, int N, int l, int I, int J, double *c, double *e)
+{
+    int a = 1 << l;
+    if (a * (I + 1) > N - 1 || a * (J + 1) > N - 1) return 0;
+    struct normal_eq ne;
+    memset(&ne, 0, sizeof ne);
+    node_midpoints(st, N, l, I, J, add_normal_eq, &ne);
+    double x[4][2];
+    if (!solve4(ne.G, ne.R, x)) return 0;
+    for (int k = 0; k < 4; ++k) { c[2 * k] = x[k][0]; c[2 * k + 1] = x[k][1]; }
+    struct misfit mf = {c, 0.0};
+    node_midpoints(st, N, l, I, J, add_misfit, &mf);
+    *e = sqrt(mf.F);
+    return 1;
+}
+
+/* Pyramid layout of the precomputed fits: levels 2..L, level l holds
+ * S_l x S_l nodes (S_l = 2^(L - l)) row-major by (J, I). */
+static size_t cluster_offset(int L, int l)
+{
+    size_t off = 0;
+    for (int k = 2; k < l; ++k) off += ((size_t)1 << (L - k)) * ((size_t)1 << (L - k));
+    return off;
+}
+
+/* Fits of level-l nodes in rows [J0, J1): c (8 per node) and e (1 per node,
+ * +inf where no cluster exists).  Safe on disjoint row ranges. */
+void oracle_cluster_build(const double *st, int N, int l, int J0, int J1, double *c_all, double *e_all)
+{
+    int L = top_level_of(N);
+    size_t S = (size_t)1 << (L - l), off = cluster_offset(L, l);
+    for (int J = J0; J < J1; ++J)
+        for (size_t I = 0; I < S; ++I) {
+            size_t k = off + (size_t)J * S + I;
+            if (!oracle_cluster_fit(st, N, l, (int)I, J, c_all + 8 * k, e_all + k)) {
+                for (int t = 0; t < 8; ++t) c_all[8 * k + t] = 0.0;
+                e_all[k] = INFINITY;
+            }
+        }
+}
+
+struct cl_query {
+    const double *st, *c_all, *e_all;
+    int N, L;
+    double x, y, ia, ib, ic, norm, mx, my, rx, ry, theta;
+    double D;
+    uint32_t flags, hsum;
+    int64_t nh;
+};
+
+/* Test m against one triangle (uv a, b, c; normals na, nb, nc) whose map
+ * u -> n has Jacobian |cross| / scale^2 (Eq. 4), accumulating Eq. 5. */
+static void cl_triangle(struct cl_query *Q, const double uv[3][2], const double nv[3][2], double scale, uint32_t id)
+{
+    double mx = Q->mx, my = Q->my;
+    double A2 = area2(nv[0][0], nv[0][1], nv[1][0], nv[1][1], nv[2][0], nv[2][1]);
+    double lox = fmin(nv[0][0], fmin(nv[1][0], nv[2][0])) - ORACLE_EDGE_EPS;
+    double hix = fmax(nv[0][0], fmax(nv[1][0], nv[2][0])) + ORACLE_EDGE_EPS;
+    double loy = fmin(nv[0][1], fmin(nv[1][1], nv[2][1])) - ORACLE_EDGE_EPS;
+    double hiy = fmax(nv[0][1], fmax(nv[1][1], nv[2][1])) + ORACLE_EDGE_EPS;
+    if (mx >= lox && mx <= hix && my >= loy && my <= hiy) {
+        double dmin = seg_dist(mx, my, nv[0][0], nv[0][1], nv[1][0], nv[1][1]);
+        dmin = fmin(dmin, seg_dist(mx, my, nv[1][0], nv[1][1], nv[2][0], nv[2][1]));
+        dmin = fmin(dmin, seg_dist(mx, my, nv[2][0], nv[2][1], nv[0][0], nv[0][1]));
+        if (dmin <= ORACLE_EDGE_EPS) Q->flags |= (A2 == 0.0) ? (OF_NEAR_EDGE | OF_DEGENERATE) : OF_NEAR_EDGE;
+    }
+    if (A2 == 0.0) return;
+    double l0 = area2(mx, my, nv[1][0], nv[1][1], nv[2][0], nv[2][1]) / A2;
+    double l1 = area2(nv[0][0], nv[0][1], mx, my, nv[2][0], nv[2][1]) / A2;
+    double l2 = area2(nv[0][0], nv[0][1], nv[1][0], nv[1][1], mx, my) / A2;
+    if (!(l0 >= 0.0 && l1 >= 0.0 && l2 >= 0.0)) return;
+    double ux = uv[0][0] * l0 + uv[1][0] * l1 + uv[2][0] * l2;
+    double uy = uv[0][1] * l0 + uv[1][1] * l1 + uv[2][1] * l2;
+    double dx = ux - Q->x, dy = uy - Q->y;
+    double q = Q->ia * dx * dx + 2.0 * Q->ib * dx * dy + Q->ic * dy * dy;
+    if (fabs(q - ORACLE_QCUT) <= ORACLE_CUT_EPS) Q->flags |= OF_NEAR_CUT;
+    if (q > ORACLE_QCUT) return;
+    double J = fabs(A2) / (scale * scale);
+    if (0.5 * fabs(A2) < ORACLE_TINY_AREA) Q->flags |= OF_TINY;
+    Q->D += Q->norm * exp(-0.5 * q) / J;
+    Q->nh += 1;
+    Q->hsum += fmix32(id);
+}
+
+static int near_threshold(double v, double thr)
+{
+    return fabs(v - thr) <= ORACLE_TAU_EPS * fmax(fabs(thr), 1e-300);
+}
+
+static void cl_visit(struct cl_query *Q, int l, int I, int J)
+{
+    int a = 1 << l, N = Q->N;
+    if (a * I > N - 2 || a * J > N - 2) return;  /* no quad of this node exists */
+    /* no content within the 4-sigma box: contributes k_r = 0 (Eq. 5) */
+    if (a * I > Q->x + Q->rx || a * (I + 1) < Q->x - Q->rx || a * J > Q->y + Q->ry || a * (J + 1) < Q->y - Q->ry)
+        return;
+    size_t S = (size_t)1 << (Q->L - l);
+    size_t k = cluster_offset(Q->L, l) + (size_t)J * S + (size_t)I;
+    double e = Q->e_all[k];
+    if (Q->theta > 0.0 && isfinite(e)) {
+        if (near_threshold(e, Q->theta)) Q->flags |= OF_NEAR_TAU;
+        if (e <= Q->theta) {
+            const double *c = Q->c_all + 8 * k;
+            double ox = a * I, oy = a * J;
+            double uv0[3][2] = {{ox, oy}, {ox + a, oy}, {ox, oy + a}};
+            double nv0[3][2] = {{c[0], c[1]}, {c[2], c[3]}, {c[4], c[5]}};
+            double uv1[3][2] = {{ox + a, oy + a}, {ox, oy + a}, {ox + a, oy}};
+            double nv1[3][2] = {{c[6], c[7]}, {c[4], c[5]}, {c[2], c[3]}};
+            uint32_t id = 0x80000000u | ((uint32_t)l << 27) | ((uint32_t)((size_t)J * S + (size_t)I) << 1);
+            cl_triangle(Q, uv0, nv0, (double)a, id);
+            cl_triangle(Q, uv1, nv1, (double)a, id | 1u);
+            return;
+        }
+    }
+    if (l == 2) {
+        for (int j = a * J; j < a * J + a && j <= N - 2; ++j)
+            for (int i = a * I; i < a * I + a && i <= N - 2; ++i)
+                for (int tri = 0; tri < 2; ++tri) {
+                    double uv[3][2], nv[3][2];
+                    quad_tri(Q->st, N, i, j, tri, uv, nv);
+                    cl_triangle(Q, uv, nv, 1.0, (uint32_t)(2u * ((uint32_t)j * (uint32_t)(N - 1) + (uint32_t)i) + (uint32_t)tri));
+                }
+        return;
+    }
+    for (int dj = 0; dj < 2; ++dj)
+        for (int di = 0; di < 2; ++di) cl_visit(Q, l - 1, 2 * I + di, 2 * J + dj);
+}
+
+static void pndf_cluster_one(const double *st, int N, const double *qq, double tau, const double *c_all,
+                             const double *e_all, double *D_out, uint32_t *flags_out, int64_t *nhits_out,
+                             uint32_t *hash_out)
+{
+    double sxx = qq[2], sxy = qq[3], syy = qq[4];
+    double det = sxx * syy - sxy * sxy;
+    if (!(sxx > 0.0) || !(syy > 0.0) || !(det > 0.0)) {
+        *D_out = NAN;
+        *flags_out = OF_INVALID;
+        *nhits_out = 0;
+        *hash_out = 0;
+        return;
+    }
+    struct cl_query Q;
+    memset(&Q, 0, sizeof Q);
+    Q.st = st; Q.c_all = c_all; Q.e_all = e_all; Q.N = N; Q.L = top_level_of(N);
+    Q.x = qq[0]; Q.y = qq[1]; Q.mx = qq[5]; Q.my = qq[6];
+    Q.ia = syy / det; Q.ib = -sxy / det; Q.ic = sxx / det;
+    Q.norm = 1.0 / (2.0 * M_PI * sqrt(det));
+    Q.rx = 4.0 * sqrt(sxx);
+    Q.ry = 4.0 * sqrt(syy);
+    Q.theta = Q.rx * Q.ry * tau;
+    /* entry level: smallest l >= 2 with 2^l >= max(r_x, r_y), at most L */
+    double r = fmax(Q.rx, Q.ry);
+    int le = 2;
+    while (le < Q.L && (double)(1 << le) < r) ++le;
+    for (int k = 2; k <= Q.L && tau > 0.0; ++k)
+        if (near_threshold(r, (double)(1 << k))) Q.flags |= OF_NEAR_TAU;
+    int a = 1 << le;
+    int I0 = (int)fmax(ceil((Q.x - Q.rx) / a) - 1.0, 0.0), I1 = (int)fmin(floor((Q.x + Q.rx) / a), (double)((1 << (Q.L - le)) - 1));
+    int J0 = (int)fmax(ceil((Q.y - Q.ry) / a) - 1.0, 0.0), J1 = (int)fmin(floor((Q.y + Q.ry) / a), (double)((1 << (Q.L - le)) - 1));
+    for (int J = J0; J <= J1; ++J)
+        for (int I = I0; I <= I1; ++I) cl_visit(&Q, le, I, J);
+    *D_out = Q.D;
+    *flags_out = Q.flags;
+    *nhits_out = Q.nh;
+    *hash_out = Q.hsum;
+}
+
+/* P-NDF with the cluster cut for queries [k0, k1); tau <= 0 cuts nothing
+ * (exact D, summed in traversal order).  c_all / e_all come from
+ * oracle_cluster_build for every level 2..L. */
+void oracle_pndf_cluster(const double *st, int N, const double *q, int64_t k0, int64_t k1, double tau,
+                         const double *c_all, const double *e_all, double *D, uint32_t *flags, int64_t *nhits,
+                         uint32_t *hsum)
+{
+    for (int64_t k = k0; k < k1; ++k)
+        pndf_cluster_one(st, N, q + 7 * k, tau, c_all, e_all, D + k, flags + k, nhits + k, hsum + k);
+}

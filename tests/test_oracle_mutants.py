@@ -7,7 +7,10 @@ swapped when mapping back to uv (Eq. 5), the footprint covariance or
 normalisation wrong, the printed "+" of Eq. 11's line term, the "d_x"
 projection cosine of App. B, a reversed arc, a wrong clip root (Alg. 1) and a
 misplaced per-triangle kernel sample, and a collapsed normal triangle
-treated as a point at its centroid.
+treated as a point at its centroid.  For the cluster hierarchy (Eq. 7-8,
+App. A): the other cluster diagonal or hat functions, an unweighted fit, the
+squared residual, a cluster Jacobian without its 2^(2l) scale, swapped
+barycentric roles or corners, and a cut on the wrong footprint size.
 """
 
 import os
@@ -15,6 +18,7 @@ import os
 import pytest
 
 import oracle
+import test_oracle_cluster as cpins  # noqa: E402
 import test_oracle_pins as pins  # noqa: E402
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "pndf_oracle.c")
@@ -23,6 +27,23 @@ PNDF_PINS = [pins.test_affine_closed_form, pins.test_mass_invariant, pins.test_b
              pins.test_transpose_symmetry]
 AREA_PINS = [pins.test_stokes_matches_area_quadrature, pins.test_projarea_normal_incidence_is_shoelace,
              pins.test_projarea_uv_form, pins.test_projarea_uv_form_collapsed_triangles]
+
+
+def cluster_dense_fit_level3(m):
+    cpins.test_fit_matches_dense_least_squares(m, 3, 1, 1)
+
+
+def cluster_mass_all_cut(m):
+    cpins.test_cluster_mass_invariant(m, 1e9)
+
+
+def cluster_mass_mixed(m):
+    cpins.test_cluster_mass_invariant(m, "mixed")
+
+
+CLUSTER_PINS = [cpins.test_fit_recovers_piecewise_linear_data, cluster_dense_fit_level3, cluster_mass_all_cut,
+                cluster_mass_mixed, cpins.test_cluster_binning_with_anisotropic_cut,
+                cpins.test_cluster_transpose_symmetry, cpins.test_piecewise_linear_map_is_unchanged_by_any_cut]
 
 MUTANTS = {
     "other_diagonal": (
@@ -54,6 +75,27 @@ MUTANTS = {
                                       "(a[1] + b[1] + cc[1]) / 3.0, w);")], AREA_PINS),
     "kernel_at_wrong_centroid": ([("double gx = i + (tri == 0 ? 1.0 / 3.0 : 2.0 / 3.0) - x;",
                                    "double gx = i + (tri == 0 ? 2.0 / 3.0 : 1.0 / 3.0) - x;")], AREA_PINS),
+    # cluster hierarchy (Eq. 7-8, App. A) and the tau cut
+    "cluster_fit_main_diagonal": ([("        phi[0] = 1.0 - s - t; phi[1] = s; phi[2] = t; phi[3] = 0.0;",
+                                    "        phi[0] = 1.0 - s; phi[1] = s - t; phi[2] = 0.0; phi[3] = t;"),
+                                   ("        phi[0] = 0.0; phi[1] = 1.0 - t; phi[2] = 1.0 - s; phi[3] = s + t - 1.0;",
+                                    "        phi[0] = 1.0 - t; phi[1] = 0.0; phi[2] = t - s; phi[3] = s;"),
+                                   ("int upper = cs + ct > 1.0;", "int upper = ct > cs;")], CLUSTER_PINS),
+    "cluster_fit_upper_hats_swapped": ([("phi[0] = 0.0; phi[1] = 1.0 - t; phi[2] = 1.0 - s;",
+                                         "phi[0] = 0.0; phi[1] = 1.0 - s; phi[2] = 1.0 - t;")], CLUSTER_PINS),
+    "cluster_fit_unweighted": ([("double w = (0.5 / 3.0) / fmax(cr, ORACLE_JAC_EPS);", "double w = (0.5 / 3.0);")],
+                               CLUSTER_PINS),
+    "cluster_residual_squared": ([("*e = sqrt(mf.F);", "*e = mf.F;")], CLUSTER_PINS),
+    "cluster_jacobian_unscaled": ([("double J = fabs(A2) / (scale * scale);", "double J = fabs(A2);")], CLUSTER_PINS),
+    "cluster_uv_roles_swapped": ([("double ux = uv[0][0] * l0 + uv[1][0] * l1 + uv[2][0] * l2;",
+                                   "double ux = uv[0][0] * l0 + uv[1][0] * l2 + uv[2][0] * l1;"),
+                                  ("double uy = uv[0][1] * l0 + uv[1][1] * l1 + uv[2][1] * l2;",
+                                   "double uy = uv[0][1] * l0 + uv[1][1] * l2 + uv[2][1] * l1;")], CLUSTER_PINS),
+    "cluster_upper_corners_swapped": ([("double nv1[3][2] = {{c[6], c[7]}, {c[4], c[5]}, {c[2], c[3]}};",
+                                        "double nv1[3][2] = {{c[6], c[7]}, {c[2], c[3]}, {c[4], c[5]}};")],
+                                      CLUSTER_PINS),
+    "cut_on_max_radius": ([("Q.theta = Q.rx * Q.ry * tau;", "Q.theta = fmax(Q.rx, Q.ry) * fmax(Q.rx, Q.ry) * tau;")],
+                          CLUSTER_PINS),
 }
 
 
