@@ -21,7 +21,9 @@ releases the GIL during each call).
 Flag bits (per query): 1 near an edge (1e-6 in normal space), 2 a hit within
 1e-4 of the q = 16 cut, 4 near a zero-area triangle, 8 a hit on a triangle of
 normal-space area < 1e-10, 16 invalid covariance, 32 (cluster cut only) a
-residual or the entry-level radius within 1e-4 (relative) of its threshold.
+node whose normal hull holds m has a residual within 1e-5 (relative) of
+r_x r_y tau, or the entry radius is within 3e-5 of a power of two: FP32
+and FP64 may then take the cut differently.
 """
 
 from __future__ import annotations
@@ -93,7 +95,9 @@ def top_level(N: int) -> int:
 class ClusterFits:
     """Corner normals c (n_nodes, 8) and residuals e (n_nodes,) of every node
     at levels 2..L, level by level, row-major (J, I) within a level; e = inf
-    where the node has no cluster (not entirely inside the map)."""
+    where the node has no cluster (not entirely inside the map).  hull
+    (n_nodes, 4): box of the normals of the node's texels, its cluster corners
+    and its children's hulls."""
 
     def __init__(self, N: int):
         self.N = N
@@ -105,6 +109,7 @@ class ClusterFits:
             off += (1 << (self.L - l)) ** 2
         self.c = np.zeros((off, 8), np.float64)
         self.e = np.full(off, np.inf, np.float64)
+        self.hull = np.zeros((off, 4), np.float64)  # normal hull of each node's pieces
 
     def level(self, l: int):
         S = 1 << (self.L - l)
@@ -145,8 +150,10 @@ class Oracle:
         lib.oracle_cluster_fit.restype = ctypes.c_int
         lib.oracle_cluster_build.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp]
         lib.oracle_cluster_build.restype = None
+        lib.oracle_cluster_hulls.argtypes = [dp, ctypes.c_int, dp, dp, dp]
+        lib.oracle_cluster_hulls.restype = None
         lib.oracle_pndf_cluster.argtypes = [dp, ctypes.c_int, dp, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
-                                            dp, dp, dp, u32p, i64p, u32p]
+                                            dp, dp, dp, dp, u32p, i64p, u32p]
         lib.oracle_pndf_cluster.restype = None
         self.lib = lib
 
@@ -196,6 +203,8 @@ class Oracle:
 
         with ThreadPoolExecutor(max_workers=threads or default_threads()) as ex:
             list(ex.map(run, jobs))
+        self.lib.oracle_cluster_hulls(_ptr(stm, ctypes.c_double), N, _ptr(fits.c, ctypes.c_double),
+                                      _ptr(fits.e, ctypes.c_double), _ptr(fits.hull, ctypes.c_double))
         return fits
 
     def pndf_cluster(self, st, queries, tau: float, fits: ClusterFits | None = None, threads: int | None = None):
@@ -214,7 +223,7 @@ class Oracle:
         def run(r):
             lib.oracle_pndf_cluster(_ptr(stm, ctypes.c_double), N, _ptr(q, ctypes.c_double), r[0], r[1],
                                     float(tau), _ptr(fits.c, ctypes.c_double), _ptr(fits.e, ctypes.c_double),
-                                    _ptr(D, ctypes.c_double), _ptr(flags, ctypes.c_uint32),
+                                    _ptr(fits.hull, ctypes.c_double), _ptr(D, ctypes.c_double), _ptr(flags, ctypes.c_uint32),
                                     _ptr(hits, ctypes.c_int64), _ptr(hh, ctypes.c_uint32))
 
         threads = threads or default_threads()

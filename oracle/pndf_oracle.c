@@ -480,9 +480,10 @@ void oracle_projarea(const double *st, int N, const double *q, const double *w,
  * level-2 node that is not cut by its exact triangles (Eq. 5).
  */
 #define ORACLE_JAC_EPS 1e-6
-#define ORACLE_TAU_EPS 1e-4
+#define ORACLE_TAU_EPS 1e-5     /* residual vs r_x r_y tau (FP32 storage and FP32 threshold) */
+#define ORACLE_RADIUS_EPS 3e-5  /* entry radius vs 2^l (FP32 square root, inflated box) */
 
-enum { OF_NEAR_TAU = 32u };  /* e^l or 2^l within 1e-4 (relative) of its threshold */
+enum { OF_NEAR_TAU = 32u };  /* a cut decision within rounding of its threshold */
 
 static int top_level_of(int N)
 {
@@ -646,8 +647,57 @@ void oracle_cluster_build(const double *st, int N, int l, int J0, int J1, double
         }
 }
 
+/*
+ * Normal hull of every node at levels 2..L (smin, tmin, smax, tmax; 4 per
+ * node, same layout as the fits): the box of the normals of all texels its
+ * quads touch, of its own cluster corners and of its children's hulls.  Any
+ * piece of any cut below a node (exact triangle or cluster triangle) lies in
+ * its hull, so where m is outside it the node's cut decision cannot change D.
+ * Sequential (one call for the whole pyramid).
+ */
+void oracle_cluster_hulls(const double *st, int N, const double *c_all, const double *e_all, double *hull)
+{
+    int L = top_level_of(N);
+    for (int l = 2; l <= L; ++l) {
+        size_t S = (size_t)1 << (L - l), off = cluster_offset(L, l);
+        int a = 1 << l;
+        for (size_t J = 0; J < S; ++J)
+            for (size_t I = 0; I < S; ++I) {
+                size_t k = off + J * S + I;
+                double *h = hull + 4 * k;
+                h[0] = h[1] = INFINITY;
+                h[2] = h[3] = -INFINITY;
+                if (l == 2) {
+                    for (int j = (int)(a * J); j <= (int)(a * J) + a && j <= N - 1; ++j)
+                        for (int i = (int)(a * I); i <= (int)(a * I) + a && i <= N - 1; ++i) {
+                            if (i > N - 1 || j > N - 1) continue;
+                            if ((int)(a * I) > N - 2 || (int)(a * J) > N - 2) continue;  /* node has no quad */
+                            double n[2];
+                            texel(st, N, i, j, n);
+                            h[0] = fmin(h[0], n[0]); h[1] = fmin(h[1], n[1]);
+                            h[2] = fmax(h[2], n[0]); h[3] = fmax(h[3], n[1]);
+                        }
+                } else {
+                    size_t Sc = S * 2, offc = cluster_offset(L, l - 1);
+                    for (int dj = 0; dj < 2; ++dj)
+                        for (int di = 0; di < 2; ++di) {
+                            const double *g = hull + 4 * (offc + (2 * J + dj) * Sc + 2 * I + di);
+                            h[0] = fmin(h[0], g[0]); h[1] = fmin(h[1], g[1]);
+                            h[2] = fmax(h[2], g[2]); h[3] = fmax(h[3], g[3]);
+                        }
+                }
+                if (isfinite(e_all[k]))
+                    for (int t = 0; t < 4; ++t) {
+                        const double *c = c_all + 8 * k + 2 * t;
+                        h[0] = fmin(h[0], c[0]); h[1] = fmin(h[1], c[1]);
+                        h[2] = fmax(h[2], c[0]); h[3] = fmax(h[3], c[1]);
+                    }
+            }
+    }
+}
+
 struct cl_query {
-    const double *st, *c_all, *e_all;
+    const double *st, *c_all, *e_all, *hull;
     int N, L;
     double x, y, ia, ib, ic, norm, mx, my, rx, ry, theta;
     double D;
@@ -689,9 +739,9 @@ static void cl_triangle(struct cl_query *Q, const double uv[3][2], const double 
     Q->hsum += fmix32(id);
 }
 
-static int near_threshold(double v, double thr)
+static int near_threshold(double v, double thr, double eps)
 {
-    return fabs(v - thr) <= ORACLE_TAU_EPS * fmax(fabs(thr), 1e-300);
+    return fabs(v - thr) <= eps * fmax(fabs(thr), 1e-300);
 }
 
 static void cl_visit(struct cl_query *Q, int l, int I, int J)
@@ -705,7 +755,11 @@ static void cl_visit(struct cl_query *Q, int l, int I, int J)
     size_t k = cluster_offset(Q->L, l) + (size_t)J * S + (size_t)I;
     double e = Q->e_all[k];
     if (Q->theta > 0.0 && isfinite(e)) {
-        if (near_threshold(e, Q->theta)) Q->flags |= OF_NEAR_TAU;
+        /* a close call matters only where m can meet the node's pieces */
+        const double *h = Q->hull + 4 * k;
+        if (near_threshold(e, Q->theta, ORACLE_TAU_EPS) && Q->mx >= h[0] - ORACLE_EDGE_EPS && Q->mx <= h[2] + ORACLE_EDGE_EPS &&
+            Q->my >= h[1] - ORACLE_EDGE_EPS && Q->my <= h[3] + ORACLE_EDGE_EPS)
+            Q->flags |= OF_NEAR_TAU;
         if (e <= Q->theta) {
             const double *c = Q->c_all + 8 * k;
             double ox = a * I, oy = a * J;
@@ -734,8 +788,8 @@ static void cl_visit(struct cl_query *Q, int l, int I, int J)
 }
 
 static void pndf_cluster_one(const double *st, int N, const double *qq, double tau, const double *c_all,
-                             const double *e_all, double *D_out, uint32_t *flags_out, int64_t *nhits_out,
-                             uint32_t *hash_out)
+                             const double *e_all, const double *hull, double *D_out, uint32_t *flags_out,
+                             int64_t *nhits_out, uint32_t *hash_out)
 {
     double sxx = qq[2], sxy = qq[3], syy = qq[4];
     double det = sxx * syy - sxy * sxy;
@@ -748,7 +802,7 @@ static void pndf_cluster_one(const double *st, int N, const double *qq, double t
     }
     struct cl_query Q;
     memset(&Q, 0, sizeof Q);
-    Q.st = st; Q.c_all = c_all; Q.e_all = e_all; Q.N = N; Q.L = top_level_of(N);
+    Q.st = st; Q.c_all = c_all; Q.e_all = e_all; Q.hull = hull; Q.N = N; Q.L = top_level_of(N);
     Q.x = qq[0]; Q.y = qq[1]; Q.mx = qq[5]; Q.my = qq[6];
     Q.ia = syy / det; Q.ib = -sxy / det; Q.ic = sxx / det;
     Q.norm = 1.0 / (2.0 * M_PI * sqrt(det));
@@ -760,7 +814,7 @@ static void pndf_cluster_one(const double *st, int N, const double *qq, double t
     int le = 2;
     while (le < Q.L && (double)(1 << le) < r) ++le;
     for (int k = 2; k <= Q.L && tau > 0.0; ++k)
-        if (near_threshold(r, (double)(1 << k))) Q.flags |= OF_NEAR_TAU;
+        if (near_threshold(r, (double)(1 << k), ORACLE_RADIUS_EPS)) Q.flags |= OF_NEAR_TAU;
     int a = 1 << le;
     int I0 = (int)fmax(ceil((Q.x - Q.rx) / a) - 1.0, 0.0), I1 = (int)fmin(floor((Q.x + Q.rx) / a), (double)((1 << (Q.L - le)) - 1));
     int J0 = (int)fmax(ceil((Q.y - Q.ry) / a) - 1.0, 0.0), J1 = (int)fmin(floor((Q.y + Q.ry) / a), (double)((1 << (Q.L - le)) - 1));
@@ -774,11 +828,11 @@ static void pndf_cluster_one(const double *st, int N, const double *qq, double t
 
 /* P-NDF with the cluster cut for queries [k0, k1); tau <= 0 cuts nothing
  * (exact D, summed in traversal order).  c_all / e_all come from
- * oracle_cluster_build for every level 2..L. */
+ * oracle_cluster_build for every level 2..L, hull from oracle_cluster_hulls. */
 void oracle_pndf_cluster(const double *st, int N, const double *q, int64_t k0, int64_t k1, double tau,
-                         const double *c_all, const double *e_all, double *D, uint32_t *flags, int64_t *nhits,
-                         uint32_t *hsum)
+                         const double *c_all, const double *e_all, const double *hull, double *D, uint32_t *flags,
+                         int64_t *nhits, uint32_t *hsum)
 {
     for (int64_t k = k0; k < k1; ++k)
-        pndf_cluster_one(st, N, q + 7 * k, tau, c_all, e_all, D + k, flags + k, nhits + k, hsum + k);
+        pndf_cluster_one(st, N, q + 7 * k, tau, c_all, e_all, hull, D + k, flags + k, nhits + k, hsum + k);
 }

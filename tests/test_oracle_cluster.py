@@ -350,3 +350,29 @@ def test_cluster_transpose_symmetry(oracle_mod):
     DT, flT, hT, _ = oracle_mod.pndf_cluster(stT, qT, tau, fT)
     ok = ((fl | flT) & oracle_mod.F_EXCLUDE) == 0
     np.testing.assert_allclose(DT[ok], D[ok], rtol=1e-9, atol=1e-300)
+
+
+def test_near_tau_flag_covers_every_close_call(oracle_mod):
+    """A cut decision within rounding of its threshold is flagged: with tau
+    set exactly at one visited node's residual, nudging tau by less than the
+    flag's band flips that node, and every query whose D changes is flagged
+    (and some do change)."""
+    st = smooth_map(64, 5)
+    fits = oracle_mod.cluster_fits(st)
+    x, y, sxx, syy = 31.5, 30.75, 9.0, 6.25
+    rx, ry = 4 * math.sqrt(sxx), 4 * math.sqrt(syy)
+    # an entry node (level 4) that is cut at tau = e / (r_x r_y) and not just below
+    e = fits.level(4)[1][1:3, 1:3].ravel()
+    tau = float(np.sort(e[np.isfinite(e)])[1]) / (rx * ry)
+    rng = np.random.default_rng(3)
+    pts = st[12:52, 12:52].reshape(-1, 2)
+    m = pts[rng.integers(0, len(pts), 3000)] + rng.normal(0, 0.01, (3000, 2))
+    q = np.zeros((3000, 7))
+    q[:, 0], q[:, 1], q[:, 2], q[:, 4], q[:, 5], q[:, 6] = x, y, sxx, syy, m[:, 0], m[:, 1]
+    D0, f0, *_ = oracle_mod.pndf_cluster(st, q, tau, fits)
+    changed = np.zeros(len(q), bool)
+    for k in (1 - 5e-6, 1 + 5e-6):
+        D1, *_ = oracle_mod.pndf_cluster(st, q, tau * k, fits)
+        changed |= D1 != D0
+    assert changed.sum() > 20, changed.sum()
+    assert np.all(f0[changed] & oracle_mod.F_NEAR_TAU), np.flatnonzero(changed & ((f0 & oracle_mod.F_NEAR_TAU) == 0))
