@@ -400,7 +400,7 @@ def run_gpu(args, world, rank, local):
     work = {}
     for tag, bf in (("f16", pndf.PNDF_BOUNDS_F16_OUTWARD), ("f32", pndf.PNDF_BOUNDS_F32)):
         h = pndf.pndf_build_hierarchy(st, bounds_fmt=bf)
-        stt = torch.zeros(nq, 8, dtype=torch.int32, device=dev)
+        stt = torch.zeros(nq, pndf.STATS_FIELDS, dtype=torch.int32, device=dev)
         pndf.pndf_eval_batch(h, q, out=D, stats=stt)
         s = stt.to(torch.int64).sum(0).cpu().tolist()
         h.free()

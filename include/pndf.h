@@ -67,6 +67,8 @@ typedef struct pndf_build_params {
     int32_t texel_fmt;   /* pndf_texel_fmt                                        */
     int32_t bounds_fmt;  /* pndf_bounds_fmt                                       */
     int32_t leaf_level;  /* 0 = default (2): stored bottom level, 2^l x 2^l quads */
+    int32_t clusters;    /* 1 = also build the cluster hierarchy (Sec. 4.3, Eq.   */
+                         /* 7-8) used by pndf_eval_config.tau; 0 = none           */
 } pndf_build_params;
 
 /* One P-NDF query, 32 bytes: footprint centre x = (x, y) in texels, the 2x2
@@ -76,7 +78,7 @@ typedef struct pndf_query {
     float x, y, sxx, sxy, syy, ms, mt, pad;
 } pndf_query;
 
-/* Optional per-query counters (32 bytes), written when stats_dev != NULL. */
+/* Optional per-query counters (40 bytes), written when stats_dev != NULL. */
 typedef struct pndf_query_stats {
     uint32_t nodes;        /* hierarchy nodes tested                                 */
     uint32_t leaf_blocks;  /* leaf blocks whose triangles were tested                */
@@ -86,6 +88,8 @@ typedef struct pndf_query_stats {
     uint32_t fp64_tris;    /* triangles evaluated in FP64 (normal area < 1e-10)      */
     uint32_t degenerate;   /* zero-area normal triangles met inside their bbox       */
     uint32_t quads;        /* per-quad (level 0) boxes tested                        */
+    uint32_t cluster_checks; /* nodes whose cluster residual was compared with the cut */
+    uint32_t clusters;     /* cluster nodes whose two triangles were tested          */
 } pndf_query_stats;
 
 /* Per-query flag bits written to flags_out_dev. */
@@ -112,6 +116,11 @@ typedef struct pndf_eval_config {
     int32_t sort;           /* query order before traversal (pndf_sort_mode)          */
     int32_t warps_per_cta;  /* 0 = library default                                   */
     int32_t ctas_per_sm;    /* 0 = as many as fit                                    */
+    float tau;              /* cluster cut (Sec. 4.3): a node whose residual e <=      */
+                            /* r_x r_y tau is evaluated as its two cluster triangles;  */
+                            /* 0 = exact (no cluster).  Needs a hierarchy built with   */
+                            /* clusters = 1, else UNSUPPORTED.  Hierarchy mode only.   */
+    int32_t reserved;       /* must be 0                                              */
     void *ev_begin;         /* optional cudaEvent_t recorded on the stream just before */
     void *ev_end;           /* and just after the traversal kernel (NULL = none)       */
 } pndf_eval_config;
@@ -128,8 +137,16 @@ typedef struct pndf_eval_config {
  * of this call's work).  On success *out owns device memory until
  * pndf_free_hierarchy().
  *   texels_dev: device, N*N texels in params->texel_fmt, row-major.
- * Errors: INVALID_ARG (null pointers, N out of range, unknown formats),
- *         OOM, CUDA.
+ * With params->clusters = 1 the cluster hierarchy of Sec. 4.3 is built too:
+ * every node of level >= 2 whose quads all lie inside the map gets the four
+ * corner normals of a two-triangle cluster (split like a quad) minimising
+ * the Jacobian-weighted L2 error of Eq. 7 (|det J| clamped at 1e-6 as in
+ * Eq. 6), solved in FP64, and its residual e = sqrt of the minimum (the
+ * 2-norm of Eq. 8, units texel^2).  Each node box is widened to hold its own
+ * cluster corners and its children's boxes, so pruning never hides a cluster
+ * triangle; 36 more bytes per node of level >= 2.
+ * Errors: INVALID_ARG (null pointers, N out of range, unknown formats,
+ *         clusters not 0 or 1), UNSUPPORTED (leaf_level), OOM, CUDA.
  */
 pndf_status pndf_build_hierarchy(const void *texels_dev, const pndf_build_params *params,
                                  void *stream, pndf_hierarchy **out);
@@ -146,6 +163,18 @@ void pndf_free_hierarchy(pndf_hierarchy *h);
 
 /* Device bytes held by a hierarchy (texel copy + pyramid). */
 size_t pndf_hierarchy_bytes(const pndf_hierarchy *h);
+
+/* Copy out level l (2 <= l <= L, 2^L >= N-1) of the cluster hierarchy
+ * (Sec. 4.3, Eq. 7-8) for inspection, nodes in row-major order (J, I),
+ * S = 2^(L-l) per side:
+ *   records_dev: device, S*S*8 floats per node (c00.s, c00.t, d10.s, d10.t,
+ *                d01.s, d01.t, d11.s, d11.t), corner normals c = c00 + d;
+ *   residual_dev: device, S*S floats, e (+inf: no cluster, the node has a
+ *                quad outside the map).
+ * Asynchronous on stream.  Errors: INVALID_ARG (level, null or misaligned
+ * pointers), UNSUPPORTED (built without clusters), CUDA. */
+pndf_status pndf_cluster_level(const pndf_hierarchy *h, int32_t level, float *records_dev, float *residual_dev,
+                               void *stream);
 
 /*
  * Batched P-NDF evaluation, Eq. 5 (the exact solution of Eq. 2):

@@ -30,53 +30,6 @@ constexpr int kTileQuadsMax = 64;
 constexpr int kTileTexMax = kTileQuadsMax + 1;
 constexpr int kBuildThreads = 256;
 
-struct Box {
-    float smin, tmin, smax, tmax;
-};
-
-__device__ __forceinline__ Box empty_box()
-{
-    return Box{__int_as_float(0x7f800000), __int_as_float(0x7f800000), __int_as_float(0xff800000),
-               __int_as_float(0xff800000)};
-}
-
-__device__ __forceinline__ void grow(Box &b, const Box &o)
-{
-    b.smin = fminf(b.smin, o.smin);
-    b.tmin = fminf(b.tmin, o.tmin);
-    b.smax = fmaxf(b.smax, o.smax);
-    b.tmax = fmaxf(b.tmax, o.tmax);
-}
-
-template <int BFMT>
-__device__ __forceinline__ void store_box(void *lv, size_t idx, const Box &b)
-{
-    if (BFMT == PNDF_BOUNDS_F32) {
-        reinterpret_cast<float4 *>(lv)[idx] = make_float4(b.smin, b.tmin, b.smax, b.tmax);
-    } else {
-        __half2 lo = __halves2half2(__float2half_rd(b.smin), __float2half_rd(b.tmin));
-        __half2 hi = __halves2half2(__float2half_ru(b.smax), __float2half_ru(b.tmax));
-        uint2 v;
-        v.x = *reinterpret_cast<uint32_t *>(&lo);
-        v.y = *reinterpret_cast<uint32_t *>(&hi);
-        reinterpret_cast<uint2 *>(lv)[idx] = v;
-    }
-}
-
-template <int BFMT>
-__device__ __forceinline__ Box load_box(const void *lv, size_t idx)
-{
-    if (BFMT == PNDF_BOUNDS_F32) {
-        float4 v = reinterpret_cast<const float4 *>(lv)[idx];
-        return Box{v.x, v.y, v.z, v.w};
-    } else {
-        uint2 v = reinterpret_cast<const uint2 *>(lv)[idx];
-        __half2 lo = *reinterpret_cast<__half2 *>(&v.x);
-        __half2 hi = *reinterpret_cast<__half2 *>(&v.y);
-        float2 l = __half22float2(lo), h = __half22float2(hi);
-        return Box{l.x, l.y, h.x, h.y};
-    }
-}
 
 template <int TFMT>
 __device__ __forceinline__ float2 load_texel(const void *t, size_t idx)
@@ -233,10 +186,13 @@ cudaError_t launch_build(const void *texels_src, pndf_hierarchy *h, cudaStream_t
     cudaError_t e = cudaMemcpyAsync(const_cast<void *>(d.texels), texels_src, tb, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return e;
     if (d.texel_fmt == PNDF_TEXEL_F32X2)
-        return d.bounds_fmt == PNDF_BOUNDS_F32 ? launch_tiles<PNDF_TEXEL_F32X2, PNDF_BOUNDS_F32>(texels_src, d, s)
-                                               : launch_tiles<PNDF_TEXEL_F32X2, PNDF_BOUNDS_F16_OUTWARD>(texels_src, d, s);
-    return d.bounds_fmt == PNDF_BOUNDS_F32 ? launch_tiles<PNDF_TEXEL_F16X2, PNDF_BOUNDS_F32>(texels_src, d, s)
-                                           : launch_tiles<PNDF_TEXEL_F16X2, PNDF_BOUNDS_F16_OUTWARD>(texels_src, d, s);
+        e = d.bounds_fmt == PNDF_BOUNDS_F32 ? launch_tiles<PNDF_TEXEL_F32X2, PNDF_BOUNDS_F32>(texels_src, d, s)
+                                            : launch_tiles<PNDF_TEXEL_F32X2, PNDF_BOUNDS_F16_OUTWARD>(texels_src, d, s);
+    else
+        e = d.bounds_fmt == PNDF_BOUNDS_F32 ? launch_tiles<PNDF_TEXEL_F16X2, PNDF_BOUNDS_F32>(texels_src, d, s)
+                                            : launch_tiles<PNDF_TEXEL_F16X2, PNDF_BOUNDS_F16_OUTWARD>(texels_src, d, s);
+    if (e == cudaSuccess && h->clusters) e = launch_clusters(h, s);
+    return e;
 }
 
 }  // namespace pndf

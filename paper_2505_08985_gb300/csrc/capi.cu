@@ -1,4 +1,5 @@
 // C ABI entry points of libpndf.so (declarations and contracts in pndf.h).
+#include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -61,6 +62,7 @@ pndf_status pndf_build_hierarchy(const void *texels_dev, const pndf_build_params
     if (p->texel_fmt != PNDF_TEXEL_F32X2 && p->texel_fmt != PNDF_TEXEL_F16X2) return PNDF_ERR_INVALID_ARG;
     if (p->bounds_fmt != PNDF_BOUNDS_F32 && p->bounds_fmt != PNDF_BOUNDS_F16_OUTWARD) return PNDF_ERR_INVALID_ARG;
     if (p->leaf_level != 0 && p->leaf_level != kLeafLevel) return PNDF_ERR_UNSUPPORTED;
+    if (p->clusters != 0 && p->clusters != 1) return PNDF_ERR_INVALID_ARG;
     if (!aligned(texels_dev, p->texel_fmt == PNDF_TEXEL_F32X2 ? 8 : 4)) return PNDF_ERR_INVALID_ARG;
 
     pndf_hierarchy *h = new (std::nothrow) pndf_hierarchy();
@@ -86,6 +88,19 @@ pndf_status pndf_build_hierarchy(const void *texels_dev, const pndf_build_params
         off[l] = total;
         total += up(level_nodes(d.L, l) * node_b);
     }
+    // cluster records (two float4 per node), residuals, build scratch
+    size_t off_cl[kMaxLevels], off_ce[kMaxLevels], off_mom = 0;
+    h->clusters = p->clusters;
+    if (h->clusters) {
+        for (int l = kLeafLevel; l <= d.L; ++l) {
+            off_cl[l] = total;
+            total += up(level_nodes(d.L, l) * 2 * sizeof(float4));
+            off_ce[l] = total;
+            total += up(level_nodes(d.L, l) * sizeof(float));
+        }
+        off_mom = total;
+        total += up(cluster_scratch_bytes(d.L));
+    }
     if (cudaMalloc(&h->mem, total) != cudaSuccess) {
         cudaGetLastError();
         delete h;
@@ -96,6 +111,15 @@ pndf_status pndf_build_hierarchy(const void *texels_dev, const pndf_build_params
     d.texels = base;
     d.lv[0] = base + off[0];
     for (int l = kLeafLevel; l <= d.L; ++l) d.lv[l] = base + off[l];
+    memset(&h->c, 0, sizeof(h->c));
+    h->moments = nullptr;
+    if (h->clusters) {
+        for (int l = kLeafLevel; l <= d.L; ++l) {
+            h->c.cl[l] = reinterpret_cast<const float4 *>(base + off_cl[l]);
+            h->c.ce[l] = reinterpret_cast<const float *>(base + off_ce[l]);
+        }
+        if (cluster_scratch_bytes(d.L)) h->moments = base + off_mom;
+    }
     cudaError_t e = launch_build(texels_dev, h, as_stream(stream));
     if (e != cudaSuccess) {
         cudaFree(h->mem);
@@ -129,6 +153,18 @@ void pndf_free_hierarchy(pndf_hierarchy *h)
 
 size_t pndf_hierarchy_bytes(const pndf_hierarchy *h) { return h ? h->bytes : 0; }
 
+pndf_status pndf_cluster_level(const pndf_hierarchy *h, int32_t level, float *records_dev, float *residual_dev,
+                               void *stream)
+{
+    pndf_status st = check_hierarchy(h);
+    if (st != PNDF_OK) return st;
+    if (!h->clusters) return PNDF_ERR_UNSUPPORTED;
+    if (level < kLeafLevel || level > h->d.L || !records_dev || !residual_dev) return PNDF_ERR_INVALID_ARG;
+    if (!aligned(records_dev, 4) || !aligned(residual_dev, 4)) return PNDF_ERR_INVALID_ARG;
+    return launch_cluster_copy(h, level, records_dev, residual_dev, as_stream(stream)) == cudaSuccess ? PNDF_OK
+                                                                                                    : PNDF_ERR_CUDA;
+}
+
 pndf_status pndf_eval_batch_ex(const pndf_hierarchy *h, const pndf_query *q_dev, int64_t nq, float *D_out_dev,
                                uint32_t *flags_out_dev, pndf_query_stats *stats_dev, const pndf_eval_config *cfg,
                                void *stream)
@@ -138,9 +174,11 @@ pndf_status pndf_eval_batch_ex(const pndf_hierarchy *h, const pndf_query *q_dev,
     if (nq < 0 || nq > int64_t(0x7fffffff)) return PNDF_ERR_INVALID_ARG;
     if (nq > 0 && (!q_dev || !D_out_dev)) return PNDF_ERR_INVALID_ARG;
     if (q_dev && !aligned(q_dev, 16)) return PNDF_ERR_INVALID_ARG;
-    pndf_eval_config c{PNDF_MODE_HIERARCHY, PNDF_SORT_DEFAULT, 0, 0, nullptr, nullptr};
+    pndf_eval_config c{PNDF_MODE_HIERARCHY, PNDF_SORT_DEFAULT, 0, 0, 0.f, 0, nullptr, nullptr};
     if (cfg) c = *cfg;
     if (c.mode != PNDF_MODE_HIERARCHY && c.mode != PNDF_MODE_FLAT) return PNDF_ERR_INVALID_ARG;
+    if (!(c.tau >= 0.f) || !isfinite(c.tau) || c.reserved != 0) return PNDF_ERR_INVALID_ARG;
+    if (c.tau > 0.f && (!h->clusters || c.mode != PNDF_MODE_HIERARCHY)) return PNDF_ERR_UNSUPPORTED;
     if (c.sort < 0 || c.sort > 4) return PNDF_ERR_INVALID_ARG;
     if (c.warps_per_cta < 0 || c.warps_per_cta > 8 || c.ctas_per_sm < 0) return PNDF_ERR_INVALID_ARG;
     return launch_eval(h, q_dev, nq, D_out_dev, flags_out_dev, stats_dev, c, as_stream(stream));
@@ -196,7 +234,7 @@ pndf_status pndf_eval_batch_host(const pndf_hierarchy *h, const pndf_query *q_ho
     float *Dd = static_cast<float *>(buf);
     pndf_query *qd = reinterpret_cast<pndf_query *>(static_cast<char *>(buf) + qoff);
     cudaError_t e = cudaMemcpyAsync(qd, q_host, qb, cudaMemcpyHostToDevice, s);
-    pndf_eval_config c{PNDF_MODE_HIERARCHY, PNDF_SORT_DEFAULT, 0, 0, nullptr, nullptr};
+    pndf_eval_config c{PNDF_MODE_HIERARCHY, PNDF_SORT_DEFAULT, 0, 0, 0.f, 0, nullptr, nullptr};
     if (e == cudaSuccess) st = launch_eval(h, qd, nq, Dd, nullptr, nullptr, c, s);
     if (e == cudaSuccess && st == PNDF_OK) e = cudaMemcpyAsync(D_host, Dd, db, cudaMemcpyDeviceToHost, s);
     cudaError_t ef = cudaFreeAsync(buf, s);

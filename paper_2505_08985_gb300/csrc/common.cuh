@@ -32,6 +32,17 @@ struct MapDesc {
                                  // (2^(L-l))^2 nodes each, Morton order
 };
 
+// Cluster hierarchy (Sec. 4.3, Eq. 7-8, App. A), levels kLeafLevel..L in the
+// same Morton order as the boxes.  Per node two float4 records,
+// (c00.s, c00.t, d10.s, d10.t) and (d01.s, d01.t, d11.s, d11.t) with the
+// corner normals c10 = c00 + d10 etc. kept as differences (a flat cluster's
+// Jacobian is the cross product of small differences), and the residual e
+// (+inf where the node has no cluster).
+struct ClusterDesc {
+    const float4 *cl[kMaxLevels];
+    const float *ce[kMaxLevels];
+};
+
 // Morton (Z-order) interleave of two 16-bit coordinates: x in the even bits.
 __host__ __device__ __forceinline__ uint32_t part1by1(uint32_t v)
 {
@@ -64,7 +75,58 @@ inline int top_level(int n)
     return L < kLeafLevel ? kLeafLevel : L;
 }
 
-inline size_t level_nodes(int L, int l)
+// Node box (s_min, t_min, s_max, t_max); empty = (+inf, +inf, -inf, -inf).
+// Stored as float4 (FP32 bounds) or as two half2 (FP16 bounds, min rounded
+// down and max rounded up).
+struct Box {
+    float smin, tmin, smax, tmax;
+};
+
+__device__ __forceinline__ Box empty_box()
+{
+    return Box{__int_as_float(0x7f800000), __int_as_float(0x7f800000), __int_as_float(0xff800000),
+               __int_as_float(0xff800000)};
+}
+
+__device__ __forceinline__ void grow(Box &b, const Box &o)
+{
+    b.smin = fminf(b.smin, o.smin);
+    b.tmin = fminf(b.tmin, o.tmin);
+    b.smax = fmaxf(b.smax, o.smax);
+    b.tmax = fmaxf(b.tmax, o.tmax);
+}
+
+template <int BFMT>
+__device__ __forceinline__ void store_box(void *lv, size_t idx, const Box &b)
+{
+    if (BFMT == PNDF_BOUNDS_F32) {
+        reinterpret_cast<float4 *>(lv)[idx] = make_float4(b.smin, b.tmin, b.smax, b.tmax);
+    } else {
+        __half2 lo = __halves2half2(__float2half_rd(b.smin), __float2half_rd(b.tmin));
+        __half2 hi = __halves2half2(__float2half_ru(b.smax), __float2half_ru(b.tmax));
+        uint2 v;
+        v.x = *reinterpret_cast<uint32_t *>(&lo);
+        v.y = *reinterpret_cast<uint32_t *>(&hi);
+        reinterpret_cast<uint2 *>(lv)[idx] = v;
+    }
+}
+
+template <int BFMT>
+__device__ __forceinline__ Box load_box(const void *lv, size_t idx)
+{
+    if (BFMT == PNDF_BOUNDS_F32) {
+        float4 v = reinterpret_cast<const float4 *>(lv)[idx];
+        return Box{v.x, v.y, v.z, v.w};
+    } else {
+        uint2 v = reinterpret_cast<const uint2 *>(lv)[idx];
+        __half2 lo = *reinterpret_cast<__half2 *>(&v.x);
+        __half2 hi = *reinterpret_cast<__half2 *>(&v.y);
+        float2 l = __half22float2(lo), h = __half22float2(hi);
+        return Box{l.x, l.y, h.x, h.y};
+    }
+}
+
+__host__ __device__ inline size_t level_nodes(int L, int l)
 {
     size_t s = size_t(1) << (L - l);
     return s * s;
@@ -78,11 +140,20 @@ struct pndf_hierarchy {
     pndf::MapDesc d;
     void *mem;
     size_t bytes;
+    int clusters;              // cluster hierarchy built (and node boxes widened to hold it)
+    pndf::ClusterDesc c;       // cluster records, when clusters != 0
+    void *moments;             // build scratch: FP64 moments of the level-6 and level-7 nodes
 };
 
 namespace pndf {
 // launchers implemented in the kernel translation units
 cudaError_t launch_build(const void *texels_src, pndf_hierarchy *h, cudaStream_t s);
+// Cluster fits of every node and the widened boxes (after launch_build's pyramid).
+cudaError_t launch_clusters(pndf_hierarchy *h, cudaStream_t s);
+// Bytes of the cluster build scratch for a pyramid of height L.
+size_t cluster_scratch_bytes(int L);
+// Level l's cluster records and residuals in row-major node order.
+cudaError_t launch_cluster_copy(const pndf_hierarchy *h, int l, float *rec, float *e, cudaStream_t s);
 pndf_status launch_eval(const pndf_hierarchy *h, const pndf_query *q, int64_t nq, float *D, uint32_t *flags,
                         pndf_query_stats *stats, const pndf_eval_config &cfg, cudaStream_t s);
 pndf_status launch_projarea(const pndf_hierarchy *h, const pndf_query *q, const float *omega, int64_t nq,

@@ -86,6 +86,7 @@ struct Query {
     float norm;          // 1 / (2 pi sqrt(det S))
     float mx, my;        // query normal
     float rx, ry;        // half-widths of the 4-sigma box (slightly inflated)
+    float theta;         // cluster cut threshold r_x r_y tau (exact 4-sigma half-widths)
     bool valid;
 };
 
@@ -107,6 +108,7 @@ __device__ __forceinline__ Query make_query(const pndf_query &r)
     // q <= 16 implies |dx| <= 4 sqrt(sxx); inflate so rounding never clips the box
     q.rx = 4.0f * sqrtf(r.sxx) * (1.0f + 1e-5f) + 1e-6f;
     q.ry = 4.0f * sqrtf(r.syy) * (1.0f + 1e-5f) + 1e-6f;
+    q.theta = 0.f;
     return q;
 }
 
@@ -199,7 +201,7 @@ constexpr uint32_t kMortonMask = (1u << 27) - 1u;
 
 struct Acc {
     float s, c;  // Neumaier compensated sum
-    uint32_t hits, hash, tests, fp64, degen, leaves, nodes, quads;
+    uint32_t hits, hash, tests, fp64, degen, leaves, nodes, quads, cchecks, clusters;
     uint32_t flags;
 };
 
@@ -304,29 +306,52 @@ __device__ __forceinline__ bool edge_test(const Query &q, float2 na, float2 nb, 
 }
 
 // Hit ring: FP32 hits waiting for their footprint weight, as (cross, e1, e2,
-// (i << 15) | (j << 1) | tri) with (i, j) the quad.
+// tag): tag (i << 15) | (j << 1) | tri for a triangle of quad (i, j), or
+// kClusterTag | (l << 27) | (morton << 1) | tri for a cluster triangle of
+// node (l, morton).
 constexpr int kHitRing = 64;
+constexpr uint32_t kClusterTag = 0x80000000u;
+constexpr uint32_t kClusterMorton = (1u << 26) - 1u;
 
 // All 32 lanes: lane k < cnt weighs hit k of the ring (the tail of test_triangle).
 template <bool STATS>
-__device__ __forceinline__ void drain_hits(const Query &q, int n, const float4 *hits, uint32_t hh, int cnt, int lane,
-                                           Acc &acc)
+__device__ __forceinline__ void drain_hits(const Query &q, int n, int L, const float4 *hits, uint32_t hh, int cnt,
+                                           int lane, Acc &acc)
 {
     if (lane < cnt) {
         float4 h = hits[(hh + uint32_t(lane)) & (kHitRing - 1)];
         uint32_t pk = __float_as_uint(h.w);
-        int gi = int(pk >> 15), gj = int((pk >> 1) & 0x3fffu), tri = int(pk & 1u);
+        const int tri = int(pk & 1u);
+        int gi, gj, l = 0;
+        if (pk & kClusterTag) {  // cluster triangle of node (l, I, J): uv scale 2^l
+            l = int((pk >> 27) & 15u);
+            uint32_t m = (pk >> 1) & kClusterMorton;
+            gi = int(compact1by1(m)) << l;
+            gj = int(compact1by1(m >> 1)) << l;
+        } else {
+            gi = int(pk >> 15);
+            gj = int((pk >> 1) & 0x3fffu);
+        }
+        const float a = float(1 << l);
         float inv = 1.0f / h.x;
         float l1 = h.y * inv, l2 = h.z * inv;
-        float dir = tri ? -1.f : 1.f;
-        float dx = (float(gi + tri) - q.x) + dir * l1;
-        float dy = (float(gj + tri) - q.y) + dir * l2;
+        float dir = tri ? -a : a;
+        float dx = (float(gi + (tri << l)) - q.x) + dir * l1;
+        float dy = (float(gj + (tri << l)) - q.y) + dir * l2;
         float qq = qform(q, dx, dy);
         if (qq <= kQCut) {
-            acc_add(acc, q.norm * expf(-0.5f * qq) / fabsf(h.x));
+            acc_add(acc, q.norm * expf(-0.5f * qq) * (a * a) / fabsf(h.x));
             if (STATS) {
                 acc.hits++;
-                acc.hash += fmix32(2u * (uint32_t(gj) * uint32_t(n - 1) + uint32_t(gi)) + uint32_t(tri));
+                uint32_t id;
+                if (pk & kClusterTag) {
+                    uint32_t S = 1u << (L - l);
+                    id = kClusterTag | (uint32_t(l) << 27) |
+                         (((uint32_t(gj) >> l) * S + (uint32_t(gi) >> l)) << 1) | uint32_t(tri);
+                } else {
+                    id = 2u * (uint32_t(gj) * uint32_t(n - 1) + uint32_t(gi)) + uint32_t(tri);
+                }
+                acc.hash += fmix32(id);
             }
         }
     }
@@ -415,7 +440,109 @@ __device__ __forceinline__ void test_quads(const MapDesc &d, const Query &q, Lea
         ls.nh += __popc(m);
         __syncwarp();
         if (ls.nh >= 32) {
-            drain_hits<STATS>(q, d.n, ls.hits, ls.hh, 32, lane, acc);
+            drain_hits<STATS>(q, d.n, d.L, ls.hits, ls.hh, 32, lane, acc);
+            ls.hh += 32;
+            ls.nh -= 32;
+            __syncwarp();
+        }
+    }
+}
+
+// Cluster triangle test (Sec. 4.3) in vertex-relative form: p = m - A,
+// b = B - A, c = C - A.  Same rule as edge_test (closed bounding box, edge
+// functions sign-consistent with the orientation); the Jacobian of the
+// cluster map is cross / 4^l, applied when the hit is weighed.  Triangles
+// with FP32 |cross| < 2e-10 are decided and weighed here in FP64.
+template <bool STATS>
+__device__ __forceinline__ bool cluster_edge_test(const Query &q, float2 p, float2 b, float2 c, int l, int ai,
+                                                  int aj, float dir, uint32_t id, Acc &acc, float &cr_o, float &e1_o,
+                                                  float &e2_o)
+{
+    if (STATS) acc.tests++;
+    if (p.x < fminf(0.f, fminf(b.x, c.x)) || p.x > fmaxf(0.f, fmaxf(b.x, c.x)) ||
+        p.y < fminf(0.f, fminf(b.y, c.y)) || p.y > fmaxf(0.f, fmaxf(b.y, c.y)))
+        return false;
+    float cr = dop(b.x, c.y, b.y, c.x);
+    if (fabsf(cr) >= kTinyCross) {
+        float e0 = dop(c.x - b.x, p.y - b.y, c.y - b.y, p.x - b.x);
+        float e1 = dop(p.x, c.y, p.y, c.x);
+        float e2 = dop(b.x, p.y, b.y, p.x);
+        bool hit = cr > 0.f ? (e0 >= 0.f && e1 >= 0.f && e2 >= 0.f) : (e0 <= 0.f && e1 <= 0.f && e2 <= 0.f);
+        cr_o = cr;
+        e1_o = e1;
+        e2_o = e2;
+        return hit;
+    }
+    double bx = b.x, by = b.y, cx = c.x, cy = c.y, px = p.x, py = p.y;
+    double dcr = bx * cy - by * cx;
+    if (dcr == 0.0) {
+        if (STATS) acc.degen++;
+        return false;
+    }
+    if (STATS) acc.fp64++;
+    acc.flags |= PNDF_QF_FP64;
+    double e0 = (cx - bx) * (py - by) - (cy - by) * (px - bx);
+    double e1 = px * cy - py * cx;
+    double e2 = bx * py - by * px;
+    bool hit = dcr > 0.0 ? (e0 >= 0.0 && e1 >= 0.0 && e2 >= 0.0) : (e0 <= 0.0 && e1 <= 0.0 && e2 <= 0.0);
+    if (!hit) return false;
+    double dl1 = e1 / dcr, dl2 = e2 / dcr;
+    double dx = (double(ai) - double(q.x)) + dir * dl1;
+    double dy = (double(aj) - double(q.y)) + dir * dl2;
+    double qq = double(q.ia) * dx * dx + 2.0 * double(q.ib) * dx * dy + double(q.ic) * dy * dy;
+    if (qq > double(kQCut)) return false;
+    double sc = double(1u << l);
+    acc_add(acc, float(double(q.norm) * exp(-0.5 * qq) * sc * sc / fabs(dcr)));
+    if (STATS) {
+        acc.hits++;
+        acc.hash += fmix32(id);
+    }
+    return false;
+}
+
+// All 32 lanes: lane k < cnt tests the two cluster triangles of the cut node
+// in last[-k] (level, Morton): lower (c00, c10, c01) at uv (O, O + (a, 0),
+// O + (0, a)), upper (c11, c01, c10) at (O + (a, a), O + (0, a), O + (a, 0)),
+// a = 2^l; hits join the hit ring.
+template <bool STATS>
+__device__ __forceinline__ void test_clusters(const MapDesc &d, const ClusterDesc &cd, const Query &q,
+                                              const uint32_t *last, int cnt, LeafState &ls, int lane, Acc &acc)
+{
+    const unsigned lt = (1u << lane) - 1u;
+    bool h0 = false, h1 = false;
+    float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
+    if (lane < cnt) {
+        uint32_t ent = last[-lane];
+        int l = int(ent >> 28);
+        uint32_t m = ent & kMortonMask;
+        const float4 *rec = cd.cl[l] + 2 * size_t(m);
+        float4 r0 = __ldg(rec), r1 = __ldg(rec + 1);
+        int ox = int(compact1by1(m)) << l, oy = int(compact1by1(m >> 1)) << l;
+        int a = 1 << l;
+        float2 p = make_float2(q.mx - r0.x, q.my - r0.y);
+        float2 d10 = make_float2(r0.z, r0.w), d01 = make_float2(r1.x, r1.y), d11 = make_float2(r1.z, r1.w);
+        uint32_t tag = kClusterTag | (uint32_t(l) << 27) | (m << 1);
+        // hit fingerprint id (stats): row-major node index at its level
+        uint32_t id = kClusterTag | (uint32_t(l) << 27) |
+                      (((uint32_t(oy >> l) << (d.L - l)) + uint32_t(ox >> l)) << 1);
+        float cr, e1, e2;
+        if (STATS) acc.clusters++;
+        h0 = cluster_edge_test<STATS>(q, p, d10, d01, l, ox, oy, float(a), id, acc, cr, e1, e2);
+        if (h0) v0 = make_float4(cr, e1, e2, __uint_as_float(tag));
+        float2 pu = make_float2(p.x - d11.x, p.y - d11.y);
+        float2 bu = make_float2(d01.x - d11.x, d01.y - d11.y), cu = make_float2(d10.x - d11.x, d10.y - d11.y);
+        h1 = cluster_edge_test<STATS>(q, pu, bu, cu, l, ox + a, oy + a, -float(a), id | 1u, acc, cr, e1, e2);
+        if (h1) v1 = make_float4(cr, e1, e2, __uint_as_float(tag | 1u));
+    }
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        bool h = t ? h1 : h0;
+        unsigned mk = __ballot_sync(kFull, h);
+        if (h) ls.hits[(ls.hh + uint32_t(ls.nh) + __popc(mk & lt)) & (kHitRing - 1)] = t ? v1 : v0;
+        ls.nh += __popc(mk);
+        __syncwarp();
+        if (ls.nh >= 32) {
+            drain_hits<STATS>(q, d.n, d.L, ls.hits, ls.hh, 32, lane, acc);
             ls.hh += 32;
             ls.nh -= 32;
             __syncwarp();
@@ -521,21 +648,23 @@ __device__ __forceinline__ int entry_level(const Query &q, int L)
     return l;
 }
 
-template <int BFMT, int TFMT, bool STATS, bool FLAT>
-__device__ void eval_one(const MapDesc &d, const pndf_query &rec, int lane, uint32_t *stk, uint32_t *lq,
-                         uint32_t *ring, float4 *hits, float &D_out, uint32_t &flags_out, pndf_query_stats *st_out)
+template <int BFMT, int TFMT, bool STATS, bool FLAT, bool CLUSTER>
+__device__ void eval_one(const MapDesc &d, const ClusterDesc &cd, float tau, const pndf_query &rec, int lane,
+                         uint32_t *stk, uint32_t *lq, uint32_t *ring, float4 *hits, float &D_out, uint32_t &flags_out,
+                         pndf_query_stats *st_out)
 {
     Query q = make_query(rec);
-    Acc acc = {0.f, 0.f, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    Acc acc = {};
     if (!q.valid) {
         if (lane == 0) {
             D_out = __int_as_float(0x7fc00000);
             flags_out = PNDF_QF_INVALID;
             atomicOr(&g_status_eval, PNDF_QF_INVALID);
-            if (STATS) *st_out = pndf_query_stats{0, 0, 0, 0, 0, 0, 0, 0};
+            if (STATS) *st_out = pndf_query_stats{0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
         }
         return;
     }
+    if (CLUSTER) q.theta = (4.0f * sqrtf(rec.sxx)) * (4.0f * sqrtf(rec.syy)) * tau;
     const int L = d.L;
     if (FLAT) {
         // every leaf block meeting the 4-sigma box, no pruning
@@ -554,7 +683,7 @@ __device__ void eval_one(const MapDesc &d, const pndf_query &rec, int lane, uint
         int a0, a1, c0, c1;
         node_range(q.x, q.rx, sz, S, a0, a1);
         node_range(q.y, q.ry, sz, S, c0, c1);
-        int top = 0, nleaf = 0;
+        int top = 0, nleaf = 0, ncl = 0;
         const unsigned lt = (1u << lane) - 1u;
         // entry nodes: at most 4 x 4
         {
@@ -562,9 +691,15 @@ __device__ void eval_one(const MapDesc &d, const pndf_query &rec, int lane, uint
             bool valid = lane < 16 && a <= a1 && c <= c1;
             bool pass = valid && node_test<BFMT>(d, q, e, a, c);
             bool inside = pass && node_inside(q, e, a, c);
+            bool cut = false;
             if (STATS) acc.nodes += valid ? 1u : 0u;
-            unsigned m = __ballot_sync(kFull, pass);
-            if (pass) {
+            if (CLUSTER && pass) {  // the cut of Sec. 4.3: e <= r_x r_y tau
+                cut = __ldg(cd.ce[e] + morton2(a, c)) <= q.theta;
+                if (STATS) acc.cchecks++;
+            }
+            unsigned m = __ballot_sync(kFull, pass && !cut);
+            unsigned mc = __ballot_sync(kFull, cut);
+            if (pass && !cut) {
                 int pos = __popc(m & lt);
                 uint32_t ent = pack(e, inside, morton2(a, c));
                 if (e == kLeafLevel)
@@ -572,10 +707,12 @@ __device__ void eval_one(const MapDesc &d, const pndf_query &rec, int lane, uint
                 else
                     stk[pos] = ent;
             }
+            if (CLUSTER && cut) lq[63 - __popc(mc & lt)] = pack(e, false, morton2(a, c));
             if (e == kLeafLevel)
                 nleaf = __popc(m);
             else
                 top = __popc(m);
+            ncl = __popc(mc);
             __syncwarp();
         }
         bool overflow = false;
@@ -583,15 +720,25 @@ __device__ void eval_one(const MapDesc &d, const pndf_query &rec, int lane, uint
         while (true) {
             process_leaves<BFMT, TFMT, STATS>(d, q, lq, nleaf, ls, lane, acc);
             nleaf = 0;
+            if (CLUSTER) {
+                // cut nodes sit at the back of the leaf queue (entry k at lq[63 - k];
+                // leaf blocks fill the front, together at most 64 per step)
+                for (int k0 = 0; k0 < ncl; k0 += 32) {
+                    test_clusters<STATS>(d, cd, q, lq + 63 - k0, min(32, ncl - k0), ls, lane, acc);
+                    __syncwarp();
+                }
+                ncl = 0;
+            }
             if (top == 0) break;
             // pop up to 16 nodes; lane k tests child (k & 3) of popped nodes
             // (k >> 2) and (k >> 2) + 8, so two box loads per lane are in flight
             int npop = min(top, 16);
             top -= npop;
-            bool pass[2], ins[2];
+            bool pass[2], ins[2], cut[2] = {false, false};
             int cl[2];
             uint32_t cm[2];
             float4 bx[2];
+            float ev[2];
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
                 int slot = (lane >> 2) + 8 * r;
@@ -610,15 +757,30 @@ __device__ void eval_one(const MapDesc &d, const pndf_query &rec, int lane, uint
             }
 #pragma unroll
             for (int r = 0; r < 2; ++r)  // both box loads issue before either is used
-                if (pass[r]) bx[r] = node_box<BFMT>(d, cl[r], cm[r]);
+                if (pass[r]) {
+                    bx[r] = node_box<BFMT>(d, cl[r], cm[r]);
+                    if (CLUSTER) ev[r] = __ldg(cd.ce[cl[r]] + cm[r]);
+                }
 #pragma unroll
-            for (int r = 0; r < 2; ++r) pass[r] = pass[r] && box_holds(bx[r], q);
+            for (int r = 0; r < 2; ++r) {
+                pass[r] = pass[r] && box_holds(bx[r], q);
+                if (CLUSTER && pass[r]) {  // the cut of Sec. 4.3: e <= r_x r_y tau
+                    cut[r] = ev[r] <= q.theta;
+                    if (STATS) acc.cchecks++;
+                }
+            }
             __syncwarp();
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
-                bool to_leaf = pass[r] && cl[r] == kLeafLevel, to_stack = pass[r] && cl[r] > kLeafLevel;
+                bool to_leaf = pass[r] && !cut[r] && cl[r] == kLeafLevel;
+                bool to_stack = pass[r] && !cut[r] && cl[r] > kLeafLevel;
                 unsigned ml = __ballot_sync(kFull, to_leaf);
                 unsigned ms = __ballot_sync(kFull, to_stack);
+                if (CLUSTER) {
+                    unsigned mc = __ballot_sync(kFull, cut[r]);
+                    if (cut[r]) lq[63 - ncl - __popc(mc & lt)] = pack(cl[r], false, cm[r]);
+                    ncl += __popc(mc);
+                }
                 if (to_leaf) lq[nleaf + __popc(ml & lt)] = pack(cl[r], ins[r], cm[r]);
                 if (to_stack) {
                     int pos = top + __popc(ms & lt);
@@ -634,7 +796,7 @@ __device__ void eval_one(const MapDesc &d, const pndf_query &rec, int lane, uint
             __syncwarp();
         }
         if (ls.nsq > 0) test_quads<TFMT, STATS>(d, q, ls, ls.nsq, lane, acc);  // nsq < 32 here
-        if (ls.nh > 0) drain_hits<STATS>(q, d.n, ls.hits, ls.hh, ls.nh, lane, acc);  // nh < 32 here
+        if (ls.nh > 0) drain_hits<STATS>(q, d.n, d.L, ls.hits, ls.hh, ls.nh, lane, acc);  // nh < 32 here
         if (overflow) acc.flags |= PNDF_QF_OVERFLOW;
     }
     // warp reduction (fixed order: deterministic for a given query)
@@ -658,22 +820,25 @@ __device__ void eval_one(const MapDesc &d, const pndf_query &rec, int lane, uint
         acc.nodes = __reduce_add_sync(kFull, acc.nodes);
         acc.leaves = __reduce_add_sync(kFull, acc.leaves);
         acc.quads = __reduce_add_sync(kFull, acc.quads);
+        acc.cchecks = __reduce_add_sync(kFull, acc.cchecks);
+        acc.clusters = __reduce_add_sync(kFull, acc.clusters);
     }
     if (lane == 0) {
         D_out = s + c;
         flags_out = fl;
         if (fl & PNDF_QF_OVERFLOW) atomicOr(&g_status_eval, PNDF_QF_OVERFLOW);
         if (STATS)
-            *st_out = pndf_query_stats{acc.nodes, acc.leaves, acc.tests, acc.hits, acc.hash, acc.fp64, acc.degen, acc.quads};
+            *st_out = pndf_query_stats{acc.nodes, acc.leaves, acc.tests, acc.hits,    acc.hash,
+                                       acc.fp64,  acc.degen,  acc.quads, acc.cchecks, acc.clusters};
     }
 }
 
-template <int BFMT, int TFMT, bool STATS, bool FLAT>
-__global__ void __launch_bounds__(256, PNDF_TRAVERSE_MIN_CTAS) traverse_kernel(MapDesc d, const pndf_query *__restrict__ qs,
-                                                      const uint32_t *__restrict__ order, int64_t nq,
-                                                      float *__restrict__ D, uint32_t *__restrict__ flags,
-                                                      pndf_query_stats *__restrict__ stats,
-                                                      unsigned long long *__restrict__ cursor)
+template <int BFMT, int TFMT, bool STATS, bool FLAT, bool CLUSTER>
+__global__ void __launch_bounds__(256, PNDF_TRAVERSE_MIN_CTAS)
+    traverse_kernel(MapDesc d, ClusterDesc cd, float tau, const pndf_query *__restrict__ qs,
+                    const uint32_t *__restrict__ order, int64_t nq, float *__restrict__ D,
+                    uint32_t *__restrict__ flags, pndf_query_stats *__restrict__ stats,
+                    unsigned long long *__restrict__ cursor)
 {
     extern __shared__ uint32_t smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -690,7 +855,8 @@ __global__ void __launch_bounds__(256, PNDF_TRAVERSE_MIN_CTAS) traverse_kernel(M
         pndf_query rec = qs[qi];
         float Dv;
         uint32_t fv;
-        eval_one<BFMT, TFMT, STATS, FLAT>(d, rec, lane, stk, lq, ring, hits, Dv, fv, stats ? stats + qi : nullptr);
+        eval_one<BFMT, TFMT, STATS, FLAT, CLUSTER>(d, cd, tau, rec, lane, stk, lq, ring, hits, Dv, fv,
+                                                   stats ? stats + qi : nullptr);
         if (lane == 0) {
             D[qi] = Dv;
             if (flags) flags[qi] = fv;
@@ -830,12 +996,12 @@ inline size_t sort_hist_bytes(int64_t nq)
     return bins * sizeof(uint32_t);
 }
 
-template <int BFMT, int TFMT, bool STATS, bool FLAT>
-cudaError_t launch_traverse(const MapDesc &d, const pndf_query *q, const uint32_t *order, int64_t nq, float *D,
-                            uint32_t *flags, pndf_query_stats *stats, unsigned long long *cursor, int warps,
-                            int ctas_per_sm, cudaStream_t s)
+template <int BFMT, int TFMT, bool STATS, bool FLAT, bool CLUSTER>
+cudaError_t launch_traverse(const MapDesc &d, const ClusterDesc &cd, float tau, const pndf_query *q,
+                            const uint32_t *order, int64_t nq, float *D, uint32_t *flags, pndf_query_stats *stats,
+                            unsigned long long *cursor, int warps, int ctas_per_sm, cudaStream_t s)
 {
-    auto kern = traverse_kernel<BFMT, TFMT, STATS, FLAT>;
+    auto kern = traverse_kernel<BFMT, TFMT, STATS, FLAT, CLUSTER>;
     int threads = warps * 32;
     size_t smem = size_t(warps) * kWarpSmemWords * sizeof(uint32_t);
     int dev = 0, sms = 0, occ = 0;
@@ -849,27 +1015,33 @@ cudaError_t launch_traverse(const MapDesc &d, const pndf_query *q, const uint32_
     int64_t grid = int64_t(sms) * occ;
     if (grid > want) grid = want;
     if (grid < 1) grid = 1;
-    kern<<<unsigned(grid), threads, smem, s>>>(d, q, order, nq, D, flags, stats, cursor);
+    kern<<<unsigned(grid), threads, smem, s>>>(d, cd, tau, q, order, nq, D, flags, stats, cursor);
     count_launches(1);
     return cudaGetLastError();
 }
 
 template <int BFMT, int TFMT>
-cudaError_t dispatch_stats(const MapDesc &d, const pndf_query *q, const uint32_t *order, int64_t nq, float *D,
-                           uint32_t *flags, pndf_query_stats *stats, unsigned long long *cursor,
-                           const pndf_eval_config &cfg, cudaStream_t s)
+cudaError_t dispatch_stats(const MapDesc &d, const ClusterDesc &cd, const pndf_query *q, const uint32_t *order,
+                           int64_t nq, float *D, uint32_t *flags, pndf_query_stats *stats,
+                           unsigned long long *cursor, const pndf_eval_config &cfg, cudaStream_t s)
 {
-    int warps = cfg.warps_per_cta > 0 ? cfg.warps_per_cta : 8;
-    bool flat = cfg.mode == PNDF_MODE_FLAT;
-    if (stats)
-        return flat ? launch_traverse<BFMT, TFMT, true, true>(d, q, order, nq, D, flags, stats, cursor, warps,
-                                                               cfg.ctas_per_sm, s)
-                    : launch_traverse<BFMT, TFMT, true, false>(d, q, order, nq, D, flags, stats, cursor, warps,
-                                                                cfg.ctas_per_sm, s);
-    return flat ? launch_traverse<BFMT, TFMT, false, true>(d, q, order, nq, D, flags, stats, cursor, warps,
-                                                            cfg.ctas_per_sm, s)
-                : launch_traverse<BFMT, TFMT, false, false>(d, q, order, nq, D, flags, stats, cursor, warps,
-                                                             cfg.ctas_per_sm, s);
+    const int warps = cfg.warps_per_cta > 0 ? cfg.warps_per_cta : 8;
+    const int cps = cfg.ctas_per_sm;
+    const float tau = cfg.tau;
+    if (cfg.mode == PNDF_MODE_FLAT)
+        return stats ? launch_traverse<BFMT, TFMT, true, true, false>(d, cd, 0.f, q, order, nq, D, flags, stats,
+                                                                       cursor, warps, cps, s)
+                     : launch_traverse<BFMT, TFMT, false, true, false>(d, cd, 0.f, q, order, nq, D, flags, stats,
+                                                                        cursor, warps, cps, s);
+    if (tau > 0.f)
+        return stats ? launch_traverse<BFMT, TFMT, true, false, true>(d, cd, tau, q, order, nq, D, flags, stats,
+                                                                       cursor, warps, cps, s)
+                     : launch_traverse<BFMT, TFMT, false, false, true>(d, cd, tau, q, order, nq, D, flags, stats,
+                                                                        cursor, warps, cps, s);
+    return stats ? launch_traverse<BFMT, TFMT, true, false, false>(d, cd, 0.f, q, order, nq, D, flags, stats, cursor,
+                                                                    warps, cps, s)
+                 : launch_traverse<BFMT, TFMT, false, false, false>(d, cd, 0.f, q, order, nq, D, flags, stats,
+                                                                     cursor, warps, cps, s);
 }
 
 }  // namespace
@@ -903,13 +1075,13 @@ pndf_status launch_eval(const pndf_hierarchy *h, const pndf_query *q, int64_t nq
     if (e == cudaSuccess) {
         if (d.bounds_fmt == PNDF_BOUNDS_F32)
             e = d.texel_fmt == PNDF_TEXEL_F32X2
-                    ? dispatch_stats<PNDF_BOUNDS_F32, PNDF_TEXEL_F32X2>(d, q, order, nq, D, flags, stats, cursor, cfg, s)
-                    : dispatch_stats<PNDF_BOUNDS_F32, PNDF_TEXEL_F16X2>(d, q, order, nq, D, flags, stats, cursor, cfg, s);
+                    ? dispatch_stats<PNDF_BOUNDS_F32, PNDF_TEXEL_F32X2>(d, h->c, q, order, nq, D, flags, stats, cursor, cfg, s)
+                    : dispatch_stats<PNDF_BOUNDS_F32, PNDF_TEXEL_F16X2>(d, h->c, q, order, nq, D, flags, stats, cursor, cfg, s);
         else
             e = d.texel_fmt == PNDF_TEXEL_F32X2
-                    ? dispatch_stats<PNDF_BOUNDS_F16_OUTWARD, PNDF_TEXEL_F32X2>(d, q, order, nq, D, flags, stats, cursor,
+                    ? dispatch_stats<PNDF_BOUNDS_F16_OUTWARD, PNDF_TEXEL_F32X2>(d, h->c, q, order, nq, D, flags, stats, cursor,
                                                                              cfg, s)
-                    : dispatch_stats<PNDF_BOUNDS_F16_OUTWARD, PNDF_TEXEL_F16X2>(d, q, order, nq, D, flags, stats, cursor,
+                    : dispatch_stats<PNDF_BOUNDS_F16_OUTWARD, PNDF_TEXEL_F16X2>(d, h->c, q, order, nq, D, flags, stats, cursor,
                                                                              cfg, s);
     }
     if (e == cudaSuccess && cfg.ev_end) e = cudaEventRecord(static_cast<cudaEvent_t>(cfg.ev_end), s);
@@ -950,6 +1122,8 @@ pndf_status launch_sort(const pndf_hierarchy *h, const pndf_query *q, int64_t nq
 // ---------------------------------------------------------------------------
 
 namespace {
+
+__constant__ ClusterDesc kNoClusters;  // unused by the exact serving path
 
 template <int BFMT, int TFMT>
 __global__ void __launch_bounds__(256, PNDF_TRAVERSE_MIN_CTAS)
@@ -992,7 +1166,8 @@ __global__ void __launch_bounds__(256, PNDF_TRAVERSE_MIN_CTAS)
         const pndf_query rec = sg.q[qi];
         float Dv;
         uint32_t fv;
-        eval_one<BFMT, TFMT, false, false>(smaps[sg.map], rec, lane, stk, lq, ring, hits, Dv, fv, nullptr);
+        eval_one<BFMT, TFMT, false, false, false>(smaps[sg.map], kNoClusters, 0.f, rec, lane, stk, lq, ring, hits,
+                                                  Dv, fv, nullptr);
         if (lane == 0) {
             sg.D[qi] = Dv;
             if (sg.flags) sg.flags[qi] = fv;
@@ -1097,7 +1272,7 @@ pndf_status launch_eval_noalloc(const pndf_hierarchy *h, const pndf_query *q, in
     void *scratch = nullptr;
     if (noalloc_scratch(&scratch) != cudaSuccess) return PNDF_ERR_CUDA;
     const MapDesc &d = h->d;
-    pndf_eval_config cfg{PNDF_MODE_HIERARCHY, PNDF_SORT_DEFAULT, 0, 0, nullptr, nullptr};
+    pndf_eval_config cfg{PNDF_MODE_HIERARCHY, PNDF_SORT_DEFAULT, 0, 0, 0.f, 0, nullptr, nullptr};
     char *base = static_cast<char *>(scratch);
     auto *cursor = reinterpret_cast<unsigned long long *>(base);
     auto *hist = reinterpret_cast<uint32_t *>(base + kNoallocHistOff);
@@ -1110,13 +1285,13 @@ pndf_status launch_eval_noalloc(const pndf_hierarchy *h, const pndf_query *q, in
     if (e != cudaSuccess) return PNDF_ERR_CUDA;
     if (d.bounds_fmt == PNDF_BOUNDS_F32)
         e = d.texel_fmt == PNDF_TEXEL_F32X2
-                ? dispatch_stats<PNDF_BOUNDS_F32, PNDF_TEXEL_F32X2>(d, q, order, nq, D, flags, nullptr, cursor, cfg, s)
-                : dispatch_stats<PNDF_BOUNDS_F32, PNDF_TEXEL_F16X2>(d, q, order, nq, D, flags, nullptr, cursor, cfg, s);
+                ? dispatch_stats<PNDF_BOUNDS_F32, PNDF_TEXEL_F32X2>(d, h->c, q, order, nq, D, flags, nullptr, cursor, cfg, s)
+                : dispatch_stats<PNDF_BOUNDS_F32, PNDF_TEXEL_F16X2>(d, h->c, q, order, nq, D, flags, nullptr, cursor, cfg, s);
     else
         e = d.texel_fmt == PNDF_TEXEL_F32X2
-                ? dispatch_stats<PNDF_BOUNDS_F16_OUTWARD, PNDF_TEXEL_F32X2>(d, q, order, nq, D, flags, nullptr, cursor,
+                ? dispatch_stats<PNDF_BOUNDS_F16_OUTWARD, PNDF_TEXEL_F32X2>(d, h->c, q, order, nq, D, flags, nullptr, cursor,
                                                                          cfg, s)
-                : dispatch_stats<PNDF_BOUNDS_F16_OUTWARD, PNDF_TEXEL_F16X2>(d, q, order, nq, D, flags, nullptr, cursor,
+                : dispatch_stats<PNDF_BOUNDS_F16_OUTWARD, PNDF_TEXEL_F16X2>(d, h->c, q, order, nq, D, flags, nullptr, cursor,
                                                                          cfg, s);
     return e == cudaSuccess ? PNDF_OK : PNDF_ERR_CUDA;
 }

@@ -41,12 +41,13 @@ class PndfError(RuntimeError):
 
 class _BuildParams(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("texel_fmt", ctypes.c_int32), ("bounds_fmt", ctypes.c_int32),
-                ("leaf_level", ctypes.c_int32)]
+                ("leaf_level", ctypes.c_int32), ("clusters", ctypes.c_int32)]
 
 
 class _EvalConfig(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("sort", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32), ("ev_begin", ctypes.c_void_p), ("ev_end", ctypes.c_void_p)]
+                ("ctas_per_sm", ctypes.c_int32), ("tau", ctypes.c_float), ("reserved", ctypes.c_int32),
+                ("ev_begin", ctypes.c_void_p), ("ev_end", ctypes.c_void_p)]
 
 
 class _Segment(ctypes.Structure):
@@ -72,6 +73,7 @@ def _load() -> ctypes.CDLL:
         "pndf_free_hierarchy": ([vp], None),
         "pndf_update_hierarchy": ([vp, vp, vp], i32),
         "pndf_hierarchy_bytes": ([vp], ctypes.c_size_t),
+        "pndf_cluster_level": ([vp, i32, vp, vp, vp], i32),
         "pndf_eval_batch": ([vp, vp, i64, vp, vp, vp, vp], i32),
         "pndf_eval_batch_ex": ([vp, vp, i64, vp, vp, vp, ctypes.POINTER(_EvalConfig), vp], i32),
         "pndf_eval_batch_host": ([vp, vp, i64, vp, vp], i32),
@@ -129,12 +131,14 @@ def _need(t: torch.Tensor, name: str, dtype=None, device=True, shape_last=None):
 class Hierarchy:
     """A built pyramid (library-owned device memory) plus the map's size/format."""
 
-    def __init__(self, handle: int, n: int, texel_fmt: int, bounds_fmt: int, device: torch.device):
+    def __init__(self, handle: int, n: int, texel_fmt: int, bounds_fmt: int, device: torch.device,
+                 clusters: bool = False):
         self.handle = handle
         self.n = n
         self.texel_fmt = texel_fmt
         self.bounds_fmt = bounds_fmt
         self.device = device
+        self.clusters = clusters
 
     @property
     def nbytes(self) -> int:
@@ -152,8 +156,10 @@ class Hierarchy:
             pass
 
 
-def pndf_build_hierarchy(texels: torch.Tensor, bounds_fmt: int = PNDF_BOUNDS_F32, stream=None) -> Hierarchy:
-    """texels: (N, N, 2) float32 or float16 CUDA tensor, texel (i, j) at [j, i]."""
+def pndf_build_hierarchy(texels: torch.Tensor, bounds_fmt: int = PNDF_BOUNDS_F32, stream=None,
+                         clusters: bool = False) -> Hierarchy:
+    """texels: (N, N, 2) float32 or float16 CUDA tensor, texel (i, j) at [j, i].
+    clusters: also build the cluster hierarchy (Sec. 4.3, Eq. 7-8) for tau > 0."""
     _need(texels, "texels", shape_last=2)
     if texels.dim() != 3 or texels.shape[0] != texels.shape[1]:
         raise ValueError("texels must be (N, N, 2)")
@@ -163,12 +169,12 @@ def pndf_build_hierarchy(texels: torch.Tensor, bounds_fmt: int = PNDF_BOUNDS_F32
         tf = PNDF_TEXEL_F16X2
     else:
         raise ValueError("texels must be float32 or float16")
-    p = _BuildParams(int(texels.shape[0]), tf, int(bounds_fmt), 0)
+    p = _BuildParams(int(texels.shape[0]), tf, int(bounds_fmt), 0, int(bool(clusters)))
     h = ctypes.c_void_p()
     with torch.cuda.device(texels.device):
         _check("pndf_build_hierarchy", LIB.pndf_build_hierarchy(_ptr(texels), ctypes.byref(p), _stream(stream),
                                                                 ctypes.byref(h)))
-    return Hierarchy(h.value, int(texels.shape[0]), tf, int(bounds_fmt), texels.device)
+    return Hierarchy(h.value, int(texels.shape[0]), tf, int(bounds_fmt), texels.device, bool(clusters))
 
 
 def pndf_update_hierarchy(h: Hierarchy, texels: torch.Tensor, stream=None) -> Hierarchy:
@@ -186,6 +192,27 @@ def pndf_free_hierarchy(h: Hierarchy):
     h.free()
 
 
+def top_level(n: int) -> int:
+    """Pyramid height L: the smallest L >= 2 with 2^L >= n - 1 quads per side."""
+    L = 0
+    while (1 << L) < n - 1:
+        L += 1
+    return max(L, 2)
+
+
+def pndf_cluster_level(h: Hierarchy, level: int, stream=None):
+    """Level `level` of the cluster hierarchy: records (S, S, 8) float32 as
+    (c00, d10, d01, d11) pairs with corners c = c00 + d, and residuals (S, S),
+    indexed [J, I] (S = 2^(L - level))."""
+    S = 1 << (top_level(h.n) - level)
+    rec = torch.empty(S, S, 8, dtype=torch.float32, device=h.device)
+    e = torch.empty(S, S, dtype=torch.float32, device=h.device)
+    with torch.cuda.device(h.device):
+        _check("pndf_cluster_level", LIB.pndf_cluster_level(h.handle, int(level), _ptr(rec), _ptr(e),
+                                                            _stream(stream)))
+    return rec, e
+
+
 def _queries(q: torch.Tensor):
     _need(q, "queries", dtype=torch.float32, shape_last=8)
     return q.shape[0]
@@ -194,7 +221,7 @@ def _queries(q: torch.Tensor):
 def pndf_eval_batch(h: Hierarchy, queries: torch.Tensor, out: torch.Tensor | None = None,
                     flags: torch.Tensor | None = None, stats: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     """queries: (nq, 8) float32 CUDA tensor (x, y, sxx, sxy, syy, ms, mt, pad).
-    Returns D (nq,) float32.  flags: optional (nq,) int32; stats: optional (nq, 8) int32."""
+    Returns D (nq,) float32.  flags: optional (nq,) int32; stats: optional (nq, STATS_FIELDS) int32."""
     return pndf_eval_batch_ex(h, queries, out=out, flags=flags, stats=stats, stream=stream)
 
 
@@ -215,10 +242,15 @@ PNDF_SORT_LEVEL_NORMAL_TILE = 4
 PNDF_SORT_DEFAULT = PNDF_SORT_LEVEL_TILE
 
 
+STATS_FIELDS = 10  # pndf_query_stats: nodes, leaf_blocks, tri_tests, hits, hit_hash, fp64_tris, degenerate,
+                   # quads, cluster_checks, clusters
+
+
 def pndf_eval_batch_ex(h: Hierarchy, queries: torch.Tensor, out=None, flags=None, stats=None, mode: int = 0,
                        sort: int = PNDF_SORT_DEFAULT, warps_per_cta: int = 0, ctas_per_sm: int = 0, stream=None,
-                       ev_begin=None, ev_end=None) -> torch.Tensor:
-    """ev_begin / ev_end: optional torch.cuda.Event recorded around the traversal kernel."""
+                       ev_begin=None, ev_end=None, tau: float = 0.0) -> torch.Tensor:
+    """ev_begin / ev_end: optional torch.cuda.Event recorded around the traversal kernel.
+    tau > 0: the cluster cut of Sec. 4.3 (the hierarchy must be built with clusters=True)."""
     nq = _queries(queries)
     if out is None:
         out = torch.empty(nq, dtype=torch.float32, device=queries.device)
@@ -226,8 +258,8 @@ def pndf_eval_batch_ex(h: Hierarchy, queries: torch.Tensor, out=None, flags=None
     if flags is not None:
         _need(flags, "flags", dtype=torch.int32)
     if stats is not None:
-        _need(stats, "stats", dtype=torch.int32, shape_last=8)
-    cfg = _EvalConfig(int(mode), int(sort), int(warps_per_cta), int(ctas_per_sm),
+        _need(stats, "stats", dtype=torch.int32, shape_last=STATS_FIELDS)
+    cfg = _EvalConfig(int(mode), int(sort), int(warps_per_cta), int(ctas_per_sm), float(tau), 0,
                       _event_handle(ev_begin), _event_handle(ev_end))
     with torch.cuda.device(queries.device):
         _check("pndf_eval_batch_ex", LIB.pndf_eval_batch_ex(h.handle, _ptr(queries), nq, _ptr(out), _ptr(flags),

@@ -73,12 +73,12 @@ def test_argument_errors_without_device(lib):
 def test_build_params_invalid_n(lib):
     class P(ctypes.Structure):
         _fields_ = [("n", ctypes.c_int32), ("texel_fmt", ctypes.c_int32), ("bounds_fmt", ctypes.c_int32),
-                    ("leaf_level", ctypes.c_int32)]
+                    ("leaf_level", ctypes.c_int32), ("clusters", ctypes.c_int32)]
 
     vp = ctypes.c_void_p
     lib.pndf_build_hierarchy.argtypes = [vp, ctypes.POINTER(P), vp, ctypes.POINTER(vp)]
     out = vp()
     dummy = ctypes.c_void_p(256)  # never dereferenced: validation fails first
-    for bad in (P(1, 0, 0, 0), P(16385, 0, 0, 0), P(64, 7, 0, 0), P(64, 0, 9, 0)):
+    for bad in (P(1, 0, 0, 0, 0), P(16385, 0, 0, 0, 0), P(64, 7, 0, 0, 0), P(64, 0, 9, 0, 0), P(64, 0, 0, 0, 2)):
         assert lib.pndf_build_hierarchy(dummy, ctypes.byref(bad), None, ctypes.byref(out)) == 1
-    assert lib.pndf_build_hierarchy(dummy, ctypes.byref(P(64, 0, 0, 3)), None, ctypes.byref(out)) == 6
+    assert lib.pndf_build_hierarchy(dummy, ctypes.byref(P(64, 0, 0, 3, 0)), None, ctypes.byref(out)) == 6

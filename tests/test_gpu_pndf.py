@@ -34,7 +34,7 @@ def run(P, st, q, bounds=0, mode=0, sort=1, warps=0, stats=True):
     h = P.pndf_build_hierarchy(st.to(DEV), bounds_fmt=bounds)
     qd = q.to(DEV)
     flags = torch.zeros(q.shape[0], dtype=torch.int32, device=DEV)
-    stt = torch.zeros(q.shape[0], 8, dtype=torch.int32, device=DEV) if stats else None
+    stt = torch.zeros(q.shape[0], P.STATS_FIELDS, dtype=torch.int32, device=DEV) if stats else None
     D = P.pndf_eval_batch_ex(h, qd, flags=flags, stats=stt, mode=mode, sort=sort, warps_per_cta=warps)
     torch.cuda.synchronize()
     out = (D.cpu().double().numpy(), flags.cpu().numpy().astype(np.uint32),
@@ -210,7 +210,7 @@ def test_scratch2048_1m_sampled(P):
     q = synth.make_queries(st, cfg["queries"], cfg["mix"], cfg["seed"])
     for bounds in (0, 1):
         h = P.pndf_build_hierarchy(st, bounds_fmt=bounds)
-        stt = torch.zeros(q.shape[0], 8, dtype=torch.int32, device=DEV)
+        stt = torch.zeros(q.shape[0], P.STATS_FIELDS, dtype=torch.int32, device=DEV)
         D = P.pndf_eval_batch(h, q, stats=stt).cpu().double().numpy()
         stt = stt.cpu().numpy().astype(np.int64)
         h.free()
@@ -240,7 +240,7 @@ def test_flake8192_4m_sampled(P):
     Ds = {}
     for bounds in (0, 1):
         h = P.pndf_build_hierarchy(st, bounds_fmt=bounds)
-        stt = torch.zeros(q.shape[0], 8, dtype=torch.int32, device=DEV)
+        stt = torch.zeros(q.shape[0], P.STATS_FIELDS, dtype=torch.int32, device=DEV)
         D = P.pndf_eval_batch(h, q, stats=stt).cpu().double().numpy()
         stt = stt.cpu().numpy().astype(np.int64)
         h.free()
