@@ -4,8 +4,8 @@ the FP64 oracle, through the C ABI.
 The fits (corner normals and residuals of every node) are compared node by
 node; D with the cut is held to the same per-query bar as the exact path on
 every query the oracle does not flag (edge and cut ties, and residuals or
-entry radii within 1e-4 of their thresholds, where FP32 and FP64 may decide
-the cut differently).
+entry radii within 1e-5 / 3e-5 of their thresholds on a node whose normal
+hull holds m, where FP32 and FP64 may decide the cut differently).
 """
 
 import numpy as np
@@ -50,8 +50,8 @@ def maps():
 @pytest.mark.parametrize("name", ["bumps256", "scratch257", "flakes256"])
 def test_cluster_fits_match_oracle(P, name):
     """Every node's corner normals and residual agree with the oracle's FP64
-    fit (the GPU rolls FP64 moments up the tree; the oracle integrates each
-    node directly)."""
+    fit (the GPU combines its children's quadratic forms up the tree; the
+    oracle integrates each node directly)."""
     st = maps()[name]
     fits = oracle.cluster_fits(st)
     for bf in (0, 1):
