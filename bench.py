@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--map-size", dest="n", type=int, default=synth.FLAKE_8192["n"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cluster-taus", default="1e-4,1e-3",
+                    help="cluster cut thresholds to measure on the same workload ('' = skip)")
     ap.add_argument("--serve-batches", type=int, default=2000, help="serving workload size (0 = skip serving)")
     ap.add_argument("--serve-load", type=float, default=0.8, help="offered load, fraction of plain FP32 capacity")
     ap.add_argument("--mixed-requests", type=int, default=4096,
@@ -383,6 +385,66 @@ def run_serving(args, dev):
 
 
 # ---------------------------------------------------------------------------
+# Cluster cut (Sec. 4.3, Eq. 7-8): the approximate variant on the same workload
+# ---------------------------------------------------------------------------
+
+def run_cluster_cut(args, world, st, q, D_exact, exact_kernel_ms):
+    """Queries/s of the cluster cut for each tau on the bench workload (hierarchy
+    with clusters built once; a step = key/sort + traversal with the cut +
+    unpermute), the work it saves, the build cost of the cluster hierarchy, and
+    how far its densities move from the exact ones (the surrogate map
+    approximates the normal map)."""
+    from paper_2505_08985_gb300 import pndf
+    dev = q.device
+    nq = q.shape[0]
+    stream = torch.cuda.current_stream()
+    D_ref = D_exact.clone()
+    D = torch.empty_like(D_ref)
+    h = pndf.pndf_build_hierarchy(st, bounds_fmt=pndf.PNDF_BOUNDS_F16_OUTWARD, clusters=True)
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pndf.pndf_update_hierarchy(h, st)
+    b0.record(stream)
+    for _ in range(3):
+        pndf.pndf_update_hierarchy(h, st)
+    b1.record(stream)
+    torch.cuda.synchronize()
+    out = {"workload": WORKLOAD, "bounds": "fp16 outward-rounded (widened to hold the cluster corners)",
+           "hierarchy_bytes": h.nbytes, "build_ms": b0.elapsed_time(b1) / 3, "per_tau": {}}
+    pos = D_ref > 0
+    for tau in [float(t) for t in args.cluster_taus.split(",") if t.strip()]:
+        stt = torch.zeros(nq, pndf.STATS_FIELDS, dtype=torch.int32, device=dev)
+        pndf.pndf_eval_batch_ex(h, q, out=D, stats=stt, tau=tau)
+        s = stt.to(torch.int64).sum(0).cpu().tolist()
+        del stt
+        for _ in range(args.warmup):
+            pndf.pndf_eval_batch_ex(h, q, out=D, tau=tau)
+        kb = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ke = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        barrier(world)
+        t0.record(stream)
+        for k in range(args.steps):
+            pndf.pndf_eval_batch_ex(h, q, out=D, tau=tau, ev_begin=kb[k], ev_end=ke[k])
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms = max_over_ranks(world, t0.elapsed_time(t1))
+        kms = sum(a.elapsed_time(b) for a, b in zip(kb, ke)) / args.steps
+        diff = (D - D_ref).abs()
+        out["per_tau"][f"{tau:g}"] = {
+            "value": sum_over_ranks(world, float(nq * args.steps)) / (ms / 1e3), "unit": UNIT,
+            "ms_per_step": ms / args.steps, "traverse_kernel_ms": kms,
+            "traversal_speedup_vs_exact": exact_kernel_ms / kms,
+            "work_per_query": {"nodes": s[0] / nq, "quads": s[7] / nq, "tri_tests": s[2] / nq,
+                               "cluster_checks": s[8] / nq, "clusters": s[9] / nq, "hits": s[3] / nq},
+            "rel_l1_vs_exact": float(diff.sum() / D_ref.abs().sum()),
+            "frac_queries_off_by_1pct": float((diff[pos] > 0.01 * D_ref[pos]).float().mean()),
+        }
+    h.free()
+    return out
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 
@@ -478,6 +540,7 @@ def run_gpu(args, world, rank, local):
 
     # roofline of the dominant kernel (traversal + leaf test), per launch
     kavg16 = sum(kms16) / len(kms16)
+    cluster = run_cluster_cut(args, world, st, q, D, kavg16) if args.cluster_taus else None
     peak, peak_kind = hbm_peak()
     achieved = work["f16"]["bytes"] / (kavg16 / 1e3) / 1e9
     traffic = committed_traffic("f16")
@@ -504,6 +567,8 @@ def run_gpu(args, world, rank, local):
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
+    if cluster:
+        line["cluster_cut"] = cluster
 
     if args.serve_batches > 0 or args.mixed_requests > 0:
         del st, q, D, st_h, q_h, D_h, st_d
