@@ -356,13 +356,15 @@ def run_serving(args, dev):
     sample = requests([0.0] * ns)
     tune = serve.autotune(h16, sample, arrivals=serve.poisson_arrivals(ns, rate, seed=5))
     batcher = serve.ContinuousBatcher(h16, step_queries=tune.step_queries, warps_per_cta=tune.warps_per_cta,
-                                      ctas_per_sm=tune.ctas_per_sm)
+                                      ctas_per_sm=tune.ctas_per_sm, sort=tune.sort)
     served_cap = batcher.run(requests([0.0] * n), realtime=False)
     arrivals = serve.poisson_arrivals(n, rate, seed=17)
     served = batcher.run(requests(arrivals), realtime=True)
     steps = batcher.steps
     batcher.close()
     plain = serve.run_plain(h32, requests(arrivals), realtime=True)
+    # context: the plain path with each batch kept in arrival order (no sort)
+    plain_unsorted_cap = serve.run_plain(h32, requests([0.0] * n), realtime=False, sort=pndf.PNDF_SORT_NONE)
     for h in h16 + h32:
         h.free()
     del qs
@@ -374,11 +376,12 @@ def run_serving(args, dev):
         "served_fp16": {k: served[k] for k in keep},
         "plain_fp32": {k: plain[k] for k in keep},
         "capacity_queries_per_s": {"served_fp16": served_cap["queries_per_s"],
-                                   "plain_fp32": plain_cap["queries_per_s"]},
+                                   "plain_fp32": plain_cap["queries_per_s"],
+                                   "plain_fp32_unsorted": plain_unsorted_cap["queries_per_s"]},
         "autotune": {"objective": "lowest p99 on the first batches at the target load",
                      "step_queries": tune.step_queries, "warps_per_cta": tune.warps_per_cta,
-                     "ctas_per_sm": tune.ctas_per_sm,
-                     "table [step, ctas_per_sm, warps, p99_ms, q/s]": tune.table},
+                     "ctas_per_sm": tune.ctas_per_sm, "sort": tune.sort,
+                     "table [step, ctas_per_sm, warps, sort, p99_ms, q/s]": tune.table},
         "steps_last_run": steps,
         "wall_s": time.perf_counter() - t0,
     }

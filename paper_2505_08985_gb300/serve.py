@@ -2,8 +2,10 @@
 
 Requests (a batch of queries on one map) arrive over time.  The batcher
 admits arrived requests while their working buffers (evaluation order and
-results, 8 bytes per query) fit a device-memory budget, sorts each once on a
-copy stream, and runs steps: each step takes up to `step_queries` queries from
+results, 8 bytes per query) fit a device-memory budget, optionally sorts each
+once on a copy stream (queries that arrive in a coherent order, such as a
+camera's pixels, run faster as they come; the autotuner decides), and runs
+steps: each step takes up to `step_queries` queries from
 the admitted requests in arrival order (a large request spans several steps;
 small ones share a step) and evaluates them in one persistent kernel launch
 replayed from a CUDA graph (pndf_server_step).  Up to slots - 1 steps are in flight,
@@ -15,7 +17,8 @@ that holds its last queries, on one clock: the device timeline anchored by an
 event recorded when the run starts.
 
 The plain baseline launches each batch alone with pndf_eval_batch (FP32
-bounds, no graphs, no sharing of launches) in arrival order.
+bounds, no graphs, no sharing of launches, the library's default query sort)
+in arrival order.
 """
 
 from __future__ import annotations
@@ -74,8 +77,9 @@ class ContinuousBatcher:
     """Continuous batching over `maps` (same texel and bounds formats)."""
 
     def __init__(self, maps, step_queries: int = 1 << 20, memory_budget: int = 2 << 30, max_segments: int = 1024,
-                 warps_per_cta: int = 0, ctas_per_sm: int = 0, slots: int = 4):
+                 warps_per_cta: int = 0, ctas_per_sm: int = 0, slots: int = 4, sort: bool = True):
         self.maps = list(maps)
+        self.sort = bool(sort)
         self.device = self.maps[0].device
         self.step_queries = int(step_queries)
         self.budget = int(memory_budget)
@@ -92,11 +96,12 @@ class ContinuousBatcher:
 
     def _admit(self, r: Request):
         with torch.cuda.stream(self.copy_stream):
-            r.order = pndf.pndf_sort_queries(self.maps[r.map], r.queries, stream=self.copy_stream)
+            r.order = pndf.pndf_sort_queries(self.maps[r.map], r.queries, stream=self.copy_stream) if self.sort else None
             r.D = torch.empty(r.n, dtype=torch.float32, device=self.device)
             r.ready = torch.cuda.Event()
             r.ready.record(self.copy_stream)
-        r.order.record_stream(self.step_stream)
+        if r.order is not None:
+            r.order.record_stream(self.step_stream)
         r.D.record_stream(self.step_stream)
         r.queries.record_stream(self.copy_stream)
         r.queries.record_stream(self.step_stream)
@@ -170,8 +175,9 @@ class ContinuousBatcher:
         return summarize(reqs, min(r.arrival for r in reqs), t_last)
 
 
-def run_plain(maps, requests, realtime: bool = True):
-    """Baseline: each batch launched alone (pndf_eval_batch) in arrival order."""
+def run_plain(maps, requests, realtime: bool = True, sort: int = pndf.PNDF_SORT_DEFAULT):
+    """Baseline: each batch launched alone (pndf_eval_batch) in arrival order;
+    sort = the query order within a batch (the library default unless given)."""
     reqs = sorted(requests, key=lambda r: r.arrival)
     dev = maps[0].device
     stream = torch.cuda.Stream(dev)
@@ -187,7 +193,7 @@ def run_plain(maps, requests, realtime: bool = True):
                 time.sleep(wait)
         with torch.cuda.stream(stream):
             r.D = torch.empty(r.n, dtype=torch.float32, device=dev)
-            pndf.pndf_eval_batch(maps[r.map], r.queries, out=r.D, stream=stream)
+            pndf.pndf_eval_batch_ex(maps[r.map], r.queries, out=r.D, sort=sort, stream=stream)
             r.done = torch.cuda.Event(enable_timing=True)
             r.done.record(stream)
     torch.cuda.synchronize(dev)
@@ -210,31 +216,35 @@ class TuneResult:
     warps_per_cta: int
     p99_ms: float
     queries_per_s: float
+    sort: bool = True
     table: list = field(default_factory=list)
 
 
 def autotune(maps, sample, arrivals=None, step_candidates=(1 << 16, 1 << 18, 1 << 20, 1 << 22),
-             cta_candidates=(0,), warp_candidates=(8, 4)):
-    """Pick step size and launch shape for the served path on a sample of
-    requests.  With `arrivals` (a Poisson stream at the target load) the
-    candidate with the lowest p99 latency wins (ties broken by throughput);
-    without, the highest saturated throughput wins."""
+             cta_candidates=(0,), warp_candidates=(8, 4), sort_candidates=(True, False)):
+    """Pick step size, launch shape and whether to sort each request for the
+    served path on a sample of requests.  With `arrivals` (a Poisson stream at
+    the target load) the candidate with the lowest p99 latency wins (ties
+    broken by throughput); without, the highest saturated throughput wins."""
     best = None
     table = []
-    for ctas in cta_candidates:
-        for warps in warp_candidates:
-            for step in step_candidates:
-                b = ContinuousBatcher(maps, step_queries=step, warps_per_cta=warps, ctas_per_sm=ctas)
-                b.run(sample, realtime=False)  # warm
-                if arrivals is not None:
-                    for r, a in zip(sample, arrivals):
-                        r.arrival = a
-                s = b.run(sample, realtime=arrivals is not None)
-                b.close()
-                table.append((step, ctas, warps, s["p99_ms"], s["queries_per_s"]))
-                key = (s["p99_ms"], -s["queries_per_s"]) if arrivals is not None else (-s["queries_per_s"],)
-                if best is None or key < best[0]:
-                    best = (key, TuneResult(step, ctas, warps, s["p99_ms"], s["queries_per_s"]))
+    for sort in sort_candidates:
+        for ctas in cta_candidates:
+            for warps in warp_candidates:
+                for step in step_candidates:
+                    b = ContinuousBatcher(maps, step_queries=step, warps_per_cta=warps, ctas_per_sm=ctas, sort=sort)
+                    for r in sample:
+                        r.arrival = 0.0
+                    b.run(sample, realtime=False)  # warm
+                    if arrivals is not None:
+                        for r, a in zip(sample, arrivals):
+                            r.arrival = a
+                    s = b.run(sample, realtime=arrivals is not None)
+                    b.close()
+                    table.append((step, ctas, warps, int(sort), s["p99_ms"], s["queries_per_s"]))
+                    key = (s["p99_ms"], -s["queries_per_s"]) if arrivals is not None else (-s["queries_per_s"],)
+                    if best is None or key < best[0]:
+                        best = (key, TuneResult(step, ctas, warps, s["p99_ms"], s["queries_per_s"], sort))
     for r in sample:
         r.arrival = 0.0
     out = best[1]

@@ -61,11 +61,22 @@ def test_served_equals_alone(P, maps_and_requests):
         assert torch.equal(r.D.cpu(), a), r.rid
     assert np.isfinite(s2["p99_ms"]) and s2["p99_ms"] >= s2["p50_ms"] >= 0
     b.close()
+    # requests kept in arrival order (no per-request sort) give the same results
+    b = serve.ContinuousBatcher(hs, step_queries=20000, max_segments=64, sort=False)
+    for r in reqs:
+        r.arrival = 0.0
+    b.run(reqs, realtime=False)
+    for r, a in zip(reqs, alone):
+        assert torch.equal(r.D.cpu(), a), r.rid
+    b.close()
     # the plain per-batch path agrees too
     sp = serve.run_plain(hs, reqs, realtime=False)
     for r, a in zip(reqs, alone):
         assert torch.equal(r.D.cpu(), a), r.rid
     assert sp["requests"] == len(reqs)
+    serve.run_plain(hs, reqs, realtime=False, sort=P.PNDF_SORT_NONE)
+    for r, a in zip(reqs, alone):
+        assert torch.equal(r.D.cpu(), a), r.rid
     for h in hs:
         h.free()
 
@@ -101,3 +112,19 @@ def test_server_rejects_mixed_formats(P):
     srv.destroy()
     a.free()
     b.free()
+
+
+def test_autotune_picks_from_its_table(P, maps_and_requests):
+    """The autotuner tries every candidate (step size, warps, sort or arrival
+    order) and returns the one with the lowest p99 at the offered load."""
+    from paper_2505_08985_gb300 import serve
+    sts, reqs = maps_and_requests
+    hs = [P.pndf_build_hierarchy(st, bounds_fmt=P.PNDF_BOUNDS_F16_OUTWARD) for st in sts]
+    sample = [serve.Request(rid=r.rid, map=r.map, queries=r.queries, arrival=0.0) for r in reqs[:20]]
+    arr = serve.poisson_arrivals(len(sample), rate=4000.0, seed=2)
+    t = serve.autotune(hs, sample, arrivals=arr, step_candidates=(1 << 14, 1 << 16), warp_candidates=(8,))
+    assert len(t.table) == 4 and {row[3] for row in t.table} == {0, 1}
+    best = min(t.table, key=lambda row: (row[4], -row[5]))
+    assert (t.step_queries, t.warps_per_cta, int(t.sort)) == (best[0], best[2], best[3])
+    for h in hs:
+        h.free()
