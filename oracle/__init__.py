@@ -6,7 +6,8 @@ CUDA package and the CUDA package imports nothing from it.
 
 Functions
 ---------
-pndf(st, queries)          -> D (float64), flags (uint32), hits (int64), hit_hash (uint32)
+pndf(st, queries, kernel=0) -> D (float64), flags (uint32), hits (int64), hit_hash (uint32);
+                              kernel 0 Gaussian (4-sigma cut), 1 disk, 2 box (1.5 sigma)
 cluster_fits(st)           -> ClusterFits: corner normals and residual of every node, Eq. 7-8
 cluster_fit(st, l, I, J)   -> (c (4, 2), e) for one node, or None outside the map
 pndf_cluster(st, queries, tau, fits=None) -> as pndf, with the cluster cut e <= r_x r_y tau
@@ -48,6 +49,7 @@ F_TINY = 8
 F_INVALID = 16
 F_NEAR_TAU = 32
 F_EXCLUDE = F_NEAR_EDGE | F_NEAR_CUT | F_DEGENERATE | F_INVALID | F_NEAR_TAU
+KERNEL_GAUSS, KERNEL_DISK, KERNEL_BOX = 0, 1, 2  # footprint kernels (see pndf_oracle.c)
 GL_POINTS = 16
 
 _lock = threading.Lock()
@@ -139,7 +141,8 @@ class Oracle:
         dp = ctypes.POINTER(ctypes.c_double)
         u32p = ctypes.POINTER(ctypes.c_uint32)
         i64p = ctypes.POINTER(ctypes.c_int64)
-        lib.oracle_pndf.argtypes = [dp, ctypes.c_int, dp, ctypes.c_int64, ctypes.c_int64, dp, u32p, i64p, u32p]
+        lib.oracle_pndf.argtypes = [dp, ctypes.c_int, dp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, dp, u32p, i64p,
+                                    u32p]
         lib.oracle_pndf.restype = None
         lib.oracle_projarea.argtypes = [dp, ctypes.c_int, dp, dp, ctypes.c_int64, ctypes.c_int64, dp, dp, dp,
                                         ctypes.c_int]
@@ -152,12 +155,12 @@ class Oracle:
         lib.oracle_cluster_build.restype = None
         lib.oracle_cluster_hulls.argtypes = [dp, ctypes.c_int, dp, dp, dp]
         lib.oracle_cluster_hulls.restype = None
-        lib.oracle_pndf_cluster.argtypes = [dp, ctypes.c_int, dp, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
-                                            dp, dp, dp, dp, u32p, i64p, u32p]
+        lib.oracle_pndf_cluster.argtypes = [dp, ctypes.c_int, dp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                            ctypes.c_double, dp, dp, dp, dp, u32p, i64p, u32p]
         lib.oracle_pndf_cluster.restype = None
         self.lib = lib
 
-    def pndf(self, st, queries, threads: int | None = None):
+    def pndf(self, st, queries, threads: int | None = None, kernel: int = 0):
         lib = self.lib
         stm = _as_map(st)
         q = _as_queries(queries)
@@ -169,7 +172,7 @@ class Oracle:
         N = stm.shape[0]
 
         def run(r):
-            lib.oracle_pndf(_ptr(stm, ctypes.c_double), N, _ptr(q, ctypes.c_double), r[0], r[1],
+            lib.oracle_pndf(_ptr(stm, ctypes.c_double), N, _ptr(q, ctypes.c_double), r[0], r[1], int(kernel),
                             _ptr(D, ctypes.c_double), _ptr(flags, ctypes.c_uint32),
                             _ptr(hits, ctypes.c_int64), _ptr(hh, ctypes.c_uint32))
 
@@ -207,7 +210,8 @@ class Oracle:
                                       _ptr(fits.e, ctypes.c_double), _ptr(fits.hull, ctypes.c_double))
         return fits
 
-    def pndf_cluster(self, st, queries, tau: float, fits: ClusterFits | None = None, threads: int | None = None):
+    def pndf_cluster(self, st, queries, tau: float, fits: ClusterFits | None = None, threads: int | None = None,
+                     kernel: int = 0):
         lib = self.lib
         stm = _as_map(st)
         q = _as_queries(queries)
@@ -222,7 +226,7 @@ class Oracle:
 
         def run(r):
             lib.oracle_pndf_cluster(_ptr(stm, ctypes.c_double), N, _ptr(q, ctypes.c_double), r[0], r[1],
-                                    float(tau), _ptr(fits.c, ctypes.c_double), _ptr(fits.e, ctypes.c_double),
+                                    int(kernel), float(tau), _ptr(fits.c, ctypes.c_double), _ptr(fits.e, ctypes.c_double),
                                     _ptr(fits.hull, ctypes.c_double), _ptr(D, ctypes.c_double), _ptr(flags, ctypes.c_uint32),
                                     _ptr(hits, ctypes.c_int64), _ptr(hh, ctypes.c_uint32))
 
@@ -270,8 +274,8 @@ def _get() -> Oracle:
     return _default
 
 
-def pndf(st, queries, threads: int | None = None):
-    return _get().pndf(st, queries, threads)
+def pndf(st, queries, threads: int | None = None, kernel: int = 0):
+    return _get().pndf(st, queries, threads, kernel)
 
 
 def projarea(st, queries, omega, threads: int | None = None):
@@ -290,5 +294,6 @@ def cluster_fits(st, threads: int | None = None) -> ClusterFits:
     return _get().cluster_fits(st, threads)
 
 
-def pndf_cluster(st, queries, tau: float, fits: ClusterFits | None = None, threads: int | None = None):
-    return _get().pndf_cluster(st, queries, tau, fits, threads)
+def pndf_cluster(st, queries, tau: float, fits: ClusterFits | None = None, threads: int | None = None,
+                 kernel: int = 0):
+    return _get().pndf_cluster(st, queries, tau, fits, threads, kernel)

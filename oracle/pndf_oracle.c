@@ -78,6 +78,53 @@ static void texel(const double *st, int N, int i, int j, double n[2])
     n[1] = st[((size_t)j * N + i) * 2 + 1];
 }
 
+/*
+ * Footprint kernels k_r(d), d = u - x, of Eq. 2 (the Gaussian of Sec. 5 and
+ * the disk and box filters of the kernel ablation, which match a Gaussian's
+ * (6 sigma)^2 footprint with a (3 sigma)^2 one), with S = [[sxx, sxy], [sxy,
+ * syy]] and q = d^T S^-1 d:
+ *   0 Gaussian: exp(-q/2) / (2 pi sqrt(det S)) where q <= 16, else 0;
+ *   1 disk: 1 / (2.25 pi sqrt(det S)) where q <= 1.5^2, else 0;
+ *   2 box: 1 / (9 sqrt(det S)) where |L^-1 d|_inf <= 1.5, S = L L^T (the
+ *     Cholesky factor; for S = sigma^2 I the square of side 3 sigma).
+ * Their supports' bounding-box half-widths (r_x, r_y): 4 (sqrt(sxx),
+ * sqrt(syy)); 1.5 (sqrt(sxx), sqrt(syy)); 1.5 (l11, |l21| + l22).  All lie
+ * inside the Gaussian's 4-sigma box.  A point within rounding of a disk or
+ * box edge flags the query like a Gaussian cut tie.
+ */
+enum { OK_GAUSS = 0, OK_DISK = 1, OK_BOX = 2 };
+#define ORACLE_SUPPORT_EPS 1e-5
+
+static void kernel_halfwidths(int kernel, double sxx, double sxy, double syy, double *rx, double *ry)
+{
+    if (kernel == OK_GAUSS) {
+        *rx = 4.0 * sqrt(sxx);
+        *ry = 4.0 * sqrt(syy);
+    } else if (kernel == OK_DISK) {
+        *rx = 1.5 * sqrt(sxx);
+        *ry = 1.5 * sqrt(syy);
+    } else {
+        double l11 = sqrt(sxx), l21 = sxy / l11, l22 = sqrt(syy - l21 * l21);
+        *rx = 1.5 * l11;
+        *ry = 1.5 * (fabs(l21) + l22);
+    }
+}
+
+/* Disk or box weight at d (q = d^T S^-1 d given); 0 outside the support. */
+static double flat_kernel(int kernel, double dx, double dy, double q, double sxx, double sxy, double syy,
+                          double det, uint32_t *flags)
+{
+    if (kernel == OK_DISK) {
+        if (fabs(q - 2.25) <= ORACLE_SUPPORT_EPS) *flags |= OF_NEAR_CUT;
+        return q <= 2.25 ? 1.0 / (2.25 * M_PI * sqrt(det)) : 0.0;
+    }
+    double l11 = sqrt(sxx), l21 = sxy / l11, l22 = sqrt(syy - l21 * l21);
+    double v1 = dx / l11, v2 = (dy - l21 * v1) / l22;
+    double vm = fmax(fabs(v1), fabs(v2));
+    if (fabs(vm - 1.5) <= ORACLE_SUPPORT_EPS) *flags |= OF_NEAR_CUT;
+    return vm <= 1.5 ? 1.0 / (9.0 * sqrt(det)) : 0.0;
+}
+
 /* Quads whose uv square [i, i+1] x [j, j+1] can meet the bounding box of the
  * 4-sigma ellipse; a generous superset is harmless (Eq. 5: triangles outside
  * the footprint contribute k_r = 0). */
@@ -101,7 +148,7 @@ static void quad_range(int N, double x, double y, double sxx, double syy,
  * bary(m, n(abc)) from signed areas (Tab. 1) and 2 ||n(abc)|| is the
  * Jacobian of Eq. 4, i.e. |(n_b - n_a) x (n_c - n_a)|.
  */
-static void pndf_one(const double *st, int N, const double *qq,
+static void pndf_one(const double *st, int N, const double *qq, int kernel,
                      double *D_out, uint32_t *flags_out, int64_t *nhits_out, uint32_t *hash_out)
 {
     double x = qq[0], y = qq[1], sxx = qq[2], sxy = qq[3], syy = qq[4], mx = qq[5], my = qq[6];
@@ -163,9 +210,18 @@ static void pndf_one(const double *st, int N, const double *qq,
                 double uy = ay * l0 + by * l1 + cy * l2;
                 double dx = ux - x, dy = uy - y;
                 double q = ia * dx * dx + 2.0 * ib * dx * dy + ic * dy * dy;
+                double J = fabs(A2);
+                if (kernel != OK_GAUSS) {
+                    double w = flat_kernel(kernel, dx, dy, q, sxx, sxy, syy, det, &flags);
+                    if (w == 0.0) continue;
+                    if (0.5 * J < ORACLE_TINY_AREA) flags |= OF_TINY;
+                    D += w / J;
+                    nh += 1;
+                    hsum += fmix32((uint32_t)(2u * ((uint32_t)j * (uint32_t)(N - 1) + (uint32_t)i) + (uint32_t)tri));
+                    continue;
+                }
                 if (fabs(q - ORACLE_QCUT) <= ORACLE_CUT_EPS) flags |= OF_NEAR_CUT;
                 if (q > ORACLE_QCUT) continue;
-                double J = fabs(A2);
                 if (0.5 * J < ORACLE_TINY_AREA) flags |= OF_TINY;
                 D += norm * exp(-0.5 * q) / J;
                 nh += 1;
@@ -180,12 +236,13 @@ static void pndf_one(const double *st, int N, const double *qq,
     *hash_out = hsum;
 }
 
-/* Evaluate queries [k0, k1).  Safe to call concurrently on disjoint ranges. */
-void oracle_pndf(const double *st, int N, const double *q, int64_t k0, int64_t k1,
+/* Evaluate queries [k0, k1) with footprint kernel `kernel` (OK_*).  Safe to
+ * call concurrently on disjoint ranges. */
+void oracle_pndf(const double *st, int N, const double *q, int64_t k0, int64_t k1, int kernel,
                  double *D, uint32_t *flags, int64_t *nhits, uint32_t *hsum)
 {
     for (int64_t k = k0; k < k1; ++k)
-        pndf_one(st, N, q + 7 * k, D + k, flags + k, nhits + k, hsum + k);
+        pndf_one(st, N, q + 7 * k, kernel, D + k, flags + k, nhits + k, hsum + k);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -698,8 +755,8 @@ void oracle_cluster_hulls(const double *st, int N, const double *c_all, const do
 
 struct cl_query {
     const double *st, *c_all, *e_all, *hull;
-    int N, L;
-    double x, y, ia, ib, ic, norm, mx, my, rx, ry, theta;
+    int N, L, kernel;
+    double x, y, ia, ib, ic, norm, mx, my, rx, ry, theta, sxx, sxy, syy, det;
     double D;
     uint32_t flags, hsum;
     int64_t nh;
@@ -730,11 +787,18 @@ static void cl_triangle(struct cl_query *Q, const double uv[3][2], const double 
     double uy = uv[0][1] * l0 + uv[1][1] * l1 + uv[2][1] * l2;
     double dx = ux - Q->x, dy = uy - Q->y;
     double q = Q->ia * dx * dx + 2.0 * Q->ib * dx * dy + Q->ic * dy * dy;
-    if (fabs(q - ORACLE_QCUT) <= ORACLE_CUT_EPS) Q->flags |= OF_NEAR_CUT;
-    if (q > ORACLE_QCUT) return;
     double J = fabs(A2) / (scale * scale);
+    double w;
+    if (Q->kernel != OK_GAUSS) {
+        w = flat_kernel(Q->kernel, dx, dy, q, Q->sxx, Q->sxy, Q->syy, Q->det, &Q->flags);
+        if (w == 0.0) return;
+    } else {
+        if (fabs(q - ORACLE_QCUT) <= ORACLE_CUT_EPS) Q->flags |= OF_NEAR_CUT;
+        if (q > ORACLE_QCUT) return;
+        w = Q->norm * exp(-0.5 * q);
+    }
     if (0.5 * fabs(A2) < ORACLE_TINY_AREA) Q->flags |= OF_TINY;
-    Q->D += Q->norm * exp(-0.5 * q) / J;
+    Q->D += w / J;
     Q->nh += 1;
     Q->hsum += fmix32(id);
 }
@@ -787,9 +851,9 @@ static void cl_visit(struct cl_query *Q, int l, int I, int J)
         for (int di = 0; di < 2; ++di) cl_visit(Q, l - 1, 2 * I + di, 2 * J + dj);
 }
 
-static void pndf_cluster_one(const double *st, int N, const double *qq, double tau, const double *c_all,
-                             const double *e_all, const double *hull, double *D_out, uint32_t *flags_out,
-                             int64_t *nhits_out, uint32_t *hash_out)
+static void pndf_cluster_one(const double *st, int N, const double *qq, int kernel, double tau,
+                             const double *c_all, const double *e_all, const double *hull, double *D_out,
+                             uint32_t *flags_out, int64_t *nhits_out, uint32_t *hash_out)
 {
     double sxx = qq[2], sxy = qq[3], syy = qq[4];
     double det = sxx * syy - sxy * sxy;
@@ -806,8 +870,9 @@ static void pndf_cluster_one(const double *st, int N, const double *qq, double t
     Q.x = qq[0]; Q.y = qq[1]; Q.mx = qq[5]; Q.my = qq[6];
     Q.ia = syy / det; Q.ib = -sxy / det; Q.ic = sxx / det;
     Q.norm = 1.0 / (2.0 * M_PI * sqrt(det));
-    Q.rx = 4.0 * sqrt(sxx);
-    Q.ry = 4.0 * sqrt(syy);
+    Q.kernel = kernel;
+    Q.sxx = sxx; Q.sxy = sxy; Q.syy = syy; Q.det = det;
+    kernel_halfwidths(kernel, sxx, sxy, syy, &Q.rx, &Q.ry);
     Q.theta = Q.rx * Q.ry * tau;
     /* entry level: smallest l >= 2 with 2^l >= max(r_x, r_y), at most L */
     double r = fmax(Q.rx, Q.ry);
@@ -826,13 +891,14 @@ static void pndf_cluster_one(const double *st, int N, const double *qq, double t
     *hash_out = Q.hsum;
 }
 
-/* P-NDF with the cluster cut for queries [k0, k1); tau <= 0 cuts nothing
+/* P-NDF with the cluster cut for queries [k0, k1) (footprint kernel as in
+ * oracle_pndf; r_x, r_y of the cut are its support half-widths); tau <= 0 cuts nothing
  * (exact D, summed in traversal order).  c_all / e_all come from
  * oracle_cluster_build for every level 2..L, hull from oracle_cluster_hulls. */
-void oracle_pndf_cluster(const double *st, int N, const double *q, int64_t k0, int64_t k1, double tau,
+void oracle_pndf_cluster(const double *st, int N, const double *q, int64_t k0, int64_t k1, int kernel, double tau,
                          const double *c_all, const double *e_all, const double *hull, double *D, uint32_t *flags,
                          int64_t *nhits, uint32_t *hsum)
 {
     for (int64_t k = k0; k < k1; ++k)
-        pndf_cluster_one(st, N, q + 7 * k, tau, c_all, e_all, hull, D + k, flags + k, nhits + k, hsum + k);
+        pndf_cluster_one(st, N, q + 7 * k, kernel, tau, c_all, e_all, hull, D + k, flags + k, nhits + k, hsum + k);
 }

@@ -10,7 +10,9 @@ misplaced per-triangle kernel sample, and a collapsed normal triangle
 treated as a point at its centroid.  For the cluster hierarchy (Eq. 7-8,
 App. A): the other cluster diagonal or hat functions, an unweighted fit, the
 squared residual, a cluster Jacobian without its 2^(2l) scale, swapped
-barycentric roles or corners, and a cut on the wrong footprint size.
+barycentric roles or corners, and a cut on the wrong footprint size.  For
+the disk and box kernels: a 3-sigma disk, the box sheared by the upper
+Cholesky factor, and the box normalised as a unit square.
 """
 
 import os
@@ -40,6 +42,24 @@ def cluster_mass_all_cut(m):
 def cluster_mass_mixed(m):
     cpins.test_cluster_mass_invariant(m, "mixed")
 
+
+def affine_disk(m):
+    pins.test_affine_closed_form_disk_box(m, 1)
+
+
+def affine_box(m):
+    pins.test_affine_closed_form_disk_box(m, 2)
+
+
+def mass_disk(m):
+    pins.test_mass_invariant_disk_box(m, 1)
+
+
+def mass_box(m):
+    pins.test_mass_invariant_disk_box(m, 2)
+
+
+KERNEL_PINS = [affine_disk, affine_box, mass_disk, mass_box, pins.test_binning_box_kernel]
 
 CLUSTER_PINS = [cpins.test_fit_recovers_piecewise_linear_data, cluster_dense_fit_level3, cluster_mass_all_cut,
                 cluster_mass_mixed, cpins.test_cluster_binning_with_anisotropic_cut,
@@ -75,6 +95,13 @@ MUTANTS = {
                                       "(a[1] + b[1] + cc[1]) / 3.0, w);")], AREA_PINS),
     "kernel_at_wrong_centroid": ([("double gx = i + (tri == 0 ? 1.0 / 3.0 : 2.0 / 3.0) - x;",
                                    "double gx = i + (tri == 0 ? 2.0 / 3.0 : 1.0 / 3.0) - x;")], AREA_PINS),
+    # disk and box footprint kernels
+    "disk_radius_3_sigma": ([("return q <= 2.25 ? 1.0 / (2.25 * M_PI * sqrt(det)) : 0.0;",
+                              "return q <= 9.0 ? 1.0 / (2.25 * M_PI * sqrt(det)) : 0.0;")], KERNEL_PINS),
+    "box_upper_cholesky": ([("double v1 = dx / l11, v2 = (dy - l21 * v1) / l22;",
+                             "double v2 = dy / l11, v1 = (dx - l21 * v2) / l22;")], KERNEL_PINS),
+    "box_norm_unit_square": ([("return vm <= 1.5 ? 1.0 / (9.0 * sqrt(det)) : 0.0;",
+                               "return vm <= 1.5 ? 1.0 / (4.0 * sqrt(det)) : 0.0;")], KERNEL_PINS),
     # cluster hierarchy (Eq. 7-8, App. A) and the tau cut
     "cluster_fit_main_diagonal": ([("        phi[0] = 1.0 - s - t; phi[1] = s; phi[2] = t; phi[3] = 0.0;",
                                     "        phi[0] = 1.0 - s; phi[1] = s - t; phi[2] = 0.0; phi[3] = t;"),

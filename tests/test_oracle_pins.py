@@ -399,3 +399,111 @@ def _check_uv_form(oracle_mod, st, q, w, rtol):
                     val = np.maximum(n[:, 0] * w[k, 0] + n[:, 1] * w[k, 1] + nz * w[k, 2], 0) / nz
                     tot += g * val.sum() / (K * K)
         assert abs(P[k] - tot) <= rtol * tot, (k, P[k], tot)
+
+
+# ---------------------------------------------------------------------------
+# disk and box footprint kernels (kernel ablation: (3 sigma)^2 footprints)
+# ---------------------------------------------------------------------------
+
+def support_weight(kernel, dx, dy, sxx, sxy, syy):
+    """Disk / box kernel from their definitions by library routines: the disk
+    is q = d^T S^-1 d <= 1.5^2 (numpy solve), the box |L^-1 d|_inf <= 1.5 with
+    L = numpy's Cholesky factor; each normalised by its support's area."""
+    out = np.zeros(len(dx))
+    for k in range(len(dx)):
+        S = np.array([[sxx[k], sxy[k]], [sxy[k], syy[k]]])
+        d = np.array([dx[k], dy[k]])
+        if kernel == 1:
+            inside = d @ np.linalg.solve(S, d) <= 2.25
+            area = np.pi * 2.25 * math.sqrt(np.linalg.det(S))
+        else:
+            v = np.linalg.solve(np.linalg.cholesky(S), d)
+            inside = np.abs(v).max() <= 1.5
+            area = 9.0 * math.sqrt(np.linalg.det(S))
+        out[k] = 1.0 / area if inside else 0.0
+    return out
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_affine_closed_form_disk_box(oracle_mod, kernel):
+    """Affine field, disk and box kernels: D = k(u* - x) / |det M| (Eq. 2)."""
+    st, q = _affine_cases(11)
+    q[:, 2:5] *= 4.0  # larger footprints so preimages land inside and outside the support
+    D, flags, hits, _ = oracle_mod.pndf(st, q, kernel=kernel)
+    M = np.asarray(AFF_M)
+    ustar = np.linalg.solve(M[None, :, :], (q[:, 5:7] - np.asarray(AFF_N0)[None, :])[:, :, None])[:, :, 0]
+    N = st.shape[0]
+    inside = np.all((ustar > 0) & (ustar < N - 1), axis=1)
+    w = support_weight(kernel, ustar[:, 0] - q[:, 0], ustar[:, 1] - q[:, 1], q[:, 2], q[:, 3], q[:, 4])
+    expect = np.where(inside, w / abs(np.linalg.det(M)), 0.0)
+    ok = (flags & oracle_mod.F_EXCLUDE) == 0
+    assert ok.sum() > 0.95 * len(q)
+    assert np.any(expect[ok] > 0) and np.any(expect[ok] == 0)
+    np.testing.assert_allclose(D[ok], expect[ok], rtol=1e-12, atol=0)
+
+
+def _mass_estimate_kernel(oracle_mod, st, x, y, S, kernel, res, seed):
+    rng = np.random.default_rng(seed)
+    N = st.shape[0]
+    r = 4 * math.sqrt(max(S[0], S[2]))
+    i0, i1 = int(max(0, math.floor(x - r) - 1)), int(min(N - 1, math.ceil(x + r) + 1))
+    j0, j1 = int(max(0, math.floor(y - r) - 1)), int(min(N - 1, math.ceil(y + r) + 1))
+    sub = st[j0:j1 + 1, i0:i1 + 1].reshape(-1, 2)
+    lo, hi = sub.min(0) - 1e-3, sub.max(0) + 1e-3
+    h = (hi - lo) / res
+    off = rng.uniform(0, 1, 2)
+    mx, my = np.meshgrid(lo[0] + (np.arange(res) + off[0]) * h[0], lo[1] + (np.arange(res) + off[1]) * h[1])
+    q = np.zeros((mx.size, 7))
+    q[:, 0], q[:, 1], q[:, 2], q[:, 3], q[:, 4] = x, y, S[0], S[1], S[2]
+    q[:, 5], q[:, 6] = mx.ravel(), my.ravel()
+    D, *_ = oracle_mod.pndf(st, q, kernel=kernel)
+    return D.sum() * h[0] * h[1]
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_mass_invariant_disk_box(oracle_mod, kernel):
+    """The disk and box kernels are normalised with no truncation: D
+    integrates to exactly 1 over the normal plane (change of variables per
+    triangle, Eq. 2), for an anisotropic, correlated S."""
+    st = synth.normals_from_height(synth.bumps_height(40, 6, seed=11, noise=0.0, sig=(3.0, 6.0))).double().numpy()
+    S = (9.0, 3.0, 5.0)
+    e_coarse = abs(_mass_estimate_kernel(oracle_mod, st, 19.5, 19.25, S, kernel, 200, 1) - 1.0)
+    e_fine = abs(_mass_estimate_kernel(oracle_mod, st, 19.5, 19.25, S, kernel, 700, 2) - 1.0)
+    assert e_fine < 0.01, (e_coarse, e_fine)
+    assert e_fine < e_coarse or e_fine < 2e-3
+
+
+def test_binning_box_kernel(oracle_mod):
+    """Binning with the box kernel and a correlated S: uv samples uniform in
+    the sheared square L [-1.5, 1.5]^2 (numpy's Cholesky factor), binned in m,
+    converge to the bin-integrated D."""
+    st = synth.normals_from_height(synth.bumps_height(32, 5, seed=5, noise=0.0, sig=(3.0, 8.0))).double().numpy()
+    x, y, S = 15.5, 15.5, np.array([[6.0, 2.5], [2.5, 3.0]])
+    L = np.linalg.cholesky(S)
+
+    def l1(nsamp, seed, sub):
+        rng = np.random.default_rng(seed)
+        k = int(math.sqrt(nsamp))
+        v = np.stack([((np.arange(k)[None, :] + rng.uniform(0, 1, (k, k))) / k).ravel(),
+                      ((np.arange(k)[:, None] + rng.uniform(0, 1, (k, k))) / k).ravel()], 1) * 3.0 - 1.5
+        u = v @ L.T + np.array([x, y])
+        w = np.full(len(u), 1.0 / len(u))  # uniform density over the support, total mass 1
+        n = interp_normal(st, u[:, 0], u[:, 1])
+        lo, hi = n.min(0), n.max(0)
+        nb = 16
+        ex, ey = np.linspace(lo[0], hi[0], nb + 1), np.linspace(lo[1], hi[1], nb + 1)
+        hist, _, _ = np.histogram2d(n[:, 0], n[:, 1], bins=[ex, ey], weights=w)
+        bx, by = ex[1] - ex[0], ey[1] - ey[0]
+        fx = (np.arange(nb * sub) + rng.uniform(0, 1, nb * sub)) / sub
+        fy = (np.arange(nb * sub) + rng.uniform(0, 1, nb * sub)) / sub
+        mx, my = np.meshgrid(ex[0] + fx * bx, ey[0] + fy * by, indexing="ij")
+        q = np.zeros((mx.size, 7))
+        q[:, 0], q[:, 1], q[:, 2], q[:, 3], q[:, 4] = x, y, S[0, 0], S[0, 1], S[1, 1]
+        q[:, 5], q[:, 6] = mx.ravel(), my.ravel()
+        D, *_ = oracle_mod.pndf(st, q, kernel=2)
+        Dm = D.reshape(nb, sub, nb, sub).mean(axis=(1, 3)) * bx * by
+        return np.abs(Dm - hist).sum() / hist.sum()
+
+    small, big = l1(250_000, 1, 8), l1(4_000_000, 2, 48)
+    assert big < 0.01, (small, big)
+    assert big < 0.5 * small
