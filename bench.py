@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--map-size", dest="n", type=int, default=synth.FLAKE_8192["n"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernels", default="disk,box", help="footprint kernels to measure besides the Gaussian ('' = skip)")
     ap.add_argument("--cluster-taus", default="1e-4,1e-3",
                     help="cluster cut thresholds to measure on the same workload ('' = skip)")
     ap.add_argument("--serve-batches", type=int, default=2000, help="serving workload size (0 = skip serving)")
@@ -447,6 +448,49 @@ def run_cluster_cut(args, world, st, q, D_exact, exact_kernel_ms):
     return out
 
 
+def run_kernels(args, world, st, q, gauss_kernel_ms, gauss_tri_tests):
+    """The disk and box footprint kernels (the (3 sigma)^2 footprints the
+    paper pairs with the Gaussian's (6 sigma)^2) on the bench workload: same
+    map, same queries, FP16 bounds; a step = key/sort + traversal + unpermute."""
+    from paper_2505_08985_gb300 import pndf
+    dev = q.device
+    nq = q.shape[0]
+    stream = torch.cuda.current_stream()
+    D = torch.empty(nq, dtype=torch.float32, device=dev)
+    h = pndf.pndf_build_hierarchy(st, bounds_fmt=pndf.PNDF_BOUNDS_F16_OUTWARD)
+    out = {"workload": WORKLOAD, "support": "disk q <= 1.5^2, box |L^-1 d|_inf <= 1.5 (S = L L^T); "
+                                            "Gaussian cut at q <= 16", "per_kernel": {}}
+    ids = {"disk": pndf.PNDF_KERNEL_DISK, "box": pndf.PNDF_KERNEL_BOX}
+    for name in [k.strip() for k in args.kernels.split(",") if k.strip()]:
+        kern = ids[name]
+        stt = torch.zeros(nq, pndf.STATS_FIELDS, dtype=torch.int32, device=dev)
+        pndf.pndf_eval_batch_ex(h, q, out=D, stats=stt, kernel=kern)
+        s = stt.to(torch.int64).sum(0).cpu().tolist()
+        del stt
+        for _ in range(args.warmup):
+            pndf.pndf_eval_batch_ex(h, q, out=D, kernel=kern)
+        kb = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ke = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        barrier(world)
+        t0.record(stream)
+        for k in range(args.steps):
+            pndf.pndf_eval_batch_ex(h, q, out=D, kernel=kern, ev_begin=kb[k], ev_end=ke[k])
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms = max_over_ranks(world, t0.elapsed_time(t1))
+        kms = sum(a.elapsed_time(b) for a, b in zip(kb, ke)) / args.steps
+        out["per_kernel"][name] = {
+            "value": sum_over_ranks(world, float(nq * args.steps)) / (ms / 1e3), "unit": UNIT,
+            "ms_per_step": ms / args.steps, "traverse_kernel_ms": kms,
+            "traversal_speedup_vs_gauss": gauss_kernel_ms / kms,
+            "tri_tests_per_query": s[2] / nq, "tri_tests_vs_gauss": s[2] / max(gauss_tri_tests, 1),
+            "hits_per_query": s[3] / nq}
+    h.free()
+    return out
+
+
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
@@ -544,6 +588,7 @@ def run_gpu(args, world, rank, local):
     # roofline of the dominant kernel (traversal + leaf test), per launch
     kavg16 = sum(kms16) / len(kms16)
     cluster = run_cluster_cut(args, world, st, q, D, kavg16) if args.cluster_taus else None
+    kernels = run_kernels(args, world, st, q, kavg16, work["f16"]["tri_tests"]) if args.kernels else None
     peak, peak_kind = hbm_peak()
     achieved = work["f16"]["bytes"] / (kavg16 / 1e3) / 1e9
     traffic = committed_traffic("f16")
@@ -572,6 +617,8 @@ def run_gpu(args, world, rank, local):
     }
     if cluster:
         line["cluster_cut"] = cluster
+    if kernels:
+        line["footprint_kernels"] = kernels
 
     if args.serve_batches > 0 or args.mixed_requests > 0:
         del st, q, D, st_h, q_h, D_h, st_d

@@ -111,6 +111,19 @@ typedef enum pndf_sort_mode {
 } pndf_sort_mode;
 #define PNDF_SORT_DEFAULT PNDF_SORT_LEVEL_TILE
 
+/* Footprint kernel k_r(d), d = u - x, q = d^T S^-1 d (Eq. 2; the Gaussian of
+ * Sec. 5 and the disk and box filters of the kernel ablation, whose (3
+ * sigma)^2 footprints the paper pairs with the Gaussian's (6 sigma)^2):
+ *   GAUSS exp(-q/2) / (2 pi sqrt(det S)) where q <= 16 (4 sigma), else 0;
+ *   DISK  1 / (2.25 pi sqrt(det S)) where q <= 1.5^2, else 0;
+ *   BOX   1 / (9 sqrt(det S)) where |L^-1 d|_inf <= 1.5, S = L L^T (Cholesky),
+ *         else 0 (for S = sigma^2 I, the square of side 3 sigma). */
+typedef enum pndf_kernel {
+    PNDF_KERNEL_GAUSS = 0,
+    PNDF_KERNEL_DISK = 1,
+    PNDF_KERNEL_BOX = 2
+} pndf_kernel;
+
 typedef struct pndf_eval_config {
     int32_t mode;           /* pndf_eval_mode                                         */
     int32_t sort;           /* query order before traversal (pndf_sort_mode)          */
@@ -120,7 +133,7 @@ typedef struct pndf_eval_config {
                             /* r_x r_y tau is evaluated as its two cluster triangles;  */
                             /* 0 = exact (no cluster).  Needs a hierarchy built with   */
                             /* clusters = 1, else UNSUPPORTED.  Hierarchy mode only.   */
-    int32_t reserved;       /* must be 0                                              */
+    int32_t kernel;         /* footprint kernel (pndf_kernel)                          */
     void *ev_begin;         /* optional cudaEvent_t recorded on the stream just before */
     void *ev_end;           /* and just after the traversal kernel (NULL = none)       */
 } pndf_eval_config;

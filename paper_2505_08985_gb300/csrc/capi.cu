@@ -174,10 +174,12 @@ pndf_status pndf_eval_batch_ex(const pndf_hierarchy *h, const pndf_query *q_dev,
     if (nq < 0 || nq > int64_t(0x7fffffff)) return PNDF_ERR_INVALID_ARG;
     if (nq > 0 && (!q_dev || !D_out_dev)) return PNDF_ERR_INVALID_ARG;
     if (q_dev && !aligned(q_dev, 16)) return PNDF_ERR_INVALID_ARG;
-    pndf_eval_config c{PNDF_MODE_HIERARCHY, PNDF_SORT_DEFAULT, 0, 0, 0.f, 0, nullptr, nullptr};
+    pndf_eval_config c{PNDF_MODE_HIERARCHY, PNDF_SORT_DEFAULT, 0, 0, 0.f, PNDF_KERNEL_GAUSS, nullptr, nullptr};
     if (cfg) c = *cfg;
     if (c.mode != PNDF_MODE_HIERARCHY && c.mode != PNDF_MODE_FLAT) return PNDF_ERR_INVALID_ARG;
-    if (!(c.tau >= 0.f) || !isfinite(c.tau) || c.reserved != 0) return PNDF_ERR_INVALID_ARG;
+    if (!(c.tau >= 0.f) || !isfinite(c.tau)) return PNDF_ERR_INVALID_ARG;
+    if (c.kernel != PNDF_KERNEL_GAUSS && c.kernel != PNDF_KERNEL_DISK && c.kernel != PNDF_KERNEL_BOX)
+        return PNDF_ERR_INVALID_ARG;
     if (c.tau > 0.f && (!h->clusters || c.mode != PNDF_MODE_HIERARCHY)) return PNDF_ERR_UNSUPPORTED;
     if (c.sort < 0 || c.sort > 4) return PNDF_ERR_INVALID_ARG;
     if (c.warps_per_cta < 0 || c.warps_per_cta > 8 || c.ctas_per_sm < 0) return PNDF_ERR_INVALID_ARG;
@@ -234,7 +236,7 @@ pndf_status pndf_eval_batch_host(const pndf_hierarchy *h, const pndf_query *q_ho
     float *Dd = static_cast<float *>(buf);
     pndf_query *qd = reinterpret_cast<pndf_query *>(static_cast<char *>(buf) + qoff);
     cudaError_t e = cudaMemcpyAsync(qd, q_host, qb, cudaMemcpyHostToDevice, s);
-    pndf_eval_config c{PNDF_MODE_HIERARCHY, PNDF_SORT_DEFAULT, 0, 0, 0.f, 0, nullptr, nullptr};
+    pndf_eval_config c{PNDF_MODE_HIERARCHY, PNDF_SORT_DEFAULT, 0, 0, 0.f, PNDF_KERNEL_GAUSS, nullptr, nullptr};
     if (e == cudaSuccess) st = launch_eval(h, qd, nq, Dd, nullptr, nullptr, c, s);
     if (e == cudaSuccess && st == PNDF_OK) e = cudaMemcpyAsync(D_host, Dd, db, cudaMemcpyDeviceToHost, s);
     cudaError_t ef = cudaFreeAsync(buf, s);

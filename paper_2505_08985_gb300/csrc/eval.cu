@@ -80,23 +80,31 @@ __device__ __forceinline__ uint32_t fmix32(uint32_t h)
     return h;
 }
 
+// Footprint kernels (pndf_kernel): the Gaussian cut at q = d^T S^-1 d <= 16,
+// and the disk (q <= 1.5^2) and box (|L^-1 d|_inf <= 1.5, S = L L^T) filters
+// of the (3 sigma)^2 footprints the paper pairs with it.
 struct Query {
     float x, y;          // footprint centre
     float ia, ib, ic;    // S^-1 = [[ia, ib], [ib, ic]]
-    float norm;          // 1 / (2 pi sqrt(det S))
+    float norm;          // kernel normalisation: 1 / (2 pi, 2.25 pi or 9) sqrt(det S)
     float mx, my;        // query normal
-    float rx, ry;        // half-widths of the 4-sigma box (slightly inflated)
-    float theta;         // cluster cut threshold r_x r_y tau (exact 4-sigma half-widths)
+    float rx, ry;        // half-widths of the support's bounding box (slightly inflated)
+    float qprune;        // the support lies in q <= qprune (16, 2.25, 4.5), with a margin
+    float theta;         // r_x r_y of the support (exact half-widths); times tau for the cluster cut
+    float inv_sxx;       // box: 1 / S_xx, so that (L^-1 d)_x^2 = dx^2 / S_xx
+    float l11, l21, l22; // box: the Cholesky factor L of S (node tests by separating axes)
+    int kernel;
     bool valid;
 };
 
-__device__ __forceinline__ Query make_query(const pndf_query &r)
+__device__ __forceinline__ Query make_query(const pndf_query &r, int kernel = PNDF_KERNEL_GAUSS)
 {
     Query q;
     q.x = r.x;
     q.y = r.y;
     q.mx = r.ms;
     q.my = r.mt;
+    q.kernel = kernel;
     float det = r.sxx * r.syy - r.sxy * r.sxy;
     q.valid = (r.sxx > 0.f) && (r.syy > 0.f) && (det > 0.f) && isfinite(det) && isfinite(r.x) &&
               isfinite(r.y) && isfinite(r.ms) && isfinite(r.mt);
@@ -104,12 +112,53 @@ __device__ __forceinline__ Query make_query(const pndf_query &r)
     q.ia = r.syy * inv;
     q.ib = -r.sxy * inv;
     q.ic = r.sxx * inv;
-    q.norm = 1.0f / (2.0f * kPi * sqrtf(det));
-    // q <= 16 implies |dx| <= 4 sqrt(sxx); inflate so rounding never clips the box
-    q.rx = 4.0f * sqrtf(r.sxx) * (1.0f + 1e-5f) + 1e-6f;
-    q.ry = 4.0f * sqrtf(r.syy) * (1.0f + 1e-5f) + 1e-6f;
-    q.theta = 0.f;
+    const float sx = sqrtf(r.sxx), sy = sqrtf(r.syy), sd = sqrtf(det);
+    float hx, hy;
+    q.inv_sxx = 0.f;
+    q.l11 = q.l21 = q.l22 = 0.f;
+    if (kernel == PNDF_KERNEL_DISK) {
+        q.norm = 1.0f / (2.25f * kPi * sd);
+        hx = 1.5f * sx;
+        hy = 1.5f * sy;
+        q.qprune = 2.25f * (1.0f + 1e-4f);
+    } else if (kernel == PNDF_KERNEL_BOX) {
+        q.norm = 1.0f / (9.0f * sd);
+        const float l21 = r.sxy / sx, l22 = sqrtf(fmaxf(r.syy - l21 * l21, 0.f));
+        hx = 1.5f * sx;
+        hy = 1.5f * (fabsf(l21) + l22);
+        q.qprune = 4.5f * (1.0f + 1e-4f);  // |v|_inf <= 1.5 implies |v|^2 <= 4.5
+        q.inv_sxx = 1.0f / r.sxx;
+        q.l11 = sx;
+        q.l21 = l21;
+        q.l22 = l22;
+    } else {
+        q.norm = 1.0f / (2.0f * kPi * sd);
+        hx = 4.0f * sx;  // q <= 16 implies |dx| <= 4 sqrt(sxx)
+        hy = 4.0f * sy;
+        q.qprune = kQPrune;
+    }
+    q.theta = hx * hy;
+    // inflate so rounding never clips the support's box
+    q.rx = hx * (1.0f + 1e-5f) + 1e-6f;
+    q.ry = hy * (1.0f + 1e-5f) + 1e-6f;
     return q;
+}
+
+// Kernel weight at offset d with q = d^T S^-1 d; 0 outside the support.
+__device__ __forceinline__ float kweight(const Query &q, float dx, float qq)
+{
+    if (q.kernel == PNDF_KERNEL_GAUSS) return qq <= kQCut ? q.norm * expf(-0.5f * qq) : 0.f;
+    if (q.kernel == PNDF_KERNEL_DISK) return qq <= 2.25f ? q.norm : 0.f;
+    const float v1 = dx * dx * q.inv_sxx;  // (L^-1 d)_x^2; (L^-1 d)_y^2 = q - v1
+    return (v1 <= 2.25f && qq - v1 <= 2.25f) ? q.norm : 0.f;
+}
+
+__device__ __forceinline__ double kweight_d(const Query &q, double dx, double qq)
+{
+    if (q.kernel == PNDF_KERNEL_GAUSS) return qq <= double(kQCut) ? double(q.norm) * exp(-0.5 * qq) : 0.0;
+    if (q.kernel == PNDF_KERNEL_DISK) return qq <= 2.25 ? double(q.norm) : 0.0;
+    const double v1 = dx * dx * double(q.inv_sxx);
+    return (v1 <= 2.25 && qq - v1 <= 2.25) ? double(q.norm) : 0.0;
 }
 
 __device__ __forceinline__ float qform(const Query &q, float dx, float dy)
@@ -157,25 +206,46 @@ __device__ __forceinline__ float2 texel(const MapDesc &d, int i, int j)
     return __half22float2(h);
 }
 
+// Box kernel: does [dx0, dx1] x [dy0, dy1] (offsets from the centre) meet the
+// support L [-1.5, 1.5]^2?  Separating axes: x and y (the support's extents
+// are the inflated half-widths rx, ry) and n = (-l21, l11), normal to L e1,
+// onto which the support projects to +-1.5 l11 l22 (slightly inflated).
+__device__ __forceinline__ bool box_support_meets(const Query &q, float dx0, float dx1, float dy0, float dy1)
+{
+    if (dx0 > q.rx || dx1 < -q.rx || dy0 > q.ry || dy1 < -q.ry) return false;
+    const float hn = 1.5f * q.l11 * q.l22 * (1.0f + 1e-4f) + 1e-6f;
+    const float p0 = -q.l21 * dx0, p1 = -q.l21 * dx1;
+    const float pmin = fminf(p0, p1) + q.l11 * dy0, pmax = fmaxf(p0, p1) + q.l11 * dy1;
+    return pmin <= hn && pmax >= -hn;
+}
+
 // Node (level l, coords a, c): uv box [a 2^l, (a+1) 2^l] x [c 2^l, (c+1) 2^l].
-// It can hold a contributing hit only if that box meets the 4-sigma ellipse.
+// It can hold a contributing hit only if that box meets the kernel's support
+// (the ellipse q <= qprune; for the box kernel the sheared square itself).
 __device__ __forceinline__ bool node_in_footprint(const Query &q, int l, uint32_t a, uint32_t c)
 {
     float sz = float(1u << l);
     float dx0 = float(a) * sz - q.x, dy0 = float(c) * sz - q.y;
-    return qmin_box(q, dx0, dx0 + sz, dy0, dy0 + sz) <= kQPrune;
+    if (q.kernel == PNDF_KERNEL_BOX) return box_support_meets(q, dx0, dx0 + sz, dy0, dy0 + sz);
+    return qmin_box(q, dx0, dx0 + sz, dy0, dy0 + sz) <= q.qprune;
 }
 
-// The node's uv box lies entirely inside the pruning ellipse (the quadratic is
-// convex, so its maximum over the box is at a corner); every descendant then
-// passes the footprint test and skips it.
+// The node's uv box lies entirely inside the pruning region (the quadratic is
+// convex, so its maximum over the box is at a corner; the box kernel's
+// support is convex too); every descendant then passes the footprint test
+// and skips it.  Claiming "inside" wrongly would only prune less.
 __device__ __forceinline__ bool node_inside(const Query &q, int l, uint32_t a, uint32_t c)
 {
     float sz = float(1u << l);
     float dx0 = float(a) * sz - q.x, dy0 = float(c) * sz - q.y;
     float dx1 = dx0 + sz, dy1 = dy0 + sz;
+    if (q.kernel == PNDF_KERNEL_BOX) {  // the support is convex: all four corners inside it
+        const float hx = 1.5f * q.l11, hv = 1.5f * q.l22, k = q.l21 / q.l11;
+        return fmaxf(fabsf(dx0), fabsf(dx1)) <= hx && fabsf(dy0 - k * dx0) <= hv && fabsf(dy0 - k * dx1) <= hv &&
+               fabsf(dy1 - k * dx0) <= hv && fabsf(dy1 - k * dx1) <= hv;
+    }
     float m = fmaxf(fmaxf(qform(q, dx0, dy0), qform(q, dx1, dy0)), fmaxf(qform(q, dx0, dy1), qform(q, dx1, dy1)));
-    return m <= kQPrune;
+    return m <= q.qprune;
 }
 
 __device__ __forceinline__ bool box_holds(const float4 &b, const Query &q)
@@ -257,8 +327,9 @@ __device__ __forceinline__ void test_triangle(const Query &q, float2 na, float2 
         double dx = (double(ai) - double(q.x)) + dir * dl1;
         double dy = (double(aj) - double(q.y)) + dir * dl2;
         double qq = double(q.ia) * dx * dx + 2.0 * double(q.ib) * dx * dy + double(q.ic) * dy * dy;
-        if (qq > double(kQCut)) return;
-        double w = double(q.norm) * exp(-0.5 * qq) / fabs(dcr);
+        double w = kweight_d(q, dx, qq);
+        if (w == 0.0) return;
+        w /= fabs(dcr);
         acc_add(acc, float(w));
         if (STATS) {
             acc.hits++;
@@ -269,8 +340,9 @@ __device__ __forceinline__ void test_triangle(const Query &q, float2 na, float2 
     float dx = (float(ai) - q.x) + dir * l1;
     float dy = (float(aj) - q.y) + dir * l2;
     float qq = qform(q, dx, dy);
-    if (qq > kQCut) return;
-    acc_add(acc, q.norm * expf(-0.5f * qq) / J);
+    float w = kweight(q, dx, qq);
+    if (w == 0.f) return;
+    acc_add(acc, w / J);
     if (STATS) {
         acc.hits++;
         acc.hash += fmix32(tri_id);
@@ -339,8 +411,9 @@ __device__ __forceinline__ void drain_hits(const Query &q, int n, int L, const f
         float dx = (float(gi + (tri << l)) - q.x) + dir * l1;
         float dy = (float(gj + (tri << l)) - q.y) + dir * l2;
         float qq = qform(q, dx, dy);
-        if (qq <= kQCut) {
-            acc_add(acc, q.norm * expf(-0.5f * qq) * (a * a) / fabsf(h.x));
+        const float w = kweight(q, dx, qq);
+        if (w != 0.f) {
+            acc_add(acc, w * (a * a) / fabsf(h.x));
             if (STATS) {
                 acc.hits++;
                 uint32_t id;
@@ -490,9 +563,10 @@ __device__ __forceinline__ bool cluster_edge_test(const Query &q, float2 p, floa
     double dx = (double(ai) - double(q.x)) + dir * dl1;
     double dy = (double(aj) - double(q.y)) + dir * dl2;
     double qq = double(q.ia) * dx * dx + 2.0 * double(q.ib) * dx * dy + double(q.ic) * dy * dy;
-    if (qq > double(kQCut)) return false;
+    const double w = kweight_d(q, dx, qq);
+    if (w == 0.0) return false;
     double sc = double(1u << l);
-    acc_add(acc, float(double(q.norm) * exp(-0.5 * qq) * sc * sc / fabs(dcr)));
+    acc_add(acc, float(w * sc * sc / fabs(dcr)));
     if (STATS) {
         acc.hits++;
         acc.hash += fmix32(id);
@@ -648,12 +722,15 @@ __device__ __forceinline__ int entry_level(const Query &q, int L)
     return l;
 }
 
-template <int BFMT, int TFMT, bool STATS, bool FLAT, bool CLUSTER>
+// KERN: the footprint kernel (pndf_kernel), a compile-time constant so the
+// query's kernel fields and branches fold away (each kernel is its own
+// instantiation).
+template <int BFMT, int TFMT, bool STATS, bool FLAT, bool CLUSTER, int KERN>
 __device__ void eval_one(const MapDesc &d, const ClusterDesc &cd, float tau, const pndf_query &rec, int lane,
-                         uint32_t *stk, uint32_t *lq, uint32_t *ring, float4 *hits, float &D_out, uint32_t &flags_out,
-                         pndf_query_stats *st_out)
+                         uint32_t *stk, uint32_t *lq, uint32_t *ring, float4 *hits, float &D_out,
+                         uint32_t &flags_out, pndf_query_stats *st_out)
 {
-    Query q = make_query(rec);
+    Query q = make_query(rec, KERN);
     Acc acc = {};
     if (!q.valid) {
         if (lane == 0) {
@@ -664,7 +741,7 @@ __device__ void eval_one(const MapDesc &d, const ClusterDesc &cd, float tau, con
         }
         return;
     }
-    if (CLUSTER) q.theta = (4.0f * sqrtf(rec.sxx)) * (4.0f * sqrtf(rec.syy)) * tau;
+    if (CLUSTER) q.theta *= tau;  // r_x r_y tau with the support's half-widths
     const int L = d.L;
     if (FLAT) {
         // every leaf block meeting the 4-sigma box, no pruning
@@ -833,7 +910,7 @@ __device__ void eval_one(const MapDesc &d, const ClusterDesc &cd, float tau, con
     }
 }
 
-template <int BFMT, int TFMT, bool STATS, bool FLAT, bool CLUSTER>
+template <int BFMT, int TFMT, bool STATS, bool FLAT, bool CLUSTER, int KERN>
 __global__ void __launch_bounds__(256, PNDF_TRAVERSE_MIN_CTAS)
     traverse_kernel(MapDesc d, ClusterDesc cd, float tau, const pndf_query *__restrict__ qs,
                     const uint32_t *__restrict__ order, int64_t nq, float *__restrict__ D,
@@ -855,8 +932,8 @@ __global__ void __launch_bounds__(256, PNDF_TRAVERSE_MIN_CTAS)
         pndf_query rec = qs[qi];
         float Dv;
         uint32_t fv;
-        eval_one<BFMT, TFMT, STATS, FLAT, CLUSTER>(d, cd, tau, rec, lane, stk, lq, ring, hits, Dv, fv,
-                                                   stats ? stats + qi : nullptr);
+        eval_one<BFMT, TFMT, STATS, FLAT, CLUSTER, KERN>(d, cd, tau, rec, lane, stk, lq, ring, hits, Dv, fv,
+                                                         stats ? stats + qi : nullptr);
         if (lane == 0) {
             D[qi] = Dv;
             if (flags) flags[qi] = fv;
@@ -996,12 +1073,12 @@ inline size_t sort_hist_bytes(int64_t nq)
     return bins * sizeof(uint32_t);
 }
 
-template <int BFMT, int TFMT, bool STATS, bool FLAT, bool CLUSTER>
+template <int BFMT, int TFMT, bool STATS, bool FLAT, bool CLUSTER, int KERN>
 cudaError_t launch_traverse(const MapDesc &d, const ClusterDesc &cd, float tau, const pndf_query *q,
                             const uint32_t *order, int64_t nq, float *D, uint32_t *flags, pndf_query_stats *stats,
                             unsigned long long *cursor, int warps, int ctas_per_sm, cudaStream_t s)
 {
-    auto kern = traverse_kernel<BFMT, TFMT, STATS, FLAT, CLUSTER>;
+    auto kern = traverse_kernel<BFMT, TFMT, STATS, FLAT, CLUSTER, KERN>;
     int threads = warps * 32;
     size_t smem = size_t(warps) * kWarpSmemWords * sizeof(uint32_t);
     int dev = 0, sms = 0, occ = 0;
@@ -1020,28 +1097,40 @@ cudaError_t launch_traverse(const MapDesc &d, const ClusterDesc &cd, float tau, 
     return cudaGetLastError();
 }
 
-template <int BFMT, int TFMT>
-cudaError_t dispatch_stats(const MapDesc &d, const ClusterDesc &cd, const pndf_query *q, const uint32_t *order,
-                           int64_t nq, float *D, uint32_t *flags, pndf_query_stats *stats,
-                           unsigned long long *cursor, const pndf_eval_config &cfg, cudaStream_t s)
+template <int BFMT, int TFMT, int KERN>
+cudaError_t dispatch_kernel(const MapDesc &d, const ClusterDesc &cd, const pndf_query *q, const uint32_t *order,
+                            int64_t nq, float *D, uint32_t *flags, pndf_query_stats *stats,
+                            unsigned long long *cursor, const pndf_eval_config &cfg, cudaStream_t s)
 {
     const int warps = cfg.warps_per_cta > 0 ? cfg.warps_per_cta : 8;
     const int cps = cfg.ctas_per_sm;
     const float tau = cfg.tau;
     if (cfg.mode == PNDF_MODE_FLAT)
-        return stats ? launch_traverse<BFMT, TFMT, true, true, false>(d, cd, 0.f, q, order, nq, D, flags, stats,
-                                                                       cursor, warps, cps, s)
-                     : launch_traverse<BFMT, TFMT, false, true, false>(d, cd, 0.f, q, order, nq, D, flags, stats,
-                                                                        cursor, warps, cps, s);
+        return stats ? launch_traverse<BFMT, TFMT, true, true, false, KERN>(d, cd, 0.f, q, order, nq, D, flags, stats,
+                                                                             cursor, warps, cps, s)
+                     : launch_traverse<BFMT, TFMT, false, true, false, KERN>(d, cd, 0.f, q, order, nq, D, flags, stats,
+                                                                              cursor, warps, cps, s);
     if (tau > 0.f)
-        return stats ? launch_traverse<BFMT, TFMT, true, false, true>(d, cd, tau, q, order, nq, D, flags, stats,
-                                                                       cursor, warps, cps, s)
-                     : launch_traverse<BFMT, TFMT, false, false, true>(d, cd, tau, q, order, nq, D, flags, stats,
-                                                                        cursor, warps, cps, s);
-    return stats ? launch_traverse<BFMT, TFMT, true, false, false>(d, cd, 0.f, q, order, nq, D, flags, stats, cursor,
-                                                                    warps, cps, s)
-                 : launch_traverse<BFMT, TFMT, false, false, false>(d, cd, 0.f, q, order, nq, D, flags, stats,
-                                                                     cursor, warps, cps, s);
+        return stats ? launch_traverse<BFMT, TFMT, true, false, true, KERN>(d, cd, tau, q, order, nq, D, flags, stats,
+                                                                             cursor, warps, cps, s)
+                     : launch_traverse<BFMT, TFMT, false, false, true, KERN>(d, cd, tau, q, order, nq, D, flags, stats,
+                                                                              cursor, warps, cps, s);
+    return stats ? launch_traverse<BFMT, TFMT, true, false, false, KERN>(d, cd, 0.f, q, order, nq, D, flags, stats,
+                                                                          cursor, warps, cps, s)
+                 : launch_traverse<BFMT, TFMT, false, false, false, KERN>(d, cd, 0.f, q, order, nq, D, flags, stats,
+                                                                           cursor, warps, cps, s);
+}
+
+template <int BFMT, int TFMT>
+cudaError_t dispatch_stats(const MapDesc &d, const ClusterDesc &cd, const pndf_query *q, const uint32_t *order,
+                           int64_t nq, float *D, uint32_t *flags, pndf_query_stats *stats,
+                           unsigned long long *cursor, const pndf_eval_config &cfg, cudaStream_t s)
+{
+    if (cfg.kernel == PNDF_KERNEL_DISK)
+        return dispatch_kernel<BFMT, TFMT, PNDF_KERNEL_DISK>(d, cd, q, order, nq, D, flags, stats, cursor, cfg, s);
+    if (cfg.kernel == PNDF_KERNEL_BOX)
+        return dispatch_kernel<BFMT, TFMT, PNDF_KERNEL_BOX>(d, cd, q, order, nq, D, flags, stats, cursor, cfg, s);
+    return dispatch_kernel<BFMT, TFMT, PNDF_KERNEL_GAUSS>(d, cd, q, order, nq, D, flags, stats, cursor, cfg, s);
 }
 
 }  // namespace
@@ -1166,8 +1255,8 @@ __global__ void __launch_bounds__(256, PNDF_TRAVERSE_MIN_CTAS)
         const pndf_query rec = sg.q[qi];
         float Dv;
         uint32_t fv;
-        eval_one<BFMT, TFMT, false, false, false>(smaps[sg.map], kNoClusters, 0.f, rec, lane, stk, lq, ring, hits,
-                                                  Dv, fv, nullptr);
+        eval_one<BFMT, TFMT, false, false, false, PNDF_KERNEL_GAUSS>(smaps[sg.map], kNoClusters, 0.f, rec, lane, stk,
+                                                                     lq, ring, hits, Dv, fv, nullptr);
         if (lane == 0) {
             sg.D[qi] = Dv;
             if (sg.flags) sg.flags[qi] = fv;
@@ -1272,7 +1361,7 @@ pndf_status launch_eval_noalloc(const pndf_hierarchy *h, const pndf_query *q, in
     void *scratch = nullptr;
     if (noalloc_scratch(&scratch) != cudaSuccess) return PNDF_ERR_CUDA;
     const MapDesc &d = h->d;
-    pndf_eval_config cfg{PNDF_MODE_HIERARCHY, PNDF_SORT_DEFAULT, 0, 0, 0.f, 0, nullptr, nullptr};
+    pndf_eval_config cfg{PNDF_MODE_HIERARCHY, PNDF_SORT_DEFAULT, 0, 0, 0.f, PNDF_KERNEL_GAUSS, nullptr, nullptr};
     char *base = static_cast<char *>(scratch);
     auto *cursor = reinterpret_cast<unsigned long long *>(base);
     auto *hist = reinterpret_cast<uint32_t *>(base + kNoallocHistOff);

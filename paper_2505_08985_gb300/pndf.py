@@ -46,7 +46,7 @@ class _BuildParams(ctypes.Structure):
 
 class _EvalConfig(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("sort", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32), ("tau", ctypes.c_float), ("reserved", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("tau", ctypes.c_float), ("kernel", ctypes.c_int32),
                 ("ev_begin", ctypes.c_void_p), ("ev_end", ctypes.c_void_p)]
 
 
@@ -242,15 +242,20 @@ PNDF_SORT_LEVEL_NORMAL_TILE = 4
 PNDF_SORT_DEFAULT = PNDF_SORT_LEVEL_TILE
 
 
+PNDF_KERNEL_GAUSS = 0  # footprint kernels (pndf_kernel): Gaussian cut at 4 sigma,
+PNDF_KERNEL_DISK = 1   # disk and box of the (3 sigma)^2 footprint
+PNDF_KERNEL_BOX = 2
+
 STATS_FIELDS = 10  # pndf_query_stats: nodes, leaf_blocks, tri_tests, hits, hit_hash, fp64_tris, degenerate,
                    # quads, cluster_checks, clusters
 
 
 def pndf_eval_batch_ex(h: Hierarchy, queries: torch.Tensor, out=None, flags=None, stats=None, mode: int = 0,
                        sort: int = PNDF_SORT_DEFAULT, warps_per_cta: int = 0, ctas_per_sm: int = 0, stream=None,
-                       ev_begin=None, ev_end=None, tau: float = 0.0) -> torch.Tensor:
+                       ev_begin=None, ev_end=None, tau: float = 0.0, kernel: int = PNDF_KERNEL_GAUSS) -> torch.Tensor:
     """ev_begin / ev_end: optional torch.cuda.Event recorded around the traversal kernel.
-    tau > 0: the cluster cut of Sec. 4.3 (the hierarchy must be built with clusters=True)."""
+    tau > 0: the cluster cut of Sec. 4.3 (the hierarchy must be built with clusters=True).
+    kernel: footprint kernel (PNDF_KERNEL_GAUSS, _DISK, _BOX)."""
     nq = _queries(queries)
     if out is None:
         out = torch.empty(nq, dtype=torch.float32, device=queries.device)
@@ -259,7 +264,7 @@ def pndf_eval_batch_ex(h: Hierarchy, queries: torch.Tensor, out=None, flags=None
         _need(flags, "flags", dtype=torch.int32)
     if stats is not None:
         _need(stats, "stats", dtype=torch.int32, shape_last=STATS_FIELDS)
-    cfg = _EvalConfig(int(mode), int(sort), int(warps_per_cta), int(ctas_per_sm), float(tau), 0,
+    cfg = _EvalConfig(int(mode), int(sort), int(warps_per_cta), int(ctas_per_sm), float(tau), int(kernel),
                       _event_handle(ev_begin), _event_handle(ev_end))
     with torch.cuda.device(queries.device):
         _check("pndf_eval_batch_ex", LIB.pndf_eval_batch_ex(h.handle, _ptr(queries), nq, _ptr(out), _ptr(flags),
