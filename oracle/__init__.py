@@ -6,8 +6,10 @@ CUDA package and the CUDA package imports nothing from it.
 
 Functions
 ---------
-pndf(st, queries, kernel=0) -> D (float64), flags (uint32), hits (int64), hit_hash (uint32);
-                              kernel 0 Gaussian (4-sigma cut), 1 disk, 2 box (1.5 sigma)
+pndf(st, queries, kernel=0, jac_eps=0) -> D (float64), flags (uint32), hits (int64), hit_hash (uint32);
+                              kernel 0 Gaussian (4-sigma cut), 1 disk, 2 box (1.5 sigma);
+                              jac_eps > 0: the Jacobian clamp of Eq. 6 (equilateral replacements)
+sample(st, queries, U, kernel=0, jac_eps=0) -> m (n, 2), triangle ids, flags: Eq. 6 sampling
 cluster_fits(st)           -> ClusterFits: corner normals and residual of every node, Eq. 7-8
 cluster_fit(st, l, I, J)   -> (c (4, 2), e) for one node, or None outside the map
 pndf_cluster(st, queries, tau, fits=None) -> as pndf, with the cluster cut e <= r_x r_y tau
@@ -48,6 +50,7 @@ F_DEGENERATE = 4
 F_TINY = 8
 F_INVALID = 16
 F_NEAR_TAU = 32
+F_OUTSIDE = 64  # (sampling) the sampled uv point lies outside the map
 F_EXCLUDE = F_NEAR_EDGE | F_NEAR_CUT | F_DEGENERATE | F_INVALID | F_NEAR_TAU
 KERNEL_GAUSS, KERNEL_DISK, KERNEL_BOX = 0, 1, 2  # footprint kernels (see pndf_oracle.c)
 GL_POINTS = 16
@@ -134,6 +137,8 @@ class Oracle:
     F_DEGENERATE = F_DEGENERATE
     F_TINY = F_TINY
     F_INVALID = F_INVALID
+    F_NEAR_TAU = F_NEAR_TAU
+    F_OUTSIDE = F_OUTSIDE
     F_EXCLUDE = F_EXCLUDE
 
     def __init__(self, so_path: str):
@@ -141,8 +146,11 @@ class Oracle:
         dp = ctypes.POINTER(ctypes.c_double)
         u32p = ctypes.POINTER(ctypes.c_uint32)
         i64p = ctypes.POINTER(ctypes.c_int64)
-        lib.oracle_pndf.argtypes = [dp, ctypes.c_int, dp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, dp, u32p, i64p,
-                                    u32p]
+        lib.oracle_pndf.argtypes = [dp, ctypes.c_int, dp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_double,
+                                    dp, u32p, i64p, u32p]
+        lib.oracle_sample.argtypes = [dp, ctypes.c_int, dp, dp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                      ctypes.c_double, dp, i64p, u32p]
+        lib.oracle_sample.restype = None
         lib.oracle_pndf.restype = None
         lib.oracle_projarea.argtypes = [dp, ctypes.c_int, dp, dp, ctypes.c_int64, ctypes.c_int64, dp, dp, dp,
                                         ctypes.c_int]
@@ -160,7 +168,7 @@ class Oracle:
         lib.oracle_pndf_cluster.restype = None
         self.lib = lib
 
-    def pndf(self, st, queries, threads: int | None = None, kernel: int = 0):
+    def pndf(self, st, queries, threads: int | None = None, kernel: int = 0, jac_eps: float = 0.0):
         lib = self.lib
         stm = _as_map(st)
         q = _as_queries(queries)
@@ -173,7 +181,7 @@ class Oracle:
 
         def run(r):
             lib.oracle_pndf(_ptr(stm, ctypes.c_double), N, _ptr(q, ctypes.c_double), r[0], r[1], int(kernel),
-                            _ptr(D, ctypes.c_double), _ptr(flags, ctypes.c_uint32),
+                            float(jac_eps), _ptr(D, ctypes.c_double), _ptr(flags, ctypes.c_uint32),
                             _ptr(hits, ctypes.c_int64), _ptr(hh, ctypes.c_uint32))
 
         threads = threads or default_threads()
@@ -181,6 +189,32 @@ class Oracle:
             with ThreadPoolExecutor(max_workers=threads) as ex:
                 list(ex.map(run, _chunks(n, threads)))
         return D, flags, hits, hh
+
+    def sample(self, st, queries, uniforms, kernel: int = 0, jac_eps: float = 0.0, threads: int | None = None):
+        """Eq. 6 sampling: one normal per query record from its two uniforms.
+        Returns m (n, 2), triangle ids (n,) (-1 where none) and flags (n,)."""
+        lib = self.lib
+        stm = _as_map(st)
+        q = _as_queries(queries)
+        U = np.ascontiguousarray(np.asarray(uniforms.cpu() if hasattr(uniforms, "cpu") else uniforms)[:, :2],
+                                 dtype=np.float64)
+        n = q.shape[0]
+        assert U.shape[0] == n
+        m = np.zeros((n, 2), np.float64)
+        tri = np.zeros(n, np.int64)
+        flags = np.zeros(n, np.uint32)
+        N = stm.shape[0]
+
+        def run(r):
+            lib.oracle_sample(_ptr(stm, ctypes.c_double), N, _ptr(q, ctypes.c_double), _ptr(U, ctypes.c_double),
+                              r[0], r[1], int(kernel), float(jac_eps), _ptr(m, ctypes.c_double),
+                              _ptr(tri, ctypes.c_int64), _ptr(flags, ctypes.c_uint32))
+
+        threads = threads or default_threads()
+        if n:
+            with ThreadPoolExecutor(max_workers=threads) as ex:
+                list(ex.map(run, _chunks(n, threads, 1024)))
+        return m, tri, flags
 
     def cluster_fit(self, st, l: int, I: int, J: int):
         stm = _as_map(st)
@@ -274,8 +308,12 @@ def _get() -> Oracle:
     return _default
 
 
-def pndf(st, queries, threads: int | None = None, kernel: int = 0):
-    return _get().pndf(st, queries, threads, kernel)
+def pndf(st, queries, threads: int | None = None, kernel: int = 0, jac_eps: float = 0.0):
+    return _get().pndf(st, queries, threads, kernel, jac_eps)
+
+
+def sample(st, queries, uniforms, kernel: int = 0, jac_eps: float = 0.0, threads: int | None = None):
+    return _get().sample(st, queries, uniforms, kernel, jac_eps, threads)
 
 
 def projarea(st, queries, omega, threads: int | None = None):

@@ -125,6 +125,25 @@ static double flat_kernel(int kernel, double dx, double dy, double q, double sxx
     return vm <= 1.5 ? 1.0 / (9.0 * sqrt(det)) : 0.0;
 }
 
+/*
+ * Eq. 6 (Jacobian clamp): a fine triangle whose Jacobian |cross| is below eps
+ * is replaced by an equilateral normal triangle of area eps / 2 (Jacobian
+ * exactly eps), centred at the normal-space centroid of its three vertices,
+ * with a fixed counter-clockwise orientation (vertex k at 90 + 120 k
+ * degrees), its vertices taking the triangle's uv vertices in order.
+ */
+static void eqtri(const double *na, const double *nb, const double *nc, double eps, double E[3][2])
+{
+    double gx = (na[0] + nb[0] + nc[0]) / 3.0, gy = (na[1] + nb[1] + nc[1]) / 3.0;
+    double side = sqrt(2.0 * eps / sqrt(3.0));  /* (sqrt(3) / 4) side^2 = eps / 2 */
+    double rho = side / sqrt(3.0);              /* circumradius */
+    for (int k = 0; k < 3; ++k) {
+        double ang = M_PI / 2.0 + 2.0 * M_PI * k / 3.0;
+        E[k][0] = gx + rho * cos(ang);
+        E[k][1] = gy + rho * sin(ang);
+    }
+}
+
 /* Quads whose uv square [i, i+1] x [j, j+1] can meet the bounding box of the
  * 4-sigma ellipse; a generous superset is harmless (Eq. 5: triangles outside
  * the footprint contribute k_r = 0). */
@@ -148,7 +167,7 @@ static void quad_range(int N, double x, double y, double sxx, double syy,
  * bary(m, n(abc)) from signed areas (Tab. 1) and 2 ||n(abc)|| is the
  * Jacobian of Eq. 4, i.e. |(n_b - n_a) x (n_c - n_a)|.
  */
-static void pndf_one(const double *st, int N, const double *qq, int kernel,
+static void pndf_one(const double *st, int N, const double *qq, int kernel, double jac_eps,
                      double *D_out, uint32_t *flags_out, int64_t *nhits_out, uint32_t *hash_out)
 {
     double x = qq[0], y = qq[1], sxx = qq[2], sxy = qq[3], syy = qq[4], mx = qq[5], my = qq[6];
@@ -188,6 +207,13 @@ static void pndf_one(const double *st, int N, const double *qq, int kernel,
                     na = n3; nb = n2; nc = n1;
                 }
                 double A2 = area2(na[0], na[1], nb[0], nb[1], nc[0], nc[1]);
+                double E[3][2];
+                if (jac_eps > 0.0 && fabs(A2) < jac_eps) {
+                    /* Eq. 6: test the equilateral replacement (Jacobian eps) instead */
+                    eqtri(na, nb, nc, jac_eps, E);
+                    na = E[0]; nb = E[1]; nc = E[2];
+                    A2 = area2(na[0], na[1], nb[0], nb[1], nc[0], nc[1]);
+                }
                 /* edge proximity census (footprint triangles only) */
                 double lox = fmin(na[0], fmin(nb[0], nc[0])) - ORACLE_EDGE_EPS;
                 double hix = fmax(na[0], fmax(nb[0], nc[0])) + ORACLE_EDGE_EPS;
@@ -211,6 +237,7 @@ static void pndf_one(const double *st, int N, const double *qq, int kernel,
                 double dx = ux - x, dy = uy - y;
                 double q = ia * dx * dx + 2.0 * ib * dx * dy + ic * dy * dy;
                 double J = fabs(A2);
+                if (jac_eps > 0.0 && J < jac_eps) J = jac_eps;  /* the replacement's exact Jacobian */
                 if (kernel != OK_GAUSS) {
                     double w = flat_kernel(kernel, dx, dy, q, sxx, sxy, syy, det, &flags);
                     if (w == 0.0) continue;
@@ -238,11 +265,11 @@ static void pndf_one(const double *st, int N, const double *qq, int kernel,
 
 /* Evaluate queries [k0, k1) with footprint kernel `kernel` (OK_*).  Safe to
  * call concurrently on disjoint ranges. */
-void oracle_pndf(const double *st, int N, const double *q, int64_t k0, int64_t k1, int kernel,
+void oracle_pndf(const double *st, int N, const double *q, int64_t k0, int64_t k1, int kernel, double jac_eps,
                  double *D, uint32_t *flags, int64_t *nhits, uint32_t *hsum)
 {
     for (int64_t k = k0; k < k1; ++k)
-        pndf_one(st, N, q + 7 * k, kernel, D + k, flags + k, nhits + k, hsum + k);
+        pndf_one(st, N, q + 7 * k, kernel, jac_eps, D + k, flags + k, nhits + k, hsum + k);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -901,4 +928,73 @@ void oracle_pndf_cluster(const double *st, int N, const double *q, int64_t k0, i
 {
     for (int64_t k = k0; k < k1; ++k)
         pndf_cluster_one(st, N, q + 7 * k, kernel, tau, c_all, e_all, hull, D + k, flags + k, nhits + k, hsum + k);
+}
+
+/*
+ * P-NDF sampling (Sec. 3, Eq. 6): u ~ k_r(u - x) by the inverse CDF of the
+ * caller's uniforms (U1, U2) in the whitened frame v, u = x + L v (S = L L^T):
+ *   Gaussian cut at q = 16: |v|^2 = -2 ln(1 - U1 (1 - e^-8)), angle 2 pi U2;
+ *   disk: |v| = 1.5 sqrt(U1), angle 2 pi U2;   box: v = 1.5 (2 U1 - 1, 2 U2 - 1);
+ * then m = n(u) by Eq. 3 (the fine triangle holding u, barycentric), or the
+ * same barycentric point of the Eq. 6 replacement when jac_eps > 0 and the
+ * triangle's Jacobian is below it.  Flags per sample: 16 invalid S, 64 u
+ * outside the map (m = 0), 1 u within 1e-9 texel of a quad or diagonal edge
+ * (the triangle choice is a tie).  tri receives the triangle id (or -1).
+ */
+enum { OF_OUTSIDE = 64u };
+
+void oracle_sample(const double *st, int N, const double *q, const double *U, int64_t k0, int64_t k1, int kernel,
+                   double jac_eps, double *m_out, int64_t *tri_out, uint32_t *flags_out)
+{
+    for (int64_t k = k0; k < k1; ++k) {
+        const double *qq = q + 7 * k;
+        double x = qq[0], y = qq[1], sxx = qq[2], sxy = qq[3], syy = qq[4];
+        double det = sxx * syy - sxy * sxy;
+        double *m = m_out + 2 * k;
+        m[0] = m[1] = 0.0;
+        tri_out[k] = -1;
+        flags_out[k] = 0;
+        if (!(sxx > 0.0) || !(syy > 0.0) || !(det > 0.0)) {
+            flags_out[k] = OF_INVALID;
+            continue;
+        }
+        double u1 = U[2 * k], u2 = U[2 * k + 1], v1, v2;
+        if (kernel == OK_BOX) {
+            v1 = 1.5 * (2.0 * u1 - 1.0);
+            v2 = 1.5 * (2.0 * u2 - 1.0);
+        } else {
+            double r = kernel == OK_DISK ? 1.5 * sqrt(u1) : sqrt(-2.0 * log(1.0 - u1 * (1.0 - exp(-8.0))));
+            v1 = r * cos(2.0 * M_PI * u2);
+            v2 = r * sin(2.0 * M_PI * u2);
+        }
+        double l11 = sqrt(sxx), l21 = sxy / l11, l22 = sqrt(syy - l21 * l21);
+        double ux = x + l11 * v1, uy = y + l21 * v1 + l22 * v2;
+        double fi = floor(ux), fj = floor(uy);
+        if (!(fi >= 0.0 && fj >= 0.0 && fi <= N - 2 && fj <= N - 2)) {
+            flags_out[k] = OF_OUTSIDE;
+            continue;
+        }
+        int i = (int)fi, j = (int)fj;
+        double fu = ux - fi, fv = uy - fj;
+        const double tie = 1e-9;
+        if (fu < tie || fu > 1.0 - tie || fv < tie || fv > 1.0 - tie || fabs(fu + fv - 1.0) < tie)
+            flags_out[k] |= OF_NEAR_EDGE;
+        int tri = fu + fv < 1.0 ? 0 : 1;
+        double uv[3][2], nv[3][2], lam[3];
+        quad_tri(st, N, i, j, tri, uv, nv);
+        if (tri == 0) {
+            lam[0] = 1.0 - fu - fv; lam[1] = fu; lam[2] = fv;
+        } else {
+            lam[0] = fu + fv - 1.0; lam[1] = 1.0 - fu; lam[2] = 1.0 - fv;
+        }
+        double A2 = area2(nv[0][0], nv[0][1], nv[1][0], nv[1][1], nv[2][0], nv[2][1]);
+        if (jac_eps > 0.0 && fabs(A2) < jac_eps) {
+            double E[3][2];
+            eqtri(nv[0], nv[1], nv[2], jac_eps, E);
+            for (int c = 0; c < 2; ++c) m[c] = lam[0] * E[0][c] + lam[1] * E[1][c] + lam[2] * E[2][c];
+        } else {
+            for (int c = 0; c < 2; ++c) m[c] = lam[0] * nv[0][c] + lam[1] * nv[1][c] + lam[2] * nv[2][c];
+        }
+        tri_out[k] = 2 * ((int64_t)j * (N - 1) + i) + tri;
+    }
 }

@@ -12,7 +12,10 @@ App. A): the other cluster diagonal or hat functions, an unweighted fit, the
 squared residual, a cluster Jacobian without its 2^(2l) scale, swapped
 barycentric roles or corners, and a cut on the wrong footprint size.  For
 the disk and box kernels: a 3-sigma disk, the box sheared by the upper
-Cholesky factor, and the box normalised as a unit square.
+Cholesky factor, and the box normalised as a unit square.  For the Eq. 6
+clamp and sampling: a replacement of area eps, a Jacobian of eps / 2, an
+untruncated sampling radius, a transposed Cholesky factor and the other
+diagonal for the sample's triangle.
 """
 
 import os
@@ -61,6 +64,16 @@ def mass_box(m):
 
 KERNEL_PINS = [affine_disk, affine_box, mass_disk, mass_box, pins.test_binning_box_kernel]
 
+import test_oracle_sampling as spins  # noqa: E402
+
+
+def samples_on_triangles(m):
+    spins.test_samples_lie_on_their_triangles(m, 0)
+
+
+SAMPLING_PINS = [spins.test_clamp_keeps_the_mass_of_flat_triangles, spins.test_sample_frequencies_follow_the_kernel,
+                 samples_on_triangles, spins.test_binned_samples_match_clamped_pndf]
+
 CLUSTER_PINS = [cpins.test_fit_recovers_piecewise_linear_data, cluster_dense_fit_level3, cluster_mass_all_cut,
                 cluster_mass_mixed, cpins.test_cluster_binning_with_anisotropic_cut,
                 cpins.test_cluster_transpose_symmetry, cpins.test_piecewise_linear_map_is_unchanged_by_any_cut]
@@ -102,6 +115,16 @@ MUTANTS = {
                              "double v2 = dy / l11, v1 = (dx - l21 * v2) / l22;")], KERNEL_PINS),
     "box_norm_unit_square": ([("return vm <= 1.5 ? 1.0 / (9.0 * sqrt(det)) : 0.0;",
                                "return vm <= 1.5 ? 1.0 / (4.0 * sqrt(det)) : 0.0;")], KERNEL_PINS),
+    # Jacobian clamp (Eq. 6) and sampling
+    "eqtri_area_eps": ([("double side = sqrt(2.0 * eps / sqrt(3.0));", "double side = sqrt(4.0 * eps / sqrt(3.0));")],
+                       SAMPLING_PINS),
+    "clamp_jacobian_half_eps": ([("if (jac_eps > 0.0 && J < jac_eps) J = jac_eps;",
+                                  "if (jac_eps > 0.0 && J < jac_eps) J = 0.5 * jac_eps;")], SAMPLING_PINS),
+    "sampler_untruncated": ([("sqrt(-2.0 * log(1.0 - u1 * (1.0 - exp(-8.0))))", "sqrt(-2.0 * log(1.0 - u1))")],
+                            SAMPLING_PINS),
+    "sampler_cholesky_transposed": ([("double ux = x + l11 * v1, uy = y + l21 * v1 + l22 * v2;",
+                                      "double ux = x + l11 * v1 + l21 * v2, uy = y + l22 * v2;")], SAMPLING_PINS),
+    "sampler_other_diagonal": ([("int tri = fu + fv < 1.0 ? 0 : 1;", "int tri = fu < fv ? 0 : 1;")], SAMPLING_PINS),
     # cluster hierarchy (Eq. 7-8, App. A) and the tau cut
     "cluster_fit_main_diagonal": ([("        phi[0] = 1.0 - s - t; phi[1] = s; phi[2] = t; phi[3] = 0.0;",
                                     "        phi[0] = 1.0 - s; phi[1] = s - t; phi[2] = 0.0; phi[3] = t;"),
