@@ -134,6 +134,12 @@ typedef struct pndf_eval_config {
                             /* 0 = exact (no cluster).  Needs a hierarchy built with   */
                             /* clusters = 1, else UNSUPPORTED.  Hierarchy mode only.   */
     int32_t kernel;         /* footprint kernel (pndf_kernel)                          */
+    float jac_eps;          /* Jacobian clamp of Eq. 6: 0 = exact; else (>= 1e-9, e.g.  */
+                            /* 1e-6) a fine triangle with |cross| < jac_eps counts as  */
+                            /* an equilateral one of Jacobian jac_eps centred at its   */
+                            /* normal centroid.  Gaussian kernel, hierarchy mode, no   */
+                            /* cluster cut (else UNSUPPORTED).                         */
+    int32_t reserved;       /* must be 0                                              */
     void *ev_begin;         /* optional cudaEvent_t recorded on the stream just before */
     void *ev_end;           /* and just after the traversal kernel (NULL = none)       */
 } pndf_eval_config;
@@ -176,6 +182,31 @@ void pndf_free_hierarchy(pndf_hierarchy *h);
 
 /* Device bytes held by a hierarchy (texel copy + pyramid). */
 size_t pndf_hierarchy_bytes(const pndf_hierarchy *h);
+
+/* Per-sample flags of pndf_sample_normals. */
+#define PNDF_SF_INVALID 1u    /* covariance not positive definite: m = 0                        */
+#define PNDF_SF_OUTSIDE 2u    /* the sampled uv point lies outside the map: m = 0               */
+
+/*
+ * P-NDF sampling (Sec. 3, Eq. 6): one normal per record of q_dev (its x and S
+ * are used), drawn by sampling the footprint kernel u ~ k_r(u - x) and
+ * querying m = n(u) (Eq. 3); with jac_eps > 0 a fine triangle whose |cross|
+ * is below jac_eps stands for its equilateral replacement (as in
+ * pndf_eval_config.jac_eps), so the sampled normals have density D (clamped
+ * alike) over the kernel mass.  u is the inverse CDF of the caller's two
+ * uniforms per sample in the whitened frame v (u = x + L v, S = L L^T):
+ * Gaussian (cut at 4 sigma) |v|^2 = -2 ln(1 - U1 (1 - e^-8)), angle 2 pi U2;
+ * disk |v| = 1.5 sqrt(U1), angle 2 pi U2; box v = 1.5 (2 U1 - 1, 2 U2 - 1).
+ *   u_dev:     device, 2n floats in [0, 1] (U1, U2 per sample)
+ *   m_out_dev: device, 2n floats (s, t per sample)
+ *   tri_out_dev (nullable): device, n triangle ids 2 (j (N-1) + i) + (0 | 1), or ~0u
+ *   flags_out_dev (nullable): device, n PNDF_SF_* words
+ * Asynchronous on stream.  Errors: INVALID_ARG (null or misaligned pointers,
+ * n < 0, kernel, jac_eps outside 0 or [1e-9, 1e-2]), CUDA.
+ */
+pndf_status pndf_sample_normals(const pndf_hierarchy *h, const pndf_query *q_dev, const float *u_dev, int64_t n,
+                                int32_t kernel, float jac_eps, float *m_out_dev, uint32_t *tri_out_dev,
+                                uint32_t *flags_out_dev, void *stream);
 
 /* Copy out level l (2 <= l <= L, 2^L >= N-1) of the cluster hierarchy
  * (Sec. 4.3, Eq. 7-8) for inspection, nodes in row-major order (J, I),

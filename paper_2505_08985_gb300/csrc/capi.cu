@@ -153,6 +153,24 @@ void pndf_free_hierarchy(pndf_hierarchy *h)
 
 size_t pndf_hierarchy_bytes(const pndf_hierarchy *h) { return h ? h->bytes : 0; }
 
+pndf_status pndf_sample_normals(const pndf_hierarchy *h, const pndf_query *q_dev, const float *u_dev, int64_t n,
+                                int32_t kernel, float jac_eps, float *m_out_dev, uint32_t *tri_out_dev,
+                                uint32_t *flags_out_dev, void *stream)
+{
+    pndf_status st = check_hierarchy(h);
+    if (st != PNDF_OK) return st;
+    if (n < 0 || (n > 0 && (!q_dev || !u_dev || !m_out_dev))) return PNDF_ERR_INVALID_ARG;
+    if ((q_dev && !aligned(q_dev, 16)) || (u_dev && !aligned(u_dev, 4)) || (m_out_dev && !aligned(m_out_dev, 4)))
+        return PNDF_ERR_INVALID_ARG;
+    if (kernel != PNDF_KERNEL_GAUSS && kernel != PNDF_KERNEL_DISK && kernel != PNDF_KERNEL_BOX)
+        return PNDF_ERR_INVALID_ARG;
+    if (!(jac_eps == 0.f || (jac_eps >= 1e-9f && jac_eps <= 1e-2f))) return PNDF_ERR_INVALID_ARG;
+    return launch_sample(h, q_dev, u_dev, n, kernel, jac_eps, m_out_dev, tri_out_dev, flags_out_dev,
+                         as_stream(stream)) == cudaSuccess
+               ? PNDF_OK
+               : PNDF_ERR_CUDA;
+}
+
 pndf_status pndf_cluster_level(const pndf_hierarchy *h, int32_t level, float *records_dev, float *residual_dev,
                                void *stream)
 {
@@ -174,12 +192,16 @@ pndf_status pndf_eval_batch_ex(const pndf_hierarchy *h, const pndf_query *q_dev,
     if (nq < 0 || nq > int64_t(0x7fffffff)) return PNDF_ERR_INVALID_ARG;
     if (nq > 0 && (!q_dev || !D_out_dev)) return PNDF_ERR_INVALID_ARG;
     if (q_dev && !aligned(q_dev, 16)) return PNDF_ERR_INVALID_ARG;
-    pndf_eval_config c{PNDF_MODE_HIERARCHY, PNDF_SORT_DEFAULT, 0, 0, 0.f, PNDF_KERNEL_GAUSS, nullptr, nullptr};
+    pndf_eval_config c{PNDF_MODE_HIERARCHY, PNDF_SORT_DEFAULT, 0, 0, 0.f, PNDF_KERNEL_GAUSS, 0.f, 0, nullptr, nullptr};
     if (cfg) c = *cfg;
     if (c.mode != PNDF_MODE_HIERARCHY && c.mode != PNDF_MODE_FLAT) return PNDF_ERR_INVALID_ARG;
     if (!(c.tau >= 0.f) || !isfinite(c.tau)) return PNDF_ERR_INVALID_ARG;
     if (c.kernel != PNDF_KERNEL_GAUSS && c.kernel != PNDF_KERNEL_DISK && c.kernel != PNDF_KERNEL_BOX)
         return PNDF_ERR_INVALID_ARG;
+    if (!(c.jac_eps == 0.f || (c.jac_eps >= 1e-9f && c.jac_eps <= 1e-2f)) || c.reserved != 0)
+        return PNDF_ERR_INVALID_ARG;
+    if (c.jac_eps > 0.f && (c.kernel != PNDF_KERNEL_GAUSS || c.mode != PNDF_MODE_HIERARCHY || c.tau > 0.f))
+        return PNDF_ERR_UNSUPPORTED;
     if (c.tau > 0.f && (!h->clusters || c.mode != PNDF_MODE_HIERARCHY)) return PNDF_ERR_UNSUPPORTED;
     if (c.sort < 0 || c.sort > 4) return PNDF_ERR_INVALID_ARG;
     if (c.warps_per_cta < 0 || c.warps_per_cta > 8 || c.ctas_per_sm < 0) return PNDF_ERR_INVALID_ARG;
@@ -236,7 +258,7 @@ pndf_status pndf_eval_batch_host(const pndf_hierarchy *h, const pndf_query *q_ho
     float *Dd = static_cast<float *>(buf);
     pndf_query *qd = reinterpret_cast<pndf_query *>(static_cast<char *>(buf) + qoff);
     cudaError_t e = cudaMemcpyAsync(qd, q_host, qb, cudaMemcpyHostToDevice, s);
-    pndf_eval_config c{PNDF_MODE_HIERARCHY, PNDF_SORT_DEFAULT, 0, 0, 0.f, PNDF_KERNEL_GAUSS, nullptr, nullptr};
+    pndf_eval_config c{PNDF_MODE_HIERARCHY, PNDF_SORT_DEFAULT, 0, 0, 0.f, PNDF_KERNEL_GAUSS, 0.f, 0, nullptr, nullptr};
     if (e == cudaSuccess) st = launch_eval(h, qd, nq, Dd, nullptr, nullptr, c, s);
     if (e == cudaSuccess && st == PNDF_OK) e = cudaMemcpyAsync(D_host, Dd, db, cudaMemcpyDeviceToHost, s);
     cudaError_t ef = cudaFreeAsync(buf, s);

@@ -152,6 +152,9 @@ cudaError_t launch_build(const void *texels_src, pndf_hierarchy *h, cudaStream_t
 cudaError_t launch_clusters(pndf_hierarchy *h, cudaStream_t s);
 // Bytes of the cluster build scratch for a pyramid of height L.
 size_t cluster_scratch_bytes(int L);
+// P-NDF sampling (sample.cu).
+cudaError_t launch_sample(const pndf_hierarchy *h, const pndf_query *q, const float *u, int64_t n, int kernel,
+                          float jac_eps, float *m, uint32_t *tri, uint32_t *flags, cudaStream_t s);
 // Level l's cluster records and residuals in row-major node order.
 cudaError_t launch_cluster_copy(const pndf_hierarchy *h, int l, float *rec, float *e, cudaStream_t s);
 pndf_status launch_eval(const pndf_hierarchy *h, const pndf_query *q, int64_t nq, float *D, uint32_t *flags,

@@ -93,13 +93,24 @@ struct Query {
     float theta;         // r_x r_y of the support (exact half-widths); times tau for the cluster cut
     float inv_sxx;       // box: 1 / S_xx, so that (L^-1 d)_x^2 = dx^2 / S_xx
     float l11, l21, l22; // box: the Cholesky factor L of S (node tests by separating axes)
+    float jac, rho;      // Eq. 6 clamp: Jacobian floor eps and the replacement's circumradius (0: off)
     int kernel;
     bool valid;
 };
 
-__device__ __forceinline__ Query make_query(const pndf_query &r, int kernel = PNDF_KERNEL_GAUSS)
+// Internal kernel id of the Gaussian with the Jacobian clamp of Eq. 6.
+constexpr int kKernGaussClamp = 3;
+
+__device__ __forceinline__ Query make_query(const pndf_query &r, int kernel = PNDF_KERNEL_GAUSS, float jac_eps = 0.f)
 {
     Query q;
+    q.jac = q.rho = 0.f;
+    if (kernel == kKernGaussClamp) {
+        // equilateral replacement of area eps / 2: side^2 = 2 eps / sqrt(3), circumradius side / sqrt(3)
+        q.jac = jac_eps;
+        q.rho = sqrtf(2.0f * jac_eps / 1.7320508f) * 0.57735027f;
+        kernel = PNDF_KERNEL_GAUSS;
+    }
     q.x = r.x;
     q.y = r.y;
     q.mx = r.ms;
@@ -248,8 +259,12 @@ __device__ __forceinline__ bool node_inside(const Query &q, int l, uint32_t a, u
     return m <= q.qprune;
 }
 
+// m in the box, widened by the clamp's replacement radius (a replacement
+// lies within rho of its triangle's centroid, hence of its box).
 __device__ __forceinline__ bool box_holds(const float4 &b, const Query &q)
 {
+    if (q.rho != 0.f)
+        return q.mx >= b.x - q.rho && q.mx <= b.z + q.rho && q.my >= b.y - q.rho && q.my <= b.w + q.rho;
     return q.mx >= b.x && q.mx <= b.z && q.my >= b.y && q.my <= b.w;
 }
 
@@ -358,10 +373,26 @@ __device__ __forceinline__ bool edge_test(const Query &q, float2 na, float2 nb, 
                                           uint32_t tri_id, Acc &acc, float &cr_o, float &e1_o, float &e2_o)
 {
     if (STATS) acc.tests++;
-    float lox = fminf(na.x, fminf(nb.x, nc.x)), hix = fmaxf(na.x, fmaxf(nb.x, nc.x));
-    float loy = fminf(na.y, fminf(nb.y, nc.y)), hiy = fmaxf(na.y, fmaxf(nb.y, nc.y));
+    float lox = fminf(na.x, fminf(nb.x, nc.x)) - q.rho, hix = fmaxf(na.x, fmaxf(nb.x, nc.x)) + q.rho;
+    float loy = fminf(na.y, fminf(nb.y, nc.y)) - q.rho, hiy = fmaxf(na.y, fmaxf(nb.y, nc.y)) + q.rho;
     if (q.mx < lox || q.mx > hix || q.my < loy || q.my > hiy) return false;
     float cr = orient(na.x, na.y, nb.x, nb.y, nc.x, nc.y);
+    if (q.jac != 0.f && fabsf(cr) < q.jac) {
+        // Eq. 6: the equilateral replacement (vertex k at 90 + 120 k degrees
+        // around the centroid g, radius rho), in vertex-relative form p = m - E0
+        const float gx = (na.x + nb.x + nc.x) * (1.0f / 3.0f), gy = (na.y + nb.y + nc.y) * (1.0f / 3.0f);
+        const float h = 0.8660254f * q.rho;  // E1 - E0 = rho (-sqrt3/2, -3/2), E2 - E0 = rho (sqrt3/2, -3/2)
+        const float2 b = make_float2(-h, -1.5f * q.rho), c = make_float2(h, -1.5f * q.rho);
+        const float2 p = make_float2(q.mx - gx, (q.my - gy) - q.rho);
+        const float ecr = dop(b.x, c.y, b.y, c.x);
+        const float e0 = dop(c.x - b.x, p.y - b.y, c.y - b.y, p.x - b.x);
+        const float e1 = dop(p.x, c.y, p.y, c.x);
+        const float e2 = dop(b.x, p.y, b.y, p.x);
+        cr_o = ecr;  // > 0: counter-clockwise
+        e1_o = e1;
+        e2_o = e2;
+        return e0 >= 0.f && e1 >= 0.f && e2 >= 0.f;
+    }
     if (fabsf(cr) >= kTinyCross) {
         float e0 = orient(nb.x, nb.y, nc.x, nc.y, q.mx, q.my);
         float e1 = orient(nc.x, nc.y, na.x, na.y, q.mx, q.my);
@@ -627,7 +658,7 @@ __device__ __forceinline__ void test_clusters(const MapDesc &d, const ClusterDes
 // Four level-0 boxes (Morton-consecutive quads) in one 32-byte (FP16) or
 // 64-byte (FP32) load; returns bit u set when box u holds m.
 template <int BFMT>
-__device__ __forceinline__ unsigned quad_boxes_hold(const MapDesc &d, uint32_t first, float mx, float my)
+__device__ __forceinline__ unsigned quad_boxes_hold(const MapDesc &d, uint32_t first, float mx, float my, float rho)
 {
     unsigned bits = 0;
     if (BFMT == PNDF_BOUNDS_F32) {
@@ -637,7 +668,7 @@ __device__ __forceinline__ unsigned quad_boxes_hold(const MapDesc &d, uint32_t f
         for (int u = 0; u < 4; ++u) b[u] = __ldg(p + u);
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-            bits |= unsigned(mx >= b[u].x && mx <= b[u].z && my >= b[u].y && my <= b[u].w) << u;
+            bits |= unsigned(mx >= b[u].x - rho && mx <= b[u].z + rho && my >= b[u].y - rho && my <= b[u].w + rho) << u;
     } else {
         const uint4 *p = reinterpret_cast<const uint4 *>(reinterpret_cast<const uint2 *>(d.lv[0]) + first);
         uint4 v0 = __ldg(p), v1 = __ldg(p + 1);
@@ -646,7 +677,7 @@ __device__ __forceinline__ unsigned quad_boxes_hold(const MapDesc &d, uint32_t f
         for (int u = 0; u < 4; ++u) {
             float2 lo = __half22float2(*reinterpret_cast<__half2 *>(&w[2 * u]));
             float2 hi = __half22float2(*reinterpret_cast<__half2 *>(&w[2 * u + 1]));
-            bits |= unsigned(mx >= lo.x && mx <= hi.x && my >= lo.y && my <= hi.y) << u;
+            bits |= unsigned(mx >= lo.x - rho && mx <= hi.x + rho && my >= lo.y - rho && my <= hi.y + rho) << u;
         }
     }
     return bits;
@@ -670,7 +701,7 @@ __device__ __forceinline__ void process_leaves(const MapDesc &d, const Query &q,
             uint32_t m = lq[blk] & kMortonMask;
             a = compact1by1(m);
             c = compact1by1(m >> 1);
-            bits = quad_boxes_hold<BFMT>(d, (m << 4) | k0, q.mx, q.my);
+            bits = quad_boxes_hold<BFMT>(d, (m << 4) | k0, q.mx, q.my, q.rho);
             if (STATS) {
                 acc.quads += 4;
                 if ((lane & 3) == 0) acc.leaves++;
@@ -726,11 +757,11 @@ __device__ __forceinline__ int entry_level(const Query &q, int L)
 // query's kernel fields and branches fold away (each kernel is its own
 // instantiation).
 template <int BFMT, int TFMT, bool STATS, bool FLAT, bool CLUSTER, int KERN>
-__device__ void eval_one(const MapDesc &d, const ClusterDesc &cd, float tau, const pndf_query &rec, int lane,
-                         uint32_t *stk, uint32_t *lq, uint32_t *ring, float4 *hits, float &D_out,
+__device__ void eval_one(const MapDesc &d, const ClusterDesc &cd, float tau, float jac_eps, const pndf_query &rec,
+                         int lane, uint32_t *stk, uint32_t *lq, uint32_t *ring, float4 *hits, float &D_out,
                          uint32_t &flags_out, pndf_query_stats *st_out)
 {
-    Query q = make_query(rec, KERN);
+    Query q = make_query(rec, KERN, jac_eps);
     Acc acc = {};
     if (!q.valid) {
         if (lane == 0) {
@@ -912,7 +943,7 @@ __device__ void eval_one(const MapDesc &d, const ClusterDesc &cd, float tau, con
 
 template <int BFMT, int TFMT, bool STATS, bool FLAT, bool CLUSTER, int KERN>
 __global__ void __launch_bounds__(256, PNDF_TRAVERSE_MIN_CTAS)
-    traverse_kernel(MapDesc d, ClusterDesc cd, float tau, const pndf_query *__restrict__ qs,
+    traverse_kernel(MapDesc d, ClusterDesc cd, float tau, float jac_eps, const pndf_query *__restrict__ qs,
                     const uint32_t *__restrict__ order, int64_t nq, float *__restrict__ D,
                     uint32_t *__restrict__ flags, pndf_query_stats *__restrict__ stats,
                     unsigned long long *__restrict__ cursor)
@@ -932,7 +963,7 @@ __global__ void __launch_bounds__(256, PNDF_TRAVERSE_MIN_CTAS)
         pndf_query rec = qs[qi];
         float Dv;
         uint32_t fv;
-        eval_one<BFMT, TFMT, STATS, FLAT, CLUSTER, KERN>(d, cd, tau, rec, lane, stk, lq, ring, hits, Dv, fv,
+        eval_one<BFMT, TFMT, STATS, FLAT, CLUSTER, KERN>(d, cd, tau, jac_eps, rec, lane, stk, lq, ring, hits, Dv, fv,
                                                          stats ? stats + qi : nullptr);
         if (lane == 0) {
             D[qi] = Dv;
@@ -1074,7 +1105,7 @@ inline size_t sort_hist_bytes(int64_t nq)
 }
 
 template <int BFMT, int TFMT, bool STATS, bool FLAT, bool CLUSTER, int KERN>
-cudaError_t launch_traverse(const MapDesc &d, const ClusterDesc &cd, float tau, const pndf_query *q,
+cudaError_t launch_traverse(const MapDesc &d, const ClusterDesc &cd, float tau, float jac_eps, const pndf_query *q,
                             const uint32_t *order, int64_t nq, float *D, uint32_t *flags, pndf_query_stats *stats,
                             unsigned long long *cursor, int warps, int ctas_per_sm, cudaStream_t s)
 {
@@ -1092,7 +1123,7 @@ cudaError_t launch_traverse(const MapDesc &d, const ClusterDesc &cd, float tau, 
     int64_t grid = int64_t(sms) * occ;
     if (grid > want) grid = want;
     if (grid < 1) grid = 1;
-    kern<<<unsigned(grid), threads, smem, s>>>(d, cd, tau, q, order, nq, D, flags, stats, cursor);
+    kern<<<unsigned(grid), threads, smem, s>>>(d, cd, tau, jac_eps, q, order, nq, D, flags, stats, cursor);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1106,18 +1137,18 @@ cudaError_t dispatch_kernel(const MapDesc &d, const ClusterDesc &cd, const pndf_
     const int cps = cfg.ctas_per_sm;
     const float tau = cfg.tau;
     if (cfg.mode == PNDF_MODE_FLAT)
-        return stats ? launch_traverse<BFMT, TFMT, true, true, false, KERN>(d, cd, 0.f, q, order, nq, D, flags, stats,
+        return stats ? launch_traverse<BFMT, TFMT, true, true, false, KERN>(d, cd, 0.f, cfg.jac_eps, q, order, nq, D, flags, stats,
                                                                              cursor, warps, cps, s)
-                     : launch_traverse<BFMT, TFMT, false, true, false, KERN>(d, cd, 0.f, q, order, nq, D, flags, stats,
+                     : launch_traverse<BFMT, TFMT, false, true, false, KERN>(d, cd, 0.f, cfg.jac_eps, q, order, nq, D, flags, stats,
                                                                               cursor, warps, cps, s);
     if (tau > 0.f)
-        return stats ? launch_traverse<BFMT, TFMT, true, false, true, KERN>(d, cd, tau, q, order, nq, D, flags, stats,
+        return stats ? launch_traverse<BFMT, TFMT, true, false, true, KERN>(d, cd, tau, cfg.jac_eps, q, order, nq, D, flags, stats,
                                                                              cursor, warps, cps, s)
-                     : launch_traverse<BFMT, TFMT, false, false, true, KERN>(d, cd, tau, q, order, nq, D, flags, stats,
+                     : launch_traverse<BFMT, TFMT, false, false, true, KERN>(d, cd, tau, cfg.jac_eps, q, order, nq, D, flags, stats,
                                                                               cursor, warps, cps, s);
-    return stats ? launch_traverse<BFMT, TFMT, true, false, false, KERN>(d, cd, 0.f, q, order, nq, D, flags, stats,
+    return stats ? launch_traverse<BFMT, TFMT, true, false, false, KERN>(d, cd, 0.f, cfg.jac_eps, q, order, nq, D, flags, stats,
                                                                           cursor, warps, cps, s)
-                 : launch_traverse<BFMT, TFMT, false, false, false, KERN>(d, cd, 0.f, q, order, nq, D, flags, stats,
+                 : launch_traverse<BFMT, TFMT, false, false, false, KERN>(d, cd, 0.f, cfg.jac_eps, q, order, nq, D, flags, stats,
                                                                            cursor, warps, cps, s);
 }
 
@@ -1126,6 +1157,13 @@ cudaError_t dispatch_stats(const MapDesc &d, const ClusterDesc &cd, const pndf_q
                            int64_t nq, float *D, uint32_t *flags, pndf_query_stats *stats,
                            unsigned long long *cursor, const pndf_eval_config &cfg, cudaStream_t s)
 {
+    if (cfg.jac_eps > 0.f)  // Gaussian, hierarchy mode, no cluster cut (checked by the caller)
+        return stats ? launch_traverse<BFMT, TFMT, true, false, false, kKernGaussClamp>(
+                           d, cd, 0.f, cfg.jac_eps, q, order, nq, D, flags, stats, cursor,
+                           cfg.warps_per_cta > 0 ? cfg.warps_per_cta : 8, cfg.ctas_per_sm, s)
+                     : launch_traverse<BFMT, TFMT, false, false, false, kKernGaussClamp>(
+                           d, cd, 0.f, cfg.jac_eps, q, order, nq, D, flags, stats, cursor,
+                           cfg.warps_per_cta > 0 ? cfg.warps_per_cta : 8, cfg.ctas_per_sm, s);
     if (cfg.kernel == PNDF_KERNEL_DISK)
         return dispatch_kernel<BFMT, TFMT, PNDF_KERNEL_DISK>(d, cd, q, order, nq, D, flags, stats, cursor, cfg, s);
     if (cfg.kernel == PNDF_KERNEL_BOX)
@@ -1255,8 +1293,8 @@ __global__ void __launch_bounds__(256, PNDF_TRAVERSE_MIN_CTAS)
         const pndf_query rec = sg.q[qi];
         float Dv;
         uint32_t fv;
-        eval_one<BFMT, TFMT, false, false, false, PNDF_KERNEL_GAUSS>(smaps[sg.map], kNoClusters, 0.f, rec, lane, stk,
-                                                                     lq, ring, hits, Dv, fv, nullptr);
+        eval_one<BFMT, TFMT, false, false, false, PNDF_KERNEL_GAUSS>(smaps[sg.map], kNoClusters, 0.f, 0.f, rec, lane,
+                                                                     stk, lq, ring, hits, Dv, fv, nullptr);
         if (lane == 0) {
             sg.D[qi] = Dv;
             if (sg.flags) sg.flags[qi] = fv;
@@ -1361,7 +1399,7 @@ pndf_status launch_eval_noalloc(const pndf_hierarchy *h, const pndf_query *q, in
     void *scratch = nullptr;
     if (noalloc_scratch(&scratch) != cudaSuccess) return PNDF_ERR_CUDA;
     const MapDesc &d = h->d;
-    pndf_eval_config cfg{PNDF_MODE_HIERARCHY, PNDF_SORT_DEFAULT, 0, 0, 0.f, PNDF_KERNEL_GAUSS, nullptr, nullptr};
+    pndf_eval_config cfg{PNDF_MODE_HIERARCHY, PNDF_SORT_DEFAULT, 0, 0, 0.f, PNDF_KERNEL_GAUSS, 0.f, 0, nullptr, nullptr};
     char *base = static_cast<char *>(scratch);
     auto *cursor = reinterpret_cast<unsigned long long *>(base);
     auto *hist = reinterpret_cast<uint32_t *>(base + kNoallocHistOff);

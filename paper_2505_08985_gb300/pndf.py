@@ -33,6 +33,11 @@ PNDF_QF_OVERFLOW = 8
 STATS_FIELDS = ("nodes", "leaf_blocks", "tri_tests", "hits", "hit_hash", "fp64_tris", "degenerate", "quads")
 
 
+PNDF_KERNEL_GAUSS = 0  # footprint kernels (pndf_kernel): Gaussian cut at 4 sigma,
+PNDF_KERNEL_DISK = 1   # disk and box of the (3 sigma)^2 footprint
+PNDF_KERNEL_BOX = 2
+
+
 class PndfError(RuntimeError):
     def __init__(self, fn: str, code: int):
         super().__init__(f"{fn}: {STATUS_NAMES.get(code, code)} (status {code})")
@@ -47,6 +52,7 @@ class _BuildParams(ctypes.Structure):
 class _EvalConfig(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("sort", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("tau", ctypes.c_float), ("kernel", ctypes.c_int32),
+                ("jac_eps", ctypes.c_float), ("reserved", ctypes.c_int32),
                 ("ev_begin", ctypes.c_void_p), ("ev_end", ctypes.c_void_p)]
 
 
@@ -74,6 +80,7 @@ def _load() -> ctypes.CDLL:
         "pndf_update_hierarchy": ([vp, vp, vp], i32),
         "pndf_hierarchy_bytes": ([vp], ctypes.c_size_t),
         "pndf_cluster_level": ([vp, i32, vp, vp, vp], i32),
+        "pndf_sample_normals": ([vp, vp, vp, i64, i32, ctypes.c_float, vp, vp, vp, vp], i32),
         "pndf_eval_batch": ([vp, vp, i64, vp, vp, vp, vp], i32),
         "pndf_eval_batch_ex": ([vp, vp, i64, vp, vp, vp, ctypes.POINTER(_EvalConfig), vp], i32),
         "pndf_eval_batch_host": ([vp, vp, i64, vp, vp], i32),
@@ -200,6 +207,29 @@ def top_level(n: int) -> int:
     return max(L, 2)
 
 
+PNDF_SF_INVALID = 1
+PNDF_SF_OUTSIDE = 2
+
+
+def pndf_sample_normals(h: Hierarchy, queries: torch.Tensor, uniforms: torch.Tensor, kernel: int = PNDF_KERNEL_GAUSS,
+                        jac_eps: float = 0.0, stream=None):
+    """Eq. 6 sampling: one normal per query record from its two uniforms
+    (uniforms: (n, 2) float32 CUDA tensor in [0, 1]).  Returns m (n, 2)
+    float32, triangle ids (n,) int32 (-1 where none) and flags (n,) int32."""
+    n = _queries(queries)
+    _need(uniforms, "uniforms", dtype=torch.float32, shape_last=2)
+    if uniforms.shape[0] != n:
+        raise ValueError("one pair of uniforms per query")
+    m = torch.empty(n, 2, dtype=torch.float32, device=queries.device)
+    tri = torch.empty(n, dtype=torch.int32, device=queries.device)
+    flags = torch.empty(n, dtype=torch.int32, device=queries.device)
+    with torch.cuda.device(queries.device):
+        _check("pndf_sample_normals", LIB.pndf_sample_normals(h.handle, _ptr(queries), _ptr(uniforms), n, int(kernel),
+                                                              float(jac_eps), _ptr(m), _ptr(tri), _ptr(flags),
+                                                              _stream(stream)))
+    return m, tri, flags
+
+
 def pndf_cluster_level(h: Hierarchy, level: int, stream=None):
     """Level `level` of the cluster hierarchy: records (S, S, 8) float32 as
     (c00, d10, d01, d11) pairs with corners c = c00 + d, and residuals (S, S),
@@ -242,20 +272,18 @@ PNDF_SORT_LEVEL_NORMAL_TILE = 4
 PNDF_SORT_DEFAULT = PNDF_SORT_LEVEL_TILE
 
 
-PNDF_KERNEL_GAUSS = 0  # footprint kernels (pndf_kernel): Gaussian cut at 4 sigma,
-PNDF_KERNEL_DISK = 1   # disk and box of the (3 sigma)^2 footprint
-PNDF_KERNEL_BOX = 2
-
 STATS_FIELDS = 10  # pndf_query_stats: nodes, leaf_blocks, tri_tests, hits, hit_hash, fp64_tris, degenerate,
                    # quads, cluster_checks, clusters
 
 
 def pndf_eval_batch_ex(h: Hierarchy, queries: torch.Tensor, out=None, flags=None, stats=None, mode: int = 0,
                        sort: int = PNDF_SORT_DEFAULT, warps_per_cta: int = 0, ctas_per_sm: int = 0, stream=None,
-                       ev_begin=None, ev_end=None, tau: float = 0.0, kernel: int = PNDF_KERNEL_GAUSS) -> torch.Tensor:
+                       ev_begin=None, ev_end=None, tau: float = 0.0, kernel: int = PNDF_KERNEL_GAUSS,
+                       jac_eps: float = 0.0) -> torch.Tensor:
     """ev_begin / ev_end: optional torch.cuda.Event recorded around the traversal kernel.
     tau > 0: the cluster cut of Sec. 4.3 (the hierarchy must be built with clusters=True).
-    kernel: footprint kernel (PNDF_KERNEL_GAUSS, _DISK, _BOX)."""
+    kernel: footprint kernel (PNDF_KERNEL_GAUSS, _DISK, _BOX).
+    jac_eps > 0: the Jacobian clamp of Eq. 6 (e.g. 1e-6)."""
     nq = _queries(queries)
     if out is None:
         out = torch.empty(nq, dtype=torch.float32, device=queries.device)
@@ -265,6 +293,7 @@ def pndf_eval_batch_ex(h: Hierarchy, queries: torch.Tensor, out=None, flags=None
     if stats is not None:
         _need(stats, "stats", dtype=torch.int32, shape_last=STATS_FIELDS)
     cfg = _EvalConfig(int(mode), int(sort), int(warps_per_cta), int(ctas_per_sm), float(tau), int(kernel),
+                      float(jac_eps), 0,
                       _event_handle(ev_begin), _event_handle(ev_end))
     with torch.cuda.device(queries.device):
         _check("pndf_eval_batch_ex", LIB.pndf_eval_batch_ex(h.handle, _ptr(queries), nq, _ptr(out), _ptr(flags),
