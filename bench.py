@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernels", default="disk,box", help="footprint kernels to measure besides the Gaussian ('' = skip)")
+    ap.add_argument("--no-clamp-sampling", action="store_true", help="skip the Eq. 6 clamp and sampling figures")
     ap.add_argument("--cluster-taus", default="1e-4,1e-3",
                     help="cluster cut thresholds to measure on the same workload ('' = skip)")
     ap.add_argument("--serve-batches", type=int, default=2000, help="serving workload size (0 = skip serving)")
@@ -491,6 +492,45 @@ def run_kernels(args, world, st, q, gauss_kernel_ms, gauss_tri_tests):
     return out
 
 
+def run_clamp_sampling(args, world, st, q, gauss_kernel_ms, D_exact):
+    """The Jacobian clamp of Eq. 6 (eps = 1e-6) on the bench workload, and
+    P-NDF sampling: one normal per query footprint from two uniforms each
+    (a step = one call over all 4M footprints, uniforms resident)."""
+    from paper_2505_08985_gb300 import pndf
+    dev = q.device
+    nq = q.shape[0]
+    stream = torch.cuda.current_stream()
+    eps = 1e-6
+    D = torch.empty(nq, dtype=torch.float32, device=dev)
+    h = pndf.pndf_build_hierarchy(st, bounds_fmt=pndf.PNDF_BOUNDS_F16_OUTWARD)
+    out = {"workload": WORKLOAD, "jac_eps": eps}
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        barrier(world)
+        t0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        return max_over_ranks(world, t0.elapsed_time(t1)) / args.steps
+
+    ms = timed(lambda: pndf.pndf_eval_batch_ex(h, q, out=D, jac_eps=eps))
+    diff = (D - D_exact).abs()
+    out["clamped_pndf"] = {"value": sum_over_ranks(world, float(nq)) / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                           "queries_changed_by_clamp": float((diff > 1e-5 * D_exact.abs()).float().mean())}
+    g = torch.Generator(device=dev).manual_seed(11)
+    U = torch.rand(nq, 2, device=dev, generator=g)
+    ms = timed(lambda: pndf.pndf_sample_normals(h, q, U, jac_eps=eps))
+    out["sampling"] = {"value": sum_over_ranks(world, float(nq)) / (ms / 1e3), "unit": "samples/s", "ms_per_step": ms,
+                       "note": "Gaussian footprints of the workload (sigma 1..512), FP64 position arithmetic"}
+    h.free()
+    return out
+
+
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
@@ -589,6 +629,7 @@ def run_gpu(args, world, rank, local):
     kavg16 = sum(kms16) / len(kms16)
     cluster = run_cluster_cut(args, world, st, q, D, kavg16) if args.cluster_taus else None
     kernels = run_kernels(args, world, st, q, kavg16, work["f16"]["tri_tests"]) if args.kernels else None
+    clamp = None if args.no_clamp_sampling else run_clamp_sampling(args, world, st, q, kavg16, D)
     peak, peak_kind = hbm_peak()
     achieved = work["f16"]["bytes"] / (kavg16 / 1e3) / 1e9
     traffic = committed_traffic("f16")
@@ -619,6 +660,8 @@ def run_gpu(args, world, rank, local):
         line["cluster_cut"] = cluster
     if kernels:
         line["footprint_kernels"] = kernels
+    if clamp:
+        line["jacobian_clamp_and_sampling"] = clamp
 
     if args.serve_batches > 0 or args.mixed_requests > 0:
         del st, q, D, st_h, q_h, D_h, st_d
