@@ -259,20 +259,20 @@ __device__ __forceinline__ bool node_inside(const Query &q, int l, uint32_t a, u
     return m <= q.qprune;
 }
 
-// m in the box, widened by the clamp's replacement radius (a replacement
-// lies within rho of its triangle's centroid, hence of its box).
+// m in the box; with the clamp (CLAMP) widened by the replacement radius (a
+// replacement lies within rho of its triangle's centroid, hence of its box).
+template <bool CLAMP>
 __device__ __forceinline__ bool box_holds(const float4 &b, const Query &q)
 {
-    if (q.rho != 0.f)
-        return q.mx >= b.x - q.rho && q.mx <= b.z + q.rho && q.my >= b.y - q.rho && q.my <= b.w + q.rho;
+    if (CLAMP) return q.mx >= b.x - q.rho && q.mx <= b.z + q.rho && q.my >= b.y - q.rho && q.my <= b.w + q.rho;
     return q.mx >= b.x && q.mx <= b.z && q.my >= b.y && q.my <= b.w;
 }
 
-template <int BFMT>
+template <int BFMT, bool CLAMP>
 __device__ __forceinline__ bool node_test(const MapDesc &d, const Query &q, int l, uint32_t a, uint32_t c)
 {
     if (!node_in_footprint(q, l, a, c)) return false;
-    return box_holds(node_box<BFMT>(d, l, morton2(a, c)), q);
+    return box_holds<CLAMP>(node_box<BFMT>(d, l, morton2(a, c)), q);
 }
 
 // Stack / leaf-queue entry: level in bits 28-31, "inside the ellipse" in bit
@@ -368,16 +368,22 @@ __device__ __forceinline__ void test_triangle(const Query &q, float2 na, float2 
 // orientation-signed cross and edge functions e1, e2, so l1 = e1 / cross,
 // l2 = e2 / cross).  Near-singular triangles (FP32 |cross| < 2e-10) are
 // decided, weighted and accumulated here in FP64 and return false.
-template <bool STATS>
+template <bool STATS, bool CLAMP>
 __device__ __forceinline__ bool edge_test(const Query &q, float2 na, float2 nb, float2 nc, int ai, int aj, float dir,
                                           uint32_t tri_id, Acc &acc, float &cr_o, float &e1_o, float &e2_o)
 {
     if (STATS) acc.tests++;
-    float lox = fminf(na.x, fminf(nb.x, nc.x)) - q.rho, hix = fmaxf(na.x, fmaxf(nb.x, nc.x)) + q.rho;
-    float loy = fminf(na.y, fminf(nb.y, nc.y)) - q.rho, hiy = fmaxf(na.y, fmaxf(nb.y, nc.y)) + q.rho;
+    float lox = fminf(na.x, fminf(nb.x, nc.x)), hix = fmaxf(na.x, fmaxf(nb.x, nc.x));
+    float loy = fminf(na.y, fminf(nb.y, nc.y)), hiy = fmaxf(na.y, fmaxf(nb.y, nc.y));
+    if (CLAMP) {
+        lox -= q.rho;
+        hix += q.rho;
+        loy -= q.rho;
+        hiy += q.rho;
+    }
     if (q.mx < lox || q.mx > hix || q.my < loy || q.my > hiy) return false;
     float cr = orient(na.x, na.y, nb.x, nb.y, nc.x, nc.y);
-    if (q.jac != 0.f && fabsf(cr) < q.jac) {
+    if (CLAMP && fabsf(cr) < q.jac) {
         // Eq. 6: the equilateral replacement (vertex k at 90 + 120 k degrees
         // around the centroid g, radius rho), in vertex-relative form p = m - E0
         const float gx = (na.x + nb.x + nc.x) * (1.0f / 3.0f), gy = (na.y + nb.y + nc.y) * (1.0f / 3.0f);
@@ -516,7 +522,7 @@ struct LeafState {
 // All 32 lanes: lane k tests both triangles of survivor quad k (k < cnt) of
 // the ring, (u0, u1, u2) and (u3, u2, u1), its four texels loaded together;
 // hits are compacted into the hit ring and weighed 32 at a time.
-template <int TFMT, bool STATS>
+template <int TFMT, bool STATS, bool CLAMP>
 __device__ __forceinline__ void test_quads(const MapDesc &d, const Query &q, LeafState &ls, int cnt, int lane,
                                            Acc &acc)
 {
@@ -531,9 +537,9 @@ __device__ __forceinline__ void test_quads(const MapDesc &d, const Query &q, Lea
         uint32_t id = 2u * (uint32_t(gj) * uint32_t(d.n - 1) + uint32_t(gi));
         uint32_t hp = (uint32_t(gi) << 15) | (uint32_t(gj) << 1);
         float cr, e1, e2;
-        h0 = edge_test<STATS>(q, n0, n1, n2, gi, gj, 1.f, id, acc, cr, e1, e2);
+        h0 = edge_test<STATS, CLAMP>(q, n0, n1, n2, gi, gj, 1.f, id, acc, cr, e1, e2);
         if (h0) v0 = make_float4(cr, e1, e2, __uint_as_float(hp));
-        h1 = edge_test<STATS>(q, n3, n2, n1, gi + 1, gj + 1, -1.f, id + 1u, acc, cr, e1, e2);
+        h1 = edge_test<STATS, CLAMP>(q, n3, n2, n1, gi + 1, gj + 1, -1.f, id + 1u, acc, cr, e1, e2);
         if (h1) v1 = make_float4(cr, e1, e2, __uint_as_float(hp | 1u));
     }
 #pragma unroll
@@ -657,9 +663,10 @@ __device__ __forceinline__ void test_clusters(const MapDesc &d, const ClusterDes
 
 // Four level-0 boxes (Morton-consecutive quads) in one 32-byte (FP16) or
 // 64-byte (FP32) load; returns bit u set when box u holds m.
-template <int BFMT>
+template <int BFMT, bool CLAMP>
 __device__ __forceinline__ unsigned quad_boxes_hold(const MapDesc &d, uint32_t first, float mx, float my, float rho)
 {
+    if (!CLAMP) rho = 0.f;  // (no widening: folds away)
     unsigned bits = 0;
     if (BFMT == PNDF_BOUNDS_F32) {
         const float4 *p = reinterpret_cast<const float4 *>(d.lv[0]) + first;
@@ -668,7 +675,9 @@ __device__ __forceinline__ unsigned quad_boxes_hold(const MapDesc &d, uint32_t f
         for (int u = 0; u < 4; ++u) b[u] = __ldg(p + u);
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-            bits |= unsigned(mx >= b[u].x - rho && mx <= b[u].z + rho && my >= b[u].y - rho && my <= b[u].w + rho) << u;
+            bits |= CLAMP ? unsigned(mx >= b[u].x - rho && mx <= b[u].z + rho && my >= b[u].y - rho &&
+                                     my <= b[u].w + rho) << u
+                          : unsigned(mx >= b[u].x && mx <= b[u].z && my >= b[u].y && my <= b[u].w) << u;
     } else {
         const uint4 *p = reinterpret_cast<const uint4 *>(reinterpret_cast<const uint2 *>(d.lv[0]) + first);
         uint4 v0 = __ldg(p), v1 = __ldg(p + 1);
@@ -677,7 +686,8 @@ __device__ __forceinline__ unsigned quad_boxes_hold(const MapDesc &d, uint32_t f
         for (int u = 0; u < 4; ++u) {
             float2 lo = __half22float2(*reinterpret_cast<__half2 *>(&w[2 * u]));
             float2 hi = __half22float2(*reinterpret_cast<__half2 *>(&w[2 * u + 1]));
-            bits |= unsigned(mx >= lo.x - rho && mx <= hi.x + rho && my >= lo.y - rho && my <= hi.y + rho) << u;
+            bits |= CLAMP ? unsigned(mx >= lo.x - rho && mx <= hi.x + rho && my >= lo.y - rho && my <= hi.y + rho) << u
+                          : unsigned(mx >= lo.x && mx <= hi.x && my >= lo.y && my <= hi.y) << u;
         }
     }
     return bits;
@@ -687,7 +697,7 @@ __device__ __forceinline__ unsigned quad_boxes_hold(const MapDesc &d, uint32_t f
 // (lane t: quads 4 (t & 3) .. 4 (t & 3) + 3 of block p + (t >> 2), eight
 // blocks per pass), compact the survivors into the ring with ballot/popc and
 // test them 32 quads (64 triangles) at a time.
-template <int BFMT, int TFMT, bool STATS>
+template <int BFMT, int TFMT, bool STATS, bool CLAMP>
 __device__ __forceinline__ void process_leaves(const MapDesc &d, const Query &q, const uint32_t *lq, int nleaf,
                                                LeafState &ls, int lane, Acc &acc)
 {
@@ -701,7 +711,7 @@ __device__ __forceinline__ void process_leaves(const MapDesc &d, const Query &q,
             uint32_t m = lq[blk] & kMortonMask;
             a = compact1by1(m);
             c = compact1by1(m >> 1);
-            bits = quad_boxes_hold<BFMT>(d, (m << 4) | k0, q.mx, q.my, q.rho);
+            bits = quad_boxes_hold<BFMT, CLAMP>(d, (m << 4) | k0, q.mx, q.my, q.rho);
             if (STATS) {
                 acc.quads += 4;
                 if ((lane & 3) == 0) acc.leaves++;
@@ -721,7 +731,7 @@ __device__ __forceinline__ void process_leaves(const MapDesc &d, const Query &q,
         }
         __syncwarp();
         while (ls.nsq >= 32) {
-            test_quads<TFMT, STATS>(d, q, ls, 32, lane, acc);
+            test_quads<TFMT, STATS, CLAMP>(d, q, ls, 32, lane, acc);
             ls.head += 32;
             ls.nsq -= 32;
             __syncwarp();
@@ -761,6 +771,7 @@ __device__ void eval_one(const MapDesc &d, const ClusterDesc &cd, float tau, flo
                          int lane, uint32_t *stk, uint32_t *lq, uint32_t *ring, float4 *hits, float &D_out,
                          uint32_t &flags_out, pndf_query_stats *st_out)
 {
+    constexpr bool CLAMP = KERN == kKernGaussClamp;
     Query q = make_query(rec, KERN, jac_eps);
     Acc acc = {};
     if (!q.valid) {
@@ -797,7 +808,7 @@ __device__ void eval_one(const MapDesc &d, const ClusterDesc &cd, float tau, flo
         {
             int a = a0 + (lane & 3), c = c0 + (lane >> 2);
             bool valid = lane < 16 && a <= a1 && c <= c1;
-            bool pass = valid && node_test<BFMT>(d, q, e, a, c);
+            bool pass = valid && node_test<BFMT, CLAMP>(d, q, e, a, c);
             bool inside = pass && node_inside(q, e, a, c);
             bool cut = false;
             if (STATS) acc.nodes += valid ? 1u : 0u;
@@ -826,7 +837,7 @@ __device__ void eval_one(const MapDesc &d, const ClusterDesc &cd, float tau, flo
         bool overflow = false;
         LeafState ls{ring, hits, 0u, 0u, 0, 0};
         while (true) {
-            process_leaves<BFMT, TFMT, STATS>(d, q, lq, nleaf, ls, lane, acc);
+            process_leaves<BFMT, TFMT, STATS, CLAMP>(d, q, lq, nleaf, ls, lane, acc);
             nleaf = 0;
             if (CLUSTER) {
                 // cut nodes sit at the back of the leaf queue (entry k at lq[63 - k];
@@ -871,7 +882,7 @@ __device__ void eval_one(const MapDesc &d, const ClusterDesc &cd, float tau, flo
                 }
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
-                pass[r] = pass[r] && box_holds(bx[r], q);
+                pass[r] = pass[r] && box_holds<CLAMP>(bx[r], q);
                 if (CLUSTER && pass[r]) {  // the cut of Sec. 4.3: e <= r_x r_y tau
                     cut[r] = ev[r] <= q.theta;
                     if (STATS) acc.cchecks++;
@@ -903,7 +914,7 @@ __device__ void eval_one(const MapDesc &d, const ClusterDesc &cd, float tau, flo
             }
             __syncwarp();
         }
-        if (ls.nsq > 0) test_quads<TFMT, STATS>(d, q, ls, ls.nsq, lane, acc);  // nsq < 32 here
+        if (ls.nsq > 0) test_quads<TFMT, STATS, CLAMP>(d, q, ls, ls.nsq, lane, acc);  // nsq < 32 here
         if (ls.nh > 0) drain_hits<STATS>(q, d.n, d.L, ls.hits, ls.hh, ls.nh, lane, acc);  // nh < 32 here
         if (overflow) acc.flags |= PNDF_QF_OVERFLOW;
     }
