@@ -14,6 +14,9 @@ cluster_fits(st)           -> ClusterFits: corner normals and residual of every 
 cluster_fit(st, l, I, J)   -> (c (4, 2), e) for one node, or None outside the map
 pndf_cluster(st, queries, tau, fits=None) -> as pndf, with the cluster cut e <= r_x r_y tau
 projarea(st, queries, w)   -> P (float64)
+ggx_fits(st)               -> Omega per mip node (Eq. 12 fit; box filter per node)
+ggx_lambda(Omega, N, q, w) -> GGX Smith Lambda'(w) at each footprint
+shadow_masking(Omega, N, q, wi, wo) -> height-correlated G (Sec. 4.4)
 tri_integral(n0, n1, n2, w) -> integral of max(m~.w, 0)/m~_z over one normal triangle
 
 ``st`` is an (N, N, 2) array (texel (i, j) at ``st[j, i]``); ``queries`` an
@@ -32,6 +35,7 @@ and FP64 may then take the cut differently.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -122,6 +126,17 @@ class ClusterFits:
         return self.c[o:o + S * S].reshape(S, S, 4, 2), self.e[o:o + S * S].reshape(S, S)
 
 
+GGX_DIRECTIONS = 16
+GGX_WZ = 0.3
+
+
+def ggx_dirs(K: int = GGX_DIRECTIONS, wz: float = GGX_WZ) -> np.ndarray:
+    """The fit directions: K azimuths 2 pi k / K at height w_z (grazing-ish)."""
+    phi = 2.0 * np.pi * np.arange(K) / K
+    r = math.sqrt(1.0 - wz * wz)
+    return np.stack([r * np.cos(phi), r * np.sin(phi), np.full(K, wz)], 1)
+
+
 def _chunks(n, threads, min_chunk=16):
     nchunks = max(1, min(threads * 8, (n + min_chunk - 1) // min_chunk))
     edges = np.linspace(0, n, nchunks + 1).astype(np.int64)
@@ -140,6 +155,7 @@ class Oracle:
     F_NEAR_TAU = F_NEAR_TAU
     F_OUTSIDE = F_OUTSIDE
     F_EXCLUDE = F_EXCLUDE
+    ggx_dirs = staticmethod(ggx_dirs)
 
     def __init__(self, so_path: str):
         lib = ctypes.CDLL(so_path)
@@ -157,6 +173,18 @@ class Oracle:
         lib.oracle_projarea.restype = None
         lib.oracle_tri_integral.argtypes = [ctypes.c_double] * 9
         lib.oracle_tri_integral.restype = ctypes.c_double
+        lib.oracle_ggx_node_P.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, ctypes.c_int,
+                                          dp, dp, ctypes.c_int, dp]
+        lib.oracle_ggx_node_P.restype = ctypes.c_int
+        lib.oracle_ggx_fit.argtypes = [dp, dp, ctypes.c_int, dp]
+        lib.oracle_ggx_fit.restype = ctypes.c_int
+        lib.oracle_ggx_build.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, ctypes.c_int,
+                                         dp, dp, ctypes.c_int, dp]
+        lib.oracle_ggx_build.restype = None
+        lib.oracle_ggx_lambda.argtypes = [dp, ctypes.c_int, dp, dp, ctypes.c_int64, ctypes.c_int64, dp]
+        lib.oracle_ggx_lambda.restype = None
+        lib.oracle_shadow_masking.argtypes = [dp, ctypes.c_int, dp, dp, dp, ctypes.c_int64, ctypes.c_int64, dp]
+        lib.oracle_shadow_masking.restype = None
         lib.oracle_cluster_fit.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp]
         lib.oracle_cluster_fit.restype = ctypes.c_int
         lib.oracle_cluster_build.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp]
@@ -270,6 +298,72 @@ class Oracle:
                 list(ex.map(run, _chunks(n, threads)))
         return D, flags, hits, hh
 
+    # -- GGX projected-area fit per mip node (Eq. 12) and shadow-masking --
+
+    def ggx_node_P(self, st, l: int, I: int, J: int, dirs=None):
+        stm = _as_map(st)
+        dirs = np.ascontiguousarray(ggx_dirs() if dirs is None else dirs, dtype=np.float64)
+        glx, glw = (np.ascontiguousarray(a) for a in np.polynomial.legendre.leggauss(GL_POINTS))
+        P = np.zeros(dirs.shape[0], np.float64)
+        ok = self.lib.oracle_ggx_node_P(_ptr(stm, ctypes.c_double), stm.shape[0], l, I, J, _ptr(dirs, ctypes.c_double),
+                                        dirs.shape[0], _ptr(glx, ctypes.c_double), _ptr(glw, ctypes.c_double),
+                                        GL_POINTS, _ptr(P, ctypes.c_double))
+        return P if ok else None
+
+    def ggx_fit(self, P, dirs=None):
+        dirs = np.ascontiguousarray(ggx_dirs() if dirs is None else dirs, dtype=np.float64)
+        P = np.ascontiguousarray(P, dtype=np.float64)
+        O = np.zeros(3, np.float64)
+        ok = self.lib.oracle_ggx_fit(_ptr(P, ctypes.c_double), _ptr(dirs, ctypes.c_double), dirs.shape[0],
+                                     _ptr(O, ctypes.c_double))
+        return O if ok else None
+
+    def ggx_fits(self, st, dirs=None, threads: int | None = None):
+        """Omega (n_nodes, 3) = (O_xx, O_xy, O_yy) of every node of levels 2..L
+        (the ClusterFits layout; NaN without a fit)."""
+        stm = _as_map(st)
+        N = stm.shape[0]
+        dirs = np.ascontiguousarray(ggx_dirs() if dirs is None else dirs, dtype=np.float64)
+        glx, glw = (np.ascontiguousarray(a) for a in np.polynomial.legendre.leggauss(GL_POINTS))
+        lay = ClusterFits(N)
+        O = np.full((lay.c.shape[0], 3), np.nan, np.float64)
+        jobs = []
+        for l in range(2, lay.L + 1):
+            S = 1 << (lay.L - l)
+            jobs += [(l, a, b) for a, b in _chunks(S, threads or default_threads(), 1)]
+        jobs.sort(key=lambda j: -j[0])
+
+        def run(j):
+            self.lib.oracle_ggx_build(_ptr(stm, ctypes.c_double), N, j[0], j[1], j[2], _ptr(dirs, ctypes.c_double),
+                                      dirs.shape[0], _ptr(glx, ctypes.c_double), _ptr(glw, ctypes.c_double),
+                                      GL_POINTS, _ptr(O, ctypes.c_double))
+
+        with ThreadPoolExecutor(max_workers=threads or default_threads()) as ex:
+            list(ex.map(run, jobs))
+        return O
+
+    def ggx_lambda(self, Omega, N: int, queries, omega):
+        q = _as_queries(queries)
+        w = np.ascontiguousarray(np.asarray(omega.cpu() if hasattr(omega, "cpu") else omega)[:, :3], dtype=np.float64)
+        O = np.ascontiguousarray(Omega, dtype=np.float64)
+        out = np.zeros(q.shape[0], np.float64)
+        if q.shape[0]:
+            self.lib.oracle_ggx_lambda(_ptr(O, ctypes.c_double), N, _ptr(q, ctypes.c_double), _ptr(w, ctypes.c_double),
+                                       0, q.shape[0], _ptr(out, ctypes.c_double))
+        return out
+
+    def shadow_masking(self, Omega, N: int, queries, wi, wo):
+        q = _as_queries(queries)
+        a = np.ascontiguousarray(np.asarray(wi.cpu() if hasattr(wi, "cpu") else wi)[:, :3], dtype=np.float64)
+        b = np.ascontiguousarray(np.asarray(wo.cpu() if hasattr(wo, "cpu") else wo)[:, :3], dtype=np.float64)
+        O = np.ascontiguousarray(Omega, dtype=np.float64)
+        out = np.zeros(q.shape[0], np.float64)
+        if q.shape[0]:
+            self.lib.oracle_shadow_masking(_ptr(O, ctypes.c_double), N, _ptr(q, ctypes.c_double),
+                                           _ptr(a, ctypes.c_double), _ptr(b, ctypes.c_double), 0, q.shape[0],
+                                           _ptr(out, ctypes.c_double))
+        return out
+
     def projarea(self, st, queries, omega, threads: int | None = None):
         lib = self.lib
         stm = _as_map(st)
@@ -335,3 +429,23 @@ def cluster_fits(st, threads: int | None = None) -> ClusterFits:
 def pndf_cluster(st, queries, tau: float, fits: ClusterFits | None = None, threads: int | None = None,
                  kernel: int = 0):
     return _get().pndf_cluster(st, queries, tau, fits, threads, kernel)
+
+
+def ggx_node_P(st, l, I, J, dirs=None):
+    return _get().ggx_node_P(st, l, I, J, dirs)
+
+
+def ggx_fit(P, dirs=None):
+    return _get().ggx_fit(P, dirs)
+
+
+def ggx_fits(st, dirs=None, threads: int | None = None):
+    return _get().ggx_fits(st, dirs, threads)
+
+
+def ggx_lambda(Omega, N, queries, omega):
+    return _get().ggx_lambda(Omega, N, queries, omega)
+
+
+def shadow_masking(Omega, N, queries, wi, wo):
+    return _get().shadow_masking(Omega, N, queries, wi, wo)

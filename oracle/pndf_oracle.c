@@ -998,3 +998,208 @@ void oracle_sample(const double *st, int N, const double *q, const double *U, in
         tri_out[k] = 2 * ((int64_t)j * (N - 1) + i) + tri;
     }
 }
+
+/* ------------------------------------------------------------------------- */
+/* GGX projected-area fit per mip node (Eq. 12) and shadow-masking (Sec. 4.4) */
+/* ------------------------------------------------------------------------- */
+/*
+ * Readings.  Eq. 12 with its parentheses restored (the printed form drops
+ * them): P'(w) = (w_z + sqrt(w_z^2 + w_xy^T Omega w_xy)) / 2, the GGX
+ * projected area (Lambda' = P'/w_z - 1 is the GGX Smith Lambda).  A mip node
+ * (level l, 2^l x 2^l quads) is filtered by the box over its own quads (k =
+ * 4^-l per unit uv area), for which Eq. 9-11 are exact.  Its P is taken at K
+ * given unit directions; each gives a_k = (2 P_k - w_z)^2 - w_z^2 =
+ * w_xy^T Omega w_xy, linear in (O_xx, O_xy, O_yy), solved by least squares
+ * (the normal equations).  Only nodes whose quads all lie in the map are
+ * fitted.  Inference blends the fits of the two mip levels around
+ * lambda = log2(sqrt(12) max(sqrt(S_xx), sqrt(S_yy))) (a box of width b has
+ * the variance b^2 / 12), each bilinear between node centres (nodes without a
+ * fit drop out and the weights renormalise), lambda clamped to [2, L].
+ * Shadow-masking, height-correlated form: G = H(m~.wi) H(m~.wo) /
+ * (1 + Lambda(wi) + Lambda(wo)).
+ */
+
+/* One triangle's V_T / |cross| (Eq. 10-11, Alg. 1; uv form when collapsed). */
+static double tri_ratio(const double *a, const double *b, const double *cc, const double *w,
+                        const double *gl_x, const double *gl_w, int ngl)
+{
+    double wx = w[0], wy = w[1], wz = w[2];
+    double phi = atan2(wy, wx), c = cos(phi), s = sin(phi), wr = sqrt(wx * wx + wy * wy);
+    double A2 = area2(a[0], a[1], b[0], b[1], cc[0], cc[1]);
+    if (fabs(A2) < 1e-12) return collapsed_uv_form(a, b, cc, w, c, s, gl_x, gl_w, ngl);
+    double v[3][2] = {{c * a[0] + s * a[1], -s * a[0] + c * a[1]},
+                      {c * b[0] + s * b[1], -s * b[0] + c * b[1]},
+                      {c * cc[0] + s * cc[1], -s * cc[0] + c * cc[1]}};
+    if (A2 < 0.0) {
+        double t0 = v[1][0], t1 = v[1][1];
+        v[1][0] = v[2][0]; v[1][1] = v[2][1];
+        v[2][0] = t0; v[2][1] = t1;
+    }
+    return tri_visible_integral(v, wr, wz) / fabs(A2);
+}
+
+/* Box-filtered projected area of node (l, I, J) at K directions (3 per):
+ * P[k] = 4^-l sum over its triangles of V_T / |cross|.  0 if the node has a
+ * quad outside the map. */
+int oracle_ggx_node_P(const double *st, int N, int l, int I, int J, const double *dirs, int K,
+                      const double *gl_x, const double *gl_w, int ngl, double *P)
+{
+    int a = 1 << l;
+    if (a * (I + 1) > N - 1 || a * (J + 1) > N - 1) return 0;
+    for (int k = 0; k < K; ++k) P[k] = 0.0;
+    for (int j = a * J; j < a * J + a; ++j)
+        for (int i = a * I; i < a * I + a; ++i)
+            for (int tri = 0; tri < 2; ++tri) {
+                double uv[3][2], nv[3][2];
+                quad_tri(st, N, i, j, tri, uv, nv);
+                for (int k = 0; k < K; ++k) P[k] += tri_ratio(nv[0], nv[1], nv[2], dirs + 3 * k, gl_x, gl_w, ngl);
+            }
+    for (int k = 0; k < K; ++k) P[k] /= (double)a * (double)a;
+    return 1;
+}
+
+/* Least-squares Omega (O_xx, O_xy, O_yy) from P at K directions.  0 if the
+ * normal equations are singular. */
+int oracle_ggx_fit(const double *P, const double *dirs, int K, double *Omega)
+{
+    double A[3][3] = {{0}}, r[3] = {0};
+    for (int k = 0; k < K; ++k) {
+        double wx = dirs[3 * k], wy = dirs[3 * k + 1], wz = dirs[3 * k + 2];
+        double t = 2.0 * P[k] - wz;
+        double ak = t * t - wz * wz;
+        double row[3] = {wx * wx, 2.0 * wx * wy, wy * wy};
+        for (int p = 0; p < 3; ++p) {
+            r[p] += row[p] * ak;
+            for (int q = 0; q < 3; ++q) A[p][q] += row[p] * row[q];
+        }
+    }
+    /* Gaussian elimination with partial pivoting */
+    for (int c = 0; c < 3; ++c) {
+        int piv = c;
+        for (int p = c + 1; p < 3; ++p)
+            if (fabs(A[p][c]) > fabs(A[piv][c])) piv = p;
+        if (A[piv][c] == 0.0) return 0;
+        if (piv != c) {
+            for (int q = 0; q < 3; ++q) { double t = A[c][q]; A[c][q] = A[piv][q]; A[piv][q] = t; }
+            double t = r[c]; r[c] = r[piv]; r[piv] = t;
+        }
+        for (int p = c + 1; p < 3; ++p) {
+            double f = A[p][c] / A[c][c];
+            for (int q = c; q < 3; ++q) A[p][q] -= f * A[c][q];
+            r[p] -= f * r[c];
+        }
+    }
+    for (int c = 2; c >= 0; --c) {
+        double v = r[c];
+        for (int q = c + 1; q < 3; ++q) v -= A[c][q] * Omega[q];
+        Omega[c] = v / A[c][c];
+    }
+    return 1;
+}
+
+/* Fits of level-l nodes in rows [J0, J1) into Omega_all (3 per node, the
+ * cluster layout of levels 2..L; NaN where the node has no fit). */
+void oracle_ggx_build(const double *st, int N, int l, int J0, int J1, const double *dirs, int K,
+                      const double *gl_x, const double *gl_w, int ngl, double *Omega_all)
+{
+    int L = top_level_of(N);
+    size_t S = (size_t)1 << (L - l), off = cluster_offset(L, l);
+    double P[64];
+    for (int J = J0; J < J1; ++J)
+        for (size_t I = 0; I < S; ++I) {
+            double *O = Omega_all + 3 * (off + (size_t)J * S + I);
+            if (K > 64 || !oracle_ggx_node_P(st, N, l, (int)I, J, dirs, K, gl_x, gl_w, ngl, P) ||
+                !oracle_ggx_fit(P, dirs, K, O))
+                O[0] = O[1] = O[2] = NAN;
+        }
+}
+
+/* Omega at a footprint (x, y, S) by the blend described above; 0 if no node
+ * contributes. */
+static int ggx_omega_at(const double *Omega_all, int N, double x, double y, double sxx, double syy, double O[3])
+{
+    int L = top_level_of(N);
+    double lam = log2(sqrt(12.0) * fmax(sqrt(sxx), sqrt(syy)));
+    if (lam < 2.0) lam = 2.0;
+    if (lam > L) lam = L;
+    int l0 = (int)floor(lam), l1 = l0 < L ? l0 + 1 : l0;
+    double tl = lam - l0;
+    double acc[3] = {0, 0, 0}, wsum = 0.0;
+    for (int side = 0; side < 2; ++side) {
+        int l = side ? l1 : l0;
+        double wl = side ? tl : 1.0 - tl;
+        if (wl == 0.0) continue;
+        double a = (double)(1 << l);
+        int S = 1 << (L - l);
+        double fx = x / a - 0.5, fy = y / a - 0.5;
+        int i0 = (int)floor(fx), j0 = (int)floor(fy);
+        double tx = fx - i0, ty = fy - j0;
+        double lacc[3] = {0, 0, 0}, lw = 0.0;
+        for (int dj = 0; dj < 2; ++dj)
+            for (int di = 0; di < 2; ++di) {
+                int I = i0 + di, Jn = j0 + dj;
+                if (I < 0) I = 0;
+                if (I > S - 1) I = S - 1;
+                if (Jn < 0) Jn = 0;
+                if (Jn > S - 1) Jn = S - 1;
+                const double *Ok = Omega_all + 3 * (cluster_offset(L, l) + (size_t)Jn * S + I);
+                if (!isfinite(Ok[0])) continue;
+                double w = (di ? tx : 1.0 - tx) * (dj ? ty : 1.0 - ty);
+                for (int c = 0; c < 3; ++c) lacc[c] += w * Ok[c];
+                lw += w;
+            }
+        if (lw > 0.0) {
+            for (int c = 0; c < 3; ++c) acc[c] += wl * lacc[c] / lw;
+            wsum += wl;
+        }
+    }
+    if (!(wsum > 0.0)) return 0;
+    for (int c = 0; c < 3; ++c) O[c] = acc[c] / wsum;
+    return 1;
+}
+
+static double ggx_P(const double O[3], const double *w)
+{
+    double q = O[0] * w[0] * w[0] + 2.0 * O[1] * w[0] * w[1] + O[2] * w[1] * w[1];
+    return 0.5 * (w[2] + sqrt(fmax(w[2] * w[2] + q, 0.0)));
+}
+
+/* Lambda'(w) = P'(w) / w_z - 1 per query (7 doubles) and direction (3);
+ * NaN where no fit covers the footprint. */
+void oracle_ggx_lambda(const double *Omega_all, int N, const double *q, const double *w, int64_t k0, int64_t k1,
+                       double *lam)
+{
+    for (int64_t k = k0; k < k1; ++k) {
+        double O[3];
+        const double *qq = q + 7 * k;
+        if (!ggx_omega_at(Omega_all, N, qq[0], qq[1], qq[2], qq[4], O)) {
+            lam[k] = NAN;
+            continue;
+        }
+        lam[k] = ggx_P(O, w + 3 * k) / w[3 * k + 2] - 1.0;
+    }
+}
+
+/* Height-correlated shadow-masking G(wi, wo, m) with the GGX Lambda', m =
+ * the query normal (ms, mt) lifted to the hemisphere. */
+void oracle_shadow_masking(const double *Omega_all, int N, const double *q, const double *wi, const double *wo,
+                           int64_t k0, int64_t k1, double *G)
+{
+    for (int64_t k = k0; k < k1; ++k) {
+        double O[3];
+        const double *qq = q + 7 * k;
+        if (!ggx_omega_at(Omega_all, N, qq[0], qq[1], qq[2], qq[4], O)) {
+            G[k] = NAN;
+            continue;
+        }
+        const double *a = wi + 3 * k, *b = wo + 3 * k;
+        double mz = sqrt(fmax(0.0, 1.0 - qq[5] * qq[5] - qq[6] * qq[6]));
+        double ci = qq[5] * a[0] + qq[6] * a[1] + mz * a[2], co = qq[5] * b[0] + qq[6] * b[1] + mz * b[2];
+        if (!(ci > 0.0 && co > 0.0)) {
+            G[k] = 0.0;
+            continue;
+        }
+        double li = ggx_P(O, a) / a[2] - 1.0, lo = ggx_P(O, b) / b[2] - 1.0;
+        G[k] = 1.0 / (1.0 + li + lo);
+    }
+}

@@ -15,7 +15,9 @@ the disk and box kernels: a 3-sigma disk, the box sheared by the upper
 Cholesky factor, and the box normalised as a unit square.  For the Eq. 6
 clamp and sampling: a replacement of area eps, a Jacobian of eps / 2, an
 untruncated sampling radius, a transposed Cholesky factor and the other
-diagonal for the sample's triangle.
+diagonal for the sample's triangle.  For the GGX fit (Eq. 12): the printed
+form without its parentheses, a wrong fit observation, a halved cross term
+and a box filter normalised by the side instead of the area.
 """
 
 import os
@@ -74,6 +76,17 @@ def samples_on_triangles(m):
 SAMPLING_PINS = [spins.test_clamp_keeps_the_mass_of_flat_triangles, spins.test_sample_frequencies_follow_the_kernel,
                  samples_on_triangles, spins.test_binned_samples_match_clamped_pndf]
 
+import test_oracle_ggx as gpins  # noqa: E402
+
+
+def ggx_node_P_0p3(m):
+    gpins.test_node_P_matches_uv_quadrature(m, 0.3)
+
+
+GGX_PINS = [gpins.test_fit_recovers_a_ggx_omega, gpins.test_flat_map_has_zero_omega, ggx_node_P_0p3,
+            gpins.test_lambda_is_ggx_smith_for_isotropic_omega, gpins.test_interpolation_properties,
+            gpins.test_shadow_masking_flat_and_backfacing]
+
 CLUSTER_PINS = [cpins.test_fit_recovers_piecewise_linear_data, cluster_dense_fit_level3, cluster_mass_all_cut,
                 cluster_mass_mixed, cpins.test_cluster_binning_with_anisotropic_cut,
                 cpins.test_cluster_transpose_symmetry, cpins.test_piecewise_linear_map_is_unchanged_by_any_cut]
@@ -125,6 +138,14 @@ MUTANTS = {
     "sampler_cholesky_transposed": ([("double ux = x + l11 * v1, uy = y + l21 * v1 + l22 * v2;",
                                       "double ux = x + l11 * v1 + l21 * v2, uy = y + l22 * v2;")], SAMPLING_PINS),
     "sampler_other_diagonal": ([("int tri = fu + fv < 1.0 ? 0 : 1;", "int tri = fu < fv ? 0 : 1;")], SAMPLING_PINS),
+    # GGX projected-area fit per mip node (Eq. 12) and shadow-masking
+    "ggx_printed_parentheses": ([("return 0.5 * (w[2] + sqrt(fmax(w[2] * w[2] + q, 0.0)));",
+                                  "return 0.5 * w[2] + sqrt(fmax(w[2] * w[2] + q, 0.0));")], GGX_PINS),
+    "ggx_fit_observation": ([("double ak = t * t - wz * wz;", "double ak = 4.0 * P[k] * P[k] - wz * wz;")], GGX_PINS),
+    "ggx_fit_cross_term": ([("double row[3] = {wx * wx, 2.0 * wx * wy, wy * wy};",
+                             "double row[3] = {wx * wx, wx * wy, wy * wy};")], GGX_PINS),
+    "ggx_box_area": ([("for (int k = 0; k < K; ++k) P[k] /= (double)a * (double)a;",
+                       "for (int k = 0; k < K; ++k) P[k] /= (double)a;")], GGX_PINS),
     # cluster hierarchy (Eq. 7-8, App. A) and the tau cut
     "cluster_fit_main_diagonal": ([("        phi[0] = 1.0 - s - t; phi[1] = s; phi[2] = t; phi[3] = 0.0;",
                                     "        phi[0] = 1.0 - s; phi[1] = s - t; phi[2] = 0.0; phi[3] = t;"),
