@@ -208,6 +208,42 @@ pndf_status pndf_sample_normals(const pndf_hierarchy *h, const pndf_query *q_dev
                                 int32_t kernel, float jac_eps, float *m_out_dev, uint32_t *tri_out_dev,
                                 uint32_t *flags_out_dev, void *stream);
 
+/*
+ * GGX projected-area fit per mip node (Eq. 12) and the shadow-masking term
+ * (Sec. 4.4).  P'(w) = (w_z + sqrt(w_z^2 + w_xy^T Omega w_xy)) / 2 (Eq. 12
+ * with its parentheses restored: the GGX projected area), so Lambda'(w) =
+ * P'(w) / w_z - 1 is the GGX Smith Lambda of Omega.  Each node of levels 2..L
+ * whose quads all lie in the map is box-filtered over its own quads (for
+ * which Eq. 9-11 are exact); its projected area at 16 directions (azimuths
+ * 2 pi k / 16 at w_z = 0.3) gives (2 P - w_z)^2 - w_z^2 = w_xy^T Omega w_xy,
+ * fitted by least squares.  A footprint (x, S) takes the two mip levels
+ * around log2(sqrt(12) max(sqrt(S_xx), sqrt(S_yy))) (clamped to [2, L]),
+ * each bilinear between node centres (nodes without a fit drop out).
+ */
+typedef struct pndf_ggx pndf_ggx;
+
+/* Fit every node of h (reads its texels during the call's work on stream).
+ * 16 bytes per node of levels >= 2; temporary scratch 128 bytes per leaf
+ * block.  Errors: INVALID_ARG, OOM, CUDA. */
+pndf_status pndf_ggx_create(const pndf_hierarchy *h, void *stream, pndf_ggx **out);
+void pndf_ggx_free(pndf_ggx *g);
+
+/* Lambda'(omega) per record of q_dev (x and S used) and unit direction
+ * omega_dev (3 floats, w_z > 0); NaN where no fit covers the footprint.
+ * Asynchronous on stream.  Errors: INVALID_ARG, CUDA. */
+pndf_status pndf_ggx_lambda(const pndf_ggx *g, const pndf_query *q_dev, const float *omega_dev, int64_t n,
+                            float *lambda_out_dev, void *stream);
+
+/* Height-correlated shadow-masking G = H(m~.wi) H(m~.wo) / (1 + Lambda'(wi)
+ * + Lambda'(wo)) per record (m = (ms, mt) lifted to the hemisphere), wi/wo
+ * 3 floats each (z > 0).  Asynchronous.  Errors: INVALID_ARG, CUDA. */
+pndf_status pndf_shadow_masking(const pndf_ggx *g, const pndf_query *q_dev, const float *wi_dev,
+                                const float *wo_dev, int64_t n, float *G_out_dev, void *stream);
+
+/* Level l (2..L) of the fit, row-major (J, I), 3 floats per node
+ * (O_xx, O_xy, O_yy; NaN without a fit).  Errors: INVALID_ARG, CUDA. */
+pndf_status pndf_ggx_level(const pndf_ggx *g, int32_t level, float *omega_out_dev, void *stream);
+
 /* Copy out level l (2 <= l <= L, 2^L >= N-1) of the cluster hierarchy
  * (Sec. 4.3, Eq. 7-8) for inspection, nodes in row-major order (J, I),
  * S = 2^(L-l) per side:

@@ -7,6 +7,7 @@
 #include <new>
 
 #include "common.cuh"
+#include "ggx.cuh"
 
 using namespace pndf;
 
@@ -169,6 +170,85 @@ pndf_status pndf_sample_normals(const pndf_hierarchy *h, const pndf_query *q_dev
                          as_stream(stream)) == cudaSuccess
                ? PNDF_OK
                : PNDF_ERR_CUDA;
+}
+
+pndf_status pndf_ggx_create(const pndf_hierarchy *h, void *stream, pndf_ggx **out)
+{
+    if (!out) return PNDF_ERR_INVALID_ARG;
+    *out = nullptr;
+    pndf_status st = check_hierarchy(h);
+    if (st != PNDF_OK) return st;
+    pndf_ggx *g = new (std::nothrow) pndf_ggx();
+    if (!g) return PNDF_ERR_OOM;
+    memset(g, 0, sizeof(*g));
+    g->device = h->device;
+    g->n = h->d.n;
+    g->L = h->d.L;
+    size_t off[kMaxLevels] = {0}, total = 0;
+    for (int l = kLeafLevel; l <= g->L; ++l) {
+        off[l] = total;
+        total += (level_nodes(g->L, l) * sizeof(float4) + 255) & ~size_t(255);
+    }
+    if (cudaMalloc(&g->mem, total) != cudaSuccess) {
+        cudaGetLastError();
+        delete g;
+        return PNDF_ERR_OOM;
+    }
+    g->bytes = total;
+    for (int l = kLeafLevel; l <= g->L; ++l) g->omega[l] = reinterpret_cast<float4 *>(static_cast<char *>(g->mem) + off[l]);
+    st = launch_ggx_build(h, g, as_stream(stream));
+    if (st != PNDF_OK) {
+        cudaFree(g->mem);
+        delete g;
+        return st;
+    }
+    *out = g;
+    return PNDF_OK;
+}
+
+void pndf_ggx_free(pndf_ggx *g)
+{
+    if (!g) return;
+    if (g->mem) cudaFree(g->mem);
+    delete g;
+}
+
+static pndf_status ggx_args(const pndf_ggx *g, const pndf_query *q, const float *a, const float *b, int64_t n,
+                            const float *out, bool need_b)
+{
+    if (!g || !g->mem || n < 0) return PNDF_ERR_INVALID_ARG;
+    if (n > 0 && (!q || !a || !out || (need_b && !b))) return PNDF_ERR_INVALID_ARG;
+    if ((q && !aligned(q, 16)) || (a && !aligned(a, 4)) || (b && !aligned(b, 4)) || (out && !aligned(out, 4)))
+        return PNDF_ERR_INVALID_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != g->device) return PNDF_ERR_INVALID_ARG;
+    return PNDF_OK;
+}
+
+pndf_status pndf_ggx_lambda(const pndf_ggx *g, const pndf_query *q_dev, const float *omega_dev, int64_t n,
+                            float *lambda_out_dev, void *stream)
+{
+    pndf_status st = ggx_args(g, q_dev, omega_dev, nullptr, n, lambda_out_dev, false);
+    if (st != PNDF_OK) return st;
+    return launch_ggx_eval(g, q_dev, omega_dev, nullptr, n, lambda_out_dev, as_stream(stream)) == cudaSuccess
+               ? PNDF_OK
+               : PNDF_ERR_CUDA;
+}
+
+pndf_status pndf_shadow_masking(const pndf_ggx *g, const pndf_query *q_dev, const float *wi_dev,
+                                const float *wo_dev, int64_t n, float *G_out_dev, void *stream)
+{
+    pndf_status st = ggx_args(g, q_dev, wi_dev, wo_dev, n, G_out_dev, true);
+    if (st != PNDF_OK) return st;
+    return launch_ggx_eval(g, q_dev, wi_dev, wo_dev, n, G_out_dev, as_stream(stream)) == cudaSuccess ? PNDF_OK
+                                                                                                     : PNDF_ERR_CUDA;
+}
+
+pndf_status pndf_ggx_level(const pndf_ggx *g, int32_t level, float *omega_out_dev, void *stream)
+{
+    if (!g || !g->mem || level < kLeafLevel || level > g->L || !omega_out_dev || !aligned(omega_out_dev, 4))
+        return PNDF_ERR_INVALID_ARG;
+    return launch_ggx_copy(g, level, omega_out_dev, as_stream(stream)) == cudaSuccess ? PNDF_OK : PNDF_ERR_CUDA;
 }
 
 pndf_status pndf_cluster_level(const pndf_hierarchy *h, int32_t level, float *records_dev, float *residual_dev,

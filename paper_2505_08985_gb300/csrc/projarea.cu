@@ -28,7 +28,7 @@
 // lane), compensated sums are reduced across the warp and stored per band;
 // a second kernel adds a request's bands in fixed order, so results do not
 // depend on scheduling or on which other requests share the launch.
-#include "common.cuh"
+#include "ggx.cuh"
 
 namespace pndf {
 
@@ -629,7 +629,284 @@ GLTable make_gl()
     return t;
 }
 
+// ---- GGX projected-area fit per mip node (Eq. 12) ----
+//
+// P'(w) = (w_z + sqrt(w_z^2 + w^T Omega w)) / 2 (Eq. 12, parentheses
+// restored).  A node is box-filtered over its own quads, so its projected
+// area is P(w) = 4^-l sum over its triangles of V_T / |cross| (Eq. 9-11,
+// exact for the box); the fit takes P at the 16 fit directions, forms a_k =
+// (2 P_k - w_z)^2 - w_z^2 = w^T Omega w and solves the 3 x 3 normal
+// equations in FP64.  Leaf blocks are summed by one warp each (lane =
+// triangle, FP32 per-triangle values with the FP64 path where needed); a
+// parent's P is the mean of its children's.
+
+struct GgxDirs {
+    Dir w[kGgxDirs];
+};
+
+__device__ bool ggx_fit(const float *P, const GgxDirs &dirs, float4 &out)
+{
+    double A[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, r[3] = {0, 0, 0};
+    for (int k = 0; k < kGgxDirs; ++k) {
+        const double wx = dirs.w[k].wx, wy = dirs.w[k].wy, wz = dirs.w[k].wz;
+        const double t = 2.0 * double(P[k]) - wz;
+        const double a = t * t - wz * wz;
+        const double row[3] = {wx * wx, 2.0 * wx * wy, wy * wy};
+        for (int p = 0; p < 3; ++p) {
+            r[p] += row[p] * a;
+            for (int q = 0; q < 3; ++q) A[p][q] += row[p] * row[q];
+        }
+    }
+    // Cholesky of the symmetric positive definite 3 x 3 system
+    double L[3][3];
+    for (int j = 0; j < 3; ++j) {
+        double dd = A[j][j];
+        for (int k = 0; k < j; ++k) dd -= L[j][k] * L[j][k];
+        if (!(dd > 0.0)) return false;
+        dd = sqrt(dd);
+        L[j][j] = dd;
+        for (int i = j + 1; i < 3; ++i) {
+            double v = A[i][j];
+            for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
+            L[i][j] = v / dd;
+        }
+    }
+    double y[3], x[3];
+    for (int i = 0; i < 3; ++i) {
+        double v = r[i];
+        for (int k = 0; k < i; ++k) v -= L[i][k] * y[k];
+        y[i] = v / L[i][i];
+    }
+    for (int i = 2; i >= 0; --i) {
+        double v = y[i];
+        for (int k = i + 1; k < 3; ++k) v -= L[k][i] * x[k];
+        x[i] = v / L[i][i];
+    }
+    out = make_float4(float(x[0]), float(x[1]), float(x[2]), 0.f);
+    return true;
+}
+
+__device__ __forceinline__ bool ggx_node_inside(const MapDesc &d, int l, uint32_t m)
+{
+    const int64_t a = int64_t(1) << l;
+    return a * (compact1by1(m) + 1) <= int64_t(d.n) - 1 && a * (compact1by1(m >> 1) + 1) <= int64_t(d.n) - 1;
+}
+
+// One warp per leaf block (Morton index): P at the fit directions (NaN when
+// the block has a quad outside the map) and the block's fit.
+template <int TFMT>
+__global__ void __launch_bounds__(256) ggx_leaf(MapDesc d, GgxDirs dirs, GLTable gl, float *__restrict__ P,
+                                                float4 *__restrict__ omega, uint32_t nleaf)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t m = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (m >= nleaf) return;
+    float *Pm = P + size_t(m) * kGgxDirs;
+    if (!ggx_node_inside(d, kLeafLevel, m)) {
+        if (lane < kGgxDirs) Pm[lane] = __int_as_float(0x7fc00000);
+        if (lane == 0) omega[m] = make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, 0.f);
+        return;
+    }
+    const int q = lane >> 1, tri = lane & 1;
+    const int i = int(compact1by1(m)) * kLeafQuads + (q & 3), j = int(compact1by1(m >> 1)) * kLeafQuads + (q >> 2);
+    const float2 na = texel<TFMT>(d, i + tri, j + tri);
+    const float2 nb = texel<TFMT>(d, i + 1 - tri, j + tri);
+    const float2 nc = texel<TFMT>(d, i + tri, j + 1 - tri);
+    const float za = zof(na), zb = zof(nb), zc = zof(nc);
+    for (int k = 0; k < kGgxDirs; ++k) {
+        float r;
+        if (!tri_ratio_fast(na, za, nb, zb, nc, zc, dirs.w[k], r)) r = tri_ratio_d(na, nb, nc, dirs.w[k], gl);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) r += __shfl_down_sync(kFull, r, off);  // fixed order
+        if (lane == 0) Pm[k] = r * (1.0f / float(kLeafQuads * kLeafQuads));
+    }
+    __syncwarp();
+    if (lane == 0) {
+        float4 o;
+        if (!ggx_fit(Pm, dirs, o)) o = make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, 0.f);
+        omega[m] = o;
+    }
+}
+
+// One thread per node of level l: P = mean of the four children's, then the fit.
+__global__ void ggx_up(MapDesc d, int l, GgxDirs dirs, const float *__restrict__ Pc, float *__restrict__ Pp,
+                       float4 *__restrict__ omega, uint32_t count)
+{
+    const uint32_t m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= count) return;
+    float Pl[kGgxDirs];
+    bool ok = ggx_node_inside(d, l, m);
+    for (int k = 0; k < kGgxDirs; ++k) {
+        float v = 0.f;
+        for (int c = 0; c < 4; ++c) v += Pc[(4 * size_t(m) + c) * kGgxDirs + k];
+        Pl[k] = 0.25f * v;
+        ok = ok && isfinite(Pl[k]);
+    }
+    for (int k = 0; k < kGgxDirs; ++k) Pp[size_t(m) * kGgxDirs + k] = ok ? Pl[k] : __int_as_float(0x7fc00000);
+    float4 o = make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, 0.f);
+    if (ok && !ggx_fit(Pl, dirs, o)) o = make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, 0.f);
+    omega[m] = o;
+}
+
+GgxDirs make_ggx_dirs()
+{
+    GgxDirs g;
+    const double r = sqrt(1.0 - double(kGgxWz) * kGgxWz);
+    for (int k = 0; k < kGgxDirs; ++k) {
+        const double ph = 2.0 * 3.14159265358979323846 * k / kGgxDirs;
+        Dir &w = g.w[k];
+        w.wx = float(r * cos(ph));
+        w.wy = float(r * sin(ph));
+        w.wz = kGgxWz;
+        w.wr = sqrtf(w.wx * w.wx + w.wy * w.wy);
+        w.c = w.wr > 0.f ? w.wx / w.wr : 1.f;
+        w.s = w.wr > 0.f ? w.wy / w.wr : 0.f;
+    }
+    return g;
+}
+
+// Omega at a footprint: two mip levels around lambda = log2(sqrt(12) sigma),
+// each bilinear between node centres, nodes without a fit dropped.
+__device__ bool ggx_omega_at(const pndf_ggx &g, float x, float y, float sxx, float syy, float3 &O)
+{
+    const int L = g.L;
+    float lam = log2f(3.4641016f * sqrtf(fmaxf(sxx, syy)));
+    lam = fminf(fmaxf(lam, 2.0f), float(L));
+    const int l0 = int(floorf(lam)), l1 = l0 < L ? l0 + 1 : l0;
+    const float tl = lam - float(l0);
+    float ax = 0.f, ay = 0.f, az = 0.f, wsum = 0.f;
+    for (int side = 0; side < 2; ++side) {
+        const int l = side ? l1 : l0;
+        const float wl = side ? tl : 1.0f - tl;
+        if (wl == 0.f) continue;
+        const float a = float(1 << l);
+        const int S = 1 << (L - l);
+        const float fx = x / a - 0.5f, fy = y / a - 0.5f;
+        const float flx = floorf(fx), fly = floorf(fy);
+        const float tx = fx - flx, ty = fy - fly;
+        float lx = 0.f, ly = 0.f, lz = 0.f, lw = 0.f;
+        for (int dj = 0; dj < 2; ++dj)
+            for (int di = 0; di < 2; ++di) {
+                const int I = int(fminf(fmaxf(flx + di, 0.f), float(S - 1)));
+                const int J = int(fminf(fmaxf(fly + dj, 0.f), float(S - 1)));
+                const float4 o = g.omega[l][morton2(uint32_t(I), uint32_t(J))];
+                if (!isfinite(o.x)) continue;
+                const float w = (di ? tx : 1.f - tx) * (dj ? ty : 1.f - ty);
+                lx += w * o.x;
+                ly += w * o.y;
+                lz += w * o.z;
+                lw += w;
+            }
+        if (lw > 0.f) {
+            ax += wl * lx / lw;
+            ay += wl * ly / lw;
+            az += wl * lz / lw;
+            wsum += wl;
+        }
+    }
+    if (!(wsum > 0.f)) return false;
+    O = make_float3(ax / wsum, ay / wsum, az / wsum);
+    return true;
+}
+
+__device__ __forceinline__ float ggx_lambda(const float3 &O, float wx, float wy, float wz)
+{
+    const float qf = O.x * wx * wx + 2.0f * O.y * wx * wy + O.z * wy * wy;
+    return 0.5f * (wz + sqrtf(fmaxf(wz * wz + qf, 0.f))) / wz - 1.0f;
+}
+
+__global__ void ggx_eval(pndf_ggx g, const pndf_query *__restrict__ q, const float *__restrict__ wi,
+                         const float *__restrict__ wo, int64_t n, float *__restrict__ out)
+{
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+        const pndf_query r = q[k];
+        float3 O;
+        if (!(r.sxx > 0.f && r.syy > 0.f) || !ggx_omega_at(g, r.x, r.y, r.sxx, r.syy, O)) {
+            out[k] = __int_as_float(0x7fc00000);
+            continue;
+        }
+        const float ix = wi[3 * k], iy = wi[3 * k + 1], iz = wi[3 * k + 2];
+        const float li = ggx_lambda(O, ix, iy, iz);
+        if (!wo) {
+            out[k] = li;
+            continue;
+        }
+        // height-correlated shadow-masking with the query normal m
+        const float ox = wo[3 * k], oy = wo[3 * k + 1], oz = wo[3 * k + 2];
+        const float mz = sqrtf(fmaxf(0.f, 1.0f - r.ms * r.ms - r.mt * r.mt));
+        const float ci = r.ms * ix + r.mt * iy + mz * iz, co = r.ms * ox + r.mt * oy + mz * oz;
+        out[k] = (ci > 0.f && co > 0.f) ? 1.0f / (1.0f + li + ggx_lambda(O, ox, oy, oz)) : 0.f;
+    }
+}
+
+__global__ void ggx_copy(pndf_ggx g, int l, float *__restrict__ out)
+{
+    const uint32_t S = 1u << (g.L - l);
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= S * S) return;
+    const float4 o = g.omega[l][morton2(i % S, i / S)];
+    out[3 * size_t(i)] = o.x;
+    out[3 * size_t(i) + 1] = o.y;
+    out[3 * size_t(i) + 2] = o.z;
+}
+
 }  // namespace
+
+pndf_status launch_ggx_build(const pndf_hierarchy *h, pndf_ggx *g, cudaStream_t s)
+{
+    const MapDesc &d = h->d;
+    const int L = d.L;
+    const uint32_t nleaf = uint32_t(level_nodes(L, kLeafLevel));
+    const size_t pbytes = size_t(nleaf) * kGgxDirs * sizeof(float);
+    void *scratch = nullptr;
+    if (cudaMallocAsync(&scratch, 2 * pbytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return PNDF_ERR_OOM;
+    }
+    float *pa = static_cast<float *>(scratch), *pb = pa + size_t(nleaf) * kGgxDirs;
+    static const GLTable gl = make_gl();
+    static const GgxDirs dirs = make_ggx_dirs();
+    const unsigned blocks = unsigned((size_t(nleaf) * 32 + 255) / 256);
+    if (d.texel_fmt == PNDF_TEXEL_F32X2)
+        ggx_leaf<PNDF_TEXEL_F32X2><<<blocks, 256, 0, s>>>(d, dirs, gl, pa, g->omega[kLeafLevel], nleaf);
+    else
+        ggx_leaf<PNDF_TEXEL_F16X2><<<blocks, 256, 0, s>>>(d, dirs, gl, pa, g->omega[kLeafLevel], nleaf);
+    count_launches(1);
+    cudaError_t e = cudaGetLastError();
+    for (int l = kLeafLevel + 1; e == cudaSuccess && l <= L; ++l) {
+        const uint32_t cnt = uint32_t(level_nodes(L, l));
+        ggx_up<<<(cnt + 127) / 128, 128, 0, s>>>(d, l, dirs, pa, pb, g->omega[l], cnt);
+        count_launches(1);
+        e = cudaGetLastError();
+        float *t = pa;
+        pa = pb;
+        pb = t;
+    }
+    cudaError_t ef = cudaFreeAsync(scratch, s);
+    return (e == cudaSuccess && ef == cudaSuccess) ? PNDF_OK : PNDF_ERR_CUDA;
+}
+
+cudaError_t launch_ggx_eval(const pndf_ggx *g, const pndf_query *q, const float *wi, const float *wo, int64_t n,
+                            float *out, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > int64_t(sms) * 16) blocks = int64_t(sms) * 16;
+    ggx_eval<<<unsigned(blocks), 256, 0, s>>>(*g, q, wi, wo, n, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ggx_copy(const pndf_ggx *g, int l, float *out, cudaStream_t s)
+{
+    const uint32_t n = uint32_t(level_nodes(g->L, l));
+    ggx_copy<<<(n + 255) / 256, 256, 0, s>>>(*g, l, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
 
 pndf_status launch_projarea(const pndf_hierarchy *h, const pndf_query *q, const float *omega, int64_t nq, float *P,
                             cudaStream_t s)

@@ -81,6 +81,11 @@ def _load() -> ctypes.CDLL:
         "pndf_hierarchy_bytes": ([vp], ctypes.c_size_t),
         "pndf_cluster_level": ([vp, i32, vp, vp, vp], i32),
         "pndf_sample_normals": ([vp, vp, vp, i64, i32, ctypes.c_float, vp, vp, vp, vp], i32),
+        "pndf_ggx_create": ([vp, vp, ctypes.POINTER(vp)], i32),
+        "pndf_ggx_free": ([vp], None),
+        "pndf_ggx_lambda": ([vp, vp, vp, i64, vp, vp], i32),
+        "pndf_shadow_masking": ([vp, vp, vp, vp, i64, vp, vp], i32),
+        "pndf_ggx_level": ([vp, i32, vp, vp], i32),
         "pndf_eval_batch": ([vp, vp, i64, vp, vp, vp, vp], i32),
         "pndf_eval_batch_ex": ([vp, vp, i64, vp, vp, vp, ctypes.POINTER(_EvalConfig), vp], i32),
         "pndf_eval_batch_host": ([vp, vp, i64, vp, vp], i32),
@@ -228,6 +233,65 @@ def pndf_sample_normals(h: Hierarchy, queries: torch.Tensor, uniforms: torch.Ten
                                                               float(jac_eps), _ptr(m), _ptr(tri), _ptr(flags),
                                                               _stream(stream)))
     return m, tri, flags
+
+
+class GGX:
+    """The GGX projected-area fit of every mip node of a hierarchy (Eq. 12)."""
+
+    def __init__(self, handle: int, n: int, device: torch.device):
+        self.handle = handle
+        self.n = n
+        self.device = device
+
+    def free(self):
+        if self.handle:
+            LIB.pndf_ggx_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def pndf_ggx_create(h: Hierarchy, stream=None) -> GGX:
+    out = ctypes.c_void_p()
+    with torch.cuda.device(h.device):
+        _check("pndf_ggx_create", LIB.pndf_ggx_create(h.handle, _stream(stream), ctypes.byref(out)))
+    return GGX(out.value, h.n, h.device)
+
+
+def pndf_ggx_lambda(g: GGX, queries: torch.Tensor, omega: torch.Tensor, stream=None) -> torch.Tensor:
+    """Lambda'(omega) per query footprint; omega (n, 3) float32 unit directions."""
+    n = _queries(queries)
+    _need(omega, "omega", dtype=torch.float32, shape_last=3)
+    out = torch.empty(n, dtype=torch.float32, device=queries.device)
+    with torch.cuda.device(queries.device):
+        _check("pndf_ggx_lambda", LIB.pndf_ggx_lambda(g.handle, _ptr(queries), _ptr(omega), n, _ptr(out),
+                                                      _stream(stream)))
+    return out
+
+
+def pndf_shadow_masking(g: GGX, queries: torch.Tensor, wi: torch.Tensor, wo: torch.Tensor, stream=None):
+    """Height-correlated G(wi, wo, m) per query (m = the query normal)."""
+    n = _queries(queries)
+    _need(wi, "wi", dtype=torch.float32, shape_last=3)
+    _need(wo, "wo", dtype=torch.float32, shape_last=3)
+    out = torch.empty(n, dtype=torch.float32, device=queries.device)
+    with torch.cuda.device(queries.device):
+        _check("pndf_shadow_masking", LIB.pndf_shadow_masking(g.handle, _ptr(queries), _ptr(wi), _ptr(wo), n,
+                                                              _ptr(out), _stream(stream)))
+    return out
+
+
+def pndf_ggx_level(g: GGX, level: int, stream=None) -> torch.Tensor:
+    """Level `level` of the fit: (S, S, 3) float32 (O_xx, O_xy, O_yy), indexed [J, I]."""
+    S = 1 << (top_level(g.n) - level)
+    out = torch.empty(S, S, 3, dtype=torch.float32, device=g.device)
+    with torch.cuda.device(g.device):
+        _check("pndf_ggx_level", LIB.pndf_ggx_level(g.handle, int(level), _ptr(out), _stream(stream)))
+    return out
 
 
 def pndf_cluster_level(h: Hierarchy, level: int, stream=None):
