@@ -323,12 +323,37 @@ def run_mixed(args, dev):
     pa_ms, pn_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
     assert torch.isfinite(P).all() and torch.isfinite(D).all()
     tris = footprint_triangles(qa, cfg["n"])
+    # GGX fit of every mip node (Eq. 12): build time, Lambda' throughput, and
+    # its projected area P' = w_z (1 + Lambda') against the analytic P above
+    ev[0].record()
+    g = pndf.pndf_ggx_create(h)
+    ev[1].record()
+    reps = max(1, (1 << 22) // nq)
+    qb, wb = qa.repeat(reps, 1), w.repeat(reps, 1)
+    lam = pndf.pndf_ggx_lambda(g, qb, wb)  # warm
+    ev[2].record()
+    lam = pndf.pndf_ggx_lambda(g, qb, wb)
+    ev[3].record()
+    torch.cuda.synchronize()
+    fit_ms, lam_ms = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
+    Pg = (w[:, 2] * (1.0 + lam[:nq])).double()
+    rel = ((Pg - P.double()).abs() / P.double().clamp_min(1e-12)).cpu()
+    graz = (w[:, 2] < 0.2).cpu()
+    g.free()
     h.free()
+
+    def pct(x, p):
+        return float(torch.quantile(x, p)) if x.numel() else float("nan")
+
     return {"workload": f"16384^2 binary16 mixed map (scratches + flakes); {nq} projected-area requests and {nq} "
                         "P-NDF queries, sigma log-U(1, 1024), light uniform on the hemisphere",
             "projected_area": {"requests_per_s": nq / (pa_ms / 1e3), "ms": pa_ms, "triangles": tris,
                                "triangles_per_s": tris / (pa_ms / 1e3)},
-            "pndf": {"queries_per_s": nq / (pn_ms / 1e3), "ms": pn_ms}}
+            "pndf": {"queries_per_s": nq / (pn_ms / 1e3), "ms": pn_ms},
+            "ggx_fit": {"build_ms": fit_ms, "lambda_per_s": qb.shape[0] / (lam_ms / 1e3),
+                        "P_rel_diff_vs_analytic": {"median": pct(rel, 0.5), "p95": pct(rel, 0.95),
+                                                   "median_grazing_wz<0.2": pct(rel[graz], 0.5),
+                                                   "median_wz>=0.2": pct(rel[~graz], 0.5)}}}
 
 
 # ---------------------------------------------------------------------------
