@@ -338,11 +338,13 @@ def run_mixed(args, dev):
     fit_ms, lam_ms = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
     Pg = (w[:, 2] * (1.0 + lam[:nq])).double()
     rel = ((Pg - P.double()).abs() / P.double().clamp_min(1e-12)).cpu()
+    covered = torch.isfinite(rel)  # footprints whose mip nodes all reach past the map border have no fit
     graz = (w[:, 2] < 0.2).cpu()
     g.free()
     h.free()
 
     def pct(x, p):
+        x = x[torch.isfinite(x)]
         return float(torch.quantile(x, p)) if x.numel() else float("nan")
 
     return {"workload": f"16384^2 binary16 mixed map (scratches + flakes); {nq} projected-area requests and {nq} "
@@ -351,6 +353,7 @@ def run_mixed(args, dev):
                                "triangles_per_s": tris / (pa_ms / 1e3)},
             "pndf": {"queries_per_s": nq / (pn_ms / 1e3), "ms": pn_ms},
             "ggx_fit": {"build_ms": fit_ms, "lambda_per_s": qb.shape[0] / (lam_ms / 1e3),
+                        "footprints_covered": float(covered.double().mean()),
                         "P_rel_diff_vs_analytic": {"median": pct(rel, 0.5), "p95": pct(rel, 0.95),
                                                    "median_grazing_wz<0.2": pct(rel[graz], 0.5),
                                                    "median_wz>=0.2": pct(rel[~graz], 0.5)}}}
