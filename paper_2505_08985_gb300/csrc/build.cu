@@ -12,11 +12,12 @@
 //
 // Kernel 1 (build_tiles): one CTA per 64 x 64-quad tile.  The tile's 65 x 65
 // texels are staged in shared memory with 16-byte vector loads (float4 = two
-// FP32 texels, uint4 = four FP16 texels), each thread builds one leaf node's
-// 16 quad boxes and their union, and levels up to 6 are reduced in shared
-// memory.  A
-// tile is a Morton-aligned square at every level, so its nodes form one
-// contiguous run and the writes are fully coalesced.
+// FP32 texels, uint4 = four FP16 texels) and stored unchanged into the
+// hierarchy's own copy of the map (each texel by exactly one tile, so the map
+// is read once per build); each thread builds one leaf node's 16 quad boxes
+// and their union, and levels up to 6 are reduced in shared memory.  A tile
+// is a Morton-aligned square at every level, so its nodes form one contiguous
+// run and the writes are fully coalesced.
 // Kernel 2 (build_up): one launch per level above the tile, four contiguous
 // children reduced per thread.
 // FP16 bounds round outward (min toward -inf, max toward +inf) so pruning
@@ -38,6 +39,20 @@ __device__ __forceinline__ float2 load_texel(const void *t, size_t idx)
     return __half22float2(reinterpret_cast<const __half2 *>(t)[idx]);
 }
 
+// Texel idx of src, loaded for staging and (own) stored unchanged in dst.
+template <int TFMT>
+__device__ __forceinline__ float2 copy_texel(const void *src, void *dst, size_t idx, bool own)
+{
+    if (TFMT == PNDF_TEXEL_F32X2) {
+        float2 v = reinterpret_cast<const float2 *>(src)[idx];
+        if (own) reinterpret_cast<float2 *>(dst)[idx] = v;
+        return v;
+    }
+    __half2 v = reinterpret_cast<const __half2 *>(src)[idx];
+    if (own) reinterpret_cast<__half2 *>(dst)[idx] = v;
+    return __half22float2(v);
+}
+
 // VEC = texels per 16-byte load (2 for FP32, 4 for FP16), or 1 when rows are
 // not 16-byte aligned (n not a multiple of VEC).
 template <int TFMT, int BFMT, int VEC>
@@ -52,32 +67,41 @@ __global__ void __launch_bounds__(kBuildThreads) build_tiles(const void *__restr
     const int c0 = blockIdx.x * tileQ, r0 = blockIdx.y * tileQ;
     const int tid = threadIdx.x;
 
-    // ---- stage texels: VEC-wide loads for the first tileQ columns ----
+    // ---- stage texels: VEC-wide loads for the first tileQ columns.  The
+    // hierarchy's own copy of the map is written on the way: a tile owns its
+    // first tileQ rows and columns, and the map's last row or column where it
+    // is the tile's shared edge, so every texel is stored exactly once ----
+    void *copy = const_cast<void *>(d.texels);
     const int nvec = tileQ / VEC;
     for (int idx = tid; idx < tw * nvec; idx += kBuildThreads) {
         int r = idx / nvec, v = idx - r * nvec;
         int gr = r0 + r, gc = c0 + v * VEC;
         if (gr >= n || gc >= n) continue;
+        const bool own = r < tileQ || gr == n - 1;
         size_t g = size_t(gr) * n + gc;
         float2 *dst = &tex[r * kTileTexMax + v * VEC];
         if (VEC == 2) {
             float4 p = reinterpret_cast<const float4 *>(src)[g >> 1];
+            if (own) reinterpret_cast<float4 *>(copy)[g >> 1] = p;
             dst[0] = make_float2(p.x, p.y);
             dst[1] = make_float2(p.z, p.w);
         } else if (VEC == 4) {
             uint4 p = reinterpret_cast<const uint4 *>(src)[g >> 2];
+            if (own) reinterpret_cast<uint4 *>(copy)[g >> 2] = p;
             dst[0] = __half22float2(*reinterpret_cast<__half2 *>(&p.x));
             dst[1] = __half22float2(*reinterpret_cast<__half2 *>(&p.y));
             dst[2] = __half22float2(*reinterpret_cast<__half2 *>(&p.z));
             dst[3] = __half22float2(*reinterpret_cast<__half2 *>(&p.w));
         } else {
-            dst[0] = load_texel<TFMT>(src, g);
+            dst[0] = copy_texel<TFMT>(src, copy, g, own);
         }
     }
     // the shared last column of the tile
     for (int r = tid; r < tw; r += kBuildThreads) {
         int gr = r0 + r, gc = c0 + tileQ;
-        if (gr < n && gc < n) tex[r * kTileTexMax + tileQ] = load_texel<TFMT>(src, size_t(gr) * n + gc);
+        if (gr < n && gc < n)
+            tex[r * kTileTexMax + tileQ] =
+                copy_texel<TFMT>(src, copy, size_t(gr) * n + gc, gc == n - 1 && (r < tileQ || gr == n - 1));
     }
     __syncthreads();
 
@@ -182,9 +206,7 @@ cudaError_t launch_tiles(const void *src, const MapDesc &d, cudaStream_t s)
 cudaError_t launch_build(const void *texels_src, pndf_hierarchy *h, cudaStream_t s)
 {
     const MapDesc &d = h->d;
-    size_t tb = size_t(d.n) * d.n * (d.texel_fmt == PNDF_TEXEL_F32X2 ? 8 : 4);
-    cudaError_t e = cudaMemcpyAsync(const_cast<void *>(d.texels), texels_src, tb, cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
     if (d.texel_fmt == PNDF_TEXEL_F32X2)
         e = d.bounds_fmt == PNDF_BOUNDS_F32 ? launch_tiles<PNDF_TEXEL_F32X2, PNDF_BOUNDS_F32>(texels_src, d, s)
                                             : launch_tiles<PNDF_TEXEL_F32X2, PNDF_BOUNDS_F16_OUTWARD>(texels_src, d, s);

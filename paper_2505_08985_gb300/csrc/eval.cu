@@ -5,26 +5,29 @@
 //       k_r(a l0 + b l1 + c l2 - x) / |(n_b - n_a) x (n_c - n_a)|.
 //
 // Pipeline (all on the caller's stream):
-//   key_hist  : entry level l = ceil(log2 r) of the 4-sigma box half-width r
-//               (App. C, "entry level") and a 16 x 16 tile of the centre ->
-//               16-bit key; shared-memory histogram.
-//   key_scan  : exclusive scan of the 4096 bins (one CTA).
-//   key_place : counting-sort placement -> query order, largest footprints
-//               first, spatially grouped inside a level.
+//   key_hist  : per query a key of 4 + sub bits: the entry level (App. C; the
+//               smallest level whose node side reaches the support's
+//               half-width), largest footprints first, above a sub-key of 6..14
+//               bits (footprint tile and/or query-normal bin); counted into a
+//               global histogram with atomics.
+//   key_scan  : exclusive scan of the histogram (one CTA).
+//   key_place : counting-sort placement -> query order.
 //   traverse  : persistent warps pull queries from an atomic cursor; one warp
 //               per query.  Depth-first descent of the min/max pyramid with a
-//               per-warp shared-memory stack: each step pops up to 8 nodes,
-//               lane k tests child (k & 3) of popped node (k >> 2) - uv box
-//               against the 4-sigma ellipse first, then the normal box against
-//               m - and ballot/popc compaction pushes survivors.  Surviving
-//               leaf blocks (4 x 4 quads) have their 16 per-quad boxes (level
-//               0, one 128-byte line in FP16) tested one per lane, two blocks
-//               per pass; quads whose box holds m are compacted into a
-//               per-warp ring and their triangles tested 32 at a time (lane =
-//               triangle).  The query's sum is reduced across the warp and
-//               written in caller order (the unpermute is fused into the
-//               store).  Flat mode skips every box and tests all 32 triangles
-//               of every leaf block in the footprint's bounding box.
+//               per-warp shared-memory stack: each step pops up to 16 nodes,
+//               lane k tests child (k & 3) of popped nodes (k >> 2) and
+//               (k >> 2) + 8 - uv box against the support first, then the
+//               normal box against m - and ballot/popc compaction pushes the
+//               survivors.  Surviving leaf blocks (4 x 4 quads) have their 16
+//               per-quad boxes (level 0, one 128-byte line in FP16) tested four
+//               per lane in one load, eight blocks per pass; quads whose box
+//               holds m are compacted into a per-warp ring and tested 32 at a
+//               time (lane = quad, both triangles), and edge-test hits are
+//               compacted once more and weighed 32 at a time.  The query's
+//               sum is reduced across the warp and written in caller order
+//               (the unpermute is fused into the store).  Flat mode skips
+//               every box and tests all 32 triangles of every leaf block in
+//               the support's bounding box.
 // Hit test (tie rule): m inside the closed normal bounding box and all three
 // edge functions sign-consistent with the triangle orientation (>= 0 after
 // orientation, i.e. closed barycentrics).  Zero-area normal triangles are a
@@ -94,6 +97,7 @@ struct Query {
     float inv_sxx;       // box: 1 / S_xx, so that (L^-1 d)_x^2 = dx^2 / S_xx
     float l11, l21, l22; // box: the Cholesky factor L of S (node tests by separating axes)
     float jac, rho;      // Eq. 6 clamp: Jacobian floor eps and the replacement's circumradius (0: off)
+    __half2 mlo, mhi;    // m rounded down / up to binary16, for tests against binary16 boxes
     int kernel;
     bool valid;
 };
@@ -115,6 +119,8 @@ __device__ __forceinline__ Query make_query(const pndf_query &r, int kernel = PN
     q.y = r.y;
     q.mx = r.ms;
     q.my = r.mt;
+    q.mlo = __halves2half2(__float2half_rd(r.ms), __float2half_rd(r.mt));
+    q.mhi = __halves2half2(__float2half_ru(r.ms), __float2half_ru(r.mt));
     q.kernel = kernel;
     float det = r.sxx * r.syy - r.sxy * r.sxy;
     q.valid = (r.sxx > 0.f) && (r.syy > 0.f) && (det > 0.f) && isfinite(det) && isfinite(r.x) &&
@@ -198,14 +204,23 @@ __device__ __forceinline__ float qmin_box(const Query &q, float dx0, float dx1, 
     return best;
 }
 
+// A node's normal box as stored: FP32 (s_min, t_min, s_max, t_max) in x..w,
+// or binary16 (s_min, t_min) and (s_max, t_max) as two half2 in x and y.
 template <int BFMT>
-__device__ __forceinline__ float4 node_box(const MapDesc &d, int l, uint32_t m)
+__device__ __forceinline__ uint4 node_box(const MapDesc &d, int l, uint32_t m)
 {
-    if (BFMT == PNDF_BOUNDS_F32) return __ldg(reinterpret_cast<const float4 *>(d.lv[l]) + m);
+    if (BFMT == PNDF_BOUNDS_F32) return __ldg(reinterpret_cast<const uint4 *>(d.lv[l]) + m);
     uint2 v = __ldg(reinterpret_cast<const uint2 *>(d.lv[l]) + m);
-    float2 lo = __half22float2(*reinterpret_cast<__half2 *>(&v.x));
-    float2 hi = __half22float2(*reinterpret_cast<__half2 *>(&v.y));
-    return make_float4(lo.x, lo.y, hi.x, hi.y);
+    return make_uint4(v.x, v.y, 0u, 0u);
+}
+
+// m in a binary16 box (lo, hi): for binary16 values lo and hi, m >= lo
+// exactly when m rounded down to binary16 is >= lo, and m <= hi exactly when
+// m rounded up is <= hi, so two packed comparisons decide it as FP32 would.
+__device__ __forceinline__ bool half_box_holds(uint32_t lo, uint32_t hi, const Query &q)
+{
+    return __hbge2(q.mlo, *reinterpret_cast<const __half2 *>(&lo)) &&
+           __hble2(q.mhi, *reinterpret_cast<const __half2 *>(&hi));
 }
 
 template <int TFMT>
@@ -268,11 +283,24 @@ __device__ __forceinline__ bool box_holds(const float4 &b, const Query &q)
     return q.mx >= b.x && q.mx <= b.z && q.my >= b.y && q.my <= b.w;
 }
 
+// m in a node box as stored (node_box).
+template <int BFMT, bool CLAMP>
+__device__ __forceinline__ bool stored_box_holds(const uint4 &v, const Query &q)
+{
+    if (BFMT == PNDF_BOUNDS_F32)
+        return box_holds<CLAMP>(make_float4(__uint_as_float(v.x), __uint_as_float(v.y), __uint_as_float(v.z),
+                                            __uint_as_float(v.w)), q);
+    if (!CLAMP) return half_box_holds(v.x, v.y, q);
+    float2 lo = __half22float2(*reinterpret_cast<const __half2 *>(&v.x));
+    float2 hi = __half22float2(*reinterpret_cast<const __half2 *>(&v.y));
+    return box_holds<CLAMP>(make_float4(lo.x, lo.y, hi.x, hi.y), q);
+}
+
 template <int BFMT, bool CLAMP>
 __device__ __forceinline__ bool node_test(const MapDesc &d, const Query &q, int l, uint32_t a, uint32_t c)
 {
     if (!node_in_footprint(q, l, a, c)) return false;
-    return box_holds<CLAMP>(node_box<BFMT>(d, l, morton2(a, c)), q);
+    return stored_box_holds<BFMT, CLAMP>(node_box<BFMT>(d, l, morton2(a, c)), q);
 }
 
 // Stack / leaf-queue entry: level in bits 28-31, "inside the ellipse" in bit
@@ -508,8 +536,15 @@ __device__ __forceinline__ void test_leaf(const MapDesc &d, const Query &q, uint
 
 // Survivor ring: quads whose level-0 box holds m, packed (i << 16) | j.
 constexpr int kRing = 256;
-// Shared memory per warp: DFS stack, leaf queue (64), survivor ring, hit ring.
-constexpr int kWarpSmemWords = kStackCap + 64 + kRing + 4 * kHitRing;
+// Leaf queue: up to 7 leaf blocks held over from the last step plus one
+// step's 64 children; cut cluster nodes fill it from the back (entry k at
+// kLeafQ - 1 - k), and a step's new leaf blocks and cut nodes number at most
+// 64 together, so the two ends never meet.
+constexpr int kLeafQ = 72;
+// Shared memory per warp: DFS stack, leaf queue, survivor ring, hit ring
+// (a multiple of four words, so the hit ring stays 16-byte aligned).
+constexpr int kWarpSmemWords = kStackCap + kLeafQ + kRing + 4 * kHitRing;
+static_assert((kStackCap + kLeafQ + kRing) % 4 == 0, "hit ring alignment");
 
 // Per-warp leaf state: survivor-quad ring and hit ring with their heads/counts.
 struct LeafState {
@@ -664,9 +699,9 @@ __device__ __forceinline__ void test_clusters(const MapDesc &d, const ClusterDes
 // Four level-0 boxes (Morton-consecutive quads) in one 32-byte (FP16) or
 // 64-byte (FP32) load; returns bit u set when box u holds m.
 template <int BFMT, bool CLAMP>
-__device__ __forceinline__ unsigned quad_boxes_hold(const MapDesc &d, uint32_t first, float mx, float my, float rho)
+__device__ __forceinline__ unsigned quad_boxes_hold(const MapDesc &d, uint32_t first, const Query &q)
 {
-    if (!CLAMP) rho = 0.f;  // (no widening: folds away)
+    const float mx = q.mx, my = q.my, rho = CLAMP ? q.rho : 0.f;
     unsigned bits = 0;
     if (BFMT == PNDF_BOUNDS_F32) {
         const float4 *p = reinterpret_cast<const float4 *>(d.lv[0]) + first;
@@ -682,6 +717,11 @@ __device__ __forceinline__ unsigned quad_boxes_hold(const MapDesc &d, uint32_t f
         const uint4 *p = reinterpret_cast<const uint4 *>(reinterpret_cast<const uint2 *>(d.lv[0]) + first);
         uint4 v0 = __ldg(p), v1 = __ldg(p + 1);
         uint32_t w[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+        if (!CLAMP) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) bits |= unsigned(half_box_holds(w[2 * u], w[2 * u + 1], q)) << u;
+            return bits;
+        }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             float2 lo = __half22float2(*reinterpret_cast<__half2 *>(&w[2 * u]));
@@ -705,13 +745,15 @@ __device__ __forceinline__ void process_leaves(const MapDesc &d, const Query &q,
     for (int p = 0; p < nleaf; p += 8) {
         const int blk = p + (lane >> 2);
         unsigned bits = 0;
-        uint32_t a = 0, c = 0;
-        const uint32_t k0 = uint32_t(lane & 3) << 2;
+        uint32_t base = 0;
         if (blk < nleaf) {
             uint32_t m = lq[blk] & kMortonMask;
-            a = compact1by1(m);
-            c = compact1by1(m >> 1);
-            bits = quad_boxes_hold<BFMT, CLAMP>(d, (m << 4) | k0, q.mx, q.my, q.rho);
+            // the lane's four quads are the 2 x 2 quad group (lane & 3) of the
+            // block (Morton order): (i0 + u & 1, j0 + u >> 1) for u = 0..3
+            const uint32_t i0 = compact1by1(m) * kLeafQuads + ((uint32_t(lane) & 1u) << 1);
+            const uint32_t j0 = compact1by1(m >> 1) * kLeafQuads + (uint32_t(lane) & 2u);
+            base = (i0 << 16) | j0;
+            bits = quad_boxes_hold<BFMT, CLAMP>(d, (m << 4) | (uint32_t(lane & 3) << 2), q);
             if (STATS) {
                 acc.quads += 4;
                 if ((lane & 3) == 0) acc.leaves++;
@@ -721,12 +763,9 @@ __device__ __forceinline__ void process_leaves(const MapDesc &d, const Query &q,
         for (int u = 0; u < 4; ++u) {
             bool pass = (bits >> u) & 1u;
             unsigned m = __ballot_sync(kFull, pass);
-            if (pass) {
-                uint32_t k = k0 | uint32_t(u);  // Morton index of the quad in its 4 x 4 block
-                uint32_t kx = (k & 1u) | ((k >> 1) & 2u), ky = ((k >> 1) & 1u) | ((k >> 2) & 2u);
-                uint32_t pk = ((a * kLeafQuads + kx) << 16) | (c * kLeafQuads + ky);
-                ls.ring[(ls.head + uint32_t(ls.nsq) + __popc(m & lt)) & (kRing - 1)] = pk;
-            }
+            if (pass)
+                ls.ring[(ls.head + uint32_t(ls.nsq) + __popc(m & lt)) & (kRing - 1)] =
+                    base + ((uint32_t(u) & 1u) << 16) + (uint32_t(u) >> 1);
             ls.nsq += __popc(m);
         }
         __syncwarp();
@@ -826,7 +865,7 @@ __device__ void eval_one(const MapDesc &d, const ClusterDesc &cd, float tau, flo
                 else
                     stk[pos] = ent;
             }
-            if (CLUSTER && cut) lq[63 - __popc(mc & lt)] = pack(e, false, morton2(a, c));
+            if (CLUSTER && cut) lq[kLeafQ - 1 - __popc(mc & lt)] = pack(e, false, morton2(a, c));
             if (e == kLeafLevel)
                 nleaf = __popc(m);
             else
@@ -837,13 +876,22 @@ __device__ void eval_one(const MapDesc &d, const ClusterDesc &cd, float tau, flo
         bool overflow = false;
         LeafState ls{ring, hits, 0u, 0u, 0, 0};
         while (true) {
-            process_leaves<BFMT, TFMT, STATS, CLAMP>(d, q, lq, nleaf, ls, lane, acc);
-            nleaf = 0;
+            // leaf blocks are filtered eight to a pass (four lanes each): while
+            // the stack still holds nodes only whole passes run, and the rest
+            // (fewer than 8) waits at the front of the queue for the next step
+            const int nrun = top == 0 ? nleaf : (nleaf & ~7);
+            process_leaves<BFMT, TFMT, STATS, CLAMP>(d, q, lq, nrun, ls, lane, acc);
+            if (nrun > 0 && nrun < nleaf) {
+                const int rest = nleaf - nrun;  // < 8 <= nrun: source and target do not overlap
+                uint32_t v = lane < rest ? lq[nrun + lane] : 0u;
+                if (lane < rest) lq[lane] = v;
+                __syncwarp();
+            }
+            nleaf -= nrun;
             if (CLUSTER) {
-                // cut nodes sit at the back of the leaf queue (entry k at lq[63 - k];
-                // leaf blocks fill the front, together at most 64 per step)
+                // cut nodes sit at the back of the leaf queue
                 for (int k0 = 0; k0 < ncl; k0 += 32) {
-                    test_clusters<STATS>(d, cd, q, lq + 63 - k0, min(32, ncl - k0), ls, lane, acc);
+                    test_clusters<STATS>(d, cd, q, lq + kLeafQ - 1 - k0, min(32, ncl - k0), ls, lane, acc);
                     __syncwarp();
                 }
                 ncl = 0;
@@ -856,7 +904,7 @@ __device__ void eval_one(const MapDesc &d, const ClusterDesc &cd, float tau, flo
             bool pass[2], ins[2], cut[2] = {false, false};
             int cl[2];
             uint32_t cm[2];
-            float4 bx[2];
+            uint4 bx[2];
             float ev[2];
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
@@ -882,7 +930,7 @@ __device__ void eval_one(const MapDesc &d, const ClusterDesc &cd, float tau, flo
                 }
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
-                pass[r] = pass[r] && box_holds<CLAMP>(bx[r], q);
+                pass[r] = pass[r] && stored_box_holds<BFMT, CLAMP>(bx[r], q);
                 if (CLUSTER && pass[r]) {  // the cut of Sec. 4.3: e <= r_x r_y tau
                     cut[r] = ev[r] <= q.theta;
                     if (STATS) acc.cchecks++;
@@ -897,7 +945,7 @@ __device__ void eval_one(const MapDesc &d, const ClusterDesc &cd, float tau, flo
                 unsigned ms = __ballot_sync(kFull, to_stack);
                 if (CLUSTER) {
                     unsigned mc = __ballot_sync(kFull, cut[r]);
-                    if (cut[r]) lq[63 - ncl - __popc(mc & lt)] = pack(cl[r], false, cm[r]);
+                    if (cut[r]) lq[kLeafQ - 1 - ncl - __popc(mc & lt)] = pack(cl[r], false, cm[r]);
                     ncl += __popc(mc);
                 }
                 if (to_leaf) lq[nleaf + __popc(ml & lt)] = pack(cl[r], ins[r], cm[r]);
@@ -963,7 +1011,7 @@ __global__ void __launch_bounds__(256, PNDF_TRAVERSE_MIN_CTAS)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t *stk = smem + warp * kWarpSmemWords;
     uint32_t *lq = stk + kStackCap;
-    uint32_t *ring = lq + 64;
+    uint32_t *ring = lq + kLeafQ;
     float4 *hits = reinterpret_cast<float4 *>(ring + kRing);
     while (true) {
         unsigned long long k = 0;
@@ -1280,7 +1328,7 @@ __global__ void __launch_bounds__(256, PNDF_TRAVERSE_MIN_CTAS)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t *stk = smem + warp * kWarpSmemWords;
     uint32_t *lq = stk + kStackCap;
-    uint32_t *ring = lq + 64;
+    uint32_t *ring = lq + kLeafQ;
     float4 *hits = reinterpret_cast<float4 *>(ring + kRing);
     const int nsegs = int(table[0]);
     const uint32_t *prefix = table + 1;

@@ -83,14 +83,20 @@ def test_fp16_outward_bounds_keep_hit_sets(P):
     check_pndf(D16, ref, hits_gpu=s16[:, 3], hash_gpu=s16[:, 4], label="scratch512 fp16 bounds")
 
 
-def test_fp16_texels(P):
-    """A binary16-stored map: the map is its FP16 values (decoded exactly by the oracle)."""
-    st = synth.flake_normals(256, 300, seed=4).half()
-    q = synth.make_queries(st.float(), 2000, synth.QueryMix(sigma=(1.0, 20.0), frac_near=0.7), 4)
+@pytest.mark.parametrize("n", [256, 203, 129])
+def test_fp16_texels(P, n):
+    """A binary16-stored map: the map is its FP16 values (decoded exactly by
+    the oracle).  256: 16-byte vector loads; 203: rows not a multiple of four
+    texels (scalar loads); 129: the map's last column is a tile's shared edge.
+    The tile build also writes the hierarchy's own copy of the texels, which
+    every leaf test reads."""
+    st = synth.flake_normals(n, 300 * n * n // 65536 + 20, seed=4).half()
+    mix = synth.QueryMix(sigma=(1.0, 20.0), frac_near=0.7, centre_margin=-4)
+    q = synth.make_queries(st.float(), 2000, mix, 4)
     ref = oracle.pndf(st.float(), q)
     for bounds in (0, 1):
         D, _, stt = run(P, st, q, bounds=bounds)
-        check_pndf(D, ref, hits_gpu=stt[:, 3], hash_gpu=stt[:, 4], label=f"fp16 texels bounds={bounds}")
+        check_pndf(D, ref, hits_gpu=stt[:, 3], hash_gpu=stt[:, 4], label=f"fp16 texels n={n} bounds={bounds}")
 
 
 @pytest.mark.parametrize("n", [2, 3, 5, 6, 37, 100, 129, 257])
