@@ -67,6 +67,11 @@ def parse():
     ap.add_argument("--serve-load", type=float, default=0.8, help="offered load, fraction of plain FP32 capacity")
     ap.add_argument("--mixed-requests", type=int, default=4096,
                     help="projected-area + P-NDF sample on the 16384^2 FP16 map (0 = skip)")
+    ap.add_argument("--mixed-map-size", type=int, default=synth.MIXED_16384["n"],
+                    help="side of the mixed scratches + flakes map (cells and grooves scale with the area)")
+    ap.add_argument("--kernel-census", action="store_true",
+                    help="launch every kernel family except the traversal once on a small workload and print "
+                         "the units each launch processed (the program the per-kernel ncu census profiles)")
     return ap.parse_args()
 
 
@@ -177,11 +182,78 @@ def hbm_peak():
 
 
 def kernel_source_hash() -> str:
+    return sources_hash(("eval.cu", "common.cuh"))
+
+
+CENSUS_FILE = os.path.join(ROOT, "profiles", "kernels_census_flake4096_mixed4096.txt")
+CENSUS_SOURCES = ("build.cu", "cluster.cu", "eval.cu", "projarea.cu", "sample.cu", "common.cuh", "ggx.cuh")
+
+
+def sources_hash(files) -> str:
     h = hashlib.sha256()
-    for f in ("eval.cu", "common.cuh"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_2505_08985_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def committed_census() -> dict:
+    """Per-unit counts of each kernel family (DRAM bytes, warp instructions,
+    FP32 and FP64 FLOPs with an FMA as two) from the committed ncu census,
+    if it was taken on the current sources; else {}."""
+    if not os.path.exists(CENSUS_FILE):
+        return {}
+    src, out = None, {}
+    with open(CENSUS_FILE) as f:
+        for line in f:
+            if line.startswith("sources_sha256_16:"):
+                src = line.split(":", 1)[1].strip()
+            elif line.startswith("per_unit "):
+                parts = line.split()
+                out[parts[1]] = {k: float(v) for k, v in (kv.split("=", 1) for kv in parts[2:])}
+    return out if src == sources_hash(CENSUS_SOURCES) else {}
+
+
+def compute_peaks(dev) -> dict:
+    """Issue and arithmetic peaks from the unit counts and the maximum SM
+    clock: 4 warp schedulers, 128 FP32 lanes and 2 FP64 lanes per SM per
+    clock (the last gives the nominal 1.25 TFLOP/s FP64), an FMA as 2 FLOPs."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f)["sm_max_mhz"])
+    except Exception:
+        mhz = 2070.0
+    clk = mhz * 1e6
+    return {"issue": sms * 4 * clk / 1e9, "fp32": sms * 128 * 2 * clk / 1e12, "fp64": sms * 2 * 2 * clk / 1e12,
+            "sms": sms, "sm_mhz": mhz}
+
+
+def family_roofline(family, kernels, ms, units, unit, hbm_bytes_per_unit, census, peaks, hbm_pk):
+    """Roofline of one kernel family from its live CUDA-event time: HBM on
+    algorithmic bytes, and (with a census of the current sources) instruction
+    issue, FP32 and FP64 FLOP/s from its per-unit counts; `bound` is the
+    resource with the largest fraction."""
+    sec = ms / 1e3
+    out = {"kernels": kernels, "ms": ms, "units": units, "unit": unit}
+    fr = {}
+    if hbm_bytes_per_unit is not None:
+        out["algorithmic_bytes"] = hbm_bytes_per_unit * units
+        fr["hbm"] = (hbm_bytes_per_unit * units / sec / 1e9, hbm_pk, "GB/s")
+    c = census.get(family)
+    if c:
+        fr["issue"] = (c["warp_inst"] * units / sec / 1e9, peaks["issue"], "G warp-inst/s")
+        fr["fp32"] = (c["fp32_flop"] * units / sec / 1e12, peaks["fp32"], "TFLOP/s")
+        fr["fp64"] = (c["fp64_flop"] * units / sec / 1e12, peaks["fp64"], "TFLOP/s")
+        out["traffic"] = c["dram_bytes"] * units
+    if not fr:
+        out.update(bound=None, achieved=None, peak=None, frac=None)
+        return out
+    bound = max(fr, key=lambda k: fr[k][0] / fr[k][1])
+    a, pk, u = fr[bound]
+    out.update(bound=bound, achieved=a, peak=pk, unit_rate=u, frac=a / pk,
+               fracs={k: v[0] / v[1] for k, v in fr.items()})
+    return out
 
 
 def committed_traffic(bounds_tag: str):
@@ -298,11 +370,89 @@ def footprint_triangles(q: torch.Tensor, n: int) -> int:
     return tot
 
 
+def mixed_map_scaled(n: int, dev) -> torch.Tensor:
+    """The binary16 scratches + flakes map at side n, with cells and grooves
+    scaled with the area so that they keep their size in texels."""
+    cfg = synth.MIXED_16384
+    a = (n / cfg["n"]) ** 2
+    return synth.mixed_map(n=n, n_cells=max(1, round(800_000 * a)), n_grooves=max(1, round(8000 * a)),
+                           seed=cfg["seed"], device=dev).half()
+
+
+def leaf_blocks(n: int) -> int:
+    """Leaf nodes (4 x 4 quads) of the pyramid over an n x n map."""
+    from paper_2505_08985_gb300 import pndf
+    return 4 ** (pndf.top_level(n) - 2)
+
+
+def tree_nodes(n: int) -> int:
+    """Nodes of levels 2..L of the pyramid over an n x n map."""
+    from paper_2505_08985_gb300 import pndf
+    L = pndf.top_level(n)
+    return sum(4 ** (L - l) for l in range(2, L + 1))
+
+
+def pyramid_bytes(n: int, texel_bytes: int, box_bytes: int) -> int:
+    """Algorithmic bytes of one pyramid build: the map read once, the
+    hierarchy's copy of it written once, and every stored box written once
+    (level 0 and levels 2..L, padded to 2^L quads per side)."""
+    from paper_2505_08985_gb300 import pndf
+    boxes = 4 ** pndf.top_level(n) + tree_nodes(n)
+    return 2 * n * n * texel_bytes + boxes * box_bytes
+
+
+def run_census(dev):
+    """Every kernel family but the traversal, each launched once in this
+    order on a small workload: the pyramid build and query sort of a 4096^2
+    FP32 flake map with 262,144 queries, sampling those footprints, the
+    cluster build of the same map, then on a 4096^2 binary16 mixed map 1024
+    projected-area requests, the GGX fit and Lambda' for 262,144 requests.
+    This is the program the per-kernel ncu census profiles; it prints the
+    units each family's launch processed."""
+    from paper_2505_08985_gb300 import pndf
+    n, nq = 4096, 1 << 18
+    cfg = synth.FLAKE_8192
+    st = synth.flake_map(n=n, n_cells=round(200_000 * (n / cfg["n"]) ** 2), seed=cfg["seed"], device=dev)
+    q = synth.make_queries(st, nq, cfg["mix"], cfg["seed"])
+    U = torch.rand(nq, 2, device=dev, generator=torch.Generator(device=dev).manual_seed(11))
+    stm = mixed_map_scaled(n, dev)
+    mcfg = synth.MIXED_16384
+    qm = synth.make_queries(stm.float(), nq, mcfg["mix"], mcfg["seed"])
+    w = synth.hemisphere_dirs(nq, seed=mcfg["seed"], device=dev)
+    npa = 1024
+    torch.cuda.synchronize()
+    calls = []
+    h = pndf.pndf_build_hierarchy(st, bounds_fmt=pndf.PNDF_BOUNDS_F16_OUTWARD)
+    calls.append(("pyramid_build", n * n))
+    pndf.pndf_sort_queries(h, q)
+    calls.append(("query_sort", nq))
+    pndf.pndf_sample_normals(h, q, U, jac_eps=1e-6)
+    calls.append(("sampling", nq))
+    torch.cuda.synchronize()
+    h.free()
+    hc = pndf.pndf_build_hierarchy(st, bounds_fmt=pndf.PNDF_BOUNDS_F16_OUTWARD, clusters=True)
+    calls.append(("cluster_fit", leaf_blocks(n)))
+    torch.cuda.synchronize()
+    hc.free()
+    hm = pndf.pndf_build_hierarchy(stm, bounds_fmt=pndf.PNDF_BOUNDS_F16_OUTWARD)
+    calls.append(("mixed_pyramid_build", n * n))
+    pndf.pndf_diffuse_projected_area(hm, qm[:npa].contiguous(), w[:npa].contiguous())
+    calls.append(("projected_area", footprint_triangles(qm[:npa], n)))
+    g = pndf.pndf_ggx_create(hm)
+    calls.append(("ggx_fit", leaf_blocks(n)))
+    pndf.pndf_ggx_lambda(g, qm, w)
+    calls.append(("ggx_lambda", nq))
+    torch.cuda.synchronize()
+    g.free()
+    hm.free()
+    print(json.dumps({"census": calls, "device_status": pndf.pndf_device_status()}), flush=True)
+
+
 def run_mixed(args, dev):
     from paper_2505_08985_gb300 import pndf
 
     cfg = synth.MIXED_16384
-    st = synth.mixed_map(n=cfg["n"], seed=cfg["seed"], device=dev).half()
+    st = mixed_map_scaled(args.mixed_map_size, dev)
     nq = args.mixed_requests
     q = synth.make_queries(st.float(), 2 * nq, cfg["mix"], cfg["seed"])
     qa, qp = q[:nq].contiguous(), q[nq:].contiguous()
@@ -322,7 +472,7 @@ def run_mixed(args, dev):
     torch.cuda.synchronize()
     pa_ms, pn_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
     assert torch.isfinite(P).all() and torch.isfinite(D).all()
-    tris = footprint_triangles(qa, cfg["n"])
+    tris = footprint_triangles(qa, st.shape[0])
     # GGX fit of every mip node (Eq. 12): build time, Lambda' throughput, and
     # its projected area P' = w_z (1 + Lambda') against the analytic P above
     ev[0].record()
@@ -352,7 +502,9 @@ def run_mixed(args, dev):
             "projected_area": {"requests_per_s": nq / (pa_ms / 1e3), "ms": pa_ms, "triangles": tris,
                                "triangles_per_s": tris / (pa_ms / 1e3)},
             "pndf": {"queries_per_s": nq / (pn_ms / 1e3), "ms": pn_ms},
-            "ggx_fit": {"build_ms": fit_ms, "lambda_per_s": qb.shape[0] / (lam_ms / 1e3),
+            "map_n": st.shape[0],
+            "ggx_fit": {"build_ms": fit_ms, "lambda_ms": lam_ms, "lambda_requests": qb.shape[0],
+                        "lambda_per_s": qb.shape[0] / (lam_ms / 1e3),
                         "footprints_covered": float(covered.double().mean()),
                         "P_rel_diff_vs_analytic": {"median": pct(rel, 0.5), "p95": pct(rel, 0.95),
                                                    "median_grazing_wz<0.2": pct(rel[graz], 0.5),
@@ -661,6 +813,7 @@ def run_gpu(args, world, rank, local):
     peak, peak_kind = hbm_peak()
     achieved = work["f16"]["bytes"] / (kavg16 / 1e3) / 1e9
     traffic = committed_traffic("f16")
+    stage_ms = time_build_and_sort(args, world, st, q)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -700,6 +853,8 @@ def run_gpu(args, world, rank, local):
     if args.serve_batches > 0:
         line["serving"] = run_serving(args, dev)
         line["serving"]["note"] = "per GPU (each rank serves its own replica of the stream)"
+    line["kernel_rooflines"] = kernel_rooflines(dev, args.n, nq, stage_ms, kavg16, work["f16"]["bytes"], traffic,
+                                                cluster, clamp, line.get("glint_diffuse_16384"))
     if (args.serve_batches > 0 or args.mixed_requests > 0) and rank == 0 and world == 1 and not args.no_cpu_baseline:
         st, q = make_workload(args, dev, rank)
 
@@ -714,12 +869,93 @@ def run_gpu(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def time_build_and_sort(args, world, st, q):
+    """CUDA-event time of the pyramid build (FP16 outward bounds) and of the
+    query sort alone, each averaged over the bench's step count after warm-up."""
+    from paper_2505_08985_gb300 import pndf
+    stream = torch.cuda.current_stream()
+    h = pndf.pndf_build_hierarchy(st, bounds_fmt=pndf.PNDF_BOUNDS_F16_OUTWARD)
+    order = torch.empty(q.shape[0], dtype=torch.int32, device=q.device)
+    out = {}
+    for name, fn in (("pyramid_build", lambda: pndf.pndf_update_hierarchy(h, st)),
+                     ("query_sort", lambda: pndf.pndf_sort_queries(h, q, order))):
+        for _ in range(args.warmup):
+            fn()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = max_over_ranks(world, t0.elapsed_time(t1)) / args.steps
+    h.free()
+    return out
+
+
+def kernel_rooflines(dev, n, nq, stage_ms, traverse_ms, traverse_bytes, traverse_traffic, cluster, clamp, mixed):
+    """Roofline of every kernel family, from the CUDA-event times measured
+    in this run.  Algorithmic bytes per unit: pyramid build, the FP32 map
+    read and its copy written (8 B each per texel) plus every FP16 box written
+    (8 B); query sort, the 32 B record read, the key written and read back
+    and the order slot written (4 B each); traversal, as in `roofline`;
+    sampling, record, uniforms, four texels and the outputs (88 B); Lambda',
+    record, direction and result (48 B) plus the 12 B Omega of the eight
+    nodes it blends (96 B); cluster fit, the map read (8 B per texel) and the
+    cluster records and residuals written (36 B per node); projected area,
+    two binary16 texels (8 B) per triangle; GGX fit, the binary16 map read
+    (4 B per texel) and Omega written (12 B per node).  Issue and FLOP rates
+    use the per-unit instruction counts of the committed ncu census, when it
+    was taken on the current sources."""
+    census = committed_census()
+    peaks = compute_peaks(dev)
+    pk, _ = hbm_peak()
+    out = {"peaks": {"hbm_gbs": pk, "issue_g_warp_inst_per_s": peaks["issue"], "fp32_tflops": peaks["fp32"],
+                     "fp64_tflops": peaks["fp64"],
+                     "derived_from": f"{peaks['sms']} SMs at {peaks['sm_mhz']:.0f} MHz; HBM measured copy"},
+           "census": "profiles/" + os.path.basename(CENSUS_FILE) if census else None}
+    fams = {}
+    fams["pyramid_build"] = family_roofline("pyramid_build", ["build_tiles", "build_up"], stage_ms["pyramid_build"],
+                                            n * n, "texel", pyramid_bytes(n, 8, 8) / (n * n), census, peaks, pk)
+    fams["query_sort"] = family_roofline("query_sort", ["key_hist", "key_scan", "key_place"], stage_ms["query_sort"],
+                                         nq, "query", 44, census, peaks, pk)
+    tr = family_roofline("traverse", ["traverse_kernel"], traverse_ms, nq, "query", traverse_bytes / nq, {}, peaks, pk)
+    tr["traffic"] = traverse_traffic
+    fams["traverse"] = tr
+    if cluster:
+        ms = cluster["build_ms"] - stage_ms["pyramid_build"]
+        fams["cluster_fit"] = family_roofline("cluster_fit", ["cluster_tiles", "cluster_up"], ms, leaf_blocks(n),
+                                              "leaf block", (8 * n * n + 36 * tree_nodes(n)) / leaf_blocks(n),
+                                              census, peaks, pk)
+        fams["cluster_fit"]["note"] = "cluster build minus the pyramid build it includes"
+    if clamp:
+        fams["sampling"] = family_roofline("sampling", ["sample_kernel"], clamp["sampling"]["ms_per_step"], nq,
+                                           "sample", 88, census, peaks, pk)
+    if mixed:
+        m = mixed["map_n"]
+        pa = mixed["projected_area"]
+        fams["projected_area"] = family_roofline("projected_area", ["pa_bands", "pa_scan", "pa_items", "pa_reduce"], pa["ms"],
+                                                 pa["triangles"], "triangle", 8, census, peaks, pk)
+        gf = mixed["ggx_fit"]
+        fams["ggx_fit"] = family_roofline("ggx_fit", ["ggx_leaf", "ggx_up"], gf["build_ms"], leaf_blocks(m),
+                                          "leaf block", (4 * m * m + 12 * tree_nodes(m)) / leaf_blocks(m), census, peaks, pk)
+        fams["ggx_fit"]["note"] = "includes the fit's allocation"
+        fams["ggx_lambda"] = family_roofline("ggx_lambda", ["ggx_eval"], gf["lambda_ms"], gf["lambda_requests"],
+                                             "request", 144, census, peaks, pk)
+    out["families"] = fams
+    return out
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
     try:
         if args.impl == "reference":
             run_reference(args, world, rank)
+        elif args.kernel_census:
+            if not torch.cuda.is_available():
+                raise SystemExit("bench.py: no CUDA device (the GPU arm has no CPU fallback)")
+            run_census(torch.device("cuda:0"))
         else:
             if not torch.cuda.is_available():
                 raise SystemExit("bench.py: no CUDA device (the GPU arm has no CPU fallback)")

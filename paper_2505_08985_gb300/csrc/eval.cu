@@ -48,7 +48,7 @@ constexpr int kStackCap = 768;     // DFS stack entries per warp (about 48 per l
 constexpr int kMaxSubBits = 14;                   // sub-key bits below the 4 entry-level bits
 constexpr int kKeyBins = 1 << (4 + kMaxSubBits);  // largest histogram (2^18 bins)
 #ifndef PNDF_TRAVERSE_MIN_CTAS
-#define PNDF_TRAVERSE_MIN_CTAS 4     // 4 x 256 threads per SM at <= 64 registers, no spills
+#define PNDF_TRAVERSE_MIN_CTAS 4     // 4 x 256 threads per SM at <= 64 registers (measured faster than 3)
 #endif
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -97,7 +97,6 @@ struct Query {
     float inv_sxx;       // box: 1 / S_xx, so that (L^-1 d)_x^2 = dx^2 / S_xx
     float l11, l21, l22; // box: the Cholesky factor L of S (node tests by separating axes)
     float jac, rho;      // Eq. 6 clamp: Jacobian floor eps and the replacement's circumradius (0: off)
-    __half2 mlo, mhi;    // m rounded down / up to binary16, for tests against binary16 boxes
     int kernel;
     bool valid;
 };
@@ -119,8 +118,6 @@ __device__ __forceinline__ Query make_query(const pndf_query &r, int kernel = PN
     q.y = r.y;
     q.mx = r.ms;
     q.my = r.mt;
-    q.mlo = __halves2half2(__float2half_rd(r.ms), __float2half_rd(r.mt));
-    q.mhi = __halves2half2(__float2half_ru(r.ms), __float2half_ru(r.mt));
     q.kernel = kernel;
     float det = r.sxx * r.syy - r.sxy * r.sxy;
     q.valid = (r.sxx > 0.f) && (r.syy > 0.f) && (det > 0.f) && isfinite(det) && isfinite(r.x) &&
@@ -205,22 +202,14 @@ __device__ __forceinline__ float qmin_box(const Query &q, float dx0, float dx1, 
 }
 
 // A node's normal box as stored: FP32 (s_min, t_min, s_max, t_max) in x..w,
-// or binary16 (s_min, t_min) and (s_max, t_max) as two half2 in x and y.
+// or binary16 (s_min, t_min) and (s_max, t_max) as two half2 in x and y
+// (decoded only where tested, so a box in flight holds two registers).
 template <int BFMT>
 __device__ __forceinline__ uint4 node_box(const MapDesc &d, int l, uint32_t m)
 {
     if (BFMT == PNDF_BOUNDS_F32) return __ldg(reinterpret_cast<const uint4 *>(d.lv[l]) + m);
     uint2 v = __ldg(reinterpret_cast<const uint2 *>(d.lv[l]) + m);
     return make_uint4(v.x, v.y, 0u, 0u);
-}
-
-// m in a binary16 box (lo, hi): for binary16 values lo and hi, m >= lo
-// exactly when m rounded down to binary16 is >= lo, and m <= hi exactly when
-// m rounded up is <= hi, so two packed comparisons decide it as FP32 would.
-__device__ __forceinline__ bool half_box_holds(uint32_t lo, uint32_t hi, const Query &q)
-{
-    return __hbge2(q.mlo, *reinterpret_cast<const __half2 *>(&lo)) &&
-           __hble2(q.mhi, *reinterpret_cast<const __half2 *>(&hi));
 }
 
 template <int TFMT>
@@ -290,7 +279,6 @@ __device__ __forceinline__ bool stored_box_holds(const uint4 &v, const Query &q)
     if (BFMT == PNDF_BOUNDS_F32)
         return box_holds<CLAMP>(make_float4(__uint_as_float(v.x), __uint_as_float(v.y), __uint_as_float(v.z),
                                             __uint_as_float(v.w)), q);
-    if (!CLAMP) return half_box_holds(v.x, v.y, q);
     float2 lo = __half22float2(*reinterpret_cast<const __half2 *>(&v.x));
     float2 hi = __half22float2(*reinterpret_cast<const __half2 *>(&v.y));
     return box_holds<CLAMP>(make_float4(lo.x, lo.y, hi.x, hi.y), q);
@@ -717,11 +705,6 @@ __device__ __forceinline__ unsigned quad_boxes_hold(const MapDesc &d, uint32_t f
         const uint4 *p = reinterpret_cast<const uint4 *>(reinterpret_cast<const uint2 *>(d.lv[0]) + first);
         uint4 v0 = __ldg(p), v1 = __ldg(p + 1);
         uint32_t w[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-        if (!CLAMP) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) bits |= unsigned(half_box_holds(w[2 * u], w[2 * u + 1], q)) << u;
-            return bits;
-        }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             float2 lo = __half22float2(*reinterpret_cast<__half2 *>(&w[2 * u]));
