@@ -94,6 +94,7 @@ struct Query {
     float rx, ry;        // half-widths of the support's bounding box (slightly inflated)
     float qprune;        // the support lies in q <= qprune (16, 2.25, 4.5), with a margin
     float theta;         // r_x r_y of the support (exact half-widths); times tau for the cluster cut
+    float kyx, kxy;      // -ib / ic and -ib / ia: the minimiser of q along a vertical / horizontal line
     float inv_sxx;       // box: 1 / S_xx, so that (L^-1 d)_x^2 = dx^2 / S_xx
     float l11, l21, l22; // box: the Cholesky factor L of S (node tests by separating axes)
     float jac, rho;      // Eq. 6 clamp: Jacobian floor eps and the replacement's circumradius (0: off)
@@ -126,6 +127,8 @@ __device__ __forceinline__ Query make_query(const pndf_query &r, int kernel = PN
     q.ia = r.syy * inv;
     q.ib = -r.sxy * inv;
     q.ic = r.sxx * inv;
+    q.kyx = -q.ib / q.ic;
+    q.kxy = -q.ib / q.ia;
     const float sx = sqrtf(r.sxx), sy = sqrtf(r.syy), sd = sqrtf(det);
     float hx, hy;
     q.inv_sxx = 0.f;
@@ -183,19 +186,21 @@ __device__ __forceinline__ float qform(const Query &q, float dx, float dy)
 // Minimum of q over the box [dx0, dx1] x [dy0, dy1] (offsets from the centre).
 // The quadratic is convex with its minimum at the origin; off the box, the
 // minimum lies on an edge whose outer side holds the origin, where it is a
-// clamped 1D minimum.
+// clamped 1D minimum (along x = X at y = -(ib / ic) X, the ratio precomputed
+// per query; a minimiser off by rounding raises the value only to second
+// order, far inside the pruning margin).
 __device__ __forceinline__ float qmin_box(const Query &q, float dx0, float dx1, float dy0, float dy1)
 {
     if (dx0 <= 0.f && dx1 >= 0.f && dy0 <= 0.f && dy1 >= 0.f) return 0.f;
     float best = __int_as_float(0x7f800000);
     if (dx0 > 0.f || dx1 < 0.f) {
         float X = dx0 > 0.f ? dx0 : dx1;
-        float y = fminf(fmaxf(-q.ib * X / q.ic, dy0), dy1);
+        float y = fminf(fmaxf(q.kyx * X, dy0), dy1);
         best = fminf(best, qform(q, X, y));
     }
     if (dy0 > 0.f || dy1 < 0.f) {
         float Y = dy0 > 0.f ? dy0 : dy1;
-        float x = fminf(fmaxf(-q.ib * Y / q.ia, dx0), dx1);
+        float x = fminf(fmaxf(q.kxy * Y, dx0), dx1);
         best = fminf(best, qform(q, x, Y));
     }
     return best;

@@ -692,13 +692,36 @@ __device__ __forceinline__ bool ggx_node_inside(const MapDesc &d, int l, uint32_
     return a * (compact1by1(m) + 1) <= int64_t(d.n) - 1 && a * (compact1by1(m >> 1) + 1) <= int64_t(d.n) - 1;
 }
 
-// One warp per leaf block (Morton index): P at the fit directions (NaN when
-// the block has a quad outside the map) and the block's fit.
+// Vertices of triangle `lane` of leaf block (i0, j0) (lane = 2 quad + tri,
+// quads row-major in the 4 x 4 block; tri 0 = (u0, u1, u2), 1 = (u3, u2, u1)).
 template <int TFMT>
-__global__ void __launch_bounds__(256) ggx_leaf(MapDesc d, GgxDirs dirs, GLTable gl, float *__restrict__ P,
-                                                float4 *__restrict__ omega, uint32_t nleaf)
+__device__ __forceinline__ void leaf_triangle(const MapDesc &d, int i0, int j0, int lane, float2 &a, float2 &b,
+                                              float2 &c)
 {
-    const int lane = threadIdx.x & 31;
+    const int q = lane >> 1, tri = lane & 1;
+    const int i = i0 + (q & 3), j = j0 + (q >> 2);
+    a = texel<TFMT>(d, i + tri, j + tri);
+    b = texel<TFMT>(d, i + 1 - tri, j + tri);
+    c = texel<TFMT>(d, i + tri, j + 1 - tri);
+}
+
+// One warp per leaf block (Morton index): P at the fit directions (NaN when
+// the block has a quad outside the map) and the block's fit.  Each lane
+// evaluates its triangle at every direction in FP32 where that is accurate;
+// the (triangle, direction) pairs that need the FP64 path are listed and
+// spread over the warp 32 at a time, so the slow path runs lane-dense.  The
+// per-direction sums then run in the same fixed order either way.
+constexpr int kGgxLeafWarps = 8;
+static_assert(kGgxDirs <= 16, "a listed pair packs the direction in 4 bits");
+
+template <int TFMT>
+__global__ void __launch_bounds__(32 * kGgxLeafWarps) ggx_leaf(MapDesc d, GgxDirs dirs, GLTable gl,
+                                                               float *__restrict__ P, float4 *__restrict__ omega,
+                                                               uint32_t nleaf)
+{
+    __shared__ float r_s[kGgxLeafWarps][kGgxDirs][32];
+    __shared__ uint16_t item_s[kGgxLeafWarps][kGgxDirs * 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t m = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (m >= nleaf) return;
     float *Pm = P + size_t(m) * kGgxDirs;
@@ -707,15 +730,42 @@ __global__ void __launch_bounds__(256) ggx_leaf(MapDesc d, GgxDirs dirs, GLTable
         if (lane == 0) omega[m] = make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, 0.f);
         return;
     }
-    const int q = lane >> 1, tri = lane & 1;
-    const int i = int(compact1by1(m)) * kLeafQuads + (q & 3), j = int(compact1by1(m >> 1)) * kLeafQuads + (q >> 2);
-    const float2 na = texel<TFMT>(d, i + tri, j + tri);
-    const float2 nb = texel<TFMT>(d, i + 1 - tri, j + tri);
-    const float2 nc = texel<TFMT>(d, i + tri, j + 1 - tri);
+    float(*rs)[32] = r_s[warp];
+    uint16_t *items = item_s[warp];
+    const int i0 = int(compact1by1(m)) * kLeafQuads, j0 = int(compact1by1(m >> 1)) * kLeafQuads;
+    float2 na, nb, nc;
+    leaf_triangle<TFMT>(d, i0, j0, lane, na, nb, nc);
     const float za = zof(na), zb = zof(nb), zc = zof(nc);
+    uint32_t need = 0;  // bit k: direction k needs the FP64 path
     for (int k = 0; k < kGgxDirs; ++k) {
         float r;
-        if (!tri_ratio_fast(na, za, nb, zb, nc, zc, dirs.w[k], r)) r = tri_ratio_d(na, nb, nc, dirs.w[k], gl);
+        if (tri_ratio_fast(na, za, nb, zb, nc, zc, dirs.w[k], r))
+            rs[k][lane] = r;
+        else
+            need |= 1u << k;
+    }
+    // list the FP64 pairs (lane-major) and evaluate them 32 at a time
+    const int cnt = __popc(need);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(kFull, incl, 31);
+    for (int p = incl - cnt; need; need &= need - 1) items[p++] = uint16_t((lane << 4) | (__ffs(need) - 1));
+    __syncwarp();
+    for (int t0 = 0; t0 < total; t0 += 32) {
+        if (t0 + lane < total) {
+            const int it = items[t0 + lane], src = it >> 4, k = it & 15;
+            float2 a, b, c;
+            leaf_triangle<TFMT>(d, i0, j0, src, a, b, c);
+            rs[k][src] = tri_ratio_d(a, b, c, dirs.w[k], gl);
+        }
+    }
+    __syncwarp();
+    for (int k = 0; k < kGgxDirs; ++k) {
+        float r = rs[k][lane];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) r += __shfl_down_sync(kFull, r, off);  // fixed order
         if (lane == 0) Pm[k] = r * (1.0f / float(kLeafQuads * kLeafQuads));
@@ -866,11 +916,11 @@ pndf_status launch_ggx_build(const pndf_hierarchy *h, pndf_ggx *g, cudaStream_t 
     float *pa = static_cast<float *>(scratch), *pb = pa + size_t(nleaf) * kGgxDirs;
     static const GLTable gl = make_gl();
     static const GgxDirs dirs = make_ggx_dirs();
-    const unsigned blocks = unsigned((size_t(nleaf) * 32 + 255) / 256);
+    const unsigned blocks = unsigned((size_t(nleaf) + kGgxLeafWarps - 1) / kGgxLeafWarps);
     if (d.texel_fmt == PNDF_TEXEL_F32X2)
-        ggx_leaf<PNDF_TEXEL_F32X2><<<blocks, 256, 0, s>>>(d, dirs, gl, pa, g->omega[kLeafLevel], nleaf);
+        ggx_leaf<PNDF_TEXEL_F32X2><<<blocks, 32 * kGgxLeafWarps, 0, s>>>(d, dirs, gl, pa, g->omega[kLeafLevel], nleaf);
     else
-        ggx_leaf<PNDF_TEXEL_F16X2><<<blocks, 256, 0, s>>>(d, dirs, gl, pa, g->omega[kLeafLevel], nleaf);
+        ggx_leaf<PNDF_TEXEL_F16X2><<<blocks, 32 * kGgxLeafWarps, 0, s>>>(d, dirs, gl, pa, g->omega[kLeafLevel], nleaf);
     count_launches(1);
     cudaError_t e = cudaGetLastError();
     for (int l = kLeafLevel + 1; e == cudaSuccess && l <= L; ++l) {

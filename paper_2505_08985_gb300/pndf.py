@@ -30,7 +30,10 @@ PNDF_QF_FP64 = 1
 PNDF_QF_INVALID = 4
 PNDF_QF_OVERFLOW = 8
 
-STATS_FIELDS = ("nodes", "leaf_blocks", "tri_tests", "hits", "hit_hash", "fp64_tris", "degenerate", "quads")
+# pndf_query_stats, one int32 per field in this order
+STATS_NAMES = ("nodes", "leaf_blocks", "tri_tests", "hits", "hit_hash", "fp64_tris", "degenerate", "quads",
+               "cluster_checks", "clusters")
+STATS_FIELDS = len(STATS_NAMES)
 
 
 PNDF_KERNEL_GAUSS = 0  # footprint kernels (pndf_kernel): Gaussian cut at 4 sigma,
@@ -334,10 +337,6 @@ PNDF_SORT_LEVEL_NORMAL = 2
 PNDF_SORT_LEVEL_TILE_NORMAL = 3
 PNDF_SORT_LEVEL_NORMAL_TILE = 4
 PNDF_SORT_DEFAULT = PNDF_SORT_LEVEL_TILE
-
-
-STATS_FIELDS = 10  # pndf_query_stats: nodes, leaf_blocks, tri_tests, hits, hit_hash, fp64_tris, degenerate,
-                   # quads, cluster_checks, clusters
 
 
 def pndf_eval_batch_ex(h: Hierarchy, queries: torch.Tensor, out=None, flags=None, stats=None, mode: int = 0,
