@@ -65,6 +65,8 @@ def parse():
                     help="cluster cut thresholds to measure on the same workload ('' = skip)")
     ap.add_argument("--serve-batches", type=int, default=2000, help="serving workload size (0 = skip serving)")
     ap.add_argument("--serve-load", type=float, default=0.8, help="offered load, fraction of plain FP32 capacity")
+    ap.add_argument("--serve-sweep", default="0.5,0.95",
+                    help="further offered loads for the latency sweep ('' = skip)")
     ap.add_argument("--mixed-requests", type=int, default=4096,
                     help="projected-area + P-NDF sample on the 16384^2 FP16 map (0 = skip)")
     ap.add_argument("--mixed-map-size", type=int, default=synth.MIXED_16384["n"],
@@ -254,6 +256,22 @@ def family_roofline(family, kernels, ms, units, unit, hbm_bytes_per_unit, census
     out.update(bound=bound, achieved=a, peak=pk, unit_rate=u, frac=a / pk,
                fracs={k: v[0] / v[1] for k, v in fr.items()})
     return out
+
+
+def committed_ncu_pct(bounds_tag: str):
+    """ncu's DRAM, L2, L1 and issue throughput (% of peak) for the traversal
+    kernel from the committed summary, if taken on the current source."""
+    p = os.path.join(ROOT, "profiles", f"traverse_{WORKLOAD}.txt")
+    if not os.path.exists(p):
+        return None
+    src, val = None, None
+    with open(p) as f:
+        for line in f:
+            if line.startswith("kernel_source_sha256_16:"):
+                src = line.split(":", 1)[1].strip()
+            if line.startswith(f"ncu_pct_of_peak_{bounds_tag}:"):
+                val = {k: float(v) for k, v in (kv.split("=") for kv in line.split(":", 1)[1].split())}
+    return val if src == kernel_source_hash() else None
 
 
 def committed_traffic(bounds_tag: str):
@@ -543,8 +561,18 @@ def run_serving(args, dev):
     arrivals = serve.poisson_arrivals(n, rate, seed=17)
     served = batcher.run(requests(arrivals), realtime=True)
     steps = batcher.steps
-    batcher.close()
     plain = serve.run_plain(h32, requests(arrivals), realtime=True)
+    # the same stream at other offered loads (same tuned batcher)
+    sweep = []
+    for load in [float(x) for x in args.serve_sweep.split(",") if x.strip()]:
+        r = load * plain_cap["queries_per_s"] / (total / n)
+        arr = serve.poisson_arrivals(n, r, seed=17)
+        sv = batcher.run(requests(arr), realtime=True)
+        pl = serve.run_plain(h32, requests(arr), realtime=True)
+        sweep.append({"load": load, "batches_per_s": r,
+                      "served_fp16": {k: sv[k] for k in ("p50_ms", "p99_ms", "queries_per_s")},
+                      "plain_fp32": {k: pl[k] for k in ("p50_ms", "p99_ms", "queries_per_s")}})
+    batcher.close()
     # context: the plain path with each batch kept in arrival order (no sort)
     plain_unsorted_cap = serve.run_plain(h32, requests([0.0] * n), realtime=False, sort=pndf.PNDF_SORT_NONE)
     for h in h16 + h32:
@@ -557,6 +585,7 @@ def run_serving(args, dev):
                     f"{args.serve_load:g} x plain FP32 capacity ({rate:.1f} batches/s)",
         "served_fp16": {k: served[k] for k in keep},
         "plain_fp32": {k: plain[k] for k in keep},
+        "load_sweep": sweep,
         "capacity_queries_per_s": {"served_fp16": served_cap["queries_per_s"],
                                    "plain_fp32": plain_cap["queries_per_s"],
                                    "plain_fp32_unsorted": plain_unsorted_cap["queries_per_s"]},
@@ -814,6 +843,7 @@ def run_gpu(args, world, rank, local):
     achieved = work["f16"]["bytes"] / (kavg16 / 1e3) / 1e9
     traffic = committed_traffic("f16")
     stage_ms = time_build_and_sort(args, world, st, q)
+    flop_model = traversal_flops(dev, work["f16"], kavg16, world, peak)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -828,8 +858,10 @@ def run_gpu(args, world, rank, local):
                               "traverse_kernel_ms": sum(kms32) / len(kms32)},
         "traverse_kernel_ms": kavg16,
         "leaf_triangle_tests_per_s": work["f16"]["tri_tests"] * world / (kavg16 / 1e3),
+        "traversal_flops": flop_model,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs",
+                     "ncu_pct_of_peak": committed_ncu_pct("f16"),
                      "algorithmic_bytes_per_launch": work["f16"]["bytes"]},
         "work_per_launch": work,
         "e2e": {"value": e2e_value, "unit": UNIT,
@@ -867,6 +899,32 @@ def run_gpu(args, world, rank, local):
                                 "sample": f"{n_done} random queries of the same workload, {secs:.1f} s wall"}
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def traversal_flops(dev, w, kernel_ms, world, hbm_pk):
+    """The traversal's arithmetic against the FP32 roofline, on the counted
+    work of the stats pass: about 20 FLOPs per node test, 20 per triangle
+    test and 40 per hit (plus one exp per hit), and leaf triangle tests per
+    second against both the FP32 and the HBM ceilings (24 B of texels per
+    test), at the maximum SM clock and at the clock measured under a
+    power-capped dense load."""
+    peaks = compute_peaks(dev)
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            loaded = float(json.load(f)["clocks_under_load"]["sm_mhz_median"])
+    except Exception:
+        loaded = 1455.0
+    sec = kernel_ms / 1e3
+    flops = 20 * w["nodes"] + 20 * w["tri_tests"] + 40 * w["hits"]
+    tf = flops / sec / 1e12
+    clocks = {f"{peaks['sm_mhz']:.0f}_mhz": peaks["fp32"], f"{loaded:.0f}_mhz": peaks["fp32"] * loaded / peaks["sm_mhz"]}
+    tests = w["tri_tests"] / sec
+    return {"model": "20 FLOPs per node test + 20 per triangle test + 40 per hit (+1 exp per hit)",
+            "flops_per_launch": flops, "achieved_tflops": tf * world,
+            "fp32_peak_tflops": clocks, "frac_fp32": {k: tf / v for k, v in clocks.items()},
+            "leaf_triangle_tests": {"value": tests * world, "unit": "tests/s", "flops_per_test": 20,
+                                    "frac_fp32": {k: tests * 20 / 1e12 / v for k, v in clocks.items()},
+                                    "frac_hbm_24B_per_test": tests * 24 / 1e9 / hbm_pk}}
 
 
 def time_build_and_sort(args, world, st, q):

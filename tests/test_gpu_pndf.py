@@ -56,6 +56,46 @@ def test_bumps256_4096_queries(P):
     assert P.pndf_device_status() == 0
 
 
+def test_stats_match_host_count(P):
+    """Stats mode counts what it claims (the work figures behind the roofline):
+    in flat mode each query's leaf blocks and triangle tests equal a host count
+    of the 4 x 4-quad blocks whose closed extent meets the support's bounding
+    box and of the triangles inside the map in them; queries whose box edge
+    lies within 1e-3 texel of a block boundary are skipped (FP32 vs FP64
+    rounding), and there must be few."""
+    cfg = synth.BUMPS_256
+    st = synth.bumps_map(n=cfg["n"], seed=cfg["seed"])
+    mix = synth.QueryMix(sigma=(0.5, 20.0), aspect=(1.0, 3.0), frac_near=0.8, centre_margin=-10.0)
+    q = synth.make_queries(st, 4096, mix, cfg["seed"])
+    _, _, s = run(P, st, q, mode=1)
+    n = st.shape[0]
+    S = 1 << (P.top_level(n) - 2)
+    qd = q.double().numpy()
+    det = qd[:, 2] * qd[:, 4] - qd[:, 3] ** 2
+    assert (det > 0).all()
+    rx = 4.0 * np.sqrt(qd[:, 2]) * (1 + 1e-5) + 1e-6
+    ry = 4.0 * np.sqrt(qd[:, 4]) * (1 + 1e-5) + 1e-6
+    blocks = np.zeros(len(qd), np.int64)
+    tris = np.zeros(len(qd), np.int64)
+    ambiguous = np.zeros(len(qd), bool)
+    quads_in = np.clip(n - 1 - 4 * np.arange(S), 0, 4)  # quads of block column (row) a inside the map
+    for k in range(len(qd)):
+        lo_hi = []
+        for c, r in ((qd[k, 0], rx[k]), (qd[k, 1], ry[k])):
+            e0, e1 = (c - r) / 4.0, (c + r) / 4.0
+            ambiguous[k] |= min(abs(e0 - round(e0)), abs(e1 - round(e1))) < 2.5e-4
+            lo_hi.append((max(math.ceil(e0) - 1, 0), min(math.floor(e1), S - 1)))
+        (a0, a1), (c0, c1) = lo_hi
+        if a0 <= a1 and c0 <= c1:
+            blocks[k] = (a1 - a0 + 1) * (c1 - c0 + 1)
+            tris[k] = 2 * quads_in[a0:a1 + 1].sum() * quads_in[c0:c1 + 1].sum()
+    ok = ~ambiguous
+    assert ambiguous.sum() < 0.01 * len(qd)
+    assert np.array_equal(s[ok, 1], blocks[ok])
+    assert np.array_equal(s[ok, 2], tris[ok])
+    assert (tris[ok] > 0).mean() > 0.9
+
+
 def test_hierarchy_prunes_only(P):
     """Pyramid traversal and flat evaluation test exactly the same contributing
     triangles (every query, ties included: both use the same leaf predicate)."""
