@@ -155,7 +155,12 @@ typedef struct pndf_eval_config {
  * hierarchy (the caller may free texels_dev once the stream reaches the end
  * of this call's work).  On success *out owns device memory until
  * pndf_free_hierarchy().
- *   texels_dev: device, N*N texels in params->texel_fmt, row-major.
+ *   texels_dev: N*N texels in params->texel_fmt, row-major, in device memory
+ *     of the current device or in page-locked host memory (cudaHostAlloc /
+ *     cudaHostRegister; the build kernel then reads the map straight over the
+ *     host link, with no staging copy).  Other pointers (pageable host
+ *     memory, another device's memory) are rejected with INVALID_ARG before
+ *     any work is queued.
  * With params->clusters = 1 the cluster hierarchy of Sec. 4.3 is built too:
  * every node of level >= 2 whose quads all lie inside the map gets the four
  * corner normals of a two-triangle cluster (split like a quad) minimising
@@ -172,8 +177,9 @@ pndf_status pndf_build_hierarchy(const void *texels_dev, const pndf_build_params
 
 /* Rebuild h in place from new texels of the same size and format (the map
  * changed): copies the texels and recomputes every pyramid level on stream,
- * with no allocation.  Work already queued on h must be on the same stream
- * or complete.  Errors: INVALID_ARG, CUDA. */
+ * with no allocation.  texels_dev as for pndf_build_hierarchy (device memory
+ * or page-locked host memory).  Work already queued on h must be on the same
+ * stream or complete.  Errors: INVALID_ARG, CUDA. */
 pndf_status pndf_update_hierarchy(pndf_hierarchy *h, const void *texels_dev, void *stream);
 
 /* Release a hierarchy (synchronises its device memory release with the

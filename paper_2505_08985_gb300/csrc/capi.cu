@@ -37,6 +37,26 @@ void keep_pool_memory()
     cudaGetLastError();
 }
 
+// The address at which the current device reads a texel array: device
+// memory of this device as is, page-locked host memory through its mapped
+// device address (the build kernel then reads the map straight over the host
+// link, with no staging copy); nullptr for anything else (pageable host
+// memory, another device's memory), which the entry points reject before any
+// work is queued.
+const void *device_view(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return a.device == dev ? p : nullptr;
+    if (a.type == cudaMemoryTypeHost) return a.devicePointer;
+    return nullptr;
+}
+
 pndf_status check_hierarchy(const pndf_hierarchy *h)
 {
     if (!h || !h->mem) return PNDF_ERR_INVALID_ARG;
@@ -65,6 +85,8 @@ pndf_status pndf_build_hierarchy(const void *texels_dev, const pndf_build_params
     if (p->leaf_level != 0 && p->leaf_level != kLeafLevel) return PNDF_ERR_UNSUPPORTED;
     if (p->clusters != 0 && p->clusters != 1) return PNDF_ERR_INVALID_ARG;
     if (!aligned(texels_dev, p->texel_fmt == PNDF_TEXEL_F32X2 ? 8 : 4)) return PNDF_ERR_INVALID_ARG;
+    const void *src = device_view(texels_dev);
+    if (!src) return PNDF_ERR_INVALID_ARG;
 
     pndf_hierarchy *h = new (std::nothrow) pndf_hierarchy();
     if (!h) return PNDF_ERR_OOM;
@@ -121,7 +143,7 @@ pndf_status pndf_build_hierarchy(const void *texels_dev, const pndf_build_params
         }
         if (cluster_scratch_bytes(d.L)) h->moments = base + off_mom;
     }
-    cudaError_t e = launch_build(texels_dev, h, as_stream(stream));
+    cudaError_t e = launch_build(src, h, as_stream(stream));
     if (e != cudaSuccess) {
         cudaFree(h->mem);
         delete h;
@@ -136,7 +158,9 @@ pndf_status pndf_update_hierarchy(pndf_hierarchy *h, const void *texels_dev, voi
     pndf_status st = check_hierarchy(h);
     if (st != PNDF_OK) return st;
     if (!texels_dev || !aligned(texels_dev, h->d.texel_fmt == PNDF_TEXEL_F32X2 ? 8 : 4)) return PNDF_ERR_INVALID_ARG;
-    return launch_build(texels_dev, h, as_stream(stream)) == cudaSuccess ? PNDF_OK : PNDF_ERR_CUDA;
+    const void *src = device_view(texels_dev);
+    if (!src) return PNDF_ERR_INVALID_ARG;
+    return launch_build(src, h, as_stream(stream)) == cudaSuccess ? PNDF_OK : PNDF_ERR_CUDA;
 }
 
 void pndf_free_hierarchy(pndf_hierarchy *h)

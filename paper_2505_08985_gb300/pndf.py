@@ -171,11 +171,24 @@ class Hierarchy:
             pass
 
 
+def _texels(texels: torch.Tensor, device=None) -> torch.device:
+    """Check a texel tensor: a CUDA tensor, or a page-locked CPU tensor that the
+    build kernel reads directly (on `device`, default the current one).
+    Returns the device the build runs on."""
+    _need(texels, "texels", device=False, shape_last=2)
+    if texels.is_cuda:
+        return texels.device
+    if not texels.is_pinned():
+        raise ValueError("texels must be a CUDA tensor or a page-locked (pinned) CPU tensor")
+    return torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+
+
 def pndf_build_hierarchy(texels: torch.Tensor, bounds_fmt: int = PNDF_BOUNDS_F32, stream=None,
                          clusters: bool = False) -> Hierarchy:
-    """texels: (N, N, 2) float32 or float16 CUDA tensor, texel (i, j) at [j, i].
+    """texels: (N, N, 2) float32 or float16 CUDA tensor, or a pinned CPU tensor
+    read directly by the build kernel; texel (i, j) at [j, i].
     clusters: also build the cluster hierarchy (Sec. 4.3, Eq. 7-8) for tau > 0."""
-    _need(texels, "texels", shape_last=2)
+    dev = _texels(texels)
     if texels.dim() != 3 or texels.shape[0] != texels.shape[1]:
         raise ValueError("texels must be (N, N, 2)")
     if texels.dtype == torch.float32:
@@ -186,19 +199,20 @@ def pndf_build_hierarchy(texels: torch.Tensor, bounds_fmt: int = PNDF_BOUNDS_F32
         raise ValueError("texels must be float32 or float16")
     p = _BuildParams(int(texels.shape[0]), tf, int(bounds_fmt), 0, int(bool(clusters)))
     h = ctypes.c_void_p()
-    with torch.cuda.device(texels.device):
+    with torch.cuda.device(dev):
         _check("pndf_build_hierarchy", LIB.pndf_build_hierarchy(_ptr(texels), ctypes.byref(p), _stream(stream),
                                                                 ctypes.byref(h)))
-    return Hierarchy(h.value, int(texels.shape[0]), tf, int(bounds_fmt), texels.device, bool(clusters))
+    return Hierarchy(h.value, int(texels.shape[0]), tf, int(bounds_fmt), dev, bool(clusters))
 
 
 def pndf_update_hierarchy(h: Hierarchy, texels: torch.Tensor, stream=None) -> Hierarchy:
-    """Rebuild h in place from new texels of the same size and dtype."""
-    _need(texels, "texels", shape_last=2)
+    """Rebuild h in place from new texels of the same size and dtype (a CUDA
+    tensor, or a pinned CPU tensor read directly by the build kernel)."""
+    dev = _texels(texels, h.device)
     tf = PNDF_TEXEL_F32X2 if texels.dtype == torch.float32 else PNDF_TEXEL_F16X2
     if texels.shape[0] != h.n or tf != h.texel_fmt:
         raise ValueError("texels must match the hierarchy's size and format")
-    with torch.cuda.device(texels.device):
+    with torch.cuda.device(dev):
         _check("pndf_update_hierarchy", LIB.pndf_update_hierarchy(h.handle, _ptr(texels), _stream(stream)))
     return h
 

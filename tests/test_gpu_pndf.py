@@ -308,3 +308,47 @@ def test_update_in_place_matches_fresh_build(P):
     D_new = P.pndf_eval_batch(h2, q.to(DEV)).cpu()
     h2.free()
     assert torch.equal(D_upd, D_new)
+
+
+@pytest.mark.parametrize("n,half", [(96, False), (97, False), (128, True), (131, True)])
+def test_pinned_host_texels(P, n, half):
+    """Texels in page-locked host memory are read by the build kernel itself
+    (no staging copy): build and update from them give exactly the hierarchy
+    built from device texels (vector and scalar staging paths, FP32 and FP16)."""
+    st = synth.flake_normals(n, 60, seed=n)
+    st = st.half() if half else st
+    q = synth.make_queries(st.float(), 1500, synth.QueryMix(sigma=(1.0, 12.0), frac_near=0.8), n)
+    qd = q.to(DEV)
+    h_dev = P.pndf_build_hierarchy(st.to(DEV), bounds_fmt=1)
+    D_dev = P.pndf_eval_batch(h_dev, qd).cpu()
+    h_dev.free()
+    pinned = st.pin_memory()
+    h = P.pndf_build_hierarchy(pinned, bounds_fmt=1)
+    D_build = P.pndf_eval_batch(h, qd).cpu()
+    other = synth.bumps_map(n=n, n_bumps=5, seed=n + 1)
+    P.pndf_update_hierarchy(h, (other.half() if half else other).to(DEV))
+    P.pndf_update_hierarchy(h, pinned)
+    D_upd = P.pndf_eval_batch(h, qd).cpu()
+    h.free()
+    assert torch.equal(D_build, D_dev) and torch.equal(D_upd, D_dev)
+    assert P.pndf_device_status() == 0
+
+
+def test_unreadable_texels_rejected(P):
+    """A pointer the device cannot read (pageable host memory) is refused on the
+    host with INVALID_ARG before any work is queued, by the C ABI itself and
+    by the binding."""
+    import ctypes
+    st = synth.bumps_map(n=64, n_bumps=4, seed=3)
+    h = P.pndf_build_hierarchy(st.to(DEV), bounds_fmt=1)
+    pageable = st.clone()
+    assert not pageable.is_pinned()
+    s = torch.cuda.current_stream().cuda_stream
+    assert P.LIB.pndf_update_hierarchy(h.handle, ctypes.c_void_p(pageable.data_ptr()), ctypes.c_void_p(s)) == 1
+    with pytest.raises(ValueError):
+        P.pndf_update_hierarchy(h, pageable)
+    with pytest.raises(ValueError):
+        P.pndf_build_hierarchy(pageable)
+    D = P.pndf_eval_batch(h, synth.make_queries(st, 100, synth.QueryMix(sigma=(1.0, 4.0)), 1).to(DEV))
+    assert torch.isfinite(D).all()
+    h.free()
