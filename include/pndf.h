@@ -392,12 +392,22 @@ typedef struct pndf_server_config {
     int32_t warps_per_cta;  /* 0 = 8                                                  */
     int32_t ctas_per_sm;    /* 0 = as many as fit                                     */
     int32_t slots;          /* table slots, 2..8 (0 = 4): steps that can be queued     */
+    int32_t kernel;         /* footprint kernel (pndf_kernel) of every query served   */
+    float tau;              /* > 0: the cluster cut of Sec. 4.3 (Gaussian kernel only;
+                               every map built with clusters = 1)                     */
+    float jac_eps;          /* > 0: the Eq. 6 clamp (Gaussian kernel, tau = 0)         */
+    int32_t reserved;       /* 0                                                      */
 } pndf_server_config;
 
 /* Create a server over nmaps (1..8) hierarchies on the current device; maps
- * must outlive the server.  Allocates its tables (device and pinned host) and
- * captures the step graphs.  Errors: INVALID_ARG (formats differ, bad counts),
- * OOM, CUDA. */
+ * must outlive the server.  Every query it serves is evaluated as
+ * pndf_eval_batch_ex evaluates it with the same kernel, tau and jac_eps (the
+ * variant is fixed per server: the step graphs capture its kernel).
+ * Allocates its tables (device and pinned host) and captures the step graphs.
+ * Errors: INVALID_ARG (formats differ, bad counts, kernel / tau / jac_eps out
+ * of range), UNSUPPORTED (tau with a map built without clusters, or with the
+ * disk / box kernel or the clamp; the clamp with the disk / box kernel), OOM,
+ * CUDA. */
 pndf_status pndf_server_create(const pndf_hierarchy *const *maps, int32_t nmaps, const pndf_server_config *cfg,
                                pndf_server **out);
 

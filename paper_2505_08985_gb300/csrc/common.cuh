@@ -163,10 +163,17 @@ pndf_status launch_projarea(const pndf_hierarchy *h, const pndf_query *q, const 
                             float *P, cudaStream_t s);
 // Evaluation order of a batch (key + counting sort).
 pndf_status launch_sort(const pndf_hierarchy *h, const pndf_query *q, int64_t nq, uint32_t *order, cudaStream_t s);
-// One serving step over a device segment table (see serve.cu).
-cudaError_t launch_serve(int texel_fmt, int bounds_fmt, const MapDesc *maps, int nmaps, const uint32_t *table,
-                         const pndf_segment *segs, unsigned long long *cursor, int warps, int ctas_per_sm,
-                         cudaStream_t s);
+// What a server evaluates for every query (fixed per server).
+struct ServeVariant {
+    int kernel;     // pndf_kernel
+    float tau;      // > 0: the cluster cut (Gaussian only)
+    float jac_eps;  // > 0: the Eq. 6 clamp (Gaussian only, tau = 0)
+};
+// One serving step over a device segment table (see serve.cu); clusters:
+// per-map cluster descriptors, read only when v.tau > 0.
+cudaError_t launch_serve(int texel_fmt, int bounds_fmt, const ServeVariant &v, const MapDesc *maps,
+                         const ClusterDesc *clusters, int nmaps, const uint32_t *table, const pndf_segment *segs,
+                         unsigned long long *cursor, int warps, int ctas_per_sm, cudaStream_t s);
 // Allocation-free evaluation with the sort scratch in a fixed device array.
 pndf_status launch_eval_noalloc(const pndf_hierarchy *h, const pndf_query *q, int64_t nq, float *D, uint32_t *flags,
                                 cudaStream_t s);

@@ -1297,12 +1297,15 @@ pndf_status launch_sort(const pndf_hierarchy *h, const pndf_query *q, int64_t nq
 
 namespace {
 
-__constant__ ClusterDesc kNoClusters;  // unused by the exact serving path
+__constant__ ClusterDesc kNoClusters;  // never read: the serving variants without the cut
 
-template <int BFMT, int TFMT>
+// CLUSTER / KERN: the server's evaluation variant (the cut, the footprint
+// kernel or the clamp), compiled in as for traverse_kernel.
+template <int BFMT, int TFMT, bool CLUSTER, int KERN>
 __global__ void __launch_bounds__(256, PNDF_TRAVERSE_MIN_CTAS)
-    serve_kernel(const MapDesc *__restrict__ maps, int nmaps, const uint32_t *__restrict__ table,
-                 const pndf_segment *__restrict__ segs, unsigned long long *__restrict__ cursor)
+    serve_kernel(const MapDesc *__restrict__ maps, const ClusterDesc *__restrict__ clusters, int nmaps,
+                 const uint32_t *__restrict__ table, const pndf_segment *__restrict__ segs,
+                 unsigned long long *__restrict__ cursor, float tau, float jac_eps)
 {
     extern __shared__ uint32_t smem[];
     __shared__ MapDesc smaps[kServeMaxMaps];
@@ -1340,8 +1343,9 @@ __global__ void __launch_bounds__(256, PNDF_TRAVERSE_MIN_CTAS)
         const pndf_query rec = sg.q[qi];
         float Dv;
         uint32_t fv;
-        eval_one<BFMT, TFMT, false, false, false, PNDF_KERNEL_GAUSS>(smaps[sg.map], kNoClusters, 0.f, 0.f, rec, lane,
-                                                                     stk, lq, ring, hits, Dv, fv, nullptr);
+        eval_one<BFMT, TFMT, false, false, CLUSTER, KERN>(smaps[sg.map], CLUSTER ? clusters[sg.map] : kNoClusters,
+                                                           tau, jac_eps, rec, lane, stk, lq, ring, hits, Dv, fv,
+                                                           nullptr);
         if (lane == 0) {
             sg.D[qi] = Dv;
             if (sg.flags) sg.flags[qi] = fv;
@@ -1349,11 +1353,12 @@ __global__ void __launch_bounds__(256, PNDF_TRAVERSE_MIN_CTAS)
     }
 }
 
-template <int BFMT, int TFMT>
-cudaError_t launch_serve_t(const MapDesc *maps, int nmaps, const uint32_t *table, const pndf_segment *segs,
-                           unsigned long long *cursor, int warps, int ctas_per_sm, cudaStream_t s)
+template <int BFMT, int TFMT, bool CLUSTER, int KERN>
+cudaError_t launch_serve_t(const ServeVariant &v, const MapDesc *maps, const ClusterDesc *clusters, int nmaps,
+                           const uint32_t *table, const pndf_segment *segs, unsigned long long *cursor, int warps,
+                           int ctas_per_sm, cudaStream_t s)
 {
-    auto kern = serve_kernel<BFMT, TFMT>;
+    auto kern = serve_kernel<BFMT, TFMT, CLUSTER, KERN>;
     int threads = warps * 32;
     size_t smem = size_t(warps) * kWarpSmemWords * sizeof(uint32_t);
     int dev = 0, sms = 0, occ = 0;
@@ -1363,25 +1368,43 @@ cudaError_t launch_serve_t(const MapDesc *maps, int nmaps, const uint32_t *table
     if (e != cudaSuccess) return e;
     if (occ < 1) occ = 1;
     if (ctas_per_sm > 0 && ctas_per_sm < occ) occ = ctas_per_sm;
-    kern<<<unsigned(sms * occ), threads, smem, s>>>(maps, nmaps, table, segs, cursor);
+    kern<<<unsigned(sms * occ), threads, smem, s>>>(maps, clusters, nmaps, table, segs, cursor, v.tau, v.jac_eps);
     return cudaGetLastError();
+}
+
+// The variant's instantiation: the cut (Gaussian), the plain Gaussian, disk,
+// box, or the Gaussian with the Eq. 6 clamp (the server validated the mix).
+template <int BFMT, int TFMT>
+cudaError_t launch_serve_v(const ServeVariant &v, const MapDesc *maps, const ClusterDesc *clusters, int nmaps,
+                           const uint32_t *table, const pndf_segment *segs, unsigned long long *cursor, int warps,
+                           int ctas_per_sm, cudaStream_t s)
+{
+#define PNDF_SERVE(C, K) launch_serve_t<BFMT, TFMT, C, K>(v, maps, clusters, nmaps, table, segs, cursor, warps, ctas_per_sm, s)
+    if (v.tau > 0.f) return PNDF_SERVE(true, PNDF_KERNEL_GAUSS);
+    if (v.jac_eps > 0.f) return PNDF_SERVE(false, kKernGaussClamp);
+    if (v.kernel == PNDF_KERNEL_DISK) return PNDF_SERVE(false, PNDF_KERNEL_DISK);
+    if (v.kernel == PNDF_KERNEL_BOX) return PNDF_SERVE(false, PNDF_KERNEL_BOX);
+    return PNDF_SERVE(false, PNDF_KERNEL_GAUSS);
+#undef PNDF_SERVE
 }
 
 }  // namespace
 
-cudaError_t launch_serve(int texel_fmt, int bounds_fmt, const MapDesc *maps, int nmaps, const uint32_t *table,
-                         const pndf_segment *segs, unsigned long long *cursor, int warps, int ctas_per_sm,
-                         cudaStream_t s)
+cudaError_t launch_serve(int texel_fmt, int bounds_fmt, const ServeVariant &v, const MapDesc *maps,
+                         const ClusterDesc *clusters, int nmaps, const uint32_t *table, const pndf_segment *segs,
+                         unsigned long long *cursor, int warps, int ctas_per_sm, cudaStream_t s)
 {
     if (bounds_fmt == PNDF_BOUNDS_F32)
         return texel_fmt == PNDF_TEXEL_F32X2
-                   ? launch_serve_t<PNDF_BOUNDS_F32, PNDF_TEXEL_F32X2>(maps, nmaps, table, segs, cursor, warps, ctas_per_sm, s)
-                   : launch_serve_t<PNDF_BOUNDS_F32, PNDF_TEXEL_F16X2>(maps, nmaps, table, segs, cursor, warps, ctas_per_sm, s);
+                   ? launch_serve_v<PNDF_BOUNDS_F32, PNDF_TEXEL_F32X2>(v, maps, clusters, nmaps, table, segs, cursor,
+                                                                      warps, ctas_per_sm, s)
+                   : launch_serve_v<PNDF_BOUNDS_F32, PNDF_TEXEL_F16X2>(v, maps, clusters, nmaps, table, segs, cursor,
+                                                                      warps, ctas_per_sm, s);
     return texel_fmt == PNDF_TEXEL_F32X2
-               ? launch_serve_t<PNDF_BOUNDS_F16_OUTWARD, PNDF_TEXEL_F32X2>(maps, nmaps, table, segs, cursor, warps,
-                                                                          ctas_per_sm, s)
-               : launch_serve_t<PNDF_BOUNDS_F16_OUTWARD, PNDF_TEXEL_F16X2>(maps, nmaps, table, segs, cursor, warps,
-                                                                          ctas_per_sm, s);
+               ? launch_serve_v<PNDF_BOUNDS_F16_OUTWARD, PNDF_TEXEL_F32X2>(v, maps, clusters, nmaps, table, segs,
+                                                                          cursor, warps, ctas_per_sm, s)
+               : launch_serve_v<PNDF_BOUNDS_F16_OUTWARD, PNDF_TEXEL_F16X2>(v, maps, clusters, nmaps, table, segs,
+                                                                          cursor, warps, ctas_per_sm, s);
 }
 
 // ---------------------------------------------------------------------------

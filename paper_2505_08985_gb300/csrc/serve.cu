@@ -6,6 +6,7 @@
 // CUDA graph (copy, cursor reset, kernel), captured once per table slot.
 // Slots rotate: writing a slot's host buffer only waits for the step that last
 // used that slot, so several steps can be queued while earlier ones run.
+#include <math.h>
 #include <string.h>
 
 #include <new>
@@ -35,7 +36,10 @@ struct pndf_server {
     int nmaps = 0;
     int texel_fmt = 0, bounds_fmt = 0;
     int max_segs = 0, warps = 8, ctas = 0;
+    int kernel = PNDF_KERNEL_GAUSS;
+    float tau = 0.f, jac_eps = 0.f;
     MapDesc *maps_dev = nullptr;
+    ClusterDesc *clusters_dev = nullptr;  // per map, read only with tau > 0
     cudaStream_t cap = nullptr;
     static constexpr int kMaxSlots = 8;
     Slot slot[kMaxSlots];
@@ -57,6 +61,7 @@ void release(pndf_server *s)
         if (sl.host) cudaFreeHost(sl.host);
     }
     if (s->maps_dev) cudaFree(s->maps_dev);
+    if (s->clusters_dev) cudaFree(s->clusters_dev);
     if (s->cap) cudaStreamDestroy(s->cap);
     delete s;
 }
@@ -72,7 +77,9 @@ cudaError_t capture_slot(pndf_server *s, Slot &sl)
     if (e != cudaSuccess) return e;
     cudaMemcpyAsync(sl.dev, sl.host, tb, cudaMemcpyHostToDevice, s->cap);
     cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), s->cap);
-    launch_serve(s->texel_fmt, s->bounds_fmt, s->maps_dev, s->nmaps, table, segs, cursor, s->warps, s->ctas, s->cap);
+    const ServeVariant v{s->kernel, s->tau, s->jac_eps};
+    launch_serve(s->texel_fmt, s->bounds_fmt, v, s->maps_dev, s->clusters_dev, s->nmaps, table, segs, cursor,
+                 s->warps, s->ctas, s->cap);
     cudaGraph_t g = nullptr;
     cudaError_t ec = cudaStreamEndCapture(s->cap, &g);
     if (ec != cudaSuccess) return ec;
@@ -98,17 +105,30 @@ pndf_status pndf_server_create(const pndf_hierarchy *const *maps, int32_t nmaps,
         if (maps[i]->d.texel_fmt != maps[0]->d.texel_fmt || maps[i]->d.bounds_fmt != maps[0]->d.bounds_fmt)
             return PNDF_ERR_INVALID_ARG;
     }
-    pndf_server_config c{1024, 8, 0, 4};
+    pndf_server_config c{1024, 8, 0, 4, PNDF_KERNEL_GAUSS, 0.f, 0.f, 0};
     if (cfg) {
         if (cfg->max_segments < 0 || cfg->warps_per_cta < 0 || cfg->warps_per_cta > 8 || cfg->ctas_per_sm < 0 ||
-            cfg->slots < 0 || cfg->slots == 1 || cfg->slots > pndf_server::kMaxSlots)
+            cfg->slots < 0 || cfg->slots == 1 || cfg->slots > pndf_server::kMaxSlots || cfg->reserved != 0)
             return PNDF_ERR_INVALID_ARG;
+        if (cfg->kernel != PNDF_KERNEL_GAUSS && cfg->kernel != PNDF_KERNEL_DISK && cfg->kernel != PNDF_KERNEL_BOX)
+            return PNDF_ERR_INVALID_ARG;
+        if (!(cfg->tau >= 0.f) || !isfinite(cfg->tau)) return PNDF_ERR_INVALID_ARG;
+        if (!(cfg->jac_eps == 0.f || (cfg->jac_eps >= 1e-9f && cfg->jac_eps <= 1e-2f))) return PNDF_ERR_INVALID_ARG;
         if (cfg->max_segments) c.max_segments = cfg->max_segments;
         if (cfg->warps_per_cta) c.warps_per_cta = cfg->warps_per_cta;
         if (cfg->slots) c.slots = cfg->slots;
         c.ctas_per_sm = cfg->ctas_per_sm;
+        c.kernel = cfg->kernel;
+        c.tau = cfg->tau;
+        c.jac_eps = cfg->jac_eps;
     }
     if (c.max_segments > (1 << 16)) return PNDF_ERR_INVALID_ARG;
+    if (c.tau > 0.f) {
+        if (c.kernel != PNDF_KERNEL_GAUSS || c.jac_eps > 0.f) return PNDF_ERR_UNSUPPORTED;
+        for (int i = 0; i < nmaps; ++i)
+            if (!maps[i]->clusters) return PNDF_ERR_UNSUPPORTED;
+    }
+    if (c.jac_eps > 0.f && c.kernel != PNDF_KERNEL_GAUSS) return PNDF_ERR_UNSUPPORTED;
     pndf_server *s = new (std::nothrow) pndf_server();
     if (!s) return PNDF_ERR_OOM;
     s->device = dev;
@@ -119,11 +139,21 @@ pndf_status pndf_server_create(const pndf_hierarchy *const *maps, int32_t nmaps,
     s->warps = c.warps_per_cta;
     s->ctas = c.ctas_per_sm;
     s->nslots = c.slots;
+    s->kernel = c.kernel;
+    s->tau = c.tau;
+    s->jac_eps = c.jac_eps;
     MapDesc host_maps[kServeMaxMaps];
-    for (int i = 0; i < nmaps; ++i) host_maps[i] = maps[i]->d;
+    ClusterDesc host_clusters[kServeMaxMaps];
+    for (int i = 0; i < nmaps; ++i) {
+        host_maps[i] = maps[i]->d;
+        host_clusters[i] = maps[i]->c;
+    }
     const size_t tb = table_bytes(s->max_segs);
     bool ok = cudaMalloc(&s->maps_dev, sizeof(MapDesc) * nmaps) == cudaSuccess &&
               cudaMemcpy(s->maps_dev, host_maps, sizeof(MapDesc) * nmaps, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMalloc(&s->clusters_dev, sizeof(ClusterDesc) * nmaps) == cudaSuccess &&
+              cudaMemcpy(s->clusters_dev, host_clusters, sizeof(ClusterDesc) * nmaps, cudaMemcpyHostToDevice) ==
+                  cudaSuccess &&
               cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) == cudaSuccess;
     for (int k = 0; ok && k < s->nslots; ++k) {
         Slot &sl = s->slot[k];

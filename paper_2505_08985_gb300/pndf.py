@@ -67,7 +67,8 @@ class _Segment(ctypes.Structure):
 
 class _ServerConfig(ctypes.Structure):
     _fields_ = [("max_segments", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32), ("slots", ctypes.c_int32)]
+                ("ctas_per_sm", ctypes.c_int32), ("slots", ctypes.c_int32), ("kernel", ctypes.c_int32),
+                ("tau", ctypes.c_float), ("jac_eps", ctypes.c_float), ("reserved", ctypes.c_int32)]
 
 
 def _load() -> ctypes.CDLL:
@@ -485,9 +486,13 @@ class Server:
 
 
 def pndf_server_create(maps: list, max_segments: int = 1024, warps_per_cta: int = 0, ctas_per_sm: int = 0,
-                       slots: int = 0) -> Server:
+                       slots: int = 0, kernel: int = PNDF_KERNEL_GAUSS, tau: float = 0.0,
+                       jac_eps: float = 0.0) -> Server:
+    """kernel / tau / jac_eps: what every served query evaluates, as in
+    pndf_eval_batch_ex (tau > 0 needs maps built with clusters=True)."""
     arr = (ctypes.c_void_p * len(maps))(*[m.handle for m in maps])
-    cfg = _ServerConfig(int(max_segments), int(warps_per_cta), int(ctas_per_sm), int(slots))
+    cfg = _ServerConfig(int(max_segments), int(warps_per_cta), int(ctas_per_sm), int(slots), int(kernel),
+                        float(tau), float(jac_eps), 0)
     h = ctypes.c_void_p()
     with torch.cuda.device(maps[0].device):
         _check("pndf_server_create", LIB.pndf_server_create(arr, len(maps), ctypes.byref(cfg), ctypes.byref(h)))

@@ -77,14 +77,18 @@ class ContinuousBatcher:
     """Continuous batching over `maps` (same texel and bounds formats)."""
 
     def __init__(self, maps, step_queries: int = 1 << 20, memory_budget: int = 2 << 30, max_segments: int = 1024,
-                 warps_per_cta: int = 0, ctas_per_sm: int = 0, slots: int = 4, sort: bool = True):
+                 warps_per_cta: int = 0, ctas_per_sm: int = 0, slots: int = 4, sort: bool = True,
+                 kernel: int = pndf.PNDF_KERNEL_GAUSS, tau: float = 0.0, jac_eps: float = 0.0):
+        """kernel / tau / jac_eps: what every query evaluates (the footprint
+        kernel, the cluster cut, the Eq. 6 clamp), as in pndf_eval_batch_ex."""
         self.maps = list(maps)
         self.sort = bool(sort)
         self.device = self.maps[0].device
         self.step_queries = int(step_queries)
         self.budget = int(memory_budget)
         self.server = pndf.pndf_server_create(self.maps, max_segments=max_segments, warps_per_cta=warps_per_cta,
-                                              ctas_per_sm=ctas_per_sm, slots=slots)
+                                              ctas_per_sm=ctas_per_sm, slots=slots, kernel=kernel, tau=tau,
+                                              jac_eps=jac_eps)
         self.max_inflight = max(1, slots - 1)
         self.max_segments = max_segments
         self.copy_stream = torch.cuda.Stream(self.device)

@@ -96,6 +96,55 @@ def test_served_matches_oracle(P, maps_and_requests):
         h.free()
 
 
+@pytest.mark.parametrize("variant", ["tau", "disk", "box", "clamp"])
+def test_served_variant_equals_alone(P, maps_and_requests, variant):
+    """A server fixed to the cluster cut, the disk or box kernel or the Eq. 6
+    clamp gives, for every request, exactly what pndf_eval_batch_ex gives on
+    its map with the same setting."""
+    from paper_2505_08985_gb300 import serve
+    sts, _ = maps_and_requests
+    kw = {"tau": {"tau": 1e-3}, "disk": {"kernel": P.PNDF_KERNEL_DISK}, "box": {"kernel": P.PNDF_KERNEL_BOX},
+          "clamp": {"jac_eps": 1e-6}}[variant]
+    hs = [P.pndf_build_hierarchy(st, bounds_fmt=P.PNDF_BOUNDS_F16_OUTWARD, clusters=variant == "tau") for st in sts]
+    # footprints of 1-24 texels, so that the cut applies (camera footprints are mostly sub-texel)
+    rng = np.random.default_rng(11)
+    mix = synth.QueryMix(sigma=(1.0, 24.0), aspect=(1.0, 3.0), frac_near=0.8)
+    sub = []
+    for k in range(16):
+        m = int(rng.integers(0, 3))
+        n = int(np.exp(rng.uniform(np.log(100), np.log(6000))))
+        sub.append(serve.Request(rid=k, map=m, queries=synth.make_queries(sts[m], n, mix, 500 + k), arrival=0.0))
+    alone = [P.pndf_eval_batch_ex(hs[r.map], r.queries, **kw).cpu() for r in sub]
+    b = serve.ContinuousBatcher(hs, step_queries=20000, max_segments=64, **kw)
+    b.run(sub, realtime=False)
+    b.close()
+    for r, a in zip(sub, alone):
+        assert torch.equal(r.D.cpu(), a), (variant, r.rid)
+    if variant != "clamp":  # (the clamp only moves hits in triangles of |cross| < 1e-6, rare here)
+        exact = [P.pndf_eval_batch(hs[r.map], r.queries).cpu() for r in sub]
+        assert any(not torch.equal(a, e) for a, e in zip(alone, exact))  # the variant changes the densities
+    for h in hs:
+        h.free()
+
+
+def test_server_variant_validation(P):
+    st = synth.bumps_map(n=64, n_bumps=4, seed=1).to(DEV)
+    plain = P.pndf_build_hierarchy(st, bounds_fmt=1)
+    clustered = P.pndf_build_hierarchy(st, bounds_fmt=1, clusters=True)
+    for kw, code in (({"tau": 1e-3}, 6), ({"tau": 1e-3, "kernel": P.PNDF_KERNEL_DISK}, 6), ({"kernel": 7}, 1),
+                     ({"tau": -1.0}, 1), ({"jac_eps": 1e-12}, 1), ({"jac_eps": 1e-6, "kernel": P.PNDF_KERNEL_BOX}, 6)):
+        maps = [clustered] if "kernel" in kw and "tau" in kw else [plain]
+        with pytest.raises(P.PndfError) as ei:
+            P.pndf_server_create(maps, **kw)
+        assert ei.value.code == code, kw
+    with pytest.raises(P.PndfError) as ei:  # the clamp and the cut together
+        P.pndf_server_create([clustered], tau=1e-3, jac_eps=1e-6)
+    assert ei.value.code == 6
+    P.pndf_server_create([clustered], tau=1e-3).destroy()
+    plain.free()
+    clustered.free()
+
+
 def test_server_rejects_mixed_formats(P):
     a = P.pndf_build_hierarchy(synth.bumps_map(n=64, n_bumps=4, seed=1).to(DEV), bounds_fmt=0)
     b = P.pndf_build_hierarchy(synth.bumps_map(n=64, n_bumps=4, seed=2).to(DEV), bounds_fmt=1)
