@@ -1,0 +1,86 @@
+"""Host logic of the continuous batcher (CPU only): latency percentiles and
+summaries, Poisson arrivals, and how a step is formed from the admitted
+requests (large requests span steps, small ones share one, FIFO, at most
+`step_queries` queries and `max_segments` slices per step)."""
+
+import math
+from collections import deque
+
+import numpy as np
+import pytest
+import torch
+
+serve = pytest.importorskip("paper_2505_08985_gb300.serve")
+
+
+def test_percentile_matches_linear_interpolation():
+    rng = np.random.default_rng(1)
+    for n in (1, 2, 7, 100):
+        xs = rng.exponential(size=n).tolist()
+        for p in (0.0, 0.5, 0.9, 0.99, 1.0):
+            assert serve.percentile(xs, p) == pytest.approx(float(np.percentile(xs, 100 * p)), rel=1e-12)
+    assert math.isnan(serve.percentile([], 0.5))
+
+
+def test_summarize():
+    reqs = []
+    for k, (n, lat) in enumerate(((10, 0.001), (30, 0.003), (60, 0.002))):
+        r = serve.Request(rid=k, map=0, queries=torch.zeros(n, 8), arrival=0.0)
+        r.latency = lat
+        reqs.append(r)
+    s = serve.summarize(reqs, 1.0, 3.0)
+    assert s["requests"] == 3 and s["queries"] == 100
+    assert s["p50_ms"] == pytest.approx(2.0) and s["mean_ms"] == pytest.approx(2.0)
+    assert s["queries_per_s"] == pytest.approx(50.0) and s["span_s"] == pytest.approx(2.0)
+
+
+def test_poisson_arrivals():
+    a = serve.poisson_arrivals(20000, rate=500.0, seed=3)
+    assert a == serve.poisson_arrivals(20000, rate=500.0, seed=3)
+    gaps = np.diff([0.0] + a)
+    assert (gaps > 0).all()
+    assert gaps.mean() == pytest.approx(1 / 500.0, rel=0.03)
+    assert gaps.std() == pytest.approx(1 / 500.0, rel=0.05)  # exponential: std = mean
+
+
+class _Stream:
+    def __init__(self):
+        self.waits = 0
+
+    def wait_event(self, ev):
+        self.waits += 1
+
+
+def _batcher(step_queries, max_segments):
+    b = serve.ContinuousBatcher.__new__(serve.ContinuousBatcher)  # host logic only: no server
+    b.step_queries, b.max_segments, b.step_stream = step_queries, max_segments, _Stream()
+    return b
+
+
+def test_step_formation_slices_fifo():
+    sizes = [50, 1000, 30, 30, 400]
+    reqs = deque()
+    for k, n in enumerate(sizes):
+        r = serve.Request(rid=k, map=k % 2, queries=torch.zeros(n, 8), arrival=0.0)
+        r.next, r.waited = 0, False
+        reqs.append(r)
+    b = _batcher(step_queries=256, max_segments=3)
+    covered = {k: [] for k in range(len(sizes))}
+    shape = []
+    while reqs:
+        segs, fin = b._form_step(reqs)
+        shape.append((sum(s[6] for s in segs), len(segs)))
+        assert 0 < shape[-1][0] <= 256 and shape[-1][1] <= 3
+        for m, q, order, D, flags, first, count in segs:
+            rid = next(r.rid for r in [*fin, *reqs] if r.queries is q)
+            covered[rid].append((first, count))
+    for k, n in enumerate(sizes):  # every query of every request exactly once, in order
+        pos = 0
+        for first, count in covered[k]:
+            assert first == pos and count > 0
+            pos += count
+        assert pos == n
+    assert b.step_stream.waits == len(sizes)  # each request's readiness awaited once
+    # a step stops only when full or out of slices (or out of requests)
+    assert all(total == 256 or nsegs == 3 for total, nsegs in shape[:-1])
+    assert shape == [(256, 2), (256, 1), (256, 1), (256, 1), (86, 3), (256, 1), (144, 1)]
