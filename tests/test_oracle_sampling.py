@@ -13,7 +13,7 @@ import math
 import numpy as np
 import pytest
 
-from test_oracle_pins import gauss, interp_normal
+from test_oracle_pins import gauss
 
 EPS = 1e-6
 N0 = np.array([0.125, -0.0625])
