@@ -191,11 +191,40 @@ CENSUS_FILE = os.path.join(ROOT, "profiles", "kernels_census_flake4096_mixed4096
 CENSUS_SOURCES = ("build.cu", "cluster.cu", "eval.cu", "projarea.cu", "sample.cu", "common.cuh", "ggx.cuh")
 
 
+def code_text(src: str) -> str:
+    """C/C++/CUDA source with its comments removed and each run of whitespace
+    made one space (comment markers inside string and character literals are
+    not comments), so that a source hash follows the code and not its
+    commentary or layout."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def sources_hash(files) -> str:
+    """Hash of the code (comments and layout aside) of the named kernel sources."""
     h = hashlib.sha256()
     for f in files:
-        with open(os.path.join(ROOT, "paper_2505_08985_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2505_08985_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(code_text(fh.read()).encode())
+        h.update(b"\0")
     return h.hexdigest()[:16]
 
 

@@ -61,3 +61,17 @@ def test_census_needs_matching_sources(bench, tmp_path, monkeypatch):
     p.write_text(f"sources_sha256_16: {bench.sources_hash(bench.CENSUS_SOURCES)}\n" + line)
     c = bench.committed_census()
     assert c["pyramid_build"]["dram_bytes"] == 24.0 and c["pyramid_build"]["warp_inst"] == 0.5
+
+
+def test_source_hash_follows_code_not_comments(bench, tmp_path, monkeypatch):
+    t = bench.code_text('int a = 1; // note\n/* block\n note */ const char *s = "x // y /* z */";\nchar q = \'"\';  b  =\n c;')
+    assert t == 'int a = 1; const char *s = "x // y /* z */"; char q = \'"\'; b = c;'
+    d = tmp_path / "paper_2505_08985_gb300" / "csrc"
+    d.mkdir(parents=True)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    (d / "k.cu").write_text("// kernel (Sec. 1)\n__global__ void k(float *x) { x[0] = 1.0f; }\n")
+    h0 = bench.sources_hash(["k.cu"])
+    (d / "k.cu").write_text("// kernel (Sec. 2), reworded\n__global__  void k(float *x)\n{\n    x[0] = 1.0f;  /* one */\n}\n")
+    assert bench.sources_hash(["k.cu"]) == h0
+    (d / "k.cu").write_text("// kernel (Sec. 2)\n__global__ void k(float *x) { x[0] = 2.0f; }\n")
+    assert bench.sources_hash(["k.cu"]) != h0
