@@ -628,7 +628,7 @@ def run_serving(args, dev):
 
 
 # ---------------------------------------------------------------------------
-# Cluster cut (Sec. 4.3, Eq. 7-8): the approximate variant on the same workload
+# Cluster cut (Sec. 4.2, Eq. 7-8): the approximate variant on the same workload
 # ---------------------------------------------------------------------------
 
 def run_cluster_cut(args, world, st, q, D_exact, exact_kernel_ms):

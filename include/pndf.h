@@ -67,7 +67,7 @@ typedef struct pndf_build_params {
     int32_t texel_fmt;   /* pndf_texel_fmt                                        */
     int32_t bounds_fmt;  /* pndf_bounds_fmt                                       */
     int32_t leaf_level;  /* 0 = default (2): stored bottom level, 2^l x 2^l quads */
-    int32_t clusters;    /* 1 = also build the cluster hierarchy (Sec. 4.3, Eq.   */
+    int32_t clusters;    /* 1 = also build the cluster hierarchy (Sec. 4.2, Eq.   */
                          /* 7-8) used by pndf_eval_config.tau; 0 = none           */
 } pndf_build_params;
 
@@ -129,7 +129,7 @@ typedef struct pndf_eval_config {
     int32_t sort;           /* query order before traversal (pndf_sort_mode)          */
     int32_t warps_per_cta;  /* 0 = library default                                   */
     int32_t ctas_per_sm;    /* 0 = as many as fit                                    */
-    float tau;              /* cluster cut (Sec. 4.3): a node whose residual e <=      */
+    float tau;              /* cluster cut (Sec. 4.2): a node whose residual e <=      */
                             /* r_x r_y tau is evaluated as its two cluster triangles;  */
                             /* 0 = exact (no cluster).  Needs a hierarchy built with   */
                             /* clusters = 1, else UNSUPPORTED.  Hierarchy mode only.   */
@@ -161,7 +161,7 @@ typedef struct pndf_eval_config {
  *     host link, with no staging copy).  Other pointers (pageable host
  *     memory, another device's memory) are rejected with INVALID_ARG before
  *     any work is queued.
- * With params->clusters = 1 the cluster hierarchy of Sec. 4.3 is built too:
+ * With params->clusters = 1 the cluster hierarchy of Sec. 4.2 is built too:
  * every node of level >= 2 whose quads all lie inside the map gets the four
  * corner normals of a two-triangle cluster (split like a quad) minimising
  * the Jacobian-weighted L2 error of Eq. 7 (|det J| clamped at 1e-6 as in
@@ -216,7 +216,7 @@ pndf_status pndf_sample_normals(const pndf_hierarchy *h, const pndf_query *q_dev
 
 /*
  * GGX projected-area fit per mip node (Eq. 12) and the shadow-masking term
- * (Sec. 4.4).  P'(w) = (w_z + sqrt(w_z^2 + w_xy^T Omega w_xy)) / 2 (Eq. 12
+ * (Sec. 4.3).  P'(w) = (w_z + sqrt(w_z^2 + w_xy^T Omega w_xy)) / 2 (Eq. 12
  * with its parentheses restored: the GGX projected area), so Lambda'(w) =
  * P'(w) / w_z - 1 is the GGX Smith Lambda of Omega.  Each node of levels 2..L
  * whose quads all lie in the map is box-filtered over its own quads (for
@@ -251,7 +251,7 @@ pndf_status pndf_shadow_masking(const pndf_ggx *g, const pndf_query *q_dev, cons
 pndf_status pndf_ggx_level(const pndf_ggx *g, int32_t level, float *omega_out_dev, void *stream);
 
 /* Copy out level l (2 <= l <= L, 2^L >= N-1) of the cluster hierarchy
- * (Sec. 4.3, Eq. 7-8) for inspection, nodes in row-major order (J, I),
+ * (Sec. 4.2, Eq. 7-8) for inspection, nodes in row-major order (J, I),
  * S = 2^(L-l) per side:
  *   records_dev: device, S*S*8 floats per node (c00.s, c00.t, d10.s, d10.t,
  *                d01.s, d01.t, d11.s, d11.t), corner normals c = c00 + d;
@@ -393,7 +393,7 @@ typedef struct pndf_server_config {
     int32_t ctas_per_sm;    /* 0 = as many as fit                                     */
     int32_t slots;          /* table slots, 2..8 (0 = 4): steps that can be queued     */
     int32_t kernel;         /* footprint kernel (pndf_kernel) of every query served   */
-    float tau;              /* > 0: the cluster cut of Sec. 4.3 (Gaussian kernel only;
+    float tau;              /* > 0: the cluster cut of Sec. 4.2 (Gaussian kernel only;
                                every map built with clusters = 1)                     */
     float jac_eps;          /* > 0: the Eq. 6 clamp (Gaussian kernel, tau = 0)         */
     int32_t reserved;       /* 0                                                      */

@@ -16,7 +16,7 @@ pndf_cluster(st, queries, tau, fits=None) -> as pndf, with the cluster cut e <= 
 projarea(st, queries, w)   -> P (float64)
 ggx_fits(st)               -> Omega per mip node (Eq. 12 fit; box filter per node)
 ggx_lambda(Omega, N, q, w) -> GGX Smith Lambda'(w) at each footprint
-shadow_masking(Omega, N, q, wi, wo) -> height-correlated G (Sec. 4.4)
+shadow_masking(Omega, N, q, wi, wo) -> height-correlated G (Sec. 4.3)
 tri_integral(n0, n1, n2, w) -> integral of max(m~.w, 0)/m~_z over one normal triangle
 
 ``st`` is an (N, N, 2) array (texel (i, j) at ``st[j, i]``); ``queries`` an

@@ -530,7 +530,7 @@ void oracle_projarea(const double *st, int N, const double *q, const double *w,
 }
 
 /* ------------------------------------------------------------------------- */
-/* Cluster hierarchy and tau cut (Sec. 4.3 on mesh clustering, Eq. 7-8,     */
+/* Cluster hierarchy and tau cut (Sec. 4.2 on mesh clustering, Eq. 7-8,     */
 /* App. A).                                                                  */
 /* ------------------------------------------------------------------------- */
 /*
@@ -1000,7 +1000,7 @@ void oracle_sample(const double *st, int N, const double *q, const double *U, in
 }
 
 /* ------------------------------------------------------------------------- */
-/* GGX projected-area fit per mip node (Eq. 12) and shadow-masking (Sec. 4.4) */
+/* GGX projected-area fit per mip node (Eq. 12) and shadow-masking (Sec. 4.3) */
 /* ------------------------------------------------------------------------- */
 /*
  * Readings.  Eq. 12 with its parentheses restored (the printed form drops

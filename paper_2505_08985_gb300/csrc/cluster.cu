@@ -1,4 +1,4 @@
-// Cluster hierarchy build (Sec. 4.3 on mesh clustering, Eq. 7-8, App. A).
+// Cluster hierarchy build (Sec. 4.2 on mesh clustering, Eq. 7-8, App. A).
 //
 // Each node (level l >= 2, 2^l x 2^l quads, entirely inside the map) gets the
 // four corner normals c00, c10, c01, c11 of a two-triangle cluster split like

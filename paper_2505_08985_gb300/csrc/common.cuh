@@ -32,7 +32,7 @@ struct MapDesc {
                                  // (2^(L-l))^2 nodes each, Morton order
 };
 
-// Cluster hierarchy (Sec. 4.3, Eq. 7-8, App. A), levels kLeafLevel..L in the
+// Cluster hierarchy (Sec. 4.2, Eq. 7-8, App. A), levels kLeafLevel..L in the
 // same Morton order as the boxes.  Per node two float4 records,
 // (c00.s, c00.t, d10.s, d10.t) and (d01.s, d01.t, d11.s, d11.t) with the
 // corner normals c10 = c00 + d10 etc. kept as differences (a flat cluster's

@@ -586,7 +586,7 @@ __device__ __forceinline__ void test_quads(const MapDesc &d, const Query &q, Lea
     }
 }
 
-// Cluster triangle test (Sec. 4.3) in vertex-relative form: p = m - A,
+// Cluster triangle test (Sec. 4.2) in vertex-relative form: p = m - A,
 // b = B - A, c = C - A.  Same rule as edge_test (closed bounding box, edge
 // functions sign-consistent with the orientation); the Jacobian of the
 // cluster map is cross / 4^l, applied when the hit is weighed.  Triangles
@@ -839,7 +839,7 @@ __device__ void eval_one(const MapDesc &d, const ClusterDesc &cd, float tau, flo
             bool inside = pass && node_inside(q, e, a, c);
             bool cut = false;
             if (STATS) acc.nodes += valid ? 1u : 0u;
-            if (CLUSTER && pass) {  // the cut of Sec. 4.3: e <= r_x r_y tau
+            if (CLUSTER && pass) {  // the cut of Sec. 4.2: e <= r_x r_y tau
                 cut = __ldg(cd.ce[e] + morton2(a, c)) <= q.theta;
                 if (STATS) acc.cchecks++;
             }
@@ -919,7 +919,7 @@ __device__ void eval_one(const MapDesc &d, const ClusterDesc &cd, float tau, flo
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
                 pass[r] = pass[r] && stored_box_holds<BFMT, CLAMP>(bx[r], q);
-                if (CLUSTER && pass[r]) {  // the cut of Sec. 4.3: e <= r_x r_y tau
+                if (CLUSTER && pass[r]) {  // the cut of Sec. 4.2: e <= r_x r_y tau
                     cut[r] = ev[r] <= q.theta;
                     if (STATS) acc.cchecks++;
                 }

@@ -1,4 +1,4 @@
-// GGX projected-area fit per mip node (Eq. 12) and shadow-masking (Sec. 4.4):
+// GGX projected-area fit per mip node (Eq. 12) and shadow-masking (Sec. 4.3):
 // the device object and its launchers (projarea.cu).
 #pragma once
 

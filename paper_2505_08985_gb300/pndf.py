@@ -188,7 +188,7 @@ def pndf_build_hierarchy(texels: torch.Tensor, bounds_fmt: int = PNDF_BOUNDS_F32
                          clusters: bool = False) -> Hierarchy:
     """texels: (N, N, 2) float32 or float16 CUDA tensor, or a pinned CPU tensor
     read directly by the build kernel; texel (i, j) at [j, i].
-    clusters: also build the cluster hierarchy (Sec. 4.3, Eq. 7-8) for tau > 0."""
+    clusters: also build the cluster hierarchy (Sec. 4.2, Eq. 7-8) for tau > 0."""
     dev = _texels(texels)
     if texels.dim() != 3 or texels.shape[0] != texels.shape[1]:
         raise ValueError("texels must be (N, N, 2)")
@@ -359,7 +359,7 @@ def pndf_eval_batch_ex(h: Hierarchy, queries: torch.Tensor, out=None, flags=None
                        ev_begin=None, ev_end=None, tau: float = 0.0, kernel: int = PNDF_KERNEL_GAUSS,
                        jac_eps: float = 0.0) -> torch.Tensor:
     """ev_begin / ev_end: optional torch.cuda.Event recorded around the traversal kernel.
-    tau > 0: the cluster cut of Sec. 4.3 (the hierarchy must be built with clusters=True).
+    tau > 0: the cluster cut of Sec. 4.2 (the hierarchy must be built with clusters=True).
     kernel: footprint kernel (PNDF_KERNEL_GAUSS, _DISK, _BOX).
     jac_eps > 0: the Jacobian clamp of Eq. 6 (e.g. 1e-6)."""
     nq = _queries(queries)

@@ -1,4 +1,4 @@
-"""GPU parity of the cluster hierarchy and tau cut (Sec. 4.3, Eq. 7-8) with
+"""GPU parity of the cluster hierarchy and tau cut (Sec. 4.2, Eq. 7-8) with
 the FP64 oracle, through the C ABI.
 
 The fits (corner normals and residuals of every node) are compared node by

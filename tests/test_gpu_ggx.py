@@ -1,5 +1,5 @@
 """GPU parity of the GGX projected-area fit per mip node (Eq. 12) and the
-shadow-masking term (Sec. 4.4) with the FP64 oracle, through the C ABI.
+shadow-masking term (Sec. 4.3) with the FP64 oracle, through the C ABI.
 
 The fitted Omega of every node is compared with the oracle's; Lambda' and G
 at random footprints and directions likewise.  Tolerances: the GPU sums the

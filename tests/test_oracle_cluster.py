@@ -1,4 +1,4 @@
-"""Pins for the oracle's cluster hierarchy (Sec. 4.3 on mesh clustering,
+"""Pins for the oracle's cluster hierarchy (Sec. 4.2 on mesh clustering,
 Eq. 7-8, App. A) and its tau cut.
 
 Expected values come by other routes than the oracle's: exact recovery of
@@ -85,7 +85,7 @@ def dense_fit(st, l, I, J, K):
 
 
 def walk_cut(fits, N, x, y, sxx, syy, tau):
-    """The cut of Sec. 4.3 taken top down from the entry nodes: returns the
+    """The cut of Sec. 4.2 taken top down from the entry nodes: returns the
     cut nodes (l, I, J) and the level-2 nodes evaluated exactly."""
     L = fits.L
     rx, ry = 4 * math.sqrt(sxx), 4 * math.sqrt(syy)

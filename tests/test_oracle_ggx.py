@@ -1,5 +1,5 @@
 """Pins for the GGX projected-area fit per mip node (Eq. 12) and the
-shadow-masking term (Sec. 4.4).
+shadow-masking term (Sec. 4.3).
 
 Independent routes: a fit fed projected areas of a known GGX Omega returns
 it; a flat map has P(w) = w_z and Omega = 0; a node's box-filtered P equals
