@@ -82,3 +82,63 @@ def test_build_params_invalid_n(lib):
     for bad in (P(1, 0, 0, 0, 0), P(16385, 0, 0, 0, 0), P(64, 7, 0, 0, 0), P(64, 0, 9, 0, 0), P(64, 0, 0, 0, 2)):
         assert lib.pndf_build_hierarchy(dummy, ctypes.byref(bad), None, ctypes.byref(out)) == 1
     assert lib.pndf_build_hierarchy(dummy, ctypes.byref(P(64, 0, 0, 3, 0)), None, ctypes.byref(out)) == 6
+
+
+def header_struct_fields(name):
+    """(field name, C type) in declaration order of `typedef struct name {...}` in pndf.h."""
+    src = open(os.path.join(ROOT, "include", "pndf.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (name, name), src, flags=re.S).group(1)
+    fields = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        m = re.match(r"(.*?)([A-Za-z_]\w*)$", decl.replace("\n", " "))
+        ctype, names = m.group(1).strip(), [m.group(2)]
+        if "," in decl:  # float x, y, ...
+            first = re.match(r"([A-Za-z_][\w ]*?)\s+([A-Za-z_]\w*)\s*,", decl)
+            ctype = first.group(1)
+            names = [n.strip() for n in decl[len(first.group(1)):].split(",")]
+        fields += [(n, ctype) for n in names]
+    return fields
+
+
+@pytest.mark.parametrize("cname,pyname", [("pndf_build_params", "_BuildParams"), ("pndf_eval_config", "_EvalConfig"),
+                                          ("pndf_segment", "_Segment"), ("pndf_server_config", "_ServerConfig")])
+def test_binding_structs_match_header(lib, cname, pyname):
+    """The binding's ctypes mirrors of the ABI structs have the header's fields,
+    in order, with matching kinds (32-bit int, float, pointer)."""
+    from paper_2505_08985_gb300 import pndf
+    ours = getattr(pndf, pyname)._fields_
+    theirs = header_struct_fields(cname)
+    assert [n for n, _ in ours] == [n for n, _ in theirs], (cname, ours, theirs)
+    for (n, t), (_, ct) in zip(ours, theirs):
+        if "*" in ct:
+            assert t is ctypes.c_void_p, (cname, n)
+        elif ct == "float":
+            assert t is ctypes.c_float, (cname, n)
+        else:
+            assert t is ctypes.c_int32, (cname, n, ct)
+
+
+def test_query_record_layout():
+    fields = header_struct_fields("pndf_query")
+    assert [n for n, _ in fields] == ["x", "y", "sxx", "sxy", "syy", "ms", "mt", "pad"]
+    assert all(t == "float" for _, t in fields)  # 32 bytes, the (nq, 8) float32 tensor of the binding
+
+
+def test_binding_refuses_pageable_texels(lib):
+    """Texels must be a CUDA tensor or page-locked: a plain CPU tensor is refused
+    before the library is called."""
+    import torch
+    from paper_2505_08985_gb300 import pndf
+    with pytest.raises(ValueError):
+        pndf.pndf_build_hierarchy(torch.zeros(8, 8, 2))
+
+
+def test_stats_names_match_header(lib):
+    from paper_2505_08985_gb300 import pndf
+    fields = header_struct_fields("pndf_query_stats")
+    assert list(pndf.STATS_NAMES) == [n for n, _ in fields] and pndf.STATS_FIELDS == len(fields)
+    assert all(t == "uint32_t" for _, t in fields)
