@@ -6,6 +6,9 @@
  * baseline leg of the benchmark may load this file's library.  It shares no
  * code, header, table or constant generator with the CUDA path.  It is a plain,
  * slow, exhaustive evaluation: no hierarchy, no blocking, no reordering.
+ * Every function is pinned by tests against closed forms, invariants, brute
+ * force or quadrature (tests/test_oracle_*.py), and altered copies of it are
+ * caught (tests/test_oracle_mutants.py): none is parity unpinned.
  *
  * Map layout: st[(j*N + i)*2 + c], texel u = (i, j), c = 0 for s, 1 for t.
  * Query layout: 7 doubles (x, y, sxx, sxy, syy, ms, mt).
