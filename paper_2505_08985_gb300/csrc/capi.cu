@@ -233,7 +233,13 @@ pndf_status pndf_ggx_create(const pndf_hierarchy *h, void *stream, pndf_ggx **ou
 void pndf_ggx_free(pndf_ggx *g)
 {
     if (!g) return;
-    if (g->mem) cudaFree(g->mem);
+    if (g->mem) {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (cur != g->device) cudaSetDevice(g->device);
+        cudaFree(g->mem);
+        if (cur != g->device && cur >= 0) cudaSetDevice(cur);
+    }
     delete g;
 }
 

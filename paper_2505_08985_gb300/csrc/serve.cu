@@ -213,6 +213,15 @@ pndf_status pndf_server_sync(pndf_server *s)
     return PNDF_OK;
 }
 
-void pndf_server_destroy(pndf_server *s) { release(s); }
+void pndf_server_destroy(pndf_server *s)
+{
+    if (!s) return;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    const int dev = s->device;
+    if (cur != dev) cudaSetDevice(dev);  // its memory, streams and graphs belong to its device
+    release(s);
+    if (cur != dev && cur >= 0) cudaSetDevice(cur);
+}
 
 }  // extern "C"
