@@ -21,7 +21,7 @@ cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
 bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 // Keep stream-ordered scratch cached in the device's default pool instead of
-// returning it to the driver at every synchronisation (once per device).
+// releasing it to the operating system at every synchronisation (once per device).
 void keep_pool_memory()
 {
     static std::atomic<uint64_t> done{0};
