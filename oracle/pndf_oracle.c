@@ -384,11 +384,30 @@ static double tri_visible_integral(const double v[3][2], double wx, double wz)
     return sum;
 }
 
+/*
+ * App. B derives the clip ellipse (m_x / w_z)^2 + m_y^2 = 1 and the arc term
+ * from w_x^2 + w_z^2 = 1 after the rotation, i.e. for a unit direction.  A
+ * direction given in single precision is unit only to about 1e-8, and the
+ * line terms (which use w as given) then disagree with the arc terms by that
+ * relative amount, which is large against a triangle whose visible part is
+ * small.  The direction is therefore taken as the unit vector w / |w|.
+ */
+static void unit_dir(const double *w_in, double w[3])
+{
+    double n = sqrt(w_in[0] * w_in[0] + w_in[1] * w_in[1] + w_in[2] * w_in[2]);
+    w[0] = w_in[0] / n;
+    w[1] = w_in[1] / n;
+    w[2] = w_in[2] / n;
+}
+
 /* Exported for the Stokes pin: one triangle, unrotated omega (unit, z > 0).
  * Returns the integral of max(m~ . w, 0) / m~_z over the normal triangle. */
 double oracle_tri_integral(double n0x, double n0y, double n1x, double n1y,
-                           double n2x, double n2y, double wx, double wy, double wz)
+                           double n2x, double n2y, double wx_in, double wy_in, double wz_in)
 {
+    double w[3], w_in[3] = {wx_in, wy_in, wz_in};
+    unit_dir(w_in, w);
+    double wx = w[0], wy = w[1], wz = w[2];
     double phi = atan2(wy, wx);
     double c = cos(phi), s = sin(phi);
     double wr = sqrt(wx * wx + wy * wy);
@@ -475,9 +494,11 @@ static double collapsed_uv_form(const double *a, const double *b, const double *
     return 0.5 * sum;
 }
 
-static double projarea_one(const double *st, int N, const double *qq, const double *w,
+static double projarea_one(const double *st, int N, const double *qq, const double *w_in,
                            const double *gl_x, const double *gl_w, int ngl)
 {
+    double w[3];
+    unit_dir(w_in, w);
     double x = qq[0], y = qq[1], sxx = qq[2], sxy = qq[3], syy = qq[4];
     double det = sxx * syy - sxy * sxy;
     if (!(sxx > 0.0) || !(syy > 0.0) || !(det > 0.0)) return NAN;
@@ -1023,9 +1044,11 @@ void oracle_sample(const double *st, int N, const double *q, const double *U, in
  */
 
 /* One triangle's V_T / |cross| (Eq. 10-11, Alg. 1; uv form when collapsed). */
-static double tri_ratio(const double *a, const double *b, const double *cc, const double *w,
+static double tri_ratio(const double *a, const double *b, const double *cc, const double *w_in,
                         const double *gl_x, const double *gl_w, int ngl)
 {
+    double w[3];
+    unit_dir(w_in, w);
     double wx = w[0], wy = w[1], wz = w[2];
     double phi = atan2(wy, wx), c = cos(phi), s = sin(phi), wr = sqrt(wx * wx + wy * wy);
     double A2 = area2(a[0], a[1], b[0], b[1], cc[0], cc[1]);
