@@ -7,7 +7,7 @@
 // (n_c - n_a).  Every triangle in the footprint is integrated (no pruning:
 // every visible triangle contributes).
 //
-// Per triangle (FP32):
+// Per triangle:
 //  * all three vertices see w  =>  the whole triangle does (the visible region,
 //    a right half-disk joined to a left half-ellipse, is convex; App. B), and
 //    V_T = w_z A + w_x Wx + w_y Wy with Wx = -oint m~_z dm_y, Wy = oint m~_z
@@ -15,13 +15,17 @@
 //    mean of m~_z is the arc-area formula of App. B; it is evaluated in a
 //    cancellation-free form (the asin difference as one atan2 of exact
 //    products), so no rotation is needed and the 1/|cross| division keeps
-//    FP32 accuracy for small triangles.
-//  * otherwise: rotate so w_y = 0, orient counter-clockwise, clip each edge
-//    with Alg. 1, sum Eq. 11's line terms (minus sign on the w_x part) and the
-//    ellipse arcs (1/2)[F(e_y) - F(s_y)] that join an exit to the next entry.
-//  * |cross| < 1e-7 (normal area < 5e-8): the 3-point edge-midpoint rule on
-//    max(m~.w, 0)/m~_z, exact for quadratics; the triangle spans < 1e-3 in
-//    normal space so its error is far below FP32 rounding of the other path.
+//    FP32 accuracy for small triangles.  Small slivers (longest edge^2 below
+//    1e-4 and aspect above 2) take the 3-point edge-midpoint rule on
+//    max(m~.w, 0)/m~_z instead, exact for quadratics.
+//  * no vertex sees w and the triangle stays clear of the visibility
+//    boundary: exactly 0 (Alg. 1 drops every edge).
+//  * otherwise (partly visible, slivers of aspect above 2000, normals
+//    collapsed onto a segment): the general path of visible.cuh in FP64 (the
+//    clip of Alg. 1 as a line-circle intersection in a scaled frame, Eq. 11's
+//    boundary integral as a corner fan plus chord and arc excesses, and the
+//    segment form of Eq. 13 in closed form), deferred and evaluated 32
+//    triangles at a time so that it runs lane-dense.
 //
 // Work decomposition: each request's footprint is cut into bands of kBand quad
 // rows; one warp integrates one band (lane = quad column, two triangles per
@@ -29,6 +33,7 @@
 // a second kernel adds a request's bands in fixed order, so results do not
 // depend on scheduling or on which other requests share the launch.
 #include "ggx.cuh"
+#include "visible.cuh"
 
 namespace pndf {
 
@@ -91,169 +96,35 @@ __device__ __forceinline__ float zdiff(float2 p, float zp, float2 q, float zq)
     return -fmaf(q.x - p.x, q.x + p.x, (q.y - p.y) * (q.y + p.y)) / (zp + zq);
 }
 
-// ---- FP64 path: the paper's per-triangle algorithm (rotation, Alg. 1,
-// Eq. 11 lines with a minus sign on the w_x part, ellipse arcs), used for
-// partially visible triangles and for ill-conditioned slivers ----
-
-__device__ __forceinline__ double Fasin_d(double p)
-{
-    p = fmin(1.0, fmax(-1.0, p));
-    return asin(p) + p * sqrt(fmax(0.0, 1.0 - p * p));
-}
-
-__device__ bool clip_edge_d(const double a[2], const double b[2], double wz, double oa[2], double ob[2], bool &ca,
-                            bool &cb)
-{
-    double dx = b[0] - a[0], dy = b[1] - a[1];
-    double w2 = wz * wz;
-    double A = w2 * dy * dy + dx * dx;
-    double B = 2.0 * (w2 * a[1] * dy + a[0] * dx);
-    double C = w2 * (a[1] * a[1] - 1.0) + a[0] * a[0];
-    double C1 = w2 * (b[1] * b[1] - 1.0) + b[0] * b[0];
-    double disc = B * B - 4.0 * A * C;
-    bool c0 = C > 0.0 && a[0] < 0.0;
-    bool c1 = C1 > 0.0 && b[0] < 0.0;
-    oa[0] = a[0];
-    oa[1] = a[1];
-    ob[0] = b[0];
-    ob[1] = b[1];
-    ca = false;
-    cb = false;
-    if (c0 || c1) {
-        if (disc < 0.0) return false;
-        double sq = sqrt(disc);
-        double t0 = (-B - sq) / (2.0 * A);
-        double t1 = (-B + sq) / (2.0 * A);
-        if (c0 && c1 && (t0 < 0.0 || t0 > 1.0 || t1 < 0.0 || t1 > 1.0)) return false;
-        if (c0) {
-            oa[0] = a[0] + t0 * dx;
-            oa[1] = a[1] + t0 * dy;
-            ca = true;
-        }
-        if (c1) {
-            ob[0] = a[0] + t1 * dx;
-            ob[1] = a[1] + t1 * dy;
-            cb = true;
-        }
-    }
-    return true;
-}
-
-__device__ double line_term_d(const double p[2], const double q[2], double wr, double wz)
-{
-    double tz = 0.5 * wz * (q[1] - p[1]) * (q[0] + p[0]);
-    double ex = q[0] - p[0], ey = q[1] - p[1];
-    double len = sqrt(ex * ex + ey * ey);
-    if (len == 0.0) return 0.0;
-    double dx = ex / len, dy = ey / len;
-    double sd = dy * p[0] - dx * p[1];
-    double r2 = 1.0 - sd * sd;
-    double r = sqrt(r2);
-    double tx = 0.5 * wr * r2 * dy * (Fasin_d((dx * q[0] + dy * q[1]) / r) - Fasin_d((dx * p[0] + dy * p[1]) / r));
-    return tz - tx;
-}
-
 struct Dir {
     float wx, wy, wz;  // unit direction
     float c, s, wr;    // rotation to w_y = 0: (c, s) = w_xy / |w_xy|, wr = |w_xy|
 };
 
-constexpr int kGL = 16;
-// Gauss-Legendre nodes and weights on [-1, 1], computed on the host.
-struct GLTable {
-    double x[kGL], w[kGL];
-};
-
-// max(m~ . w, 0) / m~_z in FP64
-__device__ __forceinline__ double vis_ratio_d(double mx, double my, double wx, double wy, double wz)
+// Unit direction from the caller's (unit to single precision) vector.
+__device__ __forceinline__ Dir make_dir_f(float wx, float wy, float wz)
 {
-    double mz = sqrt(fmax(0.0, 1.0 - mx * mx - my * my));
-    double c = mx * wx + my * wy + mz * wz;
-    return fmax(c, 0.0) / mz;
+    Dir w;
+    const float n = sqrtf(fmaf(wx, wx, fmaf(wy, wy, wz * wz)));
+    w.wx = wx / n;
+    w.wy = wy / n;
+    w.wz = wz / n;
+    w.wr = sqrtf(fmaf(w.wx, w.wx, w.wy * w.wy));
+    w.c = w.wr > 0.f ? w.wx / w.wr : 1.f;
+    w.s = w.wr > 0.f ? w.wy / w.wr : 0.f;
+    return w;
 }
 
-// Eq. 13's uv-space integral over a uv triangle (area 1/2) whose normal image
-// collapsed onto a segment: a uniform point of the triangle maps to the
-// piecewise-linear density on the sorted vertex positions tau_1..tau_3 along
-// the segment P -> Q (the farthest vertex pair); the visible interval comes
-// from Alg. 1; each linear piece is integrated by Gauss-Legendre.
-__device__ __noinline__ double collapsed_uv_form_d(const double v[3][2], double wx, double wy, double wz, double cs,
-                                                    double sn, const GLTable &gl)
+// V_T / |cross| on the general path (visible.cuh, FP64): partly visible
+// triangles, long slivers, and triangles whose normals collapsed onto a
+// segment (|cross| < 1e-12: the segment form of Eq. 13).
+__device__ __noinline__ float slow_ratio(float2 a, float2 b, float2 c, const Dir &wf)
 {
-    double best = -1.0;
-    int ip = 0, iq = 1;
-    for (int i = 0; i < 3; ++i)
-        for (int j = i + 1; j < 3; ++j) {
-            double dx = v[j][0] - v[i][0], dy = v[j][1] - v[i][1];
-            double d2 = dx * dx + dy * dy;
-            if (d2 > best) {
-                best = d2;
-                ip = i;
-                iq = j;
-            }
-        }
-    if (best == 0.0) return 0.5 * vis_ratio_d(v[0][0], v[0][1], wx, wy, wz);
-    const double *P = v[ip], *Q = v[iq];
-    double ex = Q[0] - P[0], ey = Q[1] - P[1];
-    double tau[3];
-    for (int i = 0; i < 3; ++i) tau[i] = ((v[i][0] - P[0]) * ex + (v[i][1] - P[1]) * ey) / best;
-    for (int i = 0; i < 2; ++i)
-        for (int j = 0; j < 2 - i; ++j)
-            if (tau[j] > tau[j + 1]) {
-                double t = tau[j];
-                tau[j] = tau[j + 1];
-                tau[j + 1] = t;
-            }
-    double pr[2] = {cs * P[0] + sn * P[1], -sn * P[0] + cs * P[1]};
-    double qr[2] = {cs * Q[0] + sn * Q[1], -sn * Q[0] + cs * Q[1]};
-    double oa[2], ob[2];
-    bool ca, cb;
-    if (!clip_edge_d(pr, qr, wz, oa, ob, ca, cb)) return 0.0;
-    double L2 = (qr[0] - pr[0]) * (qr[0] - pr[0]) + (qr[1] - pr[1]) * (qr[1] - pr[1]);
-    double tlo = ((oa[0] - pr[0]) * (qr[0] - pr[0]) + (oa[1] - pr[1]) * (qr[1] - pr[1])) / L2;
-    double thi = ((ob[0] - pr[0]) * (qr[0] - pr[0]) + (ob[1] - pr[1]) * (qr[1] - pr[1])) / L2;
-    double span = tau[2] - tau[0];
-    double sum = 0.0;
-    for (int piece = 0; piece < 2; ++piece) {
-        double t0 = tau[piece], t1 = tau[piece + 1];
-        double lo = fmax(t0, tlo), hi = fmin(t1, thi);
-        if (!(hi > lo) || t1 == t0) continue;
-        for (int g = 0; g < kGL; ++g) {
-            double t = 0.5 * (lo + hi) + 0.5 * (hi - lo) * gl.x[g];
-            double dens = piece == 0 ? 2.0 * (t - t0) / (span * (t1 - t0)) : 2.0 * (t1 - t) / (span * (t1 - t0));
-            sum += 0.5 * (hi - lo) * gl.w[g] * dens * vis_ratio_d(P[0] + t * ex, P[1] + t * ey, wx, wy, wz);
-        }
-    }
-    return 0.5 * sum;
-}
-
-__device__ __noinline__ float tri_ratio_d(float2 a, float2 b, float2 c, const Dir &w, const GLTable &gl)
-{
-    double wx = w.wx, wy = w.wy, wz = w.wz;
-    double wr = sqrt(wx * wx + wy * wy);
-    double cs = wr > 0.0 ? wx / wr : 1.0, sn = wr > 0.0 ? wy / wr : 0.0;
-    double A2 = (double(b.x) - a.x) * (double(c.y) - a.y) - (double(b.y) - a.y) * (double(c.x) - a.x);
-    if (fabs(A2) < 1e-12) {
-        double vv[3][2] = {{a.x, a.y}, {b.x, b.y}, {c.x, c.y}};
-        return float(collapsed_uv_form_d(vv, wx, wy, wz, cs, sn, gl));
-    }
-    double v[3][2] = {{cs * a.x + sn * a.y, -sn * a.x + cs * a.y}, {0, 0}, {0, 0}};
-    const float2 &p1 = A2 > 0.0 ? b : c, &p2 = A2 > 0.0 ? c : b;
-    v[1][0] = cs * p1.x + sn * p1.y;
-    v[1][1] = -sn * p1.x + cs * p1.y;
-    v[2][0] = cs * p2.x + sn * p2.y;
-    v[2][1] = -sn * p2.x + cs * p2.y;
-    double oa[3][2], ob[3][2];
-    bool alive[3], ca[3], cb[3];
-    for (int k = 0; k < 3; ++k) alive[k] = clip_edge_d(v[k], v[(k + 1) % 3], wz, oa[k], ob[k], ca[k], cb[k]);
-    double sum = 0.0;
-    for (int k = 0; k < 3; ++k) {
-        if (!alive[k]) continue;
-        sum += line_term_d(oa[k], ob[k], wr, wz);
-        int nx = alive[(k + 1) % 3] ? (k + 1) % 3 : (alive[(k + 2) % 3] ? (k + 2) % 3 : k);
-        if (cb[k] || ca[nx]) sum += 0.5 * (Fasin_d(ob[k][1]) - Fasin_d(oa[nx][1]));
-    }
-    return float(sum / fabs(A2));
+    const vis::DirD w = vis::make_dir(wf.wx, wf.wy, wf.wz);
+    const double cr = (double(b.x) - double(a.x)) * (double(c.y) - double(a.y)) -
+                      (double(b.y) - double(a.y)) * (double(c.x) - double(a.x));
+    if (fabs(cr) < 1e-12) return float(vis::collapsed_visible(a.x, a.y, b.x, b.y, c.x, c.y, w));
+    return float(vis::tri_visible<double>(a.x, a.y, b.x, b.y, c.x, c.y, w));
 }
 
 // Squared distance from the origin to segment p -> q.
@@ -402,8 +273,8 @@ constexpr int kDefer = 128;
 // Lane's deferred triangle (ring slot head + lane): kernel weight times the
 // FP64 value of V_T / |cross| (tri 0 = (u0, u1, u2), tri 1 = (u3, u2, u1)).
 template <int TFMT>
-__device__ __forceinline__ float deferred_value(const MapDesc &d, const Dir &w, const GLTable &gl,
-                                                const uint32_t *dq_id, const float *dq_w, uint32_t head, int lane)
+__device__ __forceinline__ float deferred_value(const MapDesc &d, const Dir &w, const uint32_t *dq_id,
+                                                const float *dq_w, uint32_t head, int lane)
 {
     uint32_t slot = (head + uint32_t(lane)) & (kDefer - 1);
     uint32_t id = dq_id[slot];
@@ -411,7 +282,7 @@ __device__ __forceinline__ float deferred_value(const MapDesc &d, const Dir &w, 
     float2 a = texel<TFMT>(d, i + tri, j + tri);
     float2 b = texel<TFMT>(d, i + 1 - tri, j + tri);
     float2 c = texel<TFMT>(d, i + tri, j + 1 - tri);
-    return dq_w[slot] * tri_ratio_d(a, b, c, w, gl);
+    return dq_w[slot] * slow_ratio(a, b, c, w);
 }
 
 __global__ void pa_bands(MapDesc d, const pndf_query *__restrict__ qs, int64_t k0, int cnt, uint32_t *__restrict__ nb)
@@ -456,7 +327,7 @@ template <int TFMT>
 __global__ void __launch_bounds__(256) pa_items(MapDesc d, const pndf_query *__restrict__ qs,
                                                const float *__restrict__ omega, int64_t k0, int cnt,
                                                const uint32_t *__restrict__ off, float2 *__restrict__ part,
-                                               unsigned int *__restrict__ cursor, GLTable gl)
+                                               unsigned int *__restrict__ cursor)
 {
     __shared__ uint32_t dq_id_s[8][kDefer];
     __shared__ float dq_w_s[8][kDefer];
@@ -482,13 +353,7 @@ __global__ void __launch_bounds__(256) pa_items(MapDesc d, const pndf_query *__r
         const int t = lo;
         const pndf_query rec = qs[k0 + t];
         const Req q = make_req(rec, d.n);
-        Dir w;
-        w.wx = omega[3 * (k0 + t)];
-        w.wy = omega[3 * (k0 + t) + 1];
-        w.wz = omega[3 * (k0 + t) + 2];
-        w.wr = sqrtf(fmaf(w.wx, w.wx, w.wy * w.wy));
-        w.c = w.wr > 0.f ? w.wx / w.wr : 1.f;
-        w.s = w.wr > 0.f ? w.wy / w.wr : 0.f;
+        const Dir w = make_dir_f(omega[3 * (k0 + t)], omega[3 * (k0 + t) + 1], omega[3 * (k0 + t) + 2]);
         const int band = int(it - off[t]);
         const int jb0 = q.j0 + band * kBand, jb1 = min(q.j1, jb0 + kBand - 1);
         float s = 0.f, c = 0.f;
@@ -540,7 +405,7 @@ __global__ void __launch_bounds__(256) pa_items(MapDesc d, const pndf_query *__r
                 }
                 __syncwarp();
                 while (nd >= 32) {
-                    float val = deferred_value<TFMT>(d, w, gl, dq_id, dq_w, head, lane);
+                    float val = deferred_value<TFMT>(d, w, dq_id, dq_w, head, lane);
                     float tt = s + val;
                     c += fabsf(s) >= fabsf(val) ? (s - tt) + val : (val - tt) + s;
                     s = tt;
@@ -551,7 +416,7 @@ __global__ void __launch_bounds__(256) pa_items(MapDesc d, const pndf_query *__r
             }
         }
         if (nd > 0) {
-            float val = lane < nd ? deferred_value<TFMT>(d, w, gl, dq_id, dq_w, head, lane) : 0.f;
+            float val = lane < nd ? deferred_value<TFMT>(d, w, dq_id, dq_w, head, lane) : 0.f;
             float tt = s + val;
             c += fabsf(s) >= fabsf(val) ? (s - tt) + val : (val - tt) + s;
             s = tt;
@@ -571,7 +436,7 @@ __global__ void __launch_bounds__(256) pa_items(MapDesc d, const pndf_query *__r
 
 // one warp per request: fixed-order sum of its bands
 __global__ void pa_reduce(const pndf_query *__restrict__ qs, int64_t k0, int cnt, const uint32_t *__restrict__ off,
-                          const float2 *__restrict__ part, float *__restrict__ P)
+                          const float2 *__restrict__ part, float *__restrict__ P, unsigned int *hier_status)
 {
     const int lane = threadIdx.x & 31;
     const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -596,37 +461,9 @@ __global__ void pa_reduce(const pndf_query *__restrict__ qs, int64_t k0, int cnt
         const pndf_query r = qs[k0 + t];
         float det = r.sxx * r.syy - r.sxy * r.sxy;
         bool valid = (r.sxx > 0.f) && (r.syy > 0.f) && (det > 0.f) && isfinite(det) && isfinite(r.x) && isfinite(r.y);
-        if (!valid) atomicOr(&g_status_projarea, PNDF_QF_INVALID);
+        if (!valid) record_status(hier_status, &g_status_projarea, PNDF_QF_INVALID);
         P[k0 + t] = valid ? s + c : __int_as_float(0x7fc00000);
     }
-}
-
-// Gauss-Legendre rule on [-1, 1]: nodes are the roots of P_n, found by
-// Newton's method from the Chebyshev-like initial guesses cos(pi (i + 3/4) /
-// (n + 1/2)); weights 2 / ((1 - x^2) P_n'(x)^2).
-GLTable make_gl()
-{
-    GLTable t;
-    const int n = kGL;
-    for (int i = 0; i < n; ++i) {
-        double x = cos(3.14159265358979323846 * (i + 0.75) / (n + 0.5));
-        double dp = 0.0;
-        for (int it = 0; it < 100; ++it) {
-            double p0 = 1.0, p1 = x;
-            for (int k = 2; k <= n; ++k) {
-                double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
-                p0 = p1;
-                p1 = p2;
-            }
-            dp = n * (x * p1 - p0) / (x * x - 1.0);
-            double dx = p1 / dp;
-            x -= dx;
-            if (fabs(dx) < 1e-16) break;
-        }
-        t.x[i] = x;
-        t.w[i] = 2.0 / ((1.0 - x * x) * dp * dp);
-    }
-    return t;
 }
 
 // ---- GGX projected-area fit per mip node (Eq. 12) ----
@@ -715,7 +552,7 @@ constexpr int kGgxLeafWarps = 8;
 static_assert(kGgxDirs <= 16, "a listed pair packs the direction in 4 bits");
 
 template <int TFMT>
-__global__ void __launch_bounds__(32 * kGgxLeafWarps) ggx_leaf(MapDesc d, GgxDirs dirs, GLTable gl,
+__global__ void __launch_bounds__(32 * kGgxLeafWarps) ggx_leaf(MapDesc d, GgxDirs dirs,
                                                                float *__restrict__ P, float4 *__restrict__ omega,
                                                                uint32_t nleaf)
 {
@@ -760,7 +597,7 @@ __global__ void __launch_bounds__(32 * kGgxLeafWarps) ggx_leaf(MapDesc d, GgxDir
             const int it = items[t0 + lane], src = it >> 4, k = it & 15;
             float2 a, b, c;
             leaf_triangle<TFMT>(d, i0, j0, src, a, b, c);
-            rs[k][src] = tri_ratio_d(a, b, c, dirs.w[k], gl);
+            rs[k][src] = slow_ratio(a, b, c, dirs.w[k]);
         }
     }
     __syncwarp();
@@ -914,13 +751,12 @@ pndf_status launch_ggx_build(const pndf_hierarchy *h, pndf_ggx *g, cudaStream_t 
         return PNDF_ERR_OOM;
     }
     float *pa = static_cast<float *>(scratch), *pb = pa + size_t(nleaf) * kGgxDirs;
-    static const GLTable gl = make_gl();
     static const GgxDirs dirs = make_ggx_dirs();
     const unsigned blocks = unsigned((size_t(nleaf) + kGgxLeafWarps - 1) / kGgxLeafWarps);
     if (d.texel_fmt == PNDF_TEXEL_F32X2)
-        ggx_leaf<PNDF_TEXEL_F32X2><<<blocks, 32 * kGgxLeafWarps, 0, s>>>(d, dirs, gl, pa, g->omega[kLeafLevel], nleaf);
+        ggx_leaf<PNDF_TEXEL_F32X2><<<blocks, 32 * kGgxLeafWarps, 0, s>>>(d, dirs, pa, g->omega[kLeafLevel], nleaf);
     else
-        ggx_leaf<PNDF_TEXEL_F16X2><<<blocks, 32 * kGgxLeafWarps, 0, s>>>(d, dirs, gl, pa, g->omega[kLeafLevel], nleaf);
+        ggx_leaf<PNDF_TEXEL_F16X2><<<blocks, 32 * kGgxLeafWarps, 0, s>>>(d, dirs, pa, g->omega[kLeafLevel], nleaf);
     count_launches(1);
     cudaError_t e = cudaGetLastError();
     for (int l = kLeafLevel + 1; e == cudaSuccess && l <= L; ++l) {
@@ -983,7 +819,6 @@ pndf_status launch_projarea(const pndf_hierarchy *h, const pndf_query *q, const 
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    static const GLTable gl = make_gl();
     cudaError_t e = cudaSuccess;
     for (int64_t k0 = 0; k0 < nq && e == cudaSuccess; k0 += chunk) {
         int cnt = int(nq - k0 < chunk ? nq - k0 : chunk);
@@ -994,12 +829,12 @@ pndf_status launch_projarea(const pndf_hierarchy *h, const pndf_query *q, const 
         int occ = 0;
         if (d.texel_fmt == PNDF_TEXEL_F32X2) {
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pa_items<PNDF_TEXEL_F32X2>, 256, 0);
-            pa_items<PNDF_TEXEL_F32X2><<<sms * (occ > 0 ? occ : 1), 256, 0, s>>>(d, q, omega, k0, cnt, off, part, cursor, gl);
+            pa_items<PNDF_TEXEL_F32X2><<<sms * (occ > 0 ? occ : 1), 256, 0, s>>>(d, q, omega, k0, cnt, off, part, cursor);
         } else {
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pa_items<PNDF_TEXEL_F16X2>, 256, 0);
-            pa_items<PNDF_TEXEL_F16X2><<<sms * (occ > 0 ? occ : 1), 256, 0, s>>>(d, q, omega, k0, cnt, off, part, cursor, gl);
+            pa_items<PNDF_TEXEL_F16X2><<<sms * (occ > 0 ? occ : 1), 256, 0, s>>>(d, q, omega, k0, cnt, off, part, cursor);
         }
-        pa_reduce<<<(cnt * 32 + 255) / 256, 256, 0, s>>>(q, k0, cnt, off, part, P);
+        pa_reduce<<<(cnt * 32 + 255) / 256, 256, 0, s>>>(q, k0, cnt, off, part, P, d.status);
         count_launches(4);
         e = cudaGetLastError();
     }
@@ -1008,18 +843,15 @@ pndf_status launch_projarea(const pndf_hierarchy *h, const pndf_query *q, const 
     return PNDF_OK;
 }
 
-cudaError_t read_status_projarea(cudaStream_t s, uint32_t *bits, bool clear)
+namespace {
+__global__ void take_projarea_word(unsigned int *out) { *out = atomicExch(&g_status_projarea, 0u); }
+}  // namespace
+
+cudaError_t take_status_projarea(unsigned int *out, cudaStream_t s)
 {
-    unsigned int v = 0;
-    cudaError_t e = cudaMemcpyFromSymbolAsync(&v, g_status_projarea, sizeof(v), 0, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e == cudaSuccess && clear && v) {
-        unsigned int z = 0;
-        e = cudaMemcpyToSymbolAsync(g_status_projarea, &z, sizeof(z), 0, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    }
-    *bits = v;
-    return e;
+    take_projarea_word<<<1, 1, 0, s>>>(out);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 }  // namespace pndf

@@ -31,6 +31,50 @@ def dirs(nq, seed, grazing=False):
     return torch.from_numpy(w.astype(np.float32))
 
 
+def grazing_dirs(nq, seed, wz=(0.01, 0.1)):
+    """Unit directions with w_z uniform in wz (light near the horizon)."""
+    rng = np.random.default_rng(seed)
+    z = rng.uniform(wz[0], wz[1], nq)
+    ph = rng.uniform(0, 2 * np.pi, nq)
+    r = np.sqrt(1 - z * z)
+    return torch.from_numpy(np.stack([r * np.cos(ph), r * np.sin(ph), z], 1).astype(np.float32))
+
+
+def general_path_fraction(st, q, w):
+    """Share of the footprint triangles (uv centroid inside the 4-sigma
+    ellipse) that are partly visible (some vertex sees w, another does not)
+    or whose normals collapsed onto a segment (|cross| < 1e-12), over all
+    requests: the triangles that take the general FP64 path."""
+    st = np.asarray(st, np.float64)
+    q = np.asarray(q, np.float64)
+    w = np.asarray(w, np.float64)
+    w = w / np.linalg.norm(w, axis=1, keepdims=True)
+    N = st.shape[0]
+    tot = slow = 0
+    for k in range(q.shape[0]):
+        x, y, sxx, sxy, syy = q[k, :5]
+        det = sxx * syy - sxy * sxy
+        i0, i1 = max(int(np.floor(x - 4 * np.sqrt(sxx))) - 1, 0), min(int(np.ceil(x + 4 * np.sqrt(sxx))), N - 2)
+        j0, j1 = max(int(np.floor(y - 4 * np.sqrt(syy))) - 1, 0), min(int(np.ceil(y + 4 * np.sqrt(syy))), N - 2)
+        if i0 > i1 or j0 > j1:
+            continue
+        J, I = np.meshgrid(np.arange(j0, j1 + 1), np.arange(i0, i1 + 1), indexing="ij")
+        n0, n1, n2, n3 = st[J, I], st[J, I + 1], st[J + 1, I], st[J + 1, I + 1]
+        for a, b, c, off in ((n0, n1, n2, 1 / 3), (n3, n2, n1, 2 / 3)):
+            dx, dy = I + off - x, J + off - y
+            inside = (syy * dx * dx - 2 * sxy * dx * dy + sxx * dy * dy) / det <= 16
+            cr = (b[..., 0] - a[..., 0]) * (c[..., 1] - a[..., 1]) - (b[..., 1] - a[..., 1]) * (c[..., 0] - a[..., 0])
+
+            def sees(n):
+                return n[..., 0] * w[k, 0] + n[..., 1] * w[k, 1] + np.sqrt(1 - (n ** 2).sum(-1)) * w[k, 2] >= 0
+
+            nv = sees(a).astype(int) + sees(b) + sees(c)
+            gen = (np.abs(cr) < 1e-12) | ((nv > 0) & (nv < 3))
+            tot += int(inside.sum())
+            slow += int((gen & inside).sum())
+    return slow / max(tot, 1)
+
+
 def run(P, st, q, w):
     h = P.pndf_build_hierarchy(st.to(DEV))
     Pv = P.pndf_diffuse_projected_area(h, q.to(DEV), w.to(DEV)).cpu().double().numpy()
@@ -58,6 +102,42 @@ def test_scratch_fp16_map_and_borders(P):
     w = torch.cat([dirs(400, 4, False), dirs(400, 5, True)])
     got = run(P, st, q, w)
     ref = oracle.projarea(st.float(), q, w)
+    r = rel_err(got, ref)
+    assert r.max() <= RTOL, (r.max(), int(np.argmax(r)))
+
+
+@pytest.mark.parametrize("fmt", ["f32", "f16"])
+def test_general_path_heavy_noise(P, fmt):
+    """Light near the horizon (w_z in [0.01, 0.1]) over a map of independent
+    per-texel normals N(0, 0.3^2) clamped to |s|, |t| <= 0.4: more than half
+    of the footprint triangles are partly visible or collapsed, so the
+    general FP64 path (clip, corner fan, chord and arc excesses, collapsed
+    segments) carries most of P."""
+    rng = np.random.default_rng(11)
+    st = torch.from_numpy(np.clip(rng.normal(0.0, 0.3, (96, 96, 2)), -0.4, 0.4).astype(np.float32))
+    if fmt == "f16":
+        st = st.half()
+    stf = st.float()
+    q = synth.make_queries(stf, 300, synth.QueryMix(sigma=(0.8, 6.0), aspect=(1.0, 3.0)), 12)
+    w = grazing_dirs(300, 13)
+    assert general_path_fraction(stf.numpy(), q.numpy(), w.numpy()) > 0.5
+    got = run(P, st, q, w)
+    ref = oracle.projarea(stf, q, w)
+    r = rel_err(got, ref)
+    assert r.max() <= RTOL, (r.max(), int(np.argmax(r)))
+
+
+def test_general_path_heavy_clamped_bumps(P):
+    """Steep bumps clamped to |s|, |t| <= 0.4 (plateaus where whole quads
+    collapse onto segments of the clamp boundary) under grazing light: more
+    than half of the footprint triangles collapsed or partly visible."""
+    h = synth.bumps_height(128, 200, seed=4, amp=(6.0, 12.0), sig=(1.5, 3.0), noise=0.05)
+    st = synth.normals_from_height(h)
+    q = synth.make_queries(st, 300, synth.QueryMix(sigma=(1.0, 8.0), aspect=(1.0, 3.0)), 14)
+    w = grazing_dirs(300, 15, wz=(0.01, 0.2))
+    assert general_path_fraction(st.numpy(), q.numpy(), w.numpy()) > 0.5
+    got = run(P, st, q, w)
+    ref = oracle.projarea(st, q, w)
     r = rel_err(got, ref)
     assert r.max() <= RTOL, (r.max(), int(np.argmax(r)))
 
