@@ -305,7 +305,8 @@ pndf_status pndf_eval_batch_ex(const pndf_hierarchy *h, const pndf_query *q_dev,
  * (about 9.4 MB) that every GPU loading the library holds until the process
  * exits; nothing is allocated or freed.  The first call on each device looks
  * up that array's device address (cudaGetSymbolAddress) with the device
- * current, so make it before any stream capture.  Every call shares the
+ * current, so make it before any stream capture; after a device reset the
+ * first call in the new context looks it up again.  Every call shares the
  * array: calls whose work can overlap on the GPU (another stream, or earlier
  * work still running) race on it and must be serialised by the caller.
  *   flags_out_dev: device, nq uint32 (PNDF_QF_* bits) or NULL.
@@ -332,12 +333,16 @@ pndf_status pndf_eval_batch_host(const pndf_hierarchy *h, const pndf_query *q_ho
  *   P(w) = sum over triangles T of k_r(T) / |(n_b - n_a) x (n_c - n_a)|
  *          * integral over n+(T) of (w_x m~_x / m~_z + w_z) dm
  * in the frame rotated so w_y = 0, with n+(T) the part of the normal
- * triangle whose normals see w, clipped per Alg. 1 and integrated by
- * Stokes (lines and ellipse arcs, Eq. 11, minus sign on the w_x line term).
- * k_r(T) is the kernel at T's uv centroid (cut at q > 16).  Normal triangles
- * with |cross| < 1e-12 use the collapse limit (1/2) max(n~.w, 0)/n~_z.  The
- * aggregated diffuse BRDF is f_d = P / (pi w_z) (Eq. 13) and the
- * shadow-masking Lambda = P / w_z - 1 (Sec. 4.3).
+ * triangle whose normals see w (clipped as in Alg. 1) and the integral
+ * taken by Stokes over its boundary (Eq. 11, minus sign on the w_x line
+ * term).  w is used as the unit vector w / |w|.  k_r(T) is the kernel at T's
+ * uv centroid (cut at q > 16).  A triangle whose normals collapsed onto a
+ * segment (|cross| < 1e-12) contributes the segment form of Eq. 13: k_r(T)
+ * times the uv-triangle integral of max(n~(u).w, 0) / n~_z(u).  Fully
+ * visible triangles are integrated in FP32; partly visible ones, long
+ * slivers and collapsed ones in FP64.  The aggregated diffuse BRDF is
+ * f_d = P / (pi w_z) (Eq. 13) and the shadow-masking Lambda = P / w_z - 1
+ * (Sec. 4.3).
  *   q_dev:     device, nq pndf_query (x, y, sxx, sxy, syy used; ms, mt ignored).
  *   omega_dev: device, 3*nq floats, unit directions with w_z > 0.
  *   P_out_dev: device, nq floats.
@@ -427,9 +432,23 @@ pndf_status pndf_server_sync(pndf_server *srv);
 void pndf_server_destroy(pndf_server *srv);
 
 /* Read and clear the per-device status word that kernels set on device-side
- * errors (synchronises stream).  PNDF_OK if none; PNDF_ERR_DEVICE otherwise,
- * with the raw PNDF_QF_* bits in *bits_out when bits_out != NULL. */
+ * errors, whichever hierarchy and stream they ran on (synchronises stream).
+ * PNDF_OK if none; PNDF_ERR_DEVICE otherwise, with the raw PNDF_QF_* bits in
+ * *bits_out when bits_out != NULL.  The read and the clear are one atomic
+ * exchange on the device, so bits set by kernels still running on other
+ * streams are kept for the next read.  Every caller on the device shares
+ * this word; pndf_last_device_status reads one hierarchy's own. */
 pndf_status pndf_device_status(void *stream, uint32_t *bits_out);
+
+/* Read and clear hierarchy h's own status word (Sec. 4.2's evaluation has no
+ * error channel of its own; this is the library's): the PNDF_QF_* bits that
+ * kernels recorded while evaluating P-NDF queries or projected areas on h
+ * (invalid covariance, traversal stack overflow), on any stream.  Waits for
+ * the work queued on stream, then takes the word with one atomic exchange on
+ * the device.  Call with h's device current.  PNDF_OK if no bit is set;
+ * PNDF_ERR_DEVICE otherwise, with the bits in *bits_out (nullable).
+ * Errors: INVALID_ARG (null h, wrong device current), CUDA. */
+pndf_status pndf_last_device_status(const pndf_hierarchy *h, void *stream, uint32_t *bits_out);
 
 /* Number of CUDA kernels this library has launched in this process (all
  * devices, all threads); lets a caller count the kernels of a region. */

@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <atomic>
+#include <mutex>
 #include <new>
 
 #include "common.cuh"
@@ -67,6 +68,26 @@ pndf_status check_hierarchy(const pndf_hierarchy *h)
     return PNDF_OK;
 }
 
+// Status read-out: kernels that take a status word (atomic exchange with 0)
+// write the old value into this page-locked, mapped host buffer; a mutex
+// orders the callers, which wait on their stream before reading.
+std::mutex g_status_mutex;
+unsigned int *g_status_host = nullptr;  // 4 words
+
+__global__ void take_word(unsigned int *word, unsigned int *out) { *out = atomicExch(word, 0u); }
+
+cudaError_t status_buffer(unsigned int **host, unsigned int **dev)
+{
+    if (!g_status_host) {
+        void *p = nullptr;
+        cudaError_t e = cudaHostAlloc(&p, 4 * sizeof(unsigned int), cudaHostAllocPortable | cudaHostAllocMapped);
+        if (e != cudaSuccess) return e;
+        g_status_host = static_cast<unsigned int *>(p);
+    }
+    *host = g_status_host;
+    return cudaHostGetDevicePointer(reinterpret_cast<void **>(dev), g_status_host, 0);
+}
+
 }  // namespace
 
 void pndf::count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
@@ -124,6 +145,8 @@ pndf_status pndf_build_hierarchy(const void *texels_dev, const pndf_build_params
         off_mom = total;
         total += up(cluster_scratch_bytes(d.L));
     }
+    const size_t off_status = total;  // the hierarchy's status word
+    total += 256;
     if (cudaMalloc(&h->mem, total) != cudaSuccess) {
         cudaGetLastError();
         delete h;
@@ -143,7 +166,9 @@ pndf_status pndf_build_hierarchy(const void *texels_dev, const pndf_build_params
         }
         if (cluster_scratch_bytes(d.L)) h->moments = base + off_mom;
     }
-    cudaError_t e = launch_build(src, h, as_stream(stream));
+    d.status = reinterpret_cast<unsigned int *>(base + off_status);
+    cudaError_t e = cudaMemsetAsync(d.status, 0, sizeof(unsigned int), as_stream(stream));
+    if (e == cudaSuccess) e = launch_build(src, h, as_stream(stream));
     if (e != cudaSuccess) {
         cudaFree(h->mem);
         delete h;
@@ -391,12 +416,35 @@ pndf_status pndf_diffuse_projected_area(const pndf_hierarchy *h, const pndf_quer
 
 pndf_status pndf_device_status(void *stream, uint32_t *bits_out)
 {
-    uint32_t a = 0, b = 0;
-    cudaError_t e = read_status_eval(as_stream(stream), &a, true);
-    if (e == cudaSuccess) e = read_status_projarea(as_stream(stream), &b, true);
-    if (bits_out) *bits_out = a | b;
+    std::lock_guard<std::mutex> lock(g_status_mutex);
+    unsigned int *host = nullptr, *dev = nullptr;
+    cudaError_t e = status_buffer(&host, &dev);
+    if (e == cudaSuccess) e = take_status_eval(dev, as_stream(stream));
+    if (e == cudaSuccess) e = take_status_projarea(dev + 1, as_stream(stream));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(as_stream(stream));
+    const uint32_t bits = e == cudaSuccess ? host[0] | host[1] : 0u;
+    if (bits_out) *bits_out = bits;
     if (e != cudaSuccess) return PNDF_ERR_CUDA;
-    return (a | b) ? PNDF_ERR_DEVICE : PNDF_OK;
+    return bits ? PNDF_ERR_DEVICE : PNDF_OK;
+}
+
+pndf_status pndf_last_device_status(const pndf_hierarchy *h, void *stream, uint32_t *bits_out)
+{
+    if (bits_out) *bits_out = 0;
+    pndf_status st = check_hierarchy(h);
+    if (st != PNDF_OK) return st;
+    std::lock_guard<std::mutex> lock(g_status_mutex);
+    unsigned int *host = nullptr, *dev = nullptr;
+    cudaError_t e = status_buffer(&host, &dev);
+    if (e == cudaSuccess) {
+        take_word<<<1, 1, 0, as_stream(stream)>>>(h->d.status, dev + 2);
+        count_launches(1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(as_stream(stream));
+    if (e != cudaSuccess) return PNDF_ERR_CUDA;
+    if (bits_out) *bits_out = host[2];
+    return host[2] ? PNDF_ERR_DEVICE : PNDF_OK;
 }
 
 const char *pndf_status_string(pndf_status s)

@@ -30,7 +30,16 @@ struct MapDesc {
     int bounds_fmt;         // pndf_bounds_fmt
     const void *lv[kMaxLevels];  // level 0 (one box per quad) and levels kLeafLevel..L:
                                  // (2^(L-l))^2 nodes each, Morton order
+    unsigned int *status;        // this hierarchy's status word (PNDF_QF_* bits OR-ed in on errors)
 };
+
+// Record device-side error bits: in the hierarchy's own word and in the
+// per-device word of the kernel's translation unit.
+__device__ __forceinline__ void record_status(unsigned int *hier_word, unsigned int *device_word, unsigned int bits)
+{
+    if (hier_word) atomicOr(hier_word, bits);
+    atomicOr(device_word, bits);
+}
 
 // Cluster hierarchy (Sec. 4.2, Eq. 7-8, App. A), levels kLeafLevel..L in the
 // same Morton order as the boxes.  Per node two float4 records,
@@ -181,7 +190,9 @@ int64_t noalloc_max_queries();
 // Count of kernels launched by the library (host-side, process-wide).
 void count_launches(int64_t n);
 // Each kernel translation unit keeps its own device status word (PNDF_QF_*
-// bits OR-ed in by kernels on errors); these read it and optionally clear it.
-cudaError_t read_status_eval(cudaStream_t s, uint32_t *bits, bool clear);
-cudaError_t read_status_projarea(cudaStream_t s, uint32_t *bits, bool clear);
+// bits OR-ed in by kernels on errors).  These queue, on s, a kernel that
+// takes the word (atomic exchange with 0, so bits OR-ed in concurrently are
+// never lost) and stores the old value at out (page-locked host memory).
+cudaError_t take_status_eval(unsigned int *out, cudaStream_t s);
+cudaError_t take_status_projarea(unsigned int *out, cudaStream_t s);
 }  // namespace pndf

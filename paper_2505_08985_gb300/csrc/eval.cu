@@ -805,7 +805,7 @@ __device__ void eval_one(const MapDesc &d, const ClusterDesc &cd, float tau, flo
         if (lane == 0) {
             D_out = __int_as_float(0x7fc00000);
             flags_out = PNDF_QF_INVALID;
-            atomicOr(&g_status_eval, PNDF_QF_INVALID);
+            record_status(d.status, &g_status_eval, PNDF_QF_INVALID);
             if (STATS) *st_out = pndf_query_stats{0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
         }
         return;
@@ -981,7 +981,7 @@ __device__ void eval_one(const MapDesc &d, const ClusterDesc &cd, float tau, flo
     if (lane == 0) {
         D_out = s + c;
         flags_out = fl;
-        if (fl & PNDF_QF_OVERFLOW) atomicOr(&g_status_eval, PNDF_QF_OVERFLOW);
+        if (fl & PNDF_QF_OVERFLOW) record_status(d.status, &g_status_eval, PNDF_QF_OVERFLOW);
         if (STATS)
             *st_out = pndf_query_stats{acc.nodes, acc.leaves, acc.tests, acc.hits,    acc.hash,
                                        acc.fp64,  acc.degen,  acc.quads, acc.cchecks, acc.clusters};
@@ -1418,7 +1418,10 @@ cudaError_t launch_serve(int texel_fmt, int bounds_fmt, const ServeVariant &v, c
 // defined here at file scope and held by every GPU that loads the library
 // until the process exits.  The host never uses the array's name as an
 // address: on the first call on each device, with that device current, the
-// device address is looked up once with cudaGetSymbolAddress and cached.
+// device address is looked up with cudaGetSymbolAddress and cached per
+// device, keyed by the id of the context it was looked up in, so that after a
+// device reset (which unloads the module with its array) the first call in the
+// new context looks the address up again.
 // Every call shares the array and it keeps the previous call's contents, so
 // the cursor and histogram are cleared on the stream at the start of each
 // call; calls whose work overlaps on the GPU (different streams, or work not
@@ -1436,24 +1439,68 @@ constexpr size_t kNoallocBytes = kNoallocOrderOff + size_t(kNoallocMaxQueries) *
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
-std::mutex g_noalloc_mutex;
-void *g_noalloc_ptr[64] = {};
+struct NoallocSlot {
+    unsigned long long ctx_id;  // id of the context the address belongs to
+    void *ptr;                  // device address of g_noalloc_scratch there (null: not looked up)
+};
 
-// Device address of g_noalloc_scratch on the current device (looked up once).
+std::mutex g_noalloc_mutex;
+NoallocSlot g_noalloc_slot[64] = {};
+
+// Id of the calling thread's current context (driver entry points taken
+// through the runtime, so the library links no driver library); false when
+// there is none yet or the driver does not provide them.
+bool current_context_id(unsigned long long *id)
+{
+    using GetCurrent = int (*)(void **);
+    using GetId = int (*)(void *, unsigned long long *);
+    static GetCurrent get_current = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult r;
+        return cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &r) == cudaSuccess &&
+                       r == cudaDriverEntryPointSuccess
+                   ? reinterpret_cast<GetCurrent>(f)
+                   : nullptr;
+    }();
+    static GetId get_id = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult r;
+        return cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &r) == cudaSuccess &&
+                       r == cudaDriverEntryPointSuccess
+                   ? reinterpret_cast<GetId>(f)
+                   : nullptr;
+    }();
+    void *ctx = nullptr;
+    if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx) return false;
+    return get_id(ctx, id) == 0;
+}
+
+// Device address of g_noalloc_scratch on the current device: looked up on
+// the first call in each context (with the device current), then cached.
 cudaError_t noalloc_scratch(void **out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    unsigned long long id = 0;
+    bool have_id = current_context_id(&id);
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_ptr[dev]) {
+    NoallocSlot &slot = g_noalloc_slot[dev];
+    if (!have_id || !slot.ptr || slot.ctx_id != id) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
-        g_noalloc_ptr[dev] = p;
+        if (!have_id) have_id = current_context_id(&id);  // the lookup made the context current
+        slot.ptr = p;
+        slot.ctx_id = have_id ? id : 0ull;
+        if (!have_id) {  // no context id to key on: look up again next time
+            *out = p;
+            slot.ptr = nullptr;
+            return cudaSuccess;
+        }
     }
-    *out = g_noalloc_ptr[dev];
+    *out = slot.ptr;
     return cudaSuccess;
 }
 
@@ -1493,18 +1540,15 @@ pndf_status launch_eval_noalloc(const pndf_hierarchy *h, const pndf_query *q, in
     return e == cudaSuccess ? PNDF_OK : PNDF_ERR_CUDA;
 }
 
-cudaError_t read_status_eval(cudaStream_t s, uint32_t *bits, bool clear)
+namespace {
+__global__ void take_eval_word(unsigned int *out) { *out = atomicExch(&g_status_eval, 0u); }
+}  // namespace
+
+cudaError_t take_status_eval(unsigned int *out, cudaStream_t s)
 {
-    unsigned int v = 0;
-    cudaError_t e = cudaMemcpyFromSymbolAsync(&v, g_status_eval, sizeof(v), 0, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e == cudaSuccess && clear && v) {
-        unsigned int z = 0;
-        e = cudaMemcpyToSymbolAsync(g_status_eval, &z, sizeof(z), 0, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    }
-    *bits = v;
-    return e;
+    take_eval_word<<<1, 1, 0, s>>>(out);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 }  // namespace pndf

@@ -97,6 +97,7 @@ def _load() -> ctypes.CDLL:
         "pndf_eval_noalloc_max_queries": ([], i64),
         "pndf_diffuse_projected_area": ([vp, vp, vp, i64, vp, vp], i32),
         "pndf_device_status": ([vp, ctypes.POINTER(ctypes.c_uint32)], i32),
+        "pndf_last_device_status": ([vp, vp, ctypes.POINTER(ctypes.c_uint32)], i32),
         "pndf_status_string": ([i32], ctypes.c_char_p),
         "pndf_version": ([], i32),
         "pndf_launch_count": ([], i64),
@@ -131,17 +132,34 @@ def _ptr(t) -> int | None:
     return None if t is None else int(t.data_ptr())
 
 
-def _need(t: torch.Tensor, name: str, dtype=None, device=True, shape_last=None):
+def _need(t: torch.Tensor, name: str, dtype=None, device=True, shape_last=None, rows=None, numel=None, on=None):
+    """Check a tensor argument before any call into the library: its type,
+    dtype, contiguity and shape (rows: the first dimension; numel: the total
+    element count; shape_last: the last dimension), then its placement (a
+    CUDA tensor, on device `on` when given).  The C ABI takes bare pointers,
+    so a short buffer or one on another GPU would otherwise be written past
+    its end or in another device's memory."""
     if not isinstance(t, torch.Tensor):
         raise TypeError(f"{name} must be a torch.Tensor")
-    if device and not t.is_cuda:
-        raise ValueError(f"{name} must be a CUDA tensor")
     if dtype is not None and t.dtype != dtype:
         raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
-    if shape_last is not None and t.shape[-1] != shape_last:
-        raise ValueError(f"{name} must have last dimension {shape_last}")
+    if shape_last is not None and (t.dim() < 1 or t.shape[-1] != shape_last):
+        raise ValueError(f"{name} must have last dimension {shape_last}, got shape {tuple(t.shape)}")
+    if rows is not None and (t.dim() < 1 or t.shape[0] != rows):
+        raise ValueError(f"{name} must have {rows} rows, got shape {tuple(t.shape)}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got shape {tuple(t.shape)}")
+    if device and not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if on is not None and t.device != torch.device(on):
+        raise ValueError(f"{name} must be on {on}, got {t.device}")
+
+
+def _same_device(h, queries: torch.Tensor):
+    if queries.device != h.device:
+        raise ValueError(f"queries are on {queries.device} but the hierarchy is on {h.device}")
 
 
 class Hierarchy:
@@ -240,9 +258,8 @@ def pndf_sample_normals(h: Hierarchy, queries: torch.Tensor, uniforms: torch.Ten
     (uniforms: (n, 2) float32 CUDA tensor in [0, 1]).  Returns m (n, 2)
     float32, triangle ids (n,) int32 (-1 where none) and flags (n,) int32."""
     n = _queries(queries)
-    _need(uniforms, "uniforms", dtype=torch.float32, shape_last=2)
-    if uniforms.shape[0] != n:
-        raise ValueError("one pair of uniforms per query")
+    _same_device(h, queries)
+    _need(uniforms, "uniforms", dtype=torch.float32, shape_last=2, rows=n, on=queries.device)
     m = torch.empty(n, 2, dtype=torch.float32, device=queries.device)
     tri = torch.empty(n, dtype=torch.int32, device=queries.device)
     flags = torch.empty(n, dtype=torch.int32, device=queries.device)
@@ -283,7 +300,8 @@ def pndf_ggx_create(h: Hierarchy, stream=None) -> GGX:
 def pndf_ggx_lambda(g: GGX, queries: torch.Tensor, omega: torch.Tensor, stream=None) -> torch.Tensor:
     """Lambda'(omega) per query footprint; omega (n, 3) float32 unit directions."""
     n = _queries(queries)
-    _need(omega, "omega", dtype=torch.float32, shape_last=3)
+    _same_device(g, queries)
+    _need(omega, "omega", dtype=torch.float32, shape_last=3, rows=n, on=queries.device)
     out = torch.empty(n, dtype=torch.float32, device=queries.device)
     with torch.cuda.device(queries.device):
         _check("pndf_ggx_lambda", LIB.pndf_ggx_lambda(g.handle, _ptr(queries), _ptr(omega), n, _ptr(out),
@@ -294,8 +312,9 @@ def pndf_ggx_lambda(g: GGX, queries: torch.Tensor, omega: torch.Tensor, stream=N
 def pndf_shadow_masking(g: GGX, queries: torch.Tensor, wi: torch.Tensor, wo: torch.Tensor, stream=None):
     """Height-correlated G(wi, wo, m) per query (m = the query normal)."""
     n = _queries(queries)
-    _need(wi, "wi", dtype=torch.float32, shape_last=3)
-    _need(wo, "wo", dtype=torch.float32, shape_last=3)
+    _same_device(g, queries)
+    _need(wi, "wi", dtype=torch.float32, shape_last=3, rows=n, on=queries.device)
+    _need(wo, "wo", dtype=torch.float32, shape_last=3, rows=n, on=queries.device)
     out = torch.empty(n, dtype=torch.float32, device=queries.device)
     with torch.cuda.device(queries.device):
         _check("pndf_shadow_masking", LIB.pndf_shadow_masking(g.handle, _ptr(queries), _ptr(wi), _ptr(wo), n,
@@ -363,13 +382,14 @@ def pndf_eval_batch_ex(h: Hierarchy, queries: torch.Tensor, out=None, flags=None
     kernel: footprint kernel (PNDF_KERNEL_GAUSS, _DISK, _BOX).
     jac_eps > 0: the Jacobian clamp of Eq. 6 (e.g. 1e-6)."""
     nq = _queries(queries)
+    _same_device(h, queries)
     if out is None:
         out = torch.empty(nq, dtype=torch.float32, device=queries.device)
-    _need(out, "out", dtype=torch.float32)
+    _need(out, "out", dtype=torch.float32, numel=nq, on=queries.device)
     if flags is not None:
-        _need(flags, "flags", dtype=torch.int32)
+        _need(flags, "flags", dtype=torch.int32, numel=nq, on=queries.device)
     if stats is not None:
-        _need(stats, "stats", dtype=torch.int32, shape_last=STATS_FIELDS)
+        _need(stats, "stats", dtype=torch.int32, shape_last=STATS_FIELDS, rows=nq, on=queries.device)
     cfg = _EvalConfig(int(mode), int(sort), int(warps_per_cta), int(ctas_per_sm), float(tau), int(kernel),
                       float(jac_eps), 0,
                       _event_handle(ev_begin), _event_handle(ev_end))
@@ -385,11 +405,12 @@ def pndf_eval_batch_noalloc(h: Hierarchy, queries: torch.Tensor, out: torch.Tens
     sort scratch is a fixed device array of the library; see pndf.h).  The
     caller supplies `out` if it must not allocate either."""
     nq = _queries(queries)
+    _same_device(h, queries)
     if out is None:
         out = torch.empty(nq, dtype=torch.float32, device=queries.device)
-    _need(out, "out", dtype=torch.float32)
+    _need(out, "out", dtype=torch.float32, numel=nq, on=queries.device)
     if flags is not None:
-        _need(flags, "flags", dtype=torch.int32)
+        _need(flags, "flags", dtype=torch.int32, numel=nq, on=queries.device)
     with torch.cuda.device(queries.device):
         _check("pndf_eval_batch_noalloc", LIB.pndf_eval_batch_noalloc(h.handle, _ptr(queries), nq, _ptr(out),
                                                                       _ptr(flags), _stream(stream)))
@@ -404,10 +425,14 @@ def pndf_eval_batch_host(h: Hierarchy, queries_host: torch.Tensor, out_host: tor
                          stream=None) -> torch.Tensor:
     """Host-buffer variant: queries_host (nq, 8) float32 CPU (pinned for full speed)."""
     _need(queries_host, "queries_host", dtype=torch.float32, device=False, shape_last=8)
+    if queries_host.is_cuda:
+        raise ValueError("queries_host must be a CPU tensor")
     nq = queries_host.shape[0]
     if out_host is None:
         out_host = torch.empty(nq, dtype=torch.float32, pin_memory=queries_host.is_pinned())
-    _need(out_host, "out_host", dtype=torch.float32, device=False)
+    _need(out_host, "out_host", dtype=torch.float32, device=False, numel=nq)
+    if out_host.is_cuda:
+        raise ValueError("out_host must be a CPU tensor")
     with torch.cuda.device(h.device):
         _check("pndf_eval_batch_host", LIB.pndf_eval_batch_host(h.handle, _ptr(queries_host), nq, _ptr(out_host),
                                                                 _stream(stream)))
@@ -418,12 +443,11 @@ def pndf_diffuse_projected_area(h: Hierarchy, queries: torch.Tensor, omega: torc
                                 out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     """omega: (nq, 3) float32 CUDA unit directions with w_z > 0.  Returns P (nq,)."""
     nq = _queries(queries)
-    _need(omega, "omega", dtype=torch.float32, shape_last=3)
-    if omega.shape[0] != nq:
-        raise ValueError("omega must have one row per query")
+    _same_device(h, queries)
+    _need(omega, "omega", dtype=torch.float32, shape_last=3, rows=nq, on=queries.device)
     if out is None:
         out = torch.empty(nq, dtype=torch.float32, device=queries.device)
-    _need(out, "out", dtype=torch.float32)
+    _need(out, "out", dtype=torch.float32, numel=nq, on=queries.device)
     with torch.cuda.device(queries.device):
         _check("pndf_diffuse_projected_area", LIB.pndf_diffuse_projected_area(h.handle, _ptr(queries), _ptr(omega), nq,
                                                                               _ptr(out), _stream(stream)))
@@ -436,6 +460,17 @@ def pndf_device_status(stream=None) -> int:
     code = LIB.pndf_device_status(_stream(stream), ctypes.byref(bits))
     if code not in (PNDF_OK, 7):
         raise PndfError("pndf_device_status", code)
+    return int(bits.value)
+
+
+def pndf_last_device_status(h: Hierarchy, stream=None) -> int:
+    """Read and clear hierarchy h's status word; returns the PNDF_QF_* bits
+    that kernels recorded on h (0 if none)."""
+    bits = ctypes.c_uint32(0)
+    with torch.cuda.device(h.device):
+        code = LIB.pndf_last_device_status(h.handle, _stream(stream), ctypes.byref(bits))
+    if code not in (PNDF_OK, 7):
+        raise PndfError("pndf_last_device_status", code)
     return int(bits.value)
 
 
@@ -455,9 +490,10 @@ def pndf_sort_queries(h: Hierarchy, queries: torch.Tensor, order: torch.Tensor |
                       stream=None) -> torch.Tensor:
     """Evaluation order of a batch (int32 permutation, largest footprints first)."""
     nq = _queries(queries)
+    _same_device(h, queries)
     if order is None:
         order = torch.empty(nq, dtype=torch.int32, device=queries.device)
-    _need(order, "order", dtype=torch.int32)
+    _need(order, "order", dtype=torch.int32, numel=nq, on=queries.device)
     with torch.cuda.device(queries.device):
         _check("pndf_sort_queries", LIB.pndf_sort_queries(h.handle, _ptr(queries), nq, _ptr(order), _stream(stream)))
     return order
@@ -507,6 +543,19 @@ def pndf_server_step(srv: Server, segments: list, stream=None, ev_done=None):
         raise ValueError("too many segments for this server")
     segs = srv._segs
     for i, (mi, q, order, D, flags, first, count) in enumerate(segments):
+        # (a map index out of range is the library's to reject)
+        dev = srv.maps[int(mi)].device if 0 <= int(mi) < len(srv.maps) else None
+        _need(q, f"segment {i} queries", dtype=torch.float32, shape_last=8, on=dev)
+        nq = q.shape[0]
+        _need(D, f"segment {i} D", dtype=torch.float32, numel=nq, on=dev)
+        if flags is not None:
+            _need(flags, f"segment {i} flags", dtype=torch.int32, numel=nq, on=dev)
+        span = nq
+        if order is not None:
+            _need(order, f"segment {i} order", dtype=torch.int32, on=dev)
+            span = order.numel()
+        if first < 0 or count < 0 or first + count > span:
+            raise ValueError(f"segment {i}: slice [{first}, {first + count}) outside its {span} entries")
         sg = segs[i]
         sg.q = _ptr(q)
         sg.order = _ptr(order)

@@ -142,3 +142,35 @@ def test_stats_names_match_header(lib):
     fields = header_struct_fields("pndf_query_stats")
     assert list(pndf.STATS_NAMES) == [n for n, _ in fields] and pndf.STATS_FIELDS == len(fields)
     assert all(t == "uint32_t" for _, t in fields)
+
+
+def test_binding_refuses_short_or_misplaced_buffers():
+    """The binding checks every buffer's size and device before the call: the
+    C ABI takes bare pointers, so a short output would be written past its end.
+    Shapes are checked before placement, so this runs without a GPU."""
+    import torch
+
+    from paper_2505_08985_gb300 import pndf
+
+    need = pndf._need
+    cuda0 = torch.device("cuda", 0)
+    with pytest.raises(ValueError, match="4 elements"):
+        need(torch.empty(3), "out", dtype=torch.float32, numel=4, on=cuda0)
+    with pytest.raises(ValueError, match="4 elements"):
+        need(torch.empty(5, dtype=torch.int32), "flags", dtype=torch.int32, numel=4, on=cuda0)
+    with pytest.raises(ValueError, match="4 rows"):
+        need(torch.empty(3, pndf.STATS_FIELDS, dtype=torch.int32), "stats", dtype=torch.int32,
+             shape_last=pndf.STATS_FIELDS, rows=4, on=cuda0)
+    with pytest.raises(ValueError, match="last dimension 3"):
+        need(torch.empty(4, 2), "omega", dtype=torch.float32, shape_last=3, rows=4, on=cuda0)
+    with pytest.raises(ValueError, match="float32"):
+        need(torch.empty(4, dtype=torch.float64), "out", dtype=torch.float32, numel=4)
+    with pytest.raises(ValueError, match="contiguous"):
+        need(torch.empty(4, 2).t(), "out", dtype=torch.float32)
+    # right shape, wrong place: a CPU tensor where a device buffer is expected
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        need(torch.empty(4), "out", dtype=torch.float32, numel=4, on=cuda0)
+    # the host variant refuses a short result buffer before copying anything
+    q = torch.zeros(4, 8)
+    with pytest.raises(ValueError, match="4 elements"):
+        pndf.pndf_eval_batch_host(None, q, out_host=torch.empty(3))

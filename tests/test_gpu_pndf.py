@@ -182,6 +182,89 @@ def test_affine_field_closed_form(P):
     assert r.max() <= RTOL, r.max()
 
 
+def test_near_singular_triangles_take_fp64(P):
+    """Normal triangles of area below 1e-10 (the fold / caustic case of Eq. 4,
+    where the Jacobian ratio is ill-conditioned) are hit-tested and weighted
+    in FP64.  The affine field n(u) = n0 + 2^-17 u (dyadic, exact in binary32)
+    makes every triangle a right triangle of legs 2^-17: |cross| = 2^-34, below
+    the FP32 cut-off of 2e-10, yet with an inradius (2.2e-6) above the 1e-6
+    edge-tie band, so D can be checked against the closed form
+    k_r(M^-1 (m - n0) - x) / |det M| (Eq. 2) and against the oracle, and the
+    FP64 flag and counter must show on every query that hits."""
+    n0 = (-0.125, 0.0625)
+    c = 2.0 ** -17
+    M = np.array(((c, 0.0), (0.0, c)))
+    N = 64
+    st = synth.affine_normals(N, n0, M)
+    assert np.array_equal(st.double().numpy()[..., 0], n0[0] + c * np.arange(N)[None, :].repeat(N, 0))
+    rng = np.random.default_rng(23)
+    nq = 1500
+    us = rng.uniform(0.05, N - 1.05, (nq, 2))
+    m = (np.asarray(n0)[None] + us @ M.T).astype(np.float32).astype(np.float64)
+    x = us[:, 0] + rng.uniform(-3, 3, nq)
+    y = us[:, 1] + rng.uniform(-3, 3, nq)
+    s = rng.uniform(1.0, 4.0, nq)
+    q = np.stack([x, y, s * s, np.zeros(nq), s * s, m[:, 0], m[:, 1], np.zeros(nq)], 1).astype(np.float32)
+    qt = torch.from_numpy(q)
+    for bounds in (P.PNDF_BOUNDS_F32, P.PNDF_BOUNDS_F16_OUTWARD):
+        D, fl, stt = run(P, st, qt, bounds=bounds)
+        ref = oracle.pndf(st, qt)
+        summary = check_pndf(D, ref, hits_gpu=stt[:, 3], hash_gpu=stt[:, 4], label="near-singular affine")
+        assert summary["compared"] > 300 and summary["nonzero"] > 200
+        hit = stt[:, 3] > 0
+        assert hit.sum() > 200
+        assert (stt[hit, 5] > 0).all(), "hits on tiny triangles must come from the FP64 branch"
+        assert ((fl[hit] & P.PNDF_QF_FP64) != 0).all()
+        assert (ref[1][hit] & oracle.F_TINY).all()  # the oracle sees the same tiny-area hits
+        # the closed form, away from edge ties
+        q64 = q.astype(np.float64)
+        ustar = (q64[:, 5:7] - np.asarray(n0)[None]) / c
+        d = ustar - q64[:, :2]
+        qq = (d ** 2).sum(1) / q64[:, 2]
+        expect = np.where(qq <= 16, np.exp(-0.5 * qq) / (2 * np.pi * q64[:, 2]) / (c * c), 0.0)
+        ok = (ref[1] & oracle.F_EXCLUDE) == 0
+        assert rel_err(D[ok], expect[ok]).max() <= RTOL
+    assert P.pndf_device_status() == 0
+
+
+def test_fold_slivers_take_fp64(P):
+    """A fold line: s falls linearly towards column 32 and rises again after
+    it, with columns 32 and 33 equal up to a few binary32 ulps, so the
+    triangles of quad column 32 have normal-space areas of order 1e-11 (not
+    zero).  Queries whose normal lies on that sliver band must be tested in
+    FP64 (flag and counter); everything away from edge ties matches the
+    oracle."""
+    N = 64
+    rng = np.random.default_rng(5)
+    i = np.arange(N)
+    s_col = np.where(i <= 32, 0.25 - 0.002 * (32 - i), 0.25 - 0.002 * (i - 33)).astype(np.float32)
+    ulp = np.spacing(np.float32(0.25))
+    s_col[33] = np.float32(0.25) + np.float32(2) * ulp
+    t_row = (0.001 * np.arange(N) - 0.03).astype(np.float32)
+    st = np.zeros((N, N, 2), np.float32)
+    st[..., 0] = s_col[None, :] + (rng.integers(-1, 2, (N, N)) * ulp).astype(np.float32) * (i[None, :] >= 32)
+    st[..., 1] = t_row[:, None]
+    st = torch.from_numpy(st)
+    nq = 800
+    # normals on the sliver band (s within the fold columns' values) and elsewhere
+    ms = np.where(rng.uniform(size=nq) < 0.5, 0.25 + rng.uniform(-4, 6, nq) * ulp, rng.uniform(0.19, 0.25, nq))
+    mt = rng.uniform(-0.028, 0.03, nq)
+    x = rng.uniform(24, 40, nq)
+    y = rng.uniform(4, 59, nq)
+    sg = rng.uniform(1.0, 5.0, nq)
+    q = torch.from_numpy(np.stack([x, y, sg * sg, np.zeros(nq), sg * sg, ms, mt, np.zeros(nq)], 1).astype(np.float32))
+    D, fl, stt = run(P, st, q)
+    ref = oracle.pndf(st, q)
+    check_pndf(D, ref, hits_gpu=stt[:, 3], hash_gpu=stt[:, 4], label="fold slivers")
+    fp64 = stt[:, 5] > 0
+    assert fp64.sum() > 50, int(fp64.sum())
+    assert ((fl[fp64] & P.PNDF_QF_FP64) != 0).all()
+    assert ((fl[~fp64] & P.PNDF_QF_FP64) == 0).all()
+    # the tiny-area hits the oracle reports all come from FP64-tested queries
+    tiny = (ref[1] & oracle.F_TINY) != 0
+    assert tiny.any() and fp64[tiny].all()
+
+
 def test_large_footprints_deep_traversal(P):
     """Footprints up to sigma = 150 on a 1024^2 flake map (deep descent, many entry nodes)."""
     st = synth.flake_normals(1024, 3000, seed=9)
@@ -218,6 +301,33 @@ def test_invalid_queries_flagged(P):
     assert P.pndf_device_status() & P.PNDF_QF_INVALID
     assert P.pndf_device_status() == 0  # cleared by the read
     h.free()
+
+
+def test_status_word_per_hierarchy(P):
+    """Each hierarchy keeps its own status word: an invalid query evaluated on
+    one map (P-NDF or projected area) sets that map's word and the device-wide
+    one, not another map's; reading a word clears it."""
+    st = synth.bumps_map(n=64, n_bumps=4, seed=2)
+    a = P.pndf_build_hierarchy(st.to(DEV))
+    b = P.pndf_build_hierarchy(st.to(DEV))
+    P.pndf_device_status()  # start from a clean device word
+    q = synth.make_queries(st, 8, synth.QueryMix(sigma=(3.0, 3.0)), 2).to(DEV)
+    bad = q.clone()
+    bad[5, 4] = -2.0  # syy < 0
+    P.pndf_eval_batch(a, bad)
+    P.pndf_eval_batch(b, q)
+    assert P.pndf_last_device_status(b) == 0
+    assert P.pndf_last_device_status(a) == P.PNDF_QF_INVALID
+    assert P.pndf_last_device_status(a) == 0  # cleared by the read
+    assert P.pndf_device_status() == P.PNDF_QF_INVALID
+    w = torch.tensor([[0.3, 0.2, math.sqrt(1 - 0.13)]], device=DEV).repeat(8, 1)
+    P.pndf_diffuse_projected_area(b, bad, w)
+    assert P.pndf_last_device_status(a) == 0
+    assert P.pndf_last_device_status(b) == P.PNDF_QF_INVALID
+    assert P.pndf_device_status() == P.PNDF_QF_INVALID
+    assert P.pndf_device_status() == 0
+    a.free()
+    b.free()
 
 
 def test_result_independent_of_batch(P):
