@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--map-size", dest="n", type=int, default=synth.FLAKE_8192["n"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the error against the FP64 oracle per workload")
     ap.add_argument("--kernels", default="disk,box", help="footprint kernels to measure besides the Gaussian ('' = skip)")
     ap.add_argument("--no-clamp-sampling", action="store_true", help="skip the Eq. 6 clamp and sampling figures")
     ap.add_argument("--cluster-taus", default="1e-4,1e-3",
@@ -303,6 +304,58 @@ def committed_ncu_pct(bounds_tag: str):
     return val if src == kernel_source_hash() else None
 
 
+def committed_profile_value(key: str):
+    """One number of the committed traversal profile summary ("key: value"),
+    if the summary was taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", f"traverse_{WORKLOAD}.txt")
+    if not os.path.exists(p):
+        return None
+    src, val = None, None
+    with open(p) as f:
+        for line in f:
+            if line.startswith("kernel_source_sha256_16:"):
+                src = line.split(":", 1)[1].strip()
+            if line.startswith(f"{key}:"):
+                val = float(line.split(":", 1)[1].split()[0])
+    return val if src == kernel_source_hash() else None
+
+
+def traversal_roofline(dev, work_f16: dict, nq: int, kernel_ms: float, world: int) -> dict:
+    """Roofline of the dominant kernel (traversal + leaf test) per launch.
+
+    HBM, on the survey's byte model (Sec. 8(d)): every visited node's box
+    (8 B in binary16) + every leaf block's (b + 1)^2 = 25 texels (8 B each,
+    FP32) + the query's 32 B record and 4 B result.  Instruction issue, on the
+    warp instructions per query of the committed ncu capture of the same
+    kernel source (152 SMs x 4 schedulers x the maximum SM clock).  `bound` is
+    the ceiling with the larger fraction; the other is kept beside it, and so
+    is the builder's own byte model (every level-0 box tested, each tested
+    triangle's three texels, 40 B per query), which counts texels of a leaf
+    block once per triangle that reads them."""
+    pk, pk_kind = hbm_peak()
+    sec = kernel_ms / 1e3
+    s8d = work_f16["nodes"] * 8 + work_f16["leaf_blocks"] * 25 * 8 + 36 * nq
+    hbm = {"achieved": s8d / sec / 1e9, "peak": pk, "unit": "GB/s", "frac": s8d / sec / 1e9 / pk,
+           "algorithmic_bytes_per_launch": s8d, "peak_source": f"{pk_kind} hbm_gbs",
+           "byte_model": "nodes x 8 B + leaf blocks x 25 texels x 8 B + 36 B per query"}
+    peaks = compute_peaks(dev)
+    wipq = committed_profile_value("warp_inst_per_query_f16")
+    issue = None
+    if wipq is not None:
+        ach = wipq * nq / sec / 1e9
+        issue = {"achieved": ach, "peak": peaks["issue"], "unit": "G warp-instructions/s", "frac": ach / peaks["issue"],
+                 "warp_instructions_per_query": wipq, "peak_source": f"{peaks['sms']} SMs x 4 x {peaks['sm_mhz']:.0f} MHz"}
+    bound = "alu" if issue and issue["frac"] > hbm["frac"] else "hbm"
+    top = issue if bound == "alu" else hbm
+    out = {"bound": bound, "achieved": top["achieved"], "peak": top["peak"], "unit": top["unit"], "frac": top["frac"],
+           "traffic": committed_traffic("f16"), "hbm": hbm, "issue": issue,
+           "ncu_pct_of_peak": committed_ncu_pct("f16"),
+           "builder_byte_model": {"bytes_per_launch": work_f16["bytes"],
+                                  "achieved_gbs": work_f16["bytes"] / sec / 1e9,
+                                  "frac_hbm": work_f16["bytes"] / sec / 1e9 / pk}}
+    return out
+
+
 def committed_traffic(bounds_tag: str):
     """DRAM bytes per launch of the traversal kernel from the committed ncu
     summary, if it was taken on the current kernel source (else None)."""
@@ -322,6 +375,15 @@ def committed_traffic(bounds_tag: str):
 # ---------------------------------------------------------------------------
 # workload
 # ---------------------------------------------------------------------------
+
+def workload_config(n: int, nq: int, world: int) -> dict:
+    """The `config` object of both arms' JSON lines: the same workload keys."""
+    return {"workload": WORKLOAD, "map": f"{n}^2 Voronoi flakes, fp32 (s,t)",
+            "queries_per_gpu": nq, "sigma": "log-uniform 1..512 texels, isotropic",
+            "bounds": "fp16 outward-rounded", "leaf_math": "fp32 (fp64 below 1e-10 area)",
+            "l2": "inputs larger than L2 (512 MiB texels + 128 MiB queries re-read each step)",
+            "step": "rebuild pyramid + key/sort + traverse/leaf + unpermute", "parallelism": f"replicas x{world}"}
+
 
 def make_workload(args, device, rank):
     cfg = synth.FLAKE_8192
@@ -379,7 +441,7 @@ def run_reference(args, world, rank):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "map": f"{args.n}^2 flakes", "queries": args.queries},
+            "config": workload_config(args.n, args.queries, args.gpus),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -441,11 +503,12 @@ def tree_nodes(n: int) -> int:
 
 def pyramid_bytes(n: int, texel_bytes: int, box_bytes: int) -> int:
     """Algorithmic bytes of one pyramid build: the map read once, the
-    hierarchy's copy of it written once, and every stored box written once
-    (level 0 and levels 2..L, padded to 2^L quads per side)."""
+    hierarchy's copy of it written once, every stored box written once
+    (level 0 and levels 2..L, padded to 2^L quads per side) and every quad's
+    8-byte capsule."""
     from paper_2505_08985_gb300 import pndf
-    boxes = 4 ** pndf.top_level(n) + tree_nodes(n)
-    return 2 * n * n * texel_bytes + boxes * box_bytes
+    quads = 4 ** pndf.top_level(n)
+    return 2 * n * n * texel_bytes + (quads + tree_nodes(n)) * box_bytes + 8 * quads
 
 
 def run_census(dev):
@@ -520,6 +583,26 @@ def run_mixed(args, dev):
     pa_ms, pn_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
     assert torch.isfinite(P).all() and torch.isfinite(D).all()
     tris = footprint_triangles(qa, st.shape[0])
+    acc = None
+    if not args.no_accuracy:
+        import oracle
+        st_cpu = st.float().cpu()
+        # P-NDF: octaves of sigma 1..1024, fewer of the costly large footprints
+        idx = sigma_strata(qp, np.exp2(np.arange(11)), [600, 600, 600, 600, 400, 200, 80, 30, 12, 5], seed=17)
+        qs = qp[torch.from_numpy(idx).to(dev)].contiguous()
+        acc = {"mixed16384_pndf": oracle_errors(st_cpu, qs, gpu_results({"fp16_bounds": h}, qs),
+                                                f"{idx.size} of {nq} queries, per octave of sigma (1..1024): "
+                                                "600 below 16, then 400, 200, 80, 30, 12, 5")}
+        ia = sigma_strata(qa, np.exp2(np.arange(11)), [20, 20, 20, 20, 12, 8, 5, 3, 2, 1], seed=19)
+        Po = oracle.projarea(st_cpu, qa[torch.from_numpy(ia).to(dev)].cpu(), w[torch.from_numpy(ia).to(dev)].cpu())
+        Pg = P[torch.from_numpy(ia).to(dev)].double().cpu().numpy()
+        nzp = Po != 0  # a footprint can see nothing of the light: P = 0 exactly
+        relp = np.abs(Pg[nzp] - Po[nzp]) / np.abs(Po[nzp])
+        acc["mixed16384_projected_area"] = {
+            "subset": f"{ia.size} of {nq} requests, per octave of sigma (1..1024): 20 below 16, then 12, 8, 5, 3, 2, 1",
+            "compared": int(ia.size), "zero_P": int((~nzp).sum()), "zero_mismatches": int(((~nzp) & (Pg != 0)).sum()),
+            "rel_err_max": float(relp.max()), "rel_err_p99": float(np.quantile(relp, 0.99)),
+            "rel_err_median": float(np.median(relp))}
     # GGX fit of every mip node (Eq. 12): build time, Lambda' throughput, and
     # its projected area P' = w_z (1 + Lambda') against the analytic P above
     ev[0].record()
@@ -544,7 +627,7 @@ def run_mixed(args, dev):
         x = x[torch.isfinite(x)]
         return float(torch.quantile(x, p)) if x.numel() else float("nan")
 
-    return {"workload": f"16384^2 binary16 mixed map (scratches + flakes); {nq} projected-area requests and {nq} "
+    out = {"workload": f"16384^2 binary16 mixed map (scratches + flakes); {nq} projected-area requests and {nq} "
                         "P-NDF queries, sigma log-U(1, 1024), light uniform on the hemisphere",
             "projected_area": {"requests_per_s": nq / (pa_ms / 1e3), "ms": pa_ms, "triangles": tris,
                                "triangles_per_s": tris / (pa_ms / 1e3)},
@@ -556,6 +639,9 @@ def run_mixed(args, dev):
                         "P_rel_diff_vs_analytic": {"median": pct(rel, 0.5), "p95": pct(rel, 0.95),
                                                    "median_grazing_wz<0.2": pct(rel[graz], 0.5),
                                                    "median_wz>=0.2": pct(rel[~graz], 0.5)}}}
+    if acc is not None:
+        out["accuracy"] = acc
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -862,13 +948,24 @@ def run_gpu(args, world, rank, local):
     e2e_value = total_q / e2e_s
     assert torch.isfinite(D_h).all()
 
+    # error against the FP64 oracle on a sigma-stratified 10k subset (untimed)
+    acc = None
+    if rank == 0 and world == 1 and not args.no_accuracy:
+        idx = sigma_strata(q, np.exp2(np.arange(10)), [1112] * 9, seed=13)
+        qs = q[torch.from_numpy(idx).to(dev)].contiguous()
+        hs = {"fp32_bounds": pndf.pndf_build_hierarchy(st, bounds_fmt=pndf.PNDF_BOUNDS_F32),
+              "fp16_bounds": pndf.pndf_build_hierarchy(st, bounds_fmt=pndf.PNDF_BOUNDS_F16_OUTWARD)}
+        acc = {"flake8192": oracle_errors(st.cpu(), qs, gpu_results(hs, qs),
+                                          f"{idx.size} of {nq} queries, equal counts per octave of sigma (1..512)")}
+        for h in hs.values():
+            h.free()
+
     # roofline of the dominant kernel (traversal + leaf test), per launch
     kavg16 = sum(kms16) / len(kms16)
     cluster = run_cluster_cut(args, world, st, q, D, kavg16) if args.cluster_taus else None
     kernels = run_kernels(args, world, st, q, kavg16, work["f16"]["tri_tests"]) if args.kernels else None
     clamp = None if args.no_clamp_sampling else run_clamp_sampling(args, world, st, q, kavg16, D)
     peak, peak_kind = hbm_peak()
-    achieved = work["f16"]["bytes"] / (kavg16 / 1e3) / 1e9
     traffic = committed_traffic("f16")
     stage_ms = time_build_and_sort(args, world, st, q)
     flop_model = traversal_flops(dev, work["f16"], kavg16, world, peak)
@@ -877,26 +974,22 @@ def run_gpu(args, world, rank, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms16_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "map": f"{args.n}^2 Voronoi flakes, fp32 (s,t)",
-                   "queries_per_gpu": nq, "sigma": "log-uniform 1..512 texels, isotropic",
-                   "bounds": "fp16 outward-rounded", "leaf_math": "fp32 (fp64 below 1e-10 area)",
-                   "l2": "inputs larger than L2 (512 MiB texels + 128 MiB queries re-read each step)",
-                   "step": "rebuild pyramid + key/sort + traverse/leaf + unpermute", "parallelism": f"replicas x{world}"},
+        "config": workload_config(args.n, nq, world),
         "fp32_bounds_plain": {"value": value32, "unit": UNIT, "ms_per_step": ms32_max / args.steps,
                               "traverse_kernel_ms": sum(kms32) / len(kms32)},
         "traverse_kernel_ms": kavg16,
         "leaf_triangle_tests_per_s": work["f16"]["tri_tests"] * world / (kavg16 / 1e3),
         "traversal_flops": flop_model,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs",
-                     "ncu_pct_of_peak": committed_ncu_pct("f16"),
-                     "algorithmic_bytes_per_launch": work["f16"]["bytes"]},
+        "roofline": traversal_roofline(dev, work["f16"], nq, kavg16, world),
         "work_per_launch": work,
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": int(st.numel() * 4 + q.numel() * 4), "d2h_bytes_per_step": int(nq * 4)},
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
+    if acc is not None:
+        acc.update(accuracy_small(dev))
+        line["accuracy_vs_fp64_oracle"] = acc
     if cluster:
         line["cluster_cut"] = cluster
     if kernels:
@@ -909,12 +1002,14 @@ def run_gpu(args, world, rank, local):
         torch.cuda.empty_cache()
     if args.mixed_requests > 0:
         line["glint_diffuse_16384"] = run_mixed(args, dev)
+        if "accuracy_vs_fp64_oracle" in line and "accuracy" in line["glint_diffuse_16384"]:
+            line["accuracy_vs_fp64_oracle"].update(line["glint_diffuse_16384"].pop("accuracy"))
         torch.cuda.empty_cache()
     if args.serve_batches > 0:
         line["serving"] = run_serving(args, dev)
         line["serving"]["note"] = "per GPU (each rank serves its own replica of the stream)"
-    line["kernel_rooflines"] = kernel_rooflines(dev, args.n, nq, stage_ms, kavg16, work["f16"]["bytes"], traffic,
-                                                cluster, clamp, line.get("glint_diffuse_16384"))
+    line["kernel_rooflines"] = kernel_rooflines(dev, args.n, nq, stage_ms, kavg16, line["roofline"], cluster, clamp,
+                                                line.get("glint_diffuse_16384"))
     if (args.serve_batches > 0 or args.mixed_requests > 0) and rank == 0 and world == 1 and not args.no_cpu_baseline:
         st, q = make_workload(args, dev, rank)
 
@@ -927,6 +1022,89 @@ def run_gpu(args, world, rank, local):
                                 "sample": f"{n_done} random queries of the same workload, {secs:.1f} s wall"}
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# error against the FP64 oracle, per workload (outside every timed region)
+# ---------------------------------------------------------------------------
+
+def sigma_strata(q: torch.Tensor, edges, per_bin, seed: int) -> np.ndarray:
+    """Indices of a sigma-stratified subset: up to per_bin[k] queries drawn at
+    random from bin [edges[k], edges[k+1]) of the footprint's major sigma."""
+    qq = q[:, 2:5].double().cpu().numpy()
+    tr, det = qq[:, 0] + qq[:, 2], qq[:, 0] * qq[:, 2] - qq[:, 1] ** 2
+    sig = np.sqrt(0.5 * tr + np.sqrt(np.maximum(0.25 * tr * tr - det, 0.0)))
+    rng = np.random.default_rng(seed)
+    out = []
+    for k, (a, b) in enumerate(zip(edges[:-1], edges[1:])):
+        cand = np.flatnonzero((sig >= a) & (sig < b))
+        if cand.size:
+            out.append(rng.choice(cand, size=min(per_bin[k], cand.size), replace=False))
+    return np.sort(np.concatenate(out)) if out else np.zeros(0, np.int64)
+
+
+def oracle_errors(st_cpu, q_sub: torch.Tensor, gpu: dict, subset: str) -> dict:
+    """Per-query relative error of each GPU result against the FP64 oracle on
+    the same queries: max / p99 / median over the compared queries (those the
+    oracle flags as ties are excluded and counted by reason), exact-zero
+    mismatches, and how many queries took the FP64 leaf branch."""
+    import oracle
+    Do, fo, _, _ = oracle.pndf(st_cpu, q_sub.cpu())
+    ok = (fo & oracle.F_EXCLUDE) == 0
+    out = {"subset": subset, "queries": int(len(Do)), "compared": int(ok.sum()),
+           "excluded": {"near_edge": int(((fo & oracle.F_NEAR_EDGE) != 0).sum()),
+                        "near_cut": int(((fo & oracle.F_NEAR_CUT) != 0).sum()),
+                        "degenerate": int(((fo & oracle.F_DEGENERATE) != 0).sum()),
+                        "invalid": int(((fo & oracle.F_INVALID) != 0).sum())},
+           "oracle_tiny_area_hits": int(((fo & oracle.F_TINY) != 0).sum()), "results": {}}
+    for name, (D, fl) in gpu.items():
+        D = D.double().cpu().numpy()
+        nz = ok & (Do != 0)
+        rel = np.abs(D[nz] - Do[nz]) / np.abs(Do[nz])
+        out["results"][name] = {
+            "rel_err_max": float(rel.max()) if rel.size else 0.0,
+            "rel_err_p99": float(np.quantile(rel, 0.99)) if rel.size else 0.0,
+            "rel_err_median": float(np.median(rel)) if rel.size else 0.0,
+            "zero_mismatches": int((ok & (Do == 0) & (D != 0)).sum()),
+            "fp64_branch_queries": int(((fl.cpu().numpy() & 1) != 0).sum())}
+    return out
+
+
+def gpu_results(h_by_name: dict, q_sub: torch.Tensor) -> dict:
+    from paper_2505_08985_gb300 import pndf
+    out = {}
+    for name, h in h_by_name.items():
+        fl = torch.zeros(q_sub.shape[0], dtype=torch.int32, device=q_sub.device)
+        D = pndf.pndf_eval_batch(h, q_sub, flags=fl)
+        out[name] = (D, fl)
+    return out
+
+
+def accuracy_small(dev) -> dict:
+    """The bumps (all 4096 queries) and scratch (10k of 1M, sigma-stratified)
+    workloads against the oracle, FP32 and FP16 bounds."""
+    from paper_2505_08985_gb300 import pndf
+    res = {}
+    for key, cfg, make, strata in (
+            ("bumps256", synth.BUMPS_256, lambda c: synth.bumps_map(n=c["n"], seed=c["seed"], device=dev), None),
+            ("scratch2048", synth.SCRATCH_2048, lambda c: synth.scratch_map(n=c["n"], seed=c["seed"], device=dev),
+             (np.exp2(np.arange(7)), [1667] * 6))):
+        st = make(cfg)
+        q = synth.make_queries(st, cfg["queries"], cfg["mix"], cfg["seed"])
+        if strata is None:
+            idx, subset = np.arange(q.shape[0]), f"all {q.shape[0]} queries"
+        else:
+            idx = sigma_strata(q, strata[0], strata[1], seed=11)
+            subset = f"{idx.size} of {q.shape[0]} queries, equal counts per octave of major sigma"
+        qs = q[torch.from_numpy(idx).to(dev)].contiguous()
+        hs = {"fp32_bounds": pndf.pndf_build_hierarchy(st, bounds_fmt=pndf.PNDF_BOUNDS_F32),
+              "fp16_bounds": pndf.pndf_build_hierarchy(st, bounds_fmt=pndf.PNDF_BOUNDS_F16_OUTWARD)}
+        res[key] = oracle_errors(st.cpu(), qs, gpu_results(hs, qs), subset)
+        for h in hs.values():
+            h.free()
+        del st, q
+    return res
+
 
 
 def traversal_flops(dev, w, kernel_ms, world, hbm_pk):
@@ -979,12 +1157,13 @@ def time_build_and_sort(args, world, st, q):
     return out
 
 
-def kernel_rooflines(dev, n, nq, stage_ms, traverse_ms, traverse_bytes, traverse_traffic, cluster, clamp, mixed):
+def kernel_rooflines(dev, n, nq, stage_ms, traverse_ms, traverse_roof, cluster, clamp, mixed):
     """Roofline of every kernel family, from the CUDA-event times measured
     in this run.  Algorithmic bytes per unit: pyramid build, the FP32 map
     read and its copy written (8 B each per texel) plus every FP16 box written
     (8 B); query sort, the 32 B record read, the key written and read back
-    and the order slot written (4 B each); traversal, as in `roofline`;
+    and the order slot written (4 B each); traversal, as in `roofline` (the
+    survey's byte model, and instruction issue from the committed capture);
     sampling, record, uniforms, four texels and the outputs (88 B); Lambda',
     record, direction and result (48 B) plus the 12 B Omega of the eight
     nodes it blends (96 B); cluster fit, the map read (8 B per texel) and the
@@ -1005,8 +1184,15 @@ def kernel_rooflines(dev, n, nq, stage_ms, traverse_ms, traverse_bytes, traverse
                                             n * n, "texel", pyramid_bytes(n, 8, 8) / (n * n), census, peaks, pk)
     fams["query_sort"] = family_roofline("query_sort", ["key_hist", "key_scan", "key_place"], stage_ms["query_sort"],
                                          nq, "query", 44, census, peaks, pk)
-    tr = family_roofline("traverse", ["traverse_kernel"], traverse_ms, nq, "query", traverse_bytes / nq, {}, peaks, pk)
-    tr["traffic"] = traverse_traffic
+    tr = family_roofline("traverse", ["traverse_kernel"], traverse_ms, nq, "query",
+                         traverse_roof["hbm"]["algorithmic_bytes_per_launch"] / nq, {}, peaks, pk)
+    if traverse_roof["issue"]:
+        tr["fracs"]["issue"] = traverse_roof["issue"]["frac"]
+        if traverse_roof["bound"] == "alu":
+            iss = traverse_roof["issue"]
+            tr.update(bound="issue", achieved=iss["achieved"], peak=iss["peak"], unit_rate=iss["unit"],
+                      frac=iss["frac"])
+    tr["traffic"] = traverse_roof["traffic"]
     fams["traverse"] = tr
     if cluster:
         ms = cluster["build_ms"] - stage_ms["pyramid_build"]

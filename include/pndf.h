@@ -151,7 +151,10 @@ typedef struct pndf_eval_config {
  * below it lie inside.  Levels leaf_level..L are stored (2^L >= N-1), each
  * in Morton order so the four children of a node are contiguous, plus level
  * 0 (one box per quad, Morton order, so a leaf block's 16 quads are
- * contiguous); nodes without quads hold an empty box.  The texels are copied into the
+ * contiguous) and beside it one capsule per quad (8 bytes: the segment
+ * between the quad's two farthest normals and a radius holding all four, a
+ * tighter filter than the box for the long slivers of quads that straddle
+ * two normal regions); nodes without quads hold an empty box.  The texels are copied into the
  * hierarchy (the caller may free texels_dev once the stream reaches the end
  * of this call's work).  On success *out owns device memory until
  * pndf_free_hierarchy().
@@ -186,7 +189,8 @@ pndf_status pndf_update_hierarchy(pndf_hierarchy *h, const void *texels_dev, voi
  * device; safe on NULL). */
 void pndf_free_hierarchy(pndf_hierarchy *h);
 
-/* Device bytes held by a hierarchy (texel copy + pyramid). */
+/* Device bytes held by a hierarchy (texel copy + pyramid + per-quad
+ * capsules + status word, and the cluster records when built). */
 size_t pndf_hierarchy_bytes(const pndf_hierarchy *h);
 
 /* Per-sample flags of pndf_sample_normals. */

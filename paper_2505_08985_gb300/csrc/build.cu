@@ -7,8 +7,10 @@
 // so the four children of node k at level l are nodes 4k..4k+3 at level l-1
 // (one 64-byte line in FP32, one 32-byte sector in FP16).
 //
-// Level 0 holds one box per quad (its four texels); the leaf level 2 box is
-// the union of its 16 quad boxes.
+// Level 0 holds one box per quad (its four texels) and, beside it, the
+// quad's capsule (the segment between its two farthest normals and a radius
+// holding the other two; see common.cuh); the leaf level 2 box is the union
+// of its 16 quad boxes.
 //
 // Kernel 1 (build_tiles): one CTA per 64 x 64-quad tile.  The tile's 65 x 65
 // texels are staged in shared memory with 16-byte vector loads (float4 = two
@@ -31,6 +33,61 @@ constexpr int kTileQuadsMax = 64;
 constexpr int kTileTexMax = kTileQuadsMax + 1;
 constexpr int kBuildThreads = 256;
 
+
+// The quad box as the traversal will read it back (binary16 bounds rounded
+// outward, so the decoded box is the stored one).
+template <int BFMT>
+__device__ __forceinline__ Box stored_box(const Box &b)
+{
+    if (BFMT == PNDF_BOUNDS_F32) return b;
+    return Box{__half2float(__float2half_rd(b.smin)), __half2float(__float2half_rd(b.tmin)),
+               __half2float(__float2half_ru(b.smax)), __half2float(__float2half_ru(b.tmax))};
+}
+
+// Capsule code of a quad with normals v[0..3] and stored box sb: the segment
+// between the farthest pair, as 8-bit fractions of the box; w = the largest
+// distance of the four normals to the decoded segment, enlarged by 2^-9
+// relative and 2^-21 absolute (more than the FP32 rounding of this distance
+// here and of the query's test) and rounded up to binary16.
+__device__ __forceinline__ uint2 encode_capsule(const float2 v[4], const Box &sb)
+{
+    int ip = 0, iq = 1;
+    float best = -1.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = i + 1; j < 4; ++j) {
+            const float dx = v[j].x - v[i].x, dy = v[j].y - v[i].y;
+            const float d2 = fmaf(dx, dx, dy * dy);
+            if (d2 > best) {
+                best = d2;
+                ip = i;
+                iq = j;
+            }
+        }
+    auto frac = [](float x, float lo, float hi) -> uint32_t {
+        const float e = hi - lo;
+        if (!(e > 0.f)) return 0u;
+        return uint32_t(fminf(fmaxf(rintf((x - lo) / e * 255.0f), 0.f), 255.f));
+    };
+    uint2 code;
+    code.x = frac(v[ip].x, sb.smin, sb.smax) | (frac(v[ip].y, sb.tmin, sb.tmax) << 8) |
+             (frac(v[iq].x, sb.smin, sb.smax) << 16) | (frac(v[iq].y, sb.tmin, sb.tmax) << 24);
+    code.y = 0u;
+    const Capsule c = decode_capsule(sb.smin, sb.tmin, sb.smax, sb.tmax, code);
+    const float L2 = fmaf(c.dx, c.dx, c.dy * c.dy);
+    float w = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float ax = v[k].x - c.px, ay = v[k].y - c.py;
+        float t = L2 > 0.f ? fminf(fmaxf(fmaf(ax, c.dx, ay * c.dy) / L2, 0.f), 1.f) : 0.f;
+        const float ex = fmaf(-t, c.dx, ax), ey = fmaf(-t, c.dy, ay);
+        w = fmaxf(w, sqrtf(fmaf(ex, ex, ey * ey)));
+    }
+    w = fmaf(w, 1.0f + 1.0f / 512.0f, 1.0f / 2097152.0f);
+    code.y = uint32_t(__half_as_ushort(__float2half_ru(w)));
+    return code;
+}
 
 template <int TFMT>
 __device__ __forceinline__ float2 load_texel(const void *t, size_t idx)
@@ -118,17 +175,22 @@ __global__ void __launch_bounds__(kBuildThreads) build_tiles(const void *__restr
         for (int k = 0; k < kLeafQuads * kLeafQuads; ++k) {
             int lx = a * kLeafQuads + int(compact1by1(k)), ly = c * kLeafQuads + int(compact1by1(k >> 1));
             Box qb = empty_box();
+            uint2 cap = make_uint2(0u, 0u);
             if (c0 + lx <= n - 2 && r0 + ly <= n - 2) {
+                float2 tv[4];
 #pragma unroll
                 for (int v = 0; v < 4; ++v) {
-                    float2 t = tex[(ly + (v >> 1)) * kTileTexMax + lx + (v & 1)];
+                    const float2 t = tex[(ly + (v >> 1)) * kTileTexMax + lx + (v & 1)];
+                    tv[v] = t;
                     qb.smin = fminf(qb.smin, t.x);
                     qb.tmin = fminf(qb.tmin, t.y);
                     qb.smax = fmaxf(qb.smax, t.x);
                     qb.tmax = fmaxf(qb.tmax, t.y);
                 }
+                cap = encode_capsule(tv, stored_box<BFMT>(qb));
             }
             store_box<BFMT>(const_cast<void *>(d.lv[0]), qbase + k, qb);
+            const_cast<uint2 *>(d.qcap)[qbase + k] = cap;
             grow(b, qb);
         }
         box[0][tid] = b;

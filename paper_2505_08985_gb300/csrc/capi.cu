@@ -128,6 +128,8 @@ pndf_status pndf_build_hierarchy(const void *texels_dev, const pndf_build_params
     size_t total = up(size_t(d.n) * d.n * texel_b);
     off[0] = total;  // level 0: one box per quad
     total += up(level_nodes(d.L, 0) * node_b);
+    const size_t off_qcap = total;  // and one capsule per quad
+    total += up(level_nodes(d.L, 0) * sizeof(uint2));
     for (int l = kLeafLevel; l <= d.L; ++l) {
         off[l] = total;
         total += up(level_nodes(d.L, l) * node_b);
@@ -156,6 +158,7 @@ pndf_status pndf_build_hierarchy(const void *texels_dev, const pndf_build_params
     char *base = static_cast<char *>(h->mem);
     d.texels = base;
     d.lv[0] = base + off[0];
+    d.qcap = reinterpret_cast<const uint2 *>(base + off_qcap);
     for (int l = kLeafLevel; l <= d.L; ++l) d.lv[l] = base + off[l];
     memset(&h->c, 0, sizeof(h->c));
     h->moments = nullptr;

@@ -31,6 +31,7 @@ struct MapDesc {
     const void *lv[kMaxLevels];  // level 0 (one box per quad) and levels kLeafLevel..L:
                                  // (2^(L-l))^2 nodes each, Morton order
     unsigned int *status;        // this hierarchy's status word (PNDF_QF_* bits OR-ed in on errors)
+    const uint2 *qcap;           // per-quad capsules (level-0 companion, same Morton order)
 };
 
 // Record device-side error bits: in the hierarchy's own word and in the
@@ -133,6 +134,51 @@ __device__ __forceinline__ Box load_box(const void *lv, size_t idx)
         float2 l = __half22float2(lo), h = __half22float2(hi);
         return Box{l.x, l.y, h.x, h.y};
     }
+}
+
+// Per-quad capsule, the level-0 companion of the quad boxes.  A quad's two
+// normal triangles lie in the convex hull of its four normals, and so within
+// distance w of the segment p-q between its two farthest normals (distance to
+// a segment is convex, so its maximum over the hull is at a vertex).  For a
+// quad straddling two flake cells the triangles are long slivers whose box is
+// mostly empty; the capsule is far tighter.  Stored in 8 bytes: p and q as
+// 8-bit fractions of the quad's stored box (x: px, py, qx, qy from the low
+// byte up), w as binary16 in the low half of y, rounded up with a margin that
+// covers FP32 rounding at build and at query time.  Build and query decode
+// with this same function, so both see the same segment.
+struct Capsule {
+    float px, py, dx, dy;  // p and q - p
+    float w;
+};
+
+__device__ __forceinline__ Capsule decode_capsule(float smin, float tmin, float smax, float tmax, uint2 code)
+{
+    const float ex = (smax - smin) * (1.0f / 255.0f), ey = (tmax - tmin) * (1.0f / 255.0f);
+    Capsule c;
+    c.px = fmaf(ex, float(code.x & 255u), smin);
+    c.py = fmaf(ey, float((code.x >> 8) & 255u), tmin);
+    c.dx = fmaf(ex, float((code.x >> 16) & 255u), smin) - c.px;
+    c.dy = fmaf(ey, float(code.x >> 24), tmin) - c.py;
+    c.w = __half2float(__ushort_as_half(static_cast<unsigned short>(code.y & 0xffffu)));
+    return c;
+}
+
+// Distance from (mx, my) to the capsule's segment, squared and compared with
+// r^2 without a division: beyond either end the distance to that end,
+// between them the perpendicular distance (cross^2 <= r^2 |d|^2).
+__device__ __forceinline__ bool capsule_holds(const Capsule &c, float mx, float my, float r)
+{
+    const float ax = mx - c.px, ay = my - c.py;
+    const float t = fmaf(ax, c.dx, ay * c.dy);
+    const float L2 = fmaf(c.dx, c.dx, c.dy * c.dy);
+    const float r2 = r * r;
+    if (t <= 0.f) return fmaf(ax, ax, ay * ay) <= r2;
+    if (t >= L2) {
+        const float bx = ax - c.dx, by = ay - c.dy;
+        return fmaf(bx, bx, by * by) <= r2;
+    }
+    const float cr = fmaf(ax, c.dy, -ay * c.dx);
+    return cr * cr <= r2 * L2;
 }
 
 __host__ __device__ inline size_t level_nodes(int L, int l)

@@ -21,7 +21,11 @@
 //               survivors.  Surviving leaf blocks (4 x 4 quads) have their 16
 //               per-quad boxes (level 0, one 128-byte line in FP16) tested four
 //               per lane in one load, eight blocks per pass; quads whose box
-//               holds m are compacted into a per-warp ring and tested 32 at a
+//               holds m are compacted into a per-warp ring and taken 64 at a
+//               time (two per lane, both loads in flight) through the quad's
+//               capsule (segment between its farthest normals plus a radius,
+//               the tight bound for slivers across normal discontinuities);
+//               capsule survivors are compacted again and tested 32 at a
 //               time (lane = quad, both triangles), and edge-test hits are
 //               compacted once more and weighed 32 at a time.  The query's
 //               sum is reduced across the warp and written in caller order
@@ -48,7 +52,10 @@ constexpr int kStackCap = 768;     // DFS stack entries per warp (about 48 per l
 constexpr int kMaxSubBits = 14;                   // sub-key bits below the 4 entry-level bits
 constexpr int kKeyBins = 1 << (4 + kMaxSubBits);  // largest histogram (2^18 bins)
 #ifndef PNDF_TRAVERSE_MIN_CTAS
-#define PNDF_TRAVERSE_MIN_CTAS 4     // 4 x 256 threads per SM at <= 64 registers (measured faster than 3)
+// 3 x 256 threads per SM at <= 85 registers: with two capsule tests per lane
+// in flight this measured 916 ms per 4M-query flake step, against 1008 ms at
+// 4 CTAs (64 registers, more spills) and 1154 ms at 2
+#define PNDF_TRAVERSE_MIN_CTAS 3
 #endif
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -529,26 +536,31 @@ __device__ __forceinline__ void test_leaf(const MapDesc &d, const Query &q, uint
 
 // Survivor ring: quads whose level-0 box holds m, packed (i << 16) | j.
 constexpr int kRing = 256;
+// Capsule ring: box survivors whose capsule holds m too (at most 31 held
+// over between rounds plus one round's 32).
+constexpr int kCapRing = 64;
 // Leaf queue: up to 7 leaf blocks held over from the last step plus one
 // step's 64 children; cut cluster nodes fill it from the back (entry k at
 // kLeafQ - 1 - k), and a step's new leaf blocks and cut nodes number at most
 // 64 together, so the two ends never meet.
 constexpr int kLeafQ = 72;
-// Shared memory per warp: DFS stack, leaf queue, survivor ring, hit ring
-// (a multiple of four words, so the hit ring stays 16-byte aligned).
-constexpr int kWarpSmemWords = kStackCap + kLeafQ + kRing + 4 * kHitRing;
-static_assert((kStackCap + kLeafQ + kRing) % 4 == 0, "hit ring alignment");
+// Shared memory per warp: DFS stack, leaf queue, survivor ring, capsule
+// ring, hit ring (a multiple of four words, so the hit ring stays 16-byte
+// aligned).
+constexpr int kWarpSmemWords = kStackCap + kLeafQ + kRing + kCapRing + 4 * kHitRing;
+static_assert((kStackCap + kLeafQ + kRing + kCapRing) % 4 == 0, "hit ring alignment");
 
-// Per-warp leaf state: survivor-quad ring and hit ring with their heads/counts.
+// Per-warp leaf state: box-survivor ring, capsule-survivor ring and hit ring
+// with their heads and counts.
 struct LeafState {
-    uint32_t *ring;
+    uint32_t *ring, *cring;
     float4 *hits;
-    uint32_t head, hh;
-    int nsq, nh;
+    uint32_t head, chead, hh;
+    int nsq, ncq, nh;
 };
 
-// All 32 lanes: lane k tests both triangles of survivor quad k (k < cnt) of
-// the ring, (u0, u1, u2) and (u3, u2, u1), its four texels loaded together;
+// All 32 lanes: lane k tests both triangles of capsule survivor k (k < cnt)
+// of the capsule ring, (u0, u1, u2) and (u3, u2, u1), its four texels loaded together;
 // hits are compacted into the hit ring and weighed 32 at a time.
 template <int TFMT, bool STATS, bool CLAMP>
 __device__ __forceinline__ void test_quads(const MapDesc &d, const Query &q, LeafState &ls, int cnt, int lane,
@@ -558,7 +570,7 @@ __device__ __forceinline__ void test_quads(const MapDesc &d, const Query &q, Lea
     bool h0 = false, h1 = false;
     float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
     if (lane < cnt) {
-        uint32_t pk = ls.ring[(ls.head + uint32_t(lane)) & (kRing - 1)];
+        uint32_t pk = ls.cring[(ls.chead + uint32_t(lane)) & (kCapRing - 1)];
         int gi = int(pk >> 16), gj = int(pk & 0xffffu);
         float2 n0 = texel<TFMT>(d, gi, gj), n1 = texel<TFMT>(d, gi + 1, gj);
         float2 n2 = texel<TFMT>(d, gi, gj + 1), n3 = texel<TFMT>(d, gi + 1, gj + 1);
@@ -721,6 +733,60 @@ __device__ __forceinline__ unsigned quad_boxes_hold(const MapDesc &d, uint32_t f
     return bits;
 }
 
+// A stored node box decoded to (s_min, t_min, s_max, t_max).
+template <int BFMT>
+__device__ __forceinline__ float4 box_floats(const uint4 &v)
+{
+    if (BFMT == PNDF_BOUNDS_F32)
+        return make_float4(__uint_as_float(v.x), __uint_as_float(v.y), __uint_as_float(v.z), __uint_as_float(v.w));
+    float2 lo = __half22float2(*reinterpret_cast<const __half2 *>(&v.x));
+    float2 hi = __half22float2(*reinterpret_cast<const __half2 *>(&v.y));
+    return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+
+// All 32 lanes: lane k takes box survivors k and k + 32 of the ring (those
+// below cnt <= 64; both quads' boxes and capsule codes are loaded before
+// either is used), tests m against each quad's capsule, and the survivors
+// are compacted into the capsule ring, whose quads are tested 32 at a time.
+template <int BFMT, int TFMT, bool STATS, bool CLAMP>
+__device__ __forceinline__ void capsule_round(const MapDesc &d, const Query &q, LeafState &ls, int cnt, int lane,
+                                              Acc &acc)
+{
+    const unsigned lt = (1u << lane) - 1u;
+    bool pass[2] = {false, false};
+    uint32_t pk[2] = {0u, 0u};
+    uint4 bx[2];
+    uint2 code[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+        if (lane + 32 * r < cnt) {
+            pk[r] = ls.ring[(ls.head + uint32_t(lane + 32 * r)) & (kRing - 1)];
+            const uint32_t mq = morton2(pk[r] >> 16, pk[r] & 0xffffu);
+            bx[r] = node_box<BFMT>(d, 0, mq);
+            code[r] = __ldg(d.qcap + mq);
+        }
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+        if (lane + 32 * r < cnt) {
+            const float4 b = box_floats<BFMT>(bx[r]);
+            const Capsule c = decode_capsule(b.x, b.y, b.z, b.w, code[r]);
+            pass[r] = capsule_holds(c, q.mx, q.my, CLAMP ? c.w + q.rho : c.w);
+        }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const unsigned m = __ballot_sync(kFull, pass[r]);
+        if (pass[r]) ls.cring[(ls.chead + uint32_t(ls.ncq) + __popc(m & lt)) & (kCapRing - 1)] = pk[r];
+        ls.ncq += __popc(m);
+        __syncwarp();
+        if (ls.ncq >= 32) {
+            test_quads<TFMT, STATS, CLAMP>(d, q, ls, 32, lane, acc);
+            ls.chead += 32;
+            ls.ncq -= 32;
+            __syncwarp();
+        }
+    }
+}
+
 // All 32 lanes: filter the queued leaf blocks' quads by their level-0 boxes
 // (lane t: quads 4 (t & 3) .. 4 (t & 3) + 3 of block p + (t >> 2), eight
 // blocks per pass), compact the survivors into the ring with ballot/popc and
@@ -757,10 +823,10 @@ __device__ __forceinline__ void process_leaves(const MapDesc &d, const Query &q,
             ls.nsq += __popc(m);
         }
         __syncwarp();
-        while (ls.nsq >= 32) {
-            test_quads<TFMT, STATS, CLAMP>(d, q, ls, 32, lane, acc);
-            ls.head += 32;
-            ls.nsq -= 32;
+        while (ls.nsq >= 64) {
+            capsule_round<BFMT, TFMT, STATS, CLAMP>(d, q, ls, 64, lane, acc);
+            ls.head += 64;
+            ls.nsq -= 64;
             __syncwarp();
         }
     }
@@ -862,7 +928,7 @@ __device__ void eval_one(const MapDesc &d, const ClusterDesc &cd, float tau, flo
             __syncwarp();
         }
         bool overflow = false;
-        LeafState ls{ring, hits, 0u, 0u, 0, 0};
+        LeafState ls{ring, ring + kRing, hits, 0u, 0u, 0u, 0, 0, 0};
         while (true) {
             // leaf blocks are filtered eight to a pass (four lanes each): while
             // the stack still holds nodes only whole passes run, and the rest
@@ -950,7 +1016,8 @@ __device__ void eval_one(const MapDesc &d, const ClusterDesc &cd, float tau, flo
             }
             __syncwarp();
         }
-        if (ls.nsq > 0) test_quads<TFMT, STATS, CLAMP>(d, q, ls, ls.nsq, lane, acc);  // nsq < 32 here
+        if (ls.nsq > 0) capsule_round<BFMT, TFMT, STATS, CLAMP>(d, q, ls, ls.nsq, lane, acc);  // nsq < 64 here
+        if (ls.ncq > 0) test_quads<TFMT, STATS, CLAMP>(d, q, ls, ls.ncq, lane, acc);  // ncq < 32 here
         if (ls.nh > 0) drain_hits<STATS>(q, d.n, d.L, ls.hits, ls.hh, ls.nh, lane, acc);  // nh < 32 here
         if (overflow) acc.flags |= PNDF_QF_OVERFLOW;
     }
@@ -1000,7 +1067,7 @@ __global__ void __launch_bounds__(256, PNDF_TRAVERSE_MIN_CTAS)
     uint32_t *stk = smem + warp * kWarpSmemWords;
     uint32_t *lq = stk + kStackCap;
     uint32_t *ring = lq + kLeafQ;
-    float4 *hits = reinterpret_cast<float4 *>(ring + kRing);
+    float4 *hits = reinterpret_cast<float4 *>(ring + kRing + kCapRing);
     while (true) {
         unsigned long long k = 0;
         if (lane == 0) k = atomicAdd(cursor, 1ull);
@@ -1320,7 +1387,7 @@ __global__ void __launch_bounds__(256, PNDF_TRAVERSE_MIN_CTAS)
     uint32_t *stk = smem + warp * kWarpSmemWords;
     uint32_t *lq = stk + kStackCap;
     uint32_t *ring = lq + kLeafQ;
-    float4 *hits = reinterpret_cast<float4 *>(ring + kRing);
+    float4 *hits = reinterpret_cast<float4 *>(ring + kRing + kCapRing);
     const int nsegs = int(table[0]);
     const uint32_t *prefix = table + 1;
     const uint32_t total = prefix[nsegs];

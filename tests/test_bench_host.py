@@ -5,6 +5,7 @@ and that ncu census counts are used only for the sources they were taken on."""
 import os
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -34,7 +35,8 @@ def test_pyramid_counts(bench):
         assert bench.tree_nodes(n) == nodes
         assert bench.leaf_blocks(n) == (1 << (L - 2)) ** 2
         # map read + copy written (8 B per FP32 texel each) + level 0 and levels 2..L (8 B boxes)
-        assert bench.pyramid_bytes(n, 8, 8) == 16 * n * n + 8 * ((1 << L) ** 2 + nodes)
+        # + one 8 B capsule per quad
+        assert bench.pyramid_bytes(n, 8, 8) == 16 * n * n + 8 * ((1 << L) ** 2 + nodes) + 8 * (1 << L) ** 2
 
 
 def test_family_roofline_picks_the_binding_resource(bench):
@@ -75,3 +77,47 @@ def test_source_hash_follows_code_not_comments(bench, tmp_path, monkeypatch):
     assert bench.sources_hash(["k.cu"]) == h0
     (d / "k.cu").write_text("// kernel (Sec. 2)\n__global__ void k(float *x) { x[0] = 2.0f; }\n")
     assert bench.sources_hash(["k.cu"]) != h0
+
+
+def test_traversal_roofline_follows_the_survey_byte_model(bench, monkeypatch):
+    """roofline.frac is reproducible from the stats counts: HBM on nodes x 8 B
+    + leaf blocks x 25 texels x 8 B + 36 B per query; with a committed
+    instruction count the issue fraction is computed beside it and `bound`
+    names the larger one."""
+    monkeypatch.setattr(bench, "compute_peaks", lambda dev: {"issue": 1000.0, "fp32": 80.0, "fp64": 1.25,
+                                                             "sms": 152, "sm_mhz": 2070.0})
+    monkeypatch.setattr(bench, "hbm_peak", lambda: (6000.0, "measured"))
+    monkeypatch.setattr(bench, "committed_traffic", lambda tag: None)
+    monkeypatch.setattr(bench, "committed_ncu_pct", lambda tag: None)
+    w = {"nodes": 1000, "leaf_blocks": 200, "bytes": 99999, "quads": 3200, "tri_tests": 50, "hits": 5}
+    monkeypatch.setattr(bench, "committed_profile_value", lambda key: None)
+    r = bench.traversal_roofline(None, w, nq=10, kernel_ms=2.0, world=1)
+    nbytes = 1000 * 8 + 200 * 25 * 8 + 36 * 10
+    assert r["hbm"]["algorithmic_bytes_per_launch"] == nbytes
+    assert r["bound"] == "hbm" and r["issue"] is None
+    assert abs(r["frac"] - nbytes / 2e-3 / 1e9 / 6000.0) < 1e-15
+    assert r["builder_byte_model"]["bytes_per_launch"] == 99999
+    monkeypatch.setattr(bench, "committed_profile_value", lambda key: 1e5 if key == "warp_inst_per_query_f16" else None)
+    r = bench.traversal_roofline(None, w, nq=10, kernel_ms=2.0, world=1)
+    assert r["bound"] == "alu" and r["unit"] == "G warp-instructions/s"
+    assert abs(r["frac"] - 1e5 * 10 / 2e-3 / 1e9 / 1000.0) < 1e-12
+    assert r["hbm"]["frac"] < r["frac"]
+
+
+def test_sigma_strata_draws_per_octave(bench):
+    import torch
+    rng = np.random.default_rng(0)
+    sig = np.exp(rng.uniform(0, np.log(64), 5000))
+    q = torch.zeros(5000, 8)
+    q[:, 2] = torch.from_numpy(sig ** 2)
+    q[:, 4] = torch.from_numpy(sig ** 2)
+    idx = bench.sigma_strata(q, np.exp2(np.arange(7)), [50] * 6, seed=1)
+    assert idx.size == 300 and np.unique(idx).size == 300
+    counts = np.histogram(np.sqrt(q[idx, 2].double().numpy()), bins=np.exp2(np.arange(7)))[0]
+    assert (counts == 50).all()
+
+
+def test_both_arms_name_the_same_workload(bench):
+    a = bench.workload_config(8192, 1 << 22, 1)
+    assert a["workload"] == bench.WORKLOAD and a["queries_per_gpu"] == 1 << 22
+    assert set(a) == set(bench.workload_config(4096, 10, 2))

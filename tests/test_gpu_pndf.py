@@ -109,6 +109,43 @@ def test_hierarchy_prunes_only(P):
     assert sh[:, 2].sum() < 0.5 * sf[:, 2].sum()
 
 
+@pytest.mark.parametrize("bounds", [0, 1])
+def test_quad_capsules_prune_only(P, bounds):
+    """The per-quad capsule (segment between the quad's farthest normals plus
+    a radius) only prunes: with query normals placed exactly on texel normals,
+    on midpoints of quad edges and diagonals, and on the farthest points of
+    the triangles (the cases where a capsule rounded too tightly would drop a
+    hit), the pyramid traversal hits exactly the triangles the flat scan hits.
+    Flake cells (long slivers across cell borders), bumps and scratches."""
+    rng = np.random.default_rng(31)
+    maps = [synth.flake_normals(256, 700, seed=31), synth.bumps_map(n=192, n_bumps=30, seed=32),
+            synth.scratch_map(n=192, n_grooves=60, seed=33)]
+    for st in maps:
+        n = st.shape[0]
+        nq = 3000
+        i = rng.integers(0, n - 1, nq)
+        j = rng.integers(0, n - 1, nq)
+        stn = st.double().numpy()
+        v = [stn[j, i], stn[j, i + 1], stn[j + 1, i], stn[j + 1, i + 1]]
+        kind = rng.integers(0, 4, nq)
+        a, b = rng.integers(0, 4, nq), rng.integers(0, 4, nq)
+        pa = np.stack(v, 0)[a, np.arange(nq)]
+        pb = np.stack(v, 0)[b, np.arange(nq)]
+        m = np.where((kind == 0)[:, None], pa, 0.5 * (pa + pb))  # a vertex or a midpoint of two
+        m = np.where((kind == 3)[:, None], pa + 1e-7 * rng.normal(size=(nq, 2)), m)
+        m = m.astype(np.float32).astype(np.float64)
+        x = i + rng.uniform(-2, 3, nq)
+        y = j + rng.uniform(-2, 3, nq)
+        sg = rng.uniform(0.8, 6.0, nq)
+        q = torch.from_numpy(np.stack([x, y, sg * sg, np.zeros(nq), sg * sg, m[:, 0], m[:, 1], np.zeros(nq)],
+                                      1).astype(np.float32))
+        Dh, _, sh = run(P, st, q, mode=0, bounds=bounds)
+        Df, _, sf = run(P, st, q, mode=1, bounds=bounds)
+        assert (sf[:, 3] > 0).mean() > 0.5
+        assert np.array_equal(sh[:, 3], sf[:, 3]) and np.array_equal(sh[:, 4], sf[:, 4])
+        assert rel_err(Dh, Df).max() <= 1e-5
+
+
 def test_fp16_outward_bounds_keep_hit_sets(P):
     """FP16 bounds rounded outward only prune less: hit sets are identical to
     FP32 bounds and D agrees to summation-order rounding."""
