@@ -60,12 +60,16 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the error against the FP64 oracle per workload")
+    ap.add_argument("--strong", action="store_true",
+                    help="under torchrun: shard one batch of --queries over the ranks (strong scaling) instead of "
+                         "one batch per rank")
     ap.add_argument("--kernels", default="disk,box", help="footprint kernels to measure besides the Gaussian ('' = skip)")
     ap.add_argument("--no-clamp-sampling", action="store_true", help="skip the Eq. 6 clamp and sampling figures")
     ap.add_argument("--cluster-taus", default="1e-4,1e-3",
                     help="cluster cut thresholds to measure on the same workload ('' = skip)")
     ap.add_argument("--serve-batches", type=int, default=2000, help="serving workload size (0 = skip serving)")
     ap.add_argument("--serve-load", type=float, default=0.8, help="offered load, fraction of plain FP32 capacity")
+    ap.add_argument("--serve-streams", type=int, default=2, help="streams the served steps alternate over")
     ap.add_argument("--serve-sweep", default="0.5,0.95",
                     help="further offered loads for the latency sweep ('' = skip)")
     ap.add_argument("--mixed-requests", type=int, default=4096,
@@ -649,68 +653,77 @@ def run_mixed(args, dev):
 # ---------------------------------------------------------------------------
 
 def run_serving(args, dev):
+    """Served FP16 path (continuous batching over graph-replayed persistent
+    steps) against the plain FP32 per-batch path, on the four-map camera
+    stream and on the same stream with every batch on the 8192^2 flake map.
+    The plain path runs both with the library's default per-batch sort and
+    with each batch in arrival (pixel) order, at every offered load."""
     from paper_2505_08985_gb300 import pndf, serve
 
     sts = synth.serving_maps(device=dev)
     batches = synth.serving_batches(args.serve_batches, seed=9)
-    qs = [synth.camera_queries(sts[m].shape[0], n, seed=sd, device=dev) for (m, n, sd) in batches]
-    h16 = [pndf.pndf_build_hierarchy(st, bounds_fmt=pndf.PNDF_BOUNDS_F16_OUTWARD) for st in sts]
-    h32 = [pndf.pndf_build_hierarchy(st, bounds_fmt=pndf.PNDF_BOUNDS_F32) for st in sts]
-    torch.cuda.synchronize()
-
-    def requests(arrivals):
-        return [serve.Request(rid=k, map=batches[k][0], queries=qs[k], arrival=a) for k, a in enumerate(arrivals)]
-
     n = len(batches)
-    total = sum(b[1] for b in batches)
+    loads = [args.serve_load] + [float(x) for x in args.serve_sweep.split(",") if x.strip()]
     t0 = time.perf_counter()
-    plain_cap = serve.run_plain(h32, requests([0.0] * n), realtime=False)
-    rate = args.serve_load * plain_cap["queries_per_s"] / (total / n)
-    # autotune on the first batches of the stream at the target load
-    ns = min(n, 300)
-    sample = requests([0.0] * ns)
-    tune = serve.autotune(h16, sample, arrivals=serve.poisson_arrivals(ns, rate, seed=5))
-    batcher = serve.ContinuousBatcher(h16, step_queries=tune.step_queries, warps_per_cta=tune.warps_per_cta,
-                                      ctas_per_sm=tune.ctas_per_sm, sort=tune.sort)
-    served_cap = batcher.run(requests([0.0] * n), realtime=False)
-    arrivals = serve.poisson_arrivals(n, rate, seed=17)
-    served = batcher.run(requests(arrivals), realtime=True)
-    steps = batcher.steps
-    plain = serve.run_plain(h32, requests(arrivals), realtime=True)
-    # the same stream at other offered loads (same tuned batcher)
-    sweep = []
-    for load in [float(x) for x in args.serve_sweep.split(",") if x.strip()]:
-        r = load * plain_cap["queries_per_s"] / (total / n)
-        arr = serve.poisson_arrivals(n, r, seed=17)
-        sv = batcher.run(requests(arr), realtime=True)
-        pl = serve.run_plain(h32, requests(arr), realtime=True)
-        sweep.append({"load": load, "batches_per_s": r,
-                      "served_fp16": {k: sv[k] for k in ("p50_ms", "p99_ms", "queries_per_s")},
-                      "plain_fp32": {k: pl[k] for k in ("p50_ms", "p99_ms", "queries_per_s")}})
-    batcher.close()
-    # context: the plain path with each batch kept in arrival order (no sort)
-    plain_unsorted_cap = serve.run_plain(h32, requests([0.0] * n), realtime=False, sort=pndf.PNDF_SORT_NONE)
-    for h in h16 + h32:
-        h.free()
-    del qs
-    keep = ("p50_ms", "p99_ms", "mean_ms", "queries_per_s", "span_s")
-    return {
-        "workload": "4 resident maps (1024^2 bumps, 2048^2 scratches, 4096^2 and 8192^2 flakes); "
-                    f"{n} camera batches, sizes log-U(1K, 1M), {total} queries; Poisson arrivals at "
-                    f"{args.serve_load:g} x plain FP32 capacity ({rate:.1f} batches/s)",
-        "served_fp16": {k: served[k] for k in keep},
-        "plain_fp32": {k: plain[k] for k in keep},
-        "load_sweep": sweep,
-        "capacity_queries_per_s": {"served_fp16": served_cap["queries_per_s"],
-                                   "plain_fp32": plain_cap["queries_per_s"],
-                                   "plain_fp32_unsorted": plain_unsorted_cap["queries_per_s"]},
-        "autotune": {"objective": "lowest p99 on the first batches at the target load",
-                     "step_queries": tune.step_queries, "warps_per_cta": tune.warps_per_cta,
-                     "ctas_per_sm": tune.ctas_per_sm, "sort": tune.sort,
-                     "table [step, ctas_per_sm, warps, sort, p99_ms, q/s]": tune.table},
-        "steps_last_run": steps,
-        "wall_s": time.perf_counter() - t0,
-    }
+
+    def stream(map_of, label):
+        qs = [synth.camera_queries(sts[map_of(m)].shape[0], sz, seed=sd, device=dev) for (m, sz, sd) in batches]
+        used = sorted({map_of(m) for (m, _, _) in batches})
+        h16 = {i: pndf.pndf_build_hierarchy(sts[i], bounds_fmt=pndf.PNDF_BOUNDS_F16_OUTWARD) for i in used}
+        h32 = {i: pndf.pndf_build_hierarchy(sts[i], bounds_fmt=pndf.PNDF_BOUNDS_F32) for i in used}
+        slot = {i: k for k, i in enumerate(used)}
+        l16 = [h16[i] for i in used]
+        l32 = [h32[i] for i in used]
+        torch.cuda.synchronize()
+
+        def requests(arrivals):
+            return [serve.Request(rid=k, map=slot[map_of(batches[k][0])], queries=qs[k], arrival=a)
+                    for k, a in enumerate(arrivals)]
+
+        total = sum(b[1] for b in batches)
+        cap_sorted = serve.run_plain(l32, requests([0.0] * n), realtime=False)
+        cap_unsorted = serve.run_plain(l32, requests([0.0] * n), realtime=False, sort=pndf.PNDF_SORT_NONE)
+        rate = args.serve_load * cap_sorted["queries_per_s"] / (total / n)
+        ns = min(n, 300)
+        tune = serve.autotune(l16, requests([0.0] * ns), arrivals=serve.poisson_arrivals(ns, rate, seed=5),
+                              streams=args.serve_streams)
+        batcher = serve.ContinuousBatcher(l16, step_queries=tune.step_queries, warps_per_cta=tune.warps_per_cta,
+                                          ctas_per_sm=tune.ctas_per_sm, sort=tune.sort, streams=args.serve_streams)
+        served_cap = batcher.run(requests([0.0] * n), realtime=False)
+        keep = ("p50_ms", "p99_ms", "mean_ms", "queries_per_s")
+        runs = []
+        for load in loads:
+            r = load * cap_sorted["queries_per_s"] / (total / n)
+            arr = serve.poisson_arrivals(n, r, seed=17)
+            sv = batcher.run(requests(arr), realtime=True)
+            steps = batcher.steps
+            pl = serve.run_plain(l32, requests(arr), realtime=True)
+            pu = serve.run_plain(l32, requests(arr), realtime=True, sort=pndf.PNDF_SORT_NONE)
+            runs.append({"load": load, "batches_per_s": r,
+                         "served_fp16": {k: sv[k] for k in keep},
+                         "plain_fp32_sorted": {k: pl[k] for k in keep},
+                         "plain_fp32_unsorted": {k: pu[k] for k in keep}})
+        batcher.close()
+        for h in list(h16.values()) + list(h32.values()):
+            h.free()
+        caps = {"served_fp16": served_cap["queries_per_s"], "plain_fp32_sorted": cap_sorted["queries_per_s"],
+                "plain_fp32_unsorted": cap_unsorted["queries_per_s"]}
+        best_plain = max(caps["plain_fp32_sorted"], caps["plain_fp32_unsorted"])
+        return {"workload": f"{label}; {n} camera batches, sizes log-U(1K, 1M), {total} queries; Poisson arrivals, "
+                            "offered load as a fraction of the sorted plain FP32 capacity",
+                "loads": runs,
+                "capacity_queries_per_s": caps,
+                "served_over_best_plain_capacity": caps["served_fp16"] / best_plain,
+                "autotune": {"objective": f"lowest p99 on the first {ns} batches at load {args.serve_load:g}",
+                             "step_queries": tune.step_queries, "warps_per_cta": tune.warps_per_cta,
+                             "ctas_per_sm": tune.ctas_per_sm, "sort": tune.sort,
+                             "table [step, ctas_per_sm, warps, sort, p99_ms, q/s]": tune.table}}
+
+    out = {"four_maps": stream(lambda m: m, "4 resident maps (1024^2 bumps, 2048^2 scratches, 4096^2 and 8192^2 "
+                                            "flakes), each batch on a random one"),
+           "flake8192_only": stream(lambda m: 3, "every batch on the 8192^2 flake map")}
+    out["wall_s"] = time.perf_counter() - t0
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -1218,6 +1231,69 @@ def kernel_rooflines(dev, n, nq, stage_ms, traverse_ms, traverse_roof, cluster, 
     return out
 
 
+def run_strong(args, world, rank, local):
+    """Strong scaling: one batch of --queries sharded over the ranks.  Every
+    rank holds a replica of the hierarchy and the same seeded batch; per step
+    rank 0 sorts the batch, splits the order into contiguous ranges of equal
+    estimated work and broadcasts the order and the bounds; each rank gathers
+    and evaluates its range in that order; the shards are all-gathered and
+    rank 0 scatters them into caller order.  The timed step includes all of
+    it; value = the batch's queries / the step time (max over ranks)."""
+    import torch.distributed as dist
+    from paper_2505_08985_gb300 import pndf, shard
+
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    st, q = make_workload(args, dev, 0)  # the same batch on every rank
+    nq = q.shape[0]
+    h = pndf.pndf_build_hierarchy(st, bounds_fmt=pndf.PNDF_BOUNDS_F16_OUTWARD)
+    out = torch.empty(nq, dtype=torch.float32, device=dev)
+    order = torch.empty(nq, dtype=torch.int32, device=dev)
+    block = shard.work_block(nq, world)
+
+    def step():
+        bounds_t = torch.zeros(world + 1, dtype=torch.int64, device=dev)
+        if rank == 0:
+            pndf.pndf_sort_queries(h, q, order)
+            parts = pndf.pndf_shard_work(q, order, block=block).cpu().tolist()
+            bounds_t.copy_(torch.tensor(shard.split_by_work(parts, world, nq, block)))
+        dist.broadcast(order, 0)
+        dist.broadcast(bounds_t, 0)
+        bounds = bounds_t.cpu().tolist()
+        a, b = bounds[rank], bounds[rank + 1]
+        qi = pndf.pndf_gather_queries(q, order, a, b - a)
+        Di = pndf.pndf_eval_batch_ex(h, qi, sort=pndf.PNDF_SORT_NONE)
+        allD = shard.gather_shards(Di, bounds, rank, world)
+        if rank == 0:
+            for i in range(world):
+                pndf.pndf_scatter_results(allD[bounds[i] - bounds[0]:bounds[i + 1] - bounds[0]].contiguous(), order,
+                                          bounds[i], out)
+        return bounds
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(args.steps):
+        bounds = step()
+    t1.record()
+    torch.cuda.synchronize()
+    ms = max_over_ranks(world, t0.elapsed_time(t1)) / args.steps
+    if rank == 0:
+        ref = pndf.pndf_eval_batch(h, q)
+        assert torch.equal(ref, out), "sharded result differs from one batch"
+        cfg = workload_config(args.n, nq, world)
+        cfg["parallelism"] = f"one batch sharded over {world} replicas"
+        print(json.dumps({"metric": METRIC, "value": nq / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                          "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                          "config": cfg, "shard_bounds": bounds}), flush=True)
+    h.free()
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
@@ -1231,7 +1307,10 @@ def main():
         else:
             if not torch.cuda.is_available():
                 raise SystemExit("bench.py: no CUDA device (the GPU arm has no CPU fallback)")
-            run_gpu(args, world, rank, local)
+            if args.strong and world > 1:
+                run_strong(args, world, rank, local)
+            else:
+                run_gpu(args, world, rank, local)
     finally:
         if world > 1:
             import torch.distributed as dist

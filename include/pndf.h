@@ -370,6 +370,43 @@ pndf_status pndf_sort_queries(const pndf_hierarchy *h, const pndf_query *q_dev, 
                               void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Sharding one batch over hierarchy replicas.
+ *
+ * Queries are independent and a hierarchy is read-only (Sec. 4.2, Eq. 5), so
+ * one batch can be split over replicas of the hierarchy (one per device, or
+ * several on one device): put the batch in evaluation order once
+ * (pndf_sort_queries), cut that order into contiguous ranges of about equal
+ * estimated work (pndf_shard_work's per-block sums), gather each range's
+ * records into a contiguous array for its replica (pndf_gather_queries),
+ * evaluate it there in the given order (pndf_eval_batch_ex with
+ * PNDF_SORT_NONE), and scatter the results back into caller order
+ * (pndf_scatter_results).  Each query's D is the same whichever shard, batch
+ * or launch evaluates it.  These calls move data only; they take device
+ * pointers of the current device and run asynchronously on stream.
+ * ------------------------------------------------------------------------- */
+
+/* Estimated work of the evaluation order in blocks of `block` positions:
+ * partial_out_dev[b] = sum over positions k in [b block, (b + 1) block) of
+ * 64 + 64 sigma_x sigma_y for query order_dev[k] (the area of its 4-sigma box
+ * in texel^2 plus a fixed descent cost; invalid covariances count 64).
+ *   order_dev:       device, nq uint32 (a permutation from pndf_sort_queries)
+ *   partial_out_dev: device, ceil(nq / block) doubles
+ * Errors: INVALID_ARG (null or misaligned pointers, nq < 0, block outside
+ * 256..2^20), CUDA. */
+pndf_status pndf_shard_work(const pndf_query *q_dev, const uint32_t *order_dev, int64_t nq, int32_t block,
+                            double *partial_out_dev, void *stream);
+
+/* q_out_dev[k] = q_dev[order_dev[first + k]] for k < count: one range of the
+ * evaluation order as a contiguous batch.  Errors: INVALID_ARG, CUDA. */
+pndf_status pndf_gather_queries(const pndf_query *q_dev, const uint32_t *order_dev, int64_t first, int64_t count,
+                                pndf_query *q_out_dev, void *stream);
+
+/* D_out_dev[order_dev[first + k]] = D_shard_dev[k] for k < count: a range's
+ * results put back in caller order.  Errors: INVALID_ARG, CUDA. */
+pndf_status pndf_scatter_results(const float *D_shard_dev, const uint32_t *order_dev, int64_t first, int64_t count,
+                                 float *D_out_dev, void *stream);
+
+/* ---------------------------------------------------------------------------
  * Serving: continuous batching over several resident hierarchies.
  *
  * A server holds a table of hierarchies (same texel and bounds formats) and

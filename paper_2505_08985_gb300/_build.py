@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libpndf.so")
-SOURCES = ["build.cu", "cluster.cu", "eval.cu", "projarea.cu", "sample.cu", "serve.cu", "capi.cu"]
+SOURCES = ["build.cu", "cluster.cu", "eval.cu", "projarea.cu", "sample.cu", "serve.cu", "shard.cu", "capi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

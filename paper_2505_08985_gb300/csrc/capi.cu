@@ -9,6 +9,7 @@
 
 #include "common.cuh"
 #include "ggx.cuh"
+#include "shard.cuh"
 
 using namespace pndf;
 
@@ -415,6 +416,44 @@ pndf_status pndf_diffuse_projected_area(const pndf_hierarchy *h, const pndf_quer
     if (nq > 0 && (!q_dev || !omega_dev || !P_out_dev)) return PNDF_ERR_INVALID_ARG;
     if (q_dev && !aligned(q_dev, 16)) return PNDF_ERR_INVALID_ARG;
     return launch_projarea(h, q_dev, omega_dev, nq, P_out_dev, as_stream(stream));
+}
+
+pndf_status pndf_shard_work(const pndf_query *q_dev, const uint32_t *order_dev, int64_t nq, int32_t block,
+                            double *partial_out_dev, void *stream)
+{
+    if (nq < 0 || block < 256 || block > (1 << 20)) return PNDF_ERR_INVALID_ARG;
+    if (nq == 0) return PNDF_OK;
+    if (!q_dev || !order_dev || !partial_out_dev || !aligned(q_dev, 16) || !aligned(order_dev, 4) ||
+        !aligned(partial_out_dev, 8))
+        return PNDF_ERR_INVALID_ARG;
+    return launch_shard_work(q_dev, order_dev, nq, block, partial_out_dev, as_stream(stream)) == cudaSuccess
+               ? PNDF_OK
+               : PNDF_ERR_CUDA;
+}
+
+pndf_status pndf_gather_queries(const pndf_query *q_dev, const uint32_t *order_dev, int64_t first, int64_t count,
+                                pndf_query *q_out_dev, void *stream)
+{
+    if (first < 0 || count < 0) return PNDF_ERR_INVALID_ARG;
+    if (count == 0) return PNDF_OK;
+    if (!q_dev || !order_dev || !q_out_dev || !aligned(q_dev, 16) || !aligned(order_dev, 4) || !aligned(q_out_dev, 16))
+        return PNDF_ERR_INVALID_ARG;
+    return launch_gather_queries(q_dev, order_dev, first, count, q_out_dev, as_stream(stream)) == cudaSuccess
+               ? PNDF_OK
+               : PNDF_ERR_CUDA;
+}
+
+pndf_status pndf_scatter_results(const float *D_shard_dev, const uint32_t *order_dev, int64_t first, int64_t count,
+                                 float *D_out_dev, void *stream)
+{
+    if (first < 0 || count < 0) return PNDF_ERR_INVALID_ARG;
+    if (count == 0) return PNDF_OK;
+    if (!D_shard_dev || !order_dev || !D_out_dev || !aligned(D_shard_dev, 4) || !aligned(order_dev, 4) ||
+        !aligned(D_out_dev, 4))
+        return PNDF_ERR_INVALID_ARG;
+    return launch_scatter_results(D_shard_dev, order_dev, first, count, D_out_dev, as_stream(stream)) == cudaSuccess
+               ? PNDF_OK
+               : PNDF_ERR_CUDA;
 }
 
 pndf_status pndf_device_status(void *stream, uint32_t *bits_out)

@@ -224,6 +224,9 @@ struct ServeVariant {
     float tau;      // > 0: the cluster cut (Gaussian only)
     float jac_eps;  // > 0: the Eq. 6 clamp (Gaussian only, tau = 0)
 };
+// Lets the serving kernel of variant v use the shared memory of `warps` warps
+// per CTA; called once before the step graphs are captured.
+cudaError_t prepare_serve(int texel_fmt, int bounds_fmt, const ServeVariant &v, int warps);
 // One serving step over a device segment table (see serve.cu); clusters:
 // per-map cluster descriptors, read only when v.tau > 0.
 cudaError_t launch_serve(int texel_fmt, int bounds_fmt, const ServeVariant &v, const MapDesc *maps,

@@ -1365,6 +1365,7 @@ pndf_status launch_sort(const pndf_hierarchy *h, const pndf_query *q, int64_t nq
 namespace {
 
 __constant__ ClusterDesc kNoClusters;  // never read: the serving variants without the cut
+constexpr int kServePrefixSmem = 1025;  // prefix sums of up to 1024 segments per step in shared memory
 
 // CLUSTER / KERN: the server's evaluation variant (the cut, the footprint
 // kernel or the clamp), compiled in as for traverse_kernel.
@@ -1376,11 +1377,17 @@ __global__ void __launch_bounds__(256, PNDF_TRAVERSE_MIN_CTAS)
 {
     extern __shared__ uint32_t smem[];
     __shared__ MapDesc smaps[kServeMaxMaps];
+    __shared__ uint32_t sprefix[kServePrefixSmem];
+    const int nsegs = int(table[0]);
+    // the segment prefix sums, searched once per query, in shared memory when they fit
+    const bool prefix_in_smem = nsegs < kServePrefixSmem;
     {
         const uint32_t *src = reinterpret_cast<const uint32_t *>(maps);
         uint32_t *dst = reinterpret_cast<uint32_t *>(smaps);
         const int words = nmaps * int(sizeof(MapDesc) / sizeof(uint32_t));
         for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+        if (prefix_in_smem)
+            for (int i = threadIdx.x; i <= nsegs; i += blockDim.x) sprefix[i] = table[1 + i];
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1388,8 +1395,7 @@ __global__ void __launch_bounds__(256, PNDF_TRAVERSE_MIN_CTAS)
     uint32_t *lq = stk + kStackCap;
     uint32_t *ring = lq + kLeafQ;
     float4 *hits = reinterpret_cast<float4 *>(ring + kRing + kCapRing);
-    const int nsegs = int(table[0]);
-    const uint32_t *prefix = table + 1;
+    const uint32_t *prefix = prefix_in_smem ? sprefix : table + 1;
     const uint32_t total = prefix[nsegs];
     while (true) {
         unsigned long long k = 0;
@@ -1439,6 +1445,25 @@ cudaError_t launch_serve_t(const ServeVariant &v, const MapDesc *maps, const Clu
     return cudaGetLastError();
 }
 
+// Allow the variant's kernel the dynamic shared memory of `warps` warps (with
+// its static tables the total passes the 48 KB a launch gets by default).
+template <int BFMT, int TFMT, bool CLUSTER, int KERN>
+cudaError_t serve_smem_t(int warps)
+{
+    return cudaFuncSetAttribute(serve_kernel<BFMT, TFMT, CLUSTER, KERN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                warps * kWarpSmemWords * int(sizeof(uint32_t)));
+}
+
+template <int BFMT, int TFMT>
+cudaError_t serve_smem_v(const ServeVariant &v, int warps)
+{
+    if (v.tau > 0.f) return serve_smem_t<BFMT, TFMT, true, PNDF_KERNEL_GAUSS>(warps);
+    if (v.jac_eps > 0.f) return serve_smem_t<BFMT, TFMT, false, kKernGaussClamp>(warps);
+    if (v.kernel == PNDF_KERNEL_DISK) return serve_smem_t<BFMT, TFMT, false, PNDF_KERNEL_DISK>(warps);
+    if (v.kernel == PNDF_KERNEL_BOX) return serve_smem_t<BFMT, TFMT, false, PNDF_KERNEL_BOX>(warps);
+    return serve_smem_t<BFMT, TFMT, false, PNDF_KERNEL_GAUSS>(warps);
+}
+
 // The variant's instantiation: the cut (Gaussian), the plain Gaussian, disk,
 // box, or the Gaussian with the Eq. 6 clamp (the server validated the mix).
 template <int BFMT, int TFMT>
@@ -1456,6 +1481,15 @@ cudaError_t launch_serve_v(const ServeVariant &v, const MapDesc *maps, const Clu
 }
 
 }  // namespace
+
+cudaError_t prepare_serve(int texel_fmt, int bounds_fmt, const ServeVariant &v, int warps)
+{
+    if (bounds_fmt == PNDF_BOUNDS_F32)
+        return texel_fmt == PNDF_TEXEL_F32X2 ? serve_smem_v<PNDF_BOUNDS_F32, PNDF_TEXEL_F32X2>(v, warps)
+                                             : serve_smem_v<PNDF_BOUNDS_F32, PNDF_TEXEL_F16X2>(v, warps);
+    return texel_fmt == PNDF_TEXEL_F32X2 ? serve_smem_v<PNDF_BOUNDS_F16_OUTWARD, PNDF_TEXEL_F32X2>(v, warps)
+                                         : serve_smem_v<PNDF_BOUNDS_F16_OUTWARD, PNDF_TEXEL_F16X2>(v, warps);
+}
 
 cudaError_t launch_serve(int texel_fmt, int bounds_fmt, const ServeVariant &v, const MapDesc *maps,
                          const ClusterDesc *clusters, int nmaps, const uint32_t *table, const pndf_segment *segs,

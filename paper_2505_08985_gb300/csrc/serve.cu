@@ -154,7 +154,9 @@ pndf_status pndf_server_create(const pndf_hierarchy *const *maps, int32_t nmaps,
               cudaMalloc(&s->clusters_dev, sizeof(ClusterDesc) * nmaps) == cudaSuccess &&
               cudaMemcpy(s->clusters_dev, host_clusters, sizeof(ClusterDesc) * nmaps, cudaMemcpyHostToDevice) ==
                   cudaSuccess &&
-              cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) == cudaSuccess;
+              cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) == cudaSuccess &&
+              prepare_serve(s->texel_fmt, s->bounds_fmt, ServeVariant{s->kernel, s->tau, s->jac_eps}, s->warps) ==
+                  cudaSuccess;
     for (int k = 0; ok && k < s->nslots; ++k) {
         Slot &sl = s->slot[k];
         ok = cudaMallocHost(&sl.host, tb) == cudaSuccess && cudaMalloc(&sl.dev, tb + 256) == cudaSuccess &&

@@ -102,6 +102,9 @@ def _load() -> ctypes.CDLL:
         "pndf_version": ([], i32),
         "pndf_launch_count": ([], i64),
         "pndf_sort_queries": ([vp, vp, i64, vp, vp], i32),
+        "pndf_shard_work": ([vp, vp, i64, i32, vp, vp], i32),
+        "pndf_gather_queries": ([vp, vp, i64, i64, vp, vp], i32),
+        "pndf_scatter_results": ([vp, vp, i64, i64, vp, vp], i32),
         "pndf_server_create": ([ctypes.POINTER(vp), i32, ctypes.POINTER(_ServerConfig), ctypes.POINTER(vp)], i32),
         "pndf_server_step": ([vp, ctypes.POINTER(_Segment), i32, vp, vp], i32),
         "pndf_server_sync": ([vp], i32),
@@ -497,6 +500,48 @@ def pndf_sort_queries(h: Hierarchy, queries: torch.Tensor, order: torch.Tensor |
     with torch.cuda.device(queries.device):
         _check("pndf_sort_queries", LIB.pndf_sort_queries(h.handle, _ptr(queries), nq, _ptr(order), _stream(stream)))
     return order
+
+
+def pndf_shard_work(queries: torch.Tensor, order: torch.Tensor, block: int = 4096, stream=None) -> torch.Tensor:
+    """Estimated work per block of `block` positions of the evaluation order
+    (float64, ceil(nq / block) entries); see pndf.h."""
+    nq = _queries(queries)
+    _need(order, "order", dtype=torch.int32, numel=nq, on=queries.device)
+    out = torch.empty((nq + block - 1) // block, dtype=torch.float64, device=queries.device)
+    with torch.cuda.device(queries.device):
+        _check("pndf_shard_work", LIB.pndf_shard_work(_ptr(queries), _ptr(order), nq, int(block), _ptr(out),
+                                                      _stream(stream)))
+    return out
+
+
+def pndf_gather_queries(queries: torch.Tensor, order: torch.Tensor, first: int, count: int, out=None,
+                        stream=None) -> torch.Tensor:
+    """queries[order[first:first + count]] as a contiguous (count, 8) batch."""
+    nq = _queries(queries)
+    _need(order, "order", dtype=torch.int32, numel=nq, on=queries.device)
+    if first < 0 or count < 0 or first + count > nq:
+        raise ValueError(f"range [{first}, {first + count}) outside the {nq}-query order")
+    if out is None:
+        out = torch.empty(count, 8, dtype=torch.float32, device=queries.device)
+    _need(out, "out", dtype=torch.float32, shape_last=8, rows=count, on=queries.device)
+    with torch.cuda.device(queries.device):
+        _check("pndf_gather_queries", LIB.pndf_gather_queries(_ptr(queries), _ptr(order), int(first), int(count),
+                                                              _ptr(out), _stream(stream)))
+    return out
+
+
+def pndf_scatter_results(D_shard: torch.Tensor, order: torch.Tensor, first: int, out: torch.Tensor, stream=None):
+    """out[order[first + k]] = D_shard[k] for every k of the shard."""
+    count = D_shard.numel()
+    _need(out, "out", dtype=torch.float32)
+    _need(order, "order", dtype=torch.int32, numel=out.numel(), on=out.device)
+    _need(D_shard, "D_shard", dtype=torch.float32, on=out.device)
+    if first < 0 or first + count > out.numel():
+        raise ValueError(f"range [{first}, {first + count}) outside the {out.numel()}-query order")
+    with torch.cuda.device(out.device):
+        _check("pndf_scatter_results", LIB.pndf_scatter_results(_ptr(D_shard), _ptr(order), int(first), int(count),
+                                                                _ptr(out), _stream(stream)))
+    return out
 
 
 class Server:

@@ -23,6 +23,7 @@ in arrival order.
 
 from __future__ import annotations
 
+import gc
 import math
 import statistics
 import time
@@ -46,7 +47,8 @@ class Request:
     order: torch.Tensor | None = None
     ready: torch.cuda.Event | None = None
     next: int = 0
-    waited: bool = False
+    waited: list = field(default_factory=list)   # step streams that waited for its sort
+    slices: list = field(default_factory=list)   # completion events of the steps holding its slices
     done: torch.cuda.Event | None = None
     latency: float = math.nan
 
@@ -78,9 +80,12 @@ class ContinuousBatcher:
 
     def __init__(self, maps, step_queries: int = 1 << 20, memory_budget: int = 2 << 30, max_segments: int = 1024,
                  warps_per_cta: int = 0, ctas_per_sm: int = 0, slots: int = 4, sort: bool = True,
-                 kernel: int = pndf.PNDF_KERNEL_GAUSS, tau: float = 0.0, jac_eps: float = 0.0):
+                 kernel: int = pndf.PNDF_KERNEL_GAUSS, tau: float = 0.0, jac_eps: float = 0.0, streams: int = 2):
         """kernel / tau / jac_eps: what every query evaluates (the footprint
-        kernel, the cluster cut, the Eq. 6 clamp), as in pndf_eval_batch_ex."""
+        kernel, the cluster cut, the Eq. 6 clamp), as in pndf_eval_batch_ex.
+        streams: steps alternate over this many streams, so that a step's
+        persistent kernel can start on the SMs the previous step's last
+        queries leave idle (its tail)."""
         self.maps = list(maps)
         self.sort = bool(sort)
         self.device = self.maps[0].device
@@ -92,7 +97,8 @@ class ContinuousBatcher:
         self.max_inflight = max(1, slots - 1)
         self.max_segments = max_segments
         self.copy_stream = torch.cuda.Stream(self.device)
-        self.step_stream = torch.cuda.Stream(self.device)
+        self.step_streams = [torch.cuda.Stream(self.device) for _ in range(max(1, int(streams)))]
+        self.step_stream = self.step_streams[0]
         self.steps = 0
 
     def close(self):
@@ -104,22 +110,27 @@ class ContinuousBatcher:
             r.D = torch.empty(r.n, dtype=torch.float32, device=self.device)
             r.ready = torch.cuda.Event()
             r.ready.record(self.copy_stream)
-        if r.order is not None:
-            r.order.record_stream(self.step_stream)
-        r.D.record_stream(self.step_stream)
         r.queries.record_stream(self.copy_stream)
-        r.queries.record_stream(self.step_stream)
+        for st in self.step_streams:
+            if r.order is not None:
+                r.order.record_stream(st)
+            r.D.record_stream(st)
+            r.queries.record_stream(st)
 
-    def _form_step(self, active: deque):
+    def _form_step(self, active: deque, stream, ev):
+        """Up to step_queries queries from the admitted requests in arrival
+        order, for a step on `stream` completing with event `ev`; returns the
+        segments and the requests whose last slice is in it."""
         segs, finishing = [], []
         total = 0
         while active and total < self.step_queries and len(segs) < self.max_segments:
             r = active[0]
-            if not r.waited:
-                self.step_stream.wait_event(r.ready)
-                r.waited = True
+            if stream not in r.waited:
+                stream.wait_event(r.ready)
+                r.waited.append(stream)
             take = min(r.n - r.next, self.step_queries - total)
             segs.append((r.map, r.queries, r.order, r.D, None, r.next, take))
+            r.slices.append(ev)
             r.next += take
             total += take
             if r.next == r.n:
@@ -132,17 +143,20 @@ class ContinuousBatcher:
         summary dict; each request gets `latency`, `D` and `done`."""
         reqs = sorted(requests, key=lambda r: r.arrival)
         for r in reqs:
-            r.next, r.waited, r.done, r.latency = 0, False, None, math.nan
+            r.next, r.waited, r.done, r.latency, r.slices = 0, [], None, math.nan, []
         torch.cuda.synchronize(self.device)
         t0_ev = torch.cuda.Event(enable_timing=True)
         t0_ev.record(self.step_stream)
         t0_ev.synchronize()
+        gc_was = gc.isenabled()
+        gc.disable()  # no collector pauses inside the host's step loop
         t0 = time.perf_counter()
         pending = deque(reqs)
         active: deque = deque()
         inflight: deque = deque()
+        waiting: list = []
         used = 0
-        while pending or active or inflight:
+        while pending or active or inflight or waiting:
             now = time.perf_counter() - t0
             progressed = False
             while pending and (not realtime or pending[0].arrival <= now) and \
@@ -153,29 +167,45 @@ class ContinuousBatcher:
                 used += r.n * BYTES_PER_QUERY
                 progressed = True
             if active and len(inflight) < self.max_inflight:
-                segs, fin = self._form_step(active)
+                stream = self.step_streams[self.steps % len(self.step_streams)]
                 ev = torch.cuda.Event(enable_timing=True)
-                pndf.pndf_server_step(self.server, segs, stream=self.step_stream, ev_done=ev)
+                segs, fin = self._form_step(active, stream, ev)
+                pndf.pndf_server_step(self.server, segs, stream=stream, ev_done=ev)
                 self.steps += 1
                 inflight.append((ev, fin, segs))
                 continue
             while inflight and inflight[0][0].query():
-                ev, fin, _ = inflight.popleft()
-                for r in fin:
-                    r.done = ev
-                    used -= r.n * BYTES_PER_QUERY
+                _, fin, _ = inflight.popleft()
+                waiting.extend(fin)
                 progressed = True
+            # a request is finished when every step holding one of its slices
+            # is (its slices may have run on different streams)
+            if waiting:
+                still = []
+                for r in waiting:
+                    if all(e.query() for e in r.slices):
+                        r.done = r.slices[-1]
+                        used -= r.n * BYTES_PER_QUERY
+                        progressed = True
+                    else:
+                        still.append(r)
+                waiting = still
             if progressed:
                 continue
             if inflight and (not pending or not realtime or pending[0].arrival > now + 2e-4 or
                              used + pending[0].n * BYTES_PER_QUERY > self.budget):
                 inflight[0][0].synchronize()
+            elif waiting and not inflight:
+                waiting[0].slices[0].synchronize()
             elif pending and realtime:
                 time.sleep(max(0.0, min(pending[0].arrival - (time.perf_counter() - t0), 5e-4)))
         torch.cuda.synchronize(self.device)
+        if gc_was:
+            gc.enable()
         for r in reqs:
-            r.latency = t0_ev.elapsed_time(r.done) / 1e3 - r.arrival
-        t_last = max(t0_ev.elapsed_time(r.done) / 1e3 for r in reqs)
+            # a request is done when the last of its slices' steps completes
+            r.latency = max(t0_ev.elapsed_time(e) for e in r.slices) / 1e3 - r.arrival
+        t_last = max(r.latency + r.arrival for r in reqs)
         return summarize(reqs, min(r.arrival for r in reqs), t_last)
 
 
@@ -225,7 +255,7 @@ class TuneResult:
 
 
 def autotune(maps, sample, arrivals=None, step_candidates=(1 << 16, 1 << 18, 1 << 20, 1 << 22),
-             cta_candidates=(0,), warp_candidates=(8, 4), sort_candidates=(True, False)):
+             cta_candidates=(0,), warp_candidates=(8, 4), sort_candidates=(True, False), streams: int = 2):
     """Pick step size, launch shape and whether to sort each request for the
     served path on a sample of requests.  With `arrivals` (a Poisson stream at
     the target load) the candidate with the lowest p99 latency wins (ties
@@ -236,7 +266,8 @@ def autotune(maps, sample, arrivals=None, step_candidates=(1 << 16, 1 << 18, 1 <
         for ctas in cta_candidates:
             for warps in warp_candidates:
                 for step in step_candidates:
-                    b = ContinuousBatcher(maps, step_queries=step, warps_per_cta=warps, ctas_per_sm=ctas, sort=sort)
+                    b = ContinuousBatcher(maps, step_queries=step, warps_per_cta=warps, ctas_per_sm=ctas, sort=sort,
+                                          streams=streams)
                     for r in sample:
                         r.arrival = 0.0
                     b.run(sample, realtime=False)  # warm

@@ -62,13 +62,17 @@ def test_step_formation_slices_fifo():
     reqs = deque()
     for k, n in enumerate(sizes):
         r = serve.Request(rid=k, map=k % 2, queries=torch.zeros(n, 8), arrival=0.0)
-        r.next, r.waited = 0, False
+        r.next, r.waited, r.slices = 0, [], []
         reqs.append(r)
+    all_reqs = list(reqs)
     b = _batcher(step_queries=256, max_segments=3)
     covered = {k: [] for k in range(len(sizes))}
     shape = []
+    streams = [b.step_stream, _Stream()]
+    nstep = 0
     while reqs:
-        segs, fin = b._form_step(reqs)
+        segs, fin = b._form_step(reqs, streams[nstep % 2], object())
+        nstep += 1
         shape.append((sum(s[6] for s in segs), len(segs)))
         assert 0 < shape[-1][0] <= 256 and shape[-1][1] <= 3
         for m, q, order, D, flags, first, count in segs:
@@ -80,7 +84,10 @@ def test_step_formation_slices_fifo():
             assert first == pos and count > 0
             pos += count
         assert pos == n
-    assert b.step_stream.waits == len(sizes)  # each request's readiness awaited once
+    # each request's readiness awaited once per step stream that runs a slice of it
+    waits = sum(len(r.waited) for r in all_reqs)
+    assert streams[0].waits + streams[1].waits == waits and len(sizes) <= waits <= 2 * len(sizes)
+    assert all(len(r.slices) == len(covered[r.rid]) for r in all_reqs)  # one completion event per slice
     # a step stops only when full or out of slices (or out of requests)
     assert all(total == 256 or nsegs == 3 for total, nsegs in shape[:-1])
     assert shape == [(256, 2), (256, 1), (256, 1), (256, 1), (86, 3), (256, 1), (144, 1)]
