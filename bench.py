@@ -74,6 +74,9 @@ def parse():
                     help="further offered loads for the latency sweep ('' = skip)")
     ap.add_argument("--mixed-requests", type=int, default=4096,
                     help="projected-area + P-NDF sample on the 16384^2 FP16 map (0 = skip)")
+    ap.add_argument("--mixed-stream-batches", type=int, default=64,
+                    help="served glint + diffuse stream on the mixed map: batches, half P-NDF and half projected "
+                         "area (0 = skip)")
     ap.add_argument("--mixed-map-size", type=int, default=synth.MIXED_16384["n"],
                     help="side of the mixed scratches + flakes map (cells and grooves scale with the area)")
     ap.add_argument("--kernel-census", action="store_true",
@@ -625,6 +628,7 @@ def run_mixed(args, dev):
     covered = torch.isfinite(rel)  # footprints whose mip nodes all reach past the map border have no fit
     graz = (w[:, 2] < 0.2).cpu()
     g.free()
+    stream_out = run_mixed_stream(args, st, h) if args.mixed_stream_batches > 0 else None
     h.free()
 
     def pct(x, p):
@@ -645,7 +649,66 @@ def run_mixed(args, dev):
                                                    "median_wz>=0.2": pct(rel[~graz], 0.5)}}}
     if acc is not None:
         out["accuracy"] = acc
+    if stream_out is not None:
+        out["served_stream"] = stream_out
     return out
+
+
+def run_mixed_stream(args, st, h):
+    """Glint + diffuse served as one stream on the binary16 mixed map: batches
+    alternate between 1024 P-NDF queries and 16 projected-area requests
+    (sigma log-U(1, 1024), light uniform on the hemisphere), Poisson arrivals
+    at 0.8 of the served path's own saturated rate on this stream; the served
+    path (continuous batching, both kinds in the same steps) against each
+    batch launched alone in arrival order."""
+    from paper_2505_08985_gb300 import pndf, serve
+    dev = st.device
+    cfg = synth.MIXED_16384
+    nb = args.mixed_stream_batches
+    npn, npa = 1024, 16
+    A = pndf.PNDF_SEGMENT_PROJECTED_AREA
+    qs = synth.make_queries(st.float(), nb * npn, cfg["mix"], cfg["seed"] + 7)
+    ws = synth.hemisphere_dirs(nb * npa, seed=cfg["seed"] + 8, device=dev)
+
+    def requests(arrivals):
+        out = []
+        for k, a in enumerate(arrivals):
+            if k % 2:
+                lo = npa * (k // 2)
+                out.append(serve.Request(rid=k, map=0, queries=qs[lo:lo + npa].contiguous(), arrival=a, kind=A,
+                                         omega=ws[lo:lo + npa].contiguous()))
+            else:
+                lo = npn * (k // 2)
+                out.append(serve.Request(rid=k, map=0, queries=qs[lo:lo + npn].contiguous(), arrival=a))
+        return out
+
+    b = serve.ContinuousBatcher([h], step_queries=4096, max_area_requests=64, sort=True)
+    b.run(requests([0.0] * nb), realtime=False)  # warm
+    cap = b.run(requests([0.0] * nb), realtime=False)
+    rate = 0.8 * nb / cap["span_s"]
+    arr = serve.poisson_arrivals(nb, rate, seed=23)
+    rs = requests(arr)
+    sv = b.run(rs, realtime=True)
+    b.close()
+    rp = requests(arr)
+    pl = serve.run_plain([h], rp, realtime=True, sort=pndf.PNDF_SORT_NONE)
+
+    def by_kind(reqs, kind):
+        lat = [1e3 * r.latency for r in reqs if r.kind == kind]
+        return {"p50_ms": serve.percentile(lat, 0.5), "p99_ms": serve.percentile(lat, 0.99)}
+
+    equal = all(torch.equal(a.D, b_.D) for a, b_ in zip(rs, rp))
+    return {"stream": f"{nb} batches alternating {npn} P-NDF queries and {npa} projected-area requests "
+                      f"({nb // 2 * npn} queries and {nb // 2 * npa} area requests, a bounded sample of the "
+                      "8M-request mix); Poisson arrivals at 0.8 of the served saturated rate "
+                      f"({rate:.1f} batches/s)",
+            "served_capacity_batches_per_s": nb / cap["span_s"],
+            "served": {"requests_per_s": (nb // 2) * (npn + npa) / sv["span_s"], "p50_ms": sv["p50_ms"],
+                       "p99_ms": sv["p99_ms"], "pndf": by_kind(rs, pndf.PNDF_SEGMENT_PNDF), "projected_area": by_kind(rs, A)},
+            "plain_per_batch": {"requests_per_s": (nb // 2) * (npn + npa) / pl["span_s"], "p50_ms": pl["p50_ms"],
+                                "p99_ms": pl["p99_ms"], "pndf": by_kind(rp, pndf.PNDF_SEGMENT_PNDF),
+                                "projected_area": by_kind(rp, A)},
+            "served_equals_plain_bitwise": equal}
 
 
 # ---------------------------------------------------------------------------

@@ -420,15 +420,23 @@ pndf_status pndf_scatter_results(const float *D_shard_dev, const uint32_t *order
  * other segments share its step (one warp evaluates it with a fixed order).
  * ------------------------------------------------------------------------- */
 
+typedef enum pndf_segment_kind {
+    PNDF_SEGMENT_PNDF = 0,            /* P-NDF queries (Eq. 5)                                */
+    PNDF_SEGMENT_PROJECTED_AREA = 1   /* projected-area requests (Eq. 9-11), as               */
+                                      /* pndf_diffuse_projected_area evaluates them           */
+} pndf_segment_kind;
+
 typedef struct pndf_segment {
     const pndf_query *q;    /* device: the request's query records                    */
     const uint32_t *order;  /* device: evaluation order (indices into q), or NULL      */
-    float *D;               /* device: the request's results, indexed like q           */
-    uint32_t *flags;        /* device: per-query PNDF_QF_* bits, or NULL               */
+                            /* (projected area: NULL)                                  */
+    float *D;               /* device: the request's results (D, or P), indexed like q */
+    uint32_t *flags;        /* device: per-query PNDF_QF_* bits, or NULL (area: NULL)  */
     int32_t map;            /* index into the server's hierarchy table                 */
     int32_t first;          /* first position of this slice (in order[], else in q[])  */
-    int32_t count;          /* queries in this slice                                   */
-    int32_t reserved;
+    int32_t count;          /* queries (requests) in this slice                        */
+    int32_t kind;           /* pndf_segment_kind                                       */
+    const float *omega;     /* projected area: 3 floats per record of q (unit, w_z > 0) */
 } pndf_segment;
 
 typedef struct pndf_server pndf_server;
@@ -442,7 +450,8 @@ typedef struct pndf_server_config {
     float tau;              /* > 0: the cluster cut of Sec. 4.2 (Gaussian kernel only;
                                every map built with clusters = 1)                     */
     float jac_eps;          /* > 0: the Eq. 6 clamp (Gaussian kernel, tau = 0)         */
-    int32_t reserved;       /* 0                                                      */
+    int32_t max_area_requests; /* projected-area requests per step, 0..65536 (0: none;
+                               their band scratch is reserved per table slot)        */
 } pndf_server_config;
 
 /* Create a server over nmaps (1..8) hierarchies on the current device; maps
@@ -450,6 +459,12 @@ typedef struct pndf_server_config {
  * pndf_eval_batch_ex evaluates it with the same kernel, tau and jac_eps (the
  * variant is fixed per server: the step graphs capture its kernel).
  * Allocates its tables (device and pinned host) and captures the step graphs.
+ * With cfg->max_area_requests > 0 a step can also hold projected-area
+ * requests (segment kind PNDF_SEGMENT_PROJECTED_AREA), evaluated in the same
+ * step graph by the kernels of pndf_diffuse_projected_area (so P is the same
+ * bit for bit as that call gives); each table slot reserves their band
+ * scratch, 4 (max + 1) + 8 max B bytes with B = (N_max + 6) / 8 + 1 bands for
+ * the largest map side N_max.
  * Errors: INVALID_ARG (formats differ, bad counts, kernel / tau / jac_eps out
  * of range), UNSUPPORTED (tau with a map built without clusters, or with the
  * disk / box kernel or the clamp; the clamp with the disk / box kernel), OOM,
@@ -461,8 +476,12 @@ pndf_status pndf_server_create(const pndf_hierarchy *const *maps, int32_t nmaps,
  * stream; ev_done (optional cudaEvent_t) is recorded when the step's kernel
  * completes.  Blocks only if the next table slot is still in use by the step
  * queued `slots` steps earlier.  All pointers in the segments must stay valid
- * until the step completes.  Errors: INVALID_ARG (bad map index, count,
- * pointers, nsegs > max_segments), CUDA. */
+ * until the step completes.  P-NDF segments are at most max_segments;
+ * projected-area segments (no order or flags, omega required) hold at most
+ * max_area_requests requests in total.  Errors: INVALID_ARG (bad map index,
+ * kind, count, pointers, too many P-NDF segments), CAPACITY (too many
+ * projected-area requests), UNSUPPORTED (projected-area segments on a server
+ * created without max_area_requests), CUDA. */
 pndf_status pndf_server_step(pndf_server *srv, const pndf_segment *segs_host, int32_t nsegs, void *stream,
                              void *ev_done);
 

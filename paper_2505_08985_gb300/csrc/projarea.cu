@@ -32,6 +32,7 @@
 // lane), compensated sums are reduced across the warp and stored per band;
 // a second kernel adds a request's bands in fixed order, so results do not
 // depend on scheduling or on which other requests share the launch.
+#include "area_step.cuh"
 #include "ggx.cuh"
 #include "visible.cuh"
 
@@ -296,7 +297,7 @@ __global__ void pa_bands(MapDesc d, const pndf_query *__restrict__ qs, int64_t k
 
 // exclusive scan of cnt (<= 65536) values in place, one CTA of 1024 threads;
 // total goes to nb[cnt]
-__global__ void __launch_bounds__(1024) pa_scan(uint32_t *__restrict__ nb, int cnt)
+__device__ __forceinline__ void scan_bands(uint32_t *__restrict__ nb, int cnt)
 {
     __shared__ uint32_t part[1024];
     const int per = (cnt + 1023) / 1024;
@@ -323,6 +324,95 @@ __global__ void __launch_bounds__(1024) pa_scan(uint32_t *__restrict__ nb, int c
     if (threadIdx.x == 1023) nb[cnt] = part[1023];
 }
 
+__global__ void __launch_bounds__(1024) pa_scan(uint32_t *__restrict__ nb, int cnt) { scan_bands(nb, cnt); }
+
+// Band `band` (kBand quad rows) of request (q, w) on map d, integrated by one
+// warp (lane = quad column, both triangles; the FP64 triangles deferred into
+// the warp's ring dq_id / dq_w and evaluated 32 at a time); returns the
+// compensated sum and its correction, reduced to lane 0 in a fixed order.
+template <int TFMT>
+__device__ __forceinline__ float2 integrate_band(const MapDesc &d, const Req &q, const Dir &w, int band, int lane,
+                                                 uint32_t *dq_id, float *dq_w)
+{
+    const unsigned lt = (1u << lane) - 1u;
+    const int jb0 = q.j0 + band * kBand, jb1 = min(q.j1, jb0 + kBand - 1);
+    float s = 0.f, c = 0.f;
+    uint32_t head = 0;
+    int nd = 0;  // deferred triangles waiting in the ring (warp-uniform)
+    for (int j = jb0; j <= jb1; ++j) {
+        const float dyl = (float(j) - q.y) + (1.f / 3.f), dyu = (float(j) - q.y) + (2.f / 3.f);
+        for (int ib = q.i0; ib <= q.i1; ib += 32) {
+            const int i = ib + lane;
+            float v[2] = {0.f, 0.f}, kw[2] = {0.f, 0.f};
+            bool dfr[2] = {false, false};
+            if (i <= q.i1) {
+                const float dxl = (float(i) - q.x) + (1.f / 3.f), dxu = (float(i) - q.x) + (2.f / 3.f);
+                const float ql = wq(q, dxl, dyl), qu = wq(q, dxu, dyu);
+                if (ql <= kQCut || qu <= kQCut) {
+                    float2 n0 = texel<TFMT>(d, i, j), n1 = texel<TFMT>(d, i + 1, j);
+                    float2 n2 = texel<TFMT>(d, i, j + 1), n3 = texel<TFMT>(d, i + 1, j + 1);
+                    float z0 = zof(n0), z1 = zof(n1), z2 = zof(n2), z3 = zof(n3);
+                    float r;
+                    if (ql <= kQCut) {
+                        kw[0] = q.norm * expf(-0.5f * ql);
+                        if (tri_ratio_fast(n0, z0, n1, z1, n2, z2, w, r))
+                            v[0] = kw[0] * r;
+                        else
+                            dfr[0] = true;
+                    }
+                    if (qu <= kQCut) {
+                        kw[1] = q.norm * expf(-0.5f * qu);
+                        if (tri_ratio_fast(n3, z3, n2, z2, n1, z1, w, r))
+                            v[1] = kw[1] * r;
+                        else
+                            dfr[1] = true;
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                float tt = s + v[k];
+                c += fabsf(s) >= fabsf(v[k]) ? (s - tt) + v[k] : (v[k] - tt) + s;
+                s = tt;
+                // queue the triangles that need the FP64 path
+                unsigned m = __ballot_sync(kFull, dfr[k]);
+                if (dfr[k]) {
+                    uint32_t pos = (head + uint32_t(nd) + __popc(m & lt)) & (kDefer - 1);
+                    dq_id[pos] = (uint32_t(i) << 15) | (uint32_t(j) << 1) | uint32_t(k);
+                    dq_w[pos] = kw[k];
+                }
+                nd += __popc(m);
+            }
+            __syncwarp();
+            while (nd >= 32) {
+                float val = deferred_value<TFMT>(d, w, dq_id, dq_w, head, lane);
+                float tt = s + val;
+                c += fabsf(s) >= fabsf(val) ? (s - tt) + val : (val - tt) + s;
+                s = tt;
+                head += 32;
+                nd -= 32;
+                __syncwarp();
+            }
+        }
+    }
+    if (nd > 0) {
+        float val = lane < nd ? deferred_value<TFMT>(d, w, dq_id, dq_w, head, lane) : 0.f;
+        float tt = s + val;
+        c += fabsf(s) >= fabsf(val) ? (s - tt) + val : (val - tt) + s;
+        s = tt;
+        __syncwarp();
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        float so = __shfl_down_sync(kFull, s, o), co = __shfl_down_sync(kFull, c, o);
+        float tt = s + so;
+        float err = fabsf(s) >= fabsf(so) ? (s - tt) + so : (so - tt) + s;
+        s = tt;
+        c += co + err;
+    }
+    return make_float2(s, c);
+}
+
 template <int TFMT>
 __global__ void __launch_bounds__(256) pa_items(MapDesc d, const pndf_query *__restrict__ qs,
                                                const float *__restrict__ omega, int64_t k0, int cnt,
@@ -332,7 +422,6 @@ __global__ void __launch_bounds__(256) pa_items(MapDesc d, const pndf_query *__r
     __shared__ uint32_t dq_id_s[8][kDefer];
     __shared__ float dq_w_s[8][kDefer];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned lt = (1u << lane) - 1u;
     uint32_t *dq_id = dq_id_s[warp];
     float *dq_w = dq_w_s[warp];
     const uint32_t total = off[cnt];
@@ -351,97 +440,23 @@ __global__ void __launch_bounds__(256) pa_items(MapDesc d, const pndf_query *__r
                 hi = mid - 1;
         }
         const int t = lo;
-        const pndf_query rec = qs[k0 + t];
-        const Req q = make_req(rec, d.n);
+        const Req q = make_req(qs[k0 + t], d.n);
         const Dir w = make_dir_f(omega[3 * (k0 + t)], omega[3 * (k0 + t) + 1], omega[3 * (k0 + t) + 2]);
-        const int band = int(it - off[t]);
-        const int jb0 = q.j0 + band * kBand, jb1 = min(q.j1, jb0 + kBand - 1);
-        float s = 0.f, c = 0.f;
-        uint32_t head = 0;
-        int nd = 0;  // deferred triangles waiting in the ring (warp-uniform)
-        for (int j = jb0; j <= jb1; ++j) {
-            const float dyl = (float(j) - q.y) + (1.f / 3.f), dyu = (float(j) - q.y) + (2.f / 3.f);
-            for (int ib = q.i0; ib <= q.i1; ib += 32) {
-                const int i = ib + lane;
-                float v[2] = {0.f, 0.f}, kw[2] = {0.f, 0.f};
-                bool dfr[2] = {false, false};
-                if (i <= q.i1) {
-                    const float dxl = (float(i) - q.x) + (1.f / 3.f), dxu = (float(i) - q.x) + (2.f / 3.f);
-                    const float ql = wq(q, dxl, dyl), qu = wq(q, dxu, dyu);
-                    if (ql <= kQCut || qu <= kQCut) {
-                        float2 n0 = texel<TFMT>(d, i, j), n1 = texel<TFMT>(d, i + 1, j);
-                        float2 n2 = texel<TFMT>(d, i, j + 1), n3 = texel<TFMT>(d, i + 1, j + 1);
-                        float z0 = zof(n0), z1 = zof(n1), z2 = zof(n2), z3 = zof(n3);
-                        float r;
-                        if (ql <= kQCut) {
-                            kw[0] = q.norm * expf(-0.5f * ql);
-                            if (tri_ratio_fast(n0, z0, n1, z1, n2, z2, w, r))
-                                v[0] = kw[0] * r;
-                            else
-                                dfr[0] = true;
-                        }
-                        if (qu <= kQCut) {
-                            kw[1] = q.norm * expf(-0.5f * qu);
-                            if (tri_ratio_fast(n3, z3, n2, z2, n1, z1, w, r))
-                                v[1] = kw[1] * r;
-                            else
-                                dfr[1] = true;
-                        }
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    float tt = s + v[k];
-                    c += fabsf(s) >= fabsf(v[k]) ? (s - tt) + v[k] : (v[k] - tt) + s;
-                    s = tt;
-                    // queue the triangles that need the FP64 path
-                    unsigned m = __ballot_sync(kFull, dfr[k]);
-                    if (dfr[k]) {
-                        uint32_t pos = (head + uint32_t(nd) + __popc(m & lt)) & (kDefer - 1);
-                        dq_id[pos] = (uint32_t(i) << 15) | (uint32_t(j) << 1) | uint32_t(k);
-                        dq_w[pos] = kw[k];
-                    }
-                    nd += __popc(m);
-                }
-                __syncwarp();
-                while (nd >= 32) {
-                    float val = deferred_value<TFMT>(d, w, dq_id, dq_w, head, lane);
-                    float tt = s + val;
-                    c += fabsf(s) >= fabsf(val) ? (s - tt) + val : (val - tt) + s;
-                    s = tt;
-                    head += 32;
-                    nd -= 32;
-                    __syncwarp();
-                }
-            }
-        }
-        if (nd > 0) {
-            float val = lane < nd ? deferred_value<TFMT>(d, w, dq_id, dq_w, head, lane) : 0.f;
-            float tt = s + val;
-            c += fabsf(s) >= fabsf(val) ? (s - tt) + val : (val - tt) + s;
-            s = tt;
-            __syncwarp();
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            float so = __shfl_down_sync(kFull, s, o), co = __shfl_down_sync(kFull, c, o);
-            float tt = s + so;
-            float err = fabsf(s) >= fabsf(so) ? (s - tt) + so : (so - tt) + s;
-            s = tt;
-            c += co + err;
-        }
-        if (lane == 0) part[it] = make_float2(s, c);
+        const float2 v = integrate_band<TFMT>(d, q, w, int(it - off[t]), lane, dq_id, dq_w);
+        if (lane == 0) part[it] = v;
     }
 }
 
-// one warp per request: fixed-order sum of its bands
-__global__ void pa_reduce(const pndf_query *__restrict__ qs, int64_t k0, int cnt, const uint32_t *__restrict__ off,
-                          const float2 *__restrict__ part, float *__restrict__ P, unsigned int *hier_status)
+// A request's P from its bands [b0, b1): one warp, fixed-order compensated
+// sum (lane 0 gets the value); NaN for an invalid covariance.
+__device__ __forceinline__ bool request_valid(const pndf_query &r)
 {
-    const int lane = threadIdx.x & 31;
-    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (t >= cnt) return;
-    const uint32_t b0 = off[t], b1 = off[t + 1];
+    const float det = r.sxx * r.syy - r.sxy * r.sxy;
+    return (r.sxx > 0.f) && (r.syy > 0.f) && (det > 0.f) && isfinite(det) && isfinite(r.x) && isfinite(r.y);
+}
+
+__device__ __forceinline__ float reduce_bands(const float2 *__restrict__ part, uint32_t b0, uint32_t b1, int lane)
+{
     float s = 0.f, c = 0.f;
     for (uint32_t b = b0 + lane; b < b1; b += 32) {
         float2 p = part[b];
@@ -457,12 +472,102 @@ __global__ void pa_reduce(const pndf_query *__restrict__ qs, int64_t k0, int cnt
         s = tt;
         c += co + err;
     }
+    return s + c;
+}
+
+// one warp per request: fixed-order sum of its bands
+__global__ void pa_reduce(const pndf_query *__restrict__ qs, int64_t k0, int cnt, const uint32_t *__restrict__ off,
+                          const float2 *__restrict__ part, float *__restrict__ P, unsigned int *hier_status)
+{
+    const int lane = threadIdx.x & 31;
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (t >= cnt) return;
+    const float v = reduce_bands(part, off[t], off[t + 1], lane);
     if (lane == 0) {
-        const pndf_query r = qs[k0 + t];
-        float det = r.sxx * r.syy - r.sxy * r.sxy;
-        bool valid = (r.sxx > 0.f) && (r.syy > 0.f) && (det > 0.f) && isfinite(det) && isfinite(r.x) && isfinite(r.y);
+        const bool valid = request_valid(qs[k0 + t]);
         if (!valid) record_status(hier_status, &g_status_projarea, PNDF_QF_INVALID);
-        P[k0 + t] = valid ? s + c : __int_as_float(0x7fc00000);
+        P[k0 + t] = valid ? v : __int_as_float(0x7fc00000);
+    }
+}
+
+// ---- projected-area requests inside a serving step (area_step.cuh) ----
+
+constexpr int kStepMaxMaps = kServeMaxMaps;
+
+__global__ void area_step_bands(const MapDesc *__restrict__ maps, const uint32_t *__restrict__ count,
+                                const AreaReq *__restrict__ areq, uint32_t *__restrict__ nb)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= int(*count)) return;
+    const AreaReq a = areq[t];
+    const Req q = make_req(*a.q, maps[a.map].n);
+    const int rows = q.j1 - q.j0 + 1;
+    nb[t] = rows > 0 ? uint32_t((rows + kBand - 1) / kBand) : 0u;
+}
+
+__global__ void __launch_bounds__(1024) area_step_scan(const uint32_t *__restrict__ count, uint32_t *__restrict__ nb)
+{
+    scan_bands(nb, int(*count));
+}
+
+template <int TFMT>
+__global__ void __launch_bounds__(256) area_step_items(const MapDesc *__restrict__ maps, int nmaps,
+                                                      const uint32_t *__restrict__ count,
+                                                      const AreaReq *__restrict__ areq,
+                                                      const uint32_t *__restrict__ off, float2 *__restrict__ part,
+                                                      unsigned int *__restrict__ cursor)
+{
+    __shared__ uint32_t dq_id_s[8][kDefer];
+    __shared__ float dq_w_s[8][kDefer];
+    __shared__ MapDesc smaps[kStepMaxMaps];
+    {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(maps);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(smaps);
+        const int words = nmaps * int(sizeof(MapDesc) / sizeof(uint32_t));
+        for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *dq_id = dq_id_s[warp];
+    float *dq_w = dq_w_s[warp];
+    const int cnt = int(*count);
+    if (cnt == 0) return;
+    const uint32_t total = off[cnt];
+    while (true) {
+        uint32_t it = 0;
+        if (lane == 0) it = atomicAdd(cursor, 1u);
+        it = __shfl_sync(kFull, it, 0);
+        if (it >= total) break;
+        int lo = 0, hi = cnt - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (off[mid] <= it)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const AreaReq a = areq[lo];
+        const MapDesc &d = smaps[a.map];
+        const Req q = make_req(*a.q, d.n);
+        const Dir w = make_dir_f(a.w[0], a.w[1], a.w[2]);
+        const float2 v = integrate_band<TFMT>(d, q, w, int(it - off[lo]), lane, dq_id, dq_w);
+        if (lane == 0) part[it] = v;
+    }
+}
+
+__global__ void area_step_reduce(const MapDesc *__restrict__ maps, const uint32_t *__restrict__ count,
+                                 const AreaReq *__restrict__ areq, const uint32_t *__restrict__ off,
+                                 const float2 *__restrict__ part)
+{
+    const int lane = threadIdx.x & 31;
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (t >= int(*count)) return;
+    const float v = reduce_bands(part, off[t], off[t + 1], lane);
+    if (lane == 0) {
+        const AreaReq a = areq[t];
+        const bool valid = request_valid(*a.q);
+        if (!valid) record_status(maps[a.map].status, &g_status_projarea, PNDF_QF_INVALID);
+        *a.out = valid ? v : __int_as_float(0x7fc00000);
     }
 }
 
@@ -791,6 +896,34 @@ cudaError_t launch_ggx_copy(const pndf_ggx *g, int l, float *out, cudaStream_t s
     const uint32_t n = uint32_t(level_nodes(g->L, l));
     ggx_copy<<<(n + 255) / 256, 256, 0, s>>>(*g, l, out);
     count_launches(1);
+    return cudaGetLastError();
+}
+
+int area_max_bands(int n) { return (n - 1 + kBand - 1) / kBand + 1; }
+
+cudaError_t launch_area_step(int texel_fmt, const MapDesc *maps, int nmaps, const uint32_t *count,
+                             const AreaReq *areq, int cap, uint32_t *off, float2 *part, unsigned int *cursor,
+                             cudaStream_t s)
+{
+    if (cap <= 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaMemsetAsync(cursor, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    area_step_bands<<<(cap + 255) / 256, 256, 0, s>>>(maps, count, areq, off);
+    area_step_scan<<<1, 1024, 0, s>>>(count, off);
+    int occ = 0;
+    if (texel_fmt == PNDF_TEXEL_F32X2) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, area_step_items<PNDF_TEXEL_F32X2>, 256, 0);
+        area_step_items<PNDF_TEXEL_F32X2><<<sms * (occ > 0 ? occ : 1), 256, 0, s>>>(maps, nmaps, count, areq, off,
+                                                                                    part, cursor);
+    } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, area_step_items<PNDF_TEXEL_F16X2>, 256, 0);
+        area_step_items<PNDF_TEXEL_F16X2><<<sms * (occ > 0 ? occ : 1), 256, 0, s>>>(maps, nmaps, count, areq, off,
+                                                                                    part, cursor);
+    }
+    area_step_reduce<<<(cap * 32 + 255) / 256, 256, 0, s>>>(maps, count, areq, off, part);
     return cudaGetLastError();
 }
 

@@ -62,13 +62,17 @@ class _EvalConfig(ctypes.Structure):
 class _Segment(ctypes.Structure):
     _fields_ = [("q", ctypes.c_void_p), ("order", ctypes.c_void_p), ("D", ctypes.c_void_p),
                 ("flags", ctypes.c_void_p), ("map", ctypes.c_int32), ("first", ctypes.c_int32),
-                ("count", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("count", ctypes.c_int32), ("kind", ctypes.c_int32), ("omega", ctypes.c_void_p)]
+
+
+PNDF_SEGMENT_PNDF = 0
+PNDF_SEGMENT_PROJECTED_AREA = 1
 
 
 class _ServerConfig(ctypes.Structure):
     _fields_ = [("max_segments", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("slots", ctypes.c_int32), ("kernel", ctypes.c_int32),
-                ("tau", ctypes.c_float), ("jac_eps", ctypes.c_float), ("reserved", ctypes.c_int32)]
+                ("tau", ctypes.c_float), ("jac_eps", ctypes.c_float), ("max_area_requests", ctypes.c_int32)]
 
 
 def _load() -> ctypes.CDLL:
@@ -568,12 +572,13 @@ class Server:
 
 def pndf_server_create(maps: list, max_segments: int = 1024, warps_per_cta: int = 0, ctas_per_sm: int = 0,
                        slots: int = 0, kernel: int = PNDF_KERNEL_GAUSS, tau: float = 0.0,
-                       jac_eps: float = 0.0) -> Server:
+                       jac_eps: float = 0.0, max_area_requests: int = 0) -> Server:
     """kernel / tau / jac_eps: what every served query evaluates, as in
-    pndf_eval_batch_ex (tau > 0 needs maps built with clusters=True)."""
+    pndf_eval_batch_ex (tau > 0 needs maps built with clusters=True).
+    max_area_requests: projected-area requests a step can hold (0: none)."""
     arr = (ctypes.c_void_p * len(maps))(*[m.handle for m in maps])
     cfg = _ServerConfig(int(max_segments), int(warps_per_cta), int(ctas_per_sm), int(slots), int(kernel),
-                        float(tau), float(jac_eps), 0)
+                        float(tau), float(jac_eps), int(max_area_requests))
     h = ctypes.c_void_p()
     with torch.cuda.device(maps[0].device):
         _check("pndf_server_create", LIB.pndf_server_create(arr, len(maps), ctypes.byref(cfg), ctypes.byref(h)))
@@ -581,13 +586,18 @@ def pndf_server_create(maps: list, max_segments: int = 1024, warps_per_cta: int 
 
 
 def pndf_server_step(srv: Server, segments: list, stream=None, ev_done=None):
-    """segments: list of (map_index, queries, order_or_None, D, flags_or_None, first, count);
-    tensors must stay alive until the step completes."""
+    """segments: list of (map_index, queries, order_or_None, D, flags_or_None,
+    first, count) for P-NDF slices, or with two more items (kind, omega) where
+    kind = PNDF_SEGMENT_PROJECTED_AREA and omega is the requests' (n, 3)
+    directions (D then receives P); tensors must stay alive until the step
+    completes."""
     n = len(segments)
     if n > srv.max_segments:
         raise ValueError("too many segments for this server")
     segs = srv._segs
-    for i, (mi, q, order, D, flags, first, count) in enumerate(segments):
+    for i, seg in enumerate(segments):
+        mi, q, order, D, flags, first, count = seg[:7]
+        kind, omega = (seg[7], seg[8]) if len(seg) > 7 else (PNDF_SEGMENT_PNDF, None)
         # (a map index out of range is the library's to reject)
         dev = srv.maps[int(mi)].device if 0 <= int(mi) < len(srv.maps) else None
         _need(q, f"segment {i} queries", dtype=torch.float32, shape_last=8, on=dev)
@@ -595,6 +605,10 @@ def pndf_server_step(srv: Server, segments: list, stream=None, ev_done=None):
         _need(D, f"segment {i} D", dtype=torch.float32, numel=nq, on=dev)
         if flags is not None:
             _need(flags, f"segment {i} flags", dtype=torch.int32, numel=nq, on=dev)
+        if kind == PNDF_SEGMENT_PROJECTED_AREA:
+            if order is not None or flags is not None:
+                raise ValueError(f"segment {i}: projected-area segments take no order or flags")
+            _need(omega, f"segment {i} omega", dtype=torch.float32, shape_last=3, rows=nq, on=dev)
         span = nq
         if order is not None:
             _need(order, f"segment {i} order", dtype=torch.int32, on=dev)
@@ -609,7 +623,8 @@ def pndf_server_step(srv: Server, segments: list, stream=None, ev_done=None):
         sg.map = int(mi)
         sg.first = int(first)
         sg.count = int(count)
-        sg.reserved = 0
+        sg.kind = int(kind)
+        sg.omega = _ptr(omega)
     _check("pndf_server_step", LIB.pndf_server_step(srv.handle, segs, n, _stream(stream), _event_handle(ev_done)))
 
 

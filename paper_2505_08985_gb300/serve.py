@@ -43,6 +43,8 @@ class Request:
     map: int
     queries: torch.Tensor            # (n, 8) float32 on the serving device, owned by the client
     arrival: float                   # seconds from the run's time origin
+    kind: int = 0                    # pndf.PNDF_SEGMENT_PNDF, or _PROJECTED_AREA (then D receives P)
+    omega: torch.Tensor | None = None  # projected area: (n, 3) float32 unit directions
     D: torch.Tensor | None = None    # results, filled by the run
     order: torch.Tensor | None = None
     ready: torch.cuda.Event | None = None
@@ -80,20 +82,23 @@ class ContinuousBatcher:
 
     def __init__(self, maps, step_queries: int = 1 << 20, memory_budget: int = 2 << 30, max_segments: int = 1024,
                  warps_per_cta: int = 0, ctas_per_sm: int = 0, slots: int = 4, sort: bool = True,
-                 kernel: int = pndf.PNDF_KERNEL_GAUSS, tau: float = 0.0, jac_eps: float = 0.0, streams: int = 2):
+                 kernel: int = pndf.PNDF_KERNEL_GAUSS, tau: float = 0.0, jac_eps: float = 0.0, streams: int = 2,
+                 max_area_requests: int = 0):
         """kernel / tau / jac_eps: what every query evaluates (the footprint
         kernel, the cluster cut, the Eq. 6 clamp), as in pndf_eval_batch_ex.
         streams: steps alternate over this many streams, so that a step's
         persistent kernel can start on the SMs the previous step's last
-        queries leave idle (its tail)."""
+        queries leave idle (its tail).  max_area_requests: projected-area
+        requests a step can hold beside its P-NDF queries (0: none)."""
         self.maps = list(maps)
         self.sort = bool(sort)
         self.device = self.maps[0].device
         self.step_queries = int(step_queries)
         self.budget = int(memory_budget)
+        self.area_cap = int(max_area_requests)
         self.server = pndf.pndf_server_create(self.maps, max_segments=max_segments, warps_per_cta=warps_per_cta,
                                               ctas_per_sm=ctas_per_sm, slots=slots, kernel=kernel, tau=tau,
-                                              jac_eps=jac_eps)
+                                              jac_eps=jac_eps, max_area_requests=self.area_cap)
         self.max_inflight = max(1, slots - 1)
         self.max_segments = max_segments
         self.copy_stream = torch.cuda.Stream(self.device)
@@ -106,7 +111,8 @@ class ContinuousBatcher:
 
     def _admit(self, r: Request):
         with torch.cuda.stream(self.copy_stream):
-            r.order = pndf.pndf_sort_queries(self.maps[r.map], r.queries, stream=self.copy_stream) if self.sort else None
+            sort = self.sort and r.kind == pndf.PNDF_SEGMENT_PNDF
+            r.order = pndf.pndf_sort_queries(self.maps[r.map], r.queries, stream=self.copy_stream) if sort else None
             r.D = torch.empty(r.n, dtype=torch.float32, device=self.device)
             r.ready = torch.cuda.Event()
             r.ready.record(self.copy_stream)
@@ -114,6 +120,8 @@ class ContinuousBatcher:
         for st in self.step_streams:
             if r.order is not None:
                 r.order.record_stream(st)
+            if r.omega is not None:
+                r.omega.record_stream(st)
             r.D.record_stream(st)
             r.queries.record_stream(st)
 
@@ -122,17 +130,25 @@ class ContinuousBatcher:
         order, for a step on `stream` completing with event `ev`; returns the
         segments and the requests whose last slice is in it."""
         segs, finishing = [], []
-        total = 0
-        while active and total < self.step_queries and len(segs) < self.max_segments:
+        total = area = 0
+        while active and len(segs) < self.max_segments:
             r = active[0]
+            is_area = r.kind == pndf.PNDF_SEGMENT_PROJECTED_AREA
+            room = self.area_cap - area if is_area else self.step_queries - total
+            if room <= 0:  # FIFO: the step ends at the first request it has no room for
+                break
             if stream not in r.waited:
                 stream.wait_event(r.ready)
                 r.waited.append(stream)
-            take = min(r.n - r.next, self.step_queries - total)
-            segs.append((r.map, r.queries, r.order, r.D, None, r.next, take))
+            take = min(r.n - r.next, room)
+            seg = (r.map, r.queries, r.order, r.D, None, r.next, take)
+            segs.append(seg + (r.kind, r.omega) if is_area else seg)
             r.slices.append(ev)
             r.next += take
-            total += take
+            if is_area:
+                area += take
+            else:
+                total += take
             if r.next == r.n:
                 finishing.append(active.popleft())
         return segs, finishing
@@ -210,8 +226,10 @@ class ContinuousBatcher:
 
 
 def run_plain(maps, requests, realtime: bool = True, sort: int = pndf.PNDF_SORT_DEFAULT):
-    """Baseline: each batch launched alone (pndf_eval_batch) in arrival order;
-    sort = the query order within a batch (the library default unless given)."""
+    """Baseline: each batch launched alone (pndf_eval_batch, or
+    pndf_diffuse_projected_area for projected-area requests) in arrival
+    order; sort = the query order within a P-NDF batch (the library default
+    unless given)."""
     reqs = sorted(requests, key=lambda r: r.arrival)
     dev = maps[0].device
     stream = torch.cuda.Stream(dev)
@@ -227,7 +245,10 @@ def run_plain(maps, requests, realtime: bool = True, sort: int = pndf.PNDF_SORT_
                 time.sleep(wait)
         with torch.cuda.stream(stream):
             r.D = torch.empty(r.n, dtype=torch.float32, device=dev)
-            pndf.pndf_eval_batch_ex(maps[r.map], r.queries, out=r.D, sort=sort, stream=stream)
+            if r.kind == pndf.PNDF_SEGMENT_PROJECTED_AREA:
+                pndf.pndf_diffuse_projected_area(maps[r.map], r.queries, r.omega, out=r.D, stream=stream)
+            else:
+                pndf.pndf_eval_batch_ex(maps[r.map], r.queries, out=r.D, sort=sort, stream=stream)
             r.done = torch.cuda.Event(enable_timing=True)
             r.done.record(stream)
     torch.cuda.synchronize(dev)

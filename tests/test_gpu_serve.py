@@ -177,3 +177,55 @@ def test_autotune_picks_from_its_table(P, maps_and_requests):
     assert (t.step_queries, t.warps_per_cta, int(t.sort)) == (best[0], best[2], best[3])
     for h in hs:
         h.free()
+
+
+def test_mixed_steps_with_projected_area_equal_alone(P):
+    """Projected-area requests served in the same steps as P-NDF queries (a
+    binary16 scratches + flakes map, the glint + diffuse mix): every P equals
+    pndf_diffuse_projected_area on the same request alone, and every D equals
+    pndf_eval_batch_ex, bit for bit, through the C ABI steps and through the
+    continuous batcher."""
+    from paper_2505_08985_gb300 import serve
+    st = synth.mixed_map(n=512, n_cells=1200, n_grooves=40, seed=5, device=DEV).half()
+    h = P.pndf_build_hierarchy(st, bounds_fmt=P.PNDF_BOUNDS_F16_OUTWARD)
+    mix = synth.QueryMix(sigma=(1.0, 40.0), frac_near=0.7)
+    qp = synth.make_queries(st.float(), 3000, mix, 5)
+    qa = synth.make_queries(st.float(), 200, mix, 6)
+    w = synth.hemisphere_dirs(200, seed=7, device=DEV)
+    ref_D = P.pndf_eval_batch_ex(h, qp)
+    ref_P = P.pndf_diffuse_projected_area(h, qa, w)
+    A = P.PNDF_SEGMENT_PROJECTED_AREA
+    srv = P.pndf_server_create([h], max_area_requests=128)
+    D = torch.full((3000,), float("nan"), device=DEV)
+    Pv = torch.full((200,), float("nan"), device=DEV)
+    P.pndf_server_step(srv, [(0, qp, None, D, None, 0, 2000), (0, qa, None, Pv, None, 0, 128, A, w)])
+    P.pndf_server_step(srv, [(0, qa, None, Pv, None, 128, 72, A, w), (0, qp, None, D, None, 2000, 1000)])
+    P.pndf_server_sync(srv)
+    assert torch.equal(D, ref_D) and torch.equal(Pv, ref_P)
+    with pytest.raises(P.PndfError) as ei:  # more area requests than a step holds
+        P.pndf_server_step(srv, [(0, qa, None, Pv, None, 0, 129, A, w)])
+    assert ei.value.code == 5
+    srv.destroy()
+    plain = P.pndf_server_create([h])
+    with pytest.raises(P.PndfError) as ei:  # a server created without area capacity
+        P.pndf_server_step(plain, [(0, qa, None, Pv, None, 0, 10, A, w)])
+    assert ei.value.code == 6
+    plain.destroy()
+    # through the batcher: a stream alternating P-NDF batches and area batches
+    reqs = []
+    for k in range(12):
+        if k % 2:
+            lo = 20 * (k // 2)
+            reqs.append(serve.Request(rid=k, map=0, queries=qa[lo:lo + 20].contiguous(), arrival=0.0,
+                                      kind=A, omega=w[lo:lo + 20].contiguous()))
+        else:
+            lo = 500 * (k // 2)
+            reqs.append(serve.Request(rid=k, map=0, queries=qp[lo:lo + 500].contiguous(), arrival=0.0))
+    b = serve.ContinuousBatcher([h], step_queries=700, max_area_requests=16)
+    b.run(reqs, realtime=False)
+    for r in reqs:
+        lo = (20 if r.kind == A else 500) * (r.rid // 2)
+        want = ref_P[lo:lo + 20] if r.kind == A else ref_D[lo:lo + 500]
+        assert torch.equal(r.D, want), r.rid
+    b.close()
+    h.free()

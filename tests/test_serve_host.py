@@ -91,3 +91,37 @@ def test_step_formation_slices_fifo():
     # a step stops only when full or out of slices (or out of requests)
     assert all(total == 256 or nsegs == 3 for total, nsegs in shape[:-1])
     assert shape == [(256, 2), (256, 1), (256, 1), (256, 1), (86, 3), (256, 1), (144, 1)]
+
+
+def test_step_formation_keeps_area_and_pndf_budgets():
+    """Projected-area requests join steps under their own budget
+    (max_area_requests per step) beside the P-NDF queries (step_queries);
+    the step ends, FIFO, at the first request it has no room for."""
+    AREA = serve.pndf.PNDF_SEGMENT_PROJECTED_AREA
+    spec = [(0, 100), (AREA, 3), (0, 300), (AREA, 9), (0, 20)]
+    reqs = deque()
+    for k, (kind, n) in enumerate(spec):
+        r = serve.Request(rid=k, map=0, queries=torch.zeros(n, 8), arrival=0.0, kind=kind,
+                          omega=torch.zeros(n, 3) if kind == AREA else None)
+        r.next, r.waited, r.slices = 0, [], []
+        reqs.append(r)
+    all_reqs = list(reqs)
+    b = _batcher(step_queries=256, max_segments=8)
+    b.area_cap = 4
+    steps = []
+    while reqs:
+        segs, fin = b._form_step(reqs, b.step_stream, object())
+        steps.append(segs)
+        area = sum(s[6] for s in segs if len(s) > 7)
+        pn = sum(s[6] for s in segs if len(s) == 7)
+        assert area <= 4 and pn <= 256 and segs
+        for s in segs:
+            if len(s) > 7:
+                assert s[7] == AREA and s[8] is not None and s[2] is None
+    covered = {r.rid: sum(s[6] for st in steps for s in st if s[1] is r.queries) for r in all_reqs}
+    assert covered == {k: n for k, (_, n) in enumerate(spec)}
+    shape = [[(len(s) > 7, s[5], s[6]) for s in st] for st in steps]
+    assert shape[0] == [(False, 0, 100), (True, 0, 3), (False, 0, 156)]
+    assert shape[1] == [(False, 156, 144), (True, 0, 4)]
+    assert shape[2] == [(True, 4, 4)]
+    assert shape[3] == [(True, 8, 1), (False, 0, 20)]
