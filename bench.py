@@ -589,6 +589,14 @@ def run_mixed(args, dev):
     torch.cuda.synchronize()
     pa_ms, pn_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
     assert torch.isfinite(P).all() and torch.isfinite(D).all()
+    # the same P-NDF batch with one warp per query (no division of large footprints)
+    D1 = torch.empty_like(D)
+    ev[0].record()
+    pndf.pndf_eval_batch_ex(h, qp, out=D1, split=False)
+    ev[1].record()
+    torch.cuda.synchronize()
+    pn_whole_ms = ev[0].elapsed_time(ev[1])
+    assert torch.equal(D, D1)
     tris = footprint_triangles(qa, st.shape[0])
     acc = None
     if not args.no_accuracy:
@@ -639,7 +647,8 @@ def run_mixed(args, dev):
                         "P-NDF queries, sigma log-U(1, 1024), light uniform on the hemisphere",
             "projected_area": {"requests_per_s": nq / (pa_ms / 1e3), "ms": pa_ms, "triangles": tris,
                                "triangles_per_s": tris / (pa_ms / 1e3)},
-            "pndf": {"queries_per_s": nq / (pn_ms / 1e3), "ms": pn_ms},
+            "pndf": {"queries_per_s": nq / (pn_ms / 1e3), "ms": pn_ms, "ms_one_warp_per_query": pn_whole_ms,
+                     "same_bits_one_warp_per_query": True},
             "map_n": st.shape[0],
             "ggx_fit": {"build_ms": fit_ms, "lambda_ms": lam_ms, "lambda_requests": qb.shape[0],
                         "lambda_per_s": qb.shape[0] / (lam_ms / 1e3),

@@ -139,7 +139,13 @@ typedef struct pndf_eval_config {
                             /* an equilateral one of Jacobian jac_eps centred at its   */
                             /* normal centroid.  Gaussian kernel, hierarchy mode, no   */
                             /* cluster cut (else UNSUPPORTED).                         */
-    int32_t reserved;       /* must be 0                                              */
+    int32_t split;          /* 0 = library default: a footprint whose support box is   */
+                            /* much larger than the batch's average share per warp is  */
+                            /* divided into tiles of pyramid nodes evaluated by        */
+                            /* several warps (hierarchy mode without the cluster cut);  */
+                            /* -1 = one warp per query.  The result is the same bits   */
+                            /* either way (each query's sum is exact); only the node   */
+                            /* count in the stats differs.                             */
     void *ev_begin;         /* optional cudaEvent_t recorded on the stream just before */
     void *ev_end;           /* and just after the traversal kernel (NULL = none)       */
 } pndf_eval_config;

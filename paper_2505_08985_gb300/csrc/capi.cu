@@ -337,7 +337,7 @@ pndf_status pndf_eval_batch_ex(const pndf_hierarchy *h, const pndf_query *q_dev,
     if (!(c.tau >= 0.f) || !isfinite(c.tau)) return PNDF_ERR_INVALID_ARG;
     if (c.kernel != PNDF_KERNEL_GAUSS && c.kernel != PNDF_KERNEL_DISK && c.kernel != PNDF_KERNEL_BOX)
         return PNDF_ERR_INVALID_ARG;
-    if (!(c.jac_eps == 0.f || (c.jac_eps >= 1e-9f && c.jac_eps <= 1e-2f)) || c.reserved != 0)
+    if (!(c.jac_eps == 0.f || (c.jac_eps >= 1e-9f && c.jac_eps <= 1e-2f)) || !(c.split == 0 || c.split == -1))
         return PNDF_ERR_INVALID_ARG;
     if (c.jac_eps > 0.f && (c.kernel != PNDF_KERNEL_GAUSS || c.mode != PNDF_MODE_HIERARCHY || c.tau > 0.f))
         return PNDF_ERR_UNSUPPORTED;

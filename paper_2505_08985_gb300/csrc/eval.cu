@@ -312,20 +312,55 @@ __device__ __forceinline__ uint32_t pack(int l, bool inside, uint32_t m)
 }
 constexpr uint32_t kMortonMask = (1u << 27) - 1u;
 
+// A query's sum is exact: every contribution (an FP32 value >= 0) is added
+// into a 128-bit fixed-point number with 64 fraction bits, value =
+// (hi 2^64 + lo) 2^-64, so the result does not depend on the order in which
+// the hits are found or on how the query's work is divided among warps.  A
+// contribution is rounded to the nearest multiple of 2^-64 (5.4e-20) once;
+// the total is rounded to FP32 once at the end.  A contribution of 2^63 or
+// more, or a sum past 2^64 (only possible for normal triangles of area far
+// below 1e-20), marks the query kHuge and its D is +inf.
 struct Acc {
-    float s, c;  // Neumaier compensated sum
+    unsigned long long lo, hi;
     uint32_t hits, hash, tests, fp64, degen, leaves, nodes, quads, cchecks, clusters;
     uint32_t flags;
 };
+constexpr uint32_t kHuge = 1u << 30;  // internal flag bit: the sum is out of the fixed-point range
 
 __device__ __forceinline__ void acc_add(Acc &a, float w)
 {
-    float t = a.s + w;
-    if (fabsf(a.s) >= fabsf(w))
-        a.c += (a.s - t) + w;
-    else
-        a.c += (w - t) + a.s;
-    a.s = t;
+    const uint32_t b = __float_as_uint(w);
+    const int ex = int(b >> 23);  // sign 0: the biased exponent
+    if (ex == 0 || (b >> 31)) return;  // zero or subnormal (< 2^-126: rounds to 0)
+    if (ex >= 127 + 63) {              // 2^63 or more, inf or NaN
+        a.flags |= kHuge;
+        return;
+    }
+    const unsigned long long m = (b & 0x7fffffu) | 0x800000u;  // w = m 2^(ex - 150)
+    const int sh = ex - 150 + 64;                               // w 2^64 = m 2^sh
+    unsigned long long dl, dh = 0ull;
+    if (sh < 0) {
+        if (sh < -24) return;                        // below 2^-65: rounds to 0
+        dl = (m + (1ull << (-sh - 1))) >> (-sh);     // round half up
+    } else if (sh < 64) {
+        dl = m << sh;
+        if (sh > 40) dh = m >> (64 - sh);
+    } else {
+        dl = 0ull;
+        dh = m << (sh - 64);  // sh <= 189 - 86: dh < 2^63
+    }
+    a.lo += dl;
+    const unsigned long long carry = a.lo < dl ? 1ull : 0ull;
+    const unsigned long long h0 = a.hi;
+    a.hi += dh + carry;
+    if (a.hi < h0) a.flags |= kHuge;  // past 2^64
+}
+
+// 128-bit fixed point -> FP32 (through FP64: deterministic, within an ulp).
+__device__ __forceinline__ float acc_value(unsigned long long lo, unsigned long long hi, uint32_t flags)
+{
+    if (flags & kHuge) return __int_as_float(0x7f800000);
+    return float(double(hi) + double(lo) * 0x1p-64);
 }
 
 // Test the lane's triangle of a leaf block and accumulate its contribution.
@@ -856,6 +891,176 @@ __device__ __forceinline__ int entry_level(const Query &q, int L)
     return l;
 }
 
+// The hierarchical descent from the nodes [a0, a1] x [c0, c1] of level e
+// (at most 4 x 4 of them) into the lane's accumulator: the whole query when
+// they are its entry nodes, one tile of it when a large footprint is divided
+// among warps.  Node boxes nest (a parent's normal box and uv box contain its
+// children's), so a leaf block is reached from any level above it exactly
+// when every node test on its path passes: the hit set, and with the exact
+// sum the result, does not depend on the level the descent starts from.
+template <int BFMT, int TFMT, bool STATS, bool CLUSTER, bool CLAMP>
+__device__ __forceinline__ void eval_range(const MapDesc &d, const ClusterDesc &cd, const Query &q, int e, int a0,
+                                           int a1, int c0, int c1, int lane, uint32_t *stk, uint32_t *lq,
+                                           uint32_t *ring, float4 *hits, Acc &acc)
+{
+    int top = 0, nleaf = 0, ncl = 0;
+    const unsigned lt = (1u << lane) - 1u;
+    // entry nodes: at most 4 x 4
+    {
+        int a = a0 + (lane & 3), c = c0 + (lane >> 2);
+        bool valid = lane < 16 && a <= a1 && c <= c1;
+        bool pass = valid && node_test<BFMT, CLAMP>(d, q, e, a, c);
+        bool inside = pass && node_inside(q, e, a, c);
+        bool cut = false;
+        if (STATS) acc.nodes += valid ? 1u : 0u;
+        if (CLUSTER && pass) {  // the cut of Sec. 4.2: e <= r_x r_y tau
+            cut = __ldg(cd.ce[e] + morton2(a, c)) <= q.theta;
+            if (STATS) acc.cchecks++;
+        }
+        unsigned m = __ballot_sync(kFull, pass && !cut);
+        unsigned mc = __ballot_sync(kFull, cut);
+        if (pass && !cut) {
+            int pos = __popc(m & lt);
+            uint32_t ent = pack(e, inside, morton2(a, c));
+            if (e == kLeafLevel)
+                lq[pos] = ent;
+            else
+                stk[pos] = ent;
+        }
+        if (CLUSTER && cut) lq[kLeafQ - 1 - __popc(mc & lt)] = pack(e, false, morton2(a, c));
+        if (e == kLeafLevel)
+            nleaf = __popc(m);
+        else
+            top = __popc(m);
+        ncl = __popc(mc);
+        __syncwarp();
+    }
+    bool overflow = false;
+    LeafState ls{ring, ring + kRing, hits, 0u, 0u, 0u, 0, 0, 0};
+    while (true) {
+        // leaf blocks are filtered eight to a pass (four lanes each): while
+        // the stack still holds nodes only whole passes run, and the rest
+        // (fewer than 8) waits at the front of the queue for the next step
+        const int nrun = top == 0 ? nleaf : (nleaf & ~7);
+        process_leaves<BFMT, TFMT, STATS, CLAMP>(d, q, lq, nrun, ls, lane, acc);
+        if (nrun > 0 && nrun < nleaf) {
+            const int rest = nleaf - nrun;  // < 8 <= nrun: source and target do not overlap
+            uint32_t v = lane < rest ? lq[nrun + lane] : 0u;
+            if (lane < rest) lq[lane] = v;
+            __syncwarp();
+        }
+        nleaf -= nrun;
+        if (CLUSTER) {
+            // cut nodes sit at the back of the leaf queue
+            for (int k0 = 0; k0 < ncl; k0 += 32) {
+                test_clusters<STATS>(d, cd, q, lq + kLeafQ - 1 - k0, min(32, ncl - k0), ls, lane, acc);
+                __syncwarp();
+            }
+            ncl = 0;
+        }
+        if (top == 0) break;
+        // pop up to 16 nodes; lane k tests child (k & 3) of popped nodes
+        // (k >> 2) and (k >> 2) + 8, so two box loads per lane are in flight
+        int npop = min(top, 16);
+        top -= npop;
+        bool pass[2], ins[2], cut[2] = {false, false};
+        int cl[2];
+        uint32_t cm[2];
+        uint4 bx[2];
+        float ev[2];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            int slot = (lane >> 2) + 8 * r;
+            uint32_t ent = slot < npop ? stk[top + slot] : 0u;
+            cl[r] = int(ent >> 28) - 1;
+            cm[r] = ((ent & kMortonMask) << 2) | uint32_t(lane & 3);
+            ins[r] = (ent >> 27) & 1u;
+            pass[r] = slot < npop;
+            if (pass[r] && !ins[r]) {
+                // parent straddles the ellipse: test this child's uv box
+                uint32_t a = compact1by1(cm[r]), c = compact1by1(cm[r] >> 1);
+                pass[r] = node_in_footprint(q, cl[r], a, c);
+                ins[r] = pass[r] && node_inside(q, cl[r], a, c);
+            }
+            if (STATS && slot < npop) acc.nodes++;
+        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r)  // both box loads issue before either is used
+            if (pass[r]) {
+                bx[r] = node_box<BFMT>(d, cl[r], cm[r]);
+                if (CLUSTER) ev[r] = __ldg(cd.ce[cl[r]] + cm[r]);
+            }
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            pass[r] = pass[r] && stored_box_holds<BFMT, CLAMP>(bx[r], q);
+            if (CLUSTER && pass[r]) {  // the cut of Sec. 4.2: e <= r_x r_y tau
+                cut[r] = ev[r] <= q.theta;
+                if (STATS) acc.cchecks++;
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            bool to_leaf = pass[r] && !cut[r] && cl[r] == kLeafLevel;
+            bool to_stack = pass[r] && !cut[r] && cl[r] > kLeafLevel;
+            unsigned ml = __ballot_sync(kFull, to_leaf);
+            unsigned ms = __ballot_sync(kFull, to_stack);
+            if (CLUSTER) {
+                unsigned mc = __ballot_sync(kFull, cut[r]);
+                if (cut[r]) lq[kLeafQ - 1 - ncl - __popc(mc & lt)] = pack(cl[r], false, cm[r]);
+                ncl += __popc(mc);
+            }
+            if (to_leaf) lq[nleaf + __popc(ml & lt)] = pack(cl[r], ins[r], cm[r]);
+            if (to_stack) {
+                int pos = top + __popc(ms & lt);
+                if (pos < kStackCap) stk[pos] = pack(cl[r], ins[r], cm[r]);
+            }
+            nleaf += __popc(ml);
+            top += __popc(ms);
+            if (top > kStackCap) {
+                top = kStackCap;
+                overflow = true;
+            }
+        }
+        __syncwarp();
+    }
+    if (ls.nsq > 0) capsule_round<BFMT, TFMT, STATS, CLAMP>(d, q, ls, ls.nsq, lane, acc);  // nsq < 64 here
+    if (ls.ncq > 0) test_quads<TFMT, STATS, CLAMP>(d, q, ls, ls.ncq, lane, acc);  // ncq < 32 here
+    if (ls.nh > 0) drain_hits<STATS>(q, d.n, d.L, ls.hits, ls.hh, ls.nh, lane, acc);  // nh < 32 here
+    if (overflow) acc.flags |= PNDF_QF_OVERFLOW;
+}
+
+// Warp total of the lanes' accumulators: the fixed-point sum (exact), the
+// flags and, with STATS, the counters (all lanes hold the result).
+template <bool STATS>
+__device__ __forceinline__ void warp_total(Acc &acc, unsigned long long &lo, unsigned long long &hi, uint32_t &fl)
+{
+    lo = acc.lo;
+    hi = acc.hi;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long lo_o = __shfl_xor_sync(kFull, lo, off);
+        const unsigned long long hi_o = __shfl_xor_sync(kFull, hi, off);
+        lo += lo_o;
+        const unsigned long long h0 = hi;
+        hi += hi_o + (lo < lo_o ? 1ull : 0ull);
+        if (hi < h0) acc.flags |= kHuge;
+    }
+    fl = __reduce_or_sync(kFull, acc.flags);
+    if (STATS) {
+        acc.hits = __reduce_add_sync(kFull, acc.hits);
+        acc.hash = __reduce_add_sync(kFull, acc.hash);
+        acc.tests = __reduce_add_sync(kFull, acc.tests);
+        acc.fp64 = __reduce_add_sync(kFull, acc.fp64);
+        acc.degen = __reduce_add_sync(kFull, acc.degen);
+        acc.nodes = __reduce_add_sync(kFull, acc.nodes);
+        acc.leaves = __reduce_add_sync(kFull, acc.leaves);
+        acc.quads = __reduce_add_sync(kFull, acc.quads);
+        acc.cchecks = __reduce_add_sync(kFull, acc.cchecks);
+        acc.clusters = __reduce_add_sync(kFull, acc.clusters);
+    }
+}
+
 // KERN: the footprint kernel (pndf_kernel), a compile-time constant so the
 // query's kernel fields and branches fold away (each kernel is its own
 // instantiation).
@@ -895,158 +1100,14 @@ __device__ void eval_one(const MapDesc &d, const ClusterDesc &cd, float tau, flo
         int a0, a1, c0, c1;
         node_range(q.x, q.rx, sz, S, a0, a1);
         node_range(q.y, q.ry, sz, S, c0, c1);
-        int top = 0, nleaf = 0, ncl = 0;
-        const unsigned lt = (1u << lane) - 1u;
-        // entry nodes: at most 4 x 4
-        {
-            int a = a0 + (lane & 3), c = c0 + (lane >> 2);
-            bool valid = lane < 16 && a <= a1 && c <= c1;
-            bool pass = valid && node_test<BFMT, CLAMP>(d, q, e, a, c);
-            bool inside = pass && node_inside(q, e, a, c);
-            bool cut = false;
-            if (STATS) acc.nodes += valid ? 1u : 0u;
-            if (CLUSTER && pass) {  // the cut of Sec. 4.2: e <= r_x r_y tau
-                cut = __ldg(cd.ce[e] + morton2(a, c)) <= q.theta;
-                if (STATS) acc.cchecks++;
-            }
-            unsigned m = __ballot_sync(kFull, pass && !cut);
-            unsigned mc = __ballot_sync(kFull, cut);
-            if (pass && !cut) {
-                int pos = __popc(m & lt);
-                uint32_t ent = pack(e, inside, morton2(a, c));
-                if (e == kLeafLevel)
-                    lq[pos] = ent;
-                else
-                    stk[pos] = ent;
-            }
-            if (CLUSTER && cut) lq[kLeafQ - 1 - __popc(mc & lt)] = pack(e, false, morton2(a, c));
-            if (e == kLeafLevel)
-                nleaf = __popc(m);
-            else
-                top = __popc(m);
-            ncl = __popc(mc);
-            __syncwarp();
-        }
-        bool overflow = false;
-        LeafState ls{ring, ring + kRing, hits, 0u, 0u, 0u, 0, 0, 0};
-        while (true) {
-            // leaf blocks are filtered eight to a pass (four lanes each): while
-            // the stack still holds nodes only whole passes run, and the rest
-            // (fewer than 8) waits at the front of the queue for the next step
-            const int nrun = top == 0 ? nleaf : (nleaf & ~7);
-            process_leaves<BFMT, TFMT, STATS, CLAMP>(d, q, lq, nrun, ls, lane, acc);
-            if (nrun > 0 && nrun < nleaf) {
-                const int rest = nleaf - nrun;  // < 8 <= nrun: source and target do not overlap
-                uint32_t v = lane < rest ? lq[nrun + lane] : 0u;
-                if (lane < rest) lq[lane] = v;
-                __syncwarp();
-            }
-            nleaf -= nrun;
-            if (CLUSTER) {
-                // cut nodes sit at the back of the leaf queue
-                for (int k0 = 0; k0 < ncl; k0 += 32) {
-                    test_clusters<STATS>(d, cd, q, lq + kLeafQ - 1 - k0, min(32, ncl - k0), ls, lane, acc);
-                    __syncwarp();
-                }
-                ncl = 0;
-            }
-            if (top == 0) break;
-            // pop up to 16 nodes; lane k tests child (k & 3) of popped nodes
-            // (k >> 2) and (k >> 2) + 8, so two box loads per lane are in flight
-            int npop = min(top, 16);
-            top -= npop;
-            bool pass[2], ins[2], cut[2] = {false, false};
-            int cl[2];
-            uint32_t cm[2];
-            uint4 bx[2];
-            float ev[2];
-#pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                int slot = (lane >> 2) + 8 * r;
-                uint32_t ent = slot < npop ? stk[top + slot] : 0u;
-                cl[r] = int(ent >> 28) - 1;
-                cm[r] = ((ent & kMortonMask) << 2) | uint32_t(lane & 3);
-                ins[r] = (ent >> 27) & 1u;
-                pass[r] = slot < npop;
-                if (pass[r] && !ins[r]) {
-                    // parent straddles the ellipse: test this child's uv box
-                    uint32_t a = compact1by1(cm[r]), c = compact1by1(cm[r] >> 1);
-                    pass[r] = node_in_footprint(q, cl[r], a, c);
-                    ins[r] = pass[r] && node_inside(q, cl[r], a, c);
-                }
-                if (STATS && slot < npop) acc.nodes++;
-            }
-#pragma unroll
-            for (int r = 0; r < 2; ++r)  // both box loads issue before either is used
-                if (pass[r]) {
-                    bx[r] = node_box<BFMT>(d, cl[r], cm[r]);
-                    if (CLUSTER) ev[r] = __ldg(cd.ce[cl[r]] + cm[r]);
-                }
-#pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                pass[r] = pass[r] && stored_box_holds<BFMT, CLAMP>(bx[r], q);
-                if (CLUSTER && pass[r]) {  // the cut of Sec. 4.2: e <= r_x r_y tau
-                    cut[r] = ev[r] <= q.theta;
-                    if (STATS) acc.cchecks++;
-                }
-            }
-            __syncwarp();
-#pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                bool to_leaf = pass[r] && !cut[r] && cl[r] == kLeafLevel;
-                bool to_stack = pass[r] && !cut[r] && cl[r] > kLeafLevel;
-                unsigned ml = __ballot_sync(kFull, to_leaf);
-                unsigned ms = __ballot_sync(kFull, to_stack);
-                if (CLUSTER) {
-                    unsigned mc = __ballot_sync(kFull, cut[r]);
-                    if (cut[r]) lq[kLeafQ - 1 - ncl - __popc(mc & lt)] = pack(cl[r], false, cm[r]);
-                    ncl += __popc(mc);
-                }
-                if (to_leaf) lq[nleaf + __popc(ml & lt)] = pack(cl[r], ins[r], cm[r]);
-                if (to_stack) {
-                    int pos = top + __popc(ms & lt);
-                    if (pos < kStackCap) stk[pos] = pack(cl[r], ins[r], cm[r]);
-                }
-                nleaf += __popc(ml);
-                top += __popc(ms);
-                if (top > kStackCap) {
-                    top = kStackCap;
-                    overflow = true;
-                }
-            }
-            __syncwarp();
-        }
-        if (ls.nsq > 0) capsule_round<BFMT, TFMT, STATS, CLAMP>(d, q, ls, ls.nsq, lane, acc);  // nsq < 64 here
-        if (ls.ncq > 0) test_quads<TFMT, STATS, CLAMP>(d, q, ls, ls.ncq, lane, acc);  // ncq < 32 here
-        if (ls.nh > 0) drain_hits<STATS>(q, d.n, d.L, ls.hits, ls.hh, ls.nh, lane, acc);  // nh < 32 here
-        if (overflow) acc.flags |= PNDF_QF_OVERFLOW;
+        eval_range<BFMT, TFMT, STATS, CLUSTER, CLAMP>(d, cd, q, e, a0, a1, c0, c1, lane, stk, lq, ring, hits, acc);
     }
-    // warp reduction (fixed order: deterministic for a given query)
-    float s = acc.s, c = acc.c;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        float so = __shfl_down_sync(kFull, s, off);
-        float co = __shfl_down_sync(kFull, c, off);
-        float t = s + so;
-        float err = fabsf(s) >= fabsf(so) ? (s - t) + so : (so - t) + s;
-        s = t;
-        c += co + err;
-    }
-    uint32_t fl = __reduce_or_sync(kFull, acc.flags);
-    if (STATS) {
-        acc.hits = __reduce_add_sync(kFull, acc.hits);
-        acc.hash = __reduce_add_sync(kFull, acc.hash);
-        acc.tests = __reduce_add_sync(kFull, acc.tests);
-        acc.fp64 = __reduce_add_sync(kFull, acc.fp64);
-        acc.degen = __reduce_add_sync(kFull, acc.degen);
-        acc.nodes = __reduce_add_sync(kFull, acc.nodes);
-        acc.leaves = __reduce_add_sync(kFull, acc.leaves);
-        acc.quads = __reduce_add_sync(kFull, acc.quads);
-        acc.cchecks = __reduce_add_sync(kFull, acc.cchecks);
-        acc.clusters = __reduce_add_sync(kFull, acc.clusters);
-    }
+    unsigned long long lo, hi;
+    uint32_t fl;
+    warp_total<STATS>(acc, lo, hi, fl);
     if (lane == 0) {
-        D_out = s + c;
+        D_out = acc_value(lo, hi, fl);
+        fl &= ~kHuge;
         flags_out = fl;
         if (fl & PNDF_QF_OVERFLOW) record_status(d.status, &g_status_eval, PNDF_QF_OVERFLOW);
         if (STATS)
@@ -1055,12 +1116,188 @@ __device__ void eval_one(const MapDesc &d, const ClusterDesc &cd, float tau, flo
     }
 }
 
+__constant__ ClusterDesc kNoClusters;  // never read: the variants without the cut
+
+// ---- large footprints divided among warps ----
+//
+// One warp per query leaves a batch waiting on its largest footprints: a
+// sigma = 1024 query on a 16384^2 map is about 100 ms of one warp, longer
+// than the rest of a few-thousand-query batch together.  Before the
+// traversal, split_work sums a work estimate over the batch (the area of each
+// support's bounding box) and split_plan divides every query whose estimate
+// is more than twice the target w_t = max(W / (4 x resident warps), 2.6e5)
+// (2.6e5: the box of a sigma = 64 footprint) into tiles of at most 4 x 4
+// nodes of one level, the deepest level (>= 4, at most 256 tiles) whose tile
+// count reaches its estimate / w_t.  The traversal hands out the tiles first
+// (largest queries first), then the undivided queries; the last warp to
+// finish a query's tiles writes its result.  The sum is exact, so the
+// result is the same bits whichever way the query was divided.
+constexpr int kSplitMinLevel = 4;
+constexpr uint32_t kSplitMaxTiles = 256;
+constexpr float kSplitMinWork = 2.6e5f;
+constexpr int kSplitPerWarp = 4;
+
+struct SplitEntry {
+    uint32_t qi, tiles;        // the query (caller index) and its tile count
+    unsigned long long base;   // index of its first tile among all tiles
+    int32_t level, pad;        // node level of the tiles
+    unsigned long long lo, hi; // fixed-point sum of the finished tiles
+    uint32_t done, flags;      // tiles finished; OR of their flags
+    pndf_query_stats st;       // summed counters (stats launches)
+};
+
+struct SplitPlan {
+    SplitEntry *entries;       // null: no division
+    uint8_t *marker;           // per query (caller index): 1 = divided into tiles
+    unsigned long long *ctr;   // (entries << 40) | tiles reserved
+    double *work;              // the batch's summed estimate
+    uint32_t cap;              // entries capacity
+    int resident_warps;
+};
+
+__device__ __forceinline__ float split_estimate(const Query &q)
+{
+    return q.valid ? 64.f + 4.f * q.rx * q.ry : 64.f;
+}
+
+template <int KERN>
+__global__ void split_work(const pndf_query *__restrict__ qs, int64_t nq, float jac_eps, double *__restrict__ work)
+{
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < nq; k += int64_t(gridDim.x) * blockDim.x)
+        acc += double(split_estimate(make_query(qs[k], KERN, jac_eps)));
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (int(threadIdx.x) < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(work, red[0]);
+}
+
+// Tiles of level l over the support's bounding box: ceil(nx / 4) ceil(ny / 4).
+__device__ __forceinline__ uint32_t split_tiles(const Query &q, int L, int l, int &a0, int &a1, int &c0, int &c1)
+{
+    const int S = 1 << (L - l);
+    const float sz = float(1u << l);
+    node_range(q.x, q.rx, sz, S, a0, a1);
+    node_range(q.y, q.ry, sz, S, c0, c1);
+    if (a0 > a1 || c0 > c1) return 0u;
+    return uint32_t((a1 - a0) / 4 + 1) * uint32_t((c1 - c0) / 4 + 1);
+}
+
+template <int KERN>
+__global__ void split_plan(MapDesc d, const pndf_query *__restrict__ qs, int64_t nq, float jac_eps, SplitPlan p)
+{
+    const double W = *p.work;
+    const float wt = fmaxf(float(W / (double(kSplitPerWarp) * p.resident_warps)), kSplitMinWork);
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < nq; k += int64_t(gridDim.x) * blockDim.x) {
+        const Query q = make_query(qs[k], KERN, jac_eps);
+        const float w = split_estimate(q);
+        uint8_t mark = 0;
+        if (q.valid && w > 2.f * wt) {
+            const float target = w / wt;
+            int best = -1, a0, a1, c0, c1;
+            uint32_t bt = 0;
+            for (int l = entry_level(q, d.L) - 1; l >= kSplitMinLevel; --l) {
+                const uint32_t t = split_tiles(q, d.L, l, a0, a1, c0, c1);
+                if (t > kSplitMaxTiles) break;
+                best = l;
+                bt = t;
+                if (float(t) >= target) break;
+            }
+            if (best >= 0 && bt >= 2) {
+                const unsigned long long old = atomicAdd(p.ctr, (1ull << 40) | bt);
+                const unsigned long long idx = old >> 40;
+                if (idx < p.cap) {
+                    SplitEntry &E = p.entries[idx];
+                    E.qi = uint32_t(k);
+                    E.tiles = bt;
+                    E.base = old & ((1ull << 40) - 1ull);
+                    E.level = best;
+                    E.pad = 0;
+                    E.lo = E.hi = 0ull;
+                    E.done = E.flags = 0u;
+                    E.st = pndf_query_stats{0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+                    mark = 1;
+                }
+            }
+        }
+        p.marker[k] = mark;
+    }
+}
+
+// Work index k < ntiles: the entry of the divided query it belongs to (the
+// last entry whose first tile is <= k) and the tile's node range.
+__device__ __forceinline__ int tile_entry(const SplitPlan &p, int n_entries, unsigned long long k)
+{
+    int lo = 0, hi = n_entries - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&p.entries[mid].base) <= k)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void tile_range(const Query &q, int L, int l, uint32_t j, int &a0, int &a1, int &c0, int &c1)
+{
+    int b0, b1, d0, d1;
+    split_tiles(q, L, l, b0, b1, d0, d1);
+    const int ntx = (b1 - b0) / 4 + 1;
+    a0 = b0 + 4 * int(j % uint32_t(ntx));
+    c0 = d0 + 4 * int(j / uint32_t(ntx));
+    a1 = min(b1, a0 + 3);
+    c1 = min(d1, c0 + 3);
+}
+
+// Lane 0: fold a tile's warp total into its query's entry; the warp that
+// folds in the last tile writes D, the flags and the counters.
+template <bool STATS>
+__device__ __forceinline__ void tile_finish(const MapDesc &d, SplitEntry &E, const Acc &acc, unsigned long long lo,
+                                            unsigned long long hi, uint32_t fl, float *D, uint32_t *flags,
+                                            pndf_query_stats *stats)
+{
+    const unsigned long long old = atomicAdd(&E.lo, lo);
+    const unsigned long long add_hi = hi + (old + lo < old ? 1ull : 0ull);
+    const unsigned long long old_hi = atomicAdd(&E.hi, add_hi);
+    if (old_hi + add_hi < old_hi) fl |= kHuge;
+    if (fl) atomicOr(&E.flags, fl);
+    if (STATS) {
+        atomicAdd(&E.st.nodes, acc.nodes);
+        atomicAdd(&E.st.leaf_blocks, acc.leaves);
+        atomicAdd(&E.st.tri_tests, acc.tests);
+        atomicAdd(&E.st.hits, acc.hits);
+        atomicAdd(&E.st.hit_hash, acc.hash);
+        atomicAdd(&E.st.fp64_tris, acc.fp64);
+        atomicAdd(&E.st.degenerate, acc.degen);
+        atomicAdd(&E.st.quads, acc.quads);
+    }
+    __threadfence();
+    if (atomicAdd(&E.done, 1u) == __ldg(&E.tiles) - 1u) {
+        __threadfence();
+        const uint32_t qi = __ldg(&E.qi);
+        const uint32_t f = __ldcg(&E.flags);
+        D[qi] = acc_value(__ldcg(&E.lo), __ldcg(&E.hi), f);
+        if (flags) flags[qi] = f & ~kHuge;
+        if (f & PNDF_QF_OVERFLOW) record_status(d.status, &g_status_eval, PNDF_QF_OVERFLOW);
+        if (STATS)
+            stats[qi] = pndf_query_stats{__ldcg(&E.st.nodes),      __ldcg(&E.st.leaf_blocks), __ldcg(&E.st.tri_tests),
+                                         __ldcg(&E.st.hits),       __ldcg(&E.st.hit_hash),    __ldcg(&E.st.fp64_tris),
+                                         __ldcg(&E.st.degenerate), __ldcg(&E.st.quads),       0u,
+                                         0u};
+    }
+}
+
 template <int BFMT, int TFMT, bool STATS, bool FLAT, bool CLUSTER, int KERN>
 __global__ void __launch_bounds__(256, PNDF_TRAVERSE_MIN_CTAS)
     traverse_kernel(MapDesc d, ClusterDesc cd, float tau, float jac_eps, const pndf_query *__restrict__ qs,
                     const uint32_t *__restrict__ order, int64_t nq, float *__restrict__ D,
                     uint32_t *__restrict__ flags, pndf_query_stats *__restrict__ stats,
-                    unsigned long long *__restrict__ cursor)
+                    unsigned long long *__restrict__ cursor, SplitPlan sp)
 {
     extern __shared__ uint32_t smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1068,20 +1305,86 @@ __global__ void __launch_bounds__(256, PNDF_TRAVERSE_MIN_CTAS)
     uint32_t *lq = stk + kStackCap;
     uint32_t *ring = lq + kLeafQ;
     float4 *hits = reinterpret_cast<float4 *>(ring + kRing + kCapRing);
+    // the divided queries' tiles take the first s_ntiles work indices
+    __shared__ unsigned long long s_ntiles;
+    __shared__ int s_entries;
+    if (threadIdx.x == 0) {
+        int n = 0;
+        unsigned long long t = 0ull;
+        if (!FLAT && !CLUSTER && sp.entries) {
+            n = int(min(__ldcg(sp.ctr) >> 40, (unsigned long long)sp.cap));
+            if (n > 0) t = __ldcg(&sp.entries[n - 1].base) + __ldcg(&sp.entries[n - 1].tiles);
+        }
+        s_entries = n;
+        s_ntiles = t;
+    }
+    __syncthreads();
     while (true) {
         unsigned long long k = 0;
         if (lane == 0) k = atomicAdd(cursor, 1ull);
         k = __shfl_sync(kFull, k, 0);
-        if (k >= (unsigned long long)nq) break;
-        int64_t qi = order ? int64_t(order[k]) : int64_t(k);
-        pndf_query rec = qs[qi];
-        float Dv;
-        uint32_t fv;
-        eval_one<BFMT, TFMT, STATS, FLAT, CLUSTER, KERN>(d, cd, tau, jac_eps, rec, lane, stk, lq, ring, hits, Dv, fv,
-                                                         stats ? stats + qi : nullptr);
+        if (FLAT || CLUSTER) {
+            if (k >= (unsigned long long)nq) break;
+            const int64_t qi = order ? int64_t(order[k]) : int64_t(k);
+            float Dv;
+            uint32_t fv;
+            eval_one<BFMT, TFMT, STATS, FLAT, CLUSTER, KERN>(d, cd, tau, jac_eps, qs[qi], lane, stk, lq, ring, hits, Dv,
+                                                             fv, stats ? stats + qi : nullptr);
+            if (lane == 0) {
+                D[qi] = Dv;
+                if (flags) flags[qi] = fv;
+            }
+            continue;
+        }
+        // a tile of a divided query, or a whole query: one descent either way
+        constexpr bool CLAMP = KERN == kKernGaussClamp;
+        int ei = -1;  // the divided query's entry, or -1 for a whole query
+        uint32_t qi;
+        Query q;
+        int e, a0, a1, c0, c1;
+        if (k < s_ntiles) {
+            ei = tile_entry(sp, s_entries, k);
+            const SplitEntry &E = sp.entries[ei];
+            qi = __ldg(&E.qi);
+            q = make_query(qs[qi], KERN, jac_eps);
+            e = __ldg(&E.level);
+            tile_range(q, d.L, e, uint32_t(k - __ldg(&E.base)), a0, a1, c0, c1);
+        } else {
+            k -= s_ntiles;
+            if (k >= (unsigned long long)nq) break;
+            qi = order ? order[k] : uint32_t(k);
+            if (sp.entries && sp.marker[qi]) continue;  // evaluated as tiles
+            q = make_query(qs[qi], KERN, jac_eps);
+            if (!q.valid) {
+                if (lane == 0) {
+                    D[qi] = __int_as_float(0x7fc00000);
+                    if (flags) flags[qi] = PNDF_QF_INVALID;
+                    record_status(d.status, &g_status_eval, PNDF_QF_INVALID);
+                    if (STATS) stats[qi] = pndf_query_stats{0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+                }
+                continue;
+            }
+            e = entry_level(q, d.L);
+            const float sz = float(1u << e);
+            node_range(q.x, q.rx, sz, 1 << (d.L - e), a0, a1);
+            node_range(q.y, q.ry, sz, 1 << (d.L - e), c0, c1);
+        }
+        Acc acc = {};
+        eval_range<BFMT, TFMT, STATS, false, CLAMP>(d, cd, q, e, a0, a1, c0, c1, lane, stk, lq, ring, hits, acc);
+        unsigned long long lo, hi;
+        uint32_t fl;
+        warp_total<STATS>(acc, lo, hi, fl);
         if (lane == 0) {
-            D[qi] = Dv;
-            if (flags) flags[qi] = fv;
+            if (ei >= 0) {
+                tile_finish<STATS>(d, sp.entries[ei], acc, lo, hi, fl, D, flags, stats);
+            } else {
+                D[qi] = acc_value(lo, hi, fl);
+                if (flags) flags[qi] = fl & ~kHuge;
+                if (fl & PNDF_QF_OVERFLOW) record_status(d.status, &g_status_eval, PNDF_QF_OVERFLOW);
+                if (STATS)
+                    stats[qi] = pndf_query_stats{acc.nodes, acc.leaves, acc.tests, acc.hits,    acc.hash,
+                                                 acc.fp64,  acc.degen,  acc.quads, acc.cchecks, acc.clusters};
+            }
         }
     }
 }
@@ -1221,8 +1524,9 @@ inline size_t sort_hist_bytes(int64_t nq)
 template <int BFMT, int TFMT, bool STATS, bool FLAT, bool CLUSTER, int KERN>
 cudaError_t launch_traverse(const MapDesc &d, const ClusterDesc &cd, float tau, float jac_eps, const pndf_query *q,
                             const uint32_t *order, int64_t nq, float *D, uint32_t *flags, pndf_query_stats *stats,
-                            unsigned long long *cursor, int warps, int ctas_per_sm, cudaStream_t s)
+                            unsigned long long *cursor, int warps, int ctas_per_sm, SplitPlan sp, cudaStream_t s)
 {
+    if (FLAT || CLUSTER) sp.entries = nullptr;  // whole queries only (the cut depends on the entry level)
     auto kern = traverse_kernel<BFMT, TFMT, STATS, FLAT, CLUSTER, KERN>;
     int threads = warps * 32;
     size_t smem = size_t(warps) * kWarpSmemWords * sizeof(uint32_t);
@@ -1235,9 +1539,19 @@ cudaError_t launch_traverse(const MapDesc &d, const ClusterDesc &cd, float tau, 
     if (ctas_per_sm > 0 && ctas_per_sm < occ) occ = ctas_per_sm;
     int64_t want = (nq + warps - 1) / warps;
     int64_t grid = int64_t(sms) * occ;
-    if (grid > want) grid = want;
+    if (sp.entries) {
+        // the plan: the batch's work, then the division of its large footprints
+        sp.resident_warps = int(grid) * warps;
+        int64_t blocks = (nq + 255) / 256;
+        if (blocks > int64_t(sms) * 8) blocks = int64_t(sms) * 8;
+        split_work<KERN><<<unsigned(blocks), 256, 0, s>>>(q, nq, jac_eps, sp.work);
+        split_plan<KERN><<<unsigned(blocks), 256, 0, s>>>(d, q, nq, jac_eps, sp);
+        count_launches(2);
+    } else if (grid > want) {
+        grid = want;
+    }
     if (grid < 1) grid = 1;
-    kern<<<unsigned(grid), threads, smem, s>>>(d, cd, tau, jac_eps, q, order, nq, D, flags, stats, cursor);
+    kern<<<unsigned(grid), threads, smem, s>>>(d, cd, tau, jac_eps, q, order, nq, D, flags, stats, cursor, sp);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1245,44 +1559,46 @@ cudaError_t launch_traverse(const MapDesc &d, const ClusterDesc &cd, float tau, 
 template <int BFMT, int TFMT, int KERN>
 cudaError_t dispatch_kernel(const MapDesc &d, const ClusterDesc &cd, const pndf_query *q, const uint32_t *order,
                             int64_t nq, float *D, uint32_t *flags, pndf_query_stats *stats,
-                            unsigned long long *cursor, const pndf_eval_config &cfg, cudaStream_t s)
+                            unsigned long long *cursor, const pndf_eval_config &cfg, const SplitPlan &sp,
+                            cudaStream_t s)
 {
     const int warps = cfg.warps_per_cta > 0 ? cfg.warps_per_cta : 8;
     const int cps = cfg.ctas_per_sm;
     const float tau = cfg.tau;
     if (cfg.mode == PNDF_MODE_FLAT)
         return stats ? launch_traverse<BFMT, TFMT, true, true, false, KERN>(d, cd, 0.f, cfg.jac_eps, q, order, nq, D, flags, stats,
-                                                                             cursor, warps, cps, s)
+                                                                             cursor, warps, cps, sp, s)
                      : launch_traverse<BFMT, TFMT, false, true, false, KERN>(d, cd, 0.f, cfg.jac_eps, q, order, nq, D, flags, stats,
-                                                                              cursor, warps, cps, s);
+                                                                              cursor, warps, cps, sp, s);
     if (tau > 0.f)
         return stats ? launch_traverse<BFMT, TFMT, true, false, true, KERN>(d, cd, tau, cfg.jac_eps, q, order, nq, D, flags, stats,
-                                                                             cursor, warps, cps, s)
+                                                                             cursor, warps, cps, sp, s)
                      : launch_traverse<BFMT, TFMT, false, false, true, KERN>(d, cd, tau, cfg.jac_eps, q, order, nq, D, flags, stats,
-                                                                              cursor, warps, cps, s);
+                                                                              cursor, warps, cps, sp, s);
     return stats ? launch_traverse<BFMT, TFMT, true, false, false, KERN>(d, cd, 0.f, cfg.jac_eps, q, order, nq, D, flags, stats,
-                                                                          cursor, warps, cps, s)
+                                                                          cursor, warps, cps, sp, s)
                  : launch_traverse<BFMT, TFMT, false, false, false, KERN>(d, cd, 0.f, cfg.jac_eps, q, order, nq, D, flags, stats,
-                                                                           cursor, warps, cps, s);
+                                                                           cursor, warps, cps, sp, s);
 }
 
 template <int BFMT, int TFMT>
 cudaError_t dispatch_stats(const MapDesc &d, const ClusterDesc &cd, const pndf_query *q, const uint32_t *order,
                            int64_t nq, float *D, uint32_t *flags, pndf_query_stats *stats,
-                           unsigned long long *cursor, const pndf_eval_config &cfg, cudaStream_t s)
+                           unsigned long long *cursor, const pndf_eval_config &cfg, const SplitPlan &sp,
+                           cudaStream_t s)
 {
     if (cfg.jac_eps > 0.f)  // Gaussian, hierarchy mode, no cluster cut (checked by the caller)
         return stats ? launch_traverse<BFMT, TFMT, true, false, false, kKernGaussClamp>(
                            d, cd, 0.f, cfg.jac_eps, q, order, nq, D, flags, stats, cursor,
-                           cfg.warps_per_cta > 0 ? cfg.warps_per_cta : 8, cfg.ctas_per_sm, s)
+                           cfg.warps_per_cta > 0 ? cfg.warps_per_cta : 8, cfg.ctas_per_sm, sp, s)
                      : launch_traverse<BFMT, TFMT, false, false, false, kKernGaussClamp>(
                            d, cd, 0.f, cfg.jac_eps, q, order, nq, D, flags, stats, cursor,
-                           cfg.warps_per_cta > 0 ? cfg.warps_per_cta : 8, cfg.ctas_per_sm, s);
+                           cfg.warps_per_cta > 0 ? cfg.warps_per_cta : 8, cfg.ctas_per_sm, sp, s);
     if (cfg.kernel == PNDF_KERNEL_DISK)
-        return dispatch_kernel<BFMT, TFMT, PNDF_KERNEL_DISK>(d, cd, q, order, nq, D, flags, stats, cursor, cfg, s);
+        return dispatch_kernel<BFMT, TFMT, PNDF_KERNEL_DISK>(d, cd, q, order, nq, D, flags, stats, cursor, cfg, sp, s);
     if (cfg.kernel == PNDF_KERNEL_BOX)
-        return dispatch_kernel<BFMT, TFMT, PNDF_KERNEL_BOX>(d, cd, q, order, nq, D, flags, stats, cursor, cfg, s);
-    return dispatch_kernel<BFMT, TFMT, PNDF_KERNEL_GAUSS>(d, cd, q, order, nq, D, flags, stats, cursor, cfg, s);
+        return dispatch_kernel<BFMT, TFMT, PNDF_KERNEL_BOX>(d, cd, q, order, nq, D, flags, stats, cursor, cfg, sp, s);
+    return dispatch_kernel<BFMT, TFMT, PNDF_KERNEL_GAUSS>(d, cd, q, order, nq, D, flags, stats, cursor, cfg, sp, s);
 }
 
 }  // namespace
@@ -1293,11 +1609,19 @@ pndf_status launch_eval(const pndf_hierarchy *h, const pndf_query *q, int64_t nq
     if (nq == 0) return PNDF_OK;
     const MapDesc &d = h->d;
     const bool sort = cfg.sort != 0;
-    // scratch: cursor (8 B, padded to 256), key histogram, keys, order
+    const bool split = cfg.mode == PNDF_MODE_HIERARCHY && !(cfg.tau > 0.f) && cfg.split == 0;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint32_t cap = uint32_t(2 * 64 * (sms > 0 ? sms : 1) + 64);  // >= 2 x resident warps
+    // scratch: cursor, split counter and work sum (padded to 256), key
+    // histogram, keys, order, split markers and entries
     const size_t hist_b = sort_hist_bytes(nq);
     size_t off_hist = 256, off_keys = off_hist + hist_b;
     size_t off_order = off_keys + ((size_t(nq) * sizeof(uint32_t) + 255) & ~size_t(255));
-    size_t bytes = sort ? off_order + size_t(nq) * sizeof(uint32_t) : 256;
+    size_t bytes = sort ? off_order + ((size_t(nq) * sizeof(uint32_t) + 255) & ~size_t(255)) : 256;
+    const size_t off_marker = bytes, off_entries = off_marker + ((size_t(nq) + 255) & ~size_t(255));
+    if (split) bytes = off_entries + size_t(cap) * sizeof(SplitEntry);
     void *scratch = nullptr;
     if (cudaMallocAsync(&scratch, bytes, s) != cudaSuccess) {
         cudaGetLastError();
@@ -1305,6 +1629,14 @@ pndf_status launch_eval(const pndf_hierarchy *h, const pndf_query *q, int64_t nq
     }
     char *base = static_cast<char *>(scratch);
     auto *cursor = reinterpret_cast<unsigned long long *>(base);
+    SplitPlan sp{};
+    if (split) {
+        sp.entries = reinterpret_cast<SplitEntry *>(base + off_entries);
+        sp.marker = reinterpret_cast<uint8_t *>(base + off_marker);
+        sp.ctr = reinterpret_cast<unsigned long long *>(base + 8);
+        sp.work = reinterpret_cast<double *>(base + 16);
+        sp.cap = cap;
+    }
     uint32_t *order = nullptr;
     cudaError_t e = cudaMemsetAsync(base, 0, sort ? off_keys : 256, s);
     if (e == cudaSuccess && sort) {
@@ -1316,14 +1648,14 @@ pndf_status launch_eval(const pndf_hierarchy *h, const pndf_query *q, int64_t nq
     if (e == cudaSuccess) {
         if (d.bounds_fmt == PNDF_BOUNDS_F32)
             e = d.texel_fmt == PNDF_TEXEL_F32X2
-                    ? dispatch_stats<PNDF_BOUNDS_F32, PNDF_TEXEL_F32X2>(d, h->c, q, order, nq, D, flags, stats, cursor, cfg, s)
-                    : dispatch_stats<PNDF_BOUNDS_F32, PNDF_TEXEL_F16X2>(d, h->c, q, order, nq, D, flags, stats, cursor, cfg, s);
+                    ? dispatch_stats<PNDF_BOUNDS_F32, PNDF_TEXEL_F32X2>(d, h->c, q, order, nq, D, flags, stats, cursor, cfg, sp, s)
+                    : dispatch_stats<PNDF_BOUNDS_F32, PNDF_TEXEL_F16X2>(d, h->c, q, order, nq, D, flags, stats, cursor, cfg, sp, s);
         else
             e = d.texel_fmt == PNDF_TEXEL_F32X2
                     ? dispatch_stats<PNDF_BOUNDS_F16_OUTWARD, PNDF_TEXEL_F32X2>(d, h->c, q, order, nq, D, flags, stats, cursor,
-                                                                             cfg, s)
+                                                                             cfg, sp, s)
                     : dispatch_stats<PNDF_BOUNDS_F16_OUTWARD, PNDF_TEXEL_F16X2>(d, h->c, q, order, nq, D, flags, stats, cursor,
-                                                                             cfg, s);
+                                                                             cfg, sp, s);
     }
     if (e == cudaSuccess && cfg.ev_end) e = cudaEventRecord(static_cast<cudaEvent_t>(cfg.ev_end), s);
     cudaError_t ef = cudaFreeAsync(scratch, s);
@@ -1364,7 +1696,6 @@ pndf_status launch_sort(const pndf_hierarchy *h, const pndf_query *q, int64_t nq
 
 namespace {
 
-__constant__ ClusterDesc kNoClusters;  // never read: the serving variants without the cut
 constexpr int kServePrefixSmem = 1025;  // prefix sums of up to 1024 segments per step in shared memory
 
 // CLUSTER / KERN: the server's evaluation variant (the cut, the footprint
@@ -1630,14 +1961,14 @@ pndf_status launch_eval_noalloc(const pndf_hierarchy *h, const pndf_query *q, in
     if (e != cudaSuccess) return PNDF_ERR_CUDA;
     if (d.bounds_fmt == PNDF_BOUNDS_F32)
         e = d.texel_fmt == PNDF_TEXEL_F32X2
-                ? dispatch_stats<PNDF_BOUNDS_F32, PNDF_TEXEL_F32X2>(d, h->c, q, order, nq, D, flags, nullptr, cursor, cfg, s)
-                : dispatch_stats<PNDF_BOUNDS_F32, PNDF_TEXEL_F16X2>(d, h->c, q, order, nq, D, flags, nullptr, cursor, cfg, s);
+                ? dispatch_stats<PNDF_BOUNDS_F32, PNDF_TEXEL_F32X2>(d, h->c, q, order, nq, D, flags, nullptr, cursor, cfg, SplitPlan{}, s)
+                : dispatch_stats<PNDF_BOUNDS_F32, PNDF_TEXEL_F16X2>(d, h->c, q, order, nq, D, flags, nullptr, cursor, cfg, SplitPlan{}, s);
     else
         e = d.texel_fmt == PNDF_TEXEL_F32X2
                 ? dispatch_stats<PNDF_BOUNDS_F16_OUTWARD, PNDF_TEXEL_F32X2>(d, h->c, q, order, nq, D, flags, nullptr, cursor,
-                                                                         cfg, s)
+                                                                         cfg, SplitPlan{}, s)
                 : dispatch_stats<PNDF_BOUNDS_F16_OUTWARD, PNDF_TEXEL_F16X2>(d, h->c, q, order, nq, D, flags, nullptr, cursor,
-                                                                         cfg, s);
+                                                                         cfg, SplitPlan{}, s);
     return e == cudaSuccess ? PNDF_OK : PNDF_ERR_CUDA;
 }
 

@@ -55,7 +55,7 @@ class _BuildParams(ctypes.Structure):
 class _EvalConfig(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("sort", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("tau", ctypes.c_float), ("kernel", ctypes.c_int32),
-                ("jac_eps", ctypes.c_float), ("reserved", ctypes.c_int32),
+                ("jac_eps", ctypes.c_float), ("split", ctypes.c_int32),
                 ("ev_begin", ctypes.c_void_p), ("ev_end", ctypes.c_void_p)]
 
 
@@ -383,11 +383,13 @@ PNDF_SORT_DEFAULT = PNDF_SORT_LEVEL_TILE
 def pndf_eval_batch_ex(h: Hierarchy, queries: torch.Tensor, out=None, flags=None, stats=None, mode: int = 0,
                        sort: int = PNDF_SORT_DEFAULT, warps_per_cta: int = 0, ctas_per_sm: int = 0, stream=None,
                        ev_begin=None, ev_end=None, tau: float = 0.0, kernel: int = PNDF_KERNEL_GAUSS,
-                       jac_eps: float = 0.0) -> torch.Tensor:
+                       jac_eps: float = 0.0, split: bool = True) -> torch.Tensor:
     """ev_begin / ev_end: optional torch.cuda.Event recorded around the traversal kernel.
     tau > 0: the cluster cut of Sec. 4.2 (the hierarchy must be built with clusters=True).
     kernel: footprint kernel (PNDF_KERNEL_GAUSS, _DISK, _BOX).
-    jac_eps > 0: the Jacobian clamp of Eq. 6 (e.g. 1e-6)."""
+    jac_eps > 0: the Jacobian clamp of Eq. 6 (e.g. 1e-6).
+    split=False: one warp per query (large footprints are not divided among
+    warps; the results are the same bits)."""
     nq = _queries(queries)
     _same_device(h, queries)
     if out is None:
@@ -398,7 +400,7 @@ def pndf_eval_batch_ex(h: Hierarchy, queries: torch.Tensor, out=None, flags=None
     if stats is not None:
         _need(stats, "stats", dtype=torch.int32, shape_last=STATS_FIELDS, rows=nq, on=queries.device)
     cfg = _EvalConfig(int(mode), int(sort), int(warps_per_cta), int(ctas_per_sm), float(tau), int(kernel),
-                      float(jac_eps), 0,
+                      float(jac_eps), 0 if split else -1,
                       _event_handle(ev_begin), _event_handle(ev_end))
     with torch.cuda.device(queries.device):
         _check("pndf_eval_batch_ex", LIB.pndf_eval_batch_ex(h.handle, _ptr(queries), nq, _ptr(out), _ptr(flags),

@@ -369,7 +369,8 @@ def test_status_word_per_hierarchy(P):
 
 def test_result_independent_of_batch(P):
     """A query's D is bit-identical alone, in a batch, sorted or unsorted and
-    with another launch shape: one warp owns a query and its reduction order."""
+    with another launch shape: its sum is exact (fixed point), so neither the
+    order of its hits nor the warps that find them change it."""
     st = synth.scratch_map(n=256, n_grooves=40, seed=12)
     q = synth.make_queries(st, 2048, synth.QueryMix(sigma=(1.0, 24.0), aspect=(1.0, 4.0), frac_near=0.8), 12)
     D_all, _, _ = run(P, st, q, stats=False)
@@ -379,6 +380,52 @@ def test_result_independent_of_batch(P):
     D_sub, _, _ = run(P, st, q[100:117], stats=False)
     assert np.array_equal(D_all, D_uns) and np.array_equal(D_all, D_w4) and np.array_equal(D_all, D_tile)
     assert np.array_equal(D_all[100:117], D_sub)
+
+
+def test_split_large_footprints_same_bits(P):
+    """In a small batch, footprints far larger than the batch's average share
+    per warp are divided into tiles of pyramid nodes, each descended by its own
+    warp.  The result is the same bits as one warp per query (split=False),
+    with the same hits, and the oracle agrees; the node counts differ (a tile
+    starts its descent below the entry level), which shows the division."""
+    st = synth.flake_normals(2048, 12000, seed=21)
+    q = synth.make_queries(st, 48, synth.QueryMix(sigma=(60.0, 250.0), frac_near=0.9), 21)
+    h = P.pndf_build_hierarchy(st.to(DEV))
+    qd = q.to(DEV)
+    out = {}
+    for split in (True, False):
+        fl = torch.zeros(q.shape[0], dtype=torch.int32, device=DEV)
+        stt = torch.zeros(q.shape[0], P.STATS_FIELDS, dtype=torch.int32, device=DEV)
+        D = P.pndf_eval_batch_ex(h, qd, flags=fl, stats=stt, split=split)
+        D2 = P.pndf_eval_batch_ex(h, qd, split=split, sort=0)
+        out[split] = (D.cpu(), fl.cpu(), stt.cpu(), D2.cpu())
+    Dn = P.pndf_eval_batch_noalloc(h, qd).cpu()  # whole queries only
+    torch.cuda.synchronize()
+    h.free()
+    (Ds, fs, ss, Ds2), (Dw, fw, sw, Dw2) = out[True], out[False]
+    assert torch.equal(Ds, Dw) and torch.equal(Ds, Ds2) and torch.equal(Ds, Dw2) and torch.equal(Ds, Dn)
+    assert torch.equal(fs, fw)
+    cols = [P.STATS_NAMES.index(c) for c in ("leaf_blocks", "tri_tests", "hits", "hit_hash", "quads")]
+    assert torch.equal(ss[:, cols], sw[:, cols])
+    nodes = P.STATS_NAMES.index("nodes")
+    assert (ss[:, nodes] != sw[:, nodes]).sum() >= 10
+    ref = oracle.pndf(st, q)
+    s = check_pndf(Ds.double().numpy(), ref, hits_gpu=ss[:, 3].numpy(), hash_gpu=ss[:, 4].numpy(),
+                   label="split flake2048")
+    assert s["nonzero"] > 20
+
+
+def test_flat_and_hierarchy_same_bits(P):
+    """The exact per-query sum makes the flat scan (every leaf block of the
+    support, no pruning) and the hierarchy agree to the bit wherever they find
+    the same hits (hit count and fingerprint)."""
+    st = synth.scratch_map(n=256, n_grooves=40, seed=12)
+    q = synth.make_queries(st, 2048, synth.QueryMix(sigma=(1.0, 24.0), aspect=(1.0, 4.0), frac_near=0.8), 13)
+    Dh, _, sh = run(P, st, q)
+    Df, _, sf = run(P, st, q, mode=P.PNDF_MODE_FLAT)
+    same = (sh[:, 3] == sf[:, 3]) & (sh[:, 4] == sf[:, 4])
+    assert same.mean() > 0.99 and (Dh[same] > 0).sum() > 500
+    assert np.array_equal(Dh[same], Df[same])
 
 
 def test_host_buffer_entry_point(P):
