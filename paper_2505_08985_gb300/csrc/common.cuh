@@ -228,10 +228,15 @@ struct ServeVariant {
 // per CTA; called once before the step graphs are captured.
 cudaError_t prepare_serve(int texel_fmt, int bounds_fmt, const ServeVariant &v, int warps);
 // One serving step over a device segment table (see serve.cu); clusters:
-// per-map cluster descriptors, read only when v.tau > 0.
+// per-map cluster descriptors, read only when v.tau > 0.  split: device
+// scratch of serve_split_bytes(split_cap) bytes for dividing the step's large
+// footprints among warps (null: one warp per query).
 cudaError_t launch_serve(int texel_fmt, int bounds_fmt, const ServeVariant &v, const MapDesc *maps,
                          const ClusterDesc *clusters, int nmaps, const uint32_t *table, const pndf_segment *segs,
-                         unsigned long long *cursor, int warps, int ctas_per_sm, cudaStream_t s);
+                         unsigned long long *cursor, int warps, int ctas_per_sm, void *split, uint32_t split_cap,
+                         cudaStream_t s);
+uint32_t serve_split_cap();
+size_t serve_split_bytes(uint32_t cap);
 // Allocation-free evaluation with the sort scratch in a fixed device array.
 pndf_status launch_eval_noalloc(const pndf_hierarchy *h, const pndf_query *q, int64_t nq, float *D, uint32_t *flags,
                                 cudaStream_t s);

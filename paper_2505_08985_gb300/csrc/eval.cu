@@ -320,12 +320,21 @@ constexpr uint32_t kMortonMask = (1u << 27) - 1u;
 // the total is rounded to FP32 once at the end.  A contribution of 2^63 or
 // more, or a sum past 2^64 (only possible for normal triangles of area far
 // below 1e-20), marks the query kHuge and its D is +inf.
+// The sum lives in shared memory (one 128-bit slot per thread of the CTA,
+// at most 256 threads), so the descent keeps its registers; the counters and
+// flags stay in registers.
 struct Acc {
-    unsigned long long lo, hi;
     uint32_t hits, hash, tests, fp64, degen, leaves, nodes, quads, cchecks, clusters;
     uint32_t flags;
 };
 constexpr uint32_t kHuge = 1u << 30;  // internal flag bit: the sum is out of the fixed-point range
+__shared__ unsigned long long s_sum_lo[256], s_sum_hi[256];
+
+__device__ __forceinline__ void acc_zero()
+{
+    s_sum_lo[threadIdx.x] = 0ull;
+    s_sum_hi[threadIdx.x] = 0ull;
+}
 
 __device__ __forceinline__ void acc_add(Acc &a, float w)
 {
@@ -349,11 +358,12 @@ __device__ __forceinline__ void acc_add(Acc &a, float w)
         dl = 0ull;
         dh = m << (sh - 64);  // sh <= 189 - 86: dh < 2^63
     }
-    a.lo += dl;
-    const unsigned long long carry = a.lo < dl ? 1ull : 0ull;
-    const unsigned long long h0 = a.hi;
-    a.hi += dh + carry;
-    if (a.hi < h0) a.flags |= kHuge;  // past 2^64
+    const unsigned long long lo = s_sum_lo[threadIdx.x] + dl;
+    s_sum_lo[threadIdx.x] = lo;
+    const unsigned long long h0 = s_sum_hi[threadIdx.x];
+    const unsigned long long hi = h0 + dh + (lo < dl ? 1ull : 0ull);
+    s_sum_hi[threadIdx.x] = hi;
+    if (hi < h0) a.flags |= kHuge;  // past 2^64
 }
 
 // 128-bit fixed point -> FP32 (through FP64: deterministic, within an ulp).
@@ -1035,8 +1045,8 @@ __device__ __forceinline__ void eval_range(const MapDesc &d, const ClusterDesc &
 template <bool STATS>
 __device__ __forceinline__ void warp_total(Acc &acc, unsigned long long &lo, unsigned long long &hi, uint32_t &fl)
 {
-    lo = acc.lo;
-    hi = acc.hi;
+    lo = s_sum_lo[threadIdx.x];
+    hi = s_sum_hi[threadIdx.x];
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         const unsigned long long lo_o = __shfl_xor_sync(kFull, lo, off);
@@ -1072,6 +1082,7 @@ __device__ void eval_one(const MapDesc &d, const ClusterDesc &cd, float tau, flo
     constexpr bool CLAMP = KERN == kKernGaussClamp;
     Query q = make_query(rec, KERN, jac_eps);
     Acc acc = {};
+    acc_zero();
     if (!q.valid) {
         if (lane == 0) {
             D_out = __int_as_float(0x7fc00000);
@@ -1151,6 +1162,7 @@ struct SplitPlan {
     uint8_t *marker;           // per query (caller index): 1 = divided into tiles
     unsigned long long *ctr;   // (entries << 40) | tiles reserved
     double *work;              // the batch's summed estimate
+    float *wt;                 // the target w_t (served steps: written by the plan for the step kernel)
     uint32_t cap;              // entries capacity
     int resident_warps;
 };
@@ -1187,44 +1199,61 @@ __device__ __forceinline__ uint32_t split_tiles(const Query &q, int L, int l, in
     return uint32_t((a1 - a0) / 4 + 1) * uint32_t((c1 - c0) / 4 + 1);
 }
 
+__device__ __forceinline__ float split_target(const SplitPlan &p)
+{
+    return fmaxf(float(*p.work / (double(kSplitPerWarp) * p.resident_warps)), kSplitMinWork);
+}
+
+// Whether query q is divided at target wt, and into which tiles: the deepest
+// level (>= kSplitMinLevel) whose tile count stays <= kSplitMaxTiles, or the
+// first going down whose count reaches estimate / wt; at least two tiles.
+__device__ __forceinline__ bool split_choice(const Query &q, int L, float wt, int &level, uint32_t &tiles)
+{
+    const float w = split_estimate(q);
+    if (!q.valid || !(w > 2.f * wt)) return false;
+    const float target = w / wt;
+    int best = -1, a0, a1, c0, c1;
+    uint32_t bt = 0;
+    for (int l = entry_level(q, L) - 1; l >= kSplitMinLevel; --l) {
+        const uint32_t t = split_tiles(q, L, l, a0, a1, c0, c1);
+        if (t > kSplitMaxTiles) break;
+        best = l;
+        bt = t;
+        if (float(t) >= target) break;
+    }
+    level = best;
+    tiles = bt;
+    return best >= 0 && bt >= 2;
+}
+
+// Reserve an entry and its tiles; false if the entries are full (never
+// expected: the division bounds them by 2 x the resident warps).
+__device__ __forceinline__ bool split_reserve(const SplitPlan &p, uint32_t qi, int seg, int level, uint32_t tiles)
+{
+    const unsigned long long old = atomicAdd(p.ctr, (1ull << 40) | tiles);
+    const unsigned long long idx = old >> 40;
+    if (idx >= p.cap) return false;
+    SplitEntry &E = p.entries[idx];
+    E.qi = qi;
+    E.tiles = tiles;
+    E.base = old & ((1ull << 40) - 1ull);
+    E.level = level;
+    E.pad = seg;
+    E.lo = E.hi = 0ull;
+    E.done = E.flags = 0u;
+    E.st = pndf_query_stats{0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    return true;
+}
+
 template <int KERN>
 __global__ void split_plan(MapDesc d, const pndf_query *__restrict__ qs, int64_t nq, float jac_eps, SplitPlan p)
 {
-    const double W = *p.work;
-    const float wt = fmaxf(float(W / (double(kSplitPerWarp) * p.resident_warps)), kSplitMinWork);
+    const float wt = split_target(p);
     for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < nq; k += int64_t(gridDim.x) * blockDim.x) {
         const Query q = make_query(qs[k], KERN, jac_eps);
-        const float w = split_estimate(q);
-        uint8_t mark = 0;
-        if (q.valid && w > 2.f * wt) {
-            const float target = w / wt;
-            int best = -1, a0, a1, c0, c1;
-            uint32_t bt = 0;
-            for (int l = entry_level(q, d.L) - 1; l >= kSplitMinLevel; --l) {
-                const uint32_t t = split_tiles(q, d.L, l, a0, a1, c0, c1);
-                if (t > kSplitMaxTiles) break;
-                best = l;
-                bt = t;
-                if (float(t) >= target) break;
-            }
-            if (best >= 0 && bt >= 2) {
-                const unsigned long long old = atomicAdd(p.ctr, (1ull << 40) | bt);
-                const unsigned long long idx = old >> 40;
-                if (idx < p.cap) {
-                    SplitEntry &E = p.entries[idx];
-                    E.qi = uint32_t(k);
-                    E.tiles = bt;
-                    E.base = old & ((1ull << 40) - 1ull);
-                    E.level = best;
-                    E.pad = 0;
-                    E.lo = E.hi = 0ull;
-                    E.done = E.flags = 0u;
-                    E.st = pndf_query_stats{0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-                    mark = 1;
-                }
-            }
-        }
-        p.marker[k] = mark;
+        int level;
+        uint32_t tiles;
+        p.marker[k] = split_choice(q, d.L, wt, level, tiles) && split_reserve(p, uint32_t(k), 0, level, tiles);
     }
 }
 
@@ -1308,6 +1337,7 @@ __global__ void __launch_bounds__(256, PNDF_TRAVERSE_MIN_CTAS)
     // the divided queries' tiles take the first s_ntiles work indices
     __shared__ unsigned long long s_ntiles;
     __shared__ int s_entries;
+    __shared__ uint32_t s_dest[8][2];  // per warp: query, entry (-1: whole query)
     if (threadIdx.x == 0) {
         int n = 0;
         unsigned long long t = 0ull;
@@ -1369,12 +1399,20 @@ __global__ void __launch_bounds__(256, PNDF_TRAVERSE_MIN_CTAS)
             node_range(q.x, q.rx, sz, 1 << (d.L - e), a0, a1);
             node_range(q.y, q.ry, sz, 1 << (d.L - e), c0, c1);
         }
+        // where the result goes waits in shared memory during the descent
+        if (lane == 0) {
+            s_dest[warp][0] = qi;
+            s_dest[warp][1] = uint32_t(ei);
+        }
         Acc acc = {};
+        acc_zero();
         eval_range<BFMT, TFMT, STATS, false, CLAMP>(d, cd, q, e, a0, a1, c0, c1, lane, stk, lq, ring, hits, acc);
         unsigned long long lo, hi;
         uint32_t fl;
         warp_total<STATS>(acc, lo, hi, fl);
         if (lane == 0) {
+            qi = s_dest[warp][0];
+            ei = int(s_dest[warp][1]);
             if (ei >= 0) {
                 tile_finish<STATS>(d, sp.entries[ei], acc, lo, hi, fl, D, flags, stats);
             } else {
@@ -1533,7 +1571,10 @@ cudaError_t launch_traverse(const MapDesc &d, const ClusterDesc &cd, float tau, 
     int dev = 0, sms = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+    // with its static arrays the kernel passes the 48 KB a launch gets by default
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) occ = 1;
     if (ctas_per_sm > 0 && ctas_per_sm < occ) occ = ctas_per_sm;
@@ -1700,15 +1741,81 @@ constexpr int kServePrefixSmem = 1025;  // prefix sums of up to 1024 segments pe
 
 // CLUSTER / KERN: the server's evaluation variant (the cut, the footprint
 // kernel or the clamp), compiled in as for traverse_kernel.
+// Segment of work index k: the last segment i with prefix[i] <= k.
+__device__ __forceinline__ int serve_segment(const uint32_t *prefix, int nsegs, uint32_t k)
+{
+    int lo = 0, hi = nsegs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= k)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// The step's division of large footprints, as for pndf_eval_batch: the work
+// estimate summed over the step's queries, then the plan (which also stores
+// the target w_t for the step kernel, which recomputes each query's choice).
+template <int KERN>
+__global__ void serve_split_work(const uint32_t *__restrict__ table, const pndf_segment *__restrict__ segs,
+                                 float jac_eps, double *__restrict__ work)
+{
+    __shared__ double red[256];
+    const int nsegs = int(table[0]);
+    const uint32_t *prefix = table + 1;
+    const uint32_t total = prefix[nsegs];
+    double acc = 0.0;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
+        const pndf_segment &sg = segs[serve_segment(prefix, nsegs, k)];
+        const int64_t j = int64_t(sg.first) + int64_t(k - prefix[&sg - segs]);
+        acc += double(split_estimate(make_query(sg.q[sg.order ? int64_t(sg.order[j]) : j], KERN, jac_eps)));
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (int(threadIdx.x) < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(work, red[0]);
+}
+
+template <int KERN>
+__global__ void serve_split_plan(const MapDesc *__restrict__ maps, const uint32_t *__restrict__ table,
+                                 const pndf_segment *__restrict__ segs, float jac_eps, SplitPlan p)
+{
+    const float wt = split_target(p);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *p.wt = wt;
+    const int nsegs = int(table[0]);
+    const uint32_t *prefix = table + 1;
+    const uint32_t total = prefix[nsegs];
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
+        const int i = serve_segment(prefix, nsegs, k);
+        const pndf_segment &sg = segs[i];
+        const int64_t j = int64_t(sg.first) + int64_t(k - prefix[i]);
+        const uint32_t qi = sg.order ? sg.order[j] : uint32_t(j);
+        const Query q = make_query(sg.q[qi], KERN, jac_eps);
+        int level;
+        uint32_t tiles;
+        if (split_choice(q, maps[sg.map].L, wt, level, tiles) && !split_reserve(p, qi, i, level, tiles))
+            record_status(maps[sg.map].status, &g_status_eval, PNDF_QF_OVERFLOW);
+    }
+}
+
 template <int BFMT, int TFMT, bool CLUSTER, int KERN>
 __global__ void __launch_bounds__(256, PNDF_TRAVERSE_MIN_CTAS)
     serve_kernel(const MapDesc *__restrict__ maps, const ClusterDesc *__restrict__ clusters, int nmaps,
                  const uint32_t *__restrict__ table, const pndf_segment *__restrict__ segs,
-                 unsigned long long *__restrict__ cursor, float tau, float jac_eps)
+                 unsigned long long *__restrict__ cursor, float tau, float jac_eps, SplitPlan sp)
 {
     extern __shared__ uint32_t smem[];
     __shared__ MapDesc smaps[kServeMaxMaps];
     __shared__ uint32_t sprefix[kServePrefixSmem];
+    __shared__ unsigned long long s_ntiles;
+    __shared__ int s_entries;
+    __shared__ float s_wt;
+    __shared__ uint32_t s_dest[8][3];  // per warp: segment, query, entry (-1: whole query)
     const int nsegs = int(table[0]);
     // the segment prefix sums, searched once per query, in shared memory when they fit
     const bool prefix_in_smem = nsegs < kServePrefixSmem;
@@ -1719,6 +1826,20 @@ __global__ void __launch_bounds__(256, PNDF_TRAVERSE_MIN_CTAS)
         for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
         if (prefix_in_smem)
             for (int i = threadIdx.x; i <= nsegs; i += blockDim.x) sprefix[i] = table[1 + i];
+        if (threadIdx.x == 0) {
+            // the divided queries' tiles take the first s_ntiles work indices
+            int n = 0;
+            unsigned long long t = 0ull;
+            float wt = __int_as_float(0x7f800000);
+            if (!CLUSTER && sp.entries) {
+                n = int(min(__ldcg(sp.ctr) >> 40, (unsigned long long)sp.cap));
+                if (n > 0) t = __ldcg(&sp.entries[n - 1].base) + __ldcg(&sp.entries[n - 1].tiles);
+                wt = __ldcg(sp.wt);
+            }
+            s_entries = n;
+            s_ntiles = t;
+            s_wt = wt;
+        }
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1732,27 +1853,89 @@ __global__ void __launch_bounds__(256, PNDF_TRAVERSE_MIN_CTAS)
         unsigned long long k = 0;
         if (lane == 0) k = atomicAdd(cursor, 1ull);
         k = __shfl_sync(kFull, k, 0);
-        if (k >= total) break;
-        int lo = 0, hi = nsegs - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (prefix[mid] <= uint32_t(k))
-                lo = mid;
-            else
-                hi = mid - 1;
+        if (CLUSTER) {
+            if (k >= total) break;
+            const int i = serve_segment(prefix, nsegs, uint32_t(k));
+            const pndf_segment sg = segs[i];
+            const int64_t j = int64_t(sg.first) + int64_t(uint32_t(k) - prefix[i]);
+            const int64_t qi = sg.order ? int64_t(sg.order[j]) : j;
+            float Dv;
+            uint32_t fv;
+            eval_one<BFMT, TFMT, false, false, CLUSTER, KERN>(smaps[sg.map], clusters[sg.map], tau, jac_eps, sg.q[qi],
+                                                               lane, stk, lq, ring, hits, Dv, fv, nullptr);
+            if (lane == 0) {
+                sg.D[qi] = Dv;
+                if (sg.flags) sg.flags[qi] = fv;
+            }
+            continue;
         }
-        const pndf_segment sg = segs[lo];
-        const int64_t j = int64_t(sg.first) + int64_t(uint32_t(k) - prefix[lo]);
-        const int64_t qi = sg.order ? int64_t(sg.order[j]) : j;
-        const pndf_query rec = sg.q[qi];
-        float Dv;
-        uint32_t fv;
-        eval_one<BFMT, TFMT, false, false, CLUSTER, KERN>(smaps[sg.map], CLUSTER ? clusters[sg.map] : kNoClusters,
-                                                           tau, jac_eps, rec, lane, stk, lq, ring, hits, Dv, fv,
-                                                           nullptr);
+        // a tile of a divided query, or a whole query: one descent either way
+        constexpr bool CLAMP = KERN == kKernGaussClamp;
+        int ei = -1;
+        int i;
+        uint32_t qi;
+        Query q;
+        int e, a0, a1, c0, c1;
+        if (k < s_ntiles) {
+            ei = tile_entry(sp, s_entries, k);
+            const SplitEntry &E = sp.entries[ei];
+            i = __ldg(&E.pad);
+            qi = __ldg(&E.qi);
+            q = make_query(segs[i].q[qi], KERN, jac_eps);
+            e = __ldg(&E.level);
+            tile_range(q, smaps[segs[i].map].L, e, uint32_t(k - __ldg(&E.base)), a0, a1, c0, c1);
+        } else {
+            k -= s_ntiles;
+            if (k >= total) break;
+            i = serve_segment(prefix, nsegs, uint32_t(k));
+            const int64_t j = int64_t(segs[i].first) + int64_t(uint32_t(k) - prefix[i]);
+            qi = segs[i].order ? segs[i].order[j] : uint32_t(j);
+            q = make_query(segs[i].q[qi], KERN, jac_eps);
+            const int L = smaps[segs[i].map].L;
+            if (!q.valid) {
+                if (lane == 0) {
+                    segs[i].D[qi] = __int_as_float(0x7fc00000);
+                    if (segs[i].flags) segs[i].flags[qi] = PNDF_QF_INVALID;
+                    record_status(smaps[segs[i].map].status, &g_status_eval, PNDF_QF_INVALID);
+                }
+                continue;
+            }
+            {
+                int l;
+                uint32_t t;
+                if (split_choice(q, L, s_wt, l, t)) continue;  // evaluated as tiles
+            }
+            e = entry_level(q, L);
+            const float sz = float(1u << e);
+            node_range(q.x, q.rx, sz, 1 << (L - e), a0, a1);
+            node_range(q.y, q.ry, sz, 1 << (L - e), c0, c1);
+        }
+        // where the result goes waits in shared memory during the descent
         if (lane == 0) {
-            sg.D[qi] = Dv;
-            if (sg.flags) sg.flags[qi] = fv;
+            s_dest[warp][0] = uint32_t(i);
+            s_dest[warp][1] = qi;
+            s_dest[warp][2] = uint32_t(ei);
+        }
+        const int map = segs[i].map;
+        Acc acc = {};
+        acc_zero();
+        eval_range<BFMT, TFMT, false, false, CLAMP>(smaps[map], kNoClusters, q, e, a0, a1, c0, c1, lane, stk, lq, ring,
+                                                    hits, acc);
+        unsigned long long lo, hi;
+        uint32_t fl;
+        warp_total<false>(acc, lo, hi, fl);
+        if (lane == 0) {
+            const pndf_segment &sg = segs[s_dest[warp][0]];
+            const uint32_t qo = s_dest[warp][1];
+            const int eo = int(s_dest[warp][2]);
+            const MapDesc &md = smaps[sg.map];
+            if (eo >= 0) {
+                tile_finish<false>(md, sp.entries[eo], acc, lo, hi, fl, sg.D, sg.flags, nullptr);
+            } else {
+                sg.D[qo] = acc_value(lo, hi, fl);
+                if (sg.flags) sg.flags[qo] = fl & ~kHuge;
+                if (fl & PNDF_QF_OVERFLOW) record_status(md.status, &g_status_eval, PNDF_QF_OVERFLOW);
+            }
         }
     }
 }
@@ -1760,7 +1943,7 @@ __global__ void __launch_bounds__(256, PNDF_TRAVERSE_MIN_CTAS)
 template <int BFMT, int TFMT, bool CLUSTER, int KERN>
 cudaError_t launch_serve_t(const ServeVariant &v, const MapDesc *maps, const ClusterDesc *clusters, int nmaps,
                            const uint32_t *table, const pndf_segment *segs, unsigned long long *cursor, int warps,
-                           int ctas_per_sm, cudaStream_t s)
+                           int ctas_per_sm, void *split, uint32_t split_cap, cudaStream_t s)
 {
     auto kern = serve_kernel<BFMT, TFMT, CLUSTER, KERN>;
     int threads = warps * 32;
@@ -1772,7 +1955,21 @@ cudaError_t launch_serve_t(const ServeVariant &v, const MapDesc *maps, const Clu
     if (e != cudaSuccess) return e;
     if (occ < 1) occ = 1;
     if (ctas_per_sm > 0 && ctas_per_sm < occ) occ = ctas_per_sm;
-    kern<<<unsigned(sms * occ), threads, smem, s>>>(maps, clusters, nmaps, table, segs, cursor, v.tau, v.jac_eps);
+    SplitPlan sp{};
+    if (!CLUSTER && split) {
+        char *b = static_cast<char *>(split);
+        sp.ctr = reinterpret_cast<unsigned long long *>(b);
+        sp.work = reinterpret_cast<double *>(b + 8);
+        sp.wt = reinterpret_cast<float *>(b + 16);
+        sp.entries = reinterpret_cast<SplitEntry *>(b + 256);
+        sp.cap = split_cap;
+        sp.resident_warps = sms * occ * warps;
+        e = cudaMemsetAsync(split, 0, 256, s);
+        if (e != cudaSuccess) return e;
+        serve_split_work<KERN><<<unsigned(sms * 4), 256, 0, s>>>(table, segs, v.jac_eps, sp.work);
+        serve_split_plan<KERN><<<unsigned(sms * 4), 256, 0, s>>>(maps, table, segs, v.jac_eps, sp);
+    }
+    kern<<<unsigned(sms * occ), threads, smem, s>>>(maps, clusters, nmaps, table, segs, cursor, v.tau, v.jac_eps, sp);
     return cudaGetLastError();
 }
 
@@ -1800,9 +1997,11 @@ cudaError_t serve_smem_v(const ServeVariant &v, int warps)
 template <int BFMT, int TFMT>
 cudaError_t launch_serve_v(const ServeVariant &v, const MapDesc *maps, const ClusterDesc *clusters, int nmaps,
                            const uint32_t *table, const pndf_segment *segs, unsigned long long *cursor, int warps,
-                           int ctas_per_sm, cudaStream_t s)
+                           int ctas_per_sm, void *split, uint32_t split_cap, cudaStream_t s)
 {
-#define PNDF_SERVE(C, K) launch_serve_t<BFMT, TFMT, C, K>(v, maps, clusters, nmaps, table, segs, cursor, warps, ctas_per_sm, s)
+#define PNDF_SERVE(C, K)                                                                                     \
+    launch_serve_t<BFMT, TFMT, C, K>(v, maps, clusters, nmaps, table, segs, cursor, warps, ctas_per_sm, split, \
+                                     split_cap, s)
     if (v.tau > 0.f) return PNDF_SERVE(true, PNDF_KERNEL_GAUSS);
     if (v.jac_eps > 0.f) return PNDF_SERVE(false, kKernGaussClamp);
     if (v.kernel == PNDF_KERNEL_DISK) return PNDF_SERVE(false, PNDF_KERNEL_DISK);
@@ -1822,21 +2021,31 @@ cudaError_t prepare_serve(int texel_fmt, int bounds_fmt, const ServeVariant &v, 
                                          : serve_smem_v<PNDF_BOUNDS_F16_OUTWARD, PNDF_TEXEL_F16X2>(v, warps);
 }
 
+// Scratch of a step's division of large footprints: a 256-byte header
+// (counter, work sum, target) and the entries.
+uint32_t serve_split_cap()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return uint32_t(2 * 64 * (sms > 0 ? sms : 1) + 64);  // >= 2 x the resident warps
+}
+
+size_t serve_split_bytes(uint32_t cap) { return 256 + size_t(cap) * sizeof(SplitEntry); }
+
 cudaError_t launch_serve(int texel_fmt, int bounds_fmt, const ServeVariant &v, const MapDesc *maps,
                          const ClusterDesc *clusters, int nmaps, const uint32_t *table, const pndf_segment *segs,
-                         unsigned long long *cursor, int warps, int ctas_per_sm, cudaStream_t s)
+                         unsigned long long *cursor, int warps, int ctas_per_sm, void *split, uint32_t split_cap,
+                         cudaStream_t s)
 {
+#define PNDF_SERVE_V(B, T) \
+    launch_serve_v<B, T>(v, maps, clusters, nmaps, table, segs, cursor, warps, ctas_per_sm, split, split_cap, s)
     if (bounds_fmt == PNDF_BOUNDS_F32)
-        return texel_fmt == PNDF_TEXEL_F32X2
-                   ? launch_serve_v<PNDF_BOUNDS_F32, PNDF_TEXEL_F32X2>(v, maps, clusters, nmaps, table, segs, cursor,
-                                                                      warps, ctas_per_sm, s)
-                   : launch_serve_v<PNDF_BOUNDS_F32, PNDF_TEXEL_F16X2>(v, maps, clusters, nmaps, table, segs, cursor,
-                                                                      warps, ctas_per_sm, s);
-    return texel_fmt == PNDF_TEXEL_F32X2
-               ? launch_serve_v<PNDF_BOUNDS_F16_OUTWARD, PNDF_TEXEL_F32X2>(v, maps, clusters, nmaps, table, segs,
-                                                                          cursor, warps, ctas_per_sm, s)
-               : launch_serve_v<PNDF_BOUNDS_F16_OUTWARD, PNDF_TEXEL_F16X2>(v, maps, clusters, nmaps, table, segs,
-                                                                          cursor, warps, ctas_per_sm, s);
+        return texel_fmt == PNDF_TEXEL_F32X2 ? PNDF_SERVE_V(PNDF_BOUNDS_F32, PNDF_TEXEL_F32X2)
+                                             : PNDF_SERVE_V(PNDF_BOUNDS_F32, PNDF_TEXEL_F16X2);
+    return texel_fmt == PNDF_TEXEL_F32X2 ? PNDF_SERVE_V(PNDF_BOUNDS_F16_OUTWARD, PNDF_TEXEL_F32X2)
+                                         : PNDF_SERVE_V(PNDF_BOUNDS_F16_OUTWARD, PNDF_TEXEL_F16X2);
+#undef PNDF_SERVE_V
 }
 
 // ---------------------------------------------------------------------------

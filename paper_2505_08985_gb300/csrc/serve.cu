@@ -48,6 +48,7 @@ struct pndf_server {
     int max_segs = 0, warps = 8, ctas = 0;
     int kernel = PNDF_KERNEL_GAUSS;
     float tau = 0.f, jac_eps = 0.f;
+    uint32_t split_cap = 0;  // entries of a step's division of large footprints (0: cluster cut, none)
     MapDesc *maps_dev = nullptr;
     ClusterDesc *clusters_dev = nullptr;  // per map, read only with tau > 0
     cudaStream_t cap = nullptr;
@@ -78,11 +79,12 @@ void release(pndf_server *s)
     delete s;
 }
 
-// Device bytes of a slot: the table, the P-NDF work cursor, and for the
-// projected-area part the band offsets, band partial sums and their cursor.
+// Device bytes of a slot: the table, the P-NDF work cursor, the division of
+// large footprints, and for the projected-area part the band offsets, band
+// partial sums and their cursor.
 size_t slot_device_bytes(const pndf_server *s)
 {
-    size_t b = up256(table_bytes(s->max_segs, s->area_cap)) + 256;
+    size_t b = up256(table_bytes(s->max_segs, s->area_cap)) + 256 + up256(serve_split_bytes(s->split_cap));
     if (s->area_cap > 0)
         b += up256((size_t(s->area_cap) + 1) * sizeof(uint32_t)) +
              up256(size_t(s->area_cap) * s->area_bands * sizeof(float2)) + 256;
@@ -101,11 +103,12 @@ cudaError_t capture_slot(pndf_server *s, Slot &sl)
     cudaMemcpyAsync(sl.dev, sl.host, tb, cudaMemcpyHostToDevice, s->cap);
     cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), s->cap);
     const ServeVariant v{s->kernel, s->tau, s->jac_eps};
+    char *split = dev + up256(tb) + 256;
     launch_serve(s->texel_fmt, s->bounds_fmt, v, s->maps_dev, s->clusters_dev, s->nmaps, table, segs, cursor,
-                 s->warps, s->ctas, s->cap);
+                 s->warps, s->ctas, s->split_cap > 0 ? split : nullptr, s->split_cap, s->cap);
     if (s->area_cap > 0) {
         char *at = dev + pndf_table_bytes(s->max_segs);
-        char *scratch = dev + up256(tb) + 256;
+        char *scratch = split + up256(serve_split_bytes(s->split_cap));
         auto *off = reinterpret_cast<uint32_t *>(scratch);
         scratch += up256((size_t(s->area_cap) + 1) * sizeof(uint32_t));
         auto *part = reinterpret_cast<float2 *>(scratch);
@@ -179,6 +182,7 @@ pndf_status pndf_server_create(const pndf_hierarchy *const *maps, int32_t nmaps,
     s->tau = c.tau;
     s->jac_eps = c.jac_eps;
     s->area_cap = c.max_area_requests;
+    s->split_cap = c.tau > 0.f ? 0u : serve_split_cap();
     for (int i = 0; i < nmaps; ++i) s->area_bands = max(s->area_bands, area_max_bands(maps[i]->d.n));
     MapDesc host_maps[kServeMaxMaps];
     ClusterDesc host_clusters[kServeMaxMaps];

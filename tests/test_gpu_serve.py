@@ -2,7 +2,8 @@
 
 Each request's densities must be the same alone (pndf_eval_batch on its map)
 and in the mix (sliced across steps, sharing steps with other requests and
-maps): one warp evaluates a query with a fixed order, so equality is bitwise.
+maps): a query's sum is exact whichever warps evaluate it, so equality is
+bitwise.
 """
 
 import numpy as np
@@ -228,4 +229,27 @@ def test_mixed_steps_with_projected_area_equal_alone(P):
         want = ref_P[lo:lo + 20] if r.kind == A else ref_D[lo:lo + 500]
         assert torch.equal(r.D, want), r.rid
     b.close()
+    h.free()
+
+
+def test_served_large_footprints_divided_same_bits(P):
+    """Steps holding a few footprints much larger than the step's average
+    share per warp divide them into tiles evaluated by several warps (as
+    pndf_eval_batch does); each result equals one warp per query to the bit."""
+    from paper_2505_08985_gb300 import serve
+    st = synth.flake_normals(2048, 12000, seed=31, device=DEV)
+    h = P.pndf_build_hierarchy(st, bounds_fmt=P.PNDF_BOUNDS_F16_OUTWARD)
+    reqs = []
+    for k in range(12):
+        sig = (60.0, 250.0) if k % 3 == 0 else (1.0, 8.0)
+        q = synth.make_queries(st, 40 if k % 3 == 0 else 400, synth.QueryMix(sigma=sig, frac_near=0.9), 300 + k)
+        reqs.append(serve.Request(rid=k, map=0, queries=q.to(DEV), arrival=0.0))
+    whole = [P.pndf_eval_batch_ex(h, r.queries, split=False).cpu() for r in reqs]
+    b = serve.ContinuousBatcher([h], step_queries=1000, max_segments=16)
+    b.run(reqs, realtime=False)
+    assert b.steps >= 3
+    for r, a in zip(reqs, whole):
+        assert torch.equal(r.D.cpu(), a), r.rid
+    b.close()
+    assert P.pndf_last_device_status(h) == 0
     h.free()
