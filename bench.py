@@ -635,6 +635,7 @@ def run_mixed(args, dev):
     rel = ((Pg - P.double()).abs() / P.double().clamp_min(1e-12)).cpu()
     covered = torch.isfinite(rel)  # footprints whose mip nodes all reach past the map border have no fit
     graz = (w[:, 2] < 0.2).cpu()
+    ggx_acc = ggx_breakdown(h, g, st, qa, dev, with_nodes=not args.no_accuracy)
     g.free()
     stream_out = run_mixed_stream(args, st, h) if args.mixed_stream_batches > 0 else None
     h.free()
@@ -655,11 +656,91 @@ def run_mixed(args, dev):
                         "footprints_covered": float(covered.double().mean()),
                         "P_rel_diff_vs_analytic": {"median": pct(rel, 0.5), "p95": pct(rel, 0.95),
                                                    "median_grazing_wz<0.2": pct(rel[graz], 0.5),
-                                                   "median_wz>=0.2": pct(rel[~graz], 0.5)}}}
+                                                   "median_wz>=0.2": pct(rel[~graz], 0.5)},
+                        "breakdown_by_wz": ggx_acc}}
     if acc is not None:
         out["accuracy"] = acc
     if stream_out is not None:
         out["served_stream"] = stream_out
+    return out
+
+
+GGX_WZ_BANDS = ((0.02, 0.1), (0.1, 0.2), (0.2, 0.4), (0.4, 0.7), (0.7, 1.0))
+
+
+def ggx_breakdown(h, g, st, qa, dev, with_nodes=True, per_band=384, nodes_per_level=16, seed=41):
+    """Where the GGX projected area P' = w_z (1 + Lambda') (Eq. 12) departs from
+    the analytic P (Eq. 9-11), per band of w_z.  At query footprints (the fit
+    interpolated between nodes and levels, Gaussian footprint): |P' - P| / P,
+    the odd part |P(w) - P(w~)| / (P(w) + P(w~)) with w~ = (-w_x, -w_y, w_z)
+    (no even model, GGX included, can represent it) and the even-part error
+    |P' - (P(w) + P(w~)) / 2| / P.  At the fit's own footprint (a node's box,
+    the exact P from the oracle at directions between the fit's azimuths):
+    |P'_node - P_node| / P_node, levels 2, 4 and 6."""
+    from paper_2505_08985_gb300 import pndf
+    rng = np.random.default_rng(seed)
+    n = min(per_band, qa.shape[0])
+    q = qa[:n].contiguous()
+    out = {"fit_directions": "16 azimuths at w_z = 0.3", "query_footprints": {}, "node_footprints": {}}
+    for lo, hi in GGX_WZ_BANDS:
+        wz = rng.uniform(lo, hi, n)
+        ph = rng.uniform(0, 2 * np.pi, n)
+        r = np.sqrt(1 - wz * wz)
+        w = torch.tensor(np.stack([r * np.cos(ph), r * np.sin(ph), wz], 1), dtype=torch.float32, device=dev)
+        wf = w.clone()
+        wf[:, :2] = -wf[:, :2]
+        P = pndf.pndf_diffuse_projected_area(h, q, w).double()
+        Pf = pndf.pndf_diffuse_projected_area(h, q, wf).double()
+        Pg = (w[:, 2] * (1.0 + pndf.pndf_ggx_lambda(g, q, w))).double()
+        ok = torch.isfinite(Pg) & (P > 0) & (Pf > 0)
+        P, Pf, Pg = P[ok], Pf[ok], Pg[ok]
+        tot = ((Pg - P).abs() / P).cpu()
+        odd = ((P - Pf).abs() / (P + Pf)).cpu()
+        even = ((Pg - 0.5 * (P + Pf)).abs() / P).cpu()
+        out["query_footprints"][f"{lo}-{hi}"] = {
+            "n": int(ok.sum()), "rel_err_median": float(tot.median()), "rel_err_p95": float(torch.quantile(tot, 0.95)),
+            "odd_part_median": float(odd.median()), "even_part_err_median": float(even.median())}
+    if with_nodes:
+        import oracle
+        from concurrent.futures import ThreadPoolExecutor
+        stc = st.float().cpu()
+        L = pndf.top_level(st.shape[0])
+        dirs = []
+        for lo, hi in GGX_WZ_BANDS:
+            wz = 0.5 * (lo + hi)
+            ph = 2 * np.pi * (np.arange(8) + 0.5) / 8  # between the fit's 16 azimuths
+            dirs.append(np.stack([np.sqrt(1 - wz * wz) * np.cos(ph), np.sqrt(1 - wz * wz) * np.sin(ph),
+                                  np.full(8, wz)], 1))
+        dirs = np.concatenate(dirs)
+        jobs = []
+        for l in (2, 4, 6):
+            S = 1 << (L - l)
+            Om = pndf.pndf_ggx_level(g, l).double().cpu().numpy()
+            for _ in range(nodes_per_level):
+                I, J = (int(v) for v in rng.integers(0, S - 1, 2))
+                if np.isfinite(Om[J, I, 0]):
+                    jobs.append((l, I, J, Om[J, I]))
+
+        def run(job):
+            l, I, J, O = job
+            return job, oracle.ggx_node_P(stc, l, I, J, dirs)
+
+        with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+            res = [r for r in ex.map(run, jobs) if r[1] is not None]
+        for b, (lo, hi) in enumerate(GGX_WZ_BANDS):
+            d = dirs[8 * b:8 * b + 8]
+            errs = []
+            for (l, I, J, O), Pn in res:
+                qf = O[0] * d[:, 0] ** 2 + 2 * O[1] * d[:, 0] * d[:, 1] + O[2] * d[:, 1] ** 2
+                Pp = 0.5 * (d[:, 2] + np.sqrt(np.maximum(d[:, 2] ** 2 + qf, 0.0)))
+                Pn = Pn[8 * b:8 * b + 8]
+                m = Pn > 0
+                errs += list(np.abs(Pp[m] - Pn[m]) / Pn[m])
+            e = np.asarray(errs)
+            out["node_footprints"][f"wz={0.5 * (lo + hi):.2f}"] = {
+                "n": int(e.size), "rel_err_median": float(np.median(e)) if e.size else float("nan"),
+                "rel_err_p95": float(np.quantile(e, 0.95)) if e.size else float("nan")}
+        out["node_sample"] = f"{len(res)} nodes of levels 2, 4, 6; 8 azimuths between the fit's per band"
     return out
 
 
@@ -776,10 +857,19 @@ def run_serving(args, dev):
                          "plain_fp32_sorted": {k: pl[k] for k in keep},
                          "plain_fp32_unsorted": {k: pu[k] for k in keep}})
         batcher.close()
+        # which part of the gap to the plain path is the bound format: the plain
+        # path on the FP16 hierarchies, and the served path on the FP32 ones
+        cap_unsorted16 = serve.run_plain(l16, requests([0.0] * n), realtime=False, sort=pndf.PNDF_SORT_NONE)
+        b32 = serve.ContinuousBatcher(l32, step_queries=tune.step_queries, warps_per_cta=tune.warps_per_cta,
+                                      ctas_per_sm=tune.ctas_per_sm, sort=tune.sort, streams=args.serve_streams)
+        b32.run(requests([0.0] * min(n, 50)), realtime=False)  # warm
+        served_cap32 = b32.run(requests([0.0] * n), realtime=False)
+        b32.close()
         for h in list(h16.values()) + list(h32.values()):
             h.free()
         caps = {"served_fp16": served_cap["queries_per_s"], "plain_fp32_sorted": cap_sorted["queries_per_s"],
-                "plain_fp32_unsorted": cap_unsorted["queries_per_s"]}
+                "plain_fp32_unsorted": cap_unsorted["queries_per_s"],
+                "plain_fp16_unsorted": cap_unsorted16["queries_per_s"], "served_fp32": served_cap32["queries_per_s"]}
         best_plain = max(caps["plain_fp32_sorted"], caps["plain_fp32_unsorted"])
         return {"workload": f"{label}; {n} camera batches, sizes log-U(1K, 1M), {total} queries; Poisson arrivals, "
                             "offered load as a fraction of the sorted plain FP32 capacity",
