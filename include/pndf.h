@@ -281,13 +281,19 @@ pndf_status pndf_cluster_level(const pndf_hierarchy *h, int32_t level, float *re
  * bounding box); zero-area normal triangles are skipped (a delta, not a
  * density); triangles of normal-space area below 1e-10 are tested and
  * weighted in FP64, all others in FP32.  The pyramid only prunes, so the set
- * of contributing triangles equals that of the flat mode.
+ * of contributing triangles equals that of the flat mode.  Each query's sum
+ * is exact: every contribution is rounded once to a multiple of 2^-64 and
+ * added in 128-bit fixed point, and the total is rounded to FP32 once, so D
+ * does not depend on the order of the hits, on the batch, the launch shape or
+ * the division of a large footprint among warps (D = +inf if a sum reaches
+ * 2^63, only possible for normal triangles of area far below 1e-20).
  *   q_dev:          device, nq pndf_query records.
  *   D_out_dev:      device, nq floats, caller order.
  *   flags_out_dev:  device, nq uint32 (PNDF_QF_* bits) or NULL.
  *   stats_dev:      device, nq pndf_query_stats or NULL.
  * nq = 0 is valid and launches nothing.  Scratch memory for the key sort
- * (8 bytes per query plus a histogram of 16 KiB to 1 MiB) is allocated
+ * (8 bytes per query plus a histogram of 16 KiB to 1 MiB) and for dividing
+ * large footprints (1 byte per query plus about 1.7 MB) is allocated
  * stream-ordered from the device's default memory pool and released on the
  * same stream.
  * Errors: INVALID_ARG, OOM, CUDA.  Invalid queries give D = NaN and set
@@ -422,8 +428,10 @@ pndf_status pndf_scatter_results(const float *D_shard_dev, const uint32_t *order
  * different sizes and maps share the GPU.  Each step is a CUDA graph (copy of
  * the segment table from pinned host memory, cursor reset, kernel) replayed
  * with new table contents; table slots rotate, so the host can queue
- * several steps while earlier ones run.  A query's result does not depend on which
- * other segments share its step (one warp evaluates it with a fixed order).
+ * several steps while earlier ones run.  Footprints far larger than the
+ * step's average share per warp are divided among warps as in
+ * pndf_eval_batch.  A query's result does not depend on which other segments
+ * share its step (its sum is exact): it equals pndf_eval_batch's bit for bit.
  * ------------------------------------------------------------------------- */
 
 typedef enum pndf_segment_kind {

@@ -172,6 +172,7 @@ class ContinuousBatcher:
         inflight: deque = deque()
         waiting: list = []
         used = 0
+        submit_s = wait_s = 0.0  # host time forming and launching steps / blocked on the device
         while pending or active or inflight or waiting:
             now = time.perf_counter() - t0
             progressed = False
@@ -183,12 +184,14 @@ class ContinuousBatcher:
                 used += r.n * BYTES_PER_QUERY
                 progressed = True
             if active and len(inflight) < self.max_inflight:
+                ts = time.perf_counter()
                 stream = self.step_streams[self.steps % len(self.step_streams)]
                 ev = torch.cuda.Event(enable_timing=True)
                 segs, fin = self._form_step(active, stream, ev)
                 pndf.pndf_server_step(self.server, segs, stream=stream, ev_done=ev)
                 self.steps += 1
                 inflight.append((ev, fin, segs))
+                submit_s += time.perf_counter() - ts
                 continue
             while inflight and inflight[0][0].query():
                 _, fin, _ = inflight.popleft()
@@ -210,9 +213,13 @@ class ContinuousBatcher:
                 continue
             if inflight and (not pending or not realtime or pending[0].arrival > now + 2e-4 or
                              used + pending[0].n * BYTES_PER_QUERY > self.budget):
+                tw = time.perf_counter()
                 inflight[0][0].synchronize()
+                wait_s += time.perf_counter() - tw
             elif waiting and not inflight:
+                tw = time.perf_counter()
                 waiting[0].slices[0].synchronize()
+                wait_s += time.perf_counter() - tw
             elif pending and realtime:
                 time.sleep(max(0.0, min(pending[0].arrival - (time.perf_counter() - t0), 5e-4)))
         torch.cuda.synchronize(self.device)
@@ -222,7 +229,10 @@ class ContinuousBatcher:
             # a request is done when the last of its slices' steps completes
             r.latency = max(t0_ev.elapsed_time(e) for e in r.slices) / 1e3 - r.arrival
         t_last = max(r.latency + r.arrival for r in reqs)
-        return summarize(reqs, min(r.arrival for r in reqs), t_last)
+        out = summarize(reqs, min(r.arrival for r in reqs), t_last)
+        wall = time.perf_counter() - t0
+        out["host"] = {"submit_s": submit_s, "blocked_on_device_s": wait_s, "wall_s": wall}
+        return out
 
 
 def run_plain(maps, requests, realtime: bool = True, sort: int = pndf.PNDF_SORT_DEFAULT):
@@ -276,12 +286,16 @@ class TuneResult:
 
 
 def autotune(maps, sample, arrivals=None, step_candidates=(1 << 16, 1 << 18, 1 << 20, 1 << 22),
-             cta_candidates=(0,), warp_candidates=(8, 4), sort_candidates=(True, False), streams: int = 2):
+             cta_candidates=(0,), warp_candidates=(8, 4), sort_candidates=(True, False), streams: int = 2,
+             capacity_margin: float = 0.97):
     """Pick step size, launch shape and whether to sort each request for the
-    served path on a sample of requests.  With `arrivals` (a Poisson stream at
-    the target load) the candidate with the lowest p99 latency wins (ties
-    broken by throughput); without, the highest saturated throughput wins."""
-    best = None
+    served path on a sample of requests.  Every candidate's saturated
+    throughput is measured; with `arrivals` (a Poisson stream at the target
+    load) the candidate with the lowest p99 latency wins among those within
+    `capacity_margin` of the best saturated throughput (ties broken by
+    throughput), so a latency gain is not bought with capacity; without, the
+    highest saturated throughput wins."""
+    runs = []
     table = []
     for sort in sort_candidates:
         for ctas in cta_candidates:
@@ -292,17 +306,24 @@ def autotune(maps, sample, arrivals=None, step_candidates=(1 << 16, 1 << 18, 1 <
                     for r in sample:
                         r.arrival = 0.0
                     b.run(sample, realtime=False)  # warm
+                    cap = b.run(sample, realtime=False)["queries_per_s"]
+                    s = None
                     if arrivals is not None:
                         for r, a in zip(sample, arrivals):
                             r.arrival = a
-                    s = b.run(sample, realtime=arrivals is not None)
+                        s = b.run(sample, realtime=True)
                     b.close()
-                    table.append((step, ctas, warps, int(sort), s["p99_ms"], s["queries_per_s"]))
-                    key = (s["p99_ms"], -s["queries_per_s"]) if arrivals is not None else (-s["queries_per_s"],)
-                    if best is None or key < best[0]:
-                        best = (key, TuneResult(step, ctas, warps, s["p99_ms"], s["queries_per_s"], sort))
+                    p99 = s["p99_ms"] if s else math.nan
+                    qps = s["queries_per_s"] if s else cap
+                    table.append((step, ctas, warps, int(sort), p99, qps, cap))
+                    runs.append((TuneResult(step, ctas, warps, p99, qps, sort), cap))
     for r in sample:
         r.arrival = 0.0
-    out = best[1]
+    best_cap = max(c for _, c in runs)
+    if arrivals is not None:
+        ok = [(t, c) for t, c in runs if c >= capacity_margin * best_cap]
+        out = min(ok, key=lambda tc: (tc[0].p99_ms, -tc[1]))[0]
+    else:
+        out = max(runs, key=lambda tc: tc[1])[0]
     out.table = table
     return out
