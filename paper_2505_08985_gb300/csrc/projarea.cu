@@ -349,23 +349,30 @@ __device__ __forceinline__ float2 integrate_band(const MapDesc &d, const Req &q,
                 const float dxl = (float(i) - q.x) + (1.f / 3.f), dxu = (float(i) - q.x) + (2.f / 3.f);
                 const float ql = wq(q, dxl, dyl), qu = wq(q, dxu, dyu);
                 if (ql <= kQCut || qu <= kQCut) {
-                    float2 n0 = texel<TFMT>(d, i, j), n1 = texel<TFMT>(d, i + 1, j);
-                    float2 n2 = texel<TFMT>(d, i, j + 1), n3 = texel<TFMT>(d, i + 1, j + 1);
-                    float z0 = zof(n0), z1 = zof(n1), z2 = zof(n2), z3 = zof(n3);
-                    float r;
-                    if (ql <= kQCut) {
-                        kw[0] = q.norm * expf(-0.5f * ql);
-                        if (tri_ratio_fast(n0, z0, n1, z1, n2, z2, w, r))
-                            v[0] = kw[0] * r;
-                        else
-                            dfr[0] = true;
-                    }
-                    if (qu <= kQCut) {
-                        kw[1] = q.norm * expf(-0.5f * qu);
-                        if (tri_ratio_fast(n3, z3, n2, z2, n1, z1, w, r))
-                            v[1] = kw[1] * r;
-                        else
-                            dfr[1] = true;
+                    // one copy of the triangle path for both triangles (tri 0 =
+                    // (u0, u1, u2), tri 1 = (u3, u2, u1)): unrolled, the kernel
+                    // stalled on instruction fetch (516 ms against 386 ms)
+                    const float2 n1 = texel<TFMT>(d, i + 1, j), n2 = texel<TFMT>(d, i, j + 1);
+                    const float z1 = zof(n1), z2 = zof(n2);
+#pragma unroll 1
+                    for (int k = 0; k < 2; ++k) {
+                        const float qk = k ? qu : ql;
+                        if (qk > kQCut) continue;
+                        const float2 na = texel<TFMT>(d, i + k, j + k);
+                        const float2 nb = k ? n2 : n1, nc = k ? n1 : n2;
+                        const float zb = k ? z2 : z1, zc = k ? z1 : z2;
+                        float r;
+                        const float kk = q.norm * expf(-0.5f * qk);
+                        const bool ok = tri_ratio_fast(na, zof(na), nb, zb, nc, zc, w, r);
+                        if (k) {
+                            kw[1] = kk;
+                            v[1] = ok ? kk * r : 0.f;
+                            dfr[1] = !ok;
+                        } else {
+                            kw[0] = kk;
+                            v[0] = ok ? kk * r : 0.f;
+                            dfr[0] = !ok;
+                        }
                     }
                 }
             }
@@ -413,8 +420,11 @@ __device__ __forceinline__ float2 integrate_band(const MapDesc &d, const Req &q,
     return make_float2(s, c);
 }
 
+// Eight CTAs per SM (32 registers, some spilled): 285 ms against 319 ms at
+// six and 516 ms at two for 1,024 requests on a 4096^2 mixed map; the warps
+// that wait on the FP64 path need company to keep the SM issuing.
 template <int TFMT>
-__global__ void __launch_bounds__(256) pa_items(MapDesc d, const pndf_query *__restrict__ qs,
+__global__ void __launch_bounds__(256, 8) pa_items(MapDesc d, const pndf_query *__restrict__ qs,
                                                const float *__restrict__ omega, int64_t k0, int cnt,
                                                const uint32_t *__restrict__ off, float2 *__restrict__ part,
                                                unsigned int *__restrict__ cursor)
@@ -511,7 +521,7 @@ __global__ void __launch_bounds__(1024) area_step_scan(const uint32_t *__restric
 }
 
 template <int TFMT>
-__global__ void __launch_bounds__(256) area_step_items(const MapDesc *__restrict__ maps, int nmaps,
+__global__ void __launch_bounds__(256, 8) area_step_items(const MapDesc *__restrict__ maps, int nmaps,
                                                       const uint32_t *__restrict__ count,
                                                       const AreaReq *__restrict__ areq,
                                                       const uint32_t *__restrict__ off, float2 *__restrict__ part,
@@ -656,8 +666,10 @@ __device__ __forceinline__ void leaf_triangle(const MapDesc &d, int i0, int j0, 
 constexpr int kGgxLeafWarps = 8;
 static_assert(kGgxDirs <= 16, "a listed pair packs the direction in 4 bits");
 
+// Eight CTAs per SM: 68 ms against 75 ms at the register-limited two for a
+// 4096^2 map (FP64 pairs dominate; more warps keep the FP64 pipe fed).
 template <int TFMT>
-__global__ void __launch_bounds__(32 * kGgxLeafWarps) ggx_leaf(MapDesc d, GgxDirs dirs,
+__global__ void __launch_bounds__(32 * kGgxLeafWarps, 8) ggx_leaf(MapDesc d, GgxDirs dirs,
                                                                float *__restrict__ P, float4 *__restrict__ omega,
                                                                uint32_t nleaf)
 {
