@@ -287,14 +287,15 @@ class TuneResult:
 
 def autotune(maps, sample, arrivals=None, step_candidates=(1 << 16, 1 << 18, 1 << 20, 1 << 22),
              cta_candidates=(0,), warp_candidates=(8, 4), sort_candidates=(True, False), streams: int = 2,
-             capacity_margin: float = 0.97):
+             capacity_margin: float = 0.97, p99_margin: float = 1.05):
     """Pick step size, launch shape and whether to sort each request for the
     served path on a sample of requests.  Every candidate's saturated
     throughput is measured; with `arrivals` (a Poisson stream at the target
-    load) the candidate with the lowest p99 latency wins among those within
-    `capacity_margin` of the best saturated throughput (ties broken by
-    throughput), so a latency gain is not bought with capacity; without, the
-    highest saturated throughput wins."""
+    load) the candidates within `capacity_margin` of the best saturated
+    throughput qualify (a latency gain is not bought with capacity), and among
+    those whose p99 is within `p99_margin` of the lowest (differences below
+    that are run-to-run noise) the highest saturated throughput wins;
+    without, the highest saturated throughput wins."""
     runs = []
     table = []
     for sort in sort_candidates:
@@ -322,7 +323,8 @@ def autotune(maps, sample, arrivals=None, step_candidates=(1 << 16, 1 << 18, 1 <
     best_cap = max(c for _, c in runs)
     if arrivals is not None:
         ok = [(t, c) for t, c in runs if c >= capacity_margin * best_cap]
-        out = min(ok, key=lambda tc: (tc[0].p99_ms, -tc[1]))[0]
+        p99 = min(t.p99_ms for t, _ in ok)
+        out = max((tc for tc in ok if tc[0].p99_ms <= p99_margin * p99), key=lambda tc: tc[1])[0]
     else:
         out = max(runs, key=lambda tc: tc[1])[0]
     out.table = table
