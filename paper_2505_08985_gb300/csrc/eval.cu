@@ -27,9 +27,12 @@
 //               the tight bound for slivers across normal discontinuities);
 //               capsule survivors are compacted again and tested 32 at a
 //               time (lane = quad, both triangles), and edge-test hits are
-//               compacted once more and weighed 32 at a time.  The query's
-//               sum is reduced across the warp and written in caller order
-//               (the unpermute is fused into the store).  Flat mode skips
+//               compacted once more and weighed 32 at a time.  Each weight
+//               is added exactly into the thread's 128-bit fixed-point sum;
+//               the warp's sums are added exactly and the total is written in
+//               caller order (the unpermute is fused into the store).  Large
+//               footprints of a batch are divided into tiles of nodes, one
+//               warp per tile (split_work / split_plan).  Flat mode skips
 //               every box and tests all 32 triangles of every leaf block in
 //               the support's bounding box.
 // Hit test (tie rule): m inside the closed normal bounding box and all three

@@ -287,7 +287,7 @@ class TuneResult:
 
 def autotune(maps, sample, arrivals=None, step_candidates=(1 << 16, 1 << 18, 1 << 20, 1 << 22),
              cta_candidates=(0,), warp_candidates=(8, 4), sort_candidates=(True, False), streams: int = 2,
-             capacity_margin: float = 0.97, p99_margin: float = 1.05):
+             capacity_margin: float = 0.97, p99_margin: float = 1.05, capacity_sample=None):
     """Pick step size, launch shape and whether to sort each request for the
     served path on a sample of requests.  Every candidate's saturated
     throughput is measured; with `arrivals` (a Poisson stream at the target
@@ -295,7 +295,9 @@ def autotune(maps, sample, arrivals=None, step_candidates=(1 << 16, 1 << 18, 1 <
     throughput qualify (a latency gain is not bought with capacity), and among
     those whose p99 is within `p99_margin` of the lowest (differences below
     that are run-to-run noise) the highest saturated throughput wins;
-    without, the highest saturated throughput wins."""
+    without, the highest saturated throughput wins.  The saturated throughput
+    is measured on `capacity_sample` when given (a longer run ranks step
+    sizes more reliably than the latency sample)."""
     runs = []
     table = []
     for sort in sort_candidates:
@@ -307,7 +309,7 @@ def autotune(maps, sample, arrivals=None, step_candidates=(1 << 16, 1 << 18, 1 <
                     for r in sample:
                         r.arrival = 0.0
                     b.run(sample, realtime=False)  # warm
-                    cap = b.run(sample, realtime=False)["queries_per_s"]
+                    cap = b.run(capacity_sample or sample, realtime=False)["queries_per_s"]
                     s = None
                     if arrivals is not None:
                         for r, a in zip(sample, arrivals):
