@@ -80,6 +80,8 @@ def summarize(reqs, t_first, t_last):
 class ContinuousBatcher:
     """Continuous batching over `maps` (same texel and bounds formats)."""
 
+    _queued = 0  # queries admitted and not yet in a step (reset per run)
+
     def __init__(self, maps, step_queries: int = 1 << 20, memory_budget: int = 2 << 30, max_segments: int = 1024,
                  warps_per_cta: int = 0, ctas_per_sm: int = 0, slots: int = 4, sort: bool = True,
                  kernel: int = pndf.PNDF_KERNEL_GAUSS, tau: float = 0.0, jac_eps: float = 0.0, streams: int = 2,
@@ -141,6 +143,7 @@ class ContinuousBatcher:
                 stream.wait_event(r.ready)
                 r.waited.append(stream)
             take = min(r.n - r.next, room)
+            self._queued -= take
             seg = (r.map, r.queries, r.order, r.D, None, r.next, take)
             segs.append(seg + (r.kind, r.omega) if is_area else seg)
             r.slices.append(ev)
@@ -160,6 +163,7 @@ class ContinuousBatcher:
         reqs = sorted(requests, key=lambda r: r.arrival)
         for r in reqs:
             r.next, r.waited, r.done, r.latency, r.slices = 0, [], None, math.nan, []
+        self._queued = 0
         torch.cuda.synchronize(self.device)
         t0_ev = torch.cuda.Event(enable_timing=True)
         t0_ev.record(self.step_stream)
@@ -173,15 +177,19 @@ class ContinuousBatcher:
         waiting: list = []
         used = 0
         submit_s = wait_s = 0.0  # host time forming and launching steps / blocked on the device
+        # admit only what the steps that can be in flight will take, so the
+        # first steps start while later requests are still being admitted
+        ahead = (self.max_inflight + 1) * self.step_queries
         while pending or active or inflight or waiting:
             now = time.perf_counter() - t0
             progressed = False
-            while pending and (not realtime or pending[0].arrival <= now) and \
+            while pending and (not realtime or pending[0].arrival <= now) and self._queued < ahead and \
                     (used + pending[0].n * BYTES_PER_QUERY <= self.budget or (not active and not inflight)):
                 r = pending.popleft()
                 self._admit(r)
                 active.append(r)
                 used += r.n * BYTES_PER_QUERY
+                self._queued += r.n
                 progressed = True
             if active and len(inflight) < self.max_inflight:
                 ts = time.perf_counter()
