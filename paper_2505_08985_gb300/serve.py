@@ -1,24 +1,26 @@
 """Continuous-batching P-NDF serving over several resident hierarchies.
 
-Requests (a batch of queries on one map) arrive over time.  The batcher
-admits arrived requests while their working buffers (evaluation order and
-results, 8 bytes per query) fit a device-memory budget, optionally sorts each
-once on a copy stream (queries that arrive in a coherent order, such as a
-camera's pixels, run faster as they come; the autotuner decides), and runs
-steps: each step takes up to `step_queries` queries from
-the admitted requests in arrival order (a large request spans several steps;
-small ones share a step) and evaluates them in one persistent kernel launch
-replayed from a CUDA graph (pndf_server_step).  Up to slots - 1 steps are in flight,
-so requests that arrive while the GPU works are admitted and joined to the
-next step as soon as memory frees up.
+Requests (a batch of P-NDF queries, or of projected-area requests, on one
+map) arrive over time.  The batcher admits arrived requests while their
+working buffers (evaluation order and results, 8 bytes per query) fit a
+device-memory budget and the admitted work not yet in a step stays under
+what the in-flight steps can take (so a burst does not hold the GPU idle
+while it is admitted), optionally sorts each once on a copy stream (queries
+that arrive in a coherent order, such as a camera's pixels, run faster as
+they come; the autotuner decides), and runs steps: each step takes up to
+`step_queries` P-NDF queries and `max_area_requests` projected-area requests
+from the admitted requests in arrival order (a large request spans several
+steps; small ones share a step) and evaluates them in one graph-replayed step
+(pndf_server_step).  Steps alternate over two streams and up to slots - 1 are
+in flight, so requests that arrive while the GPU works join the next step.
 
 A request's latency runs from its arrival to the device completion of the step
 that holds its last queries, on one clock: the device timeline anchored by an
 event recorded when the run starts.
 
-The plain baseline launches each batch alone with pndf_eval_batch (FP32
-bounds, no graphs, no sharing of launches, the library's default query sort)
-in arrival order.
+The plain baseline launches each batch alone with pndf_eval_batch (or
+pndf_diffuse_projected_area) in arrival order: no graphs, no sharing of
+launches, with the library's default query sort or none.
 """
 
 from __future__ import annotations
