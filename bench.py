@@ -74,7 +74,7 @@ def parse():
                     help="further offered loads for the latency sweep ('' = skip)")
     ap.add_argument("--mixed-requests", type=int, default=4096,
                     help="projected-area + P-NDF sample on the 16384^2 FP16 map (0 = skip)")
-    ap.add_argument("--mixed-stream-batches", type=int, default=64,
+    ap.add_argument("--mixed-stream-batches", type=int, default=256,
                     help="served glint + diffuse stream on the mixed map: batches, half P-NDF and half projected "
                          "area (0 = skip)")
     ap.add_argument("--mixed-map-size", type=int, default=synth.MIXED_16384["n"],
