@@ -389,7 +389,7 @@ def workload_config(n: int, nq: int, world: int) -> dict:
             "queries_per_gpu": nq, "sigma": "log-uniform 1..512 texels, isotropic",
             "bounds": "fp16 outward-rounded", "leaf_math": "fp32 (fp64 below 1e-10 area)",
             "l2": "inputs larger than L2 (512 MiB texels + 128 MiB queries re-read each step)",
-            "step": "rebuild pyramid + key/sort + traverse/leaf + unpermute", "parallelism": f"replicas x{world}"}
+            "step": "rebuild pyramid + key/sort + split plan + traverse/leaf + unpermute", "parallelism": f"replicas x{world}"}
 
 
 def make_workload(args, device, rank):
