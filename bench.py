@@ -330,7 +330,7 @@ def committed_profile_value(key: str):
 def traversal_roofline(dev, work_f16: dict, nq: int, kernel_ms: float, world: int) -> dict:
     """Roofline of the dominant kernel (traversal + leaf test) per launch.
 
-    HBM, on the survey's byte model (Sec. 8(d)): every visited node's box
+    HBM, on the path's byte model: every visited node's box
     (8 B in binary16) + every leaf block's (b + 1)^2 = 25 texels (8 B each,
     FP32) + the query's 32 B record and 4 B result.  Instruction issue, on the
     warp instructions per query of the committed ncu capture of the same
@@ -1354,7 +1354,7 @@ def kernel_rooflines(dev, n, nq, stage_ms, traverse_ms, traverse_roof, cluster, 
     read and its copy written (8 B each per texel) plus every FP16 box written
     (8 B); query sort, the 32 B record read, the key written and read back
     and the order slot written (4 B each); traversal, as in `roofline` (the
-    survey's byte model, and instruction issue from the committed capture);
+    path's byte model, and instruction issue from the committed capture);
     sampling, record, uniforms, four texels and the outputs (88 B); Lambda',
     record, direction and result (48 B) plus the 12 B Omega of the eight
     nodes it blends (96 B); cluster fit, the map read (8 B per texel) and the

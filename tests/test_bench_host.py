@@ -79,7 +79,7 @@ def test_source_hash_follows_code_not_comments(bench, tmp_path, monkeypatch):
     assert bench.sources_hash(["k.cu"]) != h0
 
 
-def test_traversal_roofline_follows_the_survey_byte_model(bench, monkeypatch):
+def test_traversal_roofline_follows_the_path_byte_model(bench, monkeypatch):
     """roofline.frac is reproducible from the stats counts: HBM on nodes x 8 B
     + leaf blocks x 25 texels x 8 B + 36 B per query; with a committed
     instruction count the issue fraction is computed beside it and `bound`
