@@ -351,14 +351,16 @@ __device__ __forceinline__ float2 integrate_band(const MapDesc &d, const Req &q,
                 if (ql <= kQCut || qu <= kQCut) {
                     // one copy of the triangle path for both triangles (tri 0 =
                     // (u0, u1, u2), tri 1 = (u3, u2, u1)): unrolled, the kernel
-                    // stalled on instruction fetch (516 ms against 386 ms)
+                    // stalled on instruction fetch (516 ms against 386 ms); the
+                    // quad's four texels are loaded together
                     const float2 n1 = texel<TFMT>(d, i + 1, j), n2 = texel<TFMT>(d, i, j + 1);
+                    const float2 n0 = texel<TFMT>(d, i, j), n3 = texel<TFMT>(d, i + 1, j + 1);
                     const float z1 = zof(n1), z2 = zof(n2);
 #pragma unroll 1
                     for (int k = 0; k < 2; ++k) {
                         const float qk = k ? qu : ql;
                         if (qk > kQCut) continue;
-                        const float2 na = texel<TFMT>(d, i + k, j + k);
+                        const float2 na = k ? n3 : n0;
                         const float2 nb = k ? n2 : n1, nc = k ? n1 : n2;
                         const float zb = k ? z2 : z1, zc = k ? z1 : z2;
                         float r;
