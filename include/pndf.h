@@ -314,8 +314,10 @@ pndf_status pndf_eval_batch_ex(const pndf_hierarchy *h, const pndf_query *q_dev,
  * this serves callers that may not allocate device memory, such as a
  * renderer plugin whose host owns all device allocations, a real-time thread
  * that cannot take cudaMalloc's device-wide synchronisation, or code with a
- * fixed device-memory budget).  Same result as pndf_eval_batch with the
- * default configuration, for at most pndf_eval_noalloc_max_queries()
+ * fixed device-memory budget).  Same result, bit for bit, as
+ * pndf_eval_batch with the default configuration (it evaluates every query
+ * with one warp, as it has no scratch to divide large footprints), for at
+ * most pndf_eval_noalloc_max_queries()
  * (1,048,576) queries per call; larger batches return PNDF_ERR_CAPACITY
  * before any work is queued.  The sort scratch is one fixed device array
  * (about 9.4 MB) that every GPU loading the library holds until the process
